@@ -1,0 +1,489 @@
+/*
+ * Plain, slow, obviously-correct FP64 CPU oracle for the sparse SPD solver path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, the smoke check and the CPU-baseline
+ * leg of the benchmark may load this library.  The product path never calls it,
+ * and it shares no code, header, table or constant with the CUDA library.
+ *
+ * Build: gcc -O2 -ffp-contract=off -std=c11 -fPIC -shared oracle.c -lm
+ * (-ffp-contract=off matters: a fused multiply-add would change the rounding
+ *  of every product-then-sum below, and gcc fuses by default on aarch64.)
+ *
+ * Functions and the passages they follow (paper: PETSc/TAO developments for
+ * GPU-based early exascale systems):
+ *   orc_coo_symbolic / orc_coo_numeric  -- Sec. 5, the COO definition: the
+ *       assembled A is the sum of the contributions v[k] to a_{i[k],j[k]};
+ *       negative indices mean "ignore this entry"; MatSetPreallocationCOO fixes
+ *       the pattern, MatSetValuesCOO(v, mode) fills values.
+ *   orc_spmv           -- the MatMult of Sec. 6.1: y = A x on CSR.
+ *   orc_pcg            -- the KSP CG of Sec. 6.1 with the diagonal (Jacobi)
+ *       preconditioner the batched solvers of Sec. 7 use; textbook
+ *       Hestenes-Stiefel preconditioned CG (the paper relies on PETSc's CG and
+ *       does not restate it).
+ *   orc_pcg_refined    -- the single-precision inner solve under a double
+ *       precision outer solve motivated in Sec. 2 (multiprecision, A7):
+ *       FP32 PCG inside FP64 iterative refinement.
+ *   orc_adjoint_*      -- the adjoint capability mentioned in Sec. 1, for a
+ *       linear solve: A^T lambda = g, dL/da_ij = -lambda_i x_j, dL/db = lambda.
+ *   orc_pcg_batched    -- Sec. 7: many independent systems, each solved on its
+ *       own (per-system scalars and convergence).
+ *
+ * Parity pins: every function here is pinned by tests/test_oracle_*.py against
+ * dense brute force, closed forms (Laplacian eigenpairs, the Q1 stencil),
+ * finite differences and invariants; see those tests for the list.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* status codes (numerically the same values the public C-ABI documents) */
+enum {
+  ORC_OK = 0,
+  ORC_ERR_ARG = 1,
+  ORC_ERR_INDEX = 2,
+  ORC_ERR_ALLOC = 3,
+  ORC_ERR_NOT_SPD = 5,
+  ORC_ERR_BREAKDOWN = 6,
+  ORC_ERR_NAN = 7,
+  ORC_ERR_MAXIT = 8,
+  ORC_ERR_STAGNATION = 9
+};
+
+typedef struct {
+  int32_t status, iterations, outer_iterations, pad;
+  double rnorm0, rnorm, true_rel_residual;
+} orc_result;
+
+/* ------------------------------------------------------------------------ */
+/* O1: COO -> CSR, symbolic                                                  */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int32_t i, j;
+  int64_t k;
+} orc_trip;
+
+static int cmp_trip(const void *pa, const void *pb) {
+  const orc_trip *a = (const orc_trip *)pa, *b = (const orc_trip *)pb;
+  if (a->i != b->i) return a->i < b->i ? -1 : 1;
+  if (a->j != b->j) return a->j < b->j ? -1 : 1;
+  if (a->k != b->k) return a->k < b->k ? -1 : 1; /* keeps the sort stable */
+  return 0;
+}
+
+/*
+ * Kept set K = {k : i[k] >= 0 and j[k] >= 0}.  A kept index outside
+ * [0,nrows) x [0,ncols) is an error.  The pattern is the set of distinct (i,j)
+ * over K, rows ascending and columns strictly ascending within a row.
+ * Outputs (caller-allocated):
+ *   row_ptr[nrows+1], col[>= nnz], perm[>= nkept] (sorted position -> original
+ *   COO index k), jmap[>= nnz+1] (segment p of the sorted kept entries is
+ *   [jmap[p], jmap[p+1]) ).
+ * Returns nnz >= 0, or -status on error.
+ */
+int64_t orc_coo_symbolic(int64_t nrows, int64_t ncols, int64_t ncoo,
+                         const int32_t *ci, const int32_t *cj, int32_t *row_ptr,
+                         int32_t *col, int32_t *perm, int32_t *jmap,
+                         int64_t *nkept_out) {
+  if (nrows < 0 || ncols < 0 || ncoo < 0) return -ORC_ERR_ARG;
+  int64_t nkept = 0;
+  for (int64_t k = 0; k < ncoo; ++k) {
+    if (ci[k] < 0 || cj[k] < 0) continue;
+    if ((int64_t)ci[k] >= nrows || (int64_t)cj[k] >= ncols) return -ORC_ERR_INDEX;
+    ++nkept;
+  }
+  orc_trip *t = (orc_trip *)malloc((size_t)(nkept > 0 ? nkept : 1) * sizeof(orc_trip));
+  if (!t) return -ORC_ERR_ALLOC;
+  int64_t m = 0;
+  for (int64_t k = 0; k < ncoo; ++k) {
+    if (ci[k] < 0 || cj[k] < 0) continue;
+    t[m].i = ci[k];
+    t[m].j = cj[k];
+    t[m].k = k;
+    ++m;
+  }
+  qsort(t, (size_t)nkept, sizeof(orc_trip), cmp_trip);
+
+  for (int64_t r = 0; r <= nrows; ++r) row_ptr[r] = 0;
+  int64_t nnz = 0;
+  for (int64_t s = 0; s < nkept; ++s) {
+    int head = (s == 0) || t[s].i != t[s - 1].i || t[s].j != t[s - 1].j;
+    if (head) {
+      col[nnz] = t[s].j;
+      jmap[nnz] = (int32_t)s;
+      row_ptr[t[s].i + 1] += 1; /* count of pattern entries in row i */
+      ++nnz;
+    }
+    perm[s] = (int32_t)t[s].k;
+  }
+  jmap[nnz] = (int32_t)nkept;
+  for (int64_t r = 0; r < nrows; ++r) row_ptr[r + 1] += row_ptr[r];
+  free(t);
+  if (nkept_out) *nkept_out = nkept;
+  return nnz;
+}
+
+/* ------------------------------------------------------------------------ */
+/* O1: COO -> CSR, numeric                                                   */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * a_p = left fold of v over the segment's original indices, in increasing k,
+ * starting from the first term (so a lone -0.0 stays -0.0).
+ * mode 0 = INSERT (a_p replaces), mode 1 = ADD (a_p is added to val[p]).
+ */
+void orc_coo_numeric(int64_t nnz, const int32_t *jmap, const int32_t *perm,
+                     const double *v, int mode, double *val) {
+  for (int64_t p = 0; p < nnz; ++p) {
+    double s = v[perm[jmap[p]]];
+    for (int64_t t = (int64_t)jmap[p] + 1; t < jmap[p + 1]; ++t) s = s + v[perm[t]];
+    val[p] = (mode == 1) ? val[p] + s : s;
+  }
+}
+
+/* dL/dv_k = dL/da_{p(k)} for kept k, 0 for ignored k (transpose of the above) */
+void orc_coo_scatter(int64_t nnz, int64_t ncoo, const int32_t *jmap,
+                     const int32_t *perm, const double *dlda, double *dldv) {
+  for (int64_t k = 0; k < ncoo; ++k) dldv[k] = 0.0;
+  for (int64_t p = 0; p < nnz; ++p)
+    for (int64_t t = jmap[p]; t < jmap[p + 1]; ++t) dldv[perm[t]] = dlda[p];
+}
+
+/* ------------------------------------------------------------------------ */
+/* O2: SpMV                                                                  */
+/* ------------------------------------------------------------------------ */
+
+void orc_spmv(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
+              const double *x, double *y) {
+  for (int64_t i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) s += a[p] * x[ci[p]];
+    y[i] = s;
+  }
+}
+
+static void spmv32(int64_t n, const int32_t *rp, const int32_t *ci,
+                   const float *a, const float *x, float *y) {
+  for (int64_t i = 0; i < n; ++i) {
+    float s = 0.0f;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) s += a[p] * x[ci[p]];
+    y[i] = s;
+  }
+}
+
+static double dot(int64_t n, const double *x, const double *y) {
+  double s = 0.0;
+  for (int64_t i = 0; i < n; ++i) s += x[i] * y[i];
+  return s;
+}
+
+static float dot32(int64_t n, const float *x, const float *y) {
+  float s = 0.0f;
+  for (int64_t i = 0; i < n; ++i) s += x[i] * y[i];
+  return s;
+}
+
+/* Jacobi: dinv_i = 1/a_ii; missing or non-positive diagonal is an error. */
+static int jacobi(int64_t n, const int32_t *rp, const int32_t *ci,
+                  const double *a, double *dinv) {
+  for (int64_t i = 0; i < n; ++i) {
+    double d = 0.0;
+    int found = 0;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p)
+      if (ci[p] == i) {
+        d = a[p];
+        found = 1;
+      }
+    if (!found || !(d > 0.0)) return ORC_ERR_NOT_SPD;
+    dinv[i] = 1.0 / d;
+  }
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* O3: Jacobi-preconditioned CG                                              */
+/* ------------------------------------------------------------------------ */
+
+static double true_rel(int64_t n, const int32_t *rp, const int32_t *ci,
+                       const double *a, const double *b, const double *x,
+                       double bnorm, double *work) {
+  orc_spmv(n, rp, ci, a, x, work);
+  for (int64_t i = 0; i < n; ++i) work[i] = b[i] - work[i];
+  double rn = sqrt(dot(n, work, work));
+  return bnorm > 0.0 ? rn / bnorm : rn;
+}
+
+/*
+ * Solve A x = b.  x holds the initial guess when nonzero_guess, else starts at
+ * 0.  Stops when ||r||_2 <= rtol ||b||_2 (r the recursively updated residual),
+ * checked before every product q = A p; iterations = number of such products.
+ */
+int orc_pcg(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
+            const double *b, double *x, double rtol, int64_t maxit,
+            int nonzero_guess, orc_result *res) {
+  memset(res, 0, sizeof(*res));
+  double *dinv = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double) * 5);
+  if (!dinv) return res->status = ORC_ERR_ALLOC;
+  double *r = dinv + n, *z = r + n, *p = z + n, *q = p + n;
+  int st = jacobi(n, rp, ci, a, dinv);
+  if (st != ORC_OK) {
+    free(dinv);
+    return res->status = st;
+  }
+  if (!nonzero_guess)
+    for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+  double bnorm = sqrt(dot(n, b, b));
+  if (!isfinite(bnorm)) {
+    free(dinv);
+    return res->status = ORC_ERR_NAN;
+  }
+  if (bnorm == 0.0) {
+    for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+    free(dinv);
+    return res->status = ORC_OK;
+  }
+  orc_spmv(n, rp, ci, a, x, r);
+  for (int64_t i = 0; i < n; ++i) r[i] = b[i] - r[i];
+  for (int64_t i = 0; i < n; ++i) z[i] = dinv[i] * r[i];
+  for (int64_t i = 0; i < n; ++i) p[i] = z[i];
+  double rho = dot(n, r, z);
+  double rr = dot(n, r, r);
+  res->rnorm0 = sqrt(rr);
+  int64_t it = 0;
+  st = ORC_OK;
+  for (;;) {
+    double rnorm = sqrt(rr);
+    res->rnorm = rnorm;
+    if (!isfinite(rnorm) || !isfinite(rho)) {
+      st = ORC_ERR_NAN;
+      break;
+    }
+    if (rnorm <= rtol * bnorm) break;
+    if (it >= maxit) {
+      st = ORC_ERR_MAXIT;
+      break;
+    }
+    orc_spmv(n, rp, ci, a, p, q);
+    double sigma = dot(n, p, q);
+    ++it;
+    if (isnan(sigma)) {
+      st = ORC_ERR_NAN;
+      break;
+    }
+    if (!(sigma > 0.0)) {
+      st = ORC_ERR_BREAKDOWN;
+      break;
+    }
+    double alpha = rho / sigma;
+    for (int64_t i = 0; i < n; ++i) x[i] += alpha * p[i];
+    for (int64_t i = 0; i < n; ++i) r[i] -= alpha * q[i];
+    for (int64_t i = 0; i < n; ++i) z[i] = dinv[i] * r[i];
+    double rho_new = dot(n, r, z);
+    rr = dot(n, r, r);
+    double beta = rho_new / rho;
+    for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+    rho = rho_new;
+  }
+  res->iterations = (int32_t)it;
+  res->true_rel_residual = true_rel(n, rp, ci, a, b, x, bnorm, q);
+  free(dinv);
+  return res->status = st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* O4: FP32 inner PCG inside FP64 iterative refinement                       */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Outer (FP64): r = b - A64 x; stop when ||r|| <= rtol ||b||; s = ||r||.
+ * Inner (FP32 values, vectors and accumulation): Jacobi-PCG on A32 d = RN(r/s)
+ * from d = 0 until ||r_in|| <= inner_rtol ||r_in,0||, inner_maxit products, or
+ * a non-positive / non-finite sigma.  Update x += s * d in FP64.
+ * Stagnation: ||r|| fails to halve on two consecutive outer steps.
+ * A32 = RN(A64) elementwise; dinv32 = RN(1/a_ii) with the reciprocal in FP64.
+ */
+int orc_pcg_refined(int64_t n, const int32_t *rp, const int32_t *ci,
+                    const double *a, const double *b, double *x, double rtol,
+                    double inner_rtol, int64_t inner_maxit, int32_t max_outer,
+                    int nonzero_guess, orc_result *res) {
+  memset(res, 0, sizeof(*res));
+  int64_t nnz = rp[n];
+  double *dinv = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double) * 2);
+  float *f = (float *)malloc((size_t)(n > 0 ? n : 1) * sizeof(float) * 6 +
+                             (size_t)(nnz > 0 ? nnz : 1) * sizeof(float));
+  if (!dinv || !f) {
+    free(dinv);
+    free(f);
+    return res->status = ORC_ERR_ALLOC;
+  }
+  double *r = dinv + n;
+  float *dinv32 = f, *r32 = f + n, *z32 = r32 + n, *p32 = z32 + n, *q32 = p32 + n,
+        *d32 = q32 + n, *a32 = d32 + n;
+  int st = jacobi(n, rp, ci, a, dinv);
+  if (st != ORC_OK) goto done;
+  for (int64_t i = 0; i < n; ++i) dinv32[i] = (float)dinv[i];
+  for (int64_t p = 0; p < nnz; ++p) a32[p] = (float)a[p];
+  if (!nonzero_guess)
+    for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+  double bnorm = sqrt(dot(n, b, b));
+  if (!isfinite(bnorm)) {
+    st = ORC_ERR_NAN;
+    goto done;
+  }
+  if (bnorm == 0.0) {
+    for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+    goto done;
+  }
+  double prev = INFINITY;
+  int stall = 0;
+  int32_t outer = 0;
+  int64_t inner_total = 0;
+  for (;;) {
+    orc_spmv(n, rp, ci, a, x, r);
+    for (int64_t i = 0; i < n; ++i) r[i] = b[i] - r[i];
+    double rn = sqrt(dot(n, r, r));
+    if (outer == 0) res->rnorm0 = rn;
+    res->rnorm = rn;
+    if (!isfinite(rn)) {
+      st = ORC_ERR_NAN;
+      break;
+    }
+    if (rn <= rtol * bnorm) break;
+    if (outer >= max_outer) {
+      st = ORC_ERR_MAXIT;
+      break;
+    }
+    if (outer > 0) {
+      stall = (rn > 0.5 * prev) ? stall + 1 : 0;
+      if (stall >= 2) {
+        st = ORC_ERR_STAGNATION;
+        break;
+      }
+    }
+    prev = rn;
+    double s = rn;
+    for (int64_t i = 0; i < n; ++i) r32[i] = (float)(r[i] / s);
+    /* inner FP32 Jacobi-PCG from d = 0 */
+    for (int64_t i = 0; i < n; ++i) d32[i] = 0.0f;
+    for (int64_t i = 0; i < n; ++i) z32[i] = dinv32[i] * r32[i];
+    for (int64_t i = 0; i < n; ++i) p32[i] = z32[i];
+    float rho = dot32(n, r32, z32);
+    float rr = dot32(n, r32, r32);
+    float r0 = sqrtf(rr);
+    int64_t it = 0;
+    for (;;) {
+      if (!(sqrtf(rr) > inner_rtol * r0)) break; /* also ends on NaN */
+      if (it >= inner_maxit) break;
+      spmv32(n, rp, ci, a32, p32, q32);
+      float sigma = dot32(n, p32, q32);
+      if (!(sigma > 0.0f)) break;
+      ++it;
+      float alpha = rho / sigma;
+      for (int64_t i = 0; i < n; ++i) d32[i] += alpha * p32[i];
+      for (int64_t i = 0; i < n; ++i) r32[i] -= alpha * q32[i];
+      for (int64_t i = 0; i < n; ++i) z32[i] = dinv32[i] * r32[i];
+      float rho_new = dot32(n, r32, z32);
+      rr = dot32(n, r32, r32);
+      float beta = rho_new / rho;
+      for (int64_t i = 0; i < n; ++i) p32[i] = z32[i] + beta * p32[i];
+      rho = rho_new;
+    }
+    if (it == 0) {
+      st = ORC_ERR_BREAKDOWN;
+      break;
+    }
+    inner_total += it;
+    for (int64_t i = 0; i < n; ++i) x[i] += s * (double)d32[i];
+    ++outer;
+  }
+  res->iterations = (int32_t)inner_total;
+  res->outer_iterations = outer;
+  res->true_rel_residual = true_rel(n, rp, ci, a, b, x, bnorm, r);
+done:
+  free(dinv);
+  free(f);
+  return res->status = st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* O5: adjoint of x = A^{-1} b                                               */
+/* ------------------------------------------------------------------------ */
+
+/* 1 if the CSR matrix equals its transpose exactly (pattern and values). */
+int orc_csr_is_symmetric(int64_t n, const int32_t *rp, const int32_t *ci,
+                         const double *a) {
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      int64_t j = ci[p];
+      int found = 0;
+      for (int64_t t = rp[j]; t < rp[j + 1]; ++t)
+        if (ci[t] == i) {
+          found = (a[t] == a[p]);
+          break;
+        }
+      if (!found) return 0;
+    }
+  return 1;
+}
+
+/*
+ * Given x = A^{-1} b and g = dL/dx: solve A^T lambda = g (A symmetric, so the
+ * same PCG), then dL/db = lambda and dL/da_p = -lambda_{row p} x_{col p}.
+ * dlda may be NULL.
+ */
+int orc_adjoint(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
+                const double *x, const double *g, double *lambda, double *dlda,
+                double rtol, int64_t maxit, orc_result *res) {
+  if (!orc_csr_is_symmetric(n, rp, ci, a)) {
+    memset(res, 0, sizeof(*res));
+    return res->status = ORC_ERR_ARG;
+  }
+  int st = orc_pcg(n, rp, ci, a, g, lambda, rtol, maxit, 0, res);
+  if (dlda)
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t p = rp[i]; p < rp[i + 1]; ++p) dlda[p] = -lambda[i] * x[ci[p]];
+  return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* O6: batched                                                               */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Block-diagonal CSR (global row/column numbering); system s owns rows
+ * [row_off[s], row_off[s+1]) and only couples to its own columns.  Each system
+ * is solved independently by orc_pcg (precision 0) or orc_pcg_refined
+ * (precision 1), with its own stopping test ||r_s|| <= rtol ||b_s||.
+ * res has nsys entries.  Returns the first non-OK status, else OK.
+ */
+int orc_pcg_batched(int32_t nsys, const int64_t *row_off, const int32_t *rp,
+                    const int32_t *ci, const double *a, const double *b,
+                    double *x, double rtol, int64_t maxit, int precision,
+                    double inner_rtol, int64_t inner_maxit, int32_t max_outer,
+                    orc_result *res) {
+  int first = ORC_OK;
+  for (int32_t s = 0; s < nsys; ++s) {
+    int64_t r0 = row_off[s], r1 = row_off[s + 1], n = r1 - r0;
+    int64_t base = rp[r0], nz = (int64_t)rp[r1] - base;
+    int32_t *lrp = (int32_t *)malloc((size_t)(n + 1) * sizeof(int32_t));
+    int32_t *lci = (int32_t *)malloc((size_t)(nz > 0 ? nz : 1) * sizeof(int32_t));
+    if (!lrp || !lci) {
+      free(lrp);
+      free(lci);
+      return ORC_ERR_ALLOC;
+    }
+    for (int64_t i = 0; i <= n; ++i) lrp[i] = (int32_t)(rp[r0 + i] - base);
+    for (int64_t p = 0; p < nz; ++p) lci[p] = (int32_t)(ci[base + p] - r0);
+    int st;
+    if (precision == 0)
+      st = orc_pcg(n, lrp, lci, a + base, b + r0, x + r0, rtol, maxit, 0, &res[s]);
+    else
+      st = orc_pcg_refined(n, lrp, lci, a + base, b + r0, x + r0, rtol, inner_rtol,
+                           inner_maxit, max_outer, 0, &res[s]);
+    if (st != ORC_OK && first == ORC_OK) first = st;
+    free(lrp);
+    free(lci);
+  }
+  return first;
+}
