@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Benchmark of the sparse SPD solver path on one GB300 (or N replicas).
+
+One step is one pass of the whole hot path over the Q1 hexahedral FE Poisson
+workload (96^3 elements, 912,673 rows, 56,623,104 COO entries, 24,137,569
+nonzeros), inputs resident in HBM:
+  mat_create_coo (symbolic COO -> CSR on the device), mat_set_values_coo
+  (duplicate-summing numeric stage + Jacobi), FP64 fused PCG to rtol 1e-8,
+  100 SpMVs, FP32-inner / FP64-refined PCG to rtol 1e-8, adjoint solve plus
+  gradient scatter, mat_destroy.
+The headline value is the FP64 CG solve time in seconds (lower is better);
+SpMV GB/s, the refined and adjoint times and the roofline of the persistent
+PCG kernel are reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle (the plain C implementation in
+oracle/) on a bounded sample of the same workload on the host cores.
+Multi-GPU (torchrun): independent replicas, one per GPU, no collective on the
+data path; max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("CG solve s and SpMV GB/s (% of HBM peak) at rtol 1e-8; "
+          "FP32-refined/batched/adjoint vs FP64")
+WORKLOAD = "q1hex_96: 3D Q1 FE Poisson, 96^3 elements, log-uniform kappa, seed 1002"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def pcg_alg_bytes(n: int, nnz: int, iterations: int) -> float:
+    """Algorithmic bytes of one FP64 PCG launch: per iteration the floor
+    12 nnz + 4 (n+1) + 72 n (A once; x, r, p read and written; D^-1 read; q
+    written and read), plus setup (b, D^-1 read; x, r, p written: 40 n) and the
+    closing true-residual product (12 nnz + 4 (n+1) + 16 n)."""
+    it = 12.0 * nnz + 4.0 * (n + 1) + 72.0 * n
+    return iterations * it + 40.0 * n + 12.0 * nnz + 4.0 * (n + 1) + 16.0 * n
+
+
+def spmv_alg_bytes(n: int, nnz: int) -> float:
+    return 12.0 * nnz + 4.0 * (n + 1) + 16.0 * n
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- CPU oracle
+
+def oracle_sample(p):
+    """Times the oracle on the workload: its COO assembly, then its full FP64
+    PCG solve to rtol 1e-8 (single-threaded plain C; about 20 s in all)."""
+    import oracle
+    t0 = time.perf_counter()
+    A = oracle.coo_symbolic(p.nrows, p.ncols, p.i, p.j)
+    t1 = time.perf_counter()
+    oracle.coo_numeric(A, p.v)
+    t2 = time.perf_counter()
+    x, r = oracle.pcg(A, p.b, rtol=1e-8)
+    t3 = time.perf_counter()
+    return {"symbolic_s": t1 - t0, "numeric_s": t2 - t1, "solve_s": t3 - t2,
+            "iterations": r["iterations"], "status": r["status"]}
+
+
+def run_reference(args, rank: int, world: int):
+    """The oracle as it stands, timed on the host cores: each step is its
+    numeric COO stage plus its full FP64 PCG solve of the workload."""
+    if rank != 0:
+        return 0
+    from paper_2406_08646_gb300 import workloads as W
+    import oracle
+    p = W.q1_hex(96, seed=W.SEED_C2)
+    A = oracle.coo_symbolic(p.nrows, p.ncols, p.i, p.j)
+    times, steps = [], []
+    its = None
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.coo_numeric(A, p.v)
+        t1 = time.perf_counter()
+        x, r = oracle.pcg(A, p.b, rtol=1e-8)
+        t2 = time.perf_counter()
+        its = r["iterations"]
+        if step >= args.warmup:
+            times.append(t2 - t1)
+            steps.append(t2 - t0)
+    value = statistics.median(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.mean(steps), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nrows": p.nrows, "nnz": A.nnz, "ncoo": p.ncoo,
+                       "rtol": 1e-8, "iterations": its},
+            "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
+                             "sample": "whole workload: each step is the oracle's numeric "
+                                       "COO stage and its full FP64 PCG solve "
+                                       "(single-threaded plain C)"},
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- GPU arm
+
+def run_gpu(args, rank: int, world: int):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2406_08646_gb300 import binding as B
+    from paper_2406_08646_gb300 import workloads as W
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    L = B.lib()
+    p = W.q1_hex(96, seed=W.SEED_C2)
+    rng = np.random.default_rng(77)
+    xt_h = rng.standard_normal(p.nrows)
+    i_d = torch.from_numpy(p.i).to(dev)
+    j_d = torch.from_numpy(p.j).to(dev)
+    v_d = torch.from_numpy(p.v).to(dev)
+    b_d = torch.from_numpy(p.b).to(dev)
+    xt_d = torch.from_numpy(xt_h).to(dev)
+    n, ncoo = p.nrows, p.ncoo
+    x64 = torch.empty(n, dtype=torch.float64, device=dev)
+    x32 = torch.empty(n, dtype=torch.float64, device=dev)
+    y = torch.empty(n, dtype=torch.float64, device=dev)
+    g = torch.empty(n, dtype=torch.float64, device=dev)
+    lam = torch.empty(n, dtype=torch.float64, device=dev)
+    dldv = torch.empty(ncoo, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = B._stream(stream)
+    o64 = B.make_opts(rtol=1e-8)
+    o32 = B.make_opts(rtol=1e-8, precision=B.FP32_REFINED)
+    oadj = B.make_opts(rtol=1e-8)
+    SPMV_REPS = 100
+
+    def check(st):
+        if st != B.OK:
+            raise B.GbsError(st, B.last_error())
+
+    def step(record):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
+        res = {}
+        ev[0].record(stream)
+        A = B.mat_create_coo(n, n, i_d, j_d, stream)
+        ev[1].record(stream)
+        check(L.mat_set_values_coo(A, B._dev(v_d, torch.float64), B.INSERT, sp))
+        ev[2].record(stream)
+        check(L.ksp_solve_cg(A, B._dev(b_d, torch.float64), B._dev(x64, torch.float64),
+                             B.ctypes.byref(o64), None, sp))
+        ev[3].record(stream)
+        res["fp64"] = B.ksp_get_result(A, 1, stream)[0]
+        ev[4].record(stream)
+        for _ in range(SPMV_REPS):
+            check(L.mat_mult(A, B._dev(b_d, torch.float64), B._dev(y, torch.float64), sp))
+        ev[5].record(stream)
+        check(L.ksp_solve_cg(A, B._dev(b_d, torch.float64), B._dev(x32, torch.float64),
+                             B.ctypes.byref(o32), None, sp))
+        ev[6].record(stream)
+        res["fp32_refined"] = B.ksp_get_result(A, 1, stream)[0]
+        torch.sub(x64, xt_d, out=g)
+        ev7 = torch.cuda.Event(enable_timing=True)
+        ev7.record(stream)
+        check(L.ksp_adjoint(A, B._dev(x64, torch.float64), B._dev(g, torch.float64),
+                            B._dev(lam, torch.float64), None, B._dev(dldv, torch.float64),
+                            B.ctypes.byref(oadj), None, sp))
+        ev[7].record(stream)
+        res["adjoint"] = B.ksp_get_result(A, 1, stream)[0]
+        nnz = B.mat_get_info(A)["nnz"]
+        plan = B.mat_get_plan(A)
+        B.mat_destroy(A)
+        stream.synchronize()
+        t = {"create": ev[0].elapsed_time(ev[1]), "set_values": ev[1].elapsed_time(ev[2]),
+             "solve_fp64": ev[2].elapsed_time(ev[3]),
+             "spmv_x100": ev[4].elapsed_time(ev[5]),
+             "solve_fp32_refined": ev[5].elapsed_time(ev[6]),
+             "adjoint": ev7.elapsed_time(ev[7]), "step": ev[0].elapsed_time(ev[7])}
+        return t, res, nnz, plan
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step(False)
+    barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    c0 = B.launch_count()
+    w0 = time.perf_counter()
+    rows, results = [], []
+    for _ in range(args.steps):
+        t, res, nnz, plan = step(True)
+        rows.append(t)
+        results.append(res)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - w0
+    launches = (B.launch_count() - c0) / max(args.steps, 1)
+    clk = clocks.stop()
+
+    med = {k: statistics.median(r[k] for r in rows) for k in rows[0]}
+    step_ms = statistics.mean(r["step"] for r in rows)
+    solve_s = med["solve_fp64"] / 1e3
+    if world > 1:
+        tt = torch.tensor([solve_s, step_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        solve_s, step_ms = float(tt[0]), float(tt[1])
+
+    # ---- end to end through the C-ABI from pinned host buffers (H2D + D2H in region)
+    i_h = torch.from_numpy(p.i).pin_memory()
+    j_h = torch.from_numpy(p.j).pin_memory()
+    v_h = torch.from_numpy(p.v).pin_memory()
+    b_h = torch.from_numpy(p.b).pin_memory()
+    x_h = torch.empty(n, dtype=torch.float64).pin_memory()
+    i2, j2 = torch.empty_like(i_d), torch.empty_like(j_d)
+    v2, b2 = torch.empty_like(v_d), torch.empty_like(b_d)
+    x2 = torch.empty_like(x64)
+    e2e = []
+    for rep in range(3):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        i2.copy_(i_h, non_blocking=True)
+        j2.copy_(j_h, non_blocking=True)
+        v2.copy_(v_h, non_blocking=True)
+        b2.copy_(b_h, non_blocking=True)
+        A = B.mat_create_coo(n, n, i2, j2, stream)
+        check(L.mat_set_values_coo(A, B._dev(v2, torch.float64), B.INSERT, sp))
+        check(L.ksp_solve_cg(A, B._dev(b2, torch.float64), B._dev(x2, torch.float64),
+                             B.ctypes.byref(o64), None, sp))
+        x_h.copy_(x2, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        r = B.ksp_get_result(A, 1, stream)[0]
+        B.mat_destroy(A)
+        if rep > 0:
+            e2e.append(e0.elapsed_time(e1) / 1e3)
+        assert r["status"] == B.OK
+    e2e_s = statistics.median(e2e)
+
+    r64 = results[-1]["fp64"]
+    it = r64["iterations"]
+    hbm, peak_kind = peaks()
+    achieved = pcg_alg_bytes(n, nnz, it) / solve_s / 1e9
+    spmv_s = med["spmv_x100"] / 1e3 / SPMV_REPS
+    spmv_gbs = spmv_alg_bytes(n, nnz) / spmv_s / 1e9
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        s = oracle_sample(p)
+        cpu = {"value": s["solve_s"], "unit": "s", "cores": 1, "kind": "oracle",
+               "sample": (f"whole workload, once: oracle COO assembly "
+                          f"({s['symbolic_s']:.1f} s symbolic, {s['numeric_s']:.2f} s numeric) "
+                          f"then its full FP64 PCG solve ({s['iterations']} iterations, "
+                          f"status {s['status']}); value = the solve")}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": solve_s, "unit": "s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nrows": n, "nnz": nnz, "ncoo": ncoo,
+                       "rtol": 1e-8, "spmv_reps": SPMV_REPS,
+                       "l2": "no flush: every input is larger than L2 (CSR 290 MB, COO 906 MB)",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "plan": plan},
+            "rows_ms": med,
+            "iterations": {k: results[-1][k]["iterations"] for k in results[-1]},
+            "outer_iterations_fp32_refined": results[-1]["fp32_refined"]["outer_iterations"],
+            "true_rel_residual": {k: results[-1][k]["true_rel_residual"] for k in results[-1]},
+            "status": {k: results[-1][k]["status"] for k in results[-1]},
+            "spmv": {"gbs": spmv_gbs, "frac": spmv_gbs / hbm, "us": spmv_s * 1e6,
+                     "alg_bytes": spmv_alg_bytes(n, nnz)},
+            "roofline": {"kernel": "k_pcg<false> (persistent FP64 PCG)", "bound": "hbm",
+                         "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": None,
+                         "alg_bytes": pcg_alg_bytes(n, nnz, it)},
+            "refined_vs_fp64": med["solve_fp32_refined"] / med["solve_fp64"],
+            "adjoint_vs_fp64": med["adjoint"] / med["solve_fp64"],
+            "e2e": {"value": e2e_s, "unit": "s",
+                    "h2d_bytes_per_step": int(ncoo * 16 + n * 8),
+                    "d2h_bytes_per_step": int(n * 8),
+                    "what": "pinned host COO + b -> device, assemble, FP64 solve, x -> host"},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "wall_s": wall,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gbs", choices=["gbs", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    try:
+        return run_gpu(args, rank, world)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

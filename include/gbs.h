@@ -1,0 +1,237 @@
+/*
+ * gbs.h -- C-ABI of the GB300 sparse SPD solver library (libgbs.so).
+ *
+ * The library assembles a CSR matrix on the GPU from COO triples, summing
+ * duplicates, and solves A x = b with a Jacobi-preconditioned conjugate
+ * gradient whose SpMV, vector updates and dot products run in one persistent
+ * kernel.  On top of that sit an FP32-inner / FP64-refined solve, a batched
+ * solve of many independent systems in one launch, and the adjoint of the
+ * solve.
+ *
+ * Paper: "PETSc/TAO developments for GPU-based early exascale systems".
+ *   - COO assembly: Sec. 5 (MatSetPreallocationCOO / MatSetValuesCOO).
+ *   - CG with device-resident scalars and no host round trip: Sec. 6.1
+ *     (CGAsync), Sec. 6.2.
+ *   - Diagonal (Jacobi) preconditioning and batched solvers: Sec. 7.
+ *   - Multiprecision (single-precision inner solver): Sec. 2, challenge A7.
+ *   - Adjoint capability: Sec. 1.
+ *   - One stream handle per call, device pointers in and out: Sec. 2.
+ *
+ * Conventions for every entry point:
+ *   - Pointers are DEVICE pointers unless the comment says "host".
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *     stream.  All work is enqueued on that stream.  Unless stated otherwise a
+ *     call is asynchronous: the caller keeps every borrowed buffer alive (and
+ *     unmodified, for inputs) until the stream has passed the call.
+ *   - Every function returns a status code (GBS_OK = 0).  No exception or
+ *     signal crosses the ABI.  On failure gbs_last_error() returns a
+ *     thread-local message.  Errors the host can see (bad arguments, CUDA API
+ *     failures) are returned at once; errors found on the device (index out of
+ *     range, bad diagonal, breakdown, NaN, iteration limit, barrier timeout)
+ *     are returned by the next call that synchronises (mat_create_coo*, or a
+ *     solve given a non-NULL result pointer, or ksp_get_result).
+ *   - Index type: int32 row/column indices, int32 CSR row pointers; so
+ *     nrows, ncols, ncoo and nnz must each be < 2^31.
+ *   - A matrix handle is used by one host thread at a time.
+ */
+#ifndef GBS_H
+#define GBS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gbs_mat_s *gbs_mat; /* opaque; owned by the library */
+
+enum {
+  GBS_OK = 0,
+  GBS_ERR_ARG = 1,        /* invalid argument (host check) */
+  GBS_ERR_INDEX = 2,      /* a kept COO index >= nrows / ncols */
+  GBS_ERR_ALLOC = 3,      /* device or host allocation failed */
+  GBS_ERR_CUDA = 4,       /* a CUDA runtime call failed */
+  GBS_ERR_NOT_SPD = 5,    /* missing or non-positive diagonal, or r.z <= 0 */
+  GBS_ERR_BREAKDOWN = 6,  /* p.Ap <= 0 (matrix not SPD) */
+  GBS_ERR_NAN = 7,        /* NaN / Inf met in the iteration or in b */
+  GBS_ERR_MAXIT = 8,      /* iteration limit reached before rtol */
+  GBS_ERR_STAGNATION = 9, /* refined solve: residual stopped decreasing */
+  GBS_ERR_TIMEOUT = 10,   /* an in-kernel grid-barrier wait exceeded timeout_ns */
+  GBS_ERR_LAUNCH = 11     /* persistent kernel could not be made co-resident */
+};
+
+enum { GBS_INSERT = 0, GBS_ADD = 1 };
+enum { GBS_FP64 = 0, GBS_FP32_REFINED = 1 };
+
+/* Solver options (host struct).  Fill with ksp_opts_default(), then override. */
+typedef struct {
+  double rtol;          /* stop when ||r||_2 <= rtol ||b||_2 (default 1e-8) */
+  int32_t maxit;        /* < 0: 10 n capped at 100000, n = largest system;
+                           0 stops at once with GBS_ERR_MAXIT unless b = 0 */
+  int32_t precision;    /* GBS_FP64 or GBS_FP32_REFINED */
+  double inner_rtol;    /* refined: FP32 inner tolerance (<= 0: 1e-4) */
+  int32_t max_outer;    /* refined: max refinement steps (< 0: 30) */
+  int32_t inner_maxit;  /* refined: inner products per step (< 0: as maxit) */
+  int64_t timeout_ns;   /* bound on each in-kernel barrier wait (<= 0: 2e9) */
+  int32_t nonzero_guess;/* 1: x holds the initial guess; 0: start from x = 0 */
+  int32_t debug_barrier_extra; /* testing only, normally 0: every grid barrier
+                           also waits for this many CTAs that do not exist, so
+                           each wait runs out after timeout_ns and the solve
+                           ends with GBS_ERR_TIMEOUT (exercises that path) */
+} ksp_opts;
+
+/* Per-solve (or per-system) result, host struct. */
+typedef struct {
+  int32_t status;           /* GBS_OK or the GBS_ERR_* that ended the solve */
+  int32_t iterations;       /* products q = A p (refined: total inner ones) */
+  int32_t outer_iterations; /* refined: refinement steps; FP64: 0 */
+  int32_t reserved;
+  double rnorm0;            /* ||b - A x0||_2 */
+  double rnorm;             /* last recursively updated residual norm
+                               (refined: last FP64 outer residual norm) */
+  double true_rel_residual; /* ||b - A x||_2 / ||b||_2 recomputed at exit */
+} ksp_result;
+
+/* Fills *o with the defaults listed above. */
+void ksp_opts_default(ksp_opts *o);
+
+/*
+ * Symbolic COO stage (Sec. 5, MatSetPreallocationCOO(A, n, i, j)).
+ * i, j: int32[ncoo] device arrays; an entry with i[k] < 0 or j[k] < 0 is
+ * ignored (Sec. 5 allows negative indices to mark entries to skip).  The
+ * pattern is the set of distinct kept (i, j), rows ascending and columns
+ * strictly ascending.  i and j are only read during this call and may be freed
+ * after it returns.  Builds on the device: the CSR structure, the map from
+ * sorted position to COO index (perm) and the segment offsets (jmap), the
+ * diagonal positions and the launch plan.  Synchronises `stream` (nnz is
+ * data-dependent).  Errors: GBS_ERR_ARG (sizes), GBS_ERR_INDEX (a kept index
+ * out of range), GBS_ERR_ALLOC, GBS_ERR_CUDA.  On success *out is a new
+ * handle, to be released with mat_destroy.
+ */
+int mat_create_coo(int64_t nrows, int64_t ncols, int64_t ncoo, const int32_t *i,
+                   const int32_t *j, void *stream, gbs_mat *out);
+
+/*
+ * Batched symbolic stage (Sec. 7 batched systems; Sec. 5 COO per system).
+ * nsys independent square systems; nrows_h[s], ncoo_h[s] are HOST arrays;
+ * i, j are the systems' COO indices concatenated in system order, each LOCAL to
+ * its system (0 <= i < nrows_h[s]; negative = ignored).  The handle holds one
+ * block-diagonal CSR of sum(nrows_h) rows; ksp_solve_cg_batched solves the
+ * systems independently, ksp_solve_cg solves the stacked ("ensemble", Sec. 7)
+ * system with one global norm.  Same synchronisation and errors as
+ * mat_create_coo.
+ */
+int mat_create_coo_batched(int32_t nsys, const int64_t *nrows_h, const int64_t *ncoo_h,
+                           const int32_t *i, const int32_t *j, void *stream,
+                           gbs_mat *out);
+
+/*
+ * Numeric COO stage (Sec. 5, MatSetValuesCOO(A, v, mode)).
+ * v: double[ncoo] device array in the same order as the i/j given at creation
+ * (entries that were ignored are not read).  Each nonzero a_p is the sum of its
+ * contributions in increasing COO index order, computed by one thread with no
+ * atomics; GBS_INSERT replaces the stored value, GBS_ADD adds to it.  Also
+ * refreshes the Jacobi diagonal inverse used by the solves (a missing or
+ * non-positive diagonal is reported as GBS_ERR_NOT_SPD by the next solve).
+ * Asynchronous.
+ */
+int mat_set_values_coo(gbs_mat A, const double *v, int mode, void *stream);
+
+/* y = A x (the MatMult of Sec. 6.1), FP64.  x: double[ncols], y: double[nrows],
+ * must not overlap.  Each y_i sums its row's products in CSR order.
+ * Asynchronous. */
+int mat_mult(gbs_mat A, const double *x, double *y, void *stream);
+
+/*
+ * Jacobi-preconditioned CG on the whole matrix (Sec. 6.1 CG without host
+ * round trips; Sec. 7 diagonal preconditioner).  b, x: double[nrows]; x is the
+ * initial guess when o->nonzero_guess, else overwritten from 0.  One persistent
+ * cooperative kernel runs every iteration: SpMV fused with p.Ap, the x/r
+ * updates fused with r.z and ||r||^2, and the p update, with deterministic
+ * grid reductions and device-resident scalars.  o->precision =
+ * GBS_FP32_REFINED runs FP32 inner PCG (FP32 values, vectors, reductions)
+ * inside FP64 iterative refinement (Sec. 2, A7).  o may be NULL (defaults).
+ * res (host): if non-NULL the call synchronises and fills it, and returns its
+ * status; if NULL the call is asynchronous and the result can be fetched later
+ * with ksp_get_result.
+ */
+int ksp_solve_cg(gbs_mat A, const double *b, double *x, const ksp_opts *o,
+                 ksp_result *res, void *stream);
+
+/*
+ * Batched solve of a handle made by mat_create_coo_batched: every system runs
+ * its own PCG (own alpha, beta, norms, stopping test ||r_s|| <= rtol ||b_s||)
+ * in one persistent launch, replayed from a CUDA graph; converged systems are
+ * frozen.  b, x: double[sum nrows] in system order.  res_h: HOST array of nsys
+ * results or NULL (asynchronous).  Returns the first non-OK system status when
+ * res_h is given.
+ */
+int ksp_solve_cg_batched(gbs_mat A, const double *b, double *x, const ksp_opts *o,
+                         ksp_result *res_h, void *stream);
+
+/*
+ * Adjoint of x = A^{-1} b (Sec. 1 adjoint capability), for symmetric A:
+ * solves A^T lambda = dLdx with the same CG kernels (o->rtol, default 1e-8),
+ * then writes dL/db = lambda, dLda[p] = -lambda[row p] x[col p] over the
+ * pattern (double[nnz], may be NULL) and dLdv[k] = dLda[p(k)] for every kept
+ * COO entry, 0 for ignored ones (double[ncoo], may be NULL).  Symmetry is the
+ * caller's contract (it is not checked).  res as in ksp_solve_cg.
+ */
+int ksp_adjoint(gbs_mat A, const double *x, const double *dLdx, double *lambda,
+                double *dLda, double *dLdv, const ksp_opts *o, ksp_result *res,
+                void *stream);
+
+/* Batched adjoint: per-system lambda solves in one launch, then the same
+ * scatters over the concatenated arrays.  res_h: HOST array of nsys or NULL. */
+int ksp_adjoint_batched(gbs_mat A, const double *x, const double *dLdx, double *lambda,
+                        double *dLda, double *dLdv, const ksp_opts *o,
+                        ksp_result *res_h, void *stream);
+
+/* Synchronises `stream` and copies the results of the last solve on A into the
+ * HOST array res (nsys entries for a batched solve, else 1).  Returns the first
+ * non-OK status. */
+int ksp_get_result(gbs_mat A, ksp_result *res, int32_t count, void *stream);
+
+/* Sizes (host outputs; any may be NULL). */
+int mat_get_info(gbs_mat A, int64_t *nrows, int64_t *ncols, int64_t *nnz,
+                 int64_t *ncoo, int32_t *nsys);
+
+/* Borrowed device views of the CSR arrays, valid until mat_destroy (host
+ * outputs; any may be NULL). */
+int mat_get_csr(gbs_mat A, const int32_t **row_ptr, const int32_t **col,
+                const double **val, int64_t *nnz);
+
+/* Borrowed device views of the COO maps: perm[nkept] (sorted position ->
+ * original COO index) and jmap[nnz+1] (segment offsets into perm). */
+int mat_get_coo_maps(gbs_mat A, const int32_t **perm, const int32_t **jmap,
+                     int64_t *nkept);
+
+/*
+ * Launch plan: rows_per_block rows per work block (a power of two in
+ * [32, 1024]) and threads_per_block (a multiple of 32 in [64, 512] and
+ * >= rows_per_block) used by mat_mult and the solves.  mat_set_plan
+ * synchronises the device (the old plan may be in use).  mat_create_coo picks a
+ * default; mat_autotune times candidates with CUDA events on `stream` and
+ * keeps the fastest (it synchronises).  Host outputs may be NULL.
+ */
+int mat_set_plan(gbs_mat A, int32_t rows_per_block, int32_t threads_per_block);
+int mat_get_plan(gbs_mat A, int32_t *rows_per_block, int32_t *threads_per_block,
+                 int32_t *persistent_ctas);
+int mat_autotune(gbs_mat A, void *stream);
+
+/* Releases every device buffer the handle owns.  Synchronises the device
+ * buffers' last stream first.  NULL is accepted. */
+int mat_destroy(gbs_mat A);
+
+/* Number of kernels this library has launched in this process (a diagnostic
+ * counter; a graph replay counts the kernels it contains). */
+int64_t gbs_launch_count(void);
+
+/* Thread-local message describing the last error ("" if none). */
+const char *gbs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBS_H */

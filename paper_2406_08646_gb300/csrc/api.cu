@@ -1,0 +1,417 @@
+// C-ABI entry points of libgbs.so (declared in include/gbs.h): argument
+// checks, handle lifetime, option defaults, the autotuner, and dispatch to the
+// kernels in coo.cu, spmv.cu and pcg.cu.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <new>
+
+#include "internal.cuh"
+
+namespace gbs {
+
+static thread_local char g_err[1024] = "";
+static std::atomic<int64_t> g_launches{0};
+
+void set_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+static constexpr int64_t kMaxIndex = 2147483647LL;
+
+static void free_handle(gbs_mat A) {
+  if (!A) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(A->device);
+  if (A->graph) cudaGraphExecDestroy(A->graph);
+  void *dev[] = {A->row_ptr, A->col, A->val, A->val32, A->perm, A->jmap, A->diag_pos,
+                 A->dinv, A->dinv32, A->blk_row0, A->blk_sys, A->sys_blk0, A->r, A->p,
+                 A->q, A->r32, A->p32, A->q32, A->d32, A->part, A->sys_slot0, A->sys_cnt,
+                 A->st, A->ctl};
+  for (void *p : dev)
+    if (p) cudaFree(p);
+  if (A->st_host) cudaFreeHost(A->st_host);
+  cudaSetDevice(cur);
+  delete A;
+}
+
+static int default_plan(gbs_mat A) {
+  // One row per thread, 256 threads; shorter blocks for very long rows so the
+  // staged products of a block stay within one chunk.
+  int32_t R = 256;
+  while (R > 32 && (int64_t)R * A->max_row_nnz > 8192) R >>= 1;
+  return build_plan(A, R, std::max<int32_t>(R, 64));
+}
+
+static int64_t max_system_rows(gbs_mat A, bool per_system) {
+  if (!per_system) return A->nrows;
+  int64_t m = 0;
+  for (int32_t q = 0; q < A->nsys; ++q) m = std::max(m, A->row_off_h[q + 1] - A->row_off_h[q]);
+  return m;
+}
+
+static int fill_opts(gbs_mat A, const ksp_opts *in, ksp_opts &o, bool per_system) {
+  ksp_opts_default(&o);
+  if (in) o = *in;
+  if (!(o.rtol >= 0.0) || !std::isfinite(o.rtol)) {
+    set_error("ksp opts: rtol must be finite and >= 0");
+    return GBS_ERR_ARG;
+  }
+  if (o.precision != GBS_FP64 && o.precision != GBS_FP32_REFINED) {
+    set_error("ksp opts: precision must be GBS_FP64 or GBS_FP32_REFINED");
+    return GBS_ERR_ARG;
+  }
+  if (o.debug_barrier_extra < 0) {
+    set_error("ksp opts: debug_barrier_extra must be >= 0");
+    return GBS_ERR_ARG;
+  }
+  const int64_t n = max_system_rows(A, per_system);
+  const int32_t dflt = (int32_t)std::min<int64_t>(10 * std::max<int64_t>(n, 1), 100000);
+  if (o.maxit < 0) o.maxit = dflt;
+  if (o.inner_maxit < 0) o.inner_maxit = dflt;
+  if (!(o.inner_rtol > 0.0)) o.inner_rtol = 1e-4;
+  if (o.max_outer < 0) o.max_outer = 30;
+  if (o.timeout_ns <= 0) o.timeout_ns = 2000000000LL;
+  return GBS_OK;
+}
+
+static int check_mat(gbs_mat A, const char *fn) {
+  if (!A) {
+    set_error("%s: null matrix handle", fn);
+    return GBS_ERR_ARG;
+  }
+  return GBS_OK;
+}
+
+static int use_device(gbs_mat A) {
+  GBS_TRY_CUDA(cudaSetDevice(A->device));
+  return GBS_OK;
+}
+
+static int create_common(gbs_mat *out, gbs_mat A, const int32_t *i, const int32_t *j,
+                         const int64_t *coo_off_h, cudaStream_t s) {
+  int st = symbolic(A, i, j, coo_off_h, s);
+  if (st == GBS_OK) st = default_plan(A);
+  if (st != GBS_OK) {
+    free_handle(A);
+    return st;
+  }
+  *out = A;
+  return GBS_OK;
+}
+
+}  // namespace gbs
+
+using namespace gbs;
+
+extern "C" {
+
+void ksp_opts_default(ksp_opts *o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->rtol = 1e-8;
+  o->maxit = -1;
+  o->precision = GBS_FP64;
+  o->inner_rtol = 1e-4;
+  o->max_outer = 30;
+  o->inner_maxit = -1;
+  o->timeout_ns = 2000000000LL;
+  o->nonzero_guess = 0;
+  o->debug_barrier_extra = 0;
+}
+
+int mat_create_coo(int64_t nrows, int64_t ncols, int64_t ncoo, const int32_t *i,
+                   const int32_t *j, void *stream, gbs_mat *out) {
+  if (!out) {
+    set_error("mat_create_coo: out is null");
+    return GBS_ERR_ARG;
+  }
+  *out = nullptr;
+  if (nrows < 0 || ncols < 0 || ncoo < 0 || nrows > kMaxIndex || ncols > kMaxIndex ||
+      ncoo > kMaxIndex) {
+    set_error("mat_create_coo: sizes must be in [0, 2^31)");
+    return GBS_ERR_ARG;
+  }
+  if (ncoo > 0 && (!i || !j)) {
+    set_error("mat_create_coo: null i or j");
+    return GBS_ERR_ARG;
+  }
+  gbs_mat A = new (std::nothrow) gbs_mat_s();
+  if (!A) return GBS_ERR_ALLOC;
+  cudaGetDevice(&A->device);
+  A->nrows = nrows;
+  A->ncols = ncols;
+  A->ncoo = ncoo;
+  A->nsys = 1;
+  A->row_off_h = {0, nrows};
+  return create_common(out, A, i, j, nullptr, (cudaStream_t)stream);
+}
+
+int mat_create_coo_batched(int32_t nsys, const int64_t *nrows_h, const int64_t *ncoo_h,
+                           const int32_t *i, const int32_t *j, void *stream, gbs_mat *out) {
+  if (!out) {
+    set_error("mat_create_coo_batched: out is null");
+    return GBS_ERR_ARG;
+  }
+  *out = nullptr;
+  if (nsys < 1 || !nrows_h || !ncoo_h) {
+    set_error("mat_create_coo_batched: need nsys >= 1 and host size arrays");
+    return GBS_ERR_ARG;
+  }
+  std::vector<int64_t> row_off(nsys + 1, 0), coo_off(nsys + 1, 0);
+  for (int32_t s = 0; s < nsys; ++s) {
+    if (nrows_h[s] < 0 || ncoo_h[s] < 0) {
+      set_error("mat_create_coo_batched: negative size for system %d", s);
+      return GBS_ERR_ARG;
+    }
+    row_off[s + 1] = row_off[s] + nrows_h[s];
+    coo_off[s + 1] = coo_off[s] + ncoo_h[s];
+  }
+  if (row_off[nsys] > kMaxIndex || coo_off[nsys] > kMaxIndex) {
+    set_error("mat_create_coo_batched: total rows and COO entries must be < 2^31");
+    return GBS_ERR_ARG;
+  }
+  if (coo_off[nsys] > 0 && (!i || !j)) {
+    set_error("mat_create_coo_batched: null i or j");
+    return GBS_ERR_ARG;
+  }
+  gbs_mat A = new (std::nothrow) gbs_mat_s();
+  if (!A) return GBS_ERR_ALLOC;
+  cudaGetDevice(&A->device);
+  A->nrows = A->ncols = row_off[nsys];
+  A->ncoo = coo_off[nsys];
+  A->nsys = nsys;
+  A->batched = true;
+  A->row_off_h = row_off;
+  return create_common(out, A, i, j, coo_off.data(), (cudaStream_t)stream);
+}
+
+int mat_set_values_coo(gbs_mat A, const double *v, int mode, void *stream) {
+  GBS_TRY(check_mat(A, "mat_set_values_coo"));
+  if (mode != GBS_INSERT && mode != GBS_ADD) {
+    set_error("mat_set_values_coo: mode must be GBS_INSERT or GBS_ADD");
+    return GBS_ERR_ARG;
+  }
+  if (A->nkept > 0 && !v) {
+    set_error("mat_set_values_coo: v is null");
+    return GBS_ERR_ARG;
+  }
+  GBS_TRY(use_device(A));
+  return launch_set_values(A, v, mode, (cudaStream_t)stream);
+}
+
+int mat_mult(gbs_mat A, const double *x, double *y, void *stream) {
+  GBS_TRY(check_mat(A, "mat_mult"));
+  if (A->nrows > 0 && (!x || !y)) {
+    set_error("mat_mult: null x or y");
+    return GBS_ERR_ARG;
+  }
+  if (x == y && x) {
+    set_error("mat_mult: x and y must not overlap");
+    return GBS_ERR_ARG;
+  }
+  GBS_TRY(use_device(A));
+  return launch_spmv(A, x, y, (cudaStream_t)stream);
+}
+
+static int solve_entry(gbs_mat A, const double *b, double *x, const ksp_opts *o,
+                       ksp_result *res, void *stream, bool per_system, const char *fn) {
+  GBS_TRY(check_mat(A, fn));
+  if (A->nrows != A->ncols) {
+    set_error("%s: matrix is not square", fn);
+    return GBS_ERR_ARG;
+  }
+  if (A->nrows > 0 && (!b || !x)) {
+    set_error("%s: null b or x", fn);
+    return GBS_ERR_ARG;
+  }
+  if (!A->values_set) {
+    set_error("%s: mat_set_values_coo has not been called", fn);
+    return GBS_ERR_ARG;
+  }
+  ksp_opts oo;
+  GBS_TRY(fill_opts(A, o, oo, per_system));
+  GBS_TRY(use_device(A));
+  cudaStream_t s = (cudaStream_t)stream;
+  GBS_TRY(solve(A, b, x, oo, per_system, per_system, s));
+  if (res) return read_results(A, res, per_system ? A->nsys : 1, s);
+  return GBS_OK;
+}
+
+int ksp_solve_cg(gbs_mat A, const double *b, double *x, const ksp_opts *o, ksp_result *res,
+                 void *stream) {
+  return solve_entry(A, b, x, o, res, stream, false, "ksp_solve_cg");
+}
+
+int ksp_solve_cg_batched(gbs_mat A, const double *b, double *x, const ksp_opts *o,
+                         ksp_result *res_h, void *stream) {
+  return solve_entry(A, b, x, o, res_h, stream, true, "ksp_solve_cg_batched");
+}
+
+static int adjoint_entry(gbs_mat A, const double *x, const double *dLdx, double *lambda,
+                         double *dLda, double *dLdv, const ksp_opts *o, ksp_result *res,
+                         void *stream, bool per_system, const char *fn) {
+  GBS_TRY(check_mat(A, fn));
+  if (A->nrows > 0 && (!x || !dLdx || !lambda)) {
+    set_error("%s: null x, dLdx or lambda", fn);
+    return GBS_ERR_ARG;
+  }
+  ksp_opts oo;
+  ksp_opts_default(&oo);
+  if (o) oo = *o;
+  oo.nonzero_guess = 0;
+  // the adjoint system is solved in the precision the caller asked for
+  int st = solve_entry(A, dLdx, lambda, &oo, nullptr, stream, per_system, fn);
+  if (st != GBS_OK) return st;
+  st = launch_adjoint_scatter(A, lambda, x, dLda, dLdv, (cudaStream_t)stream);
+  if (st != GBS_OK) return st;
+  if (res) return read_results(A, res, per_system ? A->nsys : 1, (cudaStream_t)stream);
+  return GBS_OK;
+}
+
+int ksp_adjoint(gbs_mat A, const double *x, const double *dLdx, double *lambda, double *dLda,
+                double *dLdv, const ksp_opts *o, ksp_result *res, void *stream) {
+  return adjoint_entry(A, x, dLdx, lambda, dLda, dLdv, o, res, stream, false, "ksp_adjoint");
+}
+
+int ksp_adjoint_batched(gbs_mat A, const double *x, const double *dLdx, double *lambda,
+                        double *dLda, double *dLdv, const ksp_opts *o, ksp_result *res_h,
+                        void *stream) {
+  return adjoint_entry(A, x, dLdx, lambda, dLda, dLdv, o, res_h, stream, true,
+                       "ksp_adjoint_batched");
+}
+
+int ksp_get_result(gbs_mat A, ksp_result *res, int32_t count, void *stream) {
+  GBS_TRY(check_mat(A, "ksp_get_result"));
+  if (!res) {
+    set_error("ksp_get_result: res is null");
+    return GBS_ERR_ARG;
+  }
+  GBS_TRY(use_device(A));
+  return read_results(A, res, count, (cudaStream_t)stream);
+}
+
+int mat_get_info(gbs_mat A, int64_t *nrows, int64_t *ncols, int64_t *nnz, int64_t *ncoo,
+                 int32_t *nsys) {
+  GBS_TRY(check_mat(A, "mat_get_info"));
+  if (nrows) *nrows = A->nrows;
+  if (ncols) *ncols = A->ncols;
+  if (nnz) *nnz = A->nnz;
+  if (ncoo) *ncoo = A->ncoo;
+  if (nsys) *nsys = A->nsys;
+  return GBS_OK;
+}
+
+int mat_get_csr(gbs_mat A, const int32_t **row_ptr, const int32_t **col, const double **val,
+                int64_t *nnz) {
+  GBS_TRY(check_mat(A, "mat_get_csr"));
+  if (row_ptr) *row_ptr = A->row_ptr;
+  if (col) *col = A->col;
+  if (val) *val = A->val;
+  if (nnz) *nnz = A->nnz;
+  return GBS_OK;
+}
+
+int mat_get_coo_maps(gbs_mat A, const int32_t **perm, const int32_t **jmap, int64_t *nkept) {
+  GBS_TRY(check_mat(A, "mat_get_coo_maps"));
+  if (perm) *perm = A->perm;
+  if (jmap) *jmap = A->jmap;
+  if (nkept) *nkept = A->nkept;
+  return GBS_OK;
+}
+
+int mat_set_plan(gbs_mat A, int32_t rows_per_block, int32_t threads_per_block) {
+  GBS_TRY(check_mat(A, "mat_set_plan"));
+  GBS_TRY(use_device(A));
+  GBS_TRY_CUDA(cudaDeviceSynchronize());  // plan arrays may be in use
+  return build_plan(A, rows_per_block, threads_per_block);
+}
+
+int mat_get_plan(gbs_mat A, int32_t *rows_per_block, int32_t *threads_per_block,
+                 int32_t *persistent_ctas) {
+  GBS_TRY(check_mat(A, "mat_get_plan"));
+  if (rows_per_block) *rows_per_block = A->rows_per_block;
+  if (threads_per_block) *threads_per_block = A->tpb;
+  if (persistent_ctas) *persistent_ctas = A->grid_fp64;
+  return GBS_OK;
+}
+
+// Times a fixed 30-iteration FP64 PCG run (rtol 0, so every candidate does
+// the same work) for each candidate plan and keeps the fastest.
+int mat_autotune(gbs_mat A, void *stream) {
+  GBS_TRY(check_mat(A, "mat_autotune"));
+  if (!A->values_set) {
+    set_error("mat_autotune: mat_set_values_coo has not been called");
+    return GBS_ERR_ARG;
+  }
+  if (A->nrows != A->ncols || A->nrows == 0) return GBS_OK;
+  GBS_TRY(use_device(A));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int cands[][2] = {{64, 64},   {128, 128}, {256, 256}, {512, 512},
+                          {128, 256}, {256, 512}, {64, 128}};
+  double *b = nullptr, *x = nullptr;
+  GBS_TRY_CUDA(cudaMalloc(&b, sizeof(double) * A->nrows));
+  GBS_TRY_CUDA(cudaMalloc(&x, sizeof(double) * A->nrows));
+  // b = A * 1 (any nonzero right-hand side will do)
+  std::vector<double> ones(A->nrows, 1.0);
+  cudaMemcpy(x, ones.data(), sizeof(double) * A->nrows, cudaMemcpyHostToDevice);
+  ksp_opts o;
+  ksp_opts_default(&o);
+  o.rtol = 0.0;
+  o.maxit = 30;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int bestR = A->rows_per_block, bestT = A->tpb;
+  float best = 1e30f;
+  int st = GBS_OK;
+  for (const auto &c : cands) {
+    if ((int64_t)c[0] * A->max_row_nnz > 4 * 8192) continue;
+    if (build_plan(A, c[0], c[1]) != GBS_OK) continue;
+    if (launch_spmv(A, x, b, s) != GBS_OK) continue;
+    if (solve(A, b, x, o, false, false, s) != GBS_OK) continue;  // warm-up
+    cudaEventRecord(e0, s);
+    for (int rep = 0; rep < 3; ++rep) solve(A, b, x, o, false, false, s);
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      st = GBS_ERR_CUDA;
+      break;
+    }
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      bestR = c[0];
+      bestT = c[1];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(b);
+  cudaFree(x);
+  if (st != GBS_OK) {
+    set_error("mat_autotune: a timed run failed");
+    return st;
+  }
+  return build_plan(A, bestR, bestT);
+}
+
+int mat_destroy(gbs_mat A) {
+  free_handle(A);
+  return GBS_OK;
+}
+
+int64_t gbs_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char *gbs_last_error(void) { return g_err; }
+
+}  // extern "C"

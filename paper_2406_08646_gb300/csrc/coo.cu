@@ -1,0 +1,649 @@
+// COO -> CSR assembly on the device (Sec. 5: MatSetPreallocationCOO /
+// MatSetValuesCOO), the Jacobi diagonal (Sec. 7), the FP32 copy used by the
+// refined solve (Sec. 2, A7) and the adjoint scatter over the pattern.
+//
+// Symbolic stage, all on the GPU:
+//   1. keep flags (negative index -> ignored; out of range -> error) and an
+//      exclusive scan, compaction into 64-bit keys i*ncols + j with the
+//      original COO index as payload;
+//   2. stable LSD radix sort of the keys (8-bit digits, as many passes as the
+//      largest key needs): per-tile digit histograms, one scan of the
+//      digit-major count table, then a stable scatter that ranks equal digits
+//      with warp match/ballot in input order;
+//   3. segment heads of the sorted keys and a scan -> nnz, jmap (segment
+//      offsets), the unique keys, then col, the diagonal positions and
+//      row_ptr (lower bound of r*ncols in the unique keys).
+// The sorted payload is perm (sorted position -> original COO index): equal
+// keys keep increasing COO index, which is what makes the numeric stage's
+// in-order sum well defined.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "device_util.cuh"
+#include "internal.cuh"
+
+namespace gbs {
+
+// ------------------------------------------------------------------ scan
+
+constexpr int SCAN_T = 256, SCAN_IPT = 16, SCAN_TILE = SCAN_T * SCAN_IPT;
+
+__device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t *warp_tot,
+                                                        uint32_t *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    uint32_t y = __shfl_up_sync(FULL_MASK, x, off);
+    if (lane >= off) x += y;
+  }
+  if (lane == 31) warp_tot[warp] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int w = 0; w < nw; ++w) {
+      uint32_t t = warp_tot[w];
+      warp_tot[w] = run;
+      run += t;
+    }
+    *total = run;
+  }
+  __syncthreads();
+  const uint32_t r = warp_tot[warp] + x - v;
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_reduce(const uint32_t *in, int64_t n,
+                                                        uint32_t *tile_sums) {
+  __shared__ uint32_t red[32];
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+  uint32_t s = 0;
+  for (int k = threadIdx.x; k < SCAN_TILE; k += SCAN_T) {
+    const int64_t idx = base + k;
+    if (idx < n) s += in[idx];
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(FULL_MASK, s, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < SCAN_T / 32; ++w) t += red[w];
+    tile_sums[blockIdx.x] = t;
+  }
+}
+
+// One CTA: exclusive scan of tile_sums in place; grand total to *total.
+__global__ void __launch_bounds__(1024) k_scan_tiles(uint32_t *tile_sums, int64_t ntiles,
+                                                     uint32_t *total) {
+  __shared__ uint32_t warp_tot[32];
+  __shared__ uint32_t chunk_tot;
+  uint32_t carry = 0;
+  for (int64_t c0 = 0; c0 < ntiles; c0 += blockDim.x) {
+    const int64_t idx = c0 + threadIdx.x;
+    const uint32_t v = idx < ntiles ? tile_sums[idx] : 0u;
+    const uint32_t ex = block_excl_scan_u32(v, warp_tot, &chunk_tot);
+    if (idx < ntiles) tile_sums[idx] = carry + ex;
+    carry += chunk_tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
+__device__ __forceinline__ int pad_idx(int k) { return k + (k >> 5); }
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_down(const uint32_t *in, int64_t n,
+                                                      const uint32_t *tile_offs,
+                                                      uint32_t *out) {
+  __shared__ uint32_t tile[SCAN_TILE + SCAN_TILE / 32];
+  __shared__ uint32_t warp_tot[32];
+  __shared__ uint32_t tot;
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+  for (int k = threadIdx.x; k < SCAN_TILE; k += SCAN_T) {
+    const int64_t idx = base + k;
+    tile[pad_idx(k)] = idx < n ? in[idx] : 0u;
+  }
+  __syncthreads();
+  uint32_t loc[SCAN_IPT];
+  uint32_t s = 0;
+#pragma unroll
+  for (int q = 0; q < SCAN_IPT; ++q) {
+    loc[q] = s;
+    s += tile[pad_idx(threadIdx.x * SCAN_IPT + q)];
+  }
+  const uint32_t ex = block_excl_scan_u32(s, warp_tot, &tot) + tile_offs[blockIdx.x];
+#pragma unroll
+  for (int q = 0; q < SCAN_IPT; ++q) tile[pad_idx(threadIdx.x * SCAN_IPT + q)] = ex + loc[q];
+  __syncthreads();
+  for (int k = threadIdx.x; k < SCAN_TILE; k += SCAN_T) {
+    const int64_t idx = base + k;
+    if (idx < n) out[idx] = tile[pad_idx(k)];
+  }
+}
+
+// Exclusive scan of n uint32 (in may equal out), reduce-then-scan; the tile
+// sums are scanned by one CTA when they fit one tile, else recursively.
+// tmp: scan_tmp_words(n) words.  Grand total written to *total (device) when
+// non-null.
+static int exclusive_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp,
+                          uint32_t *total, cudaStream_t s) {
+  const int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  if (ntiles == 0) {
+    if (total) GBS_TRY_CUDA(cudaMemsetAsync(total, 0, sizeof(uint32_t), s));
+    return GBS_OK;
+  }
+  k_scan_reduce<<<(unsigned)ntiles, SCAN_T, 0, s>>>(in, n, tmp);
+  GBS_LAUNCHED(1);
+  if (ntiles <= SCAN_TILE) {
+    k_scan_tiles<<<1, 1024, 0, s>>>(tmp, ntiles, total);
+    GBS_LAUNCHED(1);
+  } else {
+    GBS_TRY(exclusive_scan(tmp, tmp, ntiles, tmp + ntiles + 1, total, s));
+  }
+  k_scan_down<<<(unsigned)ntiles, SCAN_T, 0, s>>>(in, n, tmp, out);
+  GBS_LAUNCHED(1);
+  return GBS_OK;
+}
+
+static int64_t scan_tmp_words(int64_t n) {
+  int64_t w = 1, t = (n + SCAN_TILE - 1) / SCAN_TILE;
+  for (;;) {
+    w += t + 1;
+    if (t <= SCAN_TILE) break;
+    t = (t + SCAN_TILE - 1) / SCAN_TILE;
+  }
+  return w;
+}
+
+// ------------------------------------------------------------------ keep + compact
+
+// Batched handles pass per-system COO offsets (coo_off, nsys+1) and row offsets
+// (row_off, nsys+1): local indices are shifted to the block-diagonal numbering.
+struct KeepArgs {
+  const int32_t *i, *j;
+  int64_t ncoo, nrows, ncols;
+  const int64_t *coo_off, *row_off;  // null for a single system
+  int32_t nsys;
+};
+
+__device__ __forceinline__ bool keep_entry(const KeepArgs &a, int64_t k, int64_t &gi,
+                                           int64_t &gj, bool &bad) {
+  const int32_t li = a.i[k], lj = a.j[k];
+  bad = false;
+  if (li < 0 || lj < 0) return false;
+  if (a.coo_off) {
+    int lo = 0, hi = a.nsys;  // find s with coo_off[s] <= k < coo_off[s+1]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (__ldg(a.coo_off + mid) <= k) lo = mid; else hi = mid;
+    }
+    const int64_t r0 = __ldg(a.row_off + lo), n = __ldg(a.row_off + lo + 1) - r0;
+    if (li >= n || lj >= n) {
+      bad = true;
+      return false;
+    }
+    gi = r0 + li;
+    gj = r0 + lj;
+  } else {
+    if (li >= a.nrows || lj >= a.ncols) {
+      bad = true;
+      return false;
+    }
+    gi = li;
+    gj = lj;
+  }
+  return true;
+}
+
+__global__ void k_keep_flags(KeepArgs a, uint32_t *flags, int32_t *err) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < a.ncoo;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int64_t gi, gj;
+    bool bad;
+    const bool keep = keep_entry(a, k, gi, gj, bad);
+    if (bad) atomicExch(err, GBS_ERR_INDEX);
+    flags[k] = keep ? 1u : 0u;
+  }
+}
+
+__global__ void k_compact(KeepArgs a, const uint32_t *pos, uint64_t *keys, uint32_t *vals) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < a.ncoo;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int64_t gi, gj;
+    bool bad;
+    if (keep_entry(a, k, gi, gj, bad)) {
+      const uint32_t d = pos[k];
+      keys[d] = (uint64_t)gi * (uint64_t)a.ncols + (uint64_t)gj;
+      vals[d] = (uint32_t)k;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ radix sort
+
+constexpr int RS_T = 256, RS_WARPS = RS_T / 32, RS_SLOTS = 16, RS_TILE = RS_T * RS_SLOTS;
+
+__global__ void __launch_bounds__(RS_T) k_radix_hist(const uint64_t *keys, int64_t n,
+                                                     int shift, uint32_t *counts,
+                                                     int64_t ntiles) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+  const int lane = threadIdx.x & 31;
+  for (int k = threadIdx.x; k < RS_TILE; k += RS_T) {
+    const int64_t idx = base + k;
+    const uint32_t d = idx < n ? (uint32_t)((keys[idx] >> shift) & 255u) : 256u;
+    const unsigned peers = __match_any_sync(FULL_MASK, d);
+    if (d < 256u && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
+  }
+  __syncthreads();
+  counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter of one tile.  Warp w owns the contiguous items
+// [base + w*SLOTS*32, base + (w+1)*SLOTS*32); it walks them slot by slot, lane
+// order within a slot, which is the input order, so ranks of equal digits
+// follow input order.  vals_in == null means payload = item index.
+__global__ void __launch_bounds__(RS_T) k_radix_scatter(const uint64_t *keys_in,
+                                                        const uint32_t *vals_in, int64_t n,
+                                                        int shift, const uint32_t *offsets,
+                                                        int64_t ntiles, uint64_t *keys_out,
+                                                        uint32_t *vals_out) {
+  __shared__ uint32_t whist[RS_WARPS][256];
+  __shared__ uint32_t toff[256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int w = 0; w < RS_WARPS; ++w) whist[w][threadIdx.x] = 0;
+  toff[threadIdx.x] = offsets[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * RS_TILE + (int64_t)warp * RS_SLOTS * 32;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  uint64_t key[RS_SLOTS];
+  uint32_t val[RS_SLOTS], rank[RS_SLOTS];
+#pragma unroll
+  for (int sl = 0; sl < RS_SLOTS; ++sl) {
+    const int64_t idx = base + sl * 32 + lane;
+    const bool ok = idx < n;
+    key[sl] = ok ? keys_in[idx] : 0ull;
+    val[sl] = ok ? (vals_in ? vals_in[idx] : (uint32_t)idx) : 0u;
+  }
+#pragma unroll
+  for (int sl = 0; sl < RS_SLOTS; ++sl) {
+    const int64_t idx = base + sl * 32 + lane;
+    const uint32_t d = idx < n ? (uint32_t)((key[sl] >> shift) & 255u) : 256u;
+    const unsigned peers = __match_any_sync(FULL_MASK, d);
+    const uint32_t before = d < 256u ? whist[warp][d] : 0u;
+    rank[sl] = before + (uint32_t)__popc(peers & lt_mask);
+    __syncwarp();
+    if (d < 256u && lane == __ffs(peers) - 1) whist[warp][d] = before + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  {  // per digit: exclusive prefix over warps, plus the tile's global offset
+    const int d = threadIdx.x;
+    uint32_t run = toff[d];
+    for (int w = 0; w < RS_WARPS; ++w) {
+      const uint32_t c = whist[w][d];
+      whist[w][d] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int sl = 0; sl < RS_SLOTS; ++sl) {
+    const int64_t idx = base + sl * 32 + lane;
+    if (idx < n) {
+      const uint32_t d = (uint32_t)((key[sl] >> shift) & 255u);
+      const uint32_t dst = whist[warp][d] + rank[sl];
+      keys_out[dst] = key[sl];
+      vals_out[dst] = val[sl];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ segments
+
+__global__ void k_seg_flags(const uint64_t *keys, int64_t n, uint32_t *flags) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x)
+    flags[t] = (t == 0 || keys[t] != keys[t - 1]) ? 1u : 0u;
+}
+
+__global__ void k_seg_write(const uint64_t *keys, int64_t n, const uint32_t *flags,
+                            const uint32_t *seg, uint64_t *ukey, int32_t *jmap) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    if (flags[t]) {
+      const uint32_t s = seg[t];
+      ukey[s] = keys[t];
+      jmap[s] = (int32_t)t;
+    }
+  }
+}
+
+__global__ void k_csr_cols(const uint64_t *ukey, int64_t nnz, int64_t ncols, int32_t *col,
+                           int32_t *diag_pos) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < nnz;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = ukey[s];
+    const int64_t r = (int64_t)(k / (uint64_t)ncols), c = (int64_t)(k % (uint64_t)ncols);
+    col[s] = (int32_t)c;
+    if (r == c) diag_pos[r] = (int32_t)s;
+  }
+}
+
+// row_ptr[r] = first unique key >= r * ncols, for r in [0, nrows].
+__global__ void k_row_ptr(const uint64_t *ukey, int64_t nnz, int64_t ncols, int64_t nrows,
+                          int32_t *row_ptr) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r <= nrows;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t target = (uint64_t)r * (uint64_t)ncols;
+    int64_t lo = 0, hi = nnz;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (ukey[mid] < target) lo = mid + 1; else hi = mid;
+    }
+    row_ptr[r] = (int32_t)lo;
+  }
+}
+
+__global__ void k_max_row(const int32_t *row_ptr, int64_t nrows, int32_t *out) {
+  int32_t m = 0;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows;
+       r += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, row_ptr[r + 1] - row_ptr[r]);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_xor_sync(FULL_MASK, m, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+static unsigned grid_for(int64_t n, int tpb) {
+  int64_t g = (n + tpb - 1) / tpb;
+  if (g < 1) g = 1;
+  if (g > 1048576) g = 1048576;
+  return (unsigned)g;
+}
+
+// Symbolic stage.  coo_off_h (host, nsys+1) is non-null for batched handles;
+// A->row_off_h, nrows, ncols, ncoo, nsys are set by the caller.
+int symbolic(gbs_mat A, const int32_t *i, const int32_t *j, const int64_t *coo_off_h,
+             cudaStream_t s) {
+  const int64_t ncoo = A->ncoo;
+  KeepArgs ka{i, j, ncoo, A->nrows, A->ncols, nullptr, nullptr, A->nsys};
+  int64_t *d_off = nullptr;
+  uint32_t *flags = nullptr, *scan_tmp = nullptr, *dsc = nullptr;
+  uint64_t *kA = nullptr, *kB = nullptr, *ukey = nullptr;
+  uint32_t *vA = nullptr, *vB = nullptr, *counts = nullptr;
+  int status = GBS_OK;
+  // host mirrors read back after each synchronisation
+  struct Ctl {
+    uint32_t nkept, nnz;
+    int32_t err, maxrow;
+  } hc{};
+  Ctl *dctl = nullptr;
+
+#define SYM_CUDA(call)                                                            \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+      status = (e_ == cudaErrorMemoryAllocation) ? GBS_ERR_ALLOC : GBS_ERR_CUDA;  \
+      goto cleanup;                                                               \
+    }                                                                             \
+  } while (0)
+#define SYM_TRY(call)                                                             \
+  do {                                                                            \
+    status = (call);                                                              \
+    if (status != GBS_OK) goto cleanup;                                           \
+  } while (0)
+
+  {
+    SYM_CUDA(cudaMallocAsync(&dctl, sizeof(Ctl), s));
+    SYM_CUDA(cudaMemsetAsync(dctl, 0, sizeof(Ctl), s));
+    if (coo_off_h) {
+      SYM_CUDA(cudaMallocAsync(&d_off, sizeof(int64_t) * 2 * (A->nsys + 1), s));
+      SYM_CUDA(cudaMemcpyAsync(d_off, coo_off_h, sizeof(int64_t) * (A->nsys + 1),
+                               cudaMemcpyHostToDevice, s));
+      SYM_CUDA(cudaMemcpyAsync(d_off + A->nsys + 1, A->row_off_h.data(),
+                               sizeof(int64_t) * (A->nsys + 1), cudaMemcpyHostToDevice, s));
+      ka.coo_off = d_off;
+      ka.row_off = d_off + A->nsys + 1;
+    }
+    const int64_t nflag = std::max<int64_t>(ncoo, 1);
+    SYM_CUDA(cudaMallocAsync(&flags, sizeof(uint32_t) * nflag, s));
+    SYM_CUDA(cudaMallocAsync(&dsc, sizeof(uint32_t) * nflag, s));
+    SYM_CUDA(cudaMallocAsync(&scan_tmp, sizeof(uint32_t) * scan_tmp_words(nflag), s));
+
+    // 1. keep flags, positions, nkept
+    if (ncoo > 0) {
+      k_keep_flags<<<grid_for(ncoo, 256), 256, 0, s>>>(ka, flags, &dctl->err);
+      GBS_LAUNCHED(1);
+    }
+    SYM_TRY(exclusive_scan(flags, dsc, ncoo, scan_tmp, &dctl->nkept, s));
+    SYM_CUDA(cudaMemcpyAsync(&hc, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    SYM_CUDA(cudaStreamSynchronize(s));
+    if (hc.err != 0) {
+      set_error("mat_create_coo: a kept COO index is out of range");
+      status = GBS_ERR_INDEX;
+      goto cleanup;
+    }
+    const int64_t nkept = hc.nkept;
+    A->nkept = nkept;
+    const int64_t nk = std::max<int64_t>(nkept, 1);
+    SYM_CUDA(cudaMallocAsync(&kA, sizeof(uint64_t) * nk, s));
+    SYM_CUDA(cudaMallocAsync(&kB, sizeof(uint64_t) * nk, s));
+    SYM_CUDA(cudaMallocAsync(&vA, sizeof(uint32_t) * nk, s));
+    SYM_CUDA(cudaMalloc(&vB, sizeof(uint32_t) * nk));  // may become perm
+    if (ncoo > 0) {
+      k_compact<<<grid_for(ncoo, 256), 256, 0, s>>>(ka, dsc, kA, vA);
+      GBS_LAUNCHED(1);
+    }
+
+    // 2. stable LSD radix sort
+    const uint64_t maxkey = (uint64_t)A->nrows * (uint64_t)A->ncols;
+    int bits = 0;
+    while (bits < 64 && (maxkey > 1) && ((maxkey - 1) >> bits) != 0) ++bits;
+    const int passes = (bits + 7) / 8;
+    const int64_t ntiles = (nkept + RS_TILE - 1) / RS_TILE;
+    if (ntiles > 0 && passes > 0) {
+      const int64_t ncount = 256 * ntiles;
+      SYM_CUDA(cudaMallocAsync(&counts, sizeof(uint32_t) * ncount, s));
+      uint32_t *ctmp = nullptr;
+      SYM_CUDA(cudaMallocAsync(&ctmp, sizeof(uint32_t) * scan_tmp_words(ncount), s));
+      uint64_t *kin = kA, *kout = kB;
+      uint32_t *vin = vA, *vout = vB;
+      for (int pass = 0; pass < passes; ++pass) {
+        const int shift = 8 * pass;
+        k_radix_hist<<<(unsigned)ntiles, RS_T, 0, s>>>(kin, nkept, shift, counts, ntiles);
+        GBS_LAUNCHED(1);
+        status = exclusive_scan(counts, counts, ncount, ctmp, nullptr, s);
+        if (status != GBS_OK) {
+          cudaFreeAsync(ctmp, s);
+          goto cleanup;
+        }
+        k_radix_scatter<<<(unsigned)ntiles, RS_T, 0, s>>>(kin, vin, nkept, shift, counts,
+                                                          ntiles, kout, vout);
+        GBS_LAUNCHED(1);
+        std::swap(kin, kout);
+        std::swap(vin, vout);
+      }
+      cudaFreeAsync(ctmp, s);
+      // sorted data is in kin / vin; make kA / vB hold it
+      if (kin != kA) std::swap(kA, kB);
+      if (vin != vB) {
+        // vin == vA: copy into vB (the cudaMalloc'd buffer that becomes perm)
+        SYM_CUDA(cudaMemcpyAsync(vB, vA, sizeof(uint32_t) * nkept, cudaMemcpyDeviceToDevice, s));
+      }
+    } else if (nkept > 0) {
+      SYM_CUDA(cudaMemcpyAsync(vB, vA, sizeof(uint32_t) * nkept, cudaMemcpyDeviceToDevice, s));
+    }
+
+    // 3. segments
+    if (nkept > 0) {
+      k_seg_flags<<<grid_for(nkept, 256), 256, 0, s>>>(kA, nkept, flags);
+      GBS_LAUNCHED(1);
+    }
+    SYM_TRY(exclusive_scan(flags, dsc, nkept, scan_tmp, &dctl->nnz, s));
+    SYM_CUDA(cudaMemcpyAsync(&hc, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    SYM_CUDA(cudaStreamSynchronize(s));
+    const int64_t nnz = hc.nnz;
+    A->nnz = nnz;
+    const int64_t nz1 = std::max<int64_t>(nnz, 1);
+    SYM_CUDA(cudaMalloc(&A->jmap, sizeof(int32_t) * (nnz + 1)));
+    SYM_CUDA(cudaMalloc(&A->col, sizeof(int32_t) * nz1));
+    SYM_CUDA(cudaMalloc(&A->val, sizeof(double) * nz1));
+    SYM_CUDA(cudaMalloc(&A->row_ptr, sizeof(int32_t) * (A->nrows + 1)));
+    SYM_CUDA(cudaMalloc(&A->diag_pos, sizeof(int32_t) * std::max<int64_t>(A->nrows, 1)));
+    SYM_CUDA(cudaMalloc(&A->dinv, sizeof(double) * std::max<int64_t>(A->nrows, 1)));
+    SYM_CUDA(cudaMemsetAsync(A->val, 0, sizeof(double) * nz1, s));
+    SYM_CUDA(cudaMemsetAsync(A->diag_pos, 0xff, sizeof(int32_t) * std::max<int64_t>(A->nrows, 1), s));
+    SYM_CUDA(cudaMemsetAsync(A->dinv, 0, sizeof(double) * std::max<int64_t>(A->nrows, 1), s));
+    SYM_CUDA(cudaMallocAsync(&ukey, sizeof(uint64_t) * nz1, s));
+    A->perm = (int32_t *)vB;
+    vB = nullptr;
+    {
+      const int32_t nk32 = (int32_t)nkept;
+      SYM_CUDA(cudaMemcpyAsync(A->jmap + nnz, &nk32, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    }
+    if (nkept > 0) {
+      k_seg_write<<<grid_for(nkept, 256), 256, 0, s>>>(kA, nkept, flags, dsc, ukey, A->jmap);
+      GBS_LAUNCHED(1);
+    }
+    if (nnz > 0) {
+      k_csr_cols<<<grid_for(nnz, 256), 256, 0, s>>>(ukey, nnz, A->ncols, A->col, A->diag_pos);
+      GBS_LAUNCHED(1);
+    }
+    k_row_ptr<<<grid_for(A->nrows + 1, 256), 256, 0, s>>>(ukey, nnz, A->ncols, A->nrows,
+                                                          A->row_ptr);
+    k_max_row<<<grid_for(A->nrows, 256), 256, 0, s>>>(A->row_ptr, A->nrows, &dctl->maxrow);
+    GBS_LAUNCHED(2);
+    SYM_CUDA(cudaMemcpyAsync(&hc, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    SYM_CUDA(cudaStreamSynchronize(s));
+    A->max_row_nnz = hc.maxrow;
+  }
+
+cleanup:
+  if (dctl) cudaFreeAsync(dctl, s);
+  if (d_off) cudaFreeAsync(d_off, s);
+  if (flags) cudaFreeAsync(flags, s);
+  if (dsc) cudaFreeAsync(dsc, s);
+  if (scan_tmp) cudaFreeAsync(scan_tmp, s);
+  if (kA) cudaFreeAsync(kA, s);
+  if (kB) cudaFreeAsync(kB, s);
+  if (vA) cudaFreeAsync(vA, s);
+  if (counts) cudaFreeAsync(counts, s);
+  if (ukey) cudaFreeAsync(ukey, s);
+  if (vB) cudaFree(vB);
+  cudaStreamSynchronize(s);
+  return status;
+#undef SYM_CUDA
+#undef SYM_TRY
+}
+
+// ------------------------------------------------------------------ numeric
+
+// One thread per nonzero: a_p = v[perm[jmap[p]]] + v[perm[jmap[p]+1]] + ...
+// in increasing COO index order (Sec. 5: each thread accumulates into a single
+// nonzero, no atomics).
+__global__ void k_coo_numeric(int64_t nnz, const int32_t *__restrict__ jmap,
+                              const int32_t *__restrict__ perm, const double *__restrict__ v,
+                              int mode, double *__restrict__ val) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t t0 = __ldg(jmap + p), t1 = __ldg(jmap + p + 1);
+    double sum = __ldg(v + __ldg(perm + t0));
+    for (int32_t t = t0 + 1; t < t1; ++t) sum = __dadd_rn(sum, __ldg(v + __ldg(perm + t)));
+    val[p] = (mode == GBS_ADD) ? __dadd_rn(val[p], sum) : sum;
+  }
+}
+
+// Jacobi: dinv_r = 1 / a_rr; a missing or non-positive diagonal stores 0,
+// which the solves report as GBS_ERR_NOT_SPD for the system holding that row.
+__global__ void k_jacobi(int64_t nrows, const int32_t *__restrict__ diag_pos,
+                         const double *__restrict__ val, double *__restrict__ dinv) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t q = diag_pos[r];
+    const double d = q >= 0 ? val[q] : 0.0;
+    dinv[r] = (d > 0.0) ? 1.0 / d : 0.0;
+  }
+}
+
+int launch_set_values(gbs_mat A, const double *v, int mode, cudaStream_t s) {
+  if (A->nnz > 0) {
+    k_coo_numeric<<<grid_for(A->nnz, 256), 256, 0, s>>>(A->nnz, A->jmap, A->perm, v, mode,
+                                                        A->val);
+    GBS_LAUNCHED(1);
+  }
+  if (A->nrows > 0) {
+    k_jacobi<<<grid_for(A->nrows, 256), 256, 0, s>>>(A->nrows, A->diag_pos, A->val, A->dinv);
+    GBS_LAUNCHED(1);
+  }
+  A->values_set = true;
+  A->val32_valid = false;
+  return GBS_OK;
+}
+
+// FP32 copies for the refined solve: val32 = RN(val), dinv32 = RN(dinv).
+__global__ void k_to_fp32(int64_t nnz, const double *__restrict__ val, float *__restrict__ val32,
+                          int64_t nrows, const double *__restrict__ dinv,
+                          float *__restrict__ dinv32) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += stride)
+    val32[p] = __double2float_rn(val[p]);
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += stride)
+    dinv32[r] = __double2float_rn(dinv[r]);
+}
+
+int launch_to_fp32(gbs_mat A, cudaStream_t s) {
+  if (!A->val32) {
+    GBS_TRY_CUDA(cudaMalloc(&A->val32, sizeof(float) * std::max<int64_t>(A->nnz, 1)));
+    GBS_TRY_CUDA(cudaMalloc(&A->dinv32, sizeof(float) * std::max<int64_t>(A->nrows, 1)));
+  }
+  k_to_fp32<<<grid_for(std::max(A->nnz, A->nrows), 256), 256, 0, s>>>(
+      A->nnz, A->val, A->val32, A->nrows, A->dinv, A->dinv32);
+  GBS_LAUNCHED(1);
+  A->val32_valid = true;
+  return GBS_OK;
+}
+
+// ------------------------------------------------------------------ adjoint scatter
+
+// dLda[p] = -lambda[row p] * x[col p]; dLdv[perm[t]] = dLda[p] for t in the
+// segment of p.  One thread per row.  Ignored COO entries are zeroed by the
+// caller's memset.
+__global__ void k_adjoint_scatter(int64_t nrows, const int32_t *__restrict__ row_ptr,
+                                  const int32_t *__restrict__ col,
+                                  const int32_t *__restrict__ jmap,
+                                  const int32_t *__restrict__ perm,
+                                  const double *__restrict__ lambda,
+                                  const double *__restrict__ x, double *__restrict__ dLda,
+                                  double *__restrict__ dLdv) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const double lr = lambda[r];
+    for (int32_t p = row_ptr[r]; p < row_ptr[r + 1]; ++p) {
+      const double g = -(lr * x[col[p]]);
+      if (dLda) dLda[p] = g;
+      if (dLdv)
+        for (int32_t t = jmap[p]; t < jmap[p + 1]; ++t) dLdv[perm[t]] = g;
+    }
+  }
+}
+
+int launch_adjoint_scatter(gbs_mat A, const double *lambda, const double *x, double *dLda,
+                           double *dLdv, cudaStream_t s) {
+  if (dLdv && A->ncoo > 0 && A->nkept < A->ncoo)
+    GBS_TRY_CUDA(cudaMemsetAsync(dLdv, 0, sizeof(double) * A->ncoo, s));
+  if ((dLda || dLdv) && A->nrows > 0) {
+    k_adjoint_scatter<<<grid_for(A->nrows, 256), 256, 0, s>>>(
+        A->nrows, A->row_ptr, A->col, A->jmap, A->perm, lambda, x, dLda, dLdv);
+    GBS_LAUNCHED(1);
+  }
+  return GBS_OK;
+}
+
+}  // namespace gbs
