@@ -187,6 +187,29 @@ int ksp_adjoint_batched(gbs_mat A, const double *x, const double *dLdx, double *
                         double *dLda, double *dLdv, const ksp_opts *o,
                         ksp_result *res_h, void *stream);
 
+/*
+ * Allocation-free FP64 solve.  The paper has no counterpart: this entry point
+ * exists for callers that must not allocate device memory -- code whose
+ * device memory is budgeted and handed out by another allocator, or that
+ * cannot afford the device-wide synchronisation cudaMalloc / cudaFree imply.
+ * It runs the same persistent Jacobi-PCG kernel as ksp_solve_cg, on a CSR
+ * matrix the caller owns: row_ptr int32[n+1], col int32[nnz] (each < n),
+ * val double[nnz]; b, x double[n].  All its scratch lives in one fixed static
+ * device array (about 8.4 MB, resident on every GPU that loads the library
+ * until the process exits), so n must be <= 262144; a larger n returns
+ * GBS_ERR_ARG without touching the GPU.  It calls no cudaMalloc, cudaFree or
+ * other allocating routine.  Every call shares that array, which keeps the
+ * last call's contents: calls that overlap on the GPU (other streams or host
+ * threads) race, so the caller must serialise them.  The first call on a
+ * device looks up the array's device address; make that first call before
+ * any stream capture.  o: NULL (defaults) or precision GBS_FP64.  res (host):
+ * non-NULL synchronises and fills it; NULL leaves the call asynchronous (its
+ * result is then not retrievable).
+ */
+int ksp_solve_cg_noalloc(int64_t n, const int32_t *row_ptr, const int32_t *col,
+                         const double *val, const double *b, double *x,
+                         const ksp_opts *o, ksp_result *res, void *stream);
+
 /* Synchronises `stream` and copies the results of the last solve on A into the
  * HOST array res (nsys entries for a batched solve, else 1).  Returns the first
  * non-OK status. */

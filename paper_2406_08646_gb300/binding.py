@@ -29,7 +29,8 @@ EXPORTED = ["ksp_opts_default", "mat_create_coo", "mat_create_coo_batched",
             "mat_set_values_coo", "mat_mult", "ksp_solve_cg", "ksp_solve_cg_batched",
             "ksp_adjoint", "ksp_adjoint_batched", "ksp_get_result", "mat_get_info",
             "mat_get_csr", "mat_get_coo_maps", "mat_set_plan", "mat_get_plan",
-            "mat_autotune", "mat_destroy", "gbs_launch_count", "gbs_last_error"]
+            "mat_autotune", "mat_destroy", "gbs_launch_count", "gbs_last_error",
+            "ksp_solve_cg_noalloc"]
 
 
 class KspOpts(ctypes.Structure):
@@ -90,6 +91,7 @@ def lib() -> ctypes.CDLL:
         "mat_destroy": (ctypes.c_int, [P]),
         "gbs_launch_count": (I64, []),
         "gbs_last_error": (ctypes.c_char_p, []),
+        "ksp_solve_cg_noalloc": (ctypes.c_int, [I64, P, P, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

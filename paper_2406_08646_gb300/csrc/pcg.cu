@@ -25,7 +25,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "device_util.cuh"
 #include "internal.cuh"
@@ -723,3 +725,209 @@ int read_results(gbs_mat A, ksp_result *res, int32_t count, cudaStream_t s) {
 }
 
 }  // namespace gbs
+
+// ------------------------------------------------------------------ no-alloc solve
+//
+// ksp_solve_cg_noalloc: the same persistent FP64 PCG kernel, for callers that
+// must not allocate device memory -- e.g. code that works inside a fixed
+// memory budget owned by another allocator, or that cannot afford the device
+// synchronisation cudaMalloc / cudaFree imply.  Its scratch (the r, p, q and
+// D^-1 vectors, the block table, the reduction slots and the control words)
+// lives in one file-scope __device__ array of fixed size, so the call performs
+// no allocation of any kind.  The caller passes the CSR matrix, b and x.
+// Limit: n <= NOALLOC_MAX_ROWS rows (the array holds about 8.4 MB and stays
+// resident on every GPU that loads the library until the process exits).
+// All calls share the array: calls that overlap on the GPU (other streams,
+// other host threads) race and must be serialised by the caller.  The first
+// call on a device looks the array's device address up (cudaGetSymbolAddress,
+// with that device current); make that first call before any stream capture.
+
+namespace {
+
+constexpr int64_t NOALLOC_MAX_ROWS = 262144;
+constexpr int NOALLOC_R = 256, NOALLOC_TPB = 256, NOALLOC_CAP = 2048;
+constexpr int64_t NOALLOC_MAX_BLOCKS = NOALLOC_MAX_ROWS / NOALLOC_R;
+
+struct NoallocScratch {
+  double r[NOALLOC_MAX_ROWS], p[NOALLOC_MAX_ROWS], q[NOALLOC_MAX_ROWS],
+      dinv[NOALLOC_MAX_ROWS];
+  double part[(NOALLOC_MAX_BLOCKS + 8) * gbs::SLOT_STRIDE];
+  int32_t blk_row0[NOALLOC_MAX_BLOCKS + 1];
+  unsigned sys_cnt[4];
+  gbs::SysState st[1];
+  gbs::DevCtl ctl;
+};
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoallocScratch)];
+
+constexpr int kMaxDevices = 256;
+static void *g_noalloc_addr[kMaxDevices] = {nullptr};
+static std::mutex g_noalloc_mu;
+
+// Device address of g_noalloc_scratch on the current device (looked up once
+// per device).  In host code the array's name is only a host-side stand-in,
+// never a device address, so it must not be handed to a kernel directly.
+int noalloc_scratch(NoallocScratch **out) {
+  int dev = 0;
+  GBS_TRY_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) {
+    gbs::set_error("ksp_solve_cg_noalloc: device ordinal %d out of range", dev);
+    return GBS_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      gbs::set_error("ksp_solve_cg_noalloc: cudaGetSymbolAddress failed: %s",
+                     cudaGetErrorString(e));
+      return GBS_ERR_CUDA;
+    }
+    g_noalloc_addr[dev] = p;
+  }
+  *out = static_cast<NoallocScratch *>(g_noalloc_addr[dev]);
+  return GBS_OK;
+}
+
+// D^-1 from the caller's CSR (0 marks a missing or non-positive diagonal) and
+// the block table of ceil(n / NOALLOC_R) blocks.
+__global__ void k_noalloc_prep(int64_t n, const int32_t *__restrict__ row_ptr,
+                               const int32_t *__restrict__ col, const double *__restrict__ val,
+                               double *__restrict__ dinv, int32_t *__restrict__ blk_row0,
+                               int32_t nblocks) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+    double d = 0.0;
+    for (int32_t q = row_ptr[r]; q < row_ptr[r + 1]; ++q)
+      if (col[q] == r) d = val[q];
+    dinv[r] = (d > 0.0) ? 1.0 / d : 0.0;
+  }
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b <= nblocks; b += stride)
+    blk_row0[b] = (int32_t)(b * NOALLOC_R < n ? b * NOALLOC_R : n);
+}
+
+}  // namespace
+
+extern "C" int ksp_solve_cg_noalloc(int64_t n, const int32_t *row_ptr, const int32_t *col,
+                                    const double *val, const double *b, double *x,
+                                    const ksp_opts *o, ksp_result *res, void *stream) {
+  using namespace gbs;
+  if (n < 0 || n > NOALLOC_MAX_ROWS) {
+    set_error("ksp_solve_cg_noalloc: n = %lld is outside [0, %lld], the size of the "
+              "static scratch", (long long)n, (long long)NOALLOC_MAX_ROWS);
+    return GBS_ERR_ARG;
+  }
+  if (n > 0 && (!row_ptr || !col || !val || !b || !x)) {
+    set_error("ksp_solve_cg_noalloc: null CSR, b or x pointer");
+    return GBS_ERR_ARG;
+  }
+  ksp_opts oo;
+  ksp_opts_default(&oo);
+  if (o) oo = *o;
+  if (oo.precision != GBS_FP64) {
+    set_error("ksp_solve_cg_noalloc: only GBS_FP64 is supported");
+    return GBS_ERR_ARG;
+  }
+  if (!(oo.rtol >= 0.0) || oo.debug_barrier_extra < 0) {
+    set_error("ksp_solve_cg_noalloc: invalid options");
+    return GBS_ERR_ARG;
+  }
+  if (oo.maxit < 0) oo.maxit = (int32_t)std::min<int64_t>(10 * std::max<int64_t>(n, 1), 100000);
+  if (oo.timeout_ns <= 0) oo.timeout_ns = 2000000000LL;
+  if (n == 0) {
+    if (res) memset(res, 0, sizeof(*res));
+    return GBS_OK;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  NoallocScratch *S = nullptr;
+  GBS_TRY(noalloc_scratch(&S));
+  const int32_t nblocks = (int32_t)((n + NOALLOC_R - 1) / NOALLOC_R);
+  const size_t smem = (size_t)NOALLOC_CAP * sizeof(double) + 4 * 32 * sizeof(double);
+  int per_sm = 0, nsm = 0, dev = 0;
+  GBS_TRY_CUDA(cudaGetDevice(&dev));
+  GBS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<false>, NOALLOC_TPB,
+                                                             smem));
+  GBS_TRY_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  if (per_sm < 1) {
+    set_error("ksp_solve_cg_noalloc: persistent kernel does not fit on an SM");
+    return GBS_ERR_LAUNCH;
+  }
+  const int G = (int)std::min<int64_t>((int64_t)per_sm * nsm, nblocks);
+  {  // the kernel's dynamic shared-memory limit may have been set lower by
+     // another launch configuration; raise it if needed, never lower it
+    cudaFuncAttributes fa;
+    GBS_TRY_CUDA(cudaFuncGetAttributes(&fa, k_pcg<false>));
+    if (fa.maxDynamicSharedSizeBytes < (int)smem)
+      GBS_TRY_CUDA(cudaFuncSetAttribute(k_pcg<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
+  }
+
+  // the control words and arrival counters must start at zero on every call
+  GBS_TRY_CUDA(cudaMemsetAsync(&S->ctl, 0, sizeof(DevCtl), s));
+  GBS_TRY_CUDA(cudaMemsetAsync(S->sys_cnt, 0, sizeof(S->sys_cnt), s));
+  k_noalloc_prep<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(
+      n, row_ptr, col, val, S->dinv, S->blk_row0, nblocks);
+  GBS_LAUNCHED(1);
+
+  PcgArgs a;
+  memset(&a, 0, sizeof(a));
+  a.nsys = 1;
+  a.ensemble = 1;
+  a.nblocks = nblocks;
+  a.cap = NOALLOC_CAP;
+  a.row_ptr = row_ptr;
+  a.col = col;
+  a.val = val;
+  a.dinv = S->dinv;
+  a.blk_row0 = S->blk_row0;
+  a.b = b;
+  a.x = x;
+  a.r = S->r;
+  a.p = S->p;
+  a.q = S->q;
+  a.part = S->part;
+  a.sys_cnt = S->sys_cnt;
+  a.st = S->st;
+  a.ctl = &S->ctl;
+  a.rtol = oo.rtol;
+  a.maxit = oo.maxit;
+  a.nonzero_guess = oo.nonzero_guess;
+  a.timeout_ns = oo.timeout_ns;
+  a.barrier_extra = oo.debug_barrier_extra;
+  a.max_global = (int64_t)oo.maxit + 4;
+
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3((unsigned)G);
+  cfg.blockDim = dim3((unsigned)NOALLOC_TPB);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_pcg<false>, a);
+  if (e != cudaSuccess) {
+    set_error("ksp_solve_cg_noalloc: cooperative launch failed: %s", cudaGetErrorString(e));
+    return e == cudaErrorCooperativeLaunchTooLarge ? GBS_ERR_LAUNCH : GBS_ERR_CUDA;
+  }
+  count_launches(1);
+  if (!res) return GBS_OK;
+
+  SysState st;
+  DevCtl ctl;
+  GBS_TRY_CUDA(cudaMemcpyAsync(&st, S->st, sizeof(SysState), cudaMemcpyDeviceToHost, s));
+  GBS_TRY_CUDA(cudaMemcpyAsync(&ctl, &S->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, s));
+  GBS_TRY_CUDA(cudaStreamSynchronize(s));
+  res->status = st.active ? (ctl.err ? ctl.err : GBS_ERR_MAXIT) : st.status;
+  res->iterations = st.iterations;
+  res->outer_iterations = 0;
+  res->reserved = 0;
+  res->rnorm0 = st.rnorm0;
+  res->rnorm = st.rnorm;
+  const double bn = sqrt(st.bb);
+  res->true_rel_residual = bn > 0.0 ? sqrt(st.tt) / bn : sqrt(st.tt);
+  if (res->status != GBS_OK) set_error("ksp_solve_cg_noalloc: solve ended with status %d", res->status);
+  return res->status;
+}
