@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = ("CG solve s and SpMV GB/s (% of HBM peak) at rtol 1e-8; "
           "FP32-refined/batched/adjoint vs FP64")
-WORKLOAD = "q1hex_96: 3D Q1 FE Poisson, 96^3 elements, log-uniform kappa, seed 1002"
+WORKLOAD = "q1hex_{ne}: 3D Q1 FE Poisson, {ne}^3 elements, log-uniform kappa, seed 1002"
 
 
 def peaks():
@@ -149,7 +149,8 @@ def run_reference(args, rank: int, world: int):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * statistics.mean(steps), "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nrows": p.nrows, "nnz": A.nnz, "ncoo": p.ncoo,
+            "config": {"workload": WORKLOAD.format(ne=96), "nrows": p.nrows, "nnz": A.nnz,
+                       "ncoo": p.ncoo,
                        "rtol": 1e-8, "iterations": its},
             "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
                              "sample": "whole workload: each step is the oracle's numeric "
@@ -177,7 +178,7 @@ def run_gpu(args, rank: int, world: int):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     L = B.lib()
-    p = W.q1_hex(96, seed=W.SEED_C2)
+    p = W.q1_hex(args.ne, seed=W.SEED_C2)
     rng = np.random.default_rng(77)
     xt_h = rng.standard_normal(p.nrows)
     i_d = torch.from_numpy(p.i).to(dev)
@@ -274,15 +275,78 @@ def run_gpu(args, rank: int, world: int):
         solve_s, step_ms = float(tt[0]), float(tt[1])
 
     # ---- end to end through the C-ABI from pinned host buffers (H2D + D2H in region)
+    e2e_s = None if args.no_e2e else e2e_time(p, dev, stream, sp, L, B, o64, check)
+
+    r64 = results[-1]["fp64"]
+    it = r64["iterations"]
+    hbm, peak_kind = peaks()
+    achieved = pcg_alg_bytes(n, nnz, it) / solve_s / 1e9
+    spmv_s = med["spmv_x100"] / 1e3 / SPMV_REPS
+    spmv_gbs = spmv_alg_bytes(n, nnz) / spmv_s / 1e9
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.ne == 96:
+        s = oracle_sample(p)
+        cpu = {"value": s["solve_s"], "unit": "s", "cores": 1, "kind": "oracle",
+               "sample": (f"whole workload, once: oracle COO assembly "
+                          f"({s['symbolic_s']:.1f} s symbolic, {s['numeric_s']:.2f} s numeric) "
+                          f"then its full FP64 PCG solve ({s['iterations']} iterations, "
+                          f"status {s['status']}); value = the solve")}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": solve_s, "unit": "s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD.format(ne=args.ne), "nrows": n, "nnz": nnz,
+                       "ncoo": ncoo,
+                       "rtol": 1e-8, "spmv_reps": SPMV_REPS,
+                       "l2": "no flush: every input is larger than L2 (CSR 290 MB, COO 906 MB)",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "plan": plan},
+            "rows_ms": med,
+            "iterations": {k: results[-1][k]["iterations"] for k in results[-1]},
+            "outer_iterations_fp32_refined": results[-1]["fp32_refined"]["outer_iterations"],
+            "true_rel_residual": {k: results[-1][k]["true_rel_residual"] for k in results[-1]},
+            "status": {k: results[-1][k]["status"] for k in results[-1]},
+            "spmv": {"gbs": spmv_gbs, "frac": spmv_gbs / hbm, "us": spmv_s * 1e6,
+                     "alg_bytes": spmv_alg_bytes(n, nnz)},
+            "roofline": {"kernel": "k_pcg<false> (persistent FP64 PCG)", "bound": "hbm",
+                         "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": None,
+                         "alg_bytes": pcg_alg_bytes(n, nnz, it)},
+            "refined_vs_fp64": med["solve_fp32_refined"] / med["solve_fp64"],
+            "adjoint_vs_fp64": med["adjoint"] / med["solve_fp64"],
+            "e2e": None if e2e_s is None else {"value": e2e_s, "unit": "s",
+                    "h2d_bytes_per_step": int(ncoo * 16 + n * 8),
+                    "d2h_bytes_per_step": int(n * 8),
+                    "what": "pinned host COO + b -> device, assemble, FP64 solve, x -> host"},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "wall_s": wall,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def e2e_time(p, dev, stream, sp, L, B, o64, check):
+    """Median over 2 timed reps (after 1 untimed) of: pinned host COO (i, j, v)
+    and b copied to the device, mat_create_coo, mat_set_values_coo, FP64
+    ksp_solve_cg, x copied back to pinned host memory -- all on one stream,
+    timed with CUDA events."""
+    import torch
+    n = p.nrows
     i_h = torch.from_numpy(p.i).pin_memory()
     j_h = torch.from_numpy(p.j).pin_memory()
     v_h = torch.from_numpy(p.v).pin_memory()
     b_h = torch.from_numpy(p.b).pin_memory()
     x_h = torch.empty(n, dtype=torch.float64).pin_memory()
-    i2, j2 = torch.empty_like(i_d), torch.empty_like(j_d)
-    v2, b2 = torch.empty_like(v_d), torch.empty_like(b_d)
-    x2 = torch.empty_like(x64)
-    e2e = []
+    i2 = torch.empty(p.ncoo, dtype=torch.int32, device=dev)
+    j2 = torch.empty(p.ncoo, dtype=torch.int32, device=dev)
+    v2 = torch.empty(p.ncoo, dtype=torch.float64, device=dev)
+    b2 = torch.empty(n, dtype=torch.float64, device=dev)
+    x2 = torch.empty(n, dtype=torch.float64, device=dev)
+    out = []
     for rep in range(3):
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -301,60 +365,11 @@ def run_gpu(args, rank: int, world: int):
         e1.synchronize()
         r = B.ksp_get_result(A, 1, stream)[0]
         B.mat_destroy(A)
+        if r["status"] != B.OK:
+            raise B.GbsError(r["status"], "end-to-end solve failed")
         if rep > 0:
-            e2e.append(e0.elapsed_time(e1) / 1e3)
-        assert r["status"] == B.OK
-    e2e_s = statistics.median(e2e)
-
-    r64 = results[-1]["fp64"]
-    it = r64["iterations"]
-    hbm, peak_kind = peaks()
-    achieved = pcg_alg_bytes(n, nnz, it) / solve_s / 1e9
-    spmv_s = med["spmv_x100"] / 1e3 / SPMV_REPS
-    spmv_gbs = spmv_alg_bytes(n, nnz) / spmv_s / 1e9
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        s = oracle_sample(p)
-        cpu = {"value": s["solve_s"], "unit": "s", "cores": 1, "kind": "oracle",
-               "sample": (f"whole workload, once: oracle COO assembly "
-                          f"({s['symbolic_s']:.1f} s symbolic, {s['numeric_s']:.2f} s numeric) "
-                          f"then its full FP64 PCG solve ({s['iterations']} iterations, "
-                          f"status {s['status']}); value = the solve")}
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": solve_s, "unit": "s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
-            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nrows": n, "nnz": nnz, "ncoo": ncoo,
-                       "rtol": 1e-8, "spmv_reps": SPMV_REPS,
-                       "l2": "no flush: every input is larger than L2 (CSR 290 MB, COO 906 MB)",
-                       "parallelism": "replicas" if world > 1 else "single GPU",
-                       "plan": plan},
-            "rows_ms": med,
-            "iterations": {k: results[-1][k]["iterations"] for k in results[-1]},
-            "outer_iterations_fp32_refined": results[-1]["fp32_refined"]["outer_iterations"],
-            "true_rel_residual": {k: results[-1][k]["true_rel_residual"] for k in results[-1]},
-            "status": {k: results[-1][k]["status"] for k in results[-1]},
-            "spmv": {"gbs": spmv_gbs, "frac": spmv_gbs / hbm, "us": spmv_s * 1e6,
-                     "alg_bytes": spmv_alg_bytes(n, nnz)},
-            "roofline": {"kernel": "k_pcg<false> (persistent FP64 PCG)", "bound": "hbm",
-                         "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": None,
-                         "alg_bytes": pcg_alg_bytes(n, nnz, it)},
-            "refined_vs_fp64": med["solve_fp32_refined"] / med["solve_fp64"],
-            "adjoint_vs_fp64": med["adjoint"] / med["solve_fp64"],
-            "e2e": {"value": e2e_s, "unit": "s",
-                    "h2d_bytes_per_step": int(ncoo * 16 + n * 8),
-                    "d2h_bytes_per_step": int(n * 8),
-                    "what": "pinned host COO + b -> device, assemble, FP64 solve, x -> host"},
-            "gpu_launches": launches,
-            "clocks": clk,
-            "wall_s": wall,
-            "cpu_baseline": cpu,
-        }
-        print(json.dumps(line), flush=True)
-    return 0
+            out.append(e0.elapsed_time(e1) / 1e3)
+    return statistics.median(out)
 
 
 def main():
@@ -364,6 +379,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbs", choices=["gbs", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ne", type=int, default=96,
+                    help="elements per side of the Q1 workload (96 = the benchmark; "
+                         "smaller only for profiling captures)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
