@@ -18,7 +18,10 @@
  *   - One stream handle per call, device pointers in and out: Sec. 2.
  *
  * Conventions for every entry point:
- *   - Pointers are DEVICE pointers unless the comment says "host".
+ *   - Pointers are DEVICE pointers unless the comment says "host".  The
+ *     vectors handed to the solves (b, x, dLdx, lambda) must be 16-byte
+ *     aligned (the kernels stream them with bulk copies); GBS_ERR_ARG
+ *     otherwise.
  *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
  *     stream.  All work is enqueued on that stream.  Unless stated otherwise a
  *     call is asynchronous: the caller keeps every borrowed buffer alive (and
@@ -194,9 +197,10 @@ int ksp_adjoint_batched(gbs_mat A, const double *x, const double *dLdx, double *
  * cannot afford the device-wide synchronisation cudaMalloc / cudaFree imply.
  * It runs the same persistent Jacobi-PCG kernel as ksp_solve_cg, on a CSR
  * matrix the caller owns: row_ptr int32[n+1], col int32[nnz] (each < n),
- * val double[nnz]; b, x double[n].  All its scratch lives in one fixed static
- * device array (about 8.4 MB, resident on every GPU that loads the library
- * until the process exits), so n must be <= 262144; a larger n returns
+ * val double[nnz]; b, x double[n]; all five 16-byte aligned.  All
+ * its scratch lives in one fixed static device array (about 8.4 MB, resident
+ * on every GPU that loads the library until the process exits), so n must be
+ * <= 262144; a larger n returns
  * GBS_ERR_ARG without touching the GPU.  It calls no cudaMalloc, cudaFree or
  * other allocating routine.  Every call shares that array, which keeps the
  * last call's contents: calls that overlap on the GPU (other streams or host
@@ -215,6 +219,12 @@ int ksp_solve_cg_noalloc(int64_t n, const int32_t *row_ptr, const int32_t *col,
  * non-OK status. */
 int ksp_get_result(gbs_mat A, ksp_result *res, int32_t count, void *stream);
 
+/* Diagnostic: wall time the last solve on A spent in each phase of its
+ * persistent kernel, as seen by CTA 0 between grid barriers (ns, HOST array of
+ * 5: setup, SpMV phase, x/r update phase, p update phase, closing true
+ * residual).  Synchronises `stream`. */
+int ksp_get_phase_ns(gbs_mat A, int64_t *phase_ns, void *stream);
+
 /* Sizes (host outputs; any may be NULL). */
 int mat_get_info(gbs_mat A, int64_t *nrows, int64_t *ncols, int64_t *nnz,
                  int64_t *ncoo, int32_t *nsys);
@@ -230,16 +240,21 @@ int mat_get_coo_maps(gbs_mat A, const int32_t **perm, const int32_t **jmap,
                      int64_t *nkept);
 
 /*
- * Launch plan: rows_per_block rows per work block (a power of two in
- * [32, 1024]) and threads_per_block (a multiple of 32 in [64, 512] and
- * >= rows_per_block) used by mat_mult and the solves.  mat_set_plan
- * synchronises the device (the old plan may be in use).  mat_create_coo picks a
- * default; mat_autotune times candidates with CUDA events on `stream` and
- * keeps the fastest (it synchronises).  Host outputs may be NULL.
+ * Launch plan used by mat_mult and the solves.  Every warp of the persistent
+ * kernels is an independent worker with its own bulk-copy pipeline:
+ * spmv_rows rows per SpMV work block (a multiple of 32 in [32, 512]; lanes
+ * own rows), update_rows rows per vector-update block (a multiple of 32 in
+ * [32, 4096]), warps per CTA (1..16) and pipeline stages per warp (2..4).
+ * mat_set_plan synchronises the device (the old plan may be in use) and
+ * returns GBS_ERR_ARG for a plan whose stages do not fit in shared memory.
+ * mat_create_coo picks a default; mat_autotune times candidates (a fixed
+ * 30-iteration FP64 solve each, CUDA events on `stream`) and keeps the
+ * fastest (it synchronises).  Host outputs may be NULL.
  */
-int mat_set_plan(gbs_mat A, int32_t rows_per_block, int32_t threads_per_block);
-int mat_get_plan(gbs_mat A, int32_t *rows_per_block, int32_t *threads_per_block,
-                 int32_t *persistent_ctas);
+int mat_set_plan(gbs_mat A, int32_t spmv_rows, int32_t update_rows, int32_t warps,
+                 int32_t stages);
+int mat_get_plan(gbs_mat A, int32_t *spmv_rows, int32_t *update_rows, int32_t *warps,
+                 int32_t *stages, int32_t *persistent_ctas);
 int mat_autotune(gbs_mat A, void *stream);
 
 /* Releases every device buffer the handle owns.  Synchronises the device

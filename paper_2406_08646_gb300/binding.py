@@ -30,7 +30,7 @@ EXPORTED = ["ksp_opts_default", "mat_create_coo", "mat_create_coo_batched",
             "ksp_adjoint", "ksp_adjoint_batched", "ksp_get_result", "mat_get_info",
             "mat_get_csr", "mat_get_coo_maps", "mat_set_plan", "mat_get_plan",
             "mat_autotune", "mat_destroy", "gbs_launch_count", "gbs_last_error",
-            "ksp_solve_cg_noalloc"]
+            "ksp_solve_cg_noalloc", "ksp_get_phase_ns"]
 
 
 class KspOpts(ctypes.Structure):
@@ -85,13 +85,14 @@ def lib() -> ctypes.CDLL:
         "mat_get_info": (ctypes.c_int, [P, P, P, P, P, P]),
         "mat_get_csr": (ctypes.c_int, [P, PP, PP, PP, P]),
         "mat_get_coo_maps": (ctypes.c_int, [P, PP, PP, P]),
-        "mat_set_plan": (ctypes.c_int, [P, I32, I32]),
-        "mat_get_plan": (ctypes.c_int, [P, P, P, P]),
+        "mat_set_plan": (ctypes.c_int, [P, I32, I32, I32, I32]),
+        "mat_get_plan": (ctypes.c_int, [P, P, P, P, P, P]),
         "mat_autotune": (ctypes.c_int, [P, P]),
         "mat_destroy": (ctypes.c_int, [P]),
         "gbs_launch_count": (I64, []),
         "gbs_last_error": (ctypes.c_char_p, []),
         "ksp_solve_cg_noalloc": (ctypes.c_int, [I64, P, P, P, P, P, P, P, P]),
+        "ksp_get_phase_ns": (ctypes.c_int, [P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -231,6 +232,13 @@ def ksp_get_result(A, count: int = 1, stream=None):
     return [r.as_dict() for r in res]
 
 
+def ksp_get_phase_ns(A, stream=None) -> dict:
+    """Per-phase time (ns) of the last solve's persistent kernel (CTA 0's view)."""
+    arr = (ctypes.c_int64 * 5)()
+    _check(lib().ksp_get_phase_ns(A, ctypes.cast(arr, ctypes.c_void_p), _stream(stream)))
+    return dict(zip(["setup", "spmv", "update_xr", "update_p", "true_residual"], list(arr)))
+
+
 def mat_get_info(A) -> dict:
     nr, nc, nnz, ncoo = (ctypes.c_int64() for _ in range(4))
     nsys = ctypes.c_int32()
@@ -277,14 +285,15 @@ def mat_get_coo_maps(A):
             _view(jmap.value, info["nnz"] + 1, torch.int32))
 
 
-def mat_set_plan(A, rows_per_block: int, threads_per_block: int):
-    _check(lib().mat_set_plan(A, rows_per_block, threads_per_block))
+def mat_set_plan(A, spmv_rows: int, update_rows: int, warps: int, stages: int):
+    _check(lib().mat_set_plan(A, spmv_rows, update_rows, warps, stages))
 
 
 def mat_get_plan(A) -> dict:
-    r, t, g = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
-    _check(lib().mat_get_plan(A, ctypes.byref(r), ctypes.byref(t), ctypes.byref(g)))
-    return {"rows_per_block": r.value, "threads_per_block": t.value, "persistent_ctas": g.value}
+    v = [ctypes.c_int32() for _ in range(5)]
+    _check(lib().mat_get_plan(A, *[ctypes.byref(t) for t in v]))
+    return dict(zip(["spmv_rows", "update_rows", "warps", "stages", "persistent_ctas"],
+                    [t.value for t in v]))
 
 
 def mat_autotune(A, stream=None):
@@ -362,11 +371,14 @@ class Mat:
     def coo_maps(self):
         return mat_get_coo_maps(self.h)
 
-    def set_plan(self, rows_per_block, threads_per_block):
-        mat_set_plan(self.h, rows_per_block, threads_per_block)
+    def set_plan(self, spmv_rows, update_rows=256, warps=8, stages=2):
+        mat_set_plan(self.h, spmv_rows, update_rows, warps, stages)
 
     def plan(self) -> dict:
         return mat_get_plan(self.h)
+
+    def phase_ns(self) -> dict:
+        return ksp_get_phase_ns(self.h)
 
     def autotune(self, stream=None):
         mat_autotune(self.h, stream)

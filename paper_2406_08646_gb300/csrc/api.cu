@@ -34,22 +34,24 @@ static void free_handle(gbs_mat A) {
   cudaSetDevice(A->device);
   if (A->graph) cudaGraphExecDestroy(A->graph);
   void *dev[] = {A->row_ptr, A->col, A->val, A->val32, A->perm, A->jmap, A->diag_pos,
-                 A->dinv, A->dinv32, A->blk_row0, A->blk_sys, A->sys_blk0, A->r, A->p,
-                 A->q, A->r32, A->p32, A->q32, A->d32, A->part, A->sys_slot0, A->sys_cnt,
-                 A->st, A->ctl};
+                 A->dinv, A->dinv32, A->r, A->p, A->q, A->r32, A->p32, A->q32, A->d32,
+                 A->part, A->sys_cnt, A->st, A->ctl, A->err_word};
   for (void *p : dev)
     if (p) cudaFree(p);
+  free_table(A->ta);
+  free_table(A->te);
   if (A->st_host) cudaFreeHost(A->st_host);
   cudaSetDevice(cur);
   delete A;
 }
 
+// Default plan: SpMV blocks of 32 rows (one row per lane) for long rows, 64
+// or 128 for short ones; 256-row update blocks; 8 warps; 2 or 3 stages.
 static int default_plan(gbs_mat A) {
-  // One row per thread, 256 threads; shorter blocks for very long rows so the
-  // staged products of a block stay within one chunk.
-  int32_t R = 256;
-  while (R > 32 && (int64_t)R * A->max_row_nnz > 8192) R >>= 1;
-  return build_plan(A, R, std::max<int32_t>(R, 64));
+  const int32_t m = std::max<int32_t>(A->max_row_nnz, 1);
+  const int32_t Ra = m > 16 ? 32 : (m > 8 ? 64 : 128);
+  if (build_plan(A, Ra, 256, 8, 3) == GBS_OK) return GBS_OK;
+  return build_plan(A, Ra, 256, 8, 2);
 }
 
 static int64_t max_system_rows(gbs_mat A, bool per_system) {
@@ -238,6 +240,10 @@ static int solve_entry(gbs_mat A, const double *b, double *x, const ksp_opts *o,
     set_error("%s: mat_set_values_coo has not been called", fn);
     return GBS_ERR_ARG;
   }
+  if ((((uintptr_t)b | (uintptr_t)x) & 15u) != 0) {
+    set_error("%s: b and x must be 16-byte aligned device pointers", fn);
+    return GBS_ERR_ARG;
+  }
   ksp_opts oo;
   GBS_TRY(fill_opts(A, o, oo, per_system));
   GBS_TRY(use_device(A));
@@ -300,6 +306,21 @@ int ksp_get_result(gbs_mat A, ksp_result *res, int32_t count, void *stream) {
   return read_results(A, res, count, (cudaStream_t)stream);
 }
 
+int ksp_get_phase_ns(gbs_mat A, int64_t *phase_ns, void *stream) {
+  GBS_TRY(check_mat(A, "ksp_get_phase_ns"));
+  if (!phase_ns || !A->ctl) {
+    set_error("ksp_get_phase_ns: no solve has run on this matrix, or null output");
+    return GBS_ERR_ARG;
+  }
+  GBS_TRY(use_device(A));
+  DevCtl c;
+  GBS_TRY_CUDA(cudaMemcpyAsync(&c, A->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost,
+                               (cudaStream_t)stream));
+  GBS_TRY_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  for (int k = 0; k < 5; ++k) phase_ns[k] = c.phase_ns[k];
+  return GBS_OK;
+}
+
 int mat_get_info(gbs_mat A, int64_t *nrows, int64_t *ncols, int64_t *nnz, int64_t *ncoo,
                  int32_t *nsys) {
   GBS_TRY(check_mat(A, "mat_get_info"));
@@ -329,18 +350,21 @@ int mat_get_coo_maps(gbs_mat A, const int32_t **perm, const int32_t **jmap, int6
   return GBS_OK;
 }
 
-int mat_set_plan(gbs_mat A, int32_t rows_per_block, int32_t threads_per_block) {
+int mat_set_plan(gbs_mat A, int32_t spmv_rows, int32_t update_rows, int32_t warps,
+                 int32_t stages) {
   GBS_TRY(check_mat(A, "mat_set_plan"));
   GBS_TRY(use_device(A));
   GBS_TRY_CUDA(cudaDeviceSynchronize());  // plan arrays may be in use
-  return build_plan(A, rows_per_block, threads_per_block);
+  return build_plan(A, spmv_rows, update_rows, warps, stages);
 }
 
-int mat_get_plan(gbs_mat A, int32_t *rows_per_block, int32_t *threads_per_block,
-                 int32_t *persistent_ctas) {
+int mat_get_plan(gbs_mat A, int32_t *spmv_rows, int32_t *update_rows, int32_t *warps,
+                 int32_t *stages, int32_t *persistent_ctas) {
   GBS_TRY(check_mat(A, "mat_get_plan"));
-  if (rows_per_block) *rows_per_block = A->rows_per_block;
-  if (threads_per_block) *threads_per_block = A->tpb;
+  if (spmv_rows) *spmv_rows = A->Ra;
+  if (update_rows) *update_rows = A->Re;
+  if (warps) *warps = A->nwarps;
+  if (stages) *stages = A->nstages;
   if (persistent_ctas) *persistent_ctas = A->grid_fp64;
   return GBS_OK;
 }
@@ -356,8 +380,11 @@ int mat_autotune(gbs_mat A, void *stream) {
   if (A->nrows != A->ncols || A->nrows == 0) return GBS_OK;
   GBS_TRY(use_device(A));
   cudaStream_t s = (cudaStream_t)stream;
-  const int cands[][2] = {{64, 64},   {128, 128}, {256, 256}, {512, 512},
-                          {128, 256}, {256, 512}, {64, 128}};
+  // (SpMV rows, update rows, warps per CTA, stages)
+  const int cands[][4] = {{32, 256, 8, 2},  {32, 256, 8, 3},  {32, 512, 8, 2},
+                          {64, 256, 8, 2},  {64, 256, 8, 3},  {128, 256, 8, 3},
+                          {64, 512, 8, 2},  {128, 512, 8, 2}, {32, 256, 16, 2},
+                          {64, 256, 16, 2}, {32, 128, 12, 3}, {64, 256, 4, 4}};
   double *b = nullptr, *x = nullptr;
   GBS_TRY_CUDA(cudaMalloc(&b, sizeof(double) * A->nrows));
   GBS_TRY_CUDA(cudaMalloc(&x, sizeof(double) * A->nrows));
@@ -371,12 +398,11 @@ int mat_autotune(gbs_mat A, void *stream) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  int bestR = A->rows_per_block, bestT = A->tpb;
+  int best_plan[4] = {A->Ra, A->Re, A->nwarps, A->nstages};
   float best = 1e30f;
   int st = GBS_OK;
   for (const auto &c : cands) {
-    if ((int64_t)c[0] * A->max_row_nnz > 4 * 8192) continue;
-    if (build_plan(A, c[0], c[1]) != GBS_OK) continue;
+    if (build_plan(A, c[0], c[1], c[2], c[3]) != GBS_OK) continue;
     if (launch_spmv(A, x, b, s) != GBS_OK) continue;
     if (solve(A, b, x, o, false, false, s) != GBS_OK) continue;  // warm-up
     cudaEventRecord(e0, s);
@@ -390,8 +416,7 @@ int mat_autotune(gbs_mat A, void *stream) {
     cudaEventElapsedTime(&ms, e0, e1);
     if (ms < best) {
       best = ms;
-      bestR = c[0];
-      bestT = c[1];
+      for (int k = 0; k < 4; ++k) best_plan[k] = c[k];
     }
   }
   cudaEventDestroy(e0);
@@ -402,7 +427,7 @@ int mat_autotune(gbs_mat A, void *stream) {
     set_error("mat_autotune: a timed run failed");
     return st;
   }
-  return build_plan(A, bestR, bestT);
+  return build_plan(A, best_plan[0], best_plan[1], best_plan[2], best_plan[3]);
 }
 
 int mat_destroy(gbs_mat A) {

@@ -1,6 +1,6 @@
 // Device helpers shared by the kernels of libgbs.so: memory-order primitives,
-// bounded grid barrier, deterministic block reductions and the staged CSR row
-// product used by SpMV and by the fused CG phases.
+// shared-memory barriers and bulk copies, the bounded grid barrier and
+// deterministic block reductions.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -39,6 +39,74 @@ __device__ __forceinline__ int ld_relaxed_s32(const int32_t *p) {
 template <typename T>
 __device__ __forceinline__ T ldcg(const T *p) {
   return __ldcg(p);
+}
+
+// ---- shared-memory mbarrier + bulk (TMA) copies ---------------------------
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+
+// Make barrier initialisation visible to the async proxy (bulk copies).
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Order this thread's generic-proxy accesses (shared and global) before its
+// later async-proxy (bulk copy) accesses.
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async;" ::: "memory");
+}
+
+// 1-D bulk copy global -> shared, completion counted on `bar` (bytes: multiple
+// of 16; both addresses 16-byte aligned).  The matrix stream is marked
+// evict-first in L2 so it does not push out the vectors gathered by SpMV.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes,
+                                          uint64_t *bar, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+      "[%0], [%1], %2, [%3], %4;" ::"r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
+      : "memory");
+}
+
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
 }
 
 // Grid-wide barrier for a cooperative (co-resident) launch.  Monotonic 64-bit
@@ -81,6 +149,7 @@ struct GridBarrier {
         }
       }
       __threadfence();
+      fence_proxy_async();
       s_ok = ok;
     }
     __syncthreads();
@@ -114,55 +183,8 @@ __device__ __forceinline__ void block_reduce(T (&v)[NV], T *scratch) {
   __syncthreads();
 }
 
-// Rounded product and sum with no fused multiply-add, so a row sum reproduces
-// "s = s + a*x" evaluated left to right in the value type.
-__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
-
-// Staged CSR product for one work block of rows [r0, r1) (r1 - r0 <= blockDim.x).
-// The block's nonzeros are streamed with coalesced loads in chunks of `cap`;
-// each product val*x[col] is written to shared memory `prod`, then the thread
-// owning row r0 + threadIdx.x sums its row's products in CSR order starting
-// from 0.  Returns that row sum (0 for threads without a row).  The matrix is
-// read through the read-only path; x is read with plain loads because inside a
-// persistent kernel it is written by other CTAs between grid barriers.
-template <typename T>
-__device__ __forceinline__ T staged_row_product(const int32_t *__restrict__ row_ptr,
-                                                const int32_t *__restrict__ col,
-                                                const T *__restrict__ val, const T *x,
-                                                int32_t r0, int32_t r1, T *prod, int cap) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int32_t a = __ldg(row_ptr + r0), e = __ldg(row_ptr + r1);
-  const int32_t r = r0 + tid;
-  const bool has = r < r1;
-  const int32_t rs = has ? __ldg(row_ptr + r) : 0;
-  const int32_t re = has ? __ldg(row_ptr + r + 1) : 0;
-  T acc = T(0);
-  for (int32_t c0 = a; c0 < e; c0 += cap) {
-    const int n = min(e - c0, cap);
-    const int32_t *cc = col + c0;
-    const T *vv = val + c0;
-    int k = tid;
-    for (; k + 3 * nt < n; k += 4 * nt) {
-      const int32_t j0 = __ldg(cc + k), j1 = __ldg(cc + k + nt);
-      const int32_t j2 = __ldg(cc + k + 2 * nt), j3 = __ldg(cc + k + 3 * nt);
-      const T a0 = __ldg(vv + k), a1 = __ldg(vv + k + nt);
-      const T a2 = __ldg(vv + k + 2 * nt), a3 = __ldg(vv + k + 3 * nt);
-      const T x0 = x[j0], x1 = x[j1], x2 = x[j2], x3 = x[j3];
-      prod[k] = mul_rn(a0, x0);
-      prod[k + nt] = mul_rn(a1, x1);
-      prod[k + 2 * nt] = mul_rn(a2, x2);
-      prod[k + 3 * nt] = mul_rn(a3, x3);
-    }
-    for (; k < n; k += nt) prod[k] = mul_rn(__ldg(vv + k), x[__ldg(cc + k)]);
-    __syncthreads();
-    const int32_t lo = max(rs, c0), hi = min(re, c0 + n);
-    for (int32_t q = lo; q < hi; ++q) acc = add_rn(acc, prod[q - c0]);
-    __syncthreads();
-  }
-  return acc;
-}
+// Fused multiply-add, correctly rounded once.
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
 }  // namespace gbs

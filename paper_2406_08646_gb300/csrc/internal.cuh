@@ -69,8 +69,18 @@ struct DevCtl {
   unsigned long long bar;  // grid-barrier arrival counter (monotonic)
   int32_t err;             // GBS_ERR_TIMEOUT etc., 0 = none
   int32_t n_active;        // systems still iterating
-  int32_t diag_bad;        // set by the Jacobi setup: missing / non-positive diagonal
-  int32_t pad;
+  int64_t phase_ns[5];     // CTA 0's time per phase: setup, A, B, C, final residual
+};
+
+// Device block table plus its host mirror (see BlockTable in pipe.cuh).
+struct TableDev {
+  int32_t nblocks = 0;
+  int32_t *row0 = nullptr;       // nblocks + 1
+  int32_t *nz0 = nullptr;        // nblocks + 1
+  int32_t *sys = nullptr;        // nblocks
+  int32_t *sys_blk0 = nullptr;   // nsys + 1
+  int32_t *sys_slot0 = nullptr;  // nsys + 1 (for slot_workers workers)
+  std::vector<int32_t> sys_blk0_h;
 };
 
 }  // namespace gbs
@@ -98,22 +108,23 @@ struct gbs_mat_s {
   std::vector<int64_t> row_off_h;  // nsys + 1
   std::vector<int32_t> max_row_sys_h;
 
-  // launch plan
-  int32_t rows_per_block = 256, tpb = 256, cap = 2048;  // cap: staged products
-  int32_t nblocks = 0;
-  int32_t *blk_row0 = nullptr;  // nblocks + 1
-  int32_t *blk_sys = nullptr;   // nblocks
-  int32_t *sys_blk0 = nullptr;  // nsys + 1
-  std::vector<int32_t> sys_blk0_h;
-  int32_t grid_fp64 = 0, grid_fp32 = 0;  // persistent grid sizes (cached per plan)
+  // launch plan: two block tables (SpMV phases, vector-update phases), warps
+  // per CTA, pipeline stages and the per-warp stage size
+  gbs::TableDev ta, te;
+  int32_t Ra = 32, Re = 256;  // rows per SpMV block / per update block
+  int32_t nwarps = 8, nstages = 2;
+  int32_t tpb = 256;          // 32 * nwarps
+  int32_t cap = 1024;         // staged nonzeros per SpMV block
+  int64_t stage_bytes = 0;
+  int32_t grid_fp64 = 0, grid_fp32 = 0, grid_spmv = 0;  // persistent grid sizes (per plan)
+  int32_t *err_word = nullptr;  // device error word of the SpMV pipeline
 
   // solver workspace (device, allocated on first solve)
   double *r = nullptr, *p = nullptr, *q = nullptr;
   float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr;
-  double *part = nullptr;       // reduction slots
+  double *part = nullptr;       // reduction slots (table A region, then table E)
   int64_t part_cap = 0;
-  int32_t *sys_slot0 = nullptr; // nsys + 1, for the current grid size
-  int32_t slot_grid = -1;       // grid size sys_slot0 was built for
+  int32_t slot_workers = -1;    // worker count the slot offsets were built for
   unsigned *sys_cnt = nullptr;  // nsys arrival counters
   gbs::SysState *st = nullptr;  // nsys
   gbs::DevCtl *ctl = nullptr;
@@ -129,7 +140,9 @@ struct gbs_mat_s {
 namespace gbs {
 
 int ensure_solver_workspace(gbs_mat A, bool refined);
-int build_plan(gbs_mat A, int32_t rows_per_block, int32_t tpb);
+int build_plan(gbs_mat A, int32_t spmv_rows, int32_t update_rows, int32_t nwarps,
+               int32_t nstages);
+void free_table(TableDev &t);
 int launch_spmv(gbs_mat A, const double *x, double *y, cudaStream_t s);
 int launch_set_values(gbs_mat A, const double *v, int mode, cudaStream_t s);
 int launch_to_fp32(gbs_mat A, cudaStream_t s);

@@ -2,26 +2,33 @@
 // no host round trip; Sec. 7 diagonal preconditioning and batched systems;
 // Sec. 2 A7 FP32 inner solve under FP64 refinement).
 //
-// One cooperative launch runs the whole solve.  Rows are cut into work blocks
-// of at most rows_per_block rows that never straddle two systems; CTA c
-// handles blocks c, c+G, c+2G, ... in every phase.  Per iteration:
-//   A: q = A p (staged CSR product) fused with the partial p.q      | barrier
-//   B: x += alpha p, r -= alpha q, z = D^-1 r, partial r.z, r.r     | barrier
+// One cooperative launch runs the whole solve.  Every warp is an independent
+// worker with its own bulk-copy pipeline (pipe.cuh); global warp w takes
+// blocks w, w+W, w+2W, ... of the phase's block table (SpMV blocks for
+// products, larger update blocks for the vector updates; blocks never straddle
+// two systems).  Per iteration:
+//   A: q = A p (one FMA per nonzero) fused with the partial p.q     | barrier
+//   B: x += alpha p, r -= alpha q, z = D^-1 r (stored over q),
+//      partial r.z and r.r                                          | barrier
 //   C: p = z + beta p                                               | barrier
-// Reductions are deterministic: each CTA reduces its rows of a system in a
-// fixed tree and writes one slot per (system, CTA); the CTA whose slot arrives
-// last (atomic arrival counter per system) sums the system's slots in slot
-// order and updates that system's scalars (alpha, beta, norms, status).  Every
-// CTA then reads those scalars after the next grid barrier, so all CTAs take
+// FP64 work per row and iteration is nnz_row + 7 FMA/MUL, the least the
+// algorithm allows, because GB300's FP64 issue rate is about the same as the
+// rate at which HBM delivers nonzeros.
+//
+// Reductions are deterministic: each warp reduces its rows of a system with a
+// fixed shuffle tree and writes one slot per (system, worker); the warp whose
+// slot arrives last (atomic arrival counter per system) sums the system's
+// slots in slot order and updates that system's scalars (alpha, beta, norms,
+// status).  Every warp reads them after the next grid barrier, so all take
 // the same decisions and iteration counts are reproducible run to run.
 // Converged systems are frozen (their blocks are skipped); the launch ends
 // when no system is active.  A final phase recomputes ||b - A x|| per system.
 //
-// Refined mode (per system state machine; see the M_* modes): an FP32 PCG on
-// FP32 copies of A and D^-1 with FP32 vectors and FP32 reductions solves
+// Refined mode (per-system state machine, M_* modes): an FP32 PCG on FP32
+// copies of A and D^-1 with FP32 vectors and FP32 reductions solves
 // A d = r / ||r||; between inner solves the same A/B/C slots run the FP64
-// outer step: x += s d (slot C), r = b - A x and ||r|| (slot A), and the
-// inner restart r32 = RN(r / s), d = 0 (slot B).
+// outer step: x += s d (slot C), r = b - A x and ||r|| (slot A), and the inner
+// restart r32 = RN(r / s), d = 0 (slot B).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -31,6 +38,7 @@
 
 #include "device_util.cuh"
 #include "internal.cuh"
+#include "pipe.cuh"
 
 namespace gbs {
 
@@ -39,13 +47,16 @@ constexpr int SLOT_STRIDE = 4;  // doubles per reduction slot
 constexpr int PCG_MAX_TPB = 512;
 
 struct PcgArgs {
-  int32_t nsys, nblocks, cap, ensemble;
+  int32_t nsys, ensemble;
+  BlockTable ta, te;  // SpMV blocks, update blocks
+  int32_t cap, Ra, Re, ns;
+  int64_t stage_bytes;
+  int64_t part_e;  // first reduction slot of table te
   const int32_t *row_ptr, *col;
   const double *val;
   const float *val32;
   const double *dinv;
   const float *dinv32;
-  const int32_t *blk_row0, *blk_sys, *sys_blk0, *sys_slot0;
   const double *b;
   double *x;
   double *r, *p, *q;
@@ -61,17 +72,17 @@ struct PcgArgs {
   int64_t max_global;  // cap on loop trips: every trip advances each active system
 };
 
-__device__ __forceinline__ int sys_of(const PcgArgs &a, int b) {
-  return a.ensemble ? 0 : __ldg(a.blk_sys + b);
+__device__ __forceinline__ int sys_of(const PcgArgs &a, const BlockTable &t, int b) {
+  return a.ensemble ? 0 : __ldg(t.sys + b);
 }
-__device__ __forceinline__ int sys_b0(const PcgArgs &a, int s) {
-  return a.ensemble ? 0 : __ldg(a.sys_blk0 + s);
+__device__ __forceinline__ int sys_b0(const PcgArgs &a, const BlockTable &t, int s) {
+  return a.ensemble ? 0 : __ldg(t.sys_blk0 + s);
 }
-__device__ __forceinline__ int sys_nblk(const PcgArgs &a, int s) {
-  return a.ensemble ? a.nblocks : __ldg(a.sys_blk0 + s + 1) - __ldg(a.sys_blk0 + s);
+__device__ __forceinline__ int sys_nblk(const PcgArgs &a, const BlockTable &t, int s) {
+  return a.ensemble ? t.nblocks : __ldg(t.sys_blk0 + s + 1) - __ldg(t.sys_blk0 + s);
 }
-__device__ __forceinline__ int64_t sys_slot0(const PcgArgs &a, int s) {
-  return a.ensemble ? 0 : (int64_t)__ldg(a.sys_slot0 + s);
+__device__ __forceinline__ int64_t sys_slot0(const PcgArgs &a, const BlockTable &t, int s) {
+  return a.ensemble ? 0 : (int64_t)__ldg(t.sys_slot0 + s);
 }
 
 __device__ __forceinline__ void deactivate(const PcgArgs &a, SysState &S, int status) {
@@ -80,47 +91,56 @@ __device__ __forceinline__ void deactivate(const PcgArgs &a, SysState &S, int st
   atomicSub(&a.ctl->n_active, 1);
 }
 
-// Reduce NV per-thread partials of the CTA's run over system s (last block b)
-// into the system's slot; the last arriving CTA sums all slots and calls
-// fin(s, totals) on thread 0.  f32: FP32 accumulation throughout.
+template <typename T, int NV>
+__device__ __forceinline__ void warp_sum(T (&v)[NV]) {
+#pragma unroll
+  for (int k = 0; k < NV; ++k)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_xor_sync(FULL_MASK, v[k], off);
+}
+
+// Reduce the warp's NV partials over its run on system s (last block b of
+// table t) into the system's slot; the last arriving worker sums all slots in
+// slot order and calls fin(s, totals) on lane 0.  f32: FP32 accumulation.
 template <int NV, class Fin>
-__device__ __forceinline__ void flush(const PcgArgs &a, int s, int b, double (&acc)[NV],
-                                      double *red, bool f32, Fin &fin) {
-  __shared__ int s_last;
+__device__ __forceinline__ void wflush(const PcgArgs &a, const BlockTable &t, int64_t part_off,
+                                       int s, int b, int W, double (&acc)[NV], bool f32,
+                                       Fin &fin) {
+  const int lane = threadIdx.x & 31;
   if (f32) {
     float v[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) v[k] = (float)acc[k];
-    block_reduce<float, NV>(v, reinterpret_cast<float *>(red));
+    warp_sum<float, NV>(v);
 #pragma unroll
     for (int k = 0; k < NV; ++k) acc[k] = (double)v[k];
   } else {
-    block_reduce<double, NV>(acc, red);
+    warp_sum<double, NV>(acc);
   }
-  const int G = gridDim.x;
-  const int b0 = sys_b0(a, s), nb = sys_nblk(a, s);
-  const int ns = min(nb, G);
-  const int slot = (b - b0) % G;
-  const int64_t base = sys_slot0(a, s);
-  if (threadIdx.x == 0) {
+  const int b0 = sys_b0(a, t, s), nb = sys_nblk(a, t, s);
+  const int ns = min(nb, W);
+  const int slot = (b - b0) % W;
+  const int64_t base = part_off + sys_slot0(a, t, s);
+  int last = 0;
+  if (lane == 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) a.part[(base + slot) * SLOT_STRIDE + k] = acc[k];
     __threadfence();
     const unsigned prev = atomicAdd(a.sys_cnt + s, 1u);
-    s_last = (prev == (unsigned)(ns - 1)) ? 1 : 0;
+    last = (prev == (unsigned)(ns - 1)) ? 1 : 0;
   }
-  __syncthreads();
-  if (s_last) {
+  last = __shfl_sync(FULL_MASK, last, 0);
+  if (last) {
     __threadfence();
     if (f32) {
       float tot[NV];
 #pragma unroll
       for (int k = 0; k < NV; ++k) tot[k] = 0.f;
-      for (int t = threadIdx.x; t < ns; t += blockDim.x)
+      for (int i = lane; i < ns; i += 32)
 #pragma unroll
-        for (int k = 0; k < NV; ++k) tot[k] += (float)ldcg(a.part + (base + t) * SLOT_STRIDE + k);
-      block_reduce<float, NV>(tot, reinterpret_cast<float *>(red));
-      if (threadIdx.x == 0) {
+        for (int k = 0; k < NV; ++k) tot[k] += (float)ldcg(a.part + (base + i) * SLOT_STRIDE + k);
+      warp_sum<float, NV>(tot);
+      if (lane == 0) {
         double d[NV];
 #pragma unroll
         for (int k = 0; k < NV; ++k) d[k] = (double)tot[k];
@@ -132,94 +152,135 @@ __device__ __forceinline__ void flush(const PcgArgs &a, int s, int b, double (&a
       double tot[NV];
 #pragma unroll
       for (int k = 0; k < NV; ++k) tot[k] = 0.0;
-      for (int t = threadIdx.x; t < ns; t += blockDim.x)
+      for (int i = lane; i < ns; i += 32)
 #pragma unroll
-        for (int k = 0; k < NV; ++k) tot[k] += ldcg(a.part + (base + t) * SLOT_STRIDE + k);
-      block_reduce<double, NV>(tot, red);
-      if (threadIdx.x == 0) {
+        for (int k = 0; k < NV; ++k) tot[k] += ldcg(a.part + (base + i) * SLOT_STRIDE + k);
+      warp_sum<double, NV>(tot);
+      if (lane == 0) {
         a.sys_cnt[s] = 0u;
         fin(s, tot);
         __threadfence();
       }
     }
   }
-  __syncthreads();
+  __syncwarp();
 }
 
-// Walk this CTA's blocks.  begin(s) -> 0 (skip system), 1 (FP64 run), 2 (FP32
-// run, no flush is wanted when NV == 0).  body(s, r0, r1, acc) processes a
-// block.  A run is flushed when the system changes and at the end.
-template <int NV, class Begin, class Body, class Fin>
-__device__ __forceinline__ void run_phase(const PcgArgs &a, double *red, Begin &begin,
-                                          Body &body, Fin &fin) {
-  int cur_s = -1, cur_b = -1, cur_kind = 0;
+// One warp's pass over its wanted blocks of table t, through its pipeline
+// (PIPE) or with plain loads.  work(s, d, stage, acc) processes block d of
+// system s; partials are flushed when the system changes and at the end.
+template <int NV, bool PIPE, class Want, class Issue, class Work, class Fin, class Load>
+__device__ __forceinline__ void wwalk(const PcgArgs &a, const BlockTable &t, int64_t part_off,
+                                      WarpPipe &P, int worker, int W, bool f32, Want &want,
+                                      Issue &issue, Work &work, Fin &fin, Load &load_sys) {
+  int cur_s = -1, cur_b = -1;
   double acc[NV > 0 ? NV : 1];
-  for (int b = blockIdx.x; b < a.nblocks; b += gridDim.x) {
-    const int s = sys_of(a, b);
+  auto on_block = [&](int b, const BlkDesc &d, unsigned char *stg) {
+    const int s = sys_of(a, t, b);
     if (s != cur_s) {
       if constexpr (NV > 0) {
-        if (cur_kind) flush<NV>(a, cur_s, cur_b, acc, red, cur_kind == 2, fin);
+        if (cur_s >= 0) wflush<NV>(a, t, part_off, cur_s, cur_b, W, acc, f32, fin);
       }
       cur_s = s;
-      cur_kind = begin(s);
+      load_sys(s);
 #pragma unroll
       for (int k = 0; k < (NV > 0 ? NV : 1); ++k) acc[k] = 0.0;
     }
-    if (!cur_kind) continue;
     cur_b = b;
-    body(s, __ldg(a.blk_row0 + b), __ldg(a.blk_row0 + b + 1), acc);
+    work(s, d, stg, acc);
+  };
+  if constexpr (PIPE) {
+    warp_stream(P, t, worker, W, want, issue, on_block);
+  } else {
+    for (int b = worker; b < t.nblocks; b += W)
+      if (want(b)) on_block(b, load_desc(t, b), P.stage(0));
   }
   if constexpr (NV > 0) {
-    if (cur_kind) flush<NV>(a, cur_s, cur_b, acc, red, cur_kind == 2, fin);
+    if (cur_s >= 0) wflush<NV>(a, t, part_off, cur_s, cur_b, W, acc, f32, fin);
   }
 }
 
+// Per-system "does this phase process system s", one-entry cache (the state
+// it reads is not modified during the phase while this warp still has blocks
+// of s to visit).
+struct WantCache {
+  int s = -1;
+  bool v = false;
+};
+
 template <bool REFINED>
 __global__ void __launch_bounds__(PCG_MAX_TPB) k_pcg(PcgArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double *prod = reinterpret_cast<double *>(smem_raw);
-  double *red = prod + a.cap;
-  float *prod32 = reinterpret_cast<float *>(smem_raw);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int W = gridDim.x * nw, worker = blockIdx.x * nw + warp;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + (size_t)nw * a.ns * a.stage_bytes);
+  WarpPipe P{smem_raw + (size_t)warp * a.ns * a.stage_bytes, bars + warp * a.ns, a.ns, a.cap,
+             a.Ra, a.Re, a.stage_bytes, 0u, &a.ctl->err, a.timeout_ns, policy_evict_first(),
+             policy_evict_last()};
+  if (lane == 0) P.init_barriers();
+  __syncthreads();
   GridBarrier gb{&a.ctl->bar, &a.ctl->err, 0ull, a.timeout_ns, (unsigned)a.barrier_extra};
-  const int tid = threadIdx.x;
+  // CTA 0 keeps the time spent in each phase (between grid barriers)
+  const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+  uint64_t t_mark = timer ? global_ns() : 0;
+  int64_t t_acc[5] = {0, 0, 0, 0, 0};
+  auto lap = [&](int k) {
+    if (timer) {
+      const uint64_t t = global_ns();
+      t_acc[k] += (int64_t)(t - t_mark);
+      t_mark = t;
+    }
+  };
+  const NzRange z0(0, 0, 0);  // dummies for plain (unstaged) row products
+  const SliceRange<int32_t> rq0(0, 0);
+  const int64_t pa = 0, pe = a.part_e;  // slot regions of the two tables
 
-  // CTA-uniform copies of the current system's scalars (set by begin()).
+  // warp-uniform copies of the current system's scalars (set by load_sys())
   double c_alpha = 0, c_beta = 0, c_scale = 0;
-  int c_mode = M_INNER, c_first = 0;
-  auto load_sys = [&](int s) -> bool {
+  int c_mode = M_INNER, c_first = 0, c_zero = 0;
+  auto load_sys = [&](int s) {
     const SysState *S = a.st + s;
     c_alpha = ldcg(&S->alpha);
     c_beta = ldcg(&S->beta);
     c_scale = ldcg(&S->scale);
     c_mode = ldcg(&S->mode);
     c_first = ldcg(&S->first);
-    return ldcg(&S->active) != 0;
+    c_zero = ldcg(&S->zero_x);
+  };
+  auto active_mode = [&](WantCache &wc, const BlockTable &t, int b, int mode) -> bool {
+    const int s = sys_of(a, t, b);
+    if (s != wc.s) {
+      const SysState *S = a.st + s;
+      wc.s = s;
+      wc.v = ldcg(&S->active) != 0 && (mode < 0 || ldcg(&S->mode) == mode);
+    }
+    return wc.v;
+  };
+  auto no_issue = [&](const BlkDesc &, unsigned char *, uint64_t *) {};
+  auto plain_row = [&](const double *xv, int r) -> double {
+    return row_product<double, false>(P, nullptr, z0, rq0, a.row_ptr, a.col, a.val, xv, r);
   };
 
   // ---------------------------------------------------------------- setup
   {
-    auto begin = [&](int s) -> int { return 1; };
-    auto body = [&](int s, int r0, int r1, double(&acc)[4]) {
-      double t = 0.0;
-      if (a.nonzero_guess)
-        t = staged_row_product<double>(a.row_ptr, a.col, a.val, a.x, r0, r1, prod, a.cap);
-      const int r = r0 + tid;
-      if (r < r1) {
+    auto want = [&](int) -> bool { return true; };
+    auto work = [&](int s, const BlkDesc &d, unsigned char *, double(&acc)[4]) {
+      for (int r = d.r0 + lane; r < d.r1; r += 32) {
         const double bv = a.b[r];
-        const double rv = a.nonzero_guess ? bv - t : bv;
+        const double rv = a.nonzero_guess ? bv - plain_row(a.x, r) : bv;
         if (!a.nonzero_guess) a.x[r] = 0.0;
         const double dv = a.dinv[r];
         if (REFINED) {
           a.r[r] = rv;
-          acc[0] += rv * rv;
+          acc[0] = fma(rv, rv, acc[0]);
         } else {
           const double z = dv * rv;
           a.r[r] = rv;
           a.p[r] = z;
-          acc[0] += rv * z;
-          acc[1] += rv * rv;
+          acc[0] = fma(rv, z, acc[0]);
+          acc[1] = fma(rv, rv, acc[1]);
         }
-        acc[2] += bv * bv;
+        acc[2] = fma(bv, bv, acc[2]);
         acc[3] += (dv == 0.0) ? 1.0 : 0.0;
       }
     };
@@ -257,52 +318,22 @@ __global__ void __launch_bounds__(PCG_MAX_TPB) k_pcg(PcgArgs a) {
         atomicAdd(&a.ctl->n_active, 1);
       }
     };
-    run_phase<4>(a, red, begin, body, fin);
+    wwalk<4, false>(a, a.ta, pa, P, worker, W, false, want, no_issue, work, fin, load_sys);
   }
 
   // ---------------------------------------------------------------- iterations
   // Each trip runs one A/B/C round for every active system; the trip cap is a
   // safety net (systems left active when it trips are reported as MAXIT).
   for (int64_t trip = 0;; ++trip) {
-    if (!gb.sync()) break;
+    const bool ok_top = gb.sync();
+    lap(trip == 0 ? 0 : 3);
+    if (!ok_top) break;
     if (ld_relaxed_s32(&a.ctl->n_active) == 0) break;
     if (trip >= a.max_global) break;
 
-    // ---- slot A
+    // ---- slot A: q = A p and p.q (FP64, or FP32 inner); refined outer
+    //      residual r = b - A x and ||r||^2 in FP64 (plain pass)
     {
-      auto begin = [&](int s) -> int {
-        if (!load_sys(s)) return 0;
-        if (!REFINED) return 1;
-        if (c_mode == M_INNER) return 2;
-        if (c_mode == M_XUPD) return 1;
-        return 0;
-      };
-      auto body = [&](int s, int r0, int r1, double(&acc)[1]) {
-        const int r = r0 + tid;
-        if (!REFINED) {
-          const double qv =
-              staged_row_product<double>(a.row_ptr, a.col, a.val, a.p, r0, r1, prod, a.cap);
-          if (r < r1) {
-            a.q[r] = qv;
-            acc[0] += a.p[r] * qv;
-          }
-        } else if (c_mode == M_INNER) {
-          const float qv = staged_row_product<float>(a.row_ptr, a.col, a.val32, a.p32, r0, r1,
-                                                     prod32, a.cap);
-          if (r < r1) {
-            a.q32[r] = qv;
-            acc[0] = (double)((float)acc[0] + a.p32[r] * qv);
-          }
-        } else {  // M_XUPD: FP64 outer residual
-          const double t =
-              staged_row_product<double>(a.row_ptr, a.col, a.val, a.x, r0, r1, prod, a.cap);
-          if (r < r1) {
-            const double rv = a.b[r] - t;
-            a.r[r] = rv;
-            acc[0] += rv * rv;
-          }
-        }
-      };
       auto fin = [&](int s, double(&tot)[1]) {
         SysState &S = a.st[s];
         if (!REFINED) {
@@ -342,49 +373,67 @@ __global__ void __launch_bounds__(PCG_MAX_TPB) k_pcg(PcgArgs a) {
           }
         }
       };
-      run_phase<1>(a, red, begin, body, fin);
-    }
-    if (!gb.sync()) break;
-
-    // ---- slot B
-    {
-      auto begin = [&](int s) -> int {
-        if (!load_sys(s)) return 0;
-        if (!REFINED) return 1;
-        if (c_mode == M_INNER || c_mode == M_START) return 2;
-        return 0;
-      };
-      auto body = [&](int s, int r0, int r1, double(&acc)[2]) {
-        const int r = r0 + tid;
-        if (r >= r1) return;
-        if (!REFINED) {
-          const double pv = a.p[r], qv = a.q[r];
-          const double xv = a.x[r] + c_alpha * pv;
-          const double rv = a.r[r] - c_alpha * qv;
-          const double z = a.dinv[r] * rv;
-          a.x[r] = xv;
-          a.r[r] = rv;
-          acc[0] += rv * z;
-          acc[1] += rv * rv;
-        } else if (c_mode == M_INNER) {
-          const float al = (float)c_alpha;
-          const float pv = a.p32[r], qv = a.q32[r];
-          const float dv = a.d32[r] + al * pv;
-          const float rv = a.r32[r] - al * qv;
-          const float z = a.dinv32[r] * rv;
-          a.d32[r] = dv;
-          a.r32[r] = rv;
-          acc[0] = (double)((float)acc[0] + rv * z);
-          acc[1] = (double)((float)acc[1] + rv * rv);
-        } else {  // M_START: inner restart on the scaled FP64 residual
-          const float rv = __double2float_rn(a.r[r] / c_scale);
-          const float z = a.dinv32[r] * rv;
-          a.r32[r] = rv;
-          a.d32[r] = 0.0f;
-          acc[0] = (double)((float)acc[0] + rv * z);
-          acc[1] = (double)((float)acc[1] + rv * rv);
+      if (!REFINED) {
+        WantCache wc;
+        auto want = [&](int b) -> bool { return active_mode(wc, a.ta, b, -1); };
+        auto issue = [&](const BlkDesc &d, unsigned char *st, uint64_t *bar) {
+          const SliceRange<double> q(d.r0, d.r1);
+          if (arrive_for(bar, csr_bytes<double>(d, P.cap) + q.bytes())) {
+            csr_copy<double>(P, st, d, a.row_ptr, a.col, a.val, bar);
+            slice_copy<double>(P.SA(st), a.p, q, bar, P.pol_vec);
+          }
+        };
+        auto work = [&](int s, const BlkDesc &d, unsigned char *st, double(&acc)[1]) {
+          const SliceRange<double> q(d.r0, d.r1);
+          auto f = [&](int r, double qv) {
+            a.q[r] = qv;
+            acc[0] = fma(slice_get<double>(P.SA(st), a.p, q, r), qv, acc[0]);
+          };
+          block_rows<double>(P, st, d, a.row_ptr, a.col, a.val, a.p, f);
+        };
+        wwalk<1, true>(a, a.ta, pa, P, worker, W, false, want, issue, work, fin, load_sys);
+      } else {
+        {  // inner FP32 SpMV, pipelined
+          WantCache wc;
+          auto want = [&](int b) -> bool { return active_mode(wc, a.ta, b, M_INNER); };
+          auto issue = [&](const BlkDesc &d, unsigned char *st, uint64_t *bar) {
+            const SliceRange<float> q(d.r0, d.r1);
+            if (arrive_for(bar, csr_bytes<float>(d, P.cap) + q.bytes())) {
+              csr_copy<float>(P, st, d, a.row_ptr, a.col, a.val32, bar);
+              slice_copy<float>(P.SA(st), a.p32, q, bar, P.pol_vec);
+            }
+          };
+          auto work = [&](int s, const BlkDesc &d, unsigned char *st, double(&acc)[1]) {
+            const SliceRange<float> q(d.r0, d.r1);
+            auto f = [&](int r, float qv) {
+              a.q32[r] = qv;
+              acc[0] = (double)fmaf(slice_get<float>(P.SA(st), a.p32, q, r), qv, (float)acc[0]);
+            };
+            block_rows<float>(P, st, d, a.row_ptr, a.col, a.val32, a.p32, f);
+          };
+          wwalk<1, true>(a, a.ta, pa, P, worker, W, true, want, issue, work, fin, load_sys);
         }
-      };
+        {  // FP64 outer residual, plain
+          WantCache wc;
+          auto want = [&](int b) -> bool { return active_mode(wc, a.ta, b, M_XUPD); };
+          auto work = [&](int s, const BlkDesc &d, unsigned char *, double(&acc)[1]) {
+            for (int r = d.r0 + lane; r < d.r1; r += 32) {
+              const double rv = a.b[r] - plain_row(a.x, r);
+              a.r[r] = rv;
+              acc[0] = fma(rv, rv, acc[0]);
+            }
+          };
+          wwalk<1, false>(a, a.ta, pa, P, worker, W, false, want, no_issue, work, fin, load_sys);
+        }
+      }
+    }
+    const bool ok_a = gb.sync();
+    lap(1);
+    if (!ok_a) break;
+
+    // ---- slot B: x += alpha p, r -= alpha q, z = D^-1 r (kept in q for slot
+    //      C), r.z and r.r; or the refined inner restart
+    {
       auto fin = [&](int s, double(&tot)[2]) {
         SysState &S = a.st[s];
         if (!REFINED) {
@@ -425,77 +474,202 @@ __global__ void __launch_bounds__(PCG_MAX_TPB) k_pcg(PcgArgs a) {
           }
         }
       };
-      run_phase<2>(a, red, begin, body, fin);
+      if (!REFINED) {
+        WantCache wc;
+        auto want = [&](int b) -> bool { return active_mode(wc, a.te, b, -1); };
+        auto issue = [&](const BlkDesc &d, unsigned char *st, uint64_t *bar) {
+          const SliceRange<double> q(d.r0, d.r1);
+          if (arrive_for(bar, 5u * q.bytes())) {
+            slice_copy<double>(P.SE(st, 0), a.p, q, bar, P.pol_vec);
+            slice_copy<double>(P.SE(st, 1), a.q, q, bar, P.pol_vec);
+            slice_copy<double>(P.SE(st, 2), a.x, q, bar, P.pol_vec);
+            slice_copy<double>(P.SE(st, 3), a.r, q, bar, P.pol_vec);
+            slice_copy<double>(P.SE(st, 4), a.dinv, q, bar, P.pol_vec);
+          }
+        };
+        auto work = [&](int s, const BlkDesc &d, unsigned char *st, double(&acc)[2]) {
+          const SliceRange<double> q(d.r0, d.r1);
+          for (int r = d.r0 + lane; r < d.r1; r += 32) {
+            const double pv = slice_get<double>(P.SE(st, 0), a.p, q, r);
+            const double qv = slice_get<double>(P.SE(st, 1), a.q, q, r);
+            const double xv = fma(c_alpha, pv, slice_get<double>(P.SE(st, 2), a.x, q, r));
+            const double rv = fma(-c_alpha, qv, slice_get<double>(P.SE(st, 3), a.r, q, r));
+            const double z = slice_get<double>(P.SE(st, 4), a.dinv, q, r) * rv;
+            a.x[r] = xv;
+            a.r[r] = rv;
+            a.q[r] = z;
+            acc[0] = fma(rv, z, acc[0]);
+            acc[1] = fma(rv, rv, acc[1]);
+          }
+        };
+        wwalk<2, true>(a, a.te, pe, P, worker, W, false, want, issue, work, fin, load_sys);
+      } else {
+        {  // inner FP32 update, pipelined
+          WantCache wc;
+          auto want = [&](int b) -> bool { return active_mode(wc, a.te, b, M_INNER); };
+          auto issue = [&](const BlkDesc &d, unsigned char *st, uint64_t *bar) {
+            const SliceRange<float> q(d.r0, d.r1);
+            if (arrive_for(bar, 5u * q.bytes())) {
+              slice_copy<float>(P.SE(st, 0), a.p32, q, bar, P.pol_vec);
+              slice_copy<float>(P.SE(st, 1), a.q32, q, bar, P.pol_vec);
+              slice_copy<float>(P.SE(st, 2), a.d32, q, bar, P.pol_vec);
+              slice_copy<float>(P.SE(st, 3), a.r32, q, bar, P.pol_vec);
+              slice_copy<float>(P.SE(st, 4), a.dinv32, q, bar, P.pol_vec);
+            }
+          };
+          auto work = [&](int s, const BlkDesc &d, unsigned char *st, double(&acc)[2]) {
+            const SliceRange<float> q(d.r0, d.r1);
+            const float al = (float)c_alpha;
+            float a0 = (float)acc[0], a1 = (float)acc[1];
+            for (int r = d.r0 + lane; r < d.r1; r += 32) {
+              const float pv = slice_get<float>(P.SE(st, 0), a.p32, q, r);
+              const float qv = slice_get<float>(P.SE(st, 1), a.q32, q, r);
+              const float dv = fmaf(al, pv, slice_get<float>(P.SE(st, 2), a.d32, q, r));
+              const float rv = fmaf(-al, qv, slice_get<float>(P.SE(st, 3), a.r32, q, r));
+              const float z = slice_get<float>(P.SE(st, 4), a.dinv32, q, r) * rv;
+              a.d32[r] = dv;
+              a.r32[r] = rv;
+              a.q32[r] = z;
+              a0 = fmaf(rv, z, a0);
+              a1 = fmaf(rv, rv, a1);
+            }
+            acc[0] = (double)a0;
+            acc[1] = (double)a1;
+          };
+          wwalk<2, true>(a, a.te, pe, P, worker, W, true, want, issue, work, fin, load_sys);
+        }
+        {  // inner restart on the scaled FP64 residual, plain
+          WantCache wc;
+          auto want = [&](int b) -> bool { return active_mode(wc, a.te, b, M_START); };
+          auto work = [&](int s, const BlkDesc &d, unsigned char *, double(&acc)[2]) {
+            float a0 = (float)acc[0], a1 = (float)acc[1];
+            for (int r = d.r0 + lane; r < d.r1; r += 32) {
+              const float rv = __double2float_rn(a.r[r] / c_scale);
+              const float z = a.dinv32[r] * rv;
+              a.r32[r] = rv;
+              a.d32[r] = 0.0f;
+              a.q32[r] = z;
+              a0 = fmaf(rv, z, a0);
+              a1 = fmaf(rv, rv, a1);
+            }
+            acc[0] = (double)a0;
+            acc[1] = (double)a1;
+          };
+          wwalk<2, false>(a, a.te, pe, P, worker, W, true, want, no_issue, work, fin, load_sys);
+        }
+      }
     }
-    if (!gb.sync()) break;
+    const bool ok_b = gb.sync();
+    lap(2);
+    if (!ok_b) break;
     if (ld_relaxed_s32(&a.ctl->n_active) == 0) break;
 
-    // ---- slot C (no reduction)
+    // ---- slot C (no reduction): p = z + beta p with z from slot B; refined
+    //      x += s d
     {
-      auto begin = [&](int s) -> int {
-        if (!load_sys(s)) return 0;
-        if (!REFINED) return 1;
-        return (c_mode == M_INNER || c_mode == M_XUPD) ? 1 : 0;
-      };
-      auto body = [&](int s, int r0, int r1, double(&acc)[1]) {
-        const int r = r0 + tid;
-        if (r >= r1) return;
-        if (!REFINED) {
-          a.p[r] = a.dinv[r] * a.r[r] + c_beta * a.p[r];
-        } else if (c_mode == M_INNER) {
-          const float z = a.dinv32[r] * a.r32[r];
-          a.p32[r] = c_first ? z : z + (float)c_beta * a.p32[r];
-        } else {  // M_XUPD: x += s d
-          a.x[r] += c_scale * (double)a.d32[r];
+      auto fin = [&](int, double(&)[1]) {};
+      if (!REFINED) {
+        WantCache wc;
+        auto want = [&](int b) -> bool { return active_mode(wc, a.te, b, -1); };
+        auto issue = [&](const BlkDesc &d, unsigned char *st, uint64_t *bar) {
+          const SliceRange<double> q(d.r0, d.r1);
+          if (arrive_for(bar, 2u * q.bytes())) {
+            slice_copy<double>(P.SE(st, 0), a.p, q, bar, P.pol_vec);
+            slice_copy<double>(P.SE(st, 1), a.q, q, bar, P.pol_vec);
+          }
+        };
+        auto work = [&](int s, const BlkDesc &d, unsigned char *st, double(&)[1]) {
+          const SliceRange<double> q(d.r0, d.r1);
+          for (int r = d.r0 + lane; r < d.r1; r += 32) {
+            const double pv = slice_get<double>(P.SE(st, 0), a.p, q, r);
+            const double z = slice_get<double>(P.SE(st, 1), a.q, q, r);
+            a.p[r] = fma(c_beta, pv, z);
+          }
+        };
+        wwalk<0, true>(a, a.te, pe, P, worker, W, false, want, issue, work, fin, load_sys);
+      } else {
+        {
+          WantCache wc;
+          auto want = [&](int b) -> bool { return active_mode(wc, a.te, b, M_INNER); };
+          auto issue = [&](const BlkDesc &d, unsigned char *st, uint64_t *bar) {
+            const SliceRange<float> q(d.r0, d.r1);
+            if (arrive_for(bar, 2u * q.bytes())) {
+              slice_copy<float>(P.SE(st, 0), a.p32, q, bar, P.pol_vec);
+              slice_copy<float>(P.SE(st, 1), a.q32, q, bar, P.pol_vec);
+            }
+          };
+          auto work = [&](int s, const BlkDesc &d, unsigned char *st, double(&)[1]) {
+            const SliceRange<float> q(d.r0, d.r1);
+            const float be = (float)c_beta;
+            for (int r = d.r0 + lane; r < d.r1; r += 32) {
+              const float pv = slice_get<float>(P.SE(st, 0), a.p32, q, r);
+              const float z = slice_get<float>(P.SE(st, 1), a.q32, q, r);
+              a.p32[r] = c_first ? z : fmaf(be, pv, z);
+            }
+          };
+          wwalk<0, true>(a, a.te, pe, P, worker, W, false, want, issue, work, fin, load_sys);
         }
-      };
-      auto fin = [&](int s, double(&tot)[1]) {};
-      run_phase<0>(a, red, begin, body, fin);
+        {  // x += s d, plain
+          WantCache wc;
+          auto want = [&](int b) -> bool { return active_mode(wc, a.te, b, M_XUPD); };
+          auto work = [&](int s, const BlkDesc &d, unsigned char *, double(&)[1]) {
+            for (int r = d.r0 + lane; r < d.r1; r += 32)
+              a.x[r] = fma(c_scale, (double)a.d32[r], a.x[r]);
+          };
+          wwalk<0, false>(a, a.te, pe, P, worker, W, false, want, no_issue, work, fin, load_sys);
+        }
+      }
     }
   }
 
   // ---------------------------------------------------------------- true residual
   if (!gb.sync()) return;
+  lap(0);
   {
-    int c_zero = 0;
-    auto begin = [&](int s) -> int {
-      c_zero = ldcg(&a.st[s].zero_x);
-      return 1;
-    };
-    auto body = [&](int s, int r0, int r1, double(&acc)[1]) {
-      const int r = r0 + tid;
+    auto want = [&](int) -> bool { return true; };
+    auto work = [&](int s, const BlkDesc &d, unsigned char *, double(&acc)[1]) {
       if (c_zero) {  // b_s == 0: x_s = 0 exactly, no product needed
-        if (r < r1) a.x[r] = 0.0;
+        for (int r = d.r0 + lane; r < d.r1; r += 32) a.x[r] = 0.0;
         return;
       }
-      const double t =
-          staged_row_product<double>(a.row_ptr, a.col, a.val, a.x, r0, r1, prod, a.cap);
-      if (r < r1) {
-        const double d = a.b[r] - t;
-        acc[0] += d * d;
+      for (int r = d.r0 + lane; r < d.r1; r += 32) {
+        const double t = a.b[r] - plain_row(a.x, r);
+        acc[0] = fma(t, t, acc[0]);
       }
     };
-    auto fin = [&](int s, double(&tot)[1]) {
-      SysState &S = a.st[s];
-      S.tt = tot[0];
-    };
-    run_phase<1>(a, red, begin, body, fin);
+    auto fin = [&](int s, double(&tot)[1]) { a.st[s].tt = tot[0]; };
+    wwalk<1, false>(a, a.ta, pa, P, worker, W, false, want, no_issue, work, fin, load_sys);
   }
+  lap(4);
+  if (timer)
+    for (int k = 0; k < 5; ++k) a.ctl->phase_ns[k] = t_acc[k];
 }
 
 // ------------------------------------------------------------------ host side
 
-static size_t pcg_smem(gbs_mat A) { return (size_t)A->cap * sizeof(double) + 4 * 32 * sizeof(double); }
+static size_t pcg_smem_for(int nwarps, int ns, int64_t stage_bytes) {
+  return (size_t)nwarps * ns * (size_t)stage_bytes + (size_t)nwarps * ns * 8;
+}
+static size_t pcg_smem(gbs_mat A) { return pcg_smem_for(A->nwarps, A->nstages, A->stage_bytes); }
+
+static BlockTable view(const TableDev &t) {
+  return BlockTable{t.nblocks, t.row0, t.nz0, t.sys, t.sys_blk0, t.sys_slot0};
+}
+
+template <bool REFINED>
+static int raise_smem_limit(size_t smem) {
+  cudaFuncAttributes fa;
+  GBS_TRY_CUDA(cudaFuncGetAttributes(&fa, k_pcg<REFINED>));
+  if (fa.maxDynamicSharedSizeBytes < (int)smem)
+    GBS_TRY_CUDA(cudaFuncSetAttribute(k_pcg<REFINED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+  return GBS_OK;
+}
 
 template <bool REFINED>
 static int pcg_grid(gbs_mat A, int *grid) {
-  static int configured_smem[2] = {0, 0};
   const size_t smem = pcg_smem(A);
-  if ((int)smem > configured_smem[REFINED]) {
-    GBS_TRY_CUDA(cudaFuncSetAttribute(k_pcg<REFINED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-    configured_smem[REFINED] = (int)smem;
-  }
+  GBS_TRY(raise_smem_limit<REFINED>(smem));
   int per_sm = 0, nsm = 0;
   GBS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<REFINED>, A->tpb, smem));
   GBS_TRY_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, A->device));
@@ -503,32 +677,34 @@ static int pcg_grid(gbs_mat A, int *grid) {
     set_error("persistent PCG kernel does not fit on an SM (tpb %d, smem %zu)", A->tpb, smem);
     return GBS_ERR_LAUNCH;
   }
-  int64_t g = (int64_t)per_sm * nsm;
-  if (g > A->nblocks) g = A->nblocks;
-  if (g < 1) g = 1;
-  *grid = (int)g;
+  // no more CTAs than the larger table has blocks for its warps
+  const int64_t nb = std::max(A->ta.nblocks, A->te.nblocks);
+  int64_t g = std::min<int64_t>((int64_t)per_sm * nsm, (nb + A->nwarps - 1) / A->nwarps);
+  *grid = (int)std::max<int64_t>(g, 1);
   return GBS_OK;
 }
 
-// Slot offsets for grid size G: system s owns min(nblocks_s, G) slots.
-static int ensure_slots(gbs_mat A, int G, cudaStream_t s) {
-  const int64_t need = std::max<int64_t>((int64_t)A->nblocks, 1) + G;
+// Slot offsets for W workers: system s owns min(nblocks_s, W) slots per table.
+static int ensure_slots(gbs_mat A, int W, cudaStream_t s) {
+  const int64_t need = std::max<int64_t>((int64_t)A->ta.nblocks + A->te.nblocks, 1) + 2;
   if (A->part_cap < need) {
     if (A->part) cudaFree(A->part);
     A->part = nullptr;
     GBS_TRY_CUDA(cudaMalloc(&A->part, sizeof(double) * SLOT_STRIDE * need));
     A->part_cap = need;
   }
-  if (A->slot_grid != G) {
-    std::vector<int32_t> so(A->nsys + 1, 0);
-    for (int32_t q = 0; q < A->nsys; ++q) {
-      const int32_t nb = A->sys_blk0_h[q + 1] - A->sys_blk0_h[q];
-      so[q + 1] = so[q] + std::min(nb, G);
+  if (A->slot_workers != W) {
+    for (TableDev *t : {&A->ta, &A->te}) {
+      std::vector<int32_t> so(A->nsys + 1, 0);
+      for (int32_t q = 0; q < A->nsys; ++q) {
+        const int32_t nb = t->sys_blk0_h[q + 1] - t->sys_blk0_h[q];
+        so[q + 1] = so[q] + std::min(nb, W);
+      }
+      GBS_TRY_CUDA(cudaMemcpyAsync(t->sys_slot0, so.data(), sizeof(int32_t) * (A->nsys + 1),
+                                   cudaMemcpyHostToDevice, s));
+      GBS_TRY_CUDA(cudaStreamSynchronize(s));  // `so` is pageable and goes out of scope
     }
-    GBS_TRY_CUDA(cudaMemcpyAsync(A->sys_slot0, so.data(), sizeof(int32_t) * (A->nsys + 1),
-                                 cudaMemcpyHostToDevice, s));
-    GBS_TRY_CUDA(cudaStreamSynchronize(s));  // `so` is pageable and goes out of scope
-    A->slot_grid = G;
+    A->slot_workers = W;
   }
   return GBS_OK;
 }
@@ -539,13 +715,13 @@ int ensure_solver_workspace(gbs_mat A, bool refined) {
     GBS_TRY_CUDA(cudaMalloc(&A->r, sizeof(double) * n));
     GBS_TRY_CUDA(cudaMalloc(&A->p, sizeof(double) * n));
     GBS_TRY_CUDA(cudaMalloc(&A->q, sizeof(double) * n));
-    GBS_TRY_CUDA(cudaMalloc(&A->sys_slot0, sizeof(int32_t) * (A->nsys + 1)));
     GBS_TRY_CUDA(cudaMalloc(&A->sys_cnt, sizeof(unsigned) * A->nsys));
     GBS_TRY_CUDA(cudaMalloc(&A->st, sizeof(SysState) * A->nsys));
     GBS_TRY_CUDA(cudaMalloc(&A->ctl, sizeof(DevCtl)));
     GBS_TRY_CUDA(cudaMallocHost(&A->st_host, sizeof(SysState) * A->nsys));
     GBS_TRY_CUDA(cudaMemset(A->sys_cnt, 0, sizeof(unsigned) * A->nsys));
-    A->slot_grid = -1;
+    GBS_TRY_CUDA(cudaMemset(A->ctl, 0, sizeof(DevCtl)));
+    A->slot_workers = -1;
   }
   if (refined && !A->r32) {
     GBS_TRY_CUDA(cudaMalloc(&A->r32, sizeof(float) * n));
@@ -556,24 +732,40 @@ int ensure_solver_workspace(gbs_mat A, bool refined) {
   return GBS_OK;
 }
 
+static void fill_common(PcgArgs &a, const ksp_opts &o) {
+  a.rtol = o.rtol;
+  a.inner_rtol = o.inner_rtol;
+  a.maxit = o.maxit;
+  a.inner_maxit = o.inner_maxit;
+  a.max_outer = o.max_outer;
+  a.nonzero_guess = o.nonzero_guess;
+  a.timeout_ns = o.timeout_ns;
+  a.barrier_extra = o.debug_barrier_extra;
+  a.max_global = o.precision == GBS_FP32_REFINED
+                     ? ((int64_t)o.max_outer + 1) * ((int64_t)o.inner_maxit + 3) + 4
+                     : (int64_t)o.maxit + 4;
+}
+
 static PcgArgs make_args(gbs_mat A, const double *b, double *x, const ksp_opts &o,
                          bool per_system) {
   PcgArgs a;
   memset(&a, 0, sizeof(a));
   a.nsys = per_system ? A->nsys : 1;
   a.ensemble = per_system ? 0 : 1;
-  a.nblocks = A->nblocks;
+  a.ta = view(A->ta);
+  a.te = view(A->te);
   a.cap = A->cap;
+  a.Ra = A->Ra;
+  a.Re = A->Re;
+  a.ns = A->nstages;
+  a.stage_bytes = A->stage_bytes;
+  a.part_e = A->ta.nblocks + 1;
   a.row_ptr = A->row_ptr;
   a.col = A->col;
   a.val = A->val;
   a.val32 = A->val32;
   a.dinv = A->dinv;
   a.dinv32 = A->dinv32;
-  a.blk_row0 = A->blk_row0;
-  a.blk_sys = A->blk_sys;
-  a.sys_blk0 = A->sys_blk0;
-  a.sys_slot0 = A->sys_slot0;
   a.b = b;
   a.x = x;
   a.r = A->r;
@@ -587,36 +779,26 @@ static PcgArgs make_args(gbs_mat A, const double *b, double *x, const ksp_opts &
   a.sys_cnt = A->sys_cnt;
   a.st = A->st;
   a.ctl = A->ctl;
-  a.rtol = o.rtol;
-  a.inner_rtol = o.inner_rtol;
-  a.maxit = o.maxit;
-  a.inner_maxit = o.inner_maxit;
-  a.max_outer = o.max_outer;
-  a.nonzero_guess = o.nonzero_guess;
-  a.timeout_ns = o.timeout_ns;
-  a.barrier_extra = o.debug_barrier_extra;
-  a.max_global = o.precision == GBS_FP32_REFINED
-                     ? ((int64_t)o.max_outer + 1) * ((int64_t)o.inner_maxit + 3) + 4
-                     : (int64_t)o.maxit + 4;
+  fill_common(a, o);
   return a;
 }
 
-template <bool REFINED>
-static int launch_pcg(gbs_mat A, PcgArgs &a, int G, cudaStream_t s) {
+static int launch_coop(void (*kern)(PcgArgs), PcgArgs &a, int G, int tpb, size_t smem,
+                       cudaStream_t s) {
   cudaLaunchConfig_t cfg;
   memset(&cfg, 0, sizeof(cfg));
   cfg.gridDim = dim3((unsigned)G);
-  cfg.blockDim = dim3((unsigned)A->tpb);
-  cfg.dynamicSmemBytes = pcg_smem(A);
+  cfg.blockDim = dim3((unsigned)tpb);
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, k_pcg<REFINED>, a);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a);
   if (e != cudaSuccess) {
-    set_error("cooperative PCG launch (grid %d x %d, smem %zu): %s", G, A->tpb, pcg_smem(A),
+    set_error("cooperative PCG launch (grid %d x %d, smem %zu): %s", G, tpb, smem,
               cudaGetErrorString(e));
     return e == cudaErrorCooperativeLaunchTooLarge ? GBS_ERR_LAUNCH : GBS_ERR_CUDA;
   }
@@ -628,7 +810,8 @@ static int launch_pcg(gbs_mat A, PcgArgs &a, int G, cudaStream_t s) {
 static int enqueue_solve(gbs_mat A, PcgArgs &a, bool refined, int G, cudaStream_t s) {
   GBS_TRY_CUDA(cudaMemsetAsync(A->ctl, 0, sizeof(DevCtl), s));
   GBS_TRY_CUDA(cudaMemsetAsync(A->sys_cnt, 0, sizeof(unsigned) * A->nsys, s));
-  return refined ? launch_pcg<true>(A, a, G, s) : launch_pcg<false>(A, a, G, s);
+  return refined ? launch_coop(k_pcg<true>, a, G, A->tpb, pcg_smem(A), s)
+                 : launch_coop(k_pcg<false>, a, G, A->tpb, pcg_smem(A), s);
 }
 
 int solve(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool per_system,
@@ -638,7 +821,7 @@ int solve(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool per_sys
   if (refined && !A->val32_valid) GBS_TRY(launch_to_fp32(A, s));
   A->last_count = per_system ? A->nsys : 1;
   A->last_ensemble = !per_system;
-  if (A->nblocks == 0) {  // empty matrix: nothing to iterate
+  if (A->ta.nblocks == 0) {  // empty matrix: nothing to iterate
     GBS_TRY_CUDA(cudaMemsetAsync(A->st, 0, sizeof(SysState) * A->nsys, s));
     GBS_TRY_CUDA(cudaMemsetAsync(A->ctl, 0, sizeof(DevCtl), s));
     return GBS_OK;
@@ -646,7 +829,7 @@ int solve(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool per_sys
   int G = 0;
   GBS_TRY(refined ? pcg_grid<true>(A, &G) : pcg_grid<false>(A, &G));
   if (refined) A->grid_fp32 = G; else A->grid_fp64 = G;
-  GBS_TRY(ensure_slots(A, G, s));
+  GBS_TRY(ensure_slots(A, G * A->nwarps, s));
   PcgArgs a = make_args(A, b, x, o, per_system);
   if (!use_graph) return enqueue_solve(A, a, refined, G, s);
 
@@ -660,7 +843,7 @@ int solve(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool per_sys
            (refined ? 1u : 0u);
   key[6] = (uint64_t)o.timeout_ns ^ ((uint64_t)o.debug_barrier_extra << 48);
   key[7] = ((uint64_t)G << 32) | (uint64_t)(per_system ? 1 : 0) | ((uint64_t)A->tpb << 8) |
-           ((uint64_t)A->cap << 20);
+           ((uint64_t)A->nstages << 20) | ((uint64_t)A->Ra << 24);
   if (!A->graph || memcmp(key, A->graph_key, sizeof(key)) != 0) {
     if (A->graph) {
       cudaGraphExecDestroy(A->graph);
@@ -732,7 +915,7 @@ int read_results(gbs_mat A, ksp_result *res, int32_t count, cudaStream_t s) {
 // must not allocate device memory -- e.g. code that works inside a fixed
 // memory budget owned by another allocator, or that cannot afford the device
 // synchronisation cudaMalloc / cudaFree imply.  Its scratch (the r, p, q and
-// D^-1 vectors, the block table, the reduction slots and the control words)
+// D^-1 vectors, the block tables, the reduction slots and the control words)
 // lives in one file-scope __device__ array of fixed size, so the call performs
 // no allocation of any kind.  The caller passes the CSR matrix, b and x.
 // Limit: n <= NOALLOC_MAX_ROWS rows (the array holds about 8.4 MB and stays
@@ -745,14 +928,17 @@ int read_results(gbs_mat A, ksp_result *res, int32_t count, cudaStream_t s) {
 namespace {
 
 constexpr int64_t NOALLOC_MAX_ROWS = 262144;
-constexpr int NOALLOC_R = 256, NOALLOC_TPB = 256, NOALLOC_CAP = 2048;
-constexpr int64_t NOALLOC_MAX_BLOCKS = NOALLOC_MAX_ROWS / NOALLOC_R;
+constexpr int NOALLOC_RA = 32, NOALLOC_RE = 256, NOALLOC_NW = 8, NOALLOC_NS = 2;
+constexpr int NOALLOC_CAP = 1024;  // staged nonzeros per 32-row block (longer: plain loads)
+constexpr int64_t NOALLOC_MAX_BLK_A = NOALLOC_MAX_ROWS / NOALLOC_RA;
+constexpr int64_t NOALLOC_MAX_BLK_E = NOALLOC_MAX_ROWS / NOALLOC_RE;
 
 struct NoallocScratch {
   double r[NOALLOC_MAX_ROWS], p[NOALLOC_MAX_ROWS], q[NOALLOC_MAX_ROWS],
       dinv[NOALLOC_MAX_ROWS];
-  double part[(NOALLOC_MAX_BLOCKS + 8) * gbs::SLOT_STRIDE];
-  int32_t blk_row0[NOALLOC_MAX_BLOCKS + 1];
+  double part[(NOALLOC_MAX_BLK_A + NOALLOC_MAX_BLK_E + 8) * gbs::SLOT_STRIDE];
+  int32_t row0_a[NOALLOC_MAX_BLK_A + 4], nz0_a[NOALLOC_MAX_BLK_A + 4];
+  int32_t row0_e[NOALLOC_MAX_BLK_E + 4], nz0_e[NOALLOC_MAX_BLK_E + 4];
   unsigned sys_cnt[4];
   gbs::SysState st[1];
   gbs::DevCtl ctl;
@@ -790,20 +976,31 @@ int noalloc_scratch(NoallocScratch **out) {
 }
 
 // D^-1 from the caller's CSR (0 marks a missing or non-positive diagonal) and
-// the block table of ceil(n / NOALLOC_R) blocks.
+// the two block tables (32-row SpMV blocks, 256-row update blocks).
 __global__ void k_noalloc_prep(int64_t n, const int32_t *__restrict__ row_ptr,
                                const int32_t *__restrict__ col, const double *__restrict__ val,
-                               double *__restrict__ dinv, int32_t *__restrict__ blk_row0,
-                               int32_t nblocks) {
+                               double *__restrict__ dinv, int32_t *__restrict__ row0_a,
+                               int32_t *__restrict__ nz0_a, int32_t nba,
+                               int32_t *__restrict__ row0_e, int32_t *__restrict__ nz0_e,
+                               int32_t nbe) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int64_t r = i0; r < n; r += stride) {
     double d = 0.0;
     for (int32_t q = row_ptr[r]; q < row_ptr[r + 1]; ++q)
       if (col[q] == r) d = val[q];
     dinv[r] = (d > 0.0) ? 1.0 / d : 0.0;
   }
-  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b <= nblocks; b += stride)
-    blk_row0[b] = (int32_t)(b * NOALLOC_R < n ? b * NOALLOC_R : n);
+  for (int64_t b = i0; b <= nba; b += stride) {
+    const int64_t r = b * NOALLOC_RA < n ? b * NOALLOC_RA : n;
+    row0_a[b] = (int32_t)r;
+    nz0_a[b] = row_ptr[r];
+  }
+  for (int64_t b = i0; b <= nbe; b += stride) {
+    const int64_t r = b * NOALLOC_RE < n ? b * NOALLOC_RE : n;
+    row0_e[b] = (int32_t)r;
+    nz0_e[b] = row_ptr[r];
+  }
 }
 
 }  // namespace
@@ -819,6 +1016,11 @@ extern "C" int ksp_solve_cg_noalloc(int64_t n, const int32_t *row_ptr, const int
   }
   if (n > 0 && (!row_ptr || !col || !val || !b || !x)) {
     set_error("ksp_solve_cg_noalloc: null CSR, b or x pointer");
+    return GBS_ERR_ARG;
+  }
+  if ((((uintptr_t)row_ptr | (uintptr_t)col | (uintptr_t)val | (uintptr_t)b | (uintptr_t)x) &
+       15u) != 0) {
+    set_error("ksp_solve_cg_noalloc: row_ptr, col, val, b and x must be 16-byte aligned");
     return GBS_ERR_ARG;
   }
   ksp_opts oo;
@@ -841,45 +1043,47 @@ extern "C" int ksp_solve_cg_noalloc(int64_t n, const int32_t *row_ptr, const int
   cudaStream_t s = (cudaStream_t)stream;
   NoallocScratch *S = nullptr;
   GBS_TRY(noalloc_scratch(&S));
-  const int32_t nblocks = (int32_t)((n + NOALLOC_R - 1) / NOALLOC_R);
-  const size_t smem = (size_t)NOALLOC_CAP * sizeof(double) + 4 * 32 * sizeof(double);
+  const int32_t nba = (int32_t)((n + NOALLOC_RA - 1) / NOALLOC_RA);
+  const int32_t nbe = (int32_t)((n + NOALLOC_RE - 1) / NOALLOC_RE);
+  const int64_t sb = std::max((spmv_stage_bytes(NOALLOC_CAP, NOALLOC_RA) + 15) & ~15LL,
+                              (upd_stage_bytes(NOALLOC_RE) + 15) & ~15LL);
+  const size_t smem = pcg_smem_for(NOALLOC_NW, NOALLOC_NS, sb);
   int per_sm = 0, nsm = 0, dev = 0;
   GBS_TRY_CUDA(cudaGetDevice(&dev));
-  GBS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<false>, NOALLOC_TPB,
-                                                             smem));
+  GBS_TRY(raise_smem_limit<false>(smem));
+  GBS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<false>,
+                                                             32 * NOALLOC_NW, smem));
   GBS_TRY_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   if (per_sm < 1) {
     set_error("ksp_solve_cg_noalloc: persistent kernel does not fit on an SM");
     return GBS_ERR_LAUNCH;
   }
-  const int G = (int)std::min<int64_t>((int64_t)per_sm * nsm, nblocks);
-  {  // the kernel's dynamic shared-memory limit may have been set lower by
-     // another launch configuration; raise it if needed, never lower it
-    cudaFuncAttributes fa;
-    GBS_TRY_CUDA(cudaFuncGetAttributes(&fa, k_pcg<false>));
-    if (fa.maxDynamicSharedSizeBytes < (int)smem)
-      GBS_TRY_CUDA(cudaFuncSetAttribute(k_pcg<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem));
-  }
+  const int G = (int)std::max<int64_t>(
+      1, std::min<int64_t>((int64_t)per_sm * nsm, (nba + NOALLOC_NW - 1) / NOALLOC_NW));
 
   // the control words and arrival counters must start at zero on every call
   GBS_TRY_CUDA(cudaMemsetAsync(&S->ctl, 0, sizeof(DevCtl), s));
   GBS_TRY_CUDA(cudaMemsetAsync(S->sys_cnt, 0, sizeof(S->sys_cnt), s));
   k_noalloc_prep<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(
-      n, row_ptr, col, val, S->dinv, S->blk_row0, nblocks);
+      n, row_ptr, col, val, S->dinv, S->row0_a, S->nz0_a, nba, S->row0_e, S->nz0_e, nbe);
   GBS_LAUNCHED(1);
 
   PcgArgs a;
   memset(&a, 0, sizeof(a));
   a.nsys = 1;
   a.ensemble = 1;
-  a.nblocks = nblocks;
+  a.ta = BlockTable{nba, S->row0_a, S->nz0_a, nullptr, nullptr, nullptr};
+  a.te = BlockTable{nbe, S->row0_e, S->nz0_e, nullptr, nullptr, nullptr};
   a.cap = NOALLOC_CAP;
+  a.Ra = NOALLOC_RA;
+  a.Re = NOALLOC_RE;
+  a.ns = NOALLOC_NS;
+  a.stage_bytes = sb;
+  a.part_e = nba + 1;
   a.row_ptr = row_ptr;
   a.col = col;
   a.val = val;
   a.dinv = S->dinv;
-  a.blk_row0 = S->blk_row0;
   a.b = b;
   a.x = x;
   a.r = S->r;
@@ -889,30 +1093,8 @@ extern "C" int ksp_solve_cg_noalloc(int64_t n, const int32_t *row_ptr, const int
   a.sys_cnt = S->sys_cnt;
   a.st = S->st;
   a.ctl = &S->ctl;
-  a.rtol = oo.rtol;
-  a.maxit = oo.maxit;
-  a.nonzero_guess = oo.nonzero_guess;
-  a.timeout_ns = oo.timeout_ns;
-  a.barrier_extra = oo.debug_barrier_extra;
-  a.max_global = (int64_t)oo.maxit + 4;
-
-  cudaLaunchConfig_t cfg;
-  memset(&cfg, 0, sizeof(cfg));
-  cfg.gridDim = dim3((unsigned)G);
-  cfg.blockDim = dim3((unsigned)NOALLOC_TPB);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, k_pcg<false>, a);
-  if (e != cudaSuccess) {
-    set_error("ksp_solve_cg_noalloc: cooperative launch failed: %s", cudaGetErrorString(e));
-    return e == cudaErrorCooperativeLaunchTooLarge ? GBS_ERR_LAUNCH : GBS_ERR_CUDA;
-  }
-  count_launches(1);
+  fill_common(a, oo);
+  GBS_TRY(launch_coop(k_pcg<false>, a, G, 32 * NOALLOC_NW, smem, s));
   if (!res) return GBS_OK;
 
   SysState st;

@@ -152,10 +152,11 @@ def test_spmv_all_plans_and_irregular_rows():
     x = rng.standard_normal(n)
     yo = oracle.spmv(O, x)
     bound = abs_bound(O, x)
-    for R, T in [(32, 64), (64, 64), (128, 128), (256, 256), (512, 512), (128, 512)]:
-        A.set_plan(R, T)
+    for plan in [(32, 256, 8, 2), (64, 128, 4, 3), (128, 256, 8, 2), (512, 64, 2, 4),
+                 (32, 32, 1, 2), (96, 1024, 2, 2)]:
+        A.set_plan(*plan)
         y = A.mult(t(x)).cpu().numpy()
-        assert np.all(np.abs(y - yo) <= 1e-12 * bound), (R, T)
+        assert np.all(np.abs(y - yo) <= 1e-12 * bound), plan
     A.close()
 
 
@@ -185,7 +186,11 @@ def test_pcg_fp64_parity(name, make, rtol):
     assert r["status"] == B.OK and ro["status"] == oracle.OK
     tr = true_rel(O, p.b, xg)
     assert tr <= rtol * 1.05, tr
-    assert abs(r["true_rel_residual"] - tr) <= 1e-3 * tr + 1e-15
+    # the GPU recomputes ||b - A x|| with its own rounding (FMA rows): the two
+    # agree to the rounding error bound of the residual evaluation
+    kmax = int(np.diff(O.row_ptr).max()) + 1
+    ev = 2 * kmax * np.finfo(float).eps * np.linalg.norm(np.abs(p.b) + abs_bound(O, xg))
+    assert abs(r["true_rel_residual"] - tr) <= 1e-3 * tr + ev / np.linalg.norm(p.b)
     assert iters_close(r["iterations"], ro["iterations"]), (r["iterations"], ro["iterations"])
     assert abs(r["rnorm0"] - ro["rnorm0"]) <= 1e-12 * ro["rnorm0"]
     # both solutions solve the same system to rtol: they agree to ~cond * rtol
@@ -208,11 +213,12 @@ def test_pcg_c1_closed_form():
     A.close()
 
 
-@pytest.mark.parametrize("R,T", [(32, 64), (64, 128), (128, 128), (512, 512)])
-def test_pcg_plans(R, T):
+@pytest.mark.parametrize("plan", [(32, 256, 8, 2), (64, 96, 4, 3), (128, 128, 16, 2),
+                                  (32, 32, 1, 4)])
+def test_pcg_plans(plan):
     p = W.q1_hex(10, seed=21)
     A, O = assemble_both(p.nrows, p.ncols, p.i, p.j, p.v)
-    A.set_plan(R, T)
+    A.set_plan(*plan)
     x, r = A.solve(t(p.b), rtol=1e-9)
     assert r["status"] == B.OK
     assert true_rel(O, p.b, x.cpu().numpy()) <= 1.05e-9
