@@ -3,10 +3,11 @@
  *
  * The library assembles a CSR matrix on the GPU from COO triples, summing
  * duplicates, and solves A x = b with a Jacobi-preconditioned conjugate
- * gradient whose SpMV, vector updates and dot products run in one persistent
- * kernel.  On top of that sit an FP32-inner / FP64-refined solve, a batched
- * solve of many independent systems in one launch, and the adjoint of the
- * solve.
+ * gradient whose iterations run inside one CUDA graph: SpMV fused with p.Ap,
+ * the vector updates fused with their dot products, device-resident scalars,
+ * and a loop condition set on the device.  On top of that sit an
+ * FP32-inner / FP64-refined solve, a batched solve of many independent
+ * systems in one graph launch, and the adjoint of the solve.
  *
  * Paper: "PETSc/TAO developments for GPU-based early exascale systems".
  *   - COO assembly: Sec. 5 (MatSetPreallocationCOO / MatSetValuesCOO).
@@ -19,9 +20,8 @@
  *
  * Conventions for every entry point:
  *   - Pointers are DEVICE pointers unless the comment says "host".  The
- *     vectors handed to the solves (b, x, dLdx, lambda) must be 16-byte
- *     aligned (the kernels stream them with bulk copies); GBS_ERR_ARG
- *     otherwise.
+ *     vectors handed to the solves (b, x, dLdx, lambda) must be 8-byte
+ *     aligned (GBS_ERR_ARG otherwise).
  *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
  *     stream.  All work is enqueued on that stream.  Unless stated otherwise a
  *     call is asynchronous: the caller keeps every borrowed buffer alive (and
@@ -30,7 +30,7 @@
  *     signal crosses the ABI.  On failure gbs_last_error() returns a
  *     thread-local message.  Errors the host can see (bad arguments, CUDA API
  *     failures) are returned at once; errors found on the device (index out of
- *     range, bad diagonal, breakdown, NaN, iteration limit, barrier timeout)
+ *     range, bad diagonal, breakdown, NaN, iteration limit, time limit)
  *     are returned by the next call that synchronises (mat_create_coo*, or a
  *     solve given a non-NULL result pointer, or ksp_get_result).
  *   - Index type: int32 row/column indices, int32 CSR row pointers; so
@@ -59,12 +59,15 @@ enum {
   GBS_ERR_NAN = 7,        /* NaN / Inf met in the iteration or in b */
   GBS_ERR_MAXIT = 8,      /* iteration limit reached before rtol */
   GBS_ERR_STAGNATION = 9, /* refined solve: residual stopped decreasing */
-  GBS_ERR_TIMEOUT = 10,   /* an in-kernel grid-barrier wait exceeded timeout_ns */
-  GBS_ERR_LAUNCH = 11     /* persistent kernel could not be made co-resident */
+  GBS_ERR_TIMEOUT = 10,   /* the solve ran longer than ksp_opts.timeout_ns */
+  GBS_ERR_LAUNCH = 11     /* a kernel or graph could not be launched */
 };
 
 enum { GBS_INSERT = 0, GBS_ADD = 1 };
 enum { GBS_FP64 = 0, GBS_FP32_REFINED = 1 };
+/* Row-product kernels of a launch plan (mat_set_plan); a positive value n in
+ * {1, 2, 4, 8, 32} selects the CSR-vector kernel with n lanes per row. */
+enum { GBS_SPMV_AUTO = -1, GBS_SPMV_SELL = 0 };
 
 /* Solver options (host struct).  Fill with ksp_opts_default(), then override. */
 typedef struct {
@@ -75,12 +78,18 @@ typedef struct {
   double inner_rtol;    /* refined: FP32 inner tolerance (<= 0: 1e-4) */
   int32_t max_outer;    /* refined: max refinement steps (< 0: 30) */
   int32_t inner_maxit;  /* refined: inner products per step (< 0: as maxit) */
-  int64_t timeout_ns;   /* bound on each in-kernel barrier wait (<= 0: 2e9) */
+  int64_t timeout_ns;   /* wall-clock limit of the iteration loop, checked
+                           on the device once per iteration; systems still
+                           iterating then end with GBS_ERR_TIMEOUT (<= 0:
+                           no limit, the default) */
   int32_t nonzero_guess;/* 1: x holds the initial guess; 0: start from x = 0 */
-  int32_t debug_barrier_extra; /* testing only, normally 0: every grid barrier
-                           also waits for this many CTAs that do not exist, so
-                           each wait runs out after timeout_ns and the solve
-                           ends with GBS_ERR_TIMEOUT (exercises that path) */
+  int32_t host_loop;    /* 0 (default): one CUDA graph launch per solve, the
+                           loop runs on the device.  1: no graph; the host
+                           launches the iteration kernels in chunks of 16
+                           and reads a 4-byte stop flag after each chunk
+                           (synchronising the stream once per chunk), so
+                           profilers that cannot follow device-side graph
+                           loops see every kernel */
 } ksp_opts;
 
 /* Per-solve (or per-system) result, host struct. */
@@ -141,17 +150,22 @@ int mat_create_coo_batched(int32_t nsys, const int64_t *nrows_h, const int64_t *
 int mat_set_values_coo(gbs_mat A, const double *v, int mode, void *stream);
 
 /* y = A x (the MatMult of Sec. 6.1), FP64.  x: double[ncols], y: double[nrows],
- * must not overlap.  Each y_i sums its row's products in CSR order.
- * Asynchronous. */
+ * must not overlap.  The row products are those of the launch plan (see
+ * mat_set_plan).  Asynchronous. */
 int mat_mult(gbs_mat A, const double *x, double *y, void *stream);
 
 /*
  * Jacobi-preconditioned CG on the whole matrix (Sec. 6.1 CG without host
  * round trips; Sec. 7 diagonal preconditioner).  b, x: double[nrows]; x is the
- * initial guess when o->nonzero_guess, else overwritten from 0.  One persistent
- * cooperative kernel runs every iteration: SpMV fused with p.Ap, the x/r
- * updates fused with r.z and ||r||^2, and the p update, with deterministic
- * grid reductions and device-resident scalars.  o->precision =
+ * initial guess when o->nonzero_guess, else overwritten from 0.  One CUDA
+ * graph launch runs the solve: a setup kernel, a conditional WHILE node whose
+ * body is three kernels per iteration (SpMV fused with p.Ap; the x/r updates
+ * fused with r.z and ||r||^2; the p update, whose CTA 0 sets the loop
+ * condition), and a closing true-residual kernel.  Reductions are
+ * deterministic and the scalars stay on the device.  The graph is built on
+ * the first solve of each shape (precision, batched or not) and replayed
+ * afterwards; the call arguments are written to the device by a one-thread
+ * kernel first.  o->precision =
  * GBS_FP32_REFINED runs FP32 inner PCG (FP32 values, vectors, reductions)
  * inside FP64 iterative refinement (Sec. 2, A7).  o may be NULL (defaults).
  * res (host): if non-NULL the call synchronises and fills it, and returns its
@@ -164,8 +178,8 @@ int ksp_solve_cg(gbs_mat A, const double *b, double *x, const ksp_opts *o,
 /*
  * Batched solve of a handle made by mat_create_coo_batched: every system runs
  * its own PCG (own alpha, beta, norms, stopping test ||r_s|| <= rtol ||b_s||)
- * in one persistent launch, replayed from a CUDA graph; converged systems are
- * frozen.  b, x: double[sum nrows] in system order.  res_h: HOST array of nsys
+ * in the same graph launch, each kernel covering all systems; converged
+ * systems are frozen and the loop ends when none is left.  b, x: double[sum nrows] in system order.  res_h: HOST array of nsys
  * results or NULL (asynchronous).  Returns the first non-OK system status when
  * res_h is given.
  */
@@ -195,14 +209,16 @@ int ksp_adjoint_batched(gbs_mat A, const double *x, const double *dLdx, double *
  * exists for callers that must not allocate device memory -- code whose
  * device memory is budgeted and handed out by another allocator, or that
  * cannot afford the device-wide synchronisation cudaMalloc / cudaFree imply.
- * It runs the same persistent Jacobi-PCG kernel as ksp_solve_cg, on a CSR
+ * It runs the same Jacobi-PCG phase kernels as ksp_solve_cg, on a CSR
  * matrix the caller owns: row_ptr int32[n+1], col int32[nnz] (each < n),
  * val double[nnz]; b, x double[n]; all five 16-byte aligned.  All
- * its scratch lives in one fixed static device array (about 8.4 MB, resident
+ * its scratch lives in one fixed static device array (about 8.5 MB, resident
  * on every GPU that loads the library until the process exits), so n must be
  * <= 262144; a larger n returns
  * GBS_ERR_ARG without touching the GPU.  It calls no cudaMalloc, cudaFree or
- * other allocating routine.  Every call shares that array, which keeps the
+ * other allocating routine, and builds no CUDA graph: the host launches the
+ * iterations in chunks of 16 and reads a 4-byte stop flag after each chunk,
+ * so the call synchronises `stream` once per chunk.  Every call shares that array, which keeps the
  * last call's contents: calls that overlap on the GPU (other streams or host
  * threads) race, so the caller must serialise them.  The first call on a
  * device looks up the array's device address; make that first call before
@@ -219,10 +235,11 @@ int ksp_solve_cg_noalloc(int64_t n, const int32_t *row_ptr, const int32_t *col,
  * non-OK status. */
 int ksp_get_result(gbs_mat A, ksp_result *res, int32_t count, void *stream);
 
-/* Diagnostic: wall time the last solve on A spent in each phase of its
- * persistent kernel, as seen by CTA 0 between grid barriers (ns, HOST array of
- * 5: setup, SpMV phase, x/r update phase, p update phase, closing true
- * residual).  Synchronises `stream`. */
+/* Diagnostic: wall time the last solve on A spent in each phase (ns, HOST
+ * array of 5: setup, SpMV phase, x/r update phase, p update phase, closing
+ * true residual), summed over iterations.  A phase's time runs from the start
+ * of its kernel's CTA 0 to the start of the next phase kernel's CTA 0, so it
+ * includes the launch gap after it.  Synchronises `stream`. */
 int ksp_get_phase_ns(gbs_mat A, int64_t *phase_ns, void *stream);
 
 /* Sizes (host outputs; any may be NULL). */
@@ -240,21 +257,35 @@ int mat_get_coo_maps(gbs_mat A, const int32_t **perm, const int32_t **jmap,
                      int64_t *nkept);
 
 /*
- * Launch plan used by mat_mult and the solves.  Every warp of the persistent
- * kernels is an independent worker with its own bulk-copy pipeline:
- * spmv_rows rows per SpMV work block (a multiple of 32 in [32, 512]; lanes
- * own rows), update_rows rows per vector-update block (a multiple of 32 in
- * [32, 4096]), warps per CTA (1..16) and pipeline stages per warp (2..4).
- * mat_set_plan synchronises the device (the old plan may be in use) and
- * returns GBS_ERR_ARG for a plan whose stages do not fit in shared memory.
- * mat_create_coo picks a default; mat_autotune times candidates (a fixed
- * 30-iteration FP64 solve each, CUDA events on `stream`) and keeps the
- * fastest (it synchronises).  Host outputs may be NULL.
+ * Launch plan used by mat_mult and the solves.  Every phase kernel runs
+ * 256-thread CTAs; a CTA walks blocks c, c + grid, ... of its phase's block
+ * table.  spmv_rows: rows per block of the SpMV phases (a multiple of 32 in
+ * [32, 65536], or 0: about one block per CTA, at least 256); update_rows:
+ * rows per block of the vector-update phases (same).  kernel: the row
+ * products --
+ *   GBS_SPMV_SELL: a sliced-ELL copy of the matrix (32-row slices stored
+ *     column-major, padding skipped), one lane per row, built on first use
+ *     (about (4 + 8) bytes per padded entry more device memory, plus 4 bytes
+ *     more once a refined solve needs FP32 values);
+ *   1, 2, 4, 8 or 32: the CSR arrays read by that many lanes per row;
+ *   GBS_SPMV_AUTO: sliced ELL when padding adds at most 20% to the entries,
+ *     else CSR-vector with lanes from the mean row length.
+ * Every kernel sums each row in CSR order with one FMA per nonzero except
+ * CSR-vector with more than one lane, which splits the row over the lanes
+ * and adds the lane sums in a fixed tree.  ctas_per_sm: cap on the grids in
+ * CTAs per SM (1..64), or 0 for as many as fit on an SM at once (each phase
+ * kernel then runs in one wave and keeps one reduction slot per CTA).  mat_set_plan
+ * synchronises the device (the old tables may be in use) and drops the
+ * cached solve graphs.  mat_create_coo picks (0, 0, GBS_SPMV_AUTO, 0);
+ * mat_autotune times candidates (a fixed 30-iteration FP64 solve each, CUDA
+ * events on `stream`) and keeps the fastest (it synchronises).  mat_get_plan
+ * returns the kernel in use (never AUTO) and the grid of the SpMV-phase
+ * kernels.  Host outputs may be NULL.
  */
-int mat_set_plan(gbs_mat A, int32_t spmv_rows, int32_t update_rows, int32_t warps,
-                 int32_t stages);
-int mat_get_plan(gbs_mat A, int32_t *spmv_rows, int32_t *update_rows, int32_t *warps,
-                 int32_t *stages, int32_t *persistent_ctas);
+int mat_set_plan(gbs_mat A, int32_t spmv_rows, int32_t update_rows, int32_t kernel,
+                 int32_t ctas_per_sm);
+int mat_get_plan(gbs_mat A, int32_t *spmv_rows, int32_t *update_rows, int32_t *kernel,
+                 int32_t *ctas_per_sm, int32_t *spmv_grid);
 int mat_autotune(gbs_mat A, void *stream);
 
 /* Releases every device buffer the handle owns.  Synchronises the device
@@ -262,7 +293,8 @@ int mat_autotune(gbs_mat A, void *stream);
 int mat_destroy(gbs_mat A);
 
 /* Number of kernels this library has launched in this process (a diagnostic
- * counter; a graph replay counts the kernels it contains). */
+ * counter).  A solve graph counts its setup and closing kernels at launch and
+ * its loop kernels (three per trip) when the solve's results are read. */
 int64_t gbs_launch_count(void);
 
 /* Thread-local message describing the last error ("" if none). */

@@ -24,6 +24,7 @@ ERR_NOT_SPD, ERR_BREAKDOWN, ERR_NAN, ERR_MAXIT = 5, 6, 7, 8
 ERR_STAGNATION, ERR_TIMEOUT, ERR_LAUNCH = 9, 10, 11
 INSERT, ADD = 0, 1
 FP64, FP32_REFINED = 0, 1
+SPMV_AUTO, SPMV_SELL = -1, 0  # plan kernels; 1, 2, 4, 8, 32 = CSR-vector lanes per row
 
 EXPORTED = ["ksp_opts_default", "mat_create_coo", "mat_create_coo_batched",
             "mat_set_values_coo", "mat_mult", "ksp_solve_cg", "ksp_solve_cg_batched",
@@ -38,7 +39,7 @@ class KspOpts(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("inner_rtol", ctypes.c_double),
                 ("max_outer", ctypes.c_int32), ("inner_maxit", ctypes.c_int32),
                 ("timeout_ns", ctypes.c_int64), ("nonzero_guess", ctypes.c_int32),
-                ("debug_barrier_extra", ctypes.c_int32)]
+                ("host_loop", ctypes.c_int32)]
 
 
 class KspResult(ctypes.Structure):
@@ -136,14 +137,14 @@ def _dev(t: torch.Tensor | None, dtype, n: int | None = None, name: str = "tenso
 
 
 def make_opts(rtol=1e-8, maxit=-1, precision=FP64, inner_rtol=1e-4, max_outer=30,
-              inner_maxit=-1, timeout_ns=2_000_000_000, nonzero_guess=False,
-              debug_barrier_extra=0) -> KspOpts:
+              inner_maxit=-1, timeout_ns=0, nonzero_guess=False,
+              host_loop=False) -> KspOpts:
     o = KspOpts()
     lib().ksp_opts_default(ctypes.byref(o))
     o.rtol, o.maxit, o.precision = float(rtol), int(maxit), int(precision)
     o.inner_rtol, o.max_outer, o.inner_maxit = float(inner_rtol), int(max_outer), int(inner_maxit)
     o.timeout_ns, o.nonzero_guess = int(timeout_ns), int(bool(nonzero_guess))
-    o.debug_barrier_extra = int(debug_barrier_extra)
+    o.host_loop = int(bool(host_loop))
     return o
 
 
@@ -233,7 +234,8 @@ def ksp_get_result(A, count: int = 1, stream=None):
 
 
 def ksp_get_phase_ns(A, stream=None) -> dict:
-    """Per-phase time (ns) of the last solve's persistent kernel (CTA 0's view)."""
+    """Per-phase time (ns) of the last solve, summed over iterations (each
+    phase from its kernel's start to the next phase kernel's start)."""
     arr = (ctypes.c_int64 * 5)()
     _check(lib().ksp_get_phase_ns(A, ctypes.cast(arr, ctypes.c_void_p), _stream(stream)))
     return dict(zip(["setup", "spmv", "update_xr", "update_p", "true_residual"], list(arr)))
@@ -285,14 +287,15 @@ def mat_get_coo_maps(A):
             _view(jmap.value, info["nnz"] + 1, torch.int32))
 
 
-def mat_set_plan(A, spmv_rows: int, update_rows: int, warps: int, stages: int):
-    _check(lib().mat_set_plan(A, spmv_rows, update_rows, warps, stages))
+def mat_set_plan(A, spmv_rows: int, update_rows: int, kernel: int = SPMV_AUTO,
+                 ctas_per_sm: int = 0):
+    _check(lib().mat_set_plan(A, spmv_rows, update_rows, kernel, ctas_per_sm))
 
 
 def mat_get_plan(A) -> dict:
     v = [ctypes.c_int32() for _ in range(5)]
     _check(lib().mat_get_plan(A, *[ctypes.byref(t) for t in v]))
-    return dict(zip(["spmv_rows", "update_rows", "warps", "stages", "persistent_ctas"],
+    return dict(zip(["spmv_rows", "update_rows", "kernel", "ctas_per_sm", "spmv_grid"],
                     [t.value for t in v]))
 
 
@@ -371,8 +374,8 @@ class Mat:
     def coo_maps(self):
         return mat_get_coo_maps(self.h)
 
-    def set_plan(self, spmv_rows, update_rows=256, warps=8, stages=2):
-        mat_set_plan(self.h, spmv_rows, update_rows, warps, stages)
+    def set_plan(self, spmv_rows=0, update_rows=0, kernel=SPMV_AUTO, ctas_per_sm=0):
+        mat_set_plan(self.h, spmv_rows, update_rows, kernel, ctas_per_sm)
 
     def plan(self) -> dict:
         return mat_get_plan(self.h)

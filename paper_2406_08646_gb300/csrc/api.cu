@@ -32,27 +32,23 @@ static void free_handle(gbs_mat A) {
   int cur = 0;
   cudaGetDevice(&cur);
   cudaSetDevice(A->device);
-  if (A->graph) cudaGraphExecDestroy(A->graph);
+  drop_graphs(A);
   void *dev[] = {A->row_ptr, A->col, A->val, A->val32, A->perm, A->jmap, A->diag_pos,
                  A->dinv, A->dinv32, A->r, A->p, A->q, A->r32, A->p32, A->q32, A->d32,
-                 A->part, A->sys_cnt, A->st, A->ctl, A->err_word};
+                 A->part, A->sys_cnt, A->st, A->ctl, A->call};
   for (void *p : dev)
     if (p) cudaFree(p);
   free_table(A->ta);
   free_table(A->te);
+  free_sell(A);
   if (A->st_host) cudaFreeHost(A->st_host);
   cudaSetDevice(cur);
   delete A;
 }
 
-// Default plan: SpMV blocks of 32 rows (one row per lane) for long rows, 64
-// or 128 for short ones; 256-row update blocks; 8 warps; 2 or 3 stages.
-static int default_plan(gbs_mat A) {
-  const int32_t m = std::max<int32_t>(A->max_row_nnz, 1);
-  const int32_t Ra = m > 16 ? 32 : (m > 8 ? 64 : 128);
-  if (build_plan(A, Ra, 256, 8, 3) == GBS_OK) return GBS_OK;
-  return build_plan(A, Ra, 256, 8, 2);
-}
+// Default plan: everything automatic -- the row-product kernel chosen from
+// the matrix, one wave of CTAs per phase kernel, about one block per CTA.
+static int default_plan(gbs_mat A) { return build_plan(A, 0, 0, GBS_SPMV_AUTO, 0); }
 
 static int64_t max_system_rows(gbs_mat A, bool per_system) {
   if (!per_system) return A->nrows;
@@ -72,8 +68,8 @@ static int fill_opts(gbs_mat A, const ksp_opts *in, ksp_opts &o, bool per_system
     set_error("ksp opts: precision must be GBS_FP64 or GBS_FP32_REFINED");
     return GBS_ERR_ARG;
   }
-  if (o.debug_barrier_extra < 0) {
-    set_error("ksp opts: debug_barrier_extra must be >= 0");
+  if (o.host_loop != 0 && o.host_loop != 1) {
+    set_error("ksp opts: host_loop must be 0 or 1");
     return GBS_ERR_ARG;
   }
   const int64_t n = max_system_rows(A, per_system);
@@ -82,7 +78,7 @@ static int fill_opts(gbs_mat A, const ksp_opts *in, ksp_opts &o, bool per_system
   if (o.inner_maxit < 0) o.inner_maxit = dflt;
   if (!(o.inner_rtol > 0.0)) o.inner_rtol = 1e-4;
   if (o.max_outer < 0) o.max_outer = 30;
-  if (o.timeout_ns <= 0) o.timeout_ns = 2000000000LL;
+  if (o.timeout_ns < 0) o.timeout_ns = 0;
   return GBS_OK;
 }
 
@@ -126,9 +122,9 @@ void ksp_opts_default(ksp_opts *o) {
   o->inner_rtol = 1e-4;
   o->max_outer = 30;
   o->inner_maxit = -1;
-  o->timeout_ns = 2000000000LL;
+  o->timeout_ns = 0;
   o->nonzero_guess = 0;
-  o->debug_barrier_extra = 0;
+  o->host_loop = 0;
 }
 
 int mat_create_coo(int64_t nrows, int64_t ncols, int64_t ncoo, const int32_t *i,
@@ -240,15 +236,15 @@ static int solve_entry(gbs_mat A, const double *b, double *x, const ksp_opts *o,
     set_error("%s: mat_set_values_coo has not been called", fn);
     return GBS_ERR_ARG;
   }
-  if ((((uintptr_t)b | (uintptr_t)x) & 15u) != 0) {
-    set_error("%s: b and x must be 16-byte aligned device pointers", fn);
+  if ((((uintptr_t)b | (uintptr_t)x) & 7u) != 0) {
+    set_error("%s: b and x must be 8-byte aligned device pointers", fn);
     return GBS_ERR_ARG;
   }
   ksp_opts oo;
   GBS_TRY(fill_opts(A, o, oo, per_system));
   GBS_TRY(use_device(A));
   cudaStream_t s = (cudaStream_t)stream;
-  GBS_TRY(solve(A, b, x, oo, per_system, per_system, s));
+  GBS_TRY(solve(A, b, x, oo, per_system, s));
   if (res) return read_results(A, res, per_system ? A->nsys : 1, s);
   return GBS_OK;
 }
@@ -313,12 +309,7 @@ int ksp_get_phase_ns(gbs_mat A, int64_t *phase_ns, void *stream) {
     return GBS_ERR_ARG;
   }
   GBS_TRY(use_device(A));
-  DevCtl c;
-  GBS_TRY_CUDA(cudaMemcpyAsync(&c, A->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost,
-                               (cudaStream_t)stream));
-  GBS_TRY_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
-  for (int k = 0; k < 5; ++k) phase_ns[k] = c.phase_ns[k];
-  return GBS_OK;
+  return read_phase_ns(A, phase_ns, (cudaStream_t)stream);
 }
 
 int mat_get_info(gbs_mat A, int64_t *nrows, int64_t *ncols, int64_t *nnz, int64_t *ncoo,
@@ -350,22 +341,22 @@ int mat_get_coo_maps(gbs_mat A, const int32_t **perm, const int32_t **jmap, int6
   return GBS_OK;
 }
 
-int mat_set_plan(gbs_mat A, int32_t spmv_rows, int32_t update_rows, int32_t warps,
-                 int32_t stages) {
+int mat_set_plan(gbs_mat A, int32_t spmv_rows, int32_t update_rows, int32_t kernel,
+                 int32_t ctas_per_sm) {
   GBS_TRY(check_mat(A, "mat_set_plan"));
   GBS_TRY(use_device(A));
-  GBS_TRY_CUDA(cudaDeviceSynchronize());  // plan arrays may be in use
-  return build_plan(A, spmv_rows, update_rows, warps, stages);
+  GBS_TRY_CUDA(cudaDeviceSynchronize());  // the old tables may be in use
+  return build_plan(A, spmv_rows, update_rows, kernel, ctas_per_sm);
 }
 
-int mat_get_plan(gbs_mat A, int32_t *spmv_rows, int32_t *update_rows, int32_t *warps,
-                 int32_t *stages, int32_t *persistent_ctas) {
+int mat_get_plan(gbs_mat A, int32_t *spmv_rows, int32_t *update_rows, int32_t *kernel,
+                 int32_t *ctas_per_sm, int32_t *spmv_grid) {
   GBS_TRY(check_mat(A, "mat_get_plan"));
   if (spmv_rows) *spmv_rows = A->Ra;
   if (update_rows) *update_rows = A->Re;
-  if (warps) *warps = A->nwarps;
-  if (stages) *stages = A->nstages;
-  if (persistent_ctas) *persistent_ctas = A->grid_fp64;
+  if (kernel) *kernel = A->lanes;
+  if (ctas_per_sm) *ctas_per_sm = A->ctas_per_sm;
+  if (spmv_grid) *spmv_grid = A->ta.grid;
   return GBS_OK;
 }
 
@@ -380,11 +371,12 @@ int mat_autotune(gbs_mat A, void *stream) {
   if (A->nrows != A->ncols || A->nrows == 0) return GBS_OK;
   GBS_TRY(use_device(A));
   cudaStream_t s = (cudaStream_t)stream;
-  // (SpMV rows, update rows, warps per CTA, stages)
-  const int cands[][4] = {{32, 256, 8, 2},  {32, 256, 8, 3},  {32, 512, 8, 2},
-                          {64, 256, 8, 2},  {64, 256, 8, 3},  {128, 256, 8, 3},
-                          {64, 512, 8, 2},  {128, 512, 8, 2}, {32, 256, 16, 2},
-                          {64, 256, 16, 2}, {32, 128, 12, 3}, {64, 256, 4, 4}};
+  const int la = auto_lanes(A->nnz, A->nrows);
+  const int sk = A->lanes;  // the kernel the current plan chose
+  // (SpMV rows, update rows, row-product kernel, CTAs per SM cap)
+  const int cands[][4] = {{0, 0, sk, 0},     {0, 0, la, 0},     {256, 512, sk, 0},
+                          {512, 1024, sk, 0}, {0, 0, sk, 4},     {256, 2048, sk, 0},
+                          {0, 0, sk, 2},      {1024, 4096, sk, 0}};
   double *b = nullptr, *x = nullptr;
   GBS_TRY_CUDA(cudaMalloc(&b, sizeof(double) * A->nrows));
   GBS_TRY_CUDA(cudaMalloc(&x, sizeof(double) * A->nrows));
@@ -395,18 +387,21 @@ int mat_autotune(gbs_mat A, void *stream) {
   ksp_opts_default(&o);
   o.rtol = 0.0;
   o.maxit = 30;
+  o.inner_maxit = 30;
+  o.inner_rtol = 1e-4;
+  o.max_outer = 30;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  int best_plan[4] = {A->Ra, A->Re, A->nwarps, A->nstages};
+  int best_plan[4] = {A->Ra, A->Re, A->lanes, A->ctas_per_sm};
   float best = 1e30f;
   int st = GBS_OK;
   for (const auto &c : cands) {
     if (build_plan(A, c[0], c[1], c[2], c[3]) != GBS_OK) continue;
     if (launch_spmv(A, x, b, s) != GBS_OK) continue;
-    if (solve(A, b, x, o, false, false, s) != GBS_OK) continue;  // warm-up
+    if (solve(A, b, x, o, false, s) != GBS_OK) continue;  // warm-up (and graph build)
     cudaEventRecord(e0, s);
-    for (int rep = 0; rep < 3; ++rep) solve(A, b, x, o, false, false, s);
+    for (int rep = 0; rep < 3; ++rep) solve(A, b, x, o, false, s);
     cudaEventRecord(e1, s);
     if (cudaEventSynchronize(e1) != cudaSuccess) {
       st = GBS_ERR_CUDA;
@@ -419,6 +414,7 @@ int mat_autotune(gbs_mat A, void *stream) {
       for (int k = 0; k < 4; ++k) best_plan[k] = c[k];
     }
   }
+  A->trips_counted = true;  // the timed solves' results are never read
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(b);

@@ -582,6 +582,7 @@ int launch_set_values(gbs_mat A, const double *v, int mode, cudaStream_t s) {
     k_jacobi<<<grid_for(A->nrows, 256), 256, 0, s>>>(A->nrows, A->diag_pos, A->val, A->dinv);
     GBS_LAUNCHED(1);
   }
+  GBS_TRY(sell_values(A, s));
   A->values_set = true;
   A->val32_valid = false;
   return GBS_OK;
@@ -606,6 +607,7 @@ int launch_to_fp32(gbs_mat A, cudaStream_t s) {
   k_to_fp32<<<grid_for(std::max(A->nnz, A->nrows), 256), 256, 0, s>>>(
       A->nnz, A->val, A->val32, A->nrows, A->dinv, A->dinv32);
   GBS_LAUNCHED(1);
+  GBS_TRY(sell_values32(A, s));
   A->val32_valid = true;
   return GBS_OK;
 }

@@ -41,7 +41,7 @@ void count_launches(int64_t n);
 // ---------------------------------------------------------------- device state
 
 // Per-system solver state, written only by the CTA that completes a system's
-// reduction ("last arriver") and read by every CTA after the next grid barrier.
+// reduction ("last arriver") and read by the kernels of the following phases.
 struct SysState {
   double bb;        // ||b_s||^2
   double rho;       // r.z
@@ -57,30 +57,48 @@ struct SysState {
   int32_t iterations;
   int32_t outer;
   int32_t inner_it;
-  int32_t mode;     // refined: see pcg.cu
+  int32_t mode;     // refined: M_INNER / M_XUPD / M_START (phases.cuh)
   int32_t stall;
   int32_t first;    // refined: next p update is p = z
   int32_t zero_x;   // b == 0: x must be set to 0
   int32_t pad;
 };
 
-// Device-side error word plus counters used by the persistent kernels.
+// Per-solve control words (device).  Zeroed before every solve.
 struct DevCtl {
-  unsigned long long bar;  // grid-barrier arrival counter (monotonic)
-  int32_t err;             // GBS_ERR_TIMEOUT etc., 0 = none
   int32_t n_active;        // systems still iterating
-  int64_t phase_ns[5];     // CTA 0's time per phase: setup, A, B, C, final residual
+  int32_t err;             // GBS_ERR_TIMEOUT, 0 = none
+  int32_t stop[2];         // host-stepped loop: trip t is skipped iff stop[t & 1]
+  int64_t trips;           // loop trips completed
+  int64_t t_start;         // globaltimer at the start of the solve
+  int64_t stamp;           // globaltimer when the last phase kernel started
+  int32_t last_phase;      // index of that phase, -1 before the first
+  int32_t pad;
+  int64_t phase_ns[5];     // setup, A, B, C, final: start-to-next-start time
 };
 
-// Device block table plus its host mirror (see BlockTable in pipe.cuh).
+// Per-call solve arguments, copied to the device before each solve so that a
+// cached graph serves every call with the same shape.
+struct CallArgs {
+  const double *b;
+  double *x;
+  double rtol, inner_rtol;
+  int32_t maxit, inner_maxit, max_outer, nonzero_guess;
+  int64_t max_trips;   // cap on loop trips (a safety net; see solve())
+  int64_t timeout_ns;  // wall-clock limit of the loop, 0 = none
+};
+
+// Device block table plus its host mirror (BlockTable in phases.cuh).
 struct TableDev {
   int32_t nblocks = 0;
   int32_t *row0 = nullptr;       // nblocks + 1
-  int32_t *nz0 = nullptr;        // nblocks + 1
   int32_t *sys = nullptr;        // nblocks
   int32_t *sys_blk0 = nullptr;   // nsys + 1
-  int32_t *sys_slot0 = nullptr;  // nsys + 1 (for slot_workers workers)
+  int32_t *sys_slot0 = nullptr;  // nsys + 1 (for the table's grid)
+  int32_t *slice0 = nullptr;     // nblocks + 1: first 32-row slice of each block
   std::vector<int32_t> sys_blk0_h;
+  int32_t grid = 0;              // CTAs of the kernels that walk this table
+  int64_t nslots = 0;            // reduction slots: sum over systems of min(blocks, grid)
 };
 
 }  // namespace gbs
@@ -108,41 +126,48 @@ struct gbs_mat_s {
   std::vector<int64_t> row_off_h;  // nsys + 1
   std::vector<int32_t> max_row_sys_h;
 
-  // launch plan: two block tables (SpMV phases, vector-update phases), warps
-  // per CTA, pipeline stages and the per-warp stage size
+  // sliced-ELL copy used by the row products (sell.cu), built on demand
+  int64_t nslices = 0, sell_nnz = 0;
+  int32_t *sell_ptr = nullptr;     // nslices + 1 entry offsets (< 2^31)
+  int32_t *sell_row0 = nullptr;    // nslices + 1 first rows
+  int32_t *sell_col = nullptr;     // sell_nnz, -1 = padding
+  double *sell_val = nullptr;      // sell_nnz
+  float *sell_val32 = nullptr;     // sell_nnz (refined solves)
+  std::vector<int32_t> sell_slice0_h;  // nsys + 1 first slice of each system
+
+  // launch plan: two block tables (SpMV phases, vector-update phases), the
+  // row-product kernel (0: sliced ELL; 1, 2, 4, 8, 32: CSR-vector with that
+  // many lanes per row), CTAs per SM cap of the grids
   gbs::TableDev ta, te;
-  int32_t Ra = 32, Re = 256;  // rows per SpMV block / per update block
-  int32_t nwarps = 8, nstages = 2;
-  int32_t tpb = 256;          // 32 * nwarps
-  int32_t cap = 1024;         // staged nonzeros per SpMV block
-  int64_t stage_bytes = 0;
-  int32_t grid_fp64 = 0, grid_fp32 = 0, grid_spmv = 0;  // persistent grid sizes (per plan)
-  int32_t *err_word = nullptr;  // device error word of the SpMV pipeline
+  int32_t Ra = 256, Re = 512;   // rows per SpMV block / per update block
+  int32_t lanes = 0;
+  int32_t ctas_per_sm = 0;      // grid cap per SM, 0 = as many as fit (one wave)
 
   // solver workspace (device, allocated on first solve)
   double *r = nullptr, *p = nullptr, *q = nullptr;
   float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr;
   double *part = nullptr;       // reduction slots (table A region, then table E)
   int64_t part_cap = 0;
-  int32_t slot_workers = -1;    // worker count the slot offsets were built for
   unsigned *sys_cnt = nullptr;  // nsys arrival counters
   gbs::SysState *st = nullptr;  // nsys
   gbs::DevCtl *ctl = nullptr;
+  gbs::CallArgs *call = nullptr;
   gbs::SysState *st_host = nullptr;  // pinned copy for results
   int32_t last_count = 0;            // systems in the last solve's result
   bool last_ensemble = false;
+  bool trips_counted = true;         // launch counter already holds the last loop
 
-  // cached CUDA graph of the batched launch
-  cudaGraphExec_t graph = nullptr;
-  uint64_t graph_key[8] = {0};
+  // cached executable graphs [refined][per_system] of the solve loop
+  cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
 };
 
 namespace gbs {
 
 int ensure_solver_workspace(gbs_mat A, bool refined);
-int build_plan(gbs_mat A, int32_t spmv_rows, int32_t update_rows, int32_t nwarps,
-               int32_t nstages);
+int build_plan(gbs_mat A, int32_t spmv_rows, int32_t update_rows, int32_t lanes,
+               int32_t ctas_per_sm);
 void free_table(TableDev &t);
+void drop_graphs(gbs_mat A);
 int launch_spmv(gbs_mat A, const double *x, double *y, cudaStream_t s);
 int launch_set_values(gbs_mat A, const double *v, int mode, cudaStream_t s);
 int launch_to_fp32(gbs_mat A, cudaStream_t s);
@@ -151,7 +176,15 @@ int launch_adjoint_scatter(gbs_mat A, const double *lambda, const double *x,
 int symbolic(gbs_mat A, const int32_t *i, const int32_t *j, const int64_t *coo_off_h,
              cudaStream_t s);
 int solve(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool per_system,
-          bool use_graph, cudaStream_t s);
+          cudaStream_t s);
 int read_results(gbs_mat A, ksp_result *res, int32_t count, cudaStream_t s);
+int read_phase_ns(gbs_mat A, int64_t *phase_ns, cudaStream_t s);
+int auto_lanes(int64_t nnz, int64_t nrows);
+int phase_occupancy(int lanes, int *rows, int *upd);
+void free_sell(gbs_mat A);
+int sell_shape(gbs_mat A);
+int sell_build(gbs_mat A, cudaStream_t s);
+int sell_values(gbs_mat A, cudaStream_t s);
+int sell_values32(gbs_mat A, cudaStream_t s);
 
 }  // namespace gbs

@@ -1,34 +1,26 @@
-// Persistent fused Jacobi-PCG (Sec. 6.1 CG with device-resident scalars and
-// no host round trip; Sec. 7 diagonal preconditioning and batched systems;
-// Sec. 2 A7 FP32 inner solve under FP64 refinement).
+// Jacobi-PCG driver (Sec. 6.1 CG with device-resident scalars and no host
+// round trip; Sec. 7 diagonal preconditioning and batched systems; Sec. 2 A7
+// FP32 inner solve under FP64 refinement).  The phase bodies are in
+// phases.cuh.
 //
-// One cooperative launch runs the whole solve.  Every warp is an independent
-// worker with its own bulk-copy pipeline (pipe.cuh); global warp w takes
-// blocks w, w+W, w+2W, ... of the phase's block table (SpMV blocks for
-// products, larger update blocks for the vector updates; blocks never straddle
-// two systems).  Per iteration:
-//   A: q = A p (one FMA per nonzero) fused with the partial p.q     | barrier
-//   B: x += alpha p, r -= alpha q, z = D^-1 r (stored over q),
-//      partial r.z and r.r                                          | barrier
-//   C: p = z + beta p                                               | barrier
-// FP64 work per row and iteration is nnz_row + 7 FMA/MUL, the least the
-// algorithm allows, because GB300's FP64 issue rate is about the same as the
-// rate at which HBM delivers nonzeros.
+// A solve is one CUDA graph, built once per (precision, batched) shape and
+// matrix plan and replayed for every call:
 //
-// Reductions are deterministic: each warp reduces its rows of a system with a
-// fixed shuffle tree and writes one slot per (system, worker); the warp whose
-// slot arrives last (atomic arrival counter per system) sums the system's
-// slots in slot order and updates that system's scalars (alpha, beta, norms,
-// status).  Every warp reads them after the next grid barrier, so all take
-// the same decisions and iteration counts are reproducible run to run.
-// Converged systems are frozen (their blocks are skipped); the launch ends
-// when no system is active.  A final phase recomputes ||b - A x|| per system.
+//   memset control words -> setup -> WHILE(cond) { A -> B -> C } -> final
 //
-// Refined mode (per-system state machine, M_* modes): an FP32 PCG on FP32
-// copies of A and D^-1 with FP32 vectors and FP32 reductions solves
-// A d = r / ||r||; between inner solves the same A/B/C slots run the FP64
-// outer step: x += s d (slot C), r = b - A x and ||r|| (slot A), and the inner
-// restart r32 = RN(r / s), d = 0 (slot B).
+// The WHILE body repeats while its condition is non-zero; CTA 0 of phase C
+// sets it on the device (cudaGraphSetConditional), so the iteration count is
+// decided where the scalars live and the host never waits inside the loop.
+// The per-call arguments (b, x, tolerances, limits) sit in a small device
+// struct written by a one-thread kernel ahead of the graph, so one
+// instantiated graph serves every call.  Each phase is its own kernel at full
+// occupancy: no CTA ever waits for another, so no in-kernel wait exists that
+// could hang.
+//
+// With ksp_opts.host_loop, and always in ksp_solve_cg_noalloc (which may not
+// instantiate a graph), the same phase kernels run from a host loop instead:
+// trips are launched in chunks and each trip checks a stop flag written by
+// the previous one.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,675 +30,127 @@
 
 #include "device_util.cuh"
 #include "internal.cuh"
-#include "pipe.cuh"
+#include "phases.cuh"
 
 namespace gbs {
 
-enum { M_INNER = 0, M_XUPD = 1, M_START = 2 };
-constexpr int SLOT_STRIDE = 4;  // doubles per reduction slot
-constexpr int PCG_MAX_TPB = 512;
+// ------------------------------------------------------------------ kernels
 
-struct PcgArgs {
-  int32_t nsys, ensemble;
-  BlockTable ta, te;  // SpMV blocks, update blocks
-  int32_t cap, Ra, Re, ns;
-  int64_t stage_bytes;
-  int64_t part_e;  // first reduction slot of table te
-  const int32_t *row_ptr, *col;
-  const double *val;
-  const float *val32;
-  const double *dinv;
-  const float *dinv32;
-  const double *b;
-  double *x;
-  double *r, *p, *q;
-  float *r32, *p32, *q32, *d32;
-  double *part;
-  unsigned *sys_cnt;
-  SysState *st;
-  DevCtl *ctl;
-  double rtol, inner_rtol;
-  int32_t maxit, inner_maxit, max_outer, nonzero_guess;
-  int64_t timeout_ns;
-  int32_t barrier_extra;
-  int64_t max_global;  // cap on loop trips: every trip advances each active system
-};
+// Kernels with row products (setup, A, final) on the sliced-ELL layout
+// (L == 0) are held to 32 registers so that 8 CTAs fit per SM: the sliced
+// product is latency-bound and needs every warp slot to keep HBM busy.
+#define GBS_ROWS_BOUNDS(L) __launch_bounds__(PHASE_TPB, (L) == 0 ? SELL_MIN_CTAS : 1)
 
-__device__ __forceinline__ int sys_of(const PcgArgs &a, const BlockTable &t, int b) {
-  return a.ensemble ? 0 : __ldg(t.sys + b);
-}
-__device__ __forceinline__ int sys_b0(const PcgArgs &a, const BlockTable &t, int s) {
-  return a.ensemble ? 0 : __ldg(t.sys_blk0 + s);
-}
-__device__ __forceinline__ int sys_nblk(const PcgArgs &a, const BlockTable &t, int s) {
-  return a.ensemble ? t.nblocks : __ldg(t.sys_blk0 + s + 1) - __ldg(t.sys_blk0 + s);
-}
-__device__ __forceinline__ int64_t sys_slot0(const PcgArgs &a, const BlockTable &t, int s) {
-  return a.ensemble ? 0 : (int64_t)__ldg(t.sys_slot0 + s);
-}
-
-__device__ __forceinline__ void deactivate(const PcgArgs &a, SysState &S, int status) {
-  S.status = status;
-  S.active = 0;
-  atomicSub(&a.ctl->n_active, 1);
-}
-
-template <typename T, int NV>
-__device__ __forceinline__ void warp_sum(T (&v)[NV]) {
-#pragma unroll
-  for (int k = 0; k < NV; ++k)
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_xor_sync(FULL_MASK, v[k], off);
-}
-
-// Reduce the warp's NV partials over its run on system s (last block b of
-// table t) into the system's slot; the last arriving worker sums all slots in
-// slot order and calls fin(s, totals) on lane 0.  f32: FP32 accumulation.
-template <int NV, class Fin>
-__device__ __forceinline__ void wflush(const PcgArgs &a, const BlockTable &t, int64_t part_off,
-                                       int s, int b, int W, double (&acc)[NV], bool f32,
-                                       Fin &fin) {
-  const int lane = threadIdx.x & 31;
-  if (f32) {
-    float v[NV];
-#pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = (float)acc[k];
-    warp_sum<float, NV>(v);
-#pragma unroll
-    for (int k = 0; k < NV; ++k) acc[k] = (double)v[k];
-  } else {
-    warp_sum<double, NV>(acc);
+template <bool REFINED, int L>
+__global__ void GBS_ROWS_BOUNDS(L) k_pcg_setup(PcgArgs a) {
+  __shared__ double red[4 * 32];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int64_t t = (int64_t)global_ns();
+    a.ctl->t_start = t;
+    a.ctl->stamp = t;
+    a.ctl->last_phase = 0;
   }
-  const int b0 = sys_b0(a, t, s), nb = sys_nblk(a, t, s);
-  const int ns = min(nb, W);
-  const int slot = (b - b0) % W;
-  const int64_t base = part_off + sys_slot0(a, t, s);
-  int last = 0;
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) a.part[(base + slot) * SLOT_STRIDE + k] = acc[k];
-    __threadfence();
-    const unsigned prev = atomicAdd(a.sys_cnt + s, 1u);
-    last = (prev == (unsigned)(ns - 1)) ? 1 : 0;
-  }
-  last = __shfl_sync(FULL_MASK, last, 0);
-  if (last) {
-    __threadfence();
-    if (f32) {
-      float tot[NV];
-#pragma unroll
-      for (int k = 0; k < NV; ++k) tot[k] = 0.f;
-      for (int i = lane; i < ns; i += 32)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) tot[k] += (float)ldcg(a.part + (base + i) * SLOT_STRIDE + k);
-      warp_sum<float, NV>(tot);
-      if (lane == 0) {
-        double d[NV];
-#pragma unroll
-        for (int k = 0; k < NV; ++k) d[k] = (double)tot[k];
-        a.sys_cnt[s] = 0u;
-        fin(s, d);
-        __threadfence();
-      }
-    } else {
-      double tot[NV];
-#pragma unroll
-      for (int k = 0; k < NV; ++k) tot[k] = 0.0;
-      for (int i = lane; i < ns; i += 32)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) tot[k] += ldcg(a.part + (base + i) * SLOT_STRIDE + k);
-      warp_sum<double, NV>(tot);
-      if (lane == 0) {
-        a.sys_cnt[s] = 0u;
-        fin(s, tot);
-        __threadfence();
-      }
-    }
-  }
-  __syncwarp();
+  phase_setup<REFINED, L>(a, red);
 }
 
-// One warp's pass over its wanted blocks of table t, through its pipeline
-// (PIPE) or with plain loads.  work(s, d, stage, acc) processes block d of
-// system s; partials are flushed when the system changes and at the end.
-template <int NV, bool PIPE, class Want, class Issue, class Work, class Fin, class Load>
-__device__ __forceinline__ void wwalk(const PcgArgs &a, const BlockTable &t, int64_t part_off,
-                                      WarpPipe &P, int worker, int W, bool f32, Want &want,
-                                      Issue &issue, Work &work, Fin &fin, Load &load_sys) {
-  int cur_s = -1, cur_b = -1;
-  double acc[NV > 0 ? NV : 1];
-  auto on_block = [&](int b, const BlkDesc &d, unsigned char *stg) {
-    const int s = sys_of(a, t, b);
-    if (s != cur_s) {
-      if constexpr (NV > 0) {
-        if (cur_s >= 0) wflush<NV>(a, t, part_off, cur_s, cur_b, W, acc, f32, fin);
-      }
-      cur_s = s;
-      load_sys(s);
-#pragma unroll
-      for (int k = 0; k < (NV > 0 ? NV : 1); ++k) acc[k] = 0.0;
-    }
-    cur_b = b;
-    work(s, d, stg, acc);
-  };
-  if constexpr (PIPE) {
-    warp_stream(P, t, worker, W, want, issue, on_block);
-  } else {
-    for (int b = worker; b < t.nblocks; b += W)
-      if (want(b)) on_block(b, load_desc(t, b), P.stage(0));
-  }
-  if constexpr (NV > 0) {
-    if (cur_s >= 0) wflush<NV>(a, t, part_off, cur_s, cur_b, W, acc, f32, fin);
-  }
+template <bool REFINED, int L>
+__global__ void GBS_ROWS_BOUNDS(L) k_pcg_spmv(PcgArgs a) {
+  __shared__ double red[4 * 32];
+  if (!trip_live(a)) return;
+  stamp_phase(a, 1);
+  phase_A<REFINED, L>(a, red);
 }
-
-// Per-system "does this phase process system s", one-entry cache (the state
-// it reads is not modified during the phase while this warp still has blocks
-// of s to visit).
-struct WantCache {
-  int s = -1;
-  bool v = false;
-};
 
 template <bool REFINED>
-__global__ void __launch_bounds__(PCG_MAX_TPB) k_pcg(PcgArgs a) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const int W = gridDim.x * nw, worker = blockIdx.x * nw + warp;
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + (size_t)nw * a.ns * a.stage_bytes);
-  WarpPipe P{smem_raw + (size_t)warp * a.ns * a.stage_bytes, bars + warp * a.ns, a.ns, a.cap,
-             a.Ra, a.Re, a.stage_bytes, 0u, &a.ctl->err, a.timeout_ns, policy_evict_first(),
-             policy_evict_last()};
-  if (lane == 0) P.init_barriers();
-  __syncthreads();
-  GridBarrier gb{&a.ctl->bar, &a.ctl->err, 0ull, a.timeout_ns, (unsigned)a.barrier_extra};
-  // CTA 0 keeps the time spent in each phase (between grid barriers)
-  const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
-  uint64_t t_mark = timer ? global_ns() : 0;
-  int64_t t_acc[5] = {0, 0, 0, 0, 0};
-  auto lap = [&](int k) {
-    if (timer) {
-      const uint64_t t = global_ns();
-      t_acc[k] += (int64_t)(t - t_mark);
-      t_mark = t;
-    }
-  };
-  const NzRange z0(0, 0, 0);  // dummies for plain (unstaged) row products
-  const SliceRange<int32_t> rq0(0, 0);
-  const int64_t pa = 0, pe = a.part_e;  // slot regions of the two tables
+__global__ void __launch_bounds__(PHASE_TPB) k_pcg_update(PcgArgs a) {
+  __shared__ double red[4 * 32];
+  if (!trip_live(a)) return;
+  stamp_phase(a, 2);
+  phase_B<REFINED>(a, red);
+}
 
-  // warp-uniform copies of the current system's scalars (set by load_sys())
-  double c_alpha = 0, c_beta = 0, c_scale = 0;
-  int c_mode = M_INNER, c_first = 0, c_zero = 0;
-  auto load_sys = [&](int s) {
-    const SysState *S = a.st + s;
-    c_alpha = ldcg(&S->alpha);
-    c_beta = ldcg(&S->beta);
-    c_scale = ldcg(&S->scale);
-    c_mode = ldcg(&S->mode);
-    c_first = ldcg(&S->first);
-    c_zero = ldcg(&S->zero_x);
-  };
-  auto active_mode = [&](WantCache &wc, const BlockTable &t, int b, int mode) -> bool {
-    const int s = sys_of(a, t, b);
-    if (s != wc.s) {
-      const SysState *S = a.st + s;
-      wc.s = s;
-      wc.v = ldcg(&S->active) != 0 && (mode < 0 || ldcg(&S->mode) == mode);
-    }
-    return wc.v;
-  };
-  auto no_issue = [&](const BlkDesc &, unsigned char *, uint64_t *) {};
-  auto plain_row = [&](const double *xv, int r) -> double {
-    return row_product<double, false>(P, nullptr, z0, rq0, a.row_ptr, a.col, a.val, xv, r);
-  };
+template <bool REFINED>
+__global__ void __launch_bounds__(PHASE_TPB) k_pcg_direction(PcgArgs a) {
+  __shared__ double red[4 * 32];
+  const bool live = trip_live(a);
+  loop_control(a, live);
+  if (!live) return;
+  stamp_phase(a, 3);
+  phase_C<REFINED>(a, red);
+}
 
-  // ---------------------------------------------------------------- setup
-  {
-    auto want = [&](int) -> bool { return true; };
-    auto work = [&](int s, const BlkDesc &d, unsigned char *, double(&acc)[4]) {
-      for (int r = d.r0 + lane; r < d.r1; r += 32) {
-        const double bv = a.b[r];
-        const double rv = a.nonzero_guess ? bv - plain_row(a.x, r) : bv;
-        if (!a.nonzero_guess) a.x[r] = 0.0;
-        const double dv = a.dinv[r];
-        if (REFINED) {
-          a.r[r] = rv;
-          acc[0] = fma(rv, rv, acc[0]);
-        } else {
-          const double z = dv * rv;
-          a.r[r] = rv;
-          a.p[r] = z;
-          acc[0] = fma(rv, z, acc[0]);
-          acc[1] = fma(rv, rv, acc[1]);
-        }
-        acc[2] = fma(bv, bv, acc[2]);
-        acc[3] += (dv == 0.0) ? 1.0 : 0.0;
-      }
-    };
-    auto fin = [&](int s, double(&tot)[4]) {
-      SysState &S = a.st[s];
-      const double bb = tot[2], nbad = tot[3];
-      const double rr = REFINED ? tot[0] : tot[1];
-      const double rho = REFINED ? 0.0 : tot[0];
-      memset(&S, 0, sizeof(SysState));
-      S.bb = bb;
-      S.rho = rho;
-      S.rr = rr;
-      S.rnorm0 = S.rnorm = sqrt(rr);
-      int status = -1;
-      if (nbad > 0.0) status = GBS_ERR_NOT_SPD;
-      else if (!isfinite(bb)) status = GBS_ERR_NAN;
-      else if (bb == 0.0) {
-        status = GBS_OK;
-        S.zero_x = 1;
-        S.rnorm0 = S.rnorm = 0.0;
-      } else if (!isfinite(rr) || !isfinite(rho)) status = GBS_ERR_NAN;
-      else if (sqrt(rr) <= a.rtol * sqrt(bb)) status = GBS_OK;
-      else if (REFINED ? (a.max_outer <= 0) : (a.maxit <= 0)) status = GBS_ERR_MAXIT;
-      if (status >= 0) {
-        S.status = status;
-        S.active = 0;
-      } else {
-        S.status = GBS_OK;
-        S.active = 1;
-        if (REFINED) {
-          S.prev_rn = S.rnorm;
-          S.scale = S.rnorm;
-          S.mode = M_START;
-        }
-        atomicAdd(&a.ctl->n_active, 1);
-      }
-    };
-    wwalk<4, false>(a, a.ta, pa, P, worker, W, false, want, no_issue, work, fin, load_sys);
+template <int L>
+__global__ void GBS_ROWS_BOUNDS(L) k_pcg_final(PcgArgs a) {
+  __shared__ double red[4 * 32];
+  stamp_phase(a, 4);
+  phase_final<L>(a, red);
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    a.ctl->phase_ns[4] += (int64_t)global_ns() - a.ctl->stamp;
+}
+
+__global__ void k_put_call(CallArgs *dst, CallArgs v) { *dst = v; }
+
+struct PhaseKernels {
+  void (*setup)(PcgArgs);
+  void (*spmv)(PcgArgs);
+  void (*update)(PcgArgs);
+  void (*direction)(PcgArgs);
+  void (*final_)(PcgArgs);
+};
+
+template <bool R, int L>
+static PhaseKernels kernels_for() {
+  return PhaseKernels{k_pcg_setup<R, L>, k_pcg_spmv<R, L>, k_pcg_update<R>, k_pcg_direction<R>,
+                      k_pcg_final<L>};
+}
+
+static PhaseKernels phase_kernels(bool refined, int lanes) {
+  switch (lanes) {
+    case 1: return refined ? kernels_for<true, 1>() : kernels_for<false, 1>();
+    case 2: return refined ? kernels_for<true, 2>() : kernels_for<false, 2>();
+    case 8: return refined ? kernels_for<true, 8>() : kernels_for<false, 8>();
+    case 4: return refined ? kernels_for<true, 4>() : kernels_for<false, 4>();
+    case 32: return refined ? kernels_for<true, 32>() : kernels_for<false, 32>();
+    default: return refined ? kernels_for<true, 0>() : kernels_for<false, 0>();
   }
-
-  // ---------------------------------------------------------------- iterations
-  // Each trip runs one A/B/C round for every active system; the trip cap is a
-  // safety net (systems left active when it trips are reported as MAXIT).
-  for (int64_t trip = 0;; ++trip) {
-    const bool ok_top = gb.sync();
-    lap(trip == 0 ? 0 : 3);
-    if (!ok_top) break;
-    if (ld_relaxed_s32(&a.ctl->n_active) == 0) break;
-    if (trip >= a.max_global) break;
-
-    // ---- slot A: q = A p and p.q (FP64, or FP32 inner); refined outer
-    //      residual r = b - A x and ||r||^2 in FP64 (plain pass)
-    {
-      auto fin = [&](int s, double(&tot)[1]) {
-        SysState &S = a.st[s];
-        if (!REFINED) {
-          const double sigma = tot[0];
-          S.iterations += 1;
-          if (isnan(sigma)) deactivate(a, S, GBS_ERR_NAN);
-          else if (!(sigma > 0.0)) deactivate(a, S, GBS_ERR_BREAKDOWN);
-          else S.alpha = S.rho / sigma;
-        } else if (S.mode == M_INNER) {
-          const float sigma = (float)tot[0];
-          S.first = 0;
-          if (!(sigma > 0.0f)) {
-            if (S.inner_it == 0) deactivate(a, S, GBS_ERR_BREAKDOWN);
-            else {
-              S.mode = M_XUPD;
-              S.outer += 1;
-            }
-          } else {
-            S.alpha = (double)((float)S.rho / sigma);
-            S.inner_it += 1;
-            S.iterations += 1;
-          }
-        } else {  // outer residual
-          const double rn = sqrt(tot[0]);
-          S.rnorm = rn;
-          if (!isfinite(rn)) deactivate(a, S, GBS_ERR_NAN);
-          else if (rn <= a.rtol * sqrt(S.bb)) deactivate(a, S, GBS_OK);
-          else if (S.outer >= a.max_outer) deactivate(a, S, GBS_ERR_MAXIT);
-          else {
-            S.stall = (rn > 0.5 * S.prev_rn) ? S.stall + 1 : 0;
-            if (S.stall >= 2) deactivate(a, S, GBS_ERR_STAGNATION);
-            else {
-              S.prev_rn = rn;
-              S.scale = rn;
-              S.mode = M_START;
-            }
-          }
-        }
-      };
-      if (!REFINED) {
-        WantCache wc;
-        auto want = [&](int b) -> bool { return active_mode(wc, a.ta, b, -1); };
-        auto issue = [&](const BlkDesc &d, unsigned char *st, uint64_t *bar) {
-          const SliceRange<double> q(d.r0, d.r1);
-          if (arrive_for(bar, csr_bytes<double>(d, P.cap) + q.bytes())) {
-            csr_copy<double>(P, st, d, a.row_ptr, a.col, a.val, bar);
-            slice_copy<double>(P.SA(st), a.p, q, bar, P.pol_vec);
-          }
-        };
-        auto work = [&](int s, const BlkDesc &d, unsigned char *st, double(&acc)[1]) {
-          const SliceRange<double> q(d.r0, d.r1);
-          auto f = [&](int r, double qv) {
-            a.q[r] = qv;
-            acc[0] = fma(slice_get<double>(P.SA(st), a.p, q, r), qv, acc[0]);
-          };
-          block_rows<double>(P, st, d, a.row_ptr, a.col, a.val, a.p, f);
-        };
-        wwalk<1, true>(a, a.ta, pa, P, worker, W, false, want, issue, work, fin, load_sys);
-      } else {
-        {  // inner FP32 SpMV, pipelined
-          WantCache wc;
-          auto want = [&](int b) -> bool { return active_mode(wc, a.ta, b, M_INNER); };
-          auto issue = [&](const BlkDesc &d, unsigned char *st, uint64_t *bar) {
-            const SliceRange<float> q(d.r0, d.r1);
-            if (arrive_for(bar, csr_bytes<float>(d, P.cap) + q.bytes())) {
-              csr_copy<float>(P, st, d, a.row_ptr, a.col, a.val32, bar);
-              slice_copy<float>(P.SA(st), a.p32, q, bar, P.pol_vec);
-            }
-          };
-          auto work = [&](int s, const BlkDesc &d, unsigned char *st, double(&acc)[1]) {
-            const SliceRange<float> q(d.r0, d.r1);
-            auto f = [&](int r, float qv) {
-              a.q32[r] = qv;
-              acc[0] = (double)fmaf(slice_get<float>(P.SA(st), a.p32, q, r), qv, (float)acc[0]);
-            };
-            block_rows<float>(P, st, d, a.row_ptr, a.col, a.val32, a.p32, f);
-          };
-          wwalk<1, true>(a, a.ta, pa, P, worker, W, true, want, issue, work, fin, load_sys);
-        }
-        {  // FP64 outer residual, plain
-          WantCache wc;
-          auto want = [&](int b) -> bool { return active_mode(wc, a.ta, b, M_XUPD); };
-          auto work = [&](int s, const BlkDesc &d, unsigned char *, double(&acc)[1]) {
-            for (int r = d.r0 + lane; r < d.r1; r += 32) {
-              const double rv = a.b[r] - plain_row(a.x, r);
-              a.r[r] = rv;
-              acc[0] = fma(rv, rv, acc[0]);
-            }
-          };
-          wwalk<1, false>(a, a.ta, pa, P, worker, W, false, want, no_issue, work, fin, load_sys);
-        }
-      }
-    }
-    const bool ok_a = gb.sync();
-    lap(1);
-    if (!ok_a) break;
-
-    // ---- slot B: x += alpha p, r -= alpha q, z = D^-1 r (kept in q for slot
-    //      C), r.z and r.r; or the refined inner restart
-    {
-      auto fin = [&](int s, double(&tot)[2]) {
-        SysState &S = a.st[s];
-        if (!REFINED) {
-          const double rho_new = tot[0], rr = tot[1];
-          const double rn = sqrt(rr);
-          S.rr = rr;
-          S.rnorm = rn;
-          if (!isfinite(rn) || !isfinite(rho_new)) deactivate(a, S, GBS_ERR_NAN);
-          else if (rn <= a.rtol * sqrt(S.bb)) deactivate(a, S, GBS_OK);
-          else if (S.iterations >= a.maxit) deactivate(a, S, GBS_ERR_MAXIT);
-          else {
-            S.beta = rho_new / S.rho;
-            S.rho = rho_new;
-          }
-        } else if (S.mode == M_START) {
-          const float rho = (float)tot[0], rr = (float)tot[1];
-          const float r0 = sqrtf(rr);
-          S.rho = rho;
-          S.rr = rr;
-          S.r0in = r0;
-          S.inner_it = 0;
-          if (!((double)r0 > a.inner_rtol * (double)r0) || a.inner_maxit <= 0)
-            deactivate(a, S, GBS_ERR_BREAKDOWN);
-          else {
-            S.mode = M_INNER;
-            S.first = 1;
-          }
-        } else {  // M_INNER
-          const float rho_new = (float)tot[0], rr = (float)tot[1];
-          const float beta = rho_new / (float)S.rho;
-          S.rho = rho_new;
-          S.rr = rr;
-          if (!((double)sqrtf(rr) > a.inner_rtol * S.r0in) || S.inner_it >= a.inner_maxit) {
-            S.mode = M_XUPD;
-            S.outer += 1;
-          } else {
-            S.beta = beta;
-          }
-        }
-      };
-      if (!REFINED) {
-        WantCache wc;
-        auto want = [&](int b) -> bool { return active_mode(wc, a.te, b, -1); };
-        auto issue = [&](const BlkDesc &d, unsigned char *st, uint64_t *bar) {
-          const SliceRange<double> q(d.r0, d.r1);
-          if (arrive_for(bar, 5u * q.bytes())) {
-            slice_copy<double>(P.SE(st, 0), a.p, q, bar, P.pol_vec);
-            slice_copy<double>(P.SE(st, 1), a.q, q, bar, P.pol_vec);
-            slice_copy<double>(P.SE(st, 2), a.x, q, bar, P.pol_vec);
-            slice_copy<double>(P.SE(st, 3), a.r, q, bar, P.pol_vec);
-            slice_copy<double>(P.SE(st, 4), a.dinv, q, bar, P.pol_vec);
-          }
-        };
-        auto work = [&](int s, const BlkDesc &d, unsigned char *st, double(&acc)[2]) {
-          const SliceRange<double> q(d.r0, d.r1);
-          for (int r = d.r0 + lane; r < d.r1; r += 32) {
-            const double pv = slice_get<double>(P.SE(st, 0), a.p, q, r);
-            const double qv = slice_get<double>(P.SE(st, 1), a.q, q, r);
-            const double xv = fma(c_alpha, pv, slice_get<double>(P.SE(st, 2), a.x, q, r));
-            const double rv = fma(-c_alpha, qv, slice_get<double>(P.SE(st, 3), a.r, q, r));
-            const double z = slice_get<double>(P.SE(st, 4), a.dinv, q, r) * rv;
-            a.x[r] = xv;
-            a.r[r] = rv;
-            a.q[r] = z;
-            acc[0] = fma(rv, z, acc[0]);
-            acc[1] = fma(rv, rv, acc[1]);
-          }
-        };
-        wwalk<2, true>(a, a.te, pe, P, worker, W, false, want, issue, work, fin, load_sys);
-      } else {
-        {  // inner FP32 update, pipelined
-          WantCache wc;
-          auto want = [&](int b) -> bool { return active_mode(wc, a.te, b, M_INNER); };
-          auto issue = [&](const BlkDesc &d, unsigned char *st, uint64_t *bar) {
-            const SliceRange<float> q(d.r0, d.r1);
-            if (arrive_for(bar, 5u * q.bytes())) {
-              slice_copy<float>(P.SE(st, 0), a.p32, q, bar, P.pol_vec);
-              slice_copy<float>(P.SE(st, 1), a.q32, q, bar, P.pol_vec);
-              slice_copy<float>(P.SE(st, 2), a.d32, q, bar, P.pol_vec);
-              slice_copy<float>(P.SE(st, 3), a.r32, q, bar, P.pol_vec);
-              slice_copy<float>(P.SE(st, 4), a.dinv32, q, bar, P.pol_vec);
-            }
-          };
-          auto work = [&](int s, const BlkDesc &d, unsigned char *st, double(&acc)[2]) {
-            const SliceRange<float> q(d.r0, d.r1);
-            const float al = (float)c_alpha;
-            float a0 = (float)acc[0], a1 = (float)acc[1];
-            for (int r = d.r0 + lane; r < d.r1; r += 32) {
-              const float pv = slice_get<float>(P.SE(st, 0), a.p32, q, r);
-              const float qv = slice_get<float>(P.SE(st, 1), a.q32, q, r);
-              const float dv = fmaf(al, pv, slice_get<float>(P.SE(st, 2), a.d32, q, r));
-              const float rv = fmaf(-al, qv, slice_get<float>(P.SE(st, 3), a.r32, q, r));
-              const float z = slice_get<float>(P.SE(st, 4), a.dinv32, q, r) * rv;
-              a.d32[r] = dv;
-              a.r32[r] = rv;
-              a.q32[r] = z;
-              a0 = fmaf(rv, z, a0);
-              a1 = fmaf(rv, rv, a1);
-            }
-            acc[0] = (double)a0;
-            acc[1] = (double)a1;
-          };
-          wwalk<2, true>(a, a.te, pe, P, worker, W, true, want, issue, work, fin, load_sys);
-        }
-        {  // inner restart on the scaled FP64 residual, plain
-          WantCache wc;
-          auto want = [&](int b) -> bool { return active_mode(wc, a.te, b, M_START); };
-          auto work = [&](int s, const BlkDesc &d, unsigned char *, double(&acc)[2]) {
-            float a0 = (float)acc[0], a1 = (float)acc[1];
-            for (int r = d.r0 + lane; r < d.r1; r += 32) {
-              const float rv = __double2float_rn(a.r[r] / c_scale);
-              const float z = a.dinv32[r] * rv;
-              a.r32[r] = rv;
-              a.d32[r] = 0.0f;
-              a.q32[r] = z;
-              a0 = fmaf(rv, z, a0);
-              a1 = fmaf(rv, rv, a1);
-            }
-            acc[0] = (double)a0;
-            acc[1] = (double)a1;
-          };
-          wwalk<2, false>(a, a.te, pe, P, worker, W, true, want, no_issue, work, fin, load_sys);
-        }
-      }
-    }
-    const bool ok_b = gb.sync();
-    lap(2);
-    if (!ok_b) break;
-    if (ld_relaxed_s32(&a.ctl->n_active) == 0) break;
-
-    // ---- slot C (no reduction): p = z + beta p with z from slot B; refined
-    //      x += s d
-    {
-      auto fin = [&](int, double(&)[1]) {};
-      if (!REFINED) {
-        WantCache wc;
-        auto want = [&](int b) -> bool { return active_mode(wc, a.te, b, -1); };
-        auto issue = [&](const BlkDesc &d, unsigned char *st, uint64_t *bar) {
-          const SliceRange<double> q(d.r0, d.r1);
-          if (arrive_for(bar, 2u * q.bytes())) {
-            slice_copy<double>(P.SE(st, 0), a.p, q, bar, P.pol_vec);
-            slice_copy<double>(P.SE(st, 1), a.q, q, bar, P.pol_vec);
-          }
-        };
-        auto work = [&](int s, const BlkDesc &d, unsigned char *st, double(&)[1]) {
-          const SliceRange<double> q(d.r0, d.r1);
-          for (int r = d.r0 + lane; r < d.r1; r += 32) {
-            const double pv = slice_get<double>(P.SE(st, 0), a.p, q, r);
-            const double z = slice_get<double>(P.SE(st, 1), a.q, q, r);
-            a.p[r] = fma(c_beta, pv, z);
-          }
-        };
-        wwalk<0, true>(a, a.te, pe, P, worker, W, false, want, issue, work, fin, load_sys);
-      } else {
-        {
-          WantCache wc;
-          auto want = [&](int b) -> bool { return active_mode(wc, a.te, b, M_INNER); };
-          auto issue = [&](const BlkDesc &d, unsigned char *st, uint64_t *bar) {
-            const SliceRange<float> q(d.r0, d.r1);
-            if (arrive_for(bar, 2u * q.bytes())) {
-              slice_copy<float>(P.SE(st, 0), a.p32, q, bar, P.pol_vec);
-              slice_copy<float>(P.SE(st, 1), a.q32, q, bar, P.pol_vec);
-            }
-          };
-          auto work = [&](int s, const BlkDesc &d, unsigned char *st, double(&)[1]) {
-            const SliceRange<float> q(d.r0, d.r1);
-            const float be = (float)c_beta;
-            for (int r = d.r0 + lane; r < d.r1; r += 32) {
-              const float pv = slice_get<float>(P.SE(st, 0), a.p32, q, r);
-              const float z = slice_get<float>(P.SE(st, 1), a.q32, q, r);
-              a.p32[r] = c_first ? z : fmaf(be, pv, z);
-            }
-          };
-          wwalk<0, true>(a, a.te, pe, P, worker, W, false, want, issue, work, fin, load_sys);
-        }
-        {  // x += s d, plain
-          WantCache wc;
-          auto want = [&](int b) -> bool { return active_mode(wc, a.te, b, M_XUPD); };
-          auto work = [&](int s, const BlkDesc &d, unsigned char *, double(&)[1]) {
-            for (int r = d.r0 + lane; r < d.r1; r += 32)
-              a.x[r] = fma(c_scale, (double)a.d32[r], a.x[r]);
-          };
-          wwalk<0, false>(a, a.te, pe, P, worker, W, false, want, no_issue, work, fin, load_sys);
-        }
-      }
-    }
-  }
-
-  // ---------------------------------------------------------------- true residual
-  if (!gb.sync()) return;
-  lap(0);
-  {
-    auto want = [&](int) -> bool { return true; };
-    auto work = [&](int s, const BlkDesc &d, unsigned char *, double(&acc)[1]) {
-      if (c_zero) {  // b_s == 0: x_s = 0 exactly, no product needed
-        for (int r = d.r0 + lane; r < d.r1; r += 32) a.x[r] = 0.0;
-        return;
-      }
-      for (int r = d.r0 + lane; r < d.r1; r += 32) {
-        const double t = a.b[r] - plain_row(a.x, r);
-        acc[0] = fma(t, t, acc[0]);
-      }
-    };
-    auto fin = [&](int s, double(&tot)[1]) { a.st[s].tt = tot[0]; };
-    wwalk<1, false>(a, a.ta, pa, P, worker, W, false, want, no_issue, work, fin, load_sys);
-  }
-  lap(4);
-  if (timer)
-    for (int k = 0; k < 5; ++k) a.ctl->phase_ns[k] = t_acc[k];
 }
 
 // ------------------------------------------------------------------ host side
 
-static size_t pcg_smem_for(int nwarps, int ns, int64_t stage_bytes) {
-  return (size_t)nwarps * ns * (size_t)stage_bytes + (size_t)nwarps * ns * 8;
+// CTAs per SM that fit at once for the kernels walking the SpMV table (setup,
+// A, final) and the update table (B, C), FP64 and refined, for the plan's
+// row-product kernel.
+int phase_occupancy(int lanes, int *rows, int *upd) {
+  const PhaseKernels K[2] = {phase_kernels(false, lanes), phase_kernels(true, lanes)};
+  int r = 1 << 20, u = 1 << 20;
+  for (const PhaseKernels &k : K) {
+    for (void (*f)(PcgArgs) : {k.setup, k.spmv, k.final_}) {
+      int n = 0;
+      GBS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, PHASE_TPB, 0));
+      r = std::min(r, n);
+    }
+    for (void (*f)(PcgArgs) : {k.update, k.direction}) {
+      int n = 0;
+      GBS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, PHASE_TPB, 0));
+      u = std::min(u, n);
+    }
+  }
+  *rows = std::max(r, 1);
+  *upd = std::max(u, 1);
+  return GBS_OK;
 }
-static size_t pcg_smem(gbs_mat A) { return pcg_smem_for(A->nwarps, A->nstages, A->stage_bytes); }
 
 static BlockTable view(const TableDev &t) {
-  return BlockTable{t.nblocks, t.row0, t.nz0, t.sys, t.sys_blk0, t.sys_slot0};
+  return BlockTable{t.nblocks, t.row0, t.sys, t.sys_blk0, t.sys_slot0, t.slice0};
 }
 
-template <bool REFINED>
-static int raise_smem_limit(size_t smem) {
-  cudaFuncAttributes fa;
-  GBS_TRY_CUDA(cudaFuncGetAttributes(&fa, k_pcg<REFINED>));
-  if (fa.maxDynamicSharedSizeBytes < (int)smem)
-    GBS_TRY_CUDA(cudaFuncSetAttribute(k_pcg<REFINED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-  return GBS_OK;
-}
-
-template <bool REFINED>
-static int pcg_grid(gbs_mat A, int *grid) {
-  const size_t smem = pcg_smem(A);
-  GBS_TRY(raise_smem_limit<REFINED>(smem));
-  int per_sm = 0, nsm = 0;
-  GBS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<REFINED>, A->tpb, smem));
-  GBS_TRY_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, A->device));
-  if (per_sm < 1) {
-    set_error("persistent PCG kernel does not fit on an SM (tpb %d, smem %zu)", A->tpb, smem);
-    return GBS_ERR_LAUNCH;
-  }
-  // no more CTAs than the larger table has blocks for its warps
-  const int64_t nb = std::max(A->ta.nblocks, A->te.nblocks);
-  int64_t g = std::min<int64_t>((int64_t)per_sm * nsm, (nb + A->nwarps - 1) / A->nwarps);
-  *grid = (int)std::max<int64_t>(g, 1);
-  return GBS_OK;
-}
-
-// Slot offsets for W workers: system s owns min(nblocks_s, W) slots per table.
-static int ensure_slots(gbs_mat A, int W, cudaStream_t s) {
-  const int64_t need = std::max<int64_t>((int64_t)A->ta.nblocks + A->te.nblocks, 1) + 2;
-  if (A->part_cap < need) {
-    if (A->part) cudaFree(A->part);
-    A->part = nullptr;
-    GBS_TRY_CUDA(cudaMalloc(&A->part, sizeof(double) * SLOT_STRIDE * need));
-    A->part_cap = need;
-  }
-  if (A->slot_workers != W) {
-    for (TableDev *t : {&A->ta, &A->te}) {
-      std::vector<int32_t> so(A->nsys + 1, 0);
-      for (int32_t q = 0; q < A->nsys; ++q) {
-        const int32_t nb = t->sys_blk0_h[q + 1] - t->sys_blk0_h[q];
-        so[q + 1] = so[q] + std::min(nb, W);
+void drop_graphs(gbs_mat A) {
+  for (auto &row : A->graph)
+    for (auto &g : row)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
       }
-      GBS_TRY_CUDA(cudaMemcpyAsync(t->sys_slot0, so.data(), sizeof(int32_t) * (A->nsys + 1),
-                                   cudaMemcpyHostToDevice, s));
-      GBS_TRY_CUDA(cudaStreamSynchronize(s));  // `so` is pageable and goes out of scope
-    }
-    A->slot_workers = W;
-  }
-  return GBS_OK;
 }
 
 int ensure_solver_workspace(gbs_mat A, bool refined) {
@@ -718,56 +162,78 @@ int ensure_solver_workspace(gbs_mat A, bool refined) {
     GBS_TRY_CUDA(cudaMalloc(&A->sys_cnt, sizeof(unsigned) * A->nsys));
     GBS_TRY_CUDA(cudaMalloc(&A->st, sizeof(SysState) * A->nsys));
     GBS_TRY_CUDA(cudaMalloc(&A->ctl, sizeof(DevCtl)));
+    GBS_TRY_CUDA(cudaMalloc(&A->call, sizeof(CallArgs)));
     GBS_TRY_CUDA(cudaMallocHost(&A->st_host, sizeof(SysState) * A->nsys));
     GBS_TRY_CUDA(cudaMemset(A->sys_cnt, 0, sizeof(unsigned) * A->nsys));
     GBS_TRY_CUDA(cudaMemset(A->ctl, 0, sizeof(DevCtl)));
-    A->slot_workers = -1;
   }
   if (refined && !A->r32) {
     GBS_TRY_CUDA(cudaMalloc(&A->r32, sizeof(float) * n));
     GBS_TRY_CUDA(cudaMalloc(&A->p32, sizeof(float) * n));
     GBS_TRY_CUDA(cudaMalloc(&A->q32, sizeof(float) * n));
     GBS_TRY_CUDA(cudaMalloc(&A->d32, sizeof(float) * n));
+    drop_graphs(A);  // a cached refined graph would hold null FP32 pointers
+  }
+  const int64_t need = A->ta.nslots + A->te.nslots + 1;
+  if (A->part_cap < need) {
+    if (A->part) cudaFree(A->part);
+    A->part = nullptr;
+    A->part_cap = 0;
+    GBS_TRY_CUDA(cudaMalloc(&A->part, sizeof(double) * SLOT_STRIDE * need));
+    A->part_cap = need;
+    drop_graphs(A);  // cached graphs hold the old pointer
   }
   return GBS_OK;
 }
 
-static void fill_common(PcgArgs &a, const ksp_opts &o) {
-  a.rtol = o.rtol;
-  a.inner_rtol = o.inner_rtol;
-  a.maxit = o.maxit;
-  a.inner_maxit = o.inner_maxit;
-  a.max_outer = o.max_outer;
-  a.nonzero_guess = o.nonzero_guess;
-  a.timeout_ns = o.timeout_ns;
-  a.barrier_extra = o.debug_barrier_extra;
-  a.max_global = o.precision == GBS_FP32_REFINED
-                     ? ((int64_t)o.max_outer + 1) * ((int64_t)o.inner_maxit + 3) + 4
-                     : (int64_t)o.maxit + 4;
+// Loop-trip cap: a safety net only (each trip advances every active system).
+static int64_t max_trips_for(const ksp_opts &o) {
+  return o.precision == GBS_FP32_REFINED
+             ? ((int64_t)o.max_outer + 1) * ((int64_t)o.inner_maxit + 3) + 4
+             : (int64_t)o.maxit + 4;
 }
 
-static PcgArgs make_args(gbs_mat A, const double *b, double *x, const ksp_opts &o,
-                         bool per_system) {
+static CallArgs call_args(const double *b, double *x, const ksp_opts &o) {
+  CallArgs c;
+  memset(&c, 0, sizeof(c));
+  c.b = b;
+  c.x = x;
+  c.rtol = o.rtol;
+  c.inner_rtol = o.inner_rtol;
+  c.maxit = o.maxit;
+  c.inner_maxit = o.inner_maxit;
+  c.max_outer = o.max_outer;
+  c.nonzero_guess = o.nonzero_guess;
+  c.max_trips = max_trips_for(o);
+  c.timeout_ns = o.timeout_ns > 0 ? o.timeout_ns : 0;
+  return c;
+}
+
+static int put_call(CallArgs *dst, const CallArgs &c, cudaStream_t s) {
+  k_put_call<<<1, 1, 0, s>>>(dst, c);
+  GBS_LAUNCHED(1);
+  return GBS_OK;
+}
+
+static PcgArgs make_args(gbs_mat A, bool per_system) {
   PcgArgs a;
   memset(&a, 0, sizeof(a));
   a.nsys = per_system ? A->nsys : 1;
   a.ensemble = per_system ? 0 : 1;
   a.ta = view(A->ta);
   a.te = view(A->te);
-  a.cap = A->cap;
-  a.Ra = A->Ra;
-  a.Re = A->Re;
-  a.ns = A->nstages;
-  a.stage_bytes = A->stage_bytes;
-  a.part_e = A->ta.nblocks + 1;
+  a.part_e = A->ta.nslots;
   a.row_ptr = A->row_ptr;
   a.col = A->col;
   a.val = A->val;
   a.val32 = A->val32;
+  a.sptr = A->sell_ptr;
+  a.srow0 = A->sell_row0;
+  a.scol = A->sell_col;
+  a.sval = A->sell_val;
+  a.sval32 = A->sell_val32;
   a.dinv = A->dinv;
   a.dinv32 = A->dinv32;
-  a.b = b;
-  a.x = x;
   a.r = A->r;
   a.p = A->p;
   a.q = A->q;
@@ -779,97 +245,152 @@ static PcgArgs make_args(gbs_mat A, const double *b, double *x, const ksp_opts &
   a.sys_cnt = A->sys_cnt;
   a.st = A->st;
   a.ctl = A->ctl;
-  fill_common(a, o);
+  a.call = A->call;
   return a;
 }
 
-static int launch_coop(void (*kern)(PcgArgs), PcgArgs &a, int G, int tpb, size_t smem,
-                       cudaStream_t s) {
-  cudaLaunchConfig_t cfg;
-  memset(&cfg, 0, sizeof(cfg));
-  cfg.gridDim = dim3((unsigned)G);
-  cfg.blockDim = dim3((unsigned)tpb);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a);
+static cudaKernelNodeParams kernel_node(void (*k)(PcgArgs), int grid, void **args) {
+  cudaKernelNodeParams p;
+  memset(&p, 0, sizeof(p));
+  p.func = (void *)k;
+  p.gridDim = dim3((unsigned)std::max(grid, 1));
+  p.blockDim = dim3(PHASE_TPB);
+  p.sharedMemBytes = 0;
+  p.kernelParams = args;
+  p.extra = nullptr;
+  return p;
+}
+
+// The solve graph of handle A for one (refined, per_system) shape.
+static int build_graph(gbs_mat A, bool refined, bool per_system, cudaGraphExec_t *out) {
+  *out = nullptr;
+  const PhaseKernels K = phase_kernels(refined, A->lanes);
+  cudaGraph_t g = nullptr;
+  GBS_TRY_CUDA(cudaGraphCreate(&g, 0));
+  cudaError_t e = cudaSuccess;
+  auto fail = [&](const char *what) {
+    set_error("building the PCG graph (%s): %s", what, cudaGetErrorString(e));
+    cudaGraphDestroy(g);
+    return GBS_ERR_CUDA;
+  };
+  cudaGraphConditionalHandle h;
+  // default 1: the body runs at least once per launch; its first trip finds
+  // every system the setup already retired frozen and clears the condition
+  e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return fail("conditional handle");
+  PcgArgs a = make_args(A, per_system);
+  a.cond = h;
+  a.stepped = 0;
+  a.trip = 0;
+  void *args[] = {&a};
+
+  cudaGraphNode_t n_ctl, n_cnt, n_setup, n_loop, n_final;
+  cudaMemsetParams ms;
+  memset(&ms, 0, sizeof(ms));
+  ms.dst = A->ctl;
+  ms.value = 0;
+  ms.elementSize = 4;
+  ms.width = sizeof(DevCtl) / 4;
+  ms.height = 1;
+  e = cudaGraphAddMemsetNode(&n_ctl, g, nullptr, 0, &ms);
+  if (e != cudaSuccess) return fail("memset");
+  ms.dst = A->sys_cnt;
+  ms.width = (size_t)A->nsys;
+  e = cudaGraphAddMemsetNode(&n_cnt, g, &n_ctl, 1, &ms);
+  if (e != cudaSuccess) return fail("memset");
+  cudaKernelNodeParams kp = kernel_node(K.setup, A->ta.grid, args);
+  e = cudaGraphAddKernelNode(&n_setup, g, &n_cnt, 1, &kp);
+  if (e != cudaSuccess) return fail("setup node");
+
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};  // other members zeroed
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  e = cudaGraphAddNode(&n_loop, g, &n_setup, nullptr, 1, &cp);
+  if (e != cudaSuccess) return fail("conditional node");
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  cudaGraphNode_t n_a, n_b, n_c;
+  kp = kernel_node(K.spmv, A->ta.grid, args);
+  e = cudaGraphAddKernelNode(&n_a, body, nullptr, 0, &kp);
+  if (e != cudaSuccess) return fail("phase A node");
+  kp = kernel_node(K.update, A->te.grid, args);
+  e = cudaGraphAddKernelNode(&n_b, body, &n_a, 1, &kp);
+  if (e != cudaSuccess) return fail("phase B node");
+  kp = kernel_node(K.direction, A->te.grid, args);
+  e = cudaGraphAddKernelNode(&n_c, body, &n_b, 1, &kp);
+  if (e != cudaSuccess) return fail("phase C node");
+
+  kp = kernel_node(K.final_, A->ta.grid, args);
+  e = cudaGraphAddKernelNode(&n_final, g, &n_loop, 1, &kp);
+  if (e != cudaSuccess) return fail("final node");
+
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
   if (e != cudaSuccess) {
-    set_error("cooperative PCG launch (grid %d x %d, smem %zu): %s", G, tpb, smem,
-              cudaGetErrorString(e));
-    return e == cudaErrorCooperativeLaunchTooLarge ? GBS_ERR_LAUNCH : GBS_ERR_CUDA;
+    *out = nullptr;
+    set_error("instantiating the PCG graph: %s", cudaGetErrorString(e));
+    return GBS_ERR_CUDA;
   }
-  count_launches(1);
   return GBS_OK;
 }
 
-// Enqueue one solve: reset the control words, then the persistent launch.
-static int enqueue_solve(gbs_mat A, PcgArgs &a, bool refined, int G, cudaStream_t s) {
-  GBS_TRY_CUDA(cudaMemsetAsync(A->ctl, 0, sizeof(DevCtl), s));
-  GBS_TRY_CUDA(cudaMemsetAsync(A->sys_cnt, 0, sizeof(unsigned) * A->nsys, s));
-  return refined ? launch_coop(k_pcg<true>, a, G, A->tpb, pcg_smem(A), s)
-                 : launch_coop(k_pcg<false>, a, G, A->tpb, pcg_smem(A), s);
+constexpr int STEP_CHUNK = 16;  // host-stepped loop: trips launched between stop checks
+
+// The loop without a graph: trips are launched STEP_CHUNK at a time; each
+// trip's kernels skip their work once the previous trip has stopped the loop
+// (DevCtl::stop), and the host reads the stop flag after every chunk.  The
+// control words must be zero and the call arguments in place; setup runs
+// first, the closing kernel last.
+static int run_stepped(const PhaseKernels &K, PcgArgs a, int grid_a, int grid_e, int64_t cap,
+                       DevCtl *ctl, cudaStream_t s) {
+  a.stepped = 1;
+  a.trip = 0;
+  K.setup<<<(unsigned)grid_a, PHASE_TPB, 0, s>>>(a);
+  GBS_LAUNCHED(1);
+  for (int64_t t = 0;;) {
+    for (int k = 0; k < STEP_CHUNK; ++k, ++t) {
+      a.trip = (int32_t)(t & 1);
+      K.spmv<<<(unsigned)grid_a, PHASE_TPB, 0, s>>>(a);
+      K.update<<<(unsigned)grid_e, PHASE_TPB, 0, s>>>(a);
+      K.direction<<<(unsigned)grid_e, PHASE_TPB, 0, s>>>(a);
+      GBS_LAUNCHED(3);
+    }
+    int32_t stop = 0;  // written by the last trip launched, for the next one
+    GBS_TRY_CUDA(cudaMemcpyAsync(&stop, &ctl->stop[t & 1], sizeof(stop), cudaMemcpyDeviceToHost, s));
+    GBS_TRY_CUDA(cudaStreamSynchronize(s));
+    if (stop || t > cap) break;
+  }
+  K.final_<<<(unsigned)grid_a, PHASE_TPB, 0, s>>>(a);
+  GBS_LAUNCHED(1);
+  return GBS_OK;
 }
 
 int solve(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool per_system,
-          bool use_graph, cudaStream_t s) {
+          cudaStream_t s) {
   const bool refined = o.precision == GBS_FP32_REFINED;
   GBS_TRY(ensure_solver_workspace(A, refined));
   if (refined && !A->val32_valid) GBS_TRY(launch_to_fp32(A, s));
   A->last_count = per_system ? A->nsys : 1;
   A->last_ensemble = !per_system;
+  A->trips_counted = true;
   if (A->ta.nblocks == 0) {  // empty matrix: nothing to iterate
     GBS_TRY_CUDA(cudaMemsetAsync(A->st, 0, sizeof(SysState) * A->nsys, s));
     GBS_TRY_CUDA(cudaMemsetAsync(A->ctl, 0, sizeof(DevCtl), s));
     return GBS_OK;
   }
-  int G = 0;
-  GBS_TRY(refined ? pcg_grid<true>(A, &G) : pcg_grid<false>(A, &G));
-  if (refined) A->grid_fp32 = G; else A->grid_fp64 = G;
-  GBS_TRY(ensure_slots(A, G * A->nwarps, s));
-  PcgArgs a = make_args(A, b, x, o, per_system);
-  if (!use_graph) return enqueue_solve(A, a, refined, G, s);
-
-  // CUDA graph of (memsets + cooperative launch), re-captured when the
-  // arguments change, replayed otherwise.
-  uint64_t key[8] = {(uint64_t)(uintptr_t)b, (uint64_t)(uintptr_t)x, 0, 0, 0, 0, 0, 0};
-  memcpy(&key[2], &o.rtol, 8);
-  memcpy(&key[3], &o.inner_rtol, 8);
-  key[4] = ((uint64_t)(uint32_t)o.maxit << 32) | (uint32_t)o.inner_maxit;
-  key[5] = ((uint64_t)(uint32_t)o.max_outer << 32) | ((uint32_t)o.nonzero_guess << 1) |
-           (refined ? 1u : 0u);
-  key[6] = (uint64_t)o.timeout_ns ^ ((uint64_t)o.debug_barrier_extra << 48);
-  key[7] = ((uint64_t)G << 32) | (uint64_t)(per_system ? 1 : 0) | ((uint64_t)A->tpb << 8) |
-           ((uint64_t)A->nstages << 20) | ((uint64_t)A->Ra << 24);
-  if (!A->graph || memcmp(key, A->graph_key, sizeof(key)) != 0) {
-    if (A->graph) {
-      cudaGraphExecDestroy(A->graph);
-      A->graph = nullptr;
-    }
-    cudaStream_t cs;
-    GBS_TRY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    int st = GBS_OK;
-    if (e == cudaSuccess) {
-      st = enqueue_solve(A, a, refined, G, cs);
-      e = cudaStreamEndCapture(cs, &g);
-    }
-    if (e == cudaSuccess && st == GBS_OK) e = cudaGraphInstantiate(&A->graph, g, 0);
-    if (g) cudaGraphDestroy(g);
-    cudaStreamDestroy(cs);
-    if (st != GBS_OK) return st;
-    if (e != cudaSuccess) {
-      set_error("capturing the batched PCG graph: %s", cudaGetErrorString(e));
-      A->graph = nullptr;
-      return GBS_ERR_CUDA;
-    }
-    memcpy(A->graph_key, key, sizeof(key));
+  if (o.host_loop) {
+    GBS_TRY_CUDA(cudaMemsetAsync(A->ctl, 0, sizeof(DevCtl), s));
+    GBS_TRY_CUDA(cudaMemsetAsync(A->sys_cnt, 0, sizeof(unsigned) * A->nsys, s));
+    GBS_TRY(put_call(A->call, call_args(b, x, o), s));
+    return run_stepped(phase_kernels(refined, A->lanes), make_args(A, per_system), A->ta.grid,
+                       A->te.grid, max_trips_for(o), A->ctl, s);
   }
-  GBS_TRY_CUDA(cudaGraphLaunch(A->graph, s));
+  cudaGraphExec_t &G = A->graph[refined ? 1 : 0][per_system ? 1 : 0];
+  if (!G) GBS_TRY(build_graph(A, refined, per_system, &G));
+  GBS_TRY(put_call(A->call, call_args(b, x, o), s));
+  GBS_TRY_CUDA(cudaGraphLaunch(G, s));
+  count_launches(2);  // setup + final; the loop's kernels are counted when read
+  A->trips_counted = false;
   return GBS_OK;
 }
 
@@ -887,6 +408,10 @@ int read_results(gbs_mat A, ksp_result *res, int32_t count, cudaStream_t s) {
   GBS_TRY_CUDA(cudaMemcpyAsync(A->st_host, A->st, sizeof(SysState) * n, cudaMemcpyDeviceToHost, s));
   GBS_TRY_CUDA(cudaMemcpyAsync(&ctl, A->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, s));
   GBS_TRY_CUDA(cudaStreamSynchronize(s));
+  if (!A->trips_counted) {
+    count_launches(3 * ctl.trips);
+    A->trips_counted = true;
+  }
   int first = GBS_OK;
   for (int32_t q = 0; q < n; ++q) {
     const SysState &S = A->st_host[q];
@@ -902,34 +427,42 @@ int read_results(gbs_mat A, ksp_result *res, int32_t count, cudaStream_t s) {
     R.true_rel_residual = bn > 0.0 ? sqrt(S.tt) / bn : sqrt(S.tt);
     if (R.status != GBS_OK && first == GBS_OK) first = R.status;
   }
-  if (first == GBS_OK && ctl.err) first = ctl.err;
   if (first != GBS_OK) set_error("solve finished with status %d", first);
   return first;
+}
+
+int read_phase_ns(gbs_mat A, int64_t *phase_ns, cudaStream_t s) {
+  DevCtl c;
+  GBS_TRY_CUDA(cudaMemcpyAsync(&c, A->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, s));
+  GBS_TRY_CUDA(cudaStreamSynchronize(s));
+  for (int k = 0; k < 5; ++k) phase_ns[k] = c.phase_ns[k];
+  return GBS_OK;
 }
 
 }  // namespace gbs
 
 // ------------------------------------------------------------------ no-alloc solve
 //
-// ksp_solve_cg_noalloc: the same persistent FP64 PCG kernel, for callers that
-// must not allocate device memory -- e.g. code that works inside a fixed
-// memory budget owned by another allocator, or that cannot afford the device
+// ksp_solve_cg_noalloc: the same FP64 phase kernels, for callers that must not
+// allocate device memory -- e.g. code that works inside a fixed memory budget
+// owned by another allocator, or that cannot afford the device
 // synchronisation cudaMalloc / cudaFree imply.  Its scratch (the r, p, q and
-// D^-1 vectors, the block tables, the reduction slots and the control words)
-// lives in one file-scope __device__ array of fixed size, so the call performs
-// no allocation of any kind.  The caller passes the CSR matrix, b and x.
-// Limit: n <= NOALLOC_MAX_ROWS rows (the array holds about 8.4 MB and stays
-// resident on every GPU that loads the library until the process exits).
-// All calls share the array: calls that overlap on the GPU (other streams,
-// other host threads) race and must be serialised by the caller.  The first
-// call on a device looks the array's device address up (cudaGetSymbolAddress,
-// with that device current); make that first call before any stream capture.
+// D^-1 vectors, the block tables, the reduction slots, the control words and
+// the call arguments) lives in one file-scope __device__ array of fixed size,
+// so the call performs no allocation of any kind; it builds no CUDA graph
+// either (instantiation allocates), and steps the loop from the host.  The
+// caller passes the CSR matrix, b and x.  Limit: n <= NOALLOC_MAX_ROWS rows
+// (the array holds about 8.5 MB and stays resident on every GPU that loads the
+// library until the process exits).  All calls share the array: calls that
+// overlap on the GPU (other streams, other host threads) race and must be
+// serialised by the caller.  The first call on a device looks the array's
+// device address up (cudaGetSymbolAddress, with that device current); make
+// that first call before any stream capture.
 
 namespace {
 
 constexpr int64_t NOALLOC_MAX_ROWS = 262144;
-constexpr int NOALLOC_RA = 32, NOALLOC_RE = 256, NOALLOC_NW = 8, NOALLOC_NS = 2;
-constexpr int NOALLOC_CAP = 1024;  // staged nonzeros per 32-row block (longer: plain loads)
+constexpr int NOALLOC_RA = 256, NOALLOC_RE = 512, NOALLOC_LANES = 4;
 constexpr int64_t NOALLOC_MAX_BLK_A = NOALLOC_MAX_ROWS / NOALLOC_RA;
 constexpr int64_t NOALLOC_MAX_BLK_E = NOALLOC_MAX_ROWS / NOALLOC_RE;
 
@@ -937,11 +470,12 @@ struct NoallocScratch {
   double r[NOALLOC_MAX_ROWS], p[NOALLOC_MAX_ROWS], q[NOALLOC_MAX_ROWS],
       dinv[NOALLOC_MAX_ROWS];
   double part[(NOALLOC_MAX_BLK_A + NOALLOC_MAX_BLK_E + 8) * gbs::SLOT_STRIDE];
-  int32_t row0_a[NOALLOC_MAX_BLK_A + 4], nz0_a[NOALLOC_MAX_BLK_A + 4];
-  int32_t row0_e[NOALLOC_MAX_BLK_E + 4], nz0_e[NOALLOC_MAX_BLK_E + 4];
+  int32_t row0_a[NOALLOC_MAX_BLK_A + 4];
+  int32_t row0_e[NOALLOC_MAX_BLK_E + 4];
   unsigned sys_cnt[4];
   gbs::SysState st[1];
   gbs::DevCtl ctl;
+  gbs::CallArgs call;
 };
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoallocScratch)];
@@ -976,13 +510,11 @@ int noalloc_scratch(NoallocScratch **out) {
 }
 
 // D^-1 from the caller's CSR (0 marks a missing or non-positive diagonal) and
-// the two block tables (32-row SpMV blocks, 256-row update blocks).
+// the two block tables (256-row SpMV blocks, 512-row update blocks).
 __global__ void k_noalloc_prep(int64_t n, const int32_t *__restrict__ row_ptr,
                                const int32_t *__restrict__ col, const double *__restrict__ val,
                                double *__restrict__ dinv, int32_t *__restrict__ row0_a,
-                               int32_t *__restrict__ nz0_a, int32_t nba,
-                               int32_t *__restrict__ row0_e, int32_t *__restrict__ nz0_e,
-                               int32_t nbe) {
+                               int32_t nba, int32_t *__restrict__ row0_e, int32_t nbe) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   for (int64_t r = i0; r < n; r += stride) {
@@ -991,16 +523,10 @@ __global__ void k_noalloc_prep(int64_t n, const int32_t *__restrict__ row_ptr,
       if (col[q] == r) d = val[q];
     dinv[r] = (d > 0.0) ? 1.0 / d : 0.0;
   }
-  for (int64_t b = i0; b <= nba; b += stride) {
-    const int64_t r = b * NOALLOC_RA < n ? b * NOALLOC_RA : n;
-    row0_a[b] = (int32_t)r;
-    nz0_a[b] = row_ptr[r];
-  }
-  for (int64_t b = i0; b <= nbe; b += stride) {
-    const int64_t r = b * NOALLOC_RE < n ? b * NOALLOC_RE : n;
-    row0_e[b] = (int32_t)r;
-    nz0_e[b] = row_ptr[r];
-  }
+  for (int64_t b = i0; b <= nba; b += stride)
+    row0_a[b] = (int32_t)(b * NOALLOC_RA < n ? b * NOALLOC_RA : n);
+  for (int64_t b = i0; b <= nbe; b += stride)
+    row0_e[b] = (int32_t)(b * NOALLOC_RE < n ? b * NOALLOC_RE : n);
 }
 
 }  // namespace
@@ -1030,12 +556,11 @@ extern "C" int ksp_solve_cg_noalloc(int64_t n, const int32_t *row_ptr, const int
     set_error("ksp_solve_cg_noalloc: only GBS_FP64 is supported");
     return GBS_ERR_ARG;
   }
-  if (!(oo.rtol >= 0.0) || oo.debug_barrier_extra < 0) {
+  if (!(oo.rtol >= 0.0)) {
     set_error("ksp_solve_cg_noalloc: invalid options");
     return GBS_ERR_ARG;
   }
   if (oo.maxit < 0) oo.maxit = (int32_t)std::min<int64_t>(10 * std::max<int64_t>(n, 1), 100000);
-  if (oo.timeout_ns <= 0) oo.timeout_ns = 2000000000LL;
   if (n == 0) {
     if (res) memset(res, 0, sizeof(*res));
     return GBS_OK;
@@ -1045,47 +570,27 @@ extern "C" int ksp_solve_cg_noalloc(int64_t n, const int32_t *row_ptr, const int
   GBS_TRY(noalloc_scratch(&S));
   const int32_t nba = (int32_t)((n + NOALLOC_RA - 1) / NOALLOC_RA);
   const int32_t nbe = (int32_t)((n + NOALLOC_RE - 1) / NOALLOC_RE);
-  const int64_t sb = std::max((spmv_stage_bytes(NOALLOC_CAP, NOALLOC_RA) + 15) & ~15LL,
-                              (upd_stage_bytes(NOALLOC_RE) + 15) & ~15LL);
-  const size_t smem = pcg_smem_for(NOALLOC_NW, NOALLOC_NS, sb);
-  int per_sm = 0, nsm = 0, dev = 0;
-  GBS_TRY_CUDA(cudaGetDevice(&dev));
-  GBS_TRY(raise_smem_limit<false>(smem));
-  GBS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<false>,
-                                                             32 * NOALLOC_NW, smem));
-  GBS_TRY_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  if (per_sm < 1) {
-    set_error("ksp_solve_cg_noalloc: persistent kernel does not fit on an SM");
-    return GBS_ERR_LAUNCH;
-  }
-  const int G = (int)std::max<int64_t>(
-      1, std::min<int64_t>((int64_t)per_sm * nsm, (nba + NOALLOC_NW - 1) / NOALLOC_NW));
 
   // the control words and arrival counters must start at zero on every call
   GBS_TRY_CUDA(cudaMemsetAsync(&S->ctl, 0, sizeof(DevCtl), s));
   GBS_TRY_CUDA(cudaMemsetAsync(S->sys_cnt, 0, sizeof(S->sys_cnt), s));
   k_noalloc_prep<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(
-      n, row_ptr, col, val, S->dinv, S->row0_a, S->nz0_a, nba, S->row0_e, S->nz0_e, nbe);
+      n, row_ptr, col, val, S->dinv, S->row0_a, nba, S->row0_e, nbe);
   GBS_LAUNCHED(1);
+  GBS_TRY(put_call(&S->call, call_args(b, x, oo), s));
 
+  // one CTA per block: each table has as many slots as blocks
   PcgArgs a;
   memset(&a, 0, sizeof(a));
   a.nsys = 1;
   a.ensemble = 1;
-  a.ta = BlockTable{nba, S->row0_a, S->nz0_a, nullptr, nullptr, nullptr};
-  a.te = BlockTable{nbe, S->row0_e, S->nz0_e, nullptr, nullptr, nullptr};
-  a.cap = NOALLOC_CAP;
-  a.Ra = NOALLOC_RA;
-  a.Re = NOALLOC_RE;
-  a.ns = NOALLOC_NS;
-  a.stage_bytes = sb;
-  a.part_e = nba + 1;
+  a.ta = BlockTable{nba, S->row0_a, nullptr, nullptr, nullptr, nullptr};
+  a.te = BlockTable{nbe, S->row0_e, nullptr, nullptr, nullptr, nullptr};
+  a.part_e = nba;
   a.row_ptr = row_ptr;
   a.col = col;
   a.val = val;
   a.dinv = S->dinv;
-  a.b = b;
-  a.x = x;
   a.r = S->r;
   a.p = S->p;
   a.q = S->q;
@@ -1093,8 +598,9 @@ extern "C" int ksp_solve_cg_noalloc(int64_t n, const int32_t *row_ptr, const int
   a.sys_cnt = S->sys_cnt;
   a.st = S->st;
   a.ctl = &S->ctl;
-  fill_common(a, oo);
-  GBS_TRY(launch_coop(k_pcg<false>, a, G, 32 * NOALLOC_NW, smem, s));
+  a.call = &S->call;
+  GBS_TRY(run_stepped(phase_kernels(false, NOALLOC_LANES), a, nba, nbe, max_trips_for(oo),
+                      &S->ctl, s));
   if (!res) return GBS_OK;
 
   SysState st;
@@ -1110,6 +616,7 @@ extern "C" int ksp_solve_cg_noalloc(int64_t n, const int32_t *row_ptr, const int
   res->rnorm = st.rnorm;
   const double bn = sqrt(st.bb);
   res->true_rel_residual = bn > 0.0 ? sqrt(st.tt) / bn : sqrt(st.tt);
-  if (res->status != GBS_OK) set_error("ksp_solve_cg_noalloc: solve ended with status %d", res->status);
+  if (res->status != GBS_OK)
+    set_error("ksp_solve_cg_noalloc: solve ended with status %d", res->status);
   return res->status;
 }

@@ -1,0 +1,735 @@
+// Phase bodies of the Jacobi-PCG solve (Sec. 6.1 CG with device-resident
+// scalars and no host round trip; Sec. 7 diagonal preconditioning and batched
+// systems; Sec. 2 A7 FP32 inner solve under FP64 refinement).
+//
+// Each phase is one kernel launch; the iterations run inside a CUDA graph
+// whose conditional WHILE node repeats the body (A, B, C) until the device
+// clears its condition.  A CTA walks blocks c, c+G, c+2G, ... of the phase's
+// block table (rows of one system per block).  Per iteration:
+//   A: q = A p fused with the partial p.q
+//   B: x += alpha p, r -= alpha q, z = D^-1 r (stored over q), r.z and r.r
+//   C: p = z + beta p, and the loop condition
+// GB300 issues FP64 FMAs at about the rate HBM delivers nonzeros, so the row
+// products spend one FMA per stored nonzero and as few other FP64
+// instructions as possible (see csr_rows).
+//
+// Reductions are deterministic: a CTA reduces its rows of a system in a fixed
+// tree and writes one slot per (system, CTA); the CTA whose slot arrives last
+// (atomic arrival counter per system) sums the system's slots in slot order
+// and updates that system's scalars (alpha, beta, norms, status) in device
+// memory, where the next phase reads them.  Converged systems are frozen
+// (their blocks are skipped).
+//
+// Refined mode (per-system state machine, M_* modes): an FP32 PCG on FP32
+// copies of A and D^-1 with FP32 vectors and FP32 reductions solves
+// A d = r / ||r||; between inner solves the same A/B/C phases run the FP64
+// outer step: x += s d (phase C), r = b - A x and ||r|| (phase A), and the
+// inner restart r32 = RN(r / s), d = 0 (phase B).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "device_util.cuh"
+#include "internal.cuh"
+
+namespace gbs {
+
+enum { M_INNER = 0, M_XUPD = 1, M_START = 2 };
+constexpr int SLOT_STRIDE = 4;  // doubles per reduction slot
+constexpr int PHASE_TPB = 256;  // threads per CTA of every phase kernel
+constexpr int SELL_MIN_CTAS = 8;  // sliced-ELL kernels: 8 CTAs (2048 threads) per SM
+
+// A table of work blocks: rows [row0[b], row0[b+1]) of system sys[b].
+struct BlockTable {
+  int32_t nblocks;
+  const int32_t *row0;       // nblocks + 1
+  const int32_t *sys;        // nblocks
+  const int32_t *sys_blk0;   // nsys + 1
+  const int32_t *sys_slot0;  // nsys + 1: reduction slot offsets for this table's grid
+  const int32_t *slice0;     // nblocks + 1: first 32-row slice of each block
+};
+
+struct PcgArgs {
+  int32_t nsys, ensemble;
+  BlockTable ta, te;  // SpMV blocks, update blocks
+  int64_t part_e;     // first reduction slot of table te
+  const int32_t *row_ptr, *col;
+  const double *val;
+  const float *val32;
+  const int32_t *sptr;   // sliced-ELL copy (kernels with L == 0)
+  const int32_t *srow0, *scol;
+  const double *sval;
+  const float *sval32;
+  const double *dinv;
+  const float *dinv32;
+  double *r, *p, *q;
+  float *r32, *p32, *q32, *d32;
+  double *part;
+  unsigned *sys_cnt;
+  SysState *st;
+  DevCtl *ctl;
+  const CallArgs *call;
+  cudaGraphConditionalHandle cond;  // loop condition of the graph (stepped == 0)
+  int32_t stepped;                  // 1: loop trips launched by the host
+  int32_t trip;                     // stepped: index of this trip
+};
+
+__device__ __forceinline__ int sys_of(const PcgArgs &a, const BlockTable &t, int b) {
+  return a.ensemble ? 0 : __ldg(t.sys + b);
+}
+__device__ __forceinline__ int sys_b0(const PcgArgs &a, const BlockTable &t, int s) {
+  return a.ensemble ? 0 : __ldg(t.sys_blk0 + s);
+}
+__device__ __forceinline__ int sys_nblk(const PcgArgs &a, const BlockTable &t, int s) {
+  return a.ensemble ? t.nblocks : __ldg(t.sys_blk0 + s + 1) - __ldg(t.sys_blk0 + s);
+}
+__device__ __forceinline__ int64_t sys_slot0(const PcgArgs &a, const BlockTable &t, int s) {
+  return a.ensemble ? 0 : (int64_t)__ldg(t.sys_slot0 + s);
+}
+
+__device__ __forceinline__ void deactivate(const PcgArgs &a, SysState &S, int status) {
+  S.status = status;
+  S.active = 0;
+  atomicSub(&a.ctl->n_active, 1);
+}
+
+// Host-stepped loop: trip a.trip runs unless the previous trip stopped it.
+__device__ __forceinline__ bool trip_live(const PcgArgs &a) {
+  return !a.stepped || ldcg(&a.ctl->stop[a.trip & 1]) == 0;
+}
+
+// CTA 0 books the time since the previous phase kernel started to that
+// phase and marks the start of phase k (kernels of one solve run in order).
+__device__ __forceinline__ void stamp_phase(const PcgArgs &a, int k) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    DevCtl *c = a.ctl;
+    const int64_t t = (int64_t)global_ns();
+    c->phase_ns[c->last_phase] += t - c->stamp;
+    c->stamp = t;
+    c->last_phase = k;
+  }
+}
+
+// Reduce the CTA's NV partials over its run on system s (last block b of a
+// table processed by G CTAs) into the system's slot; the last arriving CTA
+// sums all slots in slot order and calls fin(s, totals) on thread 0.
+// f32: FP32 accumulation throughout.
+template <int NV, class Fin>
+__device__ __forceinline__ void flush(const PcgArgs &a, const BlockTable &t, int64_t part_off,
+                                      int s, int b, double (&acc)[NV], double *red, bool f32,
+                                      Fin &fin) {
+  __shared__ int s_last;
+  const int G = gridDim.x;
+  if (f32) {
+    float v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = (float)acc[k];
+    block_reduce<float, NV>(v, reinterpret_cast<float *>(red));
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = (double)v[k];
+  } else {
+    block_reduce<double, NV>(acc, red);
+  }
+  const int b0 = sys_b0(a, t, s), nb = sys_nblk(a, t, s);
+  const int ns = min(nb, G);
+  const int slot = (b - b0) % G;
+  const int64_t base = part_off + sys_slot0(a, t, s);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) a.part[(base + slot) * SLOT_STRIDE + k] = acc[k];
+    __threadfence();
+    const unsigned prev = atomicAdd(a.sys_cnt + s, 1u);
+    s_last = (prev == (unsigned)(ns - 1)) ? 1 : 0;
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    if (f32) {
+      float tot[NV];
+#pragma unroll
+      for (int k = 0; k < NV; ++k) tot[k] = 0.f;
+      for (int i = threadIdx.x; i < ns; i += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) tot[k] += (float)ldcg(a.part + (base + i) * SLOT_STRIDE + k);
+      block_reduce<float, NV>(tot, reinterpret_cast<float *>(red));
+      if (threadIdx.x == 0) {
+        double d[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) d[k] = (double)tot[k];
+        a.sys_cnt[s] = 0u;
+        fin(s, d);
+        __threadfence();
+      }
+    } else {
+      double tot[NV];
+#pragma unroll
+      for (int k = 0; k < NV; ++k) tot[k] = 0.0;
+      for (int i = threadIdx.x; i < ns; i += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) tot[k] += ldcg(a.part + (base + i) * SLOT_STRIDE + k);
+      block_reduce<double, NV>(tot, red);
+      if (threadIdx.x == 0) {
+        a.sys_cnt[s] = 0u;
+        fin(s, tot);
+        __threadfence();
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// The CTA's pass over its blocks of table t (b = blockIdx.x, + G, ...).
+// want(s) -> 0 skip / 1 FP64 / 2 FP32 reduction (uniform for a system, and
+// unchanged until the system's fin runs); work(s, b, r0, r1, acc) processes
+// block b, rows [r0, r1).  A CTA meets each system in one run of consecutive visits, so it
+// flushes once per system it touches (NV == 0: no reduction).
+template <int NV, class Want, class Work, class Fin>
+__device__ __forceinline__ void walk(const PcgArgs &a, const BlockTable &t, int64_t part_off,
+                                     double *red, Want &want, Work &work, Fin &fin) {
+  constexpr int NA = NV > 0 ? NV : 1;
+  const int G = gridDim.x;
+  int cur_s = -1, cur_b = -1, kind = 0;
+  double acc[NA];
+#pragma unroll
+  for (int k = 0; k < NA; ++k) acc[k] = 0.0;
+  for (int b = blockIdx.x; b < t.nblocks; b += G) {
+    const int s = sys_of(a, t, b);
+    if (s != cur_s) {
+      if constexpr (NV > 0) {
+        if (kind) flush<NV>(a, t, part_off, cur_s, cur_b, acc, red, kind == 2, fin);
+      }
+      cur_s = s;
+      kind = want(s);
+#pragma unroll
+      for (int k = 0; k < NA; ++k) acc[k] = 0.0;
+    }
+    if (!kind) continue;
+    cur_b = b;
+    work(s, b, __ldg(t.row0 + b), __ldg(t.row0 + b + 1), acc);
+  }
+  if constexpr (NV > 0) {
+    if (kind) flush<NV>(a, t, part_off, cur_s, cur_b, acc, red, kind == 2, fin);
+  }
+}
+
+// Combine the L row partials of each lane of an L-lane group so that lane li
+// ends with the full sum of row li: at distance d each lane keeps half of its
+// rows, sends the other half to lane li ^ d and adds what it receives -- L-1
+// adds per lane, against L log2(L) for one butterfly per row.  Fixed order.
+template <typename T, int L>
+__device__ __forceinline__ T transpose_reduce(T (&acc)[L], int li) {
+#pragma unroll
+  for (int d = L / 2; d >= 1; d >>= 1) {
+    const bool hi = (li & d) != 0;
+#pragma unroll
+    for (int i = 0; i < d; ++i) {
+      const T send = hi ? acc[i] : acc[i + d];
+      const T keep = hi ? acc[i + d] : acc[i];
+      acc[i] = keep + __shfl_xor_sync(FULL_MASK, send, d);
+    }
+  }
+  return acc[0];
+}
+
+// Row products of rows [r0, r1): f(r, sum_k a_rk x_k) for each row, every
+// product one FMA.  L < 32: each warp takes 32 consecutive rows per pass; a
+// group of L lanes owns L of them, lane li walks entries li, li+L, ... of all
+// L rows (the trip count is the warp's longest row over L, the same for every
+// lane), and transpose_reduce leaves row base+lane in lane `lane`, so f runs
+// on every lane with coalesced row indices.  L == 32: one row per warp, xor
+// butterfly, f on lane 0.  All lanes reach the shuffles.
+template <typename T, int L, class F>
+__device__ __forceinline__ void csr_rows(const int32_t *__restrict__ row_ptr,
+                                         const int32_t *__restrict__ col,
+                                         const T *__restrict__ val, const T *__restrict__ x,
+                                         int r0, int r1, F &f) {
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if constexpr (L == 32) {
+    for (int r = r0 + warp; r < r1; r += nw) {
+      const int s = __ldg(row_ptr + r), e = __ldg(row_ptr + r + 1);
+      T acc = T(0);
+      for (int q = s + lane; q < e; q += 32)
+        acc = fma_rn(__ldg(val + q), __ldg(x + __ldg(col + q)), acc);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, off);
+      if (lane == 0) f(r, acc);
+    }
+  } else {
+    const int li = lane & (L - 1), g0 = lane - li;
+    for (int base = r0 + warp * 32; base < r1; base += nw * 32) {
+      const int my = base + lane;
+      int s = 0, e = 0;
+      if (my < r1) {
+        s = __ldg(row_ptr + my);
+        e = __ldg(row_ptr + my + 1);
+      }
+      const int mxw = (int)__reduce_max_sync(FULL_MASK, (unsigned)(e - s));
+      int rs[L], len[L];
+#pragma unroll
+      for (int u = 0; u < L; ++u) {
+        rs[u] = __shfl_sync(FULL_MASK, s, g0 + u);
+        len[u] = __shfl_sync(FULL_MASK, e - s, g0 + u);
+      }
+      T acc[L];
+#pragma unroll
+      for (int u = 0; u < L; ++u) acc[u] = T(0);
+      for (int t = 0; t < mxw; t += L) {
+        const int k = t + li;
+        int c[L];
+        T v[L];
+#pragma unroll
+        for (int u = 0; u < L; ++u) {
+          const bool ok = k < len[u];
+          c[u] = ok ? __ldg(col + rs[u] + k) : -1;
+          v[u] = ok ? __ldg(val + rs[u] + k) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < L; ++u)
+          if (c[u] >= 0) acc[u] = fma_rn(v[u], __ldg(x + c[u]), acc[u]);
+      }
+      const T sum = transpose_reduce<T, L>(acc, li);
+      if (my < r1) f(my, sum);
+    }
+  }
+}
+
+// Element-wise rows [r0, r1) of a vector-update phase, thread by thread.  The
+// loads of two rows are issued before either row's stores (the vectors are
+// separate arrays, but the compiler cannot know they do not alias), so each
+// thread keeps two rows of loads in flight.
+template <class Load, class Apply>
+__device__ __forceinline__ void rows2(int r0, int r1, Load &load, Apply &apply) {
+  const int T = blockDim.x;
+  int r = r0 + threadIdx.x;
+  for (; r + T < r1; r += 2 * T) {
+    const auto u = load(r);
+    const auto w = load(r + T);
+    apply(r, u);
+    apply(r + T, w);
+  }
+  if (r < r1) apply(r, load(r));
+}
+
+template <typename T, int N>
+struct Vals {
+  T v[N];
+};
+
+// Row products of the 32-row slices [s0, s1) of the sliced-ELL copy: warp w
+// takes slices s0 + w, s0 + w + nw, ...; lane i sums row i of the slice in
+// CSR order, one FMA per stored nonzero, two entries' loads in flight per
+// step; padding (column -1) is skipped.  Entry offsets are 32-bit (the copy
+// holds fewer than 2^31 entries) and a slice's entries for lane i are
+// sptr[s] + i, + 32, ..., so the trip count is the same for every lane.
+// f(r, sum) runs on every lane whose row exists.
+template <typename T, class F>
+__device__ __forceinline__ void sell_rows(const int32_t *__restrict__ sptr,
+                                          const int32_t *__restrict__ srow0,
+                                          const int32_t *__restrict__ scol,
+                                          const T *__restrict__ sval, const T *__restrict__ x,
+                                          int s0, int s1, F &f) {
+  const int lane = threadIdx.x & 31;
+  for (int sl = s0 + (int)(threadIdx.x >> 5); sl < s1; sl += (int)(blockDim.x >> 5)) {
+    int q = __ldg(sptr + sl) + lane;
+    const int qe = __ldg(sptr + sl + 1);
+    T acc = T(0);
+    for (; q + 32 < qe; q += 64) {
+      const int c0 = __ldg(scol + q), c1 = __ldg(scol + q + 32);
+      const T v0 = __ldg(sval + q), v1 = __ldg(sval + q + 32);
+      if (c0 >= 0) acc = fma_rn(v0, __ldg(x + c0), acc);
+      if (c1 >= 0) acc = fma_rn(v1, __ldg(x + c1), acc);
+    }
+    if (q < qe) {
+      const int c0 = __ldg(scol + q);
+      if (c0 >= 0) acc = fma_rn(__ldg(sval + q), __ldg(x + c0), acc);
+    }
+    const int r = __ldg(srow0 + sl) + lane;
+    if (r < __ldg(srow0 + sl + 1)) f(r, acc);
+  }
+}
+
+// The row products of block b (rows [r0, r1) of table ta) with the plan's
+// kernel: L == 0 sliced ELL, else CSR-vector with L lanes per row.
+template <typename T, int L, class F>
+__device__ __forceinline__ void row_products(const PcgArgs &a, int b, int r0, int r1,
+                                             const T *csr_val, const T *sell_val, const T *x,
+                                             F &f) {
+  if constexpr (L == 0)
+    sell_rows<T>(a.sptr, a.srow0, a.scol, sell_val, x, __ldg(a.ta.slice0 + b),
+                 __ldg(a.ta.slice0 + b + 1), f);
+  else
+    csr_rows<T, L>(a.row_ptr, a.col, csr_val, x, r0, r1, f);
+}
+
+// Per-system scalars a phase needs, read once per system run.
+struct SysView {
+  double alpha, beta, scale;
+  int mode, first, zero;
+};
+__device__ __forceinline__ SysView view_sys(const PcgArgs &a, int s) {
+  const SysState *S = a.st + s;
+  return SysView{ldcg(&S->alpha), ldcg(&S->beta), ldcg(&S->scale),
+                 ldcg(&S->mode),  ldcg(&S->first), ldcg(&S->zero_x)};
+}
+__device__ __forceinline__ bool sys_active(const PcgArgs &a, int s) {
+  return ldcg(&a.st[s].active) != 0;
+}
+
+// ------------------------------------------------------------------ setup
+// r = b - A x0 (x0 = 0 unless nonzero_guess), z = D^-1 r, p = z (FP64 mode),
+// partials r.z, r.r, b.b and the count of missing diagonals; fin initialises
+// each system's state and its status.  Runs on table ta.
+template <bool REFINED, int L>
+__device__ __forceinline__ void phase_setup(const PcgArgs &a, double *red) {
+  const CallArgs &C = *a.call;
+  const double *b = C.b;
+  double *x = C.x;
+  const bool guess = C.nonzero_guess != 0;
+  auto want = [&](int) -> int { return 1; };
+  auto row = [&](int r, double t, double(&acc)[4]) {
+    const double bv = b[r];
+    const double rv = bv - t;
+    const double dv = a.dinv[r];
+    if (REFINED) {
+      a.r[r] = rv;
+      acc[0] = fma(rv, rv, acc[0]);
+    } else {
+      const double z = dv * rv;
+      a.r[r] = rv;
+      a.p[r] = z;
+      acc[0] = fma(rv, z, acc[0]);
+      acc[1] = fma(rv, rv, acc[1]);
+    }
+    acc[2] = fma(bv, bv, acc[2]);
+    acc[3] += (dv == 0.0) ? 1.0 : 0.0;
+  };
+  auto work = [&](int, int blk, int r0, int r1, double(&acc)[4]) {
+    if (guess) {
+      auto f = [&](int r, double t) { row(r, t, acc); };
+      row_products<double, L>(a, blk, r0, r1, a.val, a.sval, x, f);
+    } else {
+      for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        x[r] = 0.0;
+        row(r, 0.0, acc);
+      }
+    }
+  };
+  auto fin = [&](int s, double(&tot)[4]) {
+    SysState &S = a.st[s];
+    const double bb = tot[2], nbad = tot[3];
+    const double rr = REFINED ? tot[0] : tot[1];
+    const double rho = REFINED ? 0.0 : tot[0];
+    memset(&S, 0, sizeof(SysState));
+    S.bb = bb;
+    S.rho = rho;
+    S.rr = rr;
+    S.rnorm0 = S.rnorm = sqrt(rr);
+    int status = -1;
+    if (nbad > 0.0) status = GBS_ERR_NOT_SPD;
+    else if (!isfinite(bb)) status = GBS_ERR_NAN;
+    else if (bb == 0.0) {
+      status = GBS_OK;
+      S.zero_x = 1;
+      S.rnorm0 = S.rnorm = 0.0;
+    } else if (!isfinite(rr) || !isfinite(rho)) status = GBS_ERR_NAN;
+    else if (sqrt(rr) <= C.rtol * sqrt(bb)) status = GBS_OK;
+    else if (REFINED ? (C.max_outer <= 0) : (C.maxit <= 0)) status = GBS_ERR_MAXIT;
+    if (status >= 0) {
+      S.status = status;
+      S.active = 0;
+    } else {
+      S.status = GBS_OK;
+      S.active = 1;
+      if (REFINED) {
+        S.prev_rn = S.rnorm;
+        S.scale = S.rnorm;
+        S.mode = M_START;
+      }
+      atomicAdd(&a.ctl->n_active, 1);
+    }
+  };
+  walk<4>(a, a.ta, 0, red, want, work, fin);
+}
+
+// ------------------------------------------------------------------ phase A
+// FP64: q = A p, p.q -> alpha.  Refined: the FP32 inner product q32 = A32 p32
+// and p32.q32 (M_INNER), or the FP64 outer residual r = b - A x and ||r||
+// with the refinement tests (M_XUPD).
+template <bool REFINED, int L>
+__device__ __forceinline__ void phase_A(const PcgArgs &a, double *red) {
+  const CallArgs &C = *a.call;
+  auto fin = [&](int s, double(&tot)[1]) {
+    SysState &S = a.st[s];
+    if (!REFINED) {
+      const double sigma = tot[0];
+      S.iterations += 1;
+      if (isnan(sigma)) deactivate(a, S, GBS_ERR_NAN);
+      else if (!(sigma > 0.0)) deactivate(a, S, GBS_ERR_BREAKDOWN);
+      else S.alpha = S.rho / sigma;
+    } else if (S.mode == M_INNER) {
+      const float sigma = (float)tot[0];
+      S.first = 0;
+      if (!(sigma > 0.0f)) {
+        if (S.inner_it == 0) deactivate(a, S, GBS_ERR_BREAKDOWN);
+        else {
+          S.mode = M_XUPD;
+          S.outer += 1;
+        }
+      } else {
+        S.alpha = (double)((float)S.rho / sigma);
+        S.inner_it += 1;
+        S.iterations += 1;
+      }
+    } else {  // outer residual
+      const double rn = sqrt(tot[0]);
+      S.rnorm = rn;
+      if (!isfinite(rn)) deactivate(a, S, GBS_ERR_NAN);
+      else if (rn <= C.rtol * sqrt(S.bb)) deactivate(a, S, GBS_OK);
+      else if (S.outer >= C.max_outer) deactivate(a, S, GBS_ERR_MAXIT);
+      else {
+        S.stall = (rn > 0.5 * S.prev_rn) ? S.stall + 1 : 0;
+        if (S.stall >= 2) deactivate(a, S, GBS_ERR_STAGNATION);
+        else {
+          S.prev_rn = rn;
+          S.scale = rn;
+          S.mode = M_START;
+        }
+      }
+    }
+  };
+  int mode = M_INNER;
+  auto want = [&](int s) -> int {
+    if (!sys_active(a, s)) return 0;
+    if (!REFINED) return 1;
+    mode = ldcg(&a.st[s].mode);
+    return mode == M_INNER ? 2 : (mode == M_XUPD ? 1 : 0);
+  };
+  auto work = [&](int, int blk, int r0, int r1, double(&acc)[1]) {
+    if (!REFINED) {
+      double pq = acc[0];
+      auto f = [&](int r, double qv) {
+        a.q[r] = qv;
+        pq = fma(__ldg(a.p + r), qv, pq);
+      };
+      row_products<double, L>(a, blk, r0, r1, a.val, a.sval, a.p, f);
+      acc[0] = pq;
+    } else if (mode == M_INNER) {
+      float pq = 0.0f;
+      auto f = [&](int r, float qv) {
+        a.q32[r] = qv;
+        pq = fmaf(__ldg(a.p32 + r), qv, pq);
+      };
+      row_products<float, L>(a, blk, r0, r1, a.val32, a.sval32, a.p32, f);
+      acc[0] = (double)((float)acc[0] + pq);
+    } else {  // FP64 outer residual
+      const double *b = C.b;
+      double rr = acc[0];
+      auto f = [&](int r, double t) {
+        const double rv = b[r] - t;
+        a.r[r] = rv;
+        rr = fma(rv, rv, rr);
+      };
+      row_products<double, L>(a, blk, r0, r1, a.val, a.sval, C.x, f);
+      acc[0] = rr;
+    }
+  };
+  walk<1>(a, a.ta, 0, red, want, work, fin);
+}
+
+// ------------------------------------------------------------------ phase B
+template <bool REFINED>
+__device__ __forceinline__ void phase_B(const PcgArgs &a, double *red) {
+  const CallArgs &C = *a.call;
+  double *x = C.x;
+  auto fin = [&](int s, double(&tot)[2]) {
+    SysState &S = a.st[s];
+    if (!REFINED) {
+      const double rho_new = tot[0], rr = tot[1];
+      const double rn = sqrt(rr);
+      S.rr = rr;
+      S.rnorm = rn;
+      if (!isfinite(rn) || !isfinite(rho_new)) deactivate(a, S, GBS_ERR_NAN);
+      else if (rn <= C.rtol * sqrt(S.bb)) deactivate(a, S, GBS_OK);
+      else if (S.iterations >= C.maxit) deactivate(a, S, GBS_ERR_MAXIT);
+      else {
+        S.beta = rho_new / S.rho;
+        S.rho = rho_new;
+      }
+    } else if (S.mode == M_START) {
+      const float rho = (float)tot[0], rr = (float)tot[1];
+      const float r0 = sqrtf(rr);
+      S.rho = rho;
+      S.rr = rr;
+      S.r0in = r0;
+      S.inner_it = 0;
+      if (!((double)r0 > C.inner_rtol * (double)r0) || C.inner_maxit <= 0)
+        deactivate(a, S, GBS_ERR_BREAKDOWN);
+      else {
+        S.mode = M_INNER;
+        S.first = 1;
+      }
+    } else {  // M_INNER
+      const float rho_new = (float)tot[0], rr = (float)tot[1];
+      const float beta = rho_new / (float)S.rho;
+      S.rho = rho_new;
+      S.rr = rr;
+      if (!((double)sqrtf(rr) > C.inner_rtol * S.r0in) || S.inner_it >= C.inner_maxit) {
+        S.mode = M_XUPD;
+        S.outer += 1;
+      } else {
+        S.beta = beta;
+      }
+    }
+  };
+  SysView v{};
+  auto want = [&](int s) -> int {
+    if (!sys_active(a, s)) return 0;
+    v = view_sys(a, s);
+    if (!REFINED) return 1;
+    return (v.mode == M_INNER || v.mode == M_START) ? 2 : 0;
+  };
+  auto work = [&](int, int, int r0, int r1, double(&acc)[2]) {
+    if (!REFINED) {
+      const double al = v.alpha;
+      double a0 = acc[0], a1 = acc[1];
+      auto load = [&](int r) {
+        return Vals<double, 5>{{a.p[r], a.q[r], x[r], a.r[r], a.dinv[r]}};
+      };
+      auto apply = [&](int r, const Vals<double, 5> &u) {
+        const double rv = fma(-al, u.v[1], u.v[3]);
+        const double z = u.v[4] * rv;
+        x[r] = fma(al, u.v[0], u.v[2]);
+        a.r[r] = rv;
+        a.q[r] = z;
+        a0 = fma(rv, z, a0);
+        a1 = fma(rv, rv, a1);
+      };
+      rows2(r0, r1, load, apply);
+      acc[0] = a0;
+      acc[1] = a1;
+    } else if (v.mode == M_INNER) {
+      const float al = (float)v.alpha;
+      float a0 = (float)acc[0], a1 = (float)acc[1];
+      auto load = [&](int r) {
+        return Vals<float, 5>{{a.p32[r], a.q32[r], a.d32[r], a.r32[r], a.dinv32[r]}};
+      };
+      auto apply = [&](int r, const Vals<float, 5> &u) {
+        const float rv = fmaf(-al, u.v[1], u.v[3]);
+        const float z = u.v[4] * rv;
+        a.d32[r] = fmaf(al, u.v[0], u.v[2]);
+        a.r32[r] = rv;
+        a.q32[r] = z;
+        a0 = fmaf(rv, z, a0);
+        a1 = fmaf(rv, rv, a1);
+      };
+      rows2(r0, r1, load, apply);
+      acc[0] = (double)a0;
+      acc[1] = (double)a1;
+    } else {  // M_START: inner restart on the scaled FP64 residual
+      float a0 = (float)acc[0], a1 = (float)acc[1];
+      for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        const float rv = __double2float_rn(a.r[r] / v.scale);
+        const float z = a.dinv32[r] * rv;
+        a.r32[r] = rv;
+        a.d32[r] = 0.0f;
+        a.q32[r] = z;
+        a0 = fmaf(rv, z, a0);
+        a1 = fmaf(rv, rv, a1);
+      }
+      acc[0] = (double)a0;
+      acc[1] = (double)a1;
+    }
+  };
+  walk<2>(a, a.te, a.part_e, red, want, work, fin);
+}
+
+// ------------------------------------------------------------------ phase C
+// FP64: p = z + beta p.  Refined: p32 = z32 (+ beta p32) (M_INNER) or the
+// refinement step x += s d (M_XUPD).
+template <bool REFINED>
+__device__ __forceinline__ void phase_C(const PcgArgs &a, double *red) {
+  const CallArgs &C = *a.call;
+  double *x = C.x;
+  auto fin = [&](int, double(&)[1]) {};
+  SysView v{};
+  auto want = [&](int s) -> int {
+    if (!sys_active(a, s)) return 0;
+    v = view_sys(a, s);
+    if (!REFINED) return 1;
+    return (v.mode == M_INNER || v.mode == M_XUPD) ? 1 : 0;
+  };
+  auto work = [&](int, int, int r0, int r1, double(&)[1]) {
+    if (!REFINED) {
+      const double be = v.beta;
+      auto load = [&](int r) { return Vals<double, 2>{{a.p[r], a.q[r]}}; };
+      auto apply = [&](int r, const Vals<double, 2> &u) { a.p[r] = fma(be, u.v[0], u.v[1]); };
+      rows2(r0, r1, load, apply);
+    } else if (v.mode == M_INNER) {
+      const float be = v.first ? 0.0f : (float)v.beta;  // first step: p = z
+      auto load = [&](int r) { return Vals<float, 2>{{a.p32[r], a.q32[r]}}; };
+      auto apply = [&](int r, const Vals<float, 2> &u) {
+        a.p32[r] = v.first ? u.v[1] : fmaf(be, u.v[0], u.v[1]);
+      };
+      rows2(r0, r1, load, apply);
+    } else {  // M_XUPD: x += s d
+      for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x)
+        x[r] = fma(v.scale, (double)a.d32[r], x[r]);
+    }
+  };
+  walk<0>(a, a.te, a.part_e, red, want, work, fin);
+}
+
+// CTA 0 of phase C: count the trip and set the loop condition.  Every phase
+// that can retire a system (setup, A, B) has completed, so n_active is final
+// for this trip.  The trip cap and the wall-clock limit end the loop with the
+// remaining systems still active (reported as GBS_ERR_MAXIT / TIMEOUT).  A
+// trip that did not run (host-stepped loop) passes the stop on.
+__device__ __forceinline__ void loop_control(const PcgArgs &a, bool live) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  const CallArgs &C = *a.call;
+  DevCtl *c = a.ctl;
+  int go = 0;
+  if (live) {
+    const int64_t trips = c->trips + 1;
+    c->trips = trips;
+    go = (ldcg(&c->n_active) > 0 && trips < C.max_trips) ? 1 : 0;
+    if (go && C.timeout_ns > 0 && (int64_t)global_ns() - c->t_start > C.timeout_ns) {
+      c->err = GBS_ERR_TIMEOUT;
+      go = 0;
+    }
+  }
+  if (a.stepped) c->stop[(a.trip + 1) & 1] = go ? 0 : 1;
+  else cudaGraphSetConditional(a.cond, go ? 1u : 0u);
+}
+
+// ------------------------------------------------------------------ closing residual
+// ||b - A x||^2 per system (x = 0 exactly where b = 0).  Runs on table ta.
+template <int L>
+__device__ __forceinline__ void phase_final(const PcgArgs &a, double *red) {
+  const CallArgs &C = *a.call;
+  const double *b = C.b;
+  double *x = C.x;
+  int zero = 0;
+  auto want = [&](int s) -> int {
+    zero = ldcg(&a.st[s].zero_x);
+    return 1;
+  };
+  auto work = [&](int, int blk, int r0, int r1, double(&acc)[1]) {
+    if (zero) {
+      for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) x[r] = 0.0;
+      return;
+    }
+    double tt = acc[0];
+    auto f = [&](int r, double t) {
+      const double d = b[r] - t;
+      tt = fma(d, d, tt);
+    };
+    row_products<double, L>(a, blk, r0, r1, a.val, a.sval, x, f);
+    acc[0] = tt;
+  };
+  auto fin = [&](int s, double(&tot)[1]) { a.st[s].tt = tot[0]; };
+  walk<1>(a, a.ta, 0, red, want, work, fin);
+}
+
+}  // namespace gbs

@@ -1,173 +1,191 @@
 // MatMult (Sec. 6.1): y = A x on the assembled CSR, FP64, and the launch plan
-// (block tables, warps, pipeline stages) shared with the persistent solves.
+// (block tables, lanes per row, grid caps) shared with the solves.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 
 #include "device_util.cuh"
 #include "internal.cuh"
-#include "pipe.cuh"
+#include "phases.cuh"
 
 namespace gbs {
 
-constexpr int SMEM_BUDGET = 232448 - 1024;  // dynamic shared memory per CTA we plan for
+constexpr int SPMV_ROWS = 256;  // rows per CTA pass of the standalone SpMV
 
-// Persistent SpMV: every warp streams its SpMV blocks through its own
-// bulk-copy pipeline (CSR values, columns and row pointers staged in shared
-// memory) and sums each row lane by lane with one FMA per nonzero.
-__global__ void __launch_bounds__(512) k_spmv(const int32_t *__restrict__ row_ptr,
-                                              const int32_t *__restrict__ col,
-                                              const double *__restrict__ val,
-                                              const double *__restrict__ x,
-                                              double *__restrict__ y, BlockTable t, int cap,
-                                              int Ra, int Re, int ns, int64_t stage_bytes,
-                                              int32_t *err, int64_t timeout_ns) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + (size_t)nw * ns * stage_bytes);
-  WarpPipe P{smem_raw + (size_t)warp * ns * stage_bytes, bars + warp * ns, ns, cap, Ra, Re,
-             stage_bytes, 0u, err, timeout_ns, policy_evict_first(), policy_evict_last()};
-  if (lane == 0) P.init_barriers();
-  __syncwarp();
-  auto want = [](int) -> bool { return true; };
-  auto issue = [&](const BlkDesc &d, unsigned char *st, uint64_t *bar) {
-    if (arrive_for(bar, csr_bytes<double>(d, P.cap)))
-      csr_copy<double>(P, st, d, row_ptr, col, val, bar);
-  };
-  auto work = [&](int b, const BlkDesc &d, unsigned char *st) {
-    auto f = [&](int r, double s) { y[r] = s; };
-    block_rows<double>(P, st, d, row_ptr, col, val, x, f);
-  };
-  warp_stream(P, t, blockIdx.x * nw + warp, gridDim.x * nw, want, issue, work);
+// y = A x with the CSR-vector row product of the solves (csr_rows), over
+// 256-row chunks.
+template <int L>
+__global__ void __launch_bounds__(PHASE_TPB) k_spmv(const int32_t *__restrict__ row_ptr,
+                                                    const int32_t *__restrict__ col,
+                                                    const double *__restrict__ val,
+                                                    const double *__restrict__ x,
+                                                    double *__restrict__ y, int32_t n) {
+  auto f = [&](int r, double s) { y[r] = s; };
+  for (int64_t r0 = (int64_t)blockIdx.x * SPMV_ROWS; r0 < n;
+       r0 += (int64_t)gridDim.x * SPMV_ROWS) {
+    const int r1 = (int)(r0 + SPMV_ROWS < n ? r0 + SPMV_ROWS : n);
+    csr_rows<double, L>(row_ptr, col, val, x, (int)r0, r1, f);
+  }
 }
 
-static size_t spmv_smem(gbs_mat A) {
-  return (size_t)A->nwarps * A->nstages * (size_t)A->stage_bytes +
-         (size_t)A->nwarps * A->nstages * 8;
-}
-
-static BlockTable table_view(const TableDev &t) {
-  return BlockTable{t.nblocks, t.row0, t.nz0, t.sys, t.sys_blk0, t.sys_slot0};
+// y = A x with the sliced-ELL row product (sell_rows), 8 slices per CTA pass.
+__global__ void __launch_bounds__(PHASE_TPB, SELL_MIN_CTAS)
+    k_spmv_sell(const int32_t *__restrict__ sptr, const int32_t *__restrict__ srow0,
+                const int32_t *__restrict__ scol, const double *__restrict__ sval,
+                const double *__restrict__ x, double *__restrict__ y, int32_t nslices) {
+  auto f = [&](int r, double s) { y[r] = s; };
+  const int per = PHASE_TPB / 32;
+  for (int64_t s0 = (int64_t)blockIdx.x * per; s0 < nslices; s0 += (int64_t)gridDim.x * per) {
+    const int s1 = (int)(s0 + per < nslices ? s0 + per : nslices);
+    sell_rows<double>(sptr, srow0, scol, sval, x, (int)s0, s1, f);
+  }
 }
 
 int launch_spmv(gbs_mat A, const double *x, double *y, cudaStream_t s) {
-  if (A->ta.nblocks == 0) return GBS_OK;
-  const size_t smem = spmv_smem(A);
-  cudaFuncAttributes fa;
-  GBS_TRY_CUDA(cudaFuncGetAttributes(&fa, k_spmv));
-  if (fa.maxDynamicSharedSizeBytes < (int)smem)
-    GBS_TRY_CUDA(cudaFuncSetAttribute(k_spmv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  if (A->grid_spmv <= 0) {
-    int per_sm = 0, nsm = 0;
-    GBS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmv, A->tpb, smem));
-    GBS_TRY_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, A->device));
-    if (per_sm < 1) {
-      set_error("SpMV kernel does not fit on an SM (tpb %d, smem %zu)", A->tpb, smem);
-      return GBS_ERR_LAUNCH;
-    }
-    const int64_t warps_needed = A->ta.nblocks;
-    A->grid_spmv = (int32_t)std::max<int64_t>(
-        1, std::min<int64_t>((int64_t)per_sm * nsm, (warps_needed + A->nwarps - 1) / A->nwarps));
+  if (A->nrows == 0) return GBS_OK;
+  const int32_t n = (int32_t)A->nrows;
+  if (A->lanes == GBS_SPMV_SELL) {
+    const int64_t ns = A->nslices, per = PHASE_TPB / 32;
+    const unsigned grid = (unsigned)std::min<int64_t>((ns + per - 1) / per, 1 << 20);
+    k_spmv_sell<<<grid, PHASE_TPB, 0, s>>>(A->sell_ptr, A->sell_row0, A->sell_col, A->sell_val,
+                                           x, y, (int32_t)ns);
+    GBS_LAUNCHED(1);
+    return GBS_OK;
   }
-  k_spmv<<<(unsigned)A->grid_spmv, A->tpb, smem, s>>>(
-      A->row_ptr, A->col, A->val, x, y, table_view(A->ta), A->cap, A->Ra, A->Re, A->nstages,
-      A->stage_bytes, A->err_word, 2000000000LL);
+  const int64_t chunks = (A->nrows + SPMV_ROWS - 1) / SPMV_ROWS;
+  const unsigned grid = (unsigned)std::min<int64_t>(chunks, 1 << 20);
+  switch (A->lanes) {
+    case 1: k_spmv<1><<<grid, PHASE_TPB, 0, s>>>(A->row_ptr, A->col, A->val, x, y, n); break;
+    case 2: k_spmv<2><<<grid, PHASE_TPB, 0, s>>>(A->row_ptr, A->col, A->val, x, y, n); break;
+    case 8: k_spmv<8><<<grid, PHASE_TPB, 0, s>>>(A->row_ptr, A->col, A->val, x, y, n); break;
+    case 32: k_spmv<32><<<grid, PHASE_TPB, 0, s>>>(A->row_ptr, A->col, A->val, x, y, n); break;
+    default: k_spmv<4><<<grid, PHASE_TPB, 0, s>>>(A->row_ptr, A->col, A->val, x, y, n); break;
+  }
   GBS_LAUNCHED(1);
   return GBS_OK;
 }
 
+// Lanes per row from the mean row length: enough lanes that a warp's loads
+// cover whole 32-byte sectors of the value stream, few enough that masked
+// slots and the cross-lane adds stay a small part of the FP64 work.
+int auto_lanes(int64_t nnz, int64_t nrows) {
+  const double m = nrows > 0 ? (double)nnz / (double)nrows : 0.0;
+  if (m < 3.0) return 1;
+  if (m < 12.0) return 2;
+  if (m < 48.0) return 4;
+  if (m < 160.0) return 8;
+  return 32;
+}
+
 void free_table(TableDev &t) {
-  for (int32_t *p : {t.row0, t.nz0, t.sys, t.sys_blk0, t.sys_slot0})
+  for (int32_t *p : {t.row0, t.sys, t.sys_blk0, t.sys_slot0, t.slice0})
     if (p) cudaFree(p);
-  t.row0 = t.nz0 = t.sys = t.sys_blk0 = t.sys_slot0 = nullptr;
+  t.row0 = t.sys = t.sys_blk0 = t.sys_slot0 = t.slice0 = nullptr;
   t.nblocks = 0;
+  t.grid = 0;
+  t.nslots = 0;
   t.sys_blk0_h.clear();
 }
 
 // Each system's rows cut into ceil(n_s / R) blocks of R rows (the last one
-// ragged); blocks never straddle systems.
-static int build_table(gbs_mat A, const std::vector<int32_t> &rp, int32_t R, TableDev &t) {
-  std::vector<int32_t> row0, sys, sb0(A->nsys + 1, 0), nz0;
+// ragged); blocks never straddle systems.  R is a multiple of 32, so a block
+// is a whole number of the 32-row slices of the sliced-ELL layout (slice0).
+// The kernels walking the table run min(blocks, cap_per_sm x SMs) CTAs;
+// system s owns min(blocks_s, grid) reduction slots.
+static int build_table(gbs_mat A, int32_t R, int32_t cap_per_sm, TableDev &t) {
+  std::vector<int32_t> row0, sys, sb0(A->nsys + 1, 0), sl0;
+  int32_t slices = 0;
   for (int32_t q = 0; q < A->nsys; ++q) {
     const int64_t a = A->row_off_h[q], e = A->row_off_h[q + 1];
     for (int64_t r = a; r < e; r += R) {
       row0.push_back((int32_t)r);
       sys.push_back(q);
+      sl0.push_back(slices + (int32_t)((r - a) / 32));
     }
+    slices += (int32_t)((e - a + 31) / 32);
     sb0[q + 1] = (int32_t)row0.size();
   }
   row0.push_back((int32_t)A->nrows);
+  sl0.push_back(slices);
   const int32_t nb = (int32_t)sys.size();
-  nz0.resize(nb + 1);
-  for (int32_t b = 0; b <= nb; ++b) nz0[b] = rp[row0[b]];
+  int nsm = 0;
+  GBS_TRY_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, A->device));
+  int64_t grid = std::min<int64_t>(nb, (int64_t)std::max(cap_per_sm, 1) * nsm);
+  grid = std::max<int64_t>(grid, 1);
+  std::vector<int32_t> so(A->nsys + 1, 0);
+  for (int32_t q = 0; q < A->nsys; ++q)
+    so[q + 1] = so[q] + (int32_t)std::min<int64_t>(sb0[q + 1] - sb0[q], grid);
   free_table(t);
   GBS_TRY_CUDA(cudaMalloc(&t.row0, sizeof(int32_t) * (nb + 1)));
-  GBS_TRY_CUDA(cudaMalloc(&t.nz0, sizeof(int32_t) * (nb + 1)));
   GBS_TRY_CUDA(cudaMalloc(&t.sys, sizeof(int32_t) * std::max(nb, 1)));
   GBS_TRY_CUDA(cudaMalloc(&t.sys_blk0, sizeof(int32_t) * (A->nsys + 1)));
   GBS_TRY_CUDA(cudaMalloc(&t.sys_slot0, sizeof(int32_t) * (A->nsys + 1)));
+  GBS_TRY_CUDA(cudaMalloc(&t.slice0, sizeof(int32_t) * (nb + 1)));
   GBS_TRY_CUDA(cudaMemcpy(t.row0, row0.data(), sizeof(int32_t) * (nb + 1), cudaMemcpyHostToDevice));
-  GBS_TRY_CUDA(cudaMemcpy(t.nz0, nz0.data(), sizeof(int32_t) * (nb + 1), cudaMemcpyHostToDevice));
+  GBS_TRY_CUDA(cudaMemcpy(t.slice0, sl0.data(), sizeof(int32_t) * (nb + 1), cudaMemcpyHostToDevice));
   if (nb > 0)
     GBS_TRY_CUDA(cudaMemcpy(t.sys, sys.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice));
   GBS_TRY_CUDA(cudaMemcpy(t.sys_blk0, sb0.data(), sizeof(int32_t) * (A->nsys + 1),
                           cudaMemcpyHostToDevice));
+  GBS_TRY_CUDA(cudaMemcpy(t.sys_slot0, so.data(), sizeof(int32_t) * (A->nsys + 1),
+                          cudaMemcpyHostToDevice));
   t.sys_blk0_h = sb0;
   t.nblocks = nb;
+  t.grid = (int32_t)grid;
+  t.nslots = std::max<int64_t>(so[A->nsys], 1);
   return GBS_OK;
 }
 
-// Plan: SpMV blocks of Ra rows (a multiple of 32: lanes own rows), update
-// blocks of Re rows, nwarps independent warps per CTA, ns pipeline stages per
-// warp.  A warp stage holds a whole SpMV block (Ra rows of the longest row,
-// plus 16-byte rounding slack) or an update block (5 vector slices); when the
-// stages would not fit in shared memory the SpMV capacity shrinks and longer
-// blocks are read with plain loads instead.
-int build_plan(gbs_mat A, int32_t Ra, int32_t Re, int32_t nw, int32_t ns) {
-  if (Ra < 32 || Ra > 512 || (Ra % 32) != 0 || Re < 32 || Re > 4096 || (Re % 32) != 0 ||
-      nw < 1 || nw > 16 || ns < 2 || ns > PIPE_MAX_STAGES) {
-    set_error("plan: spmv_rows %d and update_rows %d must be multiples of 32 (<= 512, <= 4096), "
-              "warps %d in [1,16], stages %d in [2,%d]",
-              Ra, Re, nw, ns, PIPE_MAX_STAGES);
+// Plan: SpMV-phase blocks of Ra rows, update-phase blocks of Re rows (both
+// multiples of 32), the row-product kernel (GBS_SPMV_AUTO, GBS_SPMV_SELL or
+// CSR-vector lanes per row) and a cap of CTAs per SM on the grids (0: as many
+// as fit on an SM at once, so each phase kernel runs in one wave).  Cached graphs are dropped: they bake in the tables and grids.
+// Synchronises the device when it builds the sliced copy.
+int build_plan(gbs_mat A, int32_t Ra, int32_t Re, int32_t kernel, int32_t ctas_per_sm) {
+  const bool bad_ra = Ra != 0 && (Ra < 32 || Ra > 65536 || (Ra % 32) != 0);
+  const bool bad_re = Re != 0 && (Re < 32 || Re > 65536 || (Re % 32) != 0);
+  if (bad_ra || bad_re ||
+      !(kernel == GBS_SPMV_AUTO || kernel == GBS_SPMV_SELL || kernel == 1 || kernel == 2 ||
+        kernel == 4 || kernel == 8 || kernel == 32) ||
+      ctas_per_sm < 0 || ctas_per_sm > 64) {
+    set_error("plan: spmv_rows %d and update_rows %d must be 0 (auto) or multiples of 32 in "
+              "[32, 65536], "
+              "kernel %d one of -1 (auto), 0 (sliced ELL), 1, 2, 4, 8, 32 (CSR lanes), "
+              "ctas_per_sm %d in [0, 64]",
+              Ra, Re, kernel, ctas_per_sm);
     return GBS_ERR_ARG;
   }
-  std::vector<int32_t> rp(A->nrows + 1);
-  GBS_TRY_CUDA(cudaMemcpy(rp.data(), A->row_ptr, sizeof(int32_t) * (A->nrows + 1),
-                          cudaMemcpyDeviceToHost));
-  const int64_t upd = (upd_stage_bytes(Re) + 15) & ~15LL;
-  const int64_t per_stage_budget = (SMEM_BUDGET - 64) / ((int64_t)nw * ns) - 8;
-  if (upd > per_stage_budget) {
-    set_error("plan: %d warps x %d stages of %d-row update blocks exceed shared memory", nw, ns,
-              Re);
-    return GBS_ERR_ARG;
+  drop_graphs(A);
+  if (kernel == GBS_SPMV_AUTO) {
+    GBS_TRY(sell_shape(A));
+    kernel = (A->sell_ptr && (double)A->sell_nnz <= 1.2 * (double)A->nnz)
+                 ? GBS_SPMV_SELL
+                 : auto_lanes(A->nnz, A->nrows);
   }
-  int64_t cap = ((int64_t)Ra * std::max<int32_t>(A->max_row_nnz, 1) + 4 + 3) & ~3LL;
-  while (cap > 64 && ((spmv_stage_bytes((int)cap, Ra) + 15) & ~15LL) > per_stage_budget)
-    cap = (cap / 2) & ~3LL;
-  const int64_t spm = (spmv_stage_bytes((int)cap, Ra) + 15) & ~15LL;
-  if (spm > per_stage_budget) {
-    set_error("plan: %d warps x %d stages of %d-row SpMV blocks exceed shared memory", nw, ns, Ra);
-    return GBS_ERR_ARG;
+  if (kernel == GBS_SPMV_SELL) {
+    GBS_TRY(sell_build(A, nullptr));
+    GBS_TRY_CUDA(cudaDeviceSynchronize());
   }
-  GBS_TRY(build_table(A, rp, Ra, A->ta));
-  GBS_TRY(build_table(A, rp, Re, A->te));
-  if (!A->err_word) {
-    GBS_TRY_CUDA(cudaMalloc(&A->err_word, sizeof(int32_t)));
-    GBS_TRY_CUDA(cudaMemset(A->err_word, 0, sizeof(int32_t)));
-  }
+  // grids: one wave of the phase kernels unless capped explicitly; automatic
+  // block sizes give about one block per CTA of that wave (at least 256 rows,
+  // so every warp of a CTA has rows)
+  int occ_rows = 1, occ_upd = 1, nsm = 1;
+  GBS_TRY(phase_occupancy(kernel, &occ_rows, &occ_upd));
+  GBS_TRY_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, A->device));
+  const int cap_a = ctas_per_sm ? ctas_per_sm : occ_rows;
+  const int cap_e = ctas_per_sm ? ctas_per_sm : occ_upd;
+  auto auto_rows = [&](int cap) {
+    const int64_t per = (A->nrows + (int64_t)cap * nsm - 1) / ((int64_t)cap * nsm);
+    return (int32_t)std::min<int64_t>(65536, std::max<int64_t>(256, (per + 31) / 32 * 32));
+  };
+  if (Ra == 0) Ra = auto_rows(cap_a);
+  if (Re == 0) Re = auto_rows(cap_e);
+  GBS_TRY(build_table(A, Ra, cap_a, A->ta));
+  GBS_TRY(build_table(A, Re, cap_e, A->te));
   A->Ra = Ra;
   A->Re = Re;
-  A->nwarps = nw;
-  A->tpb = 32 * nw;
-  A->nstages = ns;
-  A->cap = (int32_t)cap;
-  A->stage_bytes = std::max(spm, upd);
-  A->slot_workers = -1;
-  A->grid_fp64 = A->grid_fp32 = A->grid_spmv = 0;
-  if (A->graph) {
-    cudaGraphExecDestroy(A->graph);
-    A->graph = nullptr;
-  }
+  A->lanes = kernel;
+  A->ctas_per_sm = ctas_per_sm;
   return GBS_OK;
 }
 

@@ -55,7 +55,7 @@ def test_struct_sizes_match_header():
 #include "gbs.h"
 int main(void) {
   printf("%zu %zu %zu %zu %zu\n", sizeof(ksp_opts), sizeof(ksp_result),
-         offsetof(ksp_opts, timeout_ns), offsetof(ksp_opts, debug_barrier_extra),
+         offsetof(ksp_opts, timeout_ns), offsetof(ksp_opts, host_loop),
          offsetof(ksp_result, true_rel_residual));
   return 0;
 }
@@ -68,7 +68,7 @@ int main(void) {
         out = subprocess.check_output([exe]).decode().split()
     got = [int(v) for v in out]
     assert got == [ctypes.sizeof(B.KspOpts), ctypes.sizeof(B.KspResult),
-                   B.KspOpts.timeout_ns.offset, B.KspOpts.debug_barrier_extra.offset,
+                   B.KspOpts.timeout_ns.offset, B.KspOpts.host_loop.offset,
                    B.KspResult.true_rel_residual.offset]
 
 
