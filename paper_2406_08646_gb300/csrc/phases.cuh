@@ -316,36 +316,62 @@ struct Vals {
   T v[N];
 };
 
+template <typename T>
+struct Pair;
+template <>
+struct Pair<double> {
+  typedef double2 type;
+};
+template <>
+struct Pair<float> {
+  typedef float2 type;
+};
+
 // Row products of the 32-row slices [s0, s1) of the sliced-ELL copy: warp w
 // takes slices s0 + w, s0 + w + nw, ...; lane i sums row i of the slice in
-// CSR order, one FMA per stored nonzero, two entries' loads in flight per
-// step; padding (column -1) is skipped.  Entry offsets are 32-bit (the copy
-// holds fewer than 2^31 entries) and a slice's entries for lane i are
-// sptr[s] + i, + 32, ..., so the trip count is the same for every lane.
-// f(r, sum) runs on every lane whose row exists.
+// CSR order, one FMA per stored nonzero; padding (column -1) is skipped.
+// Entries k = 2m, 2m + 1 of a lane's row are adjacent (pair layout, sell.cu),
+// so one 8-byte column load and one 8- or 16-byte value load fetch two
+// entries; two pairs are in flight per step.  A slice's offsets and first
+// rows are loaded before its entries, so no dependent load is left for the
+// end.  f(r, sum) runs on every lane whose row exists.
 template <typename T, class F>
 __device__ __forceinline__ void sell_rows(const int32_t *__restrict__ sptr,
                                           const int32_t *__restrict__ srow0,
                                           const int32_t *__restrict__ scol,
                                           const T *__restrict__ sval, const T *__restrict__ x,
                                           int s0, int s1, F &f) {
+  typedef typename Pair<T>::type P;
+  const int2 *__restrict__ c2 = reinterpret_cast<const int2 *>(scol);
+  const P *__restrict__ v2 = reinterpret_cast<const P *>(sval);
   const int lane = threadIdx.x & 31;
   for (int sl = s0 + (int)(threadIdx.x >> 5); sl < s1; sl += (int)(blockDim.x >> 5)) {
-    int q = __ldg(sptr + sl) + lane;
-    const int qe = __ldg(sptr + sl + 1);
+    const int b0 = __ldg(sptr + sl), b1 = __ldg(sptr + sl + 1);
+    const int r = __ldg(srow0 + sl) + lane, re = __ldg(srow0 + sl + 1);
+    // pair index of this lane's first pair, and one past its last full pair
+    int pi = (b0 >> 1) + lane;
+    const int pend = pi + 32 * ((b1 - b0) >> 6);
     T acc = T(0);
-    for (; q + 32 < qe; q += 64) {
-      const int c0 = __ldg(scol + q), c1 = __ldg(scol + q + 32);
-      const T v0 = __ldg(sval + q), v1 = __ldg(sval + q + 32);
-      if (c0 >= 0) acc = fma_rn(v0, __ldg(x + c0), acc);
-      if (c1 >= 0) acc = fma_rn(v1, __ldg(x + c1), acc);
+    for (; pi + 32 < pend; pi += 64) {
+      const int2 ca = __ldg(c2 + pi), cb = __ldg(c2 + pi + 32);
+      const P va = __ldg(v2 + pi), vb = __ldg(v2 + pi + 32);
+      if (ca.x >= 0) acc = fma_rn(va.x, __ldg(x + ca.x), acc);
+      if (ca.y >= 0) acc = fma_rn(va.y, __ldg(x + ca.y), acc);
+      if (cb.x >= 0) acc = fma_rn(vb.x, __ldg(x + cb.x), acc);
+      if (cb.y >= 0) acc = fma_rn(vb.y, __ldg(x + cb.y), acc);
     }
-    if (q < qe) {
-      const int c0 = __ldg(scol + q);
-      if (c0 >= 0) acc = fma_rn(__ldg(sval + q), __ldg(x + c0), acc);
+    if (pi < pend) {
+      const int2 ca = __ldg(c2 + pi);
+      const P va = __ldg(v2 + pi);
+      if (ca.x >= 0) acc = fma_rn(va.x, __ldg(x + ca.x), acc);
+      if (ca.y >= 0) acc = fma_rn(va.y, __ldg(x + ca.y), acc);
     }
-    const int r = __ldg(srow0 + sl) + lane;
-    if (r < __ldg(srow0 + sl + 1)) f(r, acc);
+    if (((b1 - b0) >> 5) & 1) {  // the odd last entry, stored after the pairs
+      const int q = b1 - 32 + lane;
+      const int c = __ldg(scol + q);
+      if (c >= 0) acc = fma_rn(__ldg(sval + q), __ldg(x + c), acc);
+    }
+    if (r < re) f(r, acc);
   }
 }
 

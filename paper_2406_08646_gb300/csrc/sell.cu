@@ -4,12 +4,15 @@
 //
 // Rows are cut into slices of 32 consecutive rows (aligned to each system's
 // first row, so no slice straddles two systems).  Slice s has width w_s (its
-// longest row) and stores its 32 x w_s entries column-major: entry k of the
-// slice's row i sits at sell_ptr[s] + 32 k + i, padding has column -1 and
-// value 0.  A warp then reads one slice with lane i on row i: every load of
-// the value, column and (for a stencil-like pattern) x streams is a
-// contiguous 128- or 256-byte run, each row is summed in CSR order with one
-// FMA per stored nonzero, and no cross-lane adds are needed.
+// longest row) and holds 32 x w_s entries from b = sell_ptr[s] on, padding
+// with column -1 and value 0.  Entries 2m and 2m + 1 of the slice's row i sit
+// side by side at b + 64 m + 2 i (+1) for m < w_s / 2; an odd last entry sits
+// at b + 64 (w_s / 2) + i.  A warp reads one slice with lane i on row i: each
+// load instruction fetches a contiguous 256-byte (columns, FP32 values) or
+// 512-byte (FP64 values) run holding two entries per lane, the x gathers of a
+// stencil-like pattern are contiguous too, each row is summed in CSR order
+// with one FMA per stored nonzero, and no cross-lane adds are needed.  b is a
+// multiple of 32 entries, so the paired loads are aligned.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -48,12 +51,13 @@ __global__ void k_sell_fill(int64_t nslices, const int32_t *__restrict__ sptr,
     const int32_t r = srow0[s] + lane;
     const bool live = r < srow0[s + 1];
     const int32_t rs = live ? row_ptr[r] : 0, len = live ? row_ptr[r + 1] - rs : 0;
-    const int64_t base = sptr[s] + lane;
-    const int32_t w = (int32_t)((sptr[s + 1] - sptr[s]) >> 5);
+    const int64_t b = sptr[s];
+    const int32_t w = (int32_t)((sptr[s + 1] - b) >> 5), np = w >> 1;
     for (int32_t k = 0; k < w; ++k) {
       const bool ok = k < len;
-      if (scol) scol[base + 32 * (int64_t)k] = ok ? col[rs + k] : -1;
-      if (sval) sval[base + 32 * (int64_t)k] = ok ? val[rs + k] : T(0);
+      const int64_t q = k < 2 * np ? b + 64 * (k >> 1) + 2 * lane + (k & 1) : b + 64 * np + lane;
+      if (scol) scol[q] = ok ? col[rs + k] : -1;
+      if (sval) sval[q] = ok ? val[rs + k] : T(0);
     }
   }
 }
