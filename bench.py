@@ -9,10 +9,16 @@ nonzeros), inputs resident in HBM:
   100 SpMVs, FP32-inner / FP64-refined PCG to rtol 1e-8, adjoint solve plus
   gradient scatter, mat_destroy.
 The headline value is the FP64 CG solve time in seconds (lower is better);
-SpMV GB/s, the refined and adjoint times and the roofline of the persistent
-PCG kernel are reported beside it.
+SpMV GB/s, the refined and adjoint times, the per-phase device times of the
+solve loop and the roofline of the sliced-ELL SpMV kernel (the row product
+that also runs the solve's SpMV phase) are reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--host-loop]
+
+--host-loop runs the solves with the host-stepped loop instead of the CUDA
+graph (same kernels, same grids, bit-identical results) so that a profiler's
+launch list sees every kernel of the loop.
 
 --impl reference times the FP64 CPU oracle (the plain C implementation in
 oracle/) on a bounded sample of the same workload on the host cores.
@@ -46,6 +52,34 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def source_sha() -> str:
+    """Hash of the sources of the row-product kernels (ties a stored ncu
+    traffic figure to the code it was measured on)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("phases.cuh", "spmv.cu", "sell.cu", "device_util.cuh"):
+        with open(os.path.join(ROOT, "paper_2406_08646_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(name: str):
+    """Per-launch DRAM bytes recorded in profiles/<name>.md by an ncu capture
+    of the current kernel source, else None."""
+    try:
+        kv = {}
+        with open(os.path.join(ROOT, "profiles", name + ".md")) as f:
+            for line in f:
+                if ":" in line and line.startswith("- "):
+                    k, v = line[2:].split(":", 1)
+                    kv[k.strip()] = v.strip().strip("`")
+        if kv.get("source_sha") != source_sha():
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
 def pcg_alg_bytes(n: int, nnz: int, iterations: int) -> float:
     """Algorithmic bytes of one FP64 PCG launch: per iteration the floor
     12 nnz + 4 (n+1) + 72 n (A once; x, r, p read and written; D^-1 read; q
@@ -56,7 +90,10 @@ def pcg_alg_bytes(n: int, nnz: int, iterations: int) -> float:
 
 
 def spmv_alg_bytes(n: int, nnz: int) -> float:
-    return 12.0 * nnz + 4.0 * (n + 1) + 16.0 * n
+    """Values and column indices once (12 B per nonzero), x once and y once
+    (16 B per row); the sliced layout's slice offsets replace row pointers and
+    are not counted."""
+    return 12.0 * nnz + 16.0 * n
 
 
 class Clocks:
@@ -195,9 +232,10 @@ def run_gpu(args, rank: int, world: int):
     dldv = torch.empty(ncoo, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
     sp = B._stream(stream)
-    o64 = B.make_opts(rtol=1e-8)
-    o32 = B.make_opts(rtol=1e-8, precision=B.FP32_REFINED)
-    oadj = B.make_opts(rtol=1e-8)
+    hl = bool(args.host_loop)
+    o64 = B.make_opts(rtol=1e-8, host_loop=hl)
+    o32 = B.make_opts(rtol=1e-8, precision=B.FP32_REFINED, host_loop=hl)
+    oadj = B.make_opts(rtol=1e-8, host_loop=hl)
     SPMV_REPS = 100
 
     def check(st):
@@ -216,6 +254,7 @@ def run_gpu(args, rank: int, world: int):
                              B.ctypes.byref(o64), None, sp))
         ev[3].record(stream)
         res["fp64"] = B.ksp_get_result(A, 1, stream)[0]
+        res["phases_fp64"] = B.ksp_get_phase_ns(A, stream)
         ev[4].record(stream)
         for _ in range(SPMV_REPS):
             check(L.mat_mult(A, B._dev(b_d, torch.float64), B._dev(y, torch.float64), sp))
@@ -224,6 +263,7 @@ def run_gpu(args, rank: int, world: int):
                              B.ctypes.byref(o32), None, sp))
         ev[6].record(stream)
         res["fp32_refined"] = B.ksp_get_result(A, 1, stream)[0]
+        res["phases_fp32_refined"] = B.ksp_get_phase_ns(A, stream)
         torch.sub(x64, xt_d, out=g)
         ev7 = torch.cuda.Event(enable_timing=True)
         ev7.record(stream)
@@ -280,9 +320,20 @@ def run_gpu(args, rank: int, world: int):
     r64 = results[-1]["fp64"]
     it = r64["iterations"]
     hbm, peak_kind = peaks()
-    achieved = pcg_alg_bytes(n, nnz, it) / solve_s / 1e9
+    solve_gbs = pcg_alg_bytes(n, nnz, it) / solve_s / 1e9
     spmv_s = med["spmv_x100"] / 1e3 / SPMV_REPS
     spmv_gbs = spmv_alg_bytes(n, nnz) / spmv_s / 1e9
+    traffic = stored_traffic(f"spmv_sell_q1hex{args.ne}")
+
+    def per_iter(ph, its):
+        return {k: v / 1e3 / max(its, 1) for k, v in ph.items()
+                if k in ("spmv", "update_xr", "update_p")}
+    last = results[-1]
+    phases = {"fp64_us_per_iteration": per_iter(last["phases_fp64"], it),
+              "fp32_refined_us_per_iteration":
+                  per_iter(last["phases_fp32_refined"], last["fp32_refined"]["iterations"]),
+              "what": "device clock of CTA 0 from each phase kernel's start to the next "
+                      "one's start (launch gaps included), summed over the loop"}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.ne == 96:
         s = oracle_sample(p)
@@ -302,18 +353,28 @@ def run_gpu(args, rank: int, world: int):
                        "rtol": 1e-8, "spmv_reps": SPMV_REPS,
                        "l2": "no flush: every input is larger than L2 (CSR 290 MB, COO 906 MB)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "plan": plan},
+                       "plan": plan, "loop": "host-stepped" if hl else "graph"},
             "rows_ms": med,
-            "iterations": {k: results[-1][k]["iterations"] for k in results[-1]},
-            "outer_iterations_fp32_refined": results[-1]["fp32_refined"]["outer_iterations"],
-            "true_rel_residual": {k: results[-1][k]["true_rel_residual"] for k in results[-1]},
-            "status": {k: results[-1][k]["status"] for k in results[-1]},
+            "iterations": {k: last[k]["iterations"] for k in ("fp64", "fp32_refined", "adjoint")},
+            "outer_iterations_fp32_refined": last["fp32_refined"]["outer_iterations"],
+            "true_rel_residual": {k: last[k]["true_rel_residual"]
+                                  for k in ("fp64", "fp32_refined", "adjoint")},
+            "status": {k: last[k]["status"] for k in ("fp64", "fp32_refined", "adjoint")},
             "spmv": {"gbs": spmv_gbs, "frac": spmv_gbs / hbm, "us": spmv_s * 1e6,
                      "alg_bytes": spmv_alg_bytes(n, nnz)},
-            "roofline": {"kernel": "k_pcg<false> (persistent FP64 PCG)", "bound": "hbm",
-                         "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": None,
-                         "alg_bytes": pcg_alg_bytes(n, nnz, it)},
+            "roofline": {"kernel": "k_spmv_sell (MatMult, sliced-ELL FP64 row product)",
+                         "bound": "hbm", "achieved": spmv_gbs, "peak": hbm, "unit": "GB/s",
+                         "frac": spmv_gbs / hbm, "peak_kind": f"{peak_kind} (copy, burst)",
+                         "traffic": traffic, "alg_bytes": spmv_alg_bytes(n, nnz),
+                         "timing": f"CUDA events around {SPMV_REPS} back-to-back launches "
+                                   "on the launching stream, median over steps"},
+            "solve_roofline": {"what": "whole FP64 solve (one graph launch): PCG floor bytes "
+                                       "12 nnz + 4(n+1) + 72 n per iteration, plus setup and "
+                                       "closing residual, over the solve's event time",
+                               "achieved": solve_gbs, "peak": hbm, "unit": "GB/s",
+                               "frac": solve_gbs / hbm,
+                               "alg_bytes": pcg_alg_bytes(n, nnz, it)},
+            "solve_phases": phases,
             "refined_vs_fp64": med["solve_fp32_refined"] / med["solve_fp64"],
             "adjoint_vs_fp64": med["adjoint"] / med["solve_fp64"],
             "e2e": None if e2e_s is None else {"value": e2e_s, "unit": "s",
@@ -380,6 +441,8 @@ def main():
     ap.add_argument("--impl", default="gbs", choices=["gbs", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="run the solves' loop from the host (for profiler launch lists)")
     ap.add_argument("--ne", type=int, default=96,
                     help="elements per side of the Q1 workload (96 = the benchmark; "
                          "smaller only for profiling captures)")
