@@ -20,6 +20,16 @@ that also runs the solve's SpMV phase) are reported beside it.
 graph (same kernels, same grids, bit-identical results) so that a profiler's
 launch list sees every kernel of the loop.
 
+--workload selects the comparison runs of the other configurations (each
+prints its own JSON line; the default is the Q1 benchmark above):
+  c3  7-point Laplacian 192^3: FP64 PCG vs FP32-inner / FP64-refined PCG at
+      rtol 1e-10 and 1e-8 (true residuals reported)
+  c4  2D edge diffusion 1024^2: forward FP64 solve vs adjoint solve + gradient
+      scatter, and dL/dkappa through the edge signs
+  c5  512 independent systems (~51.6M rows): one batched graph launch (FP64
+      and refined) vs 512 sequential single-system solves vs the stacked
+      ensemble solve, plus the batched adjoint
+
 --impl reference times the FP64 CPU oracle (the plain C implementation in
 oracle/) on a bounded sample of the same workload on the host cores.
 Multi-GPU (torchrun): independent replicas, one per GPU, no collective on the
@@ -200,6 +210,178 @@ def run_reference(args, rank: int, world: int):
 
 
 # ----------------------------------------------------------------- GPU arm
+
+# ----------------------------------------------------------------- other configs
+
+def _ev_time(stream, fn, reps=3, warm=1):
+    """Median CUDA-event time (s) of fn() on `stream` over `reps` after `warm`."""
+    import torch
+    out = []
+    for k in range(warm + reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        e1.synchronize()
+        if k >= warm:
+            out.append(e0.elapsed_time(e1) / 1e3)
+    return statistics.median(out), r
+
+
+def _base_line(args, metric_value, config, extra):
+    hbm, kind = peaks()
+    line = {"metric": METRIC, "value": metric_value, "unit": "s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config, "peak_hbm_gbs": hbm, "peak_kind": kind}
+    line.update(extra)
+    return line
+
+
+def run_suite(args):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2406_08646_gb300 import binding as B
+    from paper_2406_08646_gb300 import workloads as W
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream(dev)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    reps = max(1, args.steps)
+    hbm, _ = peaks()
+
+    if args.workload == "c3":
+        p = W.poisson3d(192, seed=W.SEED_C3)
+        A = B.Mat.from_coo(p.nrows, p.ncols, t(p.i), t(p.j))
+        A.set_values(t(p.v))
+        b = t(p.b)
+        x = torch.empty_like(b)
+        y = torch.empty_like(b)
+        sp, _ = _ev_time(stream, lambda: [A.mult(b, y) for _ in range(20)], reps=reps)
+        spmv_s = sp / 20
+        rows = {}
+        for rtol in (1e-10, 1e-8):
+            for prec, name in ((B.FP64, "fp64"), (B.FP32_REFINED, "fp32_refined")):
+                ts, (_, r) = _ev_time(stream, lambda: A.solve(b, x, rtol=rtol, precision=prec),
+                                      reps=reps)
+                ph = A.phase_ns()
+                rows[f"{name}@{rtol:g}"] = {
+                    "s": ts, "iterations": r["iterations"],
+                    "outer_iterations": r["outer_iterations"], "status": r["status"],
+                    "true_rel_residual": r["true_rel_residual"],
+                    "us_per_iteration": {k: v / 1e3 / max(r["iterations"], 1)
+                                         for k, v in ph.items()
+                                         if k in ("spmv", "update_xr", "update_p")}}
+        n, nnz = p.nrows, A.nnz
+        line = _base_line(
+            args, rows["fp64@1e-10"]["s"],
+            {"workload": "poisson3d_192: 7-point Laplacian 192^3, random-normal rhs, seed 1003",
+             "nrows": n, "nnz": nnz, "plan": A.plan()},
+            {"solves": rows,
+             "refined_vs_fp64": {k: rows[f"fp32_refined@{k}"]["s"] / rows[f"fp64@{k}"]["s"]
+                                 for k in ("1e-10", "1e-08")},
+             "spmv": {"us": spmv_s * 1e6, "gbs": spmv_alg_bytes(n, nnz) / spmv_s / 1e9,
+                      "frac": spmv_alg_bytes(n, nnz) / spmv_s / 1e9 / hbm},
+             "solve_gbs_fp64@1e-10": pcg_alg_bytes(n, nnz, rows["fp64@1e-10"]["iterations"])
+                                     / rows["fp64@1e-10"]["s"] / 1e9})
+        print(json.dumps(line), flush=True)
+        A.close()
+        return 0
+
+    if args.workload == "c4":
+        p = W.edge_diffusion(1024, seed=W.SEED_C4)
+        A = B.Mat.from_coo(p.nrows, p.ncols, t(p.i), t(p.j))
+        A.set_values(t(p.v))
+        b, xt = t(p.b), t(p.extra["x_target"])
+        x = torch.empty_like(b)
+        tf, (_, rf) = _ev_time(stream, lambda: A.solve(b, x, rtol=1e-8), reps=reps)
+        g = (x - xt).contiguous()
+        ta, (lam, _, dldv, ra) = _ev_time(
+            stream, lambda: A.adjoint(x, g, dlda=False, dldv=True, rtol=1e-8), reps=reps)
+        signs = t(W.EDGE_SIGNS)
+        gk = (dldv.view(-1, 4) * signs).sum(dim=1)
+        line = _base_line(
+            args, tf,
+            {"workload": "edge_diffusion_1024: 2D 5-point variable-coefficient diffusion, "
+                         "kappa log-uniform [0.1, 10], seed 1004",
+             "nrows": p.nrows, "nnz": A.nnz, "ncoo": p.ncoo, "plan": A.plan()},
+            {"forward": {"s": tf, "iterations": rf["iterations"], "status": rf["status"],
+                         "true_rel_residual": rf["true_rel_residual"]},
+             "adjoint": {"s": ta, "iterations": ra[0]["iterations"], "status": ra[0]["status"],
+                         "true_rel_residual": ra[0]["true_rel_residual"],
+                         "what": "A^T lambda = x - x_target solve plus the dL/dv scatter"},
+             "adjoint_vs_forward": ta / tf,
+             "loss": float(0.5 * ((x - xt) ** 2).sum()),
+             "grad_norms": {"dL/db": float(lam.norm()), "dL/dkappa": float(gk.norm())}})
+        print(json.dumps(line), flush=True)
+        A.close()
+        return 0
+
+    if args.workload == "c5":
+        t0 = time.perf_counter()
+        bt = W.batch(512, seed=W.SEED_C5)
+        gen_s = time.perf_counter() - t0
+        A = B.Mat.from_coo_batched(bt.nrows, bt.ncoo, t(bt.i), t(bt.j))
+        A.set_values(t(bt.v))
+        b = t(bt.b)
+        x = torch.empty_like(b)
+        rows = {}
+        for prec, name in ((B.FP64, "batched_fp64"), (B.FP32_REFINED, "batched_fp32_refined")):
+            ts, (_, rs) = _ev_time(stream, lambda: A.solve_batched(b, x, rtol=1e-8,
+                                                                   precision=prec), reps=reps)
+            its = [q["iterations"] for q in rs]
+            rows[name] = {"s": ts, "ok": sum(q["status"] == B.OK for q in rs),
+                          "iterations_max": max(its), "iterations_mean": float(np.mean(its)),
+                          "true_rel_residual_max": max(q["true_rel_residual"] for q in rs)}
+        te, (_, re) = _ev_time(stream, lambda: A.solve(b, x, rtol=1e-8), reps=reps)
+        rows["ensemble_fp64"] = {"s": te, "iterations": re["iterations"], "status": re["status"],
+                                 "what": "the stacked block-diagonal system, one global norm"}
+        xb, _ = A.solve_batched(b, rtol=1e-8)
+        g = (xb - t(bt.extra["x_target"])).contiguous()
+        tadj, (_, _, _, ra) = _ev_time(
+            stream, lambda: A.adjoint(xb, g, dlda=False, dldv=True, batched=True, rtol=1e-8),
+            reps=reps)
+        rows["batched_adjoint"] = {"s": tadj, "ok": sum(q["status"] == B.OK for q in ra)}
+        A.close()
+        # 512 separate single-system handles, solved one after another
+        ro, co = bt.row_off, bt.coo_off
+        mats, bs, xs = [], [], []
+        for q in range(bt.nsys):
+            sl = slice(int(co[q]), int(co[q + 1]))
+            M = B.Mat.from_coo(int(bt.nrows[q]), int(bt.nrows[q]), t(bt.i[sl]), t(bt.j[sl]))
+            M.set_values(t(bt.v[sl]))
+            mats.append(M)
+            bs.append(b[int(ro[q]):int(ro[q + 1])])
+            xs.append(torch.empty_like(bs[-1]))
+
+        def seq():
+            for M, bq, xq in zip(mats, bs, xs):
+                M.solve(bq, xq, rtol=1e-8, want_result=False)
+            return None
+        ts, _ = _ev_time(stream, seq, reps=max(1, reps // 2))
+        res = [M.solve(bq, xq, rtol=1e-8)[1] for M, bq, xq in zip(mats, bs, xs)]
+        rows["sequential_fp64"] = {"s": ts, "ok": sum(r["status"] == B.OK for r in res),
+                                   "what": "512 single-system handles, ksp_solve_cg each"}
+        for M in mats:
+            M.close()
+        line = _base_line(
+            args, rows["batched_fp64"]["s"],
+            {"workload": "batch_512: 2D 5-point / 3D 7-point edge-diffusion systems, rows "
+                         "uniform on [1k, 200k], kappa log-uniform [0.1, 10], seed 1005",
+             "nsys": bt.nsys, "nrows": int(bt.nrows.sum()), "ncoo": int(bt.ncoo.sum()),
+             "generate_s": gen_s},
+            {"solves": rows,
+             "batched_vs_sequential": rows["batched_fp64"]["s"] / rows["sequential_fp64"]["s"],
+             "batched_vs_ensemble": rows["batched_fp64"]["s"] / rows["ensemble_fp64"]["s"],
+             "refined_vs_fp64": rows["batched_fp32_refined"]["s"] / rows["batched_fp64"]["s"]})
+        print(json.dumps(line), flush=True)
+        return 0
+    raise SystemExit(f"unknown workload {args.workload}")
+
 
 def run_gpu(args, rank: int, world: int):
     import numpy as np
@@ -441,6 +623,8 @@ def main():
     ap.add_argument("--impl", default="gbs", choices=["gbs", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
+                    help="c2 = the benchmark (default); c3/c4/c5 = comparison runs")
     ap.add_argument("--host-loop", action="store_true",
                     help="run the solves' loop from the host (for profiler launch lists)")
     ap.add_argument("--ne", type=int, default=96,
@@ -451,6 +635,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload != "c2":
+        return run_suite(args) if rank == 0 else 0
     if world > 1:
         import torch
         import torch.distributed as dist

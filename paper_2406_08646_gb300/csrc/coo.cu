@@ -615,20 +615,39 @@ int launch_to_fp32(gbs_mat A, cudaStream_t s) {
 // ------------------------------------------------------------------ adjoint scatter
 
 // dLda[p] = -lambda[row p] * x[col p]; dLdv[perm[t]] = dLda[p] for t in the
-// segment of p.  One thread per row.  Ignored COO entries are zeroed by the
-// caller's memset.
-__global__ void k_adjoint_scatter(int64_t nrows, const int32_t *__restrict__ row_ptr,
+// segment of p.  One thread per nonzero, so the reads of col, jmap and perm
+// and the writes of dLda are coalesced.  A warp takes 32 consecutive
+// nonzeros: lane 0 finds the row of the first by binary search over row_ptr
+// (the last r with row_ptr[r] <= p0, which skips empty rows), and each lane
+// walks forward from there to its own row -- at most the number of rows the
+// warp's nonzeros span.  Ignored COO entries are zeroed by the caller's
+// memset.
+__global__ void k_adjoint_scatter(int64_t nnz, int64_t nrows, const int32_t *__restrict__ row_ptr,
                                   const int32_t *__restrict__ col,
                                   const int32_t *__restrict__ jmap,
                                   const int32_t *__restrict__ perm,
                                   const double *__restrict__ lambda,
                                   const double *__restrict__ x, double *__restrict__ dLda,
                                   double *__restrict__ dLdv) {
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows;
-       r += (int64_t)gridDim.x * blockDim.x) {
-    const double lr = lambda[r];
-    for (int32_t p = row_ptr[r]; p < row_ptr[r + 1]; ++p) {
-      const double g = -(lr * x[col[p]]);
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c * 32 < nnz; c += nw) {
+    const int64_t p0 = c * 32, p = p0 + lane;
+    int64_t r0 = 0;
+    if (lane == 0) {
+      int64_t lo = 0, hi = nrows;  // row_ptr[0] = 0 <= p0 < nnz = row_ptr[nrows]
+      while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (row_ptr[mid] <= p0) lo = mid;
+        else hi = mid - 1;
+      }
+      r0 = lo;
+    }
+    r0 = __shfl_sync(FULL_MASK, r0, 0);
+    if (p < nnz) {
+      int64_t r = r0;
+      while (row_ptr[r + 1] <= p) ++r;
+      const double g = -(lambda[r] * x[col[p]]);
       if (dLda) dLda[p] = g;
       if (dLdv)
         for (int32_t t = jmap[p]; t < jmap[p + 1]; ++t) dLdv[perm[t]] = g;
@@ -640,9 +659,9 @@ int launch_adjoint_scatter(gbs_mat A, const double *lambda, const double *x, dou
                            double *dLdv, cudaStream_t s) {
   if (dLdv && A->ncoo > 0 && A->nkept < A->ncoo)
     GBS_TRY_CUDA(cudaMemsetAsync(dLdv, 0, sizeof(double) * A->ncoo, s));
-  if ((dLda || dLdv) && A->nrows > 0) {
-    k_adjoint_scatter<<<grid_for(A->nrows, 256), 256, 0, s>>>(
-        A->nrows, A->row_ptr, A->col, A->jmap, A->perm, lambda, x, dLda, dLdv);
+  if ((dLda || dLdv) && A->nnz > 0) {
+    k_adjoint_scatter<<<grid_for((A->nnz + 31) / 32 * 32, 256), 256, 0, s>>>(
+        A->nnz, A->nrows, A->row_ptr, A->col, A->jmap, A->perm, lambda, x, dLda, dLdv);
     GBS_LAUNCHED(1);
   }
   return GBS_OK;
