@@ -75,7 +75,10 @@ typedef struct {
   int32_t maxit;        /* < 0: 10 n capped at 100000, n = largest system;
                            0 stops at once with GBS_ERR_MAXIT unless b = 0 */
   int32_t precision;    /* GBS_FP64 or GBS_FP32_REFINED */
-  double inner_rtol;    /* refined: FP32 inner tolerance (<= 0: 1e-4) */
+  double inner_rtol;    /* refined: FP32 inner tolerance (<= 0: 1e-4); an inner
+                           solve stops at max(inner_rtol, rtol ||b|| / (2 s))
+                           times its initial residual, s = the FP64 residual
+                           norm it corrects */
   int32_t max_outer;    /* refined: max refinement steps (< 0: 30) */
   int32_t inner_maxit;  /* refined: inner products per step (< 0: as maxit) */
   int64_t timeout_ns;   /* wall-clock limit of the iteration loop, checked

@@ -298,8 +298,10 @@ int orc_pcg(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
 /*
  * Outer (FP64): r = b - A64 x; stop when ||r|| <= rtol ||b||; s = ||r||.
  * Inner (FP32 values, vectors and accumulation): Jacobi-PCG on A32 d = RN(r/s)
- * from d = 0 until ||r_in|| <= inner_rtol ||r_in,0||, inner_maxit products, or
- * a non-positive / non-finite sigma.  Update x += s * d in FP64.
+ * from d = 0 until ||r_in|| <= tgt ||r_in,0|| with tgt = max(inner_rtol,
+ * rtol ||b|| / (2 s)) (the last correction only has to close the remaining
+ * gap), inner_maxit products, or a non-positive / non-finite sigma.  Update
+ * x += s * d in FP64.
  * Stagnation: ||r|| fails to halve on two consecutive outer steps.
  * A32 = RN(A64) elementwise; dinv32 = RN(1/a_ii) with the reciprocal in FP64.
  */
@@ -363,6 +365,9 @@ int orc_pcg_refined(int64_t n, const int32_t *rp, const int32_t *ci,
     }
     prev = rn;
     double s = rn;
+    /* inner target: inner_rtol, or the smaller reduction that already brings
+       the outer residual to half of rtol ||b|| */
+    const double tgt = fmax(inner_rtol, 0.5 * rtol * bnorm / s);
     for (int64_t i = 0; i < n; ++i) r32[i] = (float)(r[i] / s);
     /* inner FP32 Jacobi-PCG from d = 0 */
     for (int64_t i = 0; i < n; ++i) d32[i] = 0.0f;
@@ -370,10 +375,10 @@ int orc_pcg_refined(int64_t n, const int32_t *rp, const int32_t *ci,
     for (int64_t i = 0; i < n; ++i) p32[i] = z32[i];
     float rho = dot32(n, r32, z32);
     float rr = dot32(n, r32, r32);
-    float r0 = sqrtf(rr);
+    const double thr = tgt * (double)sqrtf(rr);
     int64_t it = 0;
     for (;;) {
-      if (!(sqrtf(rr) > inner_rtol * r0)) break; /* also ends on NaN */
+      if (!((double)sqrtf(rr) > thr)) break; /* also ends on NaN */
       if (it >= inner_maxit) break;
       spmv32(n, rp, ci, a32, p32, q32);
       float sigma = dot32(n, p32, q32);

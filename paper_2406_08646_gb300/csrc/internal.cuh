@@ -50,7 +50,7 @@ struct SysState {
   double rnorm0, rnorm;
   double scale;     // refined: s = ||r64||
   double prev_rn;   // refined: previous outer residual norm
-  double r0in;      // refined: initial inner residual norm
+  double r0in;      // refined: inner stopping threshold (target x initial norm)
   double tt;        // ||b - A x||^2 at exit
   int32_t status;
   int32_t active;   // 1 while the system still iterates

@@ -585,9 +585,12 @@ __device__ __forceinline__ void phase_B(const PcgArgs &a, double *red) {
     } else if (S.mode == M_START) {
       const float rho = (float)tot[0], rr = (float)tot[1];
       const float r0 = sqrtf(rr);
+      // inner target: inner_rtol, or the smaller reduction that already
+      // brings the outer residual to half of rtol ||b||
+      const double tgt = fmax(C.inner_rtol, 0.5 * C.rtol * sqrt(S.bb) / S.scale);
       S.rho = rho;
       S.rr = rr;
-      S.r0in = r0;
+      S.r0in = tgt * (double)r0;  // the inner stopping threshold
       S.inner_it = 0;
       if (!((double)r0 > C.inner_rtol * (double)r0) || C.inner_maxit <= 0)
         deactivate(a, S, GBS_ERR_BREAKDOWN);
@@ -600,7 +603,7 @@ __device__ __forceinline__ void phase_B(const PcgArgs &a, double *red) {
       const float beta = rho_new / (float)S.rho;
       S.rho = rho_new;
       S.rr = rr;
-      if (!((double)sqrtf(rr) > C.inner_rtol * S.r0in) || S.inner_it >= C.inner_maxit) {
+      if (!((double)sqrtf(rr) > S.r0in) || S.inner_it >= C.inner_maxit) {
         S.mode = M_XUPD;
         S.outer += 1;
       } else {

@@ -1,0 +1,119 @@
+"""GPU parity at the benchmark's full sizes, in the launch configuration
+bench.py times (the default plan: sliced-ELL row products, one-wave grids,
+the graph-driven loop).
+
+C2 (Q1 96^3) and C3 (7-point 192^3): the whole CSR structure and the values
+bit-exact against the oracle's assembly, every SpMV row within
+1e-12 * sum |a||x|, and the FP64 solve's true residual recomputed by the
+oracle from the GPU's x (C2 also against the oracle's stored iteration count,
+tests/golden/q1hex96_oracle_pcg.json).  C5 (512 systems, 51.6M rows): the
+batched launch as the benchmark runs it, checked on sampled systems the oracle
+assembles and multiplies one by one."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2406_08646_gb300 import binding as B
+from paper_2406_08646_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def abs_bound(O, x):
+    Oa = oracle.CSR(O.nrows, O.ncols, O.row_ptr, O.col, O.perm, O.jmap, O.ncoo, np.abs(O.val))
+    return oracle.spmv(Oa, np.abs(x))
+
+
+def check_assembly_and_spmv(p, A, seed):
+    O = oracle.coo_symbolic(p.nrows, p.ncols, p.i, p.j)
+    oracle.coo_numeric(O, p.v)
+    rp, col, val = (x.cpu().numpy() for x in A.csr())
+    assert np.array_equal(rp, O.row_ptr)
+    assert np.array_equal(col, O.col)
+    assert val.tobytes() == O.val.tobytes()
+    perm, jmap = (x.cpu().numpy() for x in A.coo_maps())
+    assert np.array_equal(perm, O.perm) and np.array_equal(jmap, O.jmap)
+    x = np.random.default_rng(seed).standard_normal(p.nrows)
+    y = A.mult(t(x)).cpu().numpy()
+    assert np.all(np.abs(y - oracle.spmv(O, x)) <= 1e-12 * abs_bound(O, x))
+    return O
+
+
+def test_c2_full_size():
+    p = W.q1_hex(96, seed=W.SEED_C2)
+    A = B.Mat.from_coo(p.nrows, p.ncols, t(p.i), t(p.j))
+    A.set_values(t(p.v))
+    assert A.plan()["kernel"] == B.SPMV_SELL
+    O = check_assembly_and_spmv(p, A, 5)
+    g = json.load(open(os.path.join(GOLDEN, "q1hex96_oracle_pcg.json")))["result"]
+    x, r = A.solve(t(p.b), rtol=1e-8)
+    xg = x.cpu().numpy()
+    tr = np.linalg.norm(p.b - oracle.spmv(O, xg)) / np.linalg.norm(p.b)
+    assert r["status"] == B.OK and tr <= 1.05e-8
+    assert abs(r["iterations"] - g["iterations"]) <= max(2, int(np.ceil(0.01 * g["iterations"])))
+    assert abs(r["rnorm0"] - g["rnorm0"]) <= 1e-12 * g["rnorm0"]
+    # the refined solve reaches the same FP64 residual
+    x32, r32 = A.solve(t(p.b), rtol=1e-8, precision=B.FP32_REFINED)
+    tr32 = np.linalg.norm(p.b - oracle.spmv(O, x32.cpu().numpy())) / np.linalg.norm(p.b)
+    assert r32["status"] == B.OK and tr32 <= 1.05e-8
+    A.close()
+
+
+def test_c3_full_size():
+    p = W.poisson3d(192, seed=W.SEED_C3)
+    A = B.Mat.from_coo(p.nrows, p.ncols, t(p.i), t(p.j))
+    A.set_values(t(p.v))
+    O = check_assembly_and_spmv(p, A, 6)
+    bn = np.linalg.norm(p.b)
+    for prec in (B.FP64, B.FP32_REFINED):
+        x, r = A.solve(t(p.b), rtol=1e-10, precision=prec)
+        tr = np.linalg.norm(p.b - oracle.spmv(O, x.cpu().numpy())) / bn
+        assert r["status"] == B.OK and tr <= 1.05e-10, (prec, tr)
+        # the GPU's own closing residual agrees with the oracle's recomputation
+        assert abs(r["true_rel_residual"] - tr) <= 1e-3 * tr + 1e-13
+    A.close()
+
+
+def test_c5_batched_full_size_sampled_systems():
+    bt = W.batch(512, seed=W.SEED_C5)
+    A = B.Mat.from_coo_batched(bt.nrows, bt.ncoo, t(bt.i), t(bt.j))
+    A.set_values(t(bt.v))
+    x, rs = A.solve_batched(t(bt.b), rtol=1e-8)
+    assert all(q["status"] == B.OK for q in rs)
+    rp, col, val = A.csr()
+    ro, co = bt.row_off, bt.coo_off
+    xg = x.cpu().numpy()
+    rng = np.random.default_rng(8)
+    for s in sorted(set(rng.integers(0, bt.nsys, 8).tolist()) | {0, 1, bt.nsys - 1}):
+        n = int(bt.nrows[s])
+        sl = slice(int(co[s]), int(co[s + 1]))
+        O = oracle.coo_symbolic(n, n, bt.i[sl], bt.j[sl])
+        oracle.coo_numeric(O, bt.v[sl])
+        a0, a1 = int(ro[s]), int(ro[s + 1])
+        rps = rp[a0:a1 + 1].cpu().numpy()
+        assert np.array_equal(rps - rps[0], O.row_ptr)
+        assert np.array_equal(col[rps[0]:rps[-1]].cpu().numpy() - a0, O.col)
+        assert val[rps[0]:rps[-1]].cpu().numpy().tobytes() == O.val.tobytes()
+        bs = bt.b[a0:a1]
+        tr = np.linalg.norm(bs - oracle.spmv(O, xg[a0:a1])) / np.linalg.norm(bs)
+        assert tr <= 1.05e-8, (s, tr)
+        assert abs(rs[s]["true_rel_residual"] - tr) <= 1e-3 * tr + 1e-13
+    A.close()
