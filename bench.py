@@ -63,13 +63,19 @@ def peaks():
 
 
 def source_sha() -> str:
-    """Hash of the sources of the row-product kernels (ties a stored ncu
-    traffic figure to the code it was measured on)."""
+    """Hash of the source of the sliced-ELL SpMV kernel -- spmv.cu, sell.cu,
+    device_util.cuh and the sell_rows product in phases.cuh -- which ties a
+    stored ncu traffic figure to the code it was measured on."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("phases.cuh", "spmv.cu", "sell.cu", "device_util.cuh"):
-        with open(os.path.join(ROOT, "paper_2406_08646_gb300", "csrc", f), "rb") as fh:
+    csrc = os.path.join(ROOT, "paper_2406_08646_gb300", "csrc")
+    for f in ("spmv.cu", "sell.cu", "device_util.cuh"):
+        with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
+    with open(os.path.join(csrc, "phases.cuh")) as fh:
+        src = fh.read()
+    a = src.index("struct Pair;")
+    h.update(src[a:src.index("// The row products of block b", a)].encode())
     return h.hexdigest()[:16]
 
 
