@@ -181,6 +181,7 @@ int read_results(gbs_mat A, ksp_result *res, int32_t count, cudaStream_t s);
 int read_phase_ns(gbs_mat A, int64_t *phase_ns, cudaStream_t s);
 int auto_lanes(int64_t nnz, int64_t nrows);
 int phase_occupancy(int lanes, int *rows, int *upd);
+int32_t stream_matrix(gbs_mat A, int bytes_per_entry);
 void free_sell(gbs_mat A);
 int sell_shape(gbs_mat A);
 int sell_build(gbs_mat A, cudaStream_t s);

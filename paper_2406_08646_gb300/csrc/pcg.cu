@@ -215,7 +215,7 @@ static int put_call(CallArgs *dst, const CallArgs &c, cudaStream_t s) {
   return GBS_OK;
 }
 
-static PcgArgs make_args(gbs_mat A, bool per_system) {
+static PcgArgs make_args(gbs_mat A, bool per_system, bool refined) {
   PcgArgs a;
   memset(&a, 0, sizeof(a));
   a.nsys = per_system ? A->nsys : 1;
@@ -232,6 +232,7 @@ static PcgArgs make_args(gbs_mat A, bool per_system) {
   a.scol = A->sell_col;
   a.sval = A->sell_val;
   a.sval32 = A->sell_val32;
+  a.stream_matrix = stream_matrix(A, refined ? 8 : 12);
   a.dinv = A->dinv;
   a.dinv32 = A->dinv32;
   a.r = A->r;
@@ -278,7 +279,7 @@ static int build_graph(gbs_mat A, bool refined, bool per_system, cudaGraphExec_t
   // every system the setup already retired frozen and clears the condition
   e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
   if (e != cudaSuccess) return fail("conditional handle");
-  PcgArgs a = make_args(A, per_system);
+  PcgArgs a = make_args(A, per_system, refined);
   a.cond = h;
   a.stepped = 0;
   a.trip = 0;
@@ -382,7 +383,7 @@ int solve(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool per_sys
     GBS_TRY_CUDA(cudaMemsetAsync(A->ctl, 0, sizeof(DevCtl), s));
     GBS_TRY_CUDA(cudaMemsetAsync(A->sys_cnt, 0, sizeof(unsigned) * A->nsys, s));
     GBS_TRY(put_call(A->call, call_args(b, x, o), s));
-    return run_stepped(phase_kernels(refined, A->lanes), make_args(A, per_system), A->ta.grid,
+    return run_stepped(phase_kernels(refined, A->lanes), make_args(A, per_system, refined), A->ta.grid,
                        A->te.grid, max_trips_for(o), A->ctl, s);
   }
   cudaGraphExec_t &G = A->graph[refined ? 1 : 0][per_system ? 1 : 0];

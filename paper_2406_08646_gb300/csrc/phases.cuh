@@ -60,6 +60,7 @@ struct PcgArgs {
   const int32_t *srow0, *scol;
   const double *sval;
   const float *sval32;
+  int32_t stream_matrix;  // 1: load the sliced copy evict-first (larger than L2 / 2)
   const double *dinv;
   const float *dinv32;
   double *r, *p, *q;
@@ -316,6 +317,13 @@ struct Vals {
   T v[N];
 };
 
+// Read-only load of a matrix entry, evict-first when STREAM.
+template <bool STREAM, typename T>
+__device__ __forceinline__ T ld_entry(const T *p) {
+  if constexpr (STREAM) return __ldcs(p);
+  else return __ldg(p);
+}
+
 template <typename T>
 struct Pair;
 template <>
@@ -334,8 +342,10 @@ struct Pair<float> {
 // so one 8-byte column load and one 8- or 16-byte value load fetch two
 // entries; two pairs are in flight per step.  A slice's offsets and first
 // rows are loaded before its entries, so no dependent load is left for the
-// end.  f(r, sum) runs on every lane whose row exists.
-template <typename T, class F>
+// end.  f(r, sum) runs on every lane whose row exists.  STREAM: the entries
+// are loaded with the evict-first hint, so that a matrix larger than L2 does
+// not push the vectors (x and the solver's vectors) out of it.
+template <typename T, bool STREAM, class F>
 __device__ __forceinline__ void sell_rows(const int32_t *__restrict__ sptr,
                                           const int32_t *__restrict__ srow0,
                                           const int32_t *__restrict__ scol,
@@ -353,23 +363,23 @@ __device__ __forceinline__ void sell_rows(const int32_t *__restrict__ sptr,
     const int pend = pi + 32 * ((b1 - b0) >> 6);
     T acc = T(0);
     for (; pi + 32 < pend; pi += 64) {
-      const int2 ca = __ldg(c2 + pi), cb = __ldg(c2 + pi + 32);
-      const P va = __ldg(v2 + pi), vb = __ldg(v2 + pi + 32);
+      const int2 ca = ld_entry<STREAM>(c2 + pi), cb = ld_entry<STREAM>(c2 + pi + 32);
+      const P va = ld_entry<STREAM>(v2 + pi), vb = ld_entry<STREAM>(v2 + pi + 32);
       if (ca.x >= 0) acc = fma_rn(va.x, __ldg(x + ca.x), acc);
       if (ca.y >= 0) acc = fma_rn(va.y, __ldg(x + ca.y), acc);
       if (cb.x >= 0) acc = fma_rn(vb.x, __ldg(x + cb.x), acc);
       if (cb.y >= 0) acc = fma_rn(vb.y, __ldg(x + cb.y), acc);
     }
     if (pi < pend) {
-      const int2 ca = __ldg(c2 + pi);
-      const P va = __ldg(v2 + pi);
+      const int2 ca = ld_entry<STREAM>(c2 + pi);
+      const P va = ld_entry<STREAM>(v2 + pi);
       if (ca.x >= 0) acc = fma_rn(va.x, __ldg(x + ca.x), acc);
       if (ca.y >= 0) acc = fma_rn(va.y, __ldg(x + ca.y), acc);
     }
     if (((b1 - b0) >> 5) & 1) {  // the odd last entry, stored after the pairs
       const int q = b1 - 32 + lane;
-      const int c = __ldg(scol + q);
-      if (c >= 0) acc = fma_rn(__ldg(sval + q), __ldg(x + c), acc);
+      const int c = ld_entry<STREAM>(scol + q);
+      if (c >= 0) acc = fma_rn(ld_entry<STREAM>(sval + q), __ldg(x + c), acc);
     }
     if (r < re) f(r, acc);
   }
@@ -381,10 +391,11 @@ template <typename T, int L, class F>
 __device__ __forceinline__ void row_products(const PcgArgs &a, int b, int r0, int r1,
                                              const T *csr_val, const T *sell_val, const T *x,
                                              F &f) {
-  if constexpr (L == 0)
-    sell_rows<T>(a.sptr, a.srow0, a.scol, sell_val, x, __ldg(a.ta.slice0 + b),
-                 __ldg(a.ta.slice0 + b + 1), f);
-  else
+  if constexpr (L == 0) {
+    const int s0 = __ldg(a.ta.slice0 + b), s1 = __ldg(a.ta.slice0 + b + 1);
+    if (a.stream_matrix) sell_rows<T, true>(a.sptr, a.srow0, a.scol, sell_val, x, s0, s1, f);
+    else sell_rows<T, false>(a.sptr, a.srow0, a.scol, sell_val, x, s0, s1, f);
+  } else
     csr_rows<T, L>(a.row_ptr, a.col, csr_val, x, r0, r1, f);
 }
 

@@ -32,12 +32,14 @@ __global__ void __launch_bounds__(PHASE_TPB) k_spmv(const int32_t *__restrict__ 
 __global__ void __launch_bounds__(PHASE_TPB, SELL_MIN_CTAS)
     k_spmv_sell(const int32_t *__restrict__ sptr, const int32_t *__restrict__ srow0,
                 const int32_t *__restrict__ scol, const double *__restrict__ sval,
-                const double *__restrict__ x, double *__restrict__ y, int32_t nslices) {
+                const double *__restrict__ x, double *__restrict__ y, int32_t nslices,
+                int32_t stream_matrix) {
   auto f = [&](int r, double s) { y[r] = s; };
   const int per = PHASE_TPB / 32;
   for (int64_t s0 = (int64_t)blockIdx.x * per; s0 < nslices; s0 += (int64_t)gridDim.x * per) {
     const int s1 = (int)(s0 + per < nslices ? s0 + per : nslices);
-    sell_rows<double>(sptr, srow0, scol, sval, x, (int)s0, s1, f);
+    if (stream_matrix) sell_rows<double, true>(sptr, srow0, scol, sval, x, (int)s0, s1, f);
+    else sell_rows<double, false>(sptr, srow0, scol, sval, x, (int)s0, s1, f);
   }
 }
 
@@ -48,7 +50,7 @@ int launch_spmv(gbs_mat A, const double *x, double *y, cudaStream_t s) {
     const int64_t ns = A->nslices, per = PHASE_TPB / 32;
     const unsigned grid = (unsigned)std::min<int64_t>((ns + per - 1) / per, 1 << 20);
     k_spmv_sell<<<grid, PHASE_TPB, 0, s>>>(A->sell_ptr, A->sell_row0, A->sell_col, A->sell_val,
-                                           x, y, (int32_t)ns);
+                                           x, y, (int32_t)ns, stream_matrix(A, 12));
     GBS_LAUNCHED(1);
     return GBS_OK;
   }
@@ -63,6 +65,14 @@ int launch_spmv(gbs_mat A, const double *x, double *y, cudaStream_t s) {
   }
   GBS_LAUNCHED(1);
   return GBS_OK;
+}
+
+// 1 when the sliced copy (bytes_per_entry per padded entry) is larger than
+// half of L2: its loads then carry the evict-first hint.
+int32_t stream_matrix(gbs_mat A, int bytes_per_entry) {
+  int l2 = 0;
+  if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, A->device) != cudaSuccess) l2 = 0;
+  return (double)A->sell_nnz * bytes_per_entry > 0.5 * (double)l2 ? 1 : 0;
 }
 
 // Lanes per row from the mean row length: enough lanes that a warp's loads
