@@ -68,6 +68,8 @@ enum { GBS_FP64 = 0, GBS_FP32_REFINED = 1 };
 /* Row-product kernels of a launch plan (mat_set_plan); a positive value n in
  * {1, 2, 4, 8, 32} selects the CSR-vector kernel with n lanes per row. */
 enum { GBS_SPMV_AUTO = -1, GBS_SPMV_SELL = 0 };
+/* Solvers (mat_set_solver). */
+enum { GBS_SOLVER_AUTO = 0, GBS_SOLVER_PHASES = 1, GBS_SOLVER_CTA = 2 };
 
 /* Solver options (host struct).  Fill with ksp_opts_default(), then override. */
 typedef struct {
@@ -100,7 +102,7 @@ typedef struct {
   int32_t status;           /* GBS_OK or the GBS_ERR_* that ended the solve */
   int32_t iterations;       /* products q = A p (refined: total inner ones) */
   int32_t outer_iterations; /* refined: refinement steps; FP64: 0 */
-  int32_t reserved;
+  int32_t solver;           /* GBS_SOLVER_PHASES or GBS_SOLVER_CTA: which ran */
   double rnorm0;            /* ||b - A x0||_2 */
   double rnorm;             /* last recursively updated residual norm
                                (refined: last FP64 outer residual norm) */
@@ -289,6 +291,22 @@ int mat_set_plan(gbs_mat A, int32_t spmv_rows, int32_t update_rows, int32_t kern
                  int32_t ctas_per_sm);
 int mat_get_plan(gbs_mat A, int32_t *spmv_rows, int32_t *update_rows, int32_t *kernel,
                  int32_t *ctas_per_sm, int32_t *spmv_grid);
+
+/*
+ * Which solver runs the solves on A (Sec. 6.1 device-side iteration either
+ * way; both give the same iteration up to reduction order):
+ *   GBS_SOLVER_PHASES: the grid-wide phase kernels in a CUDA graph (SpMV,
+ *     vector update, direction update per iteration), for large systems;
+ *   GBS_SOLVER_CTA: one 1024-thread CTA per system runs every iteration in
+ *     one kernel with CTA barriers only -- the latency path for small systems,
+ *     and for batches of many systems, which then run as concurrent CTAs,
+ *     largest first.  Needs the sliced-ELL plan kernel (GBS_ERR_ARG from the
+ *     solve otherwise); ignores host_loop; ksp_get_phase_ns reports zeros;
+ *   GBS_SOLVER_AUTO (default): CTA when the largest system solved has at
+ *     most 32768 nonzeros, or a batched solve has at least 2 systems per SM.
+ * ksp_result.solver tells which one ran.  No synchronisation.
+ */
+int mat_set_solver(gbs_mat A, int32_t solver);
 int mat_autotune(gbs_mat A, void *stream);
 
 /* Releases every device buffer the handle owns.  Synchronises the device

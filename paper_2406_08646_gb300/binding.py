@@ -25,13 +25,14 @@ ERR_STAGNATION, ERR_TIMEOUT, ERR_LAUNCH = 9, 10, 11
 INSERT, ADD = 0, 1
 FP64, FP32_REFINED = 0, 1
 SPMV_AUTO, SPMV_SELL = -1, 0  # plan kernels; 1, 2, 4, 8, 32 = CSR-vector lanes per row
+SOLVER_AUTO, SOLVER_PHASES, SOLVER_CTA = 0, 1, 2
 
 EXPORTED = ["ksp_opts_default", "mat_create_coo", "mat_create_coo_batched",
             "mat_set_values_coo", "mat_mult", "ksp_solve_cg", "ksp_solve_cg_batched",
             "ksp_adjoint", "ksp_adjoint_batched", "ksp_get_result", "mat_get_info",
             "mat_get_csr", "mat_get_coo_maps", "mat_set_plan", "mat_get_plan",
             "mat_autotune", "mat_destroy", "gbs_launch_count", "gbs_last_error",
-            "ksp_solve_cg_noalloc", "ksp_get_phase_ns"]
+            "ksp_solve_cg_noalloc", "ksp_get_phase_ns", "mat_set_solver"]
 
 
 class KspOpts(ctypes.Structure):
@@ -44,12 +45,12 @@ class KspOpts(ctypes.Structure):
 
 class KspResult(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32),
-                ("outer_iterations", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("outer_iterations", ctypes.c_int32), ("solver", ctypes.c_int32),
                 ("rnorm0", ctypes.c_double), ("rnorm", ctypes.c_double),
                 ("true_rel_residual", ctypes.c_double)]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class GbsError(RuntimeError):
@@ -94,6 +95,7 @@ def lib() -> ctypes.CDLL:
         "gbs_last_error": (ctypes.c_char_p, []),
         "ksp_solve_cg_noalloc": (ctypes.c_int, [I64, P, P, P, P, P, P, P, P]),
         "ksp_get_phase_ns": (ctypes.c_int, [P, P, P]),
+        "mat_set_solver": (ctypes.c_int, [P, I32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -299,6 +301,10 @@ def mat_get_plan(A) -> dict:
                     [t.value for t in v]))
 
 
+def mat_set_solver(A, solver: int):
+    _check(lib().mat_set_solver(A, solver))
+
+
 def mat_autotune(A, stream=None):
     _check(lib().mat_autotune(A, _stream(stream)))
 
@@ -379,6 +385,9 @@ class Mat:
 
     def plan(self) -> dict:
         return mat_get_plan(self.h)
+
+    def set_solver(self, solver: int):
+        mat_set_solver(self.h, solver)
 
     def phase_ns(self) -> dict:
         return ksp_get_phase_ns(self.h)

@@ -35,7 +35,7 @@ static void free_handle(gbs_mat A) {
   drop_graphs(A);
   void *dev[] = {A->row_ptr, A->col, A->val, A->val32, A->perm, A->jmap, A->diag_pos,
                  A->dinv, A->dinv32, A->r, A->p, A->q, A->r32, A->p32, A->q32, A->d32,
-                 A->part, A->sys_cnt, A->st, A->ctl, A->call};
+                 A->part, A->sys_cnt, A->st, A->ctl, A->call, A->cta_order};
   for (void *p : dev)
     if (p) cudaFree(p);
   free_table(A->ta);
@@ -347,6 +347,16 @@ int mat_set_plan(gbs_mat A, int32_t spmv_rows, int32_t update_rows, int32_t kern
   GBS_TRY(use_device(A));
   GBS_TRY_CUDA(cudaDeviceSynchronize());  // the old tables may be in use
   return build_plan(A, spmv_rows, update_rows, kernel, ctas_per_sm);
+}
+
+int mat_set_solver(gbs_mat A, int32_t solver) {
+  GBS_TRY(check_mat(A, "mat_set_solver"));
+  if (solver != GBS_SOLVER_AUTO && solver != GBS_SOLVER_PHASES && solver != GBS_SOLVER_CTA) {
+    set_error("mat_set_solver: solver must be GBS_SOLVER_AUTO, _PHASES or _CTA");
+    return GBS_ERR_ARG;
+  }
+  A->solver = solver;
+  return GBS_OK;
 }
 
 int mat_get_plan(gbs_mat A, int32_t *spmv_rows, int32_t *update_rows, int32_t *kernel,

@@ -142,6 +142,9 @@ struct gbs_mat_s {
   int32_t Ra = 256, Re = 512;   // rows per SpMV block / per update block
   int32_t lanes = 0;
   int32_t ctas_per_sm = 0;      // grid cap per SM, 0 = as many as fit (one wave)
+  int32_t solver = 0;           // GBS_SOLVER_AUTO / PHASES / CTA
+  int32_t *cta_order = nullptr; // nsys: systems by decreasing rows (per-CTA solver)
+  int64_t max_sys_rows = 0, max_sys_nnz = 0;
 
   // solver workspace (device, allocated on first solve)
   double *r = nullptr, *p = nullptr, *q = nullptr;
@@ -156,6 +159,7 @@ struct gbs_mat_s {
   int32_t last_count = 0;            // systems in the last solve's result
   bool last_ensemble = false;
   bool trips_counted = true;         // launch counter already holds the last loop
+  int32_t last_solver = 0;           // solver the last solve ran
 
   // cached executable graphs [refined][per_system] of the solve loop
   cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};

@@ -30,6 +30,7 @@
 
 #include "device_util.cuh"
 #include "internal.cuh"
+#include "cta.cuh"
 #include "phases.cuh"
 
 namespace gbs {
@@ -88,7 +89,12 @@ __global__ void GBS_ROWS_BOUNDS(L) k_pcg_final(PcgArgs a) {
     a.ctl->phase_ns[4] += (int64_t)global_ns() - a.ctl->stamp;
 }
 
-__global__ void k_put_call(CallArgs *dst, CallArgs v) { *dst = v; }
+// Writes the call arguments; with ctl, also stamps the solve's start (the
+// per-CTA solver's time limit counts from it).
+__global__ void k_put_call(CallArgs *dst, CallArgs v, DevCtl *ctl) {
+  *dst = v;
+  if (ctl) ctl->t_start = (int64_t)global_ns();
+}
 
 struct PhaseKernels {
   void (*setup)(PcgArgs);
@@ -209,8 +215,8 @@ static CallArgs call_args(const double *b, double *x, const ksp_opts &o) {
   return c;
 }
 
-static int put_call(CallArgs *dst, const CallArgs &c, cudaStream_t s) {
-  k_put_call<<<1, 1, 0, s>>>(dst, c);
+static int put_call(CallArgs *dst, const CallArgs &c, cudaStream_t s, DevCtl *ctl = nullptr) {
+  k_put_call<<<1, 1, 0, s>>>(dst, c, ctl);
   GBS_LAUNCHED(1);
   return GBS_OK;
 }
@@ -366,6 +372,22 @@ static int run_stepped(const PhaseKernels &K, PcgArgs a, int grid_a, int grid_e,
   return GBS_OK;
 }
 
+// The per-CTA solver takes systems small enough that one SM iterates them
+// faster than the phase kernels' launch and reduction latency allows (a CTA
+// has one SM's FP64 rate, 2 FMAs per clock: about 16k nonzeros per
+// iteration match the ~20 us a phase-kernel iteration costs at any size),
+// and batches with enough systems to fill every SM with CTAs.
+constexpr int64_t CTA_AUTO_NNZ = 32768;
+
+static bool use_cta_solver(gbs_mat A, bool per_system) {
+  if (A->solver == GBS_SOLVER_CTA) return true;
+  if (A->solver == GBS_SOLVER_PHASES || A->lanes != GBS_SPMV_SELL) return false;
+  int nsm = 1;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, A->device);
+  const int64_t nz = per_system ? A->max_sys_nnz : A->nnz;
+  return nz <= CTA_AUTO_NNZ || (per_system && A->nsys >= 2 * nsm);
+}
+
 int solve(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool per_system,
           cudaStream_t s) {
   const bool refined = o.precision == GBS_FP32_REFINED;
@@ -374,9 +396,26 @@ int solve(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool per_sys
   A->last_count = per_system ? A->nsys : 1;
   A->last_ensemble = !per_system;
   A->trips_counted = true;
+  A->last_solver = GBS_SOLVER_PHASES;
   if (A->ta.nblocks == 0) {  // empty matrix: nothing to iterate
     GBS_TRY_CUDA(cudaMemsetAsync(A->st, 0, sizeof(SysState) * A->nsys, s));
     GBS_TRY_CUDA(cudaMemsetAsync(A->ctl, 0, sizeof(DevCtl), s));
+    return GBS_OK;
+  }
+  if (use_cta_solver(A, per_system)) {
+    if (A->lanes != GBS_SPMV_SELL) {
+      set_error("the per-CTA solver needs the sliced-ELL row products (plan kernel)");
+      return GBS_ERR_ARG;
+    }
+    A->last_solver = GBS_SOLVER_CTA;
+    GBS_TRY_CUDA(cudaMemsetAsync(A->ctl, 0, sizeof(DevCtl), s));
+    GBS_TRY(put_call(A->call, call_args(b, x, o), s, A->ctl));
+    PcgArgs a = make_args(A, per_system, refined);
+    a.order = per_system ? A->cta_order : nullptr;
+    const unsigned grid = per_system ? (unsigned)A->nsys : 1u;
+    if (refined) k_cta_pcg<true><<<grid, CTA_TPB, 0, s>>>(a);
+    else k_cta_pcg<false><<<grid, CTA_TPB, 0, s>>>(a);
+    GBS_LAUNCHED(1);
     return GBS_OK;
   }
   if (o.host_loop) {
@@ -421,7 +460,7 @@ int read_results(gbs_mat A, ksp_result *res, int32_t count, cudaStream_t s) {
     if (S.active) R.status = ctl.err ? ctl.err : GBS_ERR_MAXIT;  // stopped early
     R.iterations = S.iterations;
     R.outer_iterations = S.outer;
-    R.reserved = 0;
+    R.solver = A->last_solver;
     R.rnorm0 = S.rnorm0;
     R.rnorm = S.rnorm;
     const double bn = sqrt(S.bb);
@@ -612,7 +651,7 @@ extern "C" int ksp_solve_cg_noalloc(int64_t n, const int32_t *row_ptr, const int
   res->status = st.active ? (ctl.err ? ctl.err : GBS_ERR_MAXIT) : st.status;
   res->iterations = st.iterations;
   res->outer_iterations = 0;
-  res->reserved = 0;
+  res->solver = GBS_SOLVER_PHASES;
   res->rnorm0 = st.rnorm0;
   res->rnorm = st.rnorm;
   const double bn = sqrt(st.bb);

@@ -36,8 +36,8 @@ namespace gbs {
 
 enum { M_INNER = 0, M_XUPD = 1, M_START = 2 };
 constexpr int SLOT_STRIDE = 4;  // doubles per reduction slot
-constexpr int PHASE_TPB = 256;  // threads per CTA of every phase kernel
-constexpr int SELL_MIN_CTAS = 8;  // sliced-ELL kernels: 8 CTAs (2048 threads) per SM
+constexpr int PHASE_TPB = 512;  // threads per CTA of every phase kernel
+constexpr int SELL_MIN_CTAS = 4;  // sliced-ELL kernels: 4 CTAs (2048 threads) per SM
 
 // A table of work blocks: rows [row0[b], row0[b+1]) of system sys[b].
 struct BlockTable {
@@ -70,6 +70,7 @@ struct PcgArgs {
   SysState *st;
   DevCtl *ctl;
   const CallArgs *call;
+  const int32_t *order;             // per-CTA solver: system of each CTA (largest first)
   cudaGraphConditionalHandle cond;  // loop condition of the graph (stepped == 0)
   int32_t stepped;                  // 1: loop trips launched by the host
   int32_t trip;                     // stepped: index of this trip
@@ -317,6 +318,14 @@ struct Vals {
   T v[N];
 };
 
+// Gather of x: the read-only path when NC, else a plain (L1-cached, coherent
+// within the CTA) load.
+template <bool NC, typename T>
+__device__ __forceinline__ T ld_x(const T *p) {
+  if constexpr (NC) return __ldg(p);
+  else return __ldca(p);
+}
+
 // Read-only load of a matrix entry, evict-first when STREAM.
 template <bool STREAM, typename T>
 __device__ __forceinline__ T ld_entry(const T *p) {
@@ -344,12 +353,14 @@ struct Pair<float> {
 // rows are loaded before its entries, so no dependent load is left for the
 // end.  f(r, sum) runs on every lane whose row exists.  STREAM: the entries
 // are loaded with the evict-first hint, so that a matrix larger than L2 does
-// not push the vectors (x and the solver's vectors) out of it.
-template <typename T, bool STREAM, class F>
+// not push the vectors (x and the solver's vectors) out of it.  NC: x is not
+// written during the kernel, so its gathers may take the read-only path;
+// false where the same CTA wrote x before a __syncthreads.
+template <typename T, bool STREAM, bool NC, class F>
 __device__ __forceinline__ void sell_rows(const int32_t *__restrict__ sptr,
                                           const int32_t *__restrict__ srow0,
                                           const int32_t *__restrict__ scol,
-                                          const T *__restrict__ sval, const T *__restrict__ x,
+                                          const T *__restrict__ sval, const T *x,
                                           int s0, int s1, F &f) {
   typedef typename Pair<T>::type P;
   const int2 *__restrict__ c2 = reinterpret_cast<const int2 *>(scol);
@@ -365,21 +376,21 @@ __device__ __forceinline__ void sell_rows(const int32_t *__restrict__ sptr,
     for (; pi + 32 < pend; pi += 64) {
       const int2 ca = ld_entry<STREAM>(c2 + pi), cb = ld_entry<STREAM>(c2 + pi + 32);
       const P va = ld_entry<STREAM>(v2 + pi), vb = ld_entry<STREAM>(v2 + pi + 32);
-      if (ca.x >= 0) acc = fma_rn(va.x, __ldg(x + ca.x), acc);
-      if (ca.y >= 0) acc = fma_rn(va.y, __ldg(x + ca.y), acc);
-      if (cb.x >= 0) acc = fma_rn(vb.x, __ldg(x + cb.x), acc);
-      if (cb.y >= 0) acc = fma_rn(vb.y, __ldg(x + cb.y), acc);
+      if (ca.x >= 0) acc = fma_rn(va.x, ld_x<NC>(x + ca.x), acc);
+      if (ca.y >= 0) acc = fma_rn(va.y, ld_x<NC>(x + ca.y), acc);
+      if (cb.x >= 0) acc = fma_rn(vb.x, ld_x<NC>(x + cb.x), acc);
+      if (cb.y >= 0) acc = fma_rn(vb.y, ld_x<NC>(x + cb.y), acc);
     }
     if (pi < pend) {
       const int2 ca = ld_entry<STREAM>(c2 + pi);
       const P va = ld_entry<STREAM>(v2 + pi);
-      if (ca.x >= 0) acc = fma_rn(va.x, __ldg(x + ca.x), acc);
-      if (ca.y >= 0) acc = fma_rn(va.y, __ldg(x + ca.y), acc);
+      if (ca.x >= 0) acc = fma_rn(va.x, ld_x<NC>(x + ca.x), acc);
+      if (ca.y >= 0) acc = fma_rn(va.y, ld_x<NC>(x + ca.y), acc);
     }
     if (((b1 - b0) >> 5) & 1) {  // the odd last entry, stored after the pairs
       const int q = b1 - 32 + lane;
       const int c = ld_entry<STREAM>(scol + q);
-      if (c >= 0) acc = fma_rn(ld_entry<STREAM>(sval + q), __ldg(x + c), acc);
+      if (c >= 0) acc = fma_rn(ld_entry<STREAM>(sval + q), ld_x<NC>(x + c), acc);
     }
     if (r < re) f(r, acc);
   }
@@ -393,8 +404,8 @@ __device__ __forceinline__ void row_products(const PcgArgs &a, int b, int r0, in
                                              F &f) {
   if constexpr (L == 0) {
     const int s0 = __ldg(a.ta.slice0 + b), s1 = __ldg(a.ta.slice0 + b + 1);
-    if (a.stream_matrix) sell_rows<T, true>(a.sptr, a.srow0, a.scol, sell_val, x, s0, s1, f);
-    else sell_rows<T, false>(a.sptr, a.srow0, a.scol, sell_val, x, s0, s1, f);
+    if (a.stream_matrix) sell_rows<T, true, true>(a.sptr, a.srow0, a.scol, sell_val, x, s0, s1, f);
+    else sell_rows<T, false, true>(a.sptr, a.srow0, a.scol, sell_val, x, s0, s1, f);
   } else
     csr_rows<T, L>(a.row_ptr, a.col, csr_val, x, r0, r1, f);
 }

@@ -10,10 +10,10 @@
 
 namespace gbs {
 
-constexpr int SPMV_ROWS = 256;  // rows per CTA pass of the standalone SpMV
+constexpr int SPMV_ROWS = PHASE_TPB;  // rows per CTA pass of the CSR-vector SpMV (32 per warp)
 
 // y = A x with the CSR-vector row product of the solves (csr_rows), over
-// 256-row chunks.
+// chunks of 32 rows per warp.
 template <int L>
 __global__ void __launch_bounds__(PHASE_TPB) k_spmv(const int32_t *__restrict__ row_ptr,
                                                     const int32_t *__restrict__ col,
@@ -38,8 +38,8 @@ __global__ void __launch_bounds__(PHASE_TPB, SELL_MIN_CTAS)
   const int per = PHASE_TPB / 32;
   for (int64_t s0 = (int64_t)blockIdx.x * per; s0 < nslices; s0 += (int64_t)gridDim.x * per) {
     const int s1 = (int)(s0 + per < nslices ? s0 + per : nslices);
-    if (stream_matrix) sell_rows<double, true>(sptr, srow0, scol, sval, x, (int)s0, s1, f);
-    else sell_rows<double, false>(sptr, srow0, scol, sval, x, (int)s0, s1, f);
+    if (stream_matrix) sell_rows<double, true, true>(sptr, srow0, scol, sval, x, (int)s0, s1, f);
+    else sell_rows<double, false, true>(sptr, srow0, scol, sval, x, (int)s0, s1, f);
   }
 }
 
@@ -146,6 +146,43 @@ static int build_table(gbs_mat A, int32_t R, int32_t cap_per_sm, TableDev &t) {
   return GBS_OK;
 }
 
+// nnz_off[q] = row_ptr[first row of system q] (q = 0 .. nsys).
+__global__ void k_system_nnz(int32_t nsys, const int32_t *__restrict__ row_ptr,
+                             const int32_t *__restrict__ row0,
+                             const int32_t *__restrict__ sys_blk0, int32_t *__restrict__ nnz_off) {
+  const int32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q <= nsys) nnz_off[q] = row_ptr[row0[sys_blk0[q]]];
+}
+
+// Systems in decreasing row count (ties by index): the per-CTA solver hands
+// them to CTAs in this order, so the longest solves start first.  Also the
+// largest system's rows and nonzeros (the solver choice uses them).
+static int build_cta_order(gbs_mat A) {
+  std::vector<int32_t> ord(A->nsys), noff(A->nsys + 1, 0);
+  int32_t *d = nullptr;
+  GBS_TRY_CUDA(cudaMalloc(&d, sizeof(int32_t) * (A->nsys + 1)));
+  k_system_nnz<<<(A->nsys + 256) / 256, 256>>>(A->nsys, A->row_ptr, A->ta.row0, A->ta.sys_blk0, d);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpy(noff.data(), d, sizeof(int32_t) * (A->nsys + 1), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  count_launches(1);
+  GBS_TRY_CUDA(e);
+  A->max_sys_rows = A->max_sys_nnz = 0;
+  for (int32_t q = 0; q < A->nsys; ++q) {
+    ord[q] = q;
+    A->max_sys_rows = std::max(A->max_sys_rows, A->row_off_h[q + 1] - A->row_off_h[q]);
+    A->max_sys_nnz = std::max<int64_t>(A->max_sys_nnz, noff[q + 1] - noff[q]);
+  }
+  std::stable_sort(ord.begin(), ord.end(), [&](int32_t u, int32_t v) {
+    return A->row_off_h[u + 1] - A->row_off_h[u] > A->row_off_h[v + 1] - A->row_off_h[v];
+  });
+  if (!A->cta_order) GBS_TRY_CUDA(cudaMalloc(&A->cta_order, sizeof(int32_t) * A->nsys));
+  GBS_TRY_CUDA(cudaMemcpy(A->cta_order, ord.data(), sizeof(int32_t) * A->nsys,
+                          cudaMemcpyHostToDevice));
+  return GBS_OK;
+}
+
 // Plan: SpMV-phase blocks of Ra rows, update-phase blocks of Re rows (both
 // multiples of 32), the row-product kernel (GBS_SPMV_AUTO, GBS_SPMV_SELL or
 // CSR-vector lanes per row) and a cap of CTAs per SM on the grids (0: as many
@@ -177,8 +214,8 @@ int build_plan(gbs_mat A, int32_t Ra, int32_t Re, int32_t kernel, int32_t ctas_p
     GBS_TRY_CUDA(cudaDeviceSynchronize());
   }
   // grids: one wave of the phase kernels unless capped explicitly; automatic
-  // block sizes give about one block per CTA of that wave (at least 256 rows,
-  // so every warp of a CTA has rows)
+  // block sizes give about one block per CTA of that wave (at least one row
+  // per thread, so every warp of a CTA has rows)
   int occ_rows = 1, occ_upd = 1, nsm = 1;
   GBS_TRY(phase_occupancy(kernel, &occ_rows, &occ_upd));
   GBS_TRY_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, A->device));
@@ -186,12 +223,13 @@ int build_plan(gbs_mat A, int32_t Ra, int32_t Re, int32_t kernel, int32_t ctas_p
   const int cap_e = ctas_per_sm ? ctas_per_sm : occ_upd;
   auto auto_rows = [&](int cap) {
     const int64_t per = (A->nrows + (int64_t)cap * nsm - 1) / ((int64_t)cap * nsm);
-    return (int32_t)std::min<int64_t>(65536, std::max<int64_t>(256, (per + 31) / 32 * 32));
+    return (int32_t)std::min<int64_t>(65536, std::max<int64_t>(PHASE_TPB, (per + 31) / 32 * 32));
   };
   if (Ra == 0) Ra = auto_rows(cap_a);
   if (Re == 0) Re = auto_rows(cap_e);
   GBS_TRY(build_table(A, Ra, cap_a, A->ta));
   GBS_TRY(build_table(A, Re, cap_e, A->te));
+  GBS_TRY(build_cta_order(A));
   A->Ra = Ra;
   A->Re = Re;
   A->lanes = kernel;

@@ -173,6 +173,10 @@ def iters_close(a, b):
     return abs(a - b) <= max(2, int(np.ceil(0.01 * max(a, b))))
 
 
+SOLVERS = [B.SOLVER_PHASES, B.SOLVER_CTA]
+
+
+@pytest.mark.parametrize("solver", SOLVERS)
 @pytest.mark.parametrize("name,make,rtol", [
     ("c1_poisson2d_64", lambda: W.poisson2d(64), 1e-8),
     ("c2_q1hex_12", lambda: W.q1_hex(12, seed=W.SEED_C2), 1e-8),
@@ -180,10 +184,12 @@ def iters_close(a, b):
     ("c4_edge_32", lambda: W.edge_diffusion(32, seed=W.SEED_C4_SMALL), 1e-8),
     ("edge_300", lambda: W.edge_diffusion(300, seed=9), 1e-8),
 ])
-def test_pcg_fp64_parity(name, make, rtol):
+def test_pcg_fp64_parity(name, make, rtol, solver):
     p = make()
     A, O = assemble_both(p.nrows, p.ncols, p.i, p.j, p.v)
+    A.set_solver(solver)
     x, r = A.solve(t(p.b), rtol=rtol)
+    assert r["solver"] == solver
     xo, ro = oracle.pcg(O, p.b, rtol=rtol)
     xg = x.cpu().numpy()
     assert r["status"] == B.OK and ro["status"] == oracle.OK
@@ -210,11 +216,13 @@ def test_host_loop_matches_graph(precision):
     graph: results are bit-identical, single and batched."""
     p = W.q1_hex(9, seed=23)
     A, O = assemble_both(p.nrows, p.ncols, p.i, p.j, p.v)
+    A.set_solver(B.SOLVER_PHASES)
     x1, r1 = A.solve(t(p.b), rtol=1e-10, precision=precision)
     x2, r2 = A.solve(t(p.b), rtol=1e-10, precision=precision, host_loop=True)
     assert r1["status"] == B.OK and torch.equal(x1, x2) and r1 == r2
     A.close()
     bt, A, O = make_batch(12, 45, 100, 2000)
+    A.set_solver(B.SOLVER_PHASES)
     x1, r1 = A.solve_batched(t(bt.b), rtol=1e-9, precision=precision)
     x2, r2 = A.solve_batched(t(bt.b), rtol=1e-9, precision=precision, host_loop=True)
     assert all(q["status"] == B.OK for q in r1) and torch.equal(x1, x2) and r1 == r2
@@ -285,12 +293,14 @@ def test_pcg_error_paths_return_status():
     assert r["status"] == B.OK
 
 
-def test_time_limit_is_reported():
+@pytest.mark.parametrize("solver", SOLVERS)
+def test_time_limit_is_reported(solver):
     """A 1 ns wall-clock limit runs out after the first iteration: the device
     ends the loop, the solve reports GBS_ERR_TIMEOUT with x finite, and the
-    next solve on the same graph is unaffected."""
+    next solve on the same handle is unaffected."""
     p = W.poisson3d(16, seed=3)
     A, O = assemble_both(p.nrows, p.ncols, p.i, p.j, p.v)
+    A.set_solver(solver)
     x, r = A.solve(t(p.b), timeout_ns=1)
     assert r["status"] == B.ERR_TIMEOUT and r["iterations"] == 1
     assert torch.isfinite(x).all()
@@ -301,12 +311,14 @@ def test_time_limit_is_reported():
 
 # ------------------------------------------------------------------ FP32-refined
 
+@pytest.mark.parametrize("solver", SOLVERS)
 @pytest.mark.parametrize("make,rtol", [(lambda: W.q1_hex(10, seed=31), 1e-10),
                                        (lambda: W.poisson3d(24, seed=W.SEED_C3), 1e-10),
                                        (lambda: W.edge_diffusion(64, seed=32), 1e-8)])
-def test_refined_parity(make, rtol):
+def test_refined_parity(make, rtol, solver):
     p = make()
     A, O = assemble_both(p.nrows, p.ncols, p.i, p.j, p.v)
+    A.set_solver(solver)
     x, r = A.solve(t(p.b), rtol=rtol, precision=B.FP32_REFINED, inner_rtol=1e-4)
     xo, ro = oracle.pcg_refined(O, p.b, rtol=rtol, inner_rtol=1e-4)
     assert r["status"] == B.OK and ro["status"] == oracle.OK
@@ -319,9 +331,11 @@ def test_refined_parity(make, rtol):
     A.close()
 
 
-def test_refined_stagnation_and_maxit():
+@pytest.mark.parametrize("solver", SOLVERS)
+def test_refined_stagnation_and_maxit(solver):
     p = W.poisson3d(10, seed=14)
     A, O = assemble_both(p.nrows, p.ncols, p.i, p.j, p.v)
+    A.set_solver(solver)
     x, r = A.solve(t(p.b), rtol=1e-10, precision=B.FP32_REFINED, inner_rtol=0.9, inner_maxit=1)
     assert r["status"] == B.ERR_STAGNATION
     x, r = A.solve(t(p.b), rtol=1e-10, precision=B.FP32_REFINED, max_outer=1)
@@ -401,9 +415,11 @@ def make_batch(nsys, seed, lo, hi):
     return bt, A, O
 
 
+@pytest.mark.parametrize("solver", SOLVERS)
 @pytest.mark.parametrize("precision", [B.FP64, B.FP32_REFINED])
-def test_batched_parity(precision):
+def test_batched_parity(precision, solver):
     bt, A, O = make_batch(24, 41, 100, 6000)
+    A.set_solver(solver)
     rp, col, val = (x.cpu().numpy() for x in A.csr())
     assert np.array_equal(rp, O.row_ptr) and np.array_equal(col, O.col)
     assert val.tobytes() == O.val.tobytes()
@@ -445,12 +461,35 @@ def test_batched_adjoint_and_ensemble():
 def test_launch_counter_and_phase_timers():
     p = W.poisson3d(12, seed=4)
     A, O = assemble_both(p.nrows, p.ncols, p.i, p.j, p.v)
+    A.set_solver(B.SOLVER_PHASES)
     c0 = B.launch_count()
     x, r = A.solve(t(p.b))
     # call-argument kernel + setup + final, and three kernels per iteration
     assert B.launch_count() == c0 + 3 + 3 * r["iterations"]
     ph = A.phase_ns()
     assert all(v > 0 for v in ph.values()), ph
+    # the per-CTA solver: the call-argument kernel and one solver kernel
+    A.set_solver(B.SOLVER_CTA)
+    c0 = B.launch_count()
+    x2, r2 = A.solve(t(p.b))
+    assert B.launch_count() == c0 + 2 and r2["solver"] == B.SOLVER_CTA
+    assert iters_close(r2["iterations"], r["iterations"])
+    A.close()
+
+
+def test_solver_auto_choice_and_determinism():
+    p = W.poisson2d(64)
+    A, O = assemble_both(p.nrows, p.ncols, p.i, p.j, p.v)
+    x, r = A.solve(t(p.b), rtol=1e-10)
+    assert r["solver"] == B.SOLVER_CTA            # 4096 rows: the latency path
+    x2, r2 = A.solve(t(p.b), rtol=1e-10)
+    assert torch.equal(x, x2) and r2 == r
+    A.close()
+    p = W.q1_hex(16, seed=6)                       # 117,649 nonzeros: the phase kernels
+    A, O = assemble_both(p.nrows, p.ncols, p.i, p.j, p.v)
+    x, r = A.solve(t(p.b), rtol=1e-8)
+    assert r["solver"] == B.SOLVER_PHASES and r["status"] == B.OK
+    assert true_rel(O, p.b, x.cpu().numpy()) <= 1.05e-8
     A.close()
 
 
