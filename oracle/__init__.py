@@ -70,6 +70,8 @@ def _load():
         lib.orc_coo_numeric.argtypes = [I64, P, P, P, ctypes.c_int, P]
         lib.orc_coo_scatter.restype = None
         lib.orc_coo_scatter.argtypes = [I64, I64, P, P, P, P]
+        lib.orc_vec_set_values_coo.restype = I64
+        lib.orc_vec_set_values_coo.argtypes = [I64, I64, P, P, ctypes.c_int, P]
         lib.orc_spmv.restype = None
         lib.orc_spmv.argtypes = [I64, P, P, P, P, P]
         lib.orc_pcg.restype = ctypes.c_int
@@ -169,6 +171,20 @@ def coo_scatter(A: CSR, dlda) -> np.ndarray:
     out = np.zeros(A.ncoo, np.float64)
     lib.orc_coo_scatter(A.nnz, A.ncoo, _p(A.jmap), _p(A.perm), _p(dlda), _p(out))
     return out
+
+
+def vec_set_values_coo(n: int, i, v, mode: int = INSERT, y=None) -> np.ndarray:
+    """Sec. 5 COO interface for vectors: y_r = in-order sum of v[k] with
+    i[k] = r (INSERT), or y_r + that sum (ADD); other entries of y unchanged."""
+    lib = _load()
+    i = _c(i, np.int32)
+    v = _c(v, np.float64)
+    assert v.shape[0] == i.shape[0]
+    y = np.zeros(n, np.float64) if y is None else _c(y, np.float64).copy()
+    st = lib.orc_vec_set_values_coo(n, i.shape[0], _p(i), _p(v), mode, _p(y))
+    if st < 0:
+        raise OracleError(int(-st), "vec_set_values_coo")
+    return y
 
 
 def spmv(A: CSR, x) -> np.ndarray:

@@ -27,6 +27,9 @@
  *       linear solve: A^T lambda = g, dL/da_ij = -lambda_i x_j, dL/db = lambda.
  *   orc_pcg_batched    -- Sec. 7: many independent systems, each solved on its
  *       own (per-system scalars and convergence).
+ *   orc_vec_set_values_coo -- Sec. 5's COO interface for vectors
+ *       (VecSetPreallocationCOO / VecSetValuesCOO): y_r is the sum of the
+ *       contributions v[k] with i[k] = r.
  *
  * Parity pins: every function here is pinned by tests/test_oracle_*.py against
  * dense brute force, closed forms (Laplacian eigenpairs, the Q1 stencil),
@@ -148,6 +151,44 @@ void orc_coo_scatter(int64_t nnz, int64_t ncoo, const int32_t *jmap,
   for (int64_t k = 0; k < ncoo; ++k) dldv[k] = 0.0;
   for (int64_t p = 0; p < nnz; ++p)
     for (int64_t t = jmap[p]; t < jmap[p + 1]; ++t) dldv[perm[t]] = dlda[p];
+}
+
+/*
+ * Vector COO assembly, straight from the definition: for every index r that
+ * appears among the kept entries (i[k] >= 0), acc_r is the left fold of its
+ * v[k] in increasing k starting from the first term; INSERT (mode 0) sets
+ * y[r] = acc_r, ADD (mode 1) sets y[r] = y[r] + acc_r; indices that do not
+ * appear leave y[r] unchanged.  An index >= n is an error (-ORC_ERR_INDEX).
+ * Returns the number of distinct indices.
+ */
+int64_t orc_vec_set_values_coo(int64_t n, int64_t ncoo, const int32_t *ci, const double *v,
+                               int mode, double *y) {
+  for (int64_t k = 0; k < ncoo; ++k)
+    if (ci[k] >= 0 && (int64_t)ci[k] >= n) return -ORC_ERR_INDEX;
+  double *acc = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+  unsigned char *seen = (unsigned char *)calloc((size_t)(n > 0 ? n : 1), 1);
+  if (!acc || !seen) {
+    free(acc);
+    free(seen);
+    return -ORC_ERR_ALLOC;
+  }
+  int64_t distinct = 0;
+  for (int64_t k = 0; k < ncoo; ++k) {
+    if (ci[k] < 0) continue;
+    const int64_t r = ci[k];
+    if (!seen[r]) {
+      seen[r] = 1;
+      acc[r] = v[k];
+      ++distinct;
+    } else {
+      acc[r] = acc[r] + v[k];
+    }
+  }
+  for (int64_t r = 0; r < n; ++r)
+    if (seen[r]) y[r] = (mode == 1) ? y[r] + acc[r] : acc[r];
+  free(acc);
+  free(seen);
+  return distinct;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -175,3 +175,48 @@ def test_hand_worked_example():
     assert A.val.tolist() == ex["val"]
     assert A.perm.tolist() == ex["perm"]
     assert A.jmap.tolist() == ex["jmap"]
+
+
+# ------------------------------------------------------------------ vectors
+
+@pytest.mark.parametrize("seed", range(4))
+def test_vec_coo_equals_matrix_route_and_dense_sum(seed):
+    """Vector COO assembly (Sec. 5 for vectors) pinned two other ways: the
+    matrix assembly of the same entries as an n x 1 matrix (sort route), and,
+    for integer values, a dense np.add.at accumulate; ADD adds to y, indices
+    that do not appear keep y."""
+    rng = np.random.default_rng(100 + seed)
+    n, ncoo = 97, 2000
+    i, _, v = random_coo(rng, n, ncoo)
+    y0 = rng.standard_normal(n)
+    A = oracle.coo_symbolic(n, 1, i, np.zeros_like(i))
+    a = oracle.coo_numeric(A, v)
+    rows = np.repeat(np.arange(n), np.diff(A.row_ptr))
+    yi = oracle.vec_set_values_coo(n, i, v, oracle.INSERT, y0)
+    exp = y0.copy()
+    exp[rows] = a
+    assert yi.tobytes() == exp.tobytes()
+    ya = oracle.vec_set_values_coo(n, i, v, oracle.ADD, y0)
+    exp = y0.copy()
+    exp[rows] = y0[rows] + a
+    assert ya.tobytes() == exp.tobytes()
+    iv = rng.integers(-8, 9, ncoo).astype(np.float64)
+    dense = np.zeros(n)
+    keep = i >= 0
+    np.add.at(dense, i[keep], iv[keep])
+    got = oracle.vec_set_values_coo(n, i, iv, oracle.ADD, np.zeros(n))
+    assert np.array_equal(got, dense)
+
+
+def test_vec_coo_order_and_errors():
+    # the fold starts from the first term: a lone -0.0 stays -0.0, and the
+    # order is increasing COO index (1e16 + 1 - 1e16 = 0, but 1e16 - 1e16 + 1 = 1)
+    y = oracle.vec_set_values_coo(3, np.array([2, 0, 0, 0], np.int32),
+                                  np.array([-0.0, 1e16, 1.0, -1e16]), oracle.INSERT,
+                                  np.array([5.0, 6.0, 7.0]))
+    assert np.signbit(y[2]) and y[2] == 0.0 and y[1] == 6.0 and y[0] == 0.0
+    y = oracle.vec_set_values_coo(2, np.array([0, 0, 0], np.int32),
+                                  np.array([1e16, -1e16, 1.0]), oracle.INSERT)
+    assert y[0] == 1.0
+    with pytest.raises(oracle.OracleError):
+        oracle.vec_set_values_coo(2, np.array([2], np.int32), np.array([1.0]))
