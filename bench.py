@@ -26,9 +26,11 @@ prints its own JSON line; the default is the Q1 benchmark above):
       rtol 1e-10 and 1e-8 (true residuals reported)
   c4  2D edge diffusion 1024^2: forward FP64 solve vs adjoint solve + gradient
       scatter, and dL/dkappa through the edge signs
-  c5  512 independent systems (~51.6M rows): one batched graph launch (FP64
-      and refined) vs 512 sequential single-system solves vs the stacked
-      ensemble solve, plus the batched adjoint
+  c5  512 independent systems (~51.6M rows): one batched launch (FP64 and
+      refined) vs 512 sequential single-system solves vs the stacked ensemble
+      solve, plus the batched adjoint
+  vec vector COO assembly of the Q1 96^3 element load vector (7.08M entries
+      into 912,673 nodes): symbolic and numeric stage times, numeric GB/s
 
 --impl reference times the FP64 CPU oracle (the plain C implementation in
 oracle/) on a bounded sample of the same workload on the host cores.
@@ -325,6 +327,27 @@ def run_suite(args):
              "grad_norms": {"dL/db": float(lam.norm()), "dL/dkappa": float(gk.norm())}})
         print(json.dumps(line), flush=True)
         A.close()
+        return 0
+
+    if args.workload == "vec":
+        n, iv, vv = W.q1_load_vector(96)
+        i_d, v_d = t(iv), t(vv)
+        y = torch.zeros(n, dtype=torch.float64, device=dev)
+        tc, V = _ev_time(stream, lambda: B.Vec(n, i_d), reps=reps)
+        ts, _ = _ev_time(stream, lambda: [V.set_values(v_d, y) for _ in range(20)], reps=reps)
+        ts /= 20
+        ne = V.info["nentries"]
+        alg = 12.0 * iv.shape[0] + 28.0 * ne
+        line = _base_line(
+            args, ts,
+            {"workload": "q1_load_vector_96: 8 entries per element of the Q1 96^3 mesh",
+             "n": n, "ncoo": int(iv.shape[0]), "nentries": ne},
+            {"symbolic_s": tc, "numeric_s": ts, "numeric_alg_bytes": alg,
+             "numeric_gbs": alg / ts / 1e9, "numeric_frac": alg / ts / 1e9 / hbm,
+             "what": "numeric = vec_set_values_coo (in-order sums + scatter into y), "
+                     "algorithmic bytes 12 per COO entry + 28 per distinct index"})
+        print(json.dumps(line), flush=True)
+        V.close()
         return 0
 
     if args.workload == "c5":
@@ -629,7 +652,7 @@ def main():
     ap.add_argument("--impl", default="gbs", choices=["gbs", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "vec"],
                     help="c2 = the benchmark (default); c3/c4/c5 = comparison runs")
     ap.add_argument("--host-loop", action="store_true",
                     help="run the solves' loop from the host (for profiler launch lists)")

@@ -47,6 +47,7 @@ extern "C" {
 #endif
 
 typedef struct gbs_mat_s *gbs_mat; /* opaque; owned by the library */
+typedef struct gbs_vec_s *gbs_vec; /* opaque; owned by the library */
 
 enum {
   GBS_OK = 0,
@@ -312,6 +313,25 @@ int mat_autotune(gbs_mat A, void *stream);
 /* Releases every device buffer the handle owns.  Synchronises the device
  * buffers' last stream first.  NULL is accepted. */
 int mat_destroy(gbs_mat A);
+
+/*
+ * Vector COO assembly (Sec. 5's COO interface applied to vectors:
+ * VecSetPreallocationCOO / VecSetValuesCOO).  vec_create_coo: i int32[ncoo]
+ * device array of indices in [0, n) (negative = ignored; read only during
+ * the call); builds the set of distinct kept indices and the maps with the
+ * matrix symbolic stage (an n x 1 pattern).  Synchronises `stream`; errors as
+ * mat_create_coo (GBS_ERR_INDEX for an index >= n).
+ * vec_set_values_coo: v double[ncoo] in the same order; for every index r
+ * that appears, y[r] becomes the in-order sum of its v[k] (GBS_INSERT) or
+ * y[r] plus that sum (GBS_ADD); entries of y whose index does not appear are
+ * left as they are.  y: double[n] device array.  Asynchronous.
+ * vec_get_info: n, the number of distinct indices and ncoo (host outputs,
+ * any may be NULL).  vec_destroy: releases the handle (NULL accepted).
+ */
+int vec_create_coo(int64_t n, int64_t ncoo, const int32_t *i, void *stream, gbs_vec *out);
+int vec_set_values_coo(gbs_vec V, const double *v, int mode, double *y, void *stream);
+int vec_get_info(gbs_vec V, int64_t *n, int64_t *nentries, int64_t *ncoo);
+int vec_destroy(gbs_vec V);
 
 /* Number of kernels this library has launched in this process (a diagnostic
  * counter).  A solve graph counts its setup and closing kernels at launch and

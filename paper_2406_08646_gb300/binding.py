@@ -32,7 +32,8 @@ EXPORTED = ["ksp_opts_default", "mat_create_coo", "mat_create_coo_batched",
             "ksp_adjoint", "ksp_adjoint_batched", "ksp_get_result", "mat_get_info",
             "mat_get_csr", "mat_get_coo_maps", "mat_set_plan", "mat_get_plan",
             "mat_autotune", "mat_destroy", "gbs_launch_count", "gbs_last_error",
-            "ksp_solve_cg_noalloc", "ksp_get_phase_ns", "mat_set_solver"]
+            "ksp_solve_cg_noalloc", "ksp_get_phase_ns", "mat_set_solver",
+            "vec_create_coo", "vec_set_values_coo", "vec_get_info", "vec_destroy"]
 
 
 class KspOpts(ctypes.Structure):
@@ -96,6 +97,10 @@ def lib() -> ctypes.CDLL:
         "ksp_solve_cg_noalloc": (ctypes.c_int, [I64, P, P, P, P, P, P, P, P]),
         "ksp_get_phase_ns": (ctypes.c_int, [P, P, P]),
         "mat_set_solver": (ctypes.c_int, [P, I32]),
+        "vec_create_coo": (ctypes.c_int, [I64, I64, P, P, PP]),
+        "vec_set_values_coo": (ctypes.c_int, [P, P, ctypes.c_int, P, P]),
+        "vec_get_info": (ctypes.c_int, [P, P, P, P]),
+        "vec_destroy": (ctypes.c_int, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -312,6 +317,49 @@ def mat_autotune(A, stream=None):
 def mat_destroy(A):
     if A:
         lib().mat_destroy(A)
+
+
+def vec_create_coo(n: int, i: torch.Tensor, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().vec_create_coo(n, i.numel(), _dev(i, torch.int32, None, "i"), _stream(stream),
+                                ctypes.byref(h)))
+    return h
+
+
+def vec_set_values_coo(V, v: torch.Tensor, y: torch.Tensor, mode: int = INSERT, stream=None):
+    _check(lib().vec_set_values_coo(V, _dev(v, torch.float64, None, "v"), mode,
+                                    _dev(y, torch.float64, None, "y"), _stream(stream)))
+
+
+def vec_get_info(V) -> dict:
+    n, ne, nc = (ctypes.c_int64() for _ in range(3))
+    _check(lib().vec_get_info(V, ctypes.byref(n), ctypes.byref(ne), ctypes.byref(nc)))
+    return {"n": n.value, "nentries": ne.value, "ncoo": nc.value}
+
+
+class Vec:
+    """Owning wrapper of a gbs_vec handle (vector COO assembly)."""
+
+    def __init__(self, n, i, stream=None):
+        self.h = vec_create_coo(n, i, stream)
+        self.info = vec_get_info(self.h)
+
+    def set_values(self, v, y=None, mode=INSERT, stream=None):
+        if y is None:
+            y = torch.zeros(self.info["n"], dtype=torch.float64, device=v.device)
+        vec_set_values_coo(self.h, v, y, mode, stream)
+        return y
+
+    def close(self):
+        if self.h:
+            lib().vec_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # --------------------------------------------------------------- wrapper

@@ -441,6 +441,97 @@ int mat_destroy(gbs_mat A) {
   return GBS_OK;
 }
 
+// A vector COO handle is the symbolic stage of an n x 1 matrix whose COO
+// column indices are all 0 (the pattern is then the set of distinct i).
+struct gbs_vec_s {
+  gbs_mat A = nullptr;
+};
+
+int vec_create_coo(int64_t n, int64_t ncoo, const int32_t *i, void *stream, gbs_vec *out) {
+  if (!out) {
+    set_error("vec_create_coo: out is null");
+    return GBS_ERR_ARG;
+  }
+  *out = nullptr;
+  if (n < 0 || ncoo < 0 || n > kMaxIndex || ncoo > kMaxIndex) {
+    set_error("vec_create_coo: sizes must be in [0, 2^31)");
+    return GBS_ERR_ARG;
+  }
+  if (ncoo > 0 && !i) {
+    set_error("vec_create_coo: null i");
+    return GBS_ERR_ARG;
+  }
+  gbs_vec V = new (std::nothrow) gbs_vec_s();
+  if (!V) return GBS_ERR_ALLOC;
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t *zeros = nullptr;
+  int st = GBS_OK;
+  if (ncoo > 0) {
+    if (cudaMalloc(&zeros, sizeof(int32_t) * ncoo) != cudaSuccess ||
+        cudaMemsetAsync(zeros, 0, sizeof(int32_t) * ncoo, s) != cudaSuccess) {
+      set_error("vec_create_coo: allocating the column indices failed");
+      st = GBS_ERR_ALLOC;
+    }
+  }
+  if (st == GBS_OK) {
+    gbs_mat A = new (std::nothrow) gbs_mat_s();
+    if (!A) st = GBS_ERR_ALLOC;
+    else {
+      cudaGetDevice(&A->device);
+      A->nrows = n;
+      A->ncols = 1;
+      A->ncoo = ncoo;
+      A->nsys = 1;
+      A->row_off_h = {0, n};
+      st = symbolic(A, i, zeros, nullptr, s);
+      if (st == GBS_OK) V->A = A;
+      else free_handle(A);
+    }
+  }
+  if (zeros) cudaFree(zeros);
+  if (st != GBS_OK) {
+    delete V;
+    return st;
+  }
+  *out = V;
+  return GBS_OK;
+}
+
+int vec_set_values_coo(gbs_vec V, const double *v, int mode, double *y, void *stream) {
+  if (!V || !V->A) {
+    set_error("vec_set_values_coo: null vector handle");
+    return GBS_ERR_ARG;
+  }
+  if (mode != GBS_INSERT && mode != GBS_ADD) {
+    set_error("vec_set_values_coo: mode must be GBS_INSERT or GBS_ADD");
+    return GBS_ERR_ARG;
+  }
+  if ((V->A->nkept > 0 && !v) || (V->A->nrows > 0 && !y)) {
+    set_error("vec_set_values_coo: null v or y");
+    return GBS_ERR_ARG;
+  }
+  GBS_TRY(use_device(V->A));
+  return launch_vec_set_values(V->A, v, mode, y, (cudaStream_t)stream);
+}
+
+int vec_get_info(gbs_vec V, int64_t *n, int64_t *nentries, int64_t *ncoo) {
+  if (!V || !V->A) {
+    set_error("vec_get_info: null vector handle");
+    return GBS_ERR_ARG;
+  }
+  if (n) *n = V->A->nrows;
+  if (nentries) *nentries = V->A->nnz;
+  if (ncoo) *ncoo = V->A->ncoo;
+  return GBS_OK;
+}
+
+int vec_destroy(gbs_vec V) {
+  if (!V) return GBS_OK;
+  free_handle(V->A);
+  delete V;
+  return GBS_OK;
+}
+
 int64_t gbs_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 const char *gbs_last_error(void) { return g_err; }

@@ -612,6 +612,34 @@ int launch_to_fp32(gbs_mat A, cudaStream_t s) {
   return GBS_OK;
 }
 
+// ------------------------------------------------------------------ vectors
+
+// y[r] = a_{p(r)} (INSERT) or y[r] + a_{p(r)} (ADD) for every index r that
+// has an entry (its row of the n x 1 pattern is non-empty); other y[r] keep.
+__global__ void k_vec_scatter(int64_t n, const int32_t *__restrict__ row_ptr,
+                              const double *__restrict__ val, int mode, double *__restrict__ y) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t p = row_ptr[r];
+    if (row_ptr[r + 1] > p) y[r] = (mode == GBS_ADD) ? y[r] + val[p] : val[p];
+  }
+}
+
+// Vector numeric stage: the in-order sums of the n x 1 pattern (the matrix
+// numeric kernel, INSERT into val), then the scatter into y.
+int launch_vec_set_values(gbs_mat A, const double *v, int mode, double *y, cudaStream_t s) {
+  if (A->nnz > 0) {
+    k_coo_numeric<<<grid_for(A->nnz, 256), 256, 0, s>>>(A->nnz, A->jmap, A->perm, v, GBS_INSERT,
+                                                        A->val);
+    GBS_LAUNCHED(1);
+  }
+  if (A->nrows > 0) {
+    k_vec_scatter<<<grid_for(A->nrows, 256), 256, 0, s>>>(A->nrows, A->row_ptr, A->val, mode, y);
+    GBS_LAUNCHED(1);
+  }
+  return GBS_OK;
+}
+
 // ------------------------------------------------------------------ adjoint scatter
 
 // dLda[p] = -lambda[row p] * x[col p]; dLdv[perm[t]] = dLda[p] for t in the

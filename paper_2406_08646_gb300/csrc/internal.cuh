@@ -174,6 +174,7 @@ void free_table(TableDev &t);
 void drop_graphs(gbs_mat A);
 int launch_spmv(gbs_mat A, const double *x, double *y, cudaStream_t s);
 int launch_set_values(gbs_mat A, const double *v, int mode, cudaStream_t s);
+int launch_vec_set_values(gbs_mat A, const double *v, int mode, double *y, cudaStream_t s);
 int launch_to_fp32(gbs_mat A, cudaStream_t s);
 int launch_adjoint_scatter(gbs_mat A, const double *lambda, const double *x,
                            double *dLda, double *dLdv, cudaStream_t s);

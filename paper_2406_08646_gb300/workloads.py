@@ -162,6 +162,23 @@ def q1_reference_stiffness() -> np.ndarray:
     return K
 
 
+def q1_load_vector(ne: int = 96, seed: int = SEED_C2 + 100):
+    """Element load vector of the Q1 mesh of q1_hex: element e contributes 8
+    COO entries (node g(e, a), f_e / 8) in element order, f_e ~ U[0.1, 10].
+    Returns (n, i int32[8 ne^3], v float64[8 ne^3])."""
+    nn = ne + 1
+    rng = np.random.default_rng(seed)
+    E = ne ** 3
+    e = np.arange(E, dtype=np.int64)
+    ex, ey, ez = e % ne, (e // ne) % ne, e // (ne * ne)
+    loc = np.array([[a & 1, (a >> 1) & 1, (a >> 2) & 1] for a in range(8)], np.int64)
+    node = ((ex[:, None] + loc[None, :, 0])
+            + nn * ((ey[:, None] + loc[None, :, 1]) + nn * (ez[:, None] + loc[None, :, 2])))
+    f = rng.uniform(0.1, 10.0, size=E)
+    v = np.repeat(f / 8.0, 8)
+    return nn ** 3, node.reshape(-1).astype(np.int32), v
+
+
 def q1_hex(ne: int = 96, seed: int = SEED_C2, kappa: np.ndarray | None = None) -> Problem:
     """3D Q1 FE Poisson on ne^3 hex elements of the unit cube, h = 1/ne.
 

@@ -513,3 +513,17 @@ def test_batched_with_capped_grid_and_frozen_systems(kernel):
         assert np.linalg.norm(resid[sl]) <= 1.05e-9 * np.linalg.norm(bt.b[sl])
         assert iters_close(rs[s]["iterations"], ros[s]["iterations"])
     A.close()
+
+
+def test_autotune_keeps_a_valid_plan_and_parity():
+    p = W.q1_hex(14, seed=12)
+    A, O = assemble_both(p.nrows, p.ncols, p.i, p.j, p.v)
+    A.set_solver(B.SOLVER_PHASES)
+    A.autotune()
+    pl = A.plan()
+    assert pl["kernel"] in (B.SPMV_SELL, 1, 2, 4, 8, 32) and pl["spmv_grid"] >= 1
+    x, r = A.solve(t(p.b), rtol=1e-9)
+    assert r["status"] == B.OK and true_rel(O, p.b, x.cpu().numpy()) <= 1.05e-9
+    y = A.mult(t(p.b)).cpu().numpy()
+    assert np.all(np.abs(y - oracle.spmv(O, p.b)) <= 1e-12 * abs_bound(O, p.b))
+    A.close()
