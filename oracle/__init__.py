@@ -70,6 +70,12 @@ def _load():
         lib.orc_coo_numeric.argtypes = [I64, P, P, P, ctypes.c_int, P]
         lib.orc_coo_scatter.restype = None
         lib.orc_coo_scatter.argtypes = [I64, I64, P, P, P, P]
+        lib.orc_bicg.restype = ctypes.c_int
+        lib.orc_bicg.argtypes = [I64, P, P, P, P, P, D, I64, ctypes.c_int, P]
+        lib.orc_tfqmr.restype = ctypes.c_int
+        lib.orc_tfqmr.argtypes = [I64, P, P, P, P, P, D, I64, ctypes.c_int, P]
+        lib.orc_krylov_batched.restype = ctypes.c_int
+        lib.orc_krylov_batched.argtypes = [I32, P, P, P, P, P, P, D, I64, ctypes.c_int, P]
         lib.orc_vec_set_values_coo.restype = I64
         lib.orc_vec_set_values_coo.argtypes = [I64, I64, P, P, ctypes.c_int, P]
         lib.orc_spmv.restype = None
@@ -171,6 +177,46 @@ def coo_scatter(A: CSR, dlda) -> np.ndarray:
     out = np.zeros(A.ncoo, np.float64)
     lib.orc_coo_scatter(A.nnz, A.ncoo, _p(A.jmap), _p(A.perm), _p(dlda), _p(out))
     return out
+
+
+BICG, TFQMR = 1, 2
+
+
+def _nonsym(fn, A: CSR, b, rtol, maxit, x0):
+    lib = _load()
+    b = _c(b, np.float64)
+    x = np.zeros(A.nrows, np.float64) if x0 is None else _c(x0, np.float64).copy()
+    res = _Result()
+    maxit = default_maxit(A.nrows) if maxit is None else maxit
+    getattr(lib, fn)(A.nrows, _p(A.row_ptr), _p(A.col), _p(A.val), _p(b), _p(x), rtol,
+                     maxit, 0 if x0 is None else 1, ctypes.byref(res))
+    return x, res.as_dict()
+
+
+def bicg(A: CSR, b, rtol: float = 1e-8, maxit: int | None = None, x0=None):
+    """BiCG with the diagonal preconditioner (Sec. 7 batched solvers), rt_0 = r_0."""
+    return _nonsym("orc_bicg", A, b, rtol, maxit, x0)
+
+
+def tfqmr(A: CSR, b, rtol: float = 1e-8, maxit: int | None = None, x0=None):
+    """TFQMR, right-preconditioned with the diagonal (Sec. 7 batched solvers)."""
+    return _nonsym("orc_tfqmr", A, b, rtol, maxit, x0)
+
+
+def krylov_batched(A: CSR, row_off, b, method: int, rtol: float = 1e-8,
+                   maxit: int | None = None):
+    """Batched BiCG (method 1) or TFQMR (method 2): each diagonal block alone."""
+    lib = _load()
+    row_off = _c(row_off, np.int64)
+    nsys = int(row_off.shape[0] - 1)
+    b = _c(b, np.float64)
+    x = np.zeros(A.nrows, np.float64)
+    res = (_Result * max(nsys, 1))()
+    mx = int(np.diff(row_off).max()) if nsys else 1
+    maxit = default_maxit(mx) if maxit is None else maxit
+    lib.orc_krylov_batched(nsys, _p(row_off), _p(A.row_ptr), _p(A.col), _p(A.val), _p(b),
+                           _p(x), rtol, maxit, method, ctypes.cast(res, ctypes.c_void_p))
+    return x, [res[s].as_dict() for s in range(nsys)]
 
 
 def vec_set_values_coo(n: int, i, v, mode: int = INSERT, y=None) -> np.ndarray:

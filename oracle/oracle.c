@@ -27,6 +27,9 @@
  *       linear solve: A^T lambda = g, dL/da_ij = -lambda_i x_j, dL/db = lambda.
  *   orc_pcg_batched    -- Sec. 7: many independent systems, each solved on its
  *       own (per-system scalars and convergence).
+ *   orc_bicg / orc_tfqmr / orc_krylov_batched -- Sec. 7's batched solvers
+ *       for nonsymmetric systems (BiCG and TFQMR with the diagonal
+ *       preconditioner), one system at a time.
  *   orc_vec_set_values_coo -- Sec. 5's COO interface for vectors
  *       (VecSetPreallocationCOO / VecSetValuesCOO): y_r is the sum of the
  *       contributions v[k] with i[k] = r.
@@ -450,6 +453,247 @@ done:
   free(dinv);
   free(f);
   return res->status = st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Nonsymmetric solvers with the diagonal preconditioner (Sec. 7)            */
+/* ------------------------------------------------------------------------ */
+
+/* y = A^T x: y_j = sum_i a_ij x_i, each sum in increasing i. */
+static void spmv_t(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
+                   const double *x, double *y) {
+  for (int64_t j = 0; j < n; ++j) y[j] = 0.0;
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) y[ci[p]] = y[ci[p]] + a[p] * x[i];
+}
+
+static int start_residual(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
+                          const double *b, double *x, int nonzero_guess, double *r,
+                          double *bnorm, orc_result *res) {
+  if (!nonzero_guess)
+    for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+  orc_spmv(n, rp, ci, a, x, r);
+  for (int64_t i = 0; i < n; ++i) r[i] = b[i] - r[i];
+  *bnorm = sqrt(dot(n, b, b));
+  res->rnorm0 = res->rnorm = sqrt(dot(n, r, r));
+  if (!isfinite(*bnorm)) return ORC_ERR_NAN;
+  return ORC_OK;
+}
+
+/*
+ * Preconditioned BiCG with M = diag(A) (applied to both sequences, M^T = M)
+ * and shadow residual rt_0 = r_0:
+ *   z = M^-1 r, zt = M^-1 rt, rho = z.rt; p = z + beta p, pt = zt + beta pt
+ *   (beta = rho / rho_prev; p = z, pt = zt first); q = A p, qt = A^T pt;
+ *   alpha = rho / (pt.q); x += alpha p; r -= alpha q; rt -= alpha qt.
+ * Stops when ||r|| <= rtol ||b|| (checked before each iteration);
+ * iterations counts the products q = A p.  rho = 0 or pt.q = 0: BREAKDOWN.
+ * For symmetric A, rt stays equal to r and the iteration is PCG's, operation
+ * for operation.
+ */
+int orc_bicg(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
+             const double *b, double *x, double rtol, int64_t maxit, int nonzero_guess,
+             orc_result *res) {
+  memset(res, 0, sizeof(*res));
+  double *w = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double) * 9);
+  if (!w) return res->status = ORC_ERR_ALLOC;
+  double *dinv = w, *r = w + n, *rt = r + n, *z = rt + n, *zt = z + n, *p = zt + n,
+         *pt = p + n, *q = pt + n, *qt = q + n;
+  double bnorm = 0.0;
+  int st = jacobi(n, rp, ci, a, dinv);
+  if (st == ORC_OK) st = start_residual(n, rp, ci, a, b, x, nonzero_guess, r, &bnorm, res);
+  if (st == ORC_OK && bnorm == 0.0) {
+    for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+    res->rnorm0 = res->rnorm = 0.0;
+  } else if (st == ORC_OK) {
+    for (int64_t i = 0; i < n; ++i) rt[i] = r[i];
+    double rho_prev = 0.0;
+    int64_t it = 0;
+    for (;;) {
+      const double rn = sqrt(dot(n, r, r));
+      res->rnorm = rn;
+      if (!isfinite(rn)) {
+        st = ORC_ERR_NAN;
+        break;
+      }
+      if (rn <= rtol * bnorm) break;
+      if (it >= maxit) {
+        st = ORC_ERR_MAXIT;
+        break;
+      }
+      for (int64_t i = 0; i < n; ++i) z[i] = dinv[i] * r[i];
+      for (int64_t i = 0; i < n; ++i) zt[i] = dinv[i] * rt[i];
+      const double rho = dot(n, z, rt);
+      if (rho == 0.0) {
+        st = ORC_ERR_BREAKDOWN;
+        break;
+      }
+      if (it == 0) {
+        for (int64_t i = 0; i < n; ++i) p[i] = z[i];
+        for (int64_t i = 0; i < n; ++i) pt[i] = zt[i];
+      } else {
+        const double beta = rho / rho_prev;
+        for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+        for (int64_t i = 0; i < n; ++i) pt[i] = zt[i] + beta * pt[i];
+      }
+      orc_spmv(n, rp, ci, a, p, q);
+      spmv_t(n, rp, ci, a, pt, qt);
+      ++it;
+      const double sigma = dot(n, pt, q);
+      if (isnan(sigma)) {
+        st = ORC_ERR_NAN;
+        break;
+      }
+      if (sigma == 0.0) {
+        st = ORC_ERR_BREAKDOWN;
+        break;
+      }
+      const double alpha = rho / sigma;
+      for (int64_t i = 0; i < n; ++i) x[i] = x[i] + alpha * p[i];
+      for (int64_t i = 0; i < n; ++i) r[i] = r[i] - alpha * q[i];
+      for (int64_t i = 0; i < n; ++i) rt[i] = rt[i] - alpha * qt[i];
+      rho_prev = rho;
+    }
+    res->iterations = (int32_t)it;
+  }
+  if (st == ORC_OK || st == ORC_ERR_MAXIT || st == ORC_ERR_BREAKDOWN || st == ORC_ERR_NAN)
+    res->true_rel_residual = true_rel(n, rp, ci, a, b, x, bnorm, q);
+  free(w);
+  return res->status = st;
+}
+
+/*
+ * TFQMR (Freund's transpose-free QMR) on the right-preconditioned system
+ * A M^-1 u = b, x = M^-1 u, M = diag(A), so that its quasi-residual bound
+ * refers to the true residual b - A x.  With B = A M^-1 and rt = r_0:
+ *   w = y1 = r_0; v = B y1; d = 0; tau = ||r_0||; theta = eta = 0;
+ *   rho = rt.r_0.  Each step: alpha = rho / (rt.v); y2 = y1 - alpha v;
+ *   then two half steps with (y, By) = (y1, B y1) and (y2, B y2):
+ *     w -= alpha By; d = y + (theta^2 eta / alpha) d; theta = ||w|| / tau;
+ *     c = 1 / sqrt(1 + theta^2); tau = tau theta c; eta = c^2 alpha;
+ *     x += eta M^-1 d;  stop when tau sqrt(m + 1) <= rtol ||b||
+ *     (m = half steps taken, counting from 1);
+ *   rho_new = rt.w; beta = rho_new / rho; y1 = w + beta y2;
+ *   v = B y1 + beta (B y2 + beta v).
+ * iterations counts the products with B; rnorm reports the bound at exit.
+ * rt.v = 0 or rho = 0: BREAKDOWN.
+ */
+int orc_tfqmr(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
+              const double *b, double *x, double rtol, int64_t maxit, int nonzero_guess,
+              orc_result *res) {
+  memset(res, 0, sizeof(*res));
+  double *wk = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double) * 11);
+  if (!wk) return res->status = ORC_ERR_ALLOC;
+  double *dinv = wk, *r = wk + n, *rt = r + n, *w = rt + n, *y1 = w + n, *y2 = y1 + n,
+         *v = y2 + n, *by1 = v + n, *by2 = by1 + n, *d = by2 + n, *t = d + n;
+  double bnorm = 0.0;
+  int st = jacobi(n, rp, ci, a, dinv);
+  if (st == ORC_OK) st = start_residual(n, rp, ci, a, b, x, nonzero_guess, r, &bnorm, res);
+  /* B y = A (M^-1 y) */
+#define ORC_BMUL(yv, out)                                              \
+  do {                                                                 \
+    for (int64_t i_ = 0; i_ < n; ++i_) t[i_] = dinv[i_] * (yv)[i_];    \
+    orc_spmv(n, rp, ci, a, t, (out));                                  \
+  } while (0)
+  if (st == ORC_OK && bnorm == 0.0) {
+    for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+    res->rnorm0 = res->rnorm = 0.0;
+  } else if (st == ORC_OK && res->rnorm0 <= rtol * bnorm) {
+    /* already converged */
+  } else if (st == ORC_OK) {
+    for (int64_t i = 0; i < n; ++i) {
+      rt[i] = r[i];
+      w[i] = r[i];
+      y1[i] = r[i];
+      d[i] = 0.0;
+    }
+    ORC_BMUL(y1, by1);
+    for (int64_t i = 0; i < n; ++i) v[i] = by1[i];
+    int64_t it = 1, m = 0;
+    double tau = res->rnorm0, theta = 0.0, eta = 0.0;
+    double rho = dot(n, rt, r);
+    for (;;) {
+      if (!isfinite(tau) || !isfinite(rho)) {
+        st = ORC_ERR_NAN;
+        break;
+      }
+      const double sigma = dot(n, rt, v);
+      if (sigma == 0.0 || rho == 0.0) {
+        st = ORC_ERR_BREAKDOWN;
+        break;
+      }
+      const double alpha = rho / sigma;
+      for (int64_t i = 0; i < n; ++i) y2[i] = y1[i] - alpha * v[i];
+      ORC_BMUL(y2, by2);
+      ++it;
+      int done = 0;
+      for (int half = 0; half < 2 && !done; ++half) {
+        const double *yh = half == 0 ? y1 : y2;
+        const double *byh = half == 0 ? by1 : by2;
+        const double coef = theta * theta * eta / alpha;
+        for (int64_t i = 0; i < n; ++i) w[i] = w[i] - alpha * byh[i];
+        for (int64_t i = 0; i < n; ++i) d[i] = yh[i] + coef * d[i];
+        theta = sqrt(dot(n, w, w)) / tau;
+        const double c = 1.0 / sqrt(1.0 + theta * theta);
+        tau = tau * theta * c;
+        eta = c * c * alpha;
+        for (int64_t i = 0; i < n; ++i) x[i] = x[i] + eta * (dinv[i] * d[i]);
+        ++m;
+        res->rnorm = tau * sqrt((double)(m + 1));
+        if (!isfinite(res->rnorm)) {
+          st = ORC_ERR_NAN;
+          done = 1;
+        } else if (res->rnorm <= rtol * bnorm) {
+          done = 1;
+        }
+      }
+      if (done) break;
+      if (it >= maxit) {
+        st = ORC_ERR_MAXIT;
+        break;
+      }
+      const double rho_new = dot(n, rt, w);
+      const double beta = rho_new / rho;
+      rho = rho_new;
+      for (int64_t i = 0; i < n; ++i) y1[i] = w[i] + beta * y2[i];
+      ORC_BMUL(y1, by1);
+      ++it;
+      for (int64_t i = 0; i < n; ++i) v[i] = by1[i] + beta * (by2[i] + beta * v[i]);
+    }
+    res->iterations = (int32_t)it;
+  }
+#undef ORC_BMUL
+  if (st == ORC_OK || st == ORC_ERR_MAXIT || st == ORC_ERR_BREAKDOWN || st == ORC_ERR_NAN)
+    res->true_rel_residual = true_rel(n, rp, ci, a, b, x, bnorm, t);
+  free(wk);
+  return res->status = st;
+}
+
+/* Batched nonsymmetric solves: method 1 = BiCG, 2 = TFQMR, each system alone. */
+int orc_krylov_batched(int32_t nsys, const int64_t *row_off, const int32_t *rp,
+                       const int32_t *ci, const double *a, const double *b, double *x,
+                       double rtol, int64_t maxit, int method, orc_result *res) {
+  int first = ORC_OK;
+  for (int32_t s = 0; s < nsys; ++s) {
+    int64_t r0 = row_off[s], r1 = row_off[s + 1], n = r1 - r0;
+    int64_t base = rp[r0], nz = (int64_t)rp[r1] - base;
+    int32_t *lrp = (int32_t *)malloc((size_t)(n + 1) * sizeof(int32_t));
+    int32_t *lci = (int32_t *)malloc((size_t)(nz > 0 ? nz : 1) * sizeof(int32_t));
+    if (!lrp || !lci) {
+      free(lrp);
+      free(lci);
+      return ORC_ERR_ALLOC;
+    }
+    for (int64_t i = 0; i <= n; ++i) lrp[i] = (int32_t)(rp[r0 + i] - base);
+    for (int64_t p = 0; p < nz; ++p) lci[p] = (int32_t)(ci[base + p] - r0);
+    const int st = method == 1
+                       ? orc_bicg(n, lrp, lci, a + base, b + r0, x + r0, rtol, maxit, 0, &res[s])
+                       : orc_tfqmr(n, lrp, lci, a + base, b + r0, x + r0, rtol, maxit, 0, &res[s]);
+    if (st != ORC_OK && first == ORC_OK) first = st;
+    free(lrp);
+    free(lci);
+  }
+  return first;
 }
 
 /* ------------------------------------------------------------------------ */

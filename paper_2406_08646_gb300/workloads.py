@@ -37,6 +37,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 SEED_C2, SEED_C3, SEED_C4, SEED_C4_SMALL, SEED_C5 = 1002, 1003, 1004, 1014, 1005
+SEED_C6 = 1006  # nonsymmetric (convection-diffusion) batches
 
 
 @dataclass
@@ -143,6 +144,47 @@ def poisson3d(m: int = 192, seed: int = SEED_C3) -> Problem:
     I, J, V = _stencil_coo((m, m, m), 6.0 / h ** 2, -1.0 / h ** 2)
     b = rng.standard_normal(m ** 3)
     return Problem(f"poisson3d_{m}", m ** 3, m ** 3, I, J, V, b, {"h": h, "m": m})
+
+
+def convdiff2d(m: int, bx: float, by: float, seed: int = SEED_C6) -> Problem:
+    """2D convection-diffusion -lap u + (bx, by) . grad u on an m x m interior
+    grid, h = 1/(m+1), first-order upwind convection (a nonsymmetric M-matrix):
+    row = h^-2 [4; -1 x4] plus, for the x direction, |bx|/h on the diagonal
+    and -|bx|/h on the upwind neighbour (west if bx > 0, east if bx < 0); the
+    same for y.  Entry order per row as _stencil_coo; b ~ N(0,1)."""
+    h = 1.0 / (m + 1)
+    I, J, V = _stencil_coo((m, m), 4.0 / h ** 2, -1.0 / h ** 2)
+    V = V.reshape(-1, 5).copy()
+    V[:, 0] += (abs(bx) + abs(by)) / h
+    V[:, 1 if bx > 0 else 2] -= abs(bx) / h      # -x or +x neighbour
+    V[:, 3 if by > 0 else 4] -= abs(by) / h      # -y or +y neighbour
+    rng = np.random.default_rng(seed)
+    b = rng.standard_normal(m * m)
+    return Problem(f"convdiff2d_{m}", m * m, m * m, I, J, V.reshape(-1), b,
+                   {"h": h, "m": m, "velocity": (bx, by)})
+
+
+def convdiff_batch(nsys: int = 512, seed: int = SEED_C6, size_range=(1000, 50000),
+                   peclet=(1.0, 100.0)) -> Batch:
+    """Independent 2D convection-diffusion systems (convdiff2d): side
+    L = round(sqrt(n_s)) with n_s ~ U_int[lo, hi]; velocity angle ~ U[0, 2 pi)
+    and magnitude ~ log-uniform[peclet] (times 1, the domain length).
+    Draws in order: all sizes; all angles; all magnitudes; all b."""
+    rng = np.random.default_rng(seed)
+    target = rng.integers(size_range[0], size_range[1], size=nsys, endpoint=True)
+    ang = rng.uniform(0.0, 2.0 * np.pi, size=nsys)
+    mag = 10.0 ** rng.uniform(np.log10(peclet[0]), np.log10(peclet[1]), size=nsys)
+    Is, Js, Vs, nrows, ncoo = [], [], [], [], []
+    for s in range(nsys):
+        L = max(2, int(round(float(target[s]) ** 0.5)))
+        p = convdiff2d(L, mag[s] * np.cos(ang[s]), mag[s] * np.sin(ang[s]))
+        Is.append(p.i); Js.append(p.j); Vs.append(p.v)
+        nrows.append(p.nrows); ncoo.append(p.i.shape[0])
+    nrows = np.array(nrows, np.int64)
+    b = rng.standard_normal(int(nrows.sum()))
+    return Batch(f"convdiff_batch_{nsys}", nrows, np.array(ncoo, np.int64),
+                 np.concatenate(Is), np.concatenate(Js), np.concatenate(Vs), b,
+                 {"angle": ang, "magnitude": mag})
 
 
 # --------------------------------------------------------------------------
