@@ -71,6 +71,8 @@ enum { GBS_FP64 = 0, GBS_FP32_REFINED = 1 };
 enum { GBS_SPMV_AUTO = -1, GBS_SPMV_SELL = 0 };
 /* Solvers (mat_set_solver). */
 enum { GBS_SOLVER_AUTO = 0, GBS_SOLVER_PHASES = 1, GBS_SOLVER_CTA = 2 };
+/* Krylov methods (ksp_opts.method; Sec. 7 batched solvers). */
+enum { GBS_KSP_CG = 0, GBS_KSP_BICG = 1, GBS_KSP_TFQMR = 2 };
 
 /* Solver options (host struct).  Fill with ksp_opts_default(), then override. */
 typedef struct {
@@ -96,17 +98,22 @@ typedef struct {
                            (synchronising the stream once per chunk), so
                            profilers that cannot follow device-side graph
                            loops see every kernel */
+  int32_t method;       /* GBS_KSP_CG (default), GBS_KSP_BICG or GBS_KSP_TFQMR;
+                           only ksp_solve / ksp_solve_batched accept a method
+                           other than CG */
 } ksp_opts;
 
 /* Per-solve (or per-system) result, host struct. */
 typedef struct {
   int32_t status;           /* GBS_OK or the GBS_ERR_* that ended the solve */
-  int32_t iterations;       /* products q = A p (refined: total inner ones) */
+  int32_t iterations;       /* CG and BiCG: products q = A p (refined: total
+                               inner ones); TFQMR: products with A D^-1 */
   int32_t outer_iterations; /* refined: refinement steps; FP64: 0 */
   int32_t solver;           /* GBS_SOLVER_PHASES or GBS_SOLVER_CTA: which ran */
   double rnorm0;            /* ||b - A x0||_2 */
   double rnorm;             /* last recursively updated residual norm
-                               (refined: last FP64 outer residual norm) */
+                               (refined: last FP64 outer residual norm;
+                               TFQMR: the quasi-residual bound tau sqrt(m+1)) */
   double true_rel_residual; /* ||b - A x||_2 / ||b||_2 recomputed at exit */
 } ksp_result;
 
@@ -176,7 +183,7 @@ int mat_mult(gbs_mat A, const double *x, double *y, void *stream);
  * inside FP64 iterative refinement (Sec. 2, A7).  o may be NULL (defaults).
  * res (host): if non-NULL the call synchronises and fills it, and returns its
  * status; if NULL the call is asynchronous and the result can be fetched later
- * with ksp_get_result.
+ * with ksp_get_result.  o->method must be GBS_KSP_CG (else GBS_ERR_ARG).
  */
 int ksp_solve_cg(gbs_mat A, const double *b, double *x, const ksp_opts *o,
                  ksp_result *res, void *stream);
@@ -191,6 +198,41 @@ int ksp_solve_cg(gbs_mat A, const double *b, double *x, const ksp_opts *o,
  */
 int ksp_solve_cg_batched(gbs_mat A, const double *b, double *x, const ksp_opts *o,
                          ksp_result *res_h, void *stream);
+
+/*
+ * Krylov solve with the method o->method (Sec. 7: PETSc's batched solvers are
+ * TFQMR and BiCG with diagonal preconditioning; CG as in ksp_solve_cg).
+ * ksp_solve treats the whole matrix as one system (for a batched handle, the
+ * stacked "ensemble" of Sec. 7); ksp_solve_batched solves each system of a
+ * batched handle on its own, with its own scalars and stopping test.
+ *
+ *   GBS_KSP_CG: identical to ksp_solve_cg / ksp_solve_cg_batched.
+ *   GBS_KSP_BICG: biconjugate gradients with M = diag(A) on both sequences
+ *     and shadow residual rt0 = r0; q = A p and qt = A^T pt each iteration,
+ *     A^T from a transposed sliced-ELL copy built on the first BiCG solve
+ *     (its values refreshed after every mat_set_values_coo).  Stops when
+ *     ||r|| <= rtol ||b|| (tested before each iteration).  For symmetric A
+ *     it performs PCG's operations.
+ *   GBS_KSP_TFQMR: Freund's transpose-free QMR on A M^-1 u = b, x = M^-1 u,
+ *     M = diag(A) (right preconditioning, so its bound refers to b - A x);
+ *     stops when the quasi-residual bound tau sqrt(m + 1) <= rtol ||b||
+ *     (m = half steps).  Two products with A per step.
+ *
+ * BiCG and TFQMR run in FP64 on the per-CTA solver (one 1024-thread CTA per
+ * system, every iteration inside one kernel launch, systems largest first),
+ * whatever mat_set_solver chose for CG; o->precision must be GBS_FP64 and
+ * o->host_loop is ignored.  A zero or negative diagonal entry ends the solve
+ * with GBS_ERR_NOT_SPD (the Jacobi preconditioner needs a positive diagonal);
+ * rt.v = 0 or rho = 0 (TFQMR), rho = 0 or pt.q = 0 (BiCG) with
+ * GBS_ERR_BREAKDOWN.  Arguments, results and synchronisation as in
+ * ksp_solve_cg / ksp_solve_cg_batched (a handle made by mat_create_coo has
+ * one system).  Workspace: 9 (TFQMR) or 6 (BiCG) FP64 vectors of
+ * nrows, allocated on first use and kept with the handle.
+ */
+int ksp_solve(gbs_mat A, const double *b, double *x, const ksp_opts *o, ksp_result *res,
+              void *stream);
+int ksp_solve_batched(gbs_mat A, const double *b, double *x, const ksp_opts *o,
+                      ksp_result *res_h, void *stream);
 
 /*
  * Adjoint of x = A^{-1} b (Sec. 1 adjoint capability), for symmetric A:

@@ -26,6 +26,7 @@ INSERT, ADD = 0, 1
 FP64, FP32_REFINED = 0, 1
 SPMV_AUTO, SPMV_SELL = -1, 0  # plan kernels; 1, 2, 4, 8, 32 = CSR-vector lanes per row
 SOLVER_AUTO, SOLVER_PHASES, SOLVER_CTA = 0, 1, 2
+KSP_CG, KSP_BICG, KSP_TFQMR = 0, 1, 2
 
 EXPORTED = ["ksp_opts_default", "mat_create_coo", "mat_create_coo_batched",
             "mat_set_values_coo", "mat_mult", "ksp_solve_cg", "ksp_solve_cg_batched",
@@ -33,7 +34,8 @@ EXPORTED = ["ksp_opts_default", "mat_create_coo", "mat_create_coo_batched",
             "mat_get_csr", "mat_get_coo_maps", "mat_set_plan", "mat_get_plan",
             "mat_autotune", "mat_destroy", "gbs_launch_count", "gbs_last_error",
             "ksp_solve_cg_noalloc", "ksp_get_phase_ns", "mat_set_solver",
-            "vec_create_coo", "vec_set_values_coo", "vec_get_info", "vec_destroy"]
+            "vec_create_coo", "vec_set_values_coo", "vec_get_info", "vec_destroy",
+            "ksp_solve", "ksp_solve_batched"]
 
 
 class KspOpts(ctypes.Structure):
@@ -41,7 +43,7 @@ class KspOpts(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("inner_rtol", ctypes.c_double),
                 ("max_outer", ctypes.c_int32), ("inner_maxit", ctypes.c_int32),
                 ("timeout_ns", ctypes.c_int64), ("nonzero_guess", ctypes.c_int32),
-                ("host_loop", ctypes.c_int32)]
+                ("host_loop", ctypes.c_int32), ("method", ctypes.c_int32)]
 
 
 class KspResult(ctypes.Structure):
@@ -82,6 +84,8 @@ def lib() -> ctypes.CDLL:
         "mat_mult": (ctypes.c_int, [P, P, P, P]),
         "ksp_solve_cg": (ctypes.c_int, [P, P, P, P, P, P]),
         "ksp_solve_cg_batched": (ctypes.c_int, [P, P, P, P, P, P]),
+        "ksp_solve": (ctypes.c_int, [P, P, P, P, P, P]),
+        "ksp_solve_batched": (ctypes.c_int, [P, P, P, P, P, P]),
         "ksp_adjoint": (ctypes.c_int, [P, P, P, P, P, P, P, P, P]),
         "ksp_adjoint_batched": (ctypes.c_int, [P, P, P, P, P, P, P, P, P]),
         "ksp_get_result": (ctypes.c_int, [P, P, I32, P]),
@@ -145,13 +149,14 @@ def _dev(t: torch.Tensor | None, dtype, n: int | None = None, name: str = "tenso
 
 def make_opts(rtol=1e-8, maxit=-1, precision=FP64, inner_rtol=1e-4, max_outer=30,
               inner_maxit=-1, timeout_ns=0, nonzero_guess=False,
-              host_loop=False) -> KspOpts:
+              host_loop=False, method=KSP_CG) -> KspOpts:
     o = KspOpts()
     lib().ksp_opts_default(ctypes.byref(o))
     o.rtol, o.maxit, o.precision = float(rtol), int(maxit), int(precision)
     o.inner_rtol, o.max_outer, o.inner_maxit = float(inner_rtol), int(max_outer), int(inner_maxit)
     o.timeout_ns, o.nonzero_guess = int(timeout_ns), int(bool(nonzero_guess))
     o.host_loop = int(bool(host_loop))
+    o.method = int(method)
     return o
 
 
@@ -206,6 +211,25 @@ def ksp_solve_cg_batched(A, b, x, nsys: int, opts: KspOpts | None = None, want_r
                                     ctypes.byref(opts) if opts is not None else None,
                                     ctypes.cast(res, ctypes.c_void_p) if want_result else None,
                                     _stream(stream))
+    return _solve_status(st, list(res) if want_result else None)
+
+
+def ksp_solve(A, b, x, opts: KspOpts | None = None, want_result=True, stream=None):
+    res = KspResult()
+    st = lib().ksp_solve(A, _dev(b, torch.float64, None, "b"), _dev(x, torch.float64, None, "x"),
+                         ctypes.byref(opts) if opts is not None else None,
+                         ctypes.byref(res) if want_result else None, _stream(stream))
+    return _solve_status(st, [res] if want_result else None)
+
+
+def ksp_solve_batched(A, b, x, nsys: int, opts: KspOpts | None = None, want_result=True,
+                      stream=None):
+    res = (KspResult * nsys)()
+    st = lib().ksp_solve_batched(A, _dev(b, torch.float64, None, "b"),
+                                 _dev(x, torch.float64, None, "x"),
+                                 ctypes.byref(opts) if opts is not None else None,
+                                 ctypes.cast(res, ctypes.c_void_p) if want_result else None,
+                                 _stream(stream))
     return _solve_status(st, list(res) if want_result else None)
 
 
@@ -404,13 +428,13 @@ class Mat:
     def solve(self, b, x=None, stream=None, want_result=True, **kw):
         if x is None:
             x = torch.empty_like(b)
-        r = ksp_solve_cg(self.h, b, x, make_opts(**kw), want_result, stream)
+        r = ksp_solve(self.h, b, x, make_opts(**kw), want_result, stream)
         return x, (r[0] if r else None)
 
     def solve_batched(self, b, x=None, stream=None, want_result=True, **kw):
         if x is None:
             x = torch.empty_like(b)
-        r = ksp_solve_cg_batched(self.h, b, x, self.nsys, make_opts(**kw), want_result, stream)
+        r = ksp_solve_batched(self.h, b, x, self.nsys, make_opts(**kw), want_result, stream)
         return x, r
 
     def adjoint(self, x, dldx, dlda=True, dldv=True, stream=None, want_result=True,

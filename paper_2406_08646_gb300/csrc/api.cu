@@ -27,15 +27,17 @@ void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relax
 
 static constexpr int64_t kMaxIndex = 2147483647LL;
 
-static void free_handle(gbs_mat A) {
+void free_handle(gbs_mat A) {
   if (!A) return;
   int cur = 0;
   cudaGetDevice(&cur);
   cudaSetDevice(A->device);
   drop_graphs(A);
+  free_handle(A->At);
   void *dev[] = {A->row_ptr, A->col, A->val, A->val32, A->perm, A->jmap, A->diag_pos,
                  A->dinv, A->dinv32, A->r, A->p, A->q, A->r32, A->p32, A->q32, A->d32,
-                 A->part, A->sys_cnt, A->st, A->ctl, A->call, A->cta_order};
+                 A->part, A->sys_cnt, A->st, A->ctl, A->call, A->cta_order,
+                 A->kv, A->sys_row0};  // sys_slice0 lies inside sys_row0's block
   for (void *p : dev)
     if (p) cudaFree(p);
   free_table(A->ta);
@@ -70,6 +72,14 @@ static int fill_opts(gbs_mat A, const ksp_opts *in, ksp_opts &o, bool per_system
   }
   if (o.host_loop != 0 && o.host_loop != 1) {
     set_error("ksp opts: host_loop must be 0 or 1");
+    return GBS_ERR_ARG;
+  }
+  if (o.method != GBS_KSP_CG && o.method != GBS_KSP_BICG && o.method != GBS_KSP_TFQMR) {
+    set_error("ksp opts: method must be GBS_KSP_CG, GBS_KSP_BICG or GBS_KSP_TFQMR");
+    return GBS_ERR_ARG;
+  }
+  if (o.method != GBS_KSP_CG && o.precision != GBS_FP64) {
+    set_error("ksp opts: BiCG and TFQMR run in FP64 only (precision GBS_FP64)");
     return GBS_ERR_ARG;
   }
   const int64_t n = max_system_rows(A, per_system);
@@ -221,8 +231,10 @@ int mat_mult(gbs_mat A, const double *x, double *y, void *stream) {
   return launch_spmv(A, x, y, (cudaStream_t)stream);
 }
 
+// any_method: the generic entry points (ksp_solve*); the CG ones accept CG only.
 static int solve_entry(gbs_mat A, const double *b, double *x, const ksp_opts *o,
-                       ksp_result *res, void *stream, bool per_system, const char *fn) {
+                       ksp_result *res, void *stream, bool per_system, bool any_method,
+                       const char *fn) {
   GBS_TRY(check_mat(A, fn));
   if (A->nrows != A->ncols) {
     set_error("%s: matrix is not square", fn);
@@ -242,21 +254,36 @@ static int solve_entry(gbs_mat A, const double *b, double *x, const ksp_opts *o,
   }
   ksp_opts oo;
   GBS_TRY(fill_opts(A, o, oo, per_system));
+  if (!any_method && oo.method != GBS_KSP_CG) {
+    set_error("%s: o->method must be GBS_KSP_CG (ksp_solve takes the others)", fn);
+    return GBS_ERR_ARG;
+  }
   GBS_TRY(use_device(A));
   cudaStream_t s = (cudaStream_t)stream;
-  GBS_TRY(solve(A, b, x, oo, per_system, s));
+  if (oo.method == GBS_KSP_CG) GBS_TRY(solve(A, b, x, oo, per_system, s));
+  else GBS_TRY(solve_krylov(A, b, x, oo, per_system, s));
   if (res) return read_results(A, res, per_system ? A->nsys : 1, s);
   return GBS_OK;
 }
 
 int ksp_solve_cg(gbs_mat A, const double *b, double *x, const ksp_opts *o, ksp_result *res,
                  void *stream) {
-  return solve_entry(A, b, x, o, res, stream, false, "ksp_solve_cg");
+  return solve_entry(A, b, x, o, res, stream, false, false, "ksp_solve_cg");
 }
 
 int ksp_solve_cg_batched(gbs_mat A, const double *b, double *x, const ksp_opts *o,
                          ksp_result *res_h, void *stream) {
-  return solve_entry(A, b, x, o, res_h, stream, true, "ksp_solve_cg_batched");
+  return solve_entry(A, b, x, o, res_h, stream, true, false, "ksp_solve_cg_batched");
+}
+
+int ksp_solve(gbs_mat A, const double *b, double *x, const ksp_opts *o, ksp_result *res,
+              void *stream) {
+  return solve_entry(A, b, x, o, res, stream, false, true, "ksp_solve");
+}
+
+int ksp_solve_batched(gbs_mat A, const double *b, double *x, const ksp_opts *o,
+                      ksp_result *res_h, void *stream) {
+  return solve_entry(A, b, x, o, res_h, stream, true, true, "ksp_solve_batched");
 }
 
 static int adjoint_entry(gbs_mat A, const double *x, const double *dLdx, double *lambda,
@@ -272,7 +299,7 @@ static int adjoint_entry(gbs_mat A, const double *x, const double *dLdx, double 
   if (o) oo = *o;
   oo.nonzero_guess = 0;
   // the adjoint system is solved in the precision the caller asked for
-  int st = solve_entry(A, dLdx, lambda, &oo, nullptr, stream, per_system, fn);
+  int st = solve_entry(A, dLdx, lambda, &oo, nullptr, stream, per_system, false, fn);
   if (st != GBS_OK) return st;
   st = launch_adjoint_scatter(A, lambda, x, dLda, dLdv, (cudaStream_t)stream);
   if (st != GBS_OK) return st;

@@ -585,6 +585,7 @@ int launch_set_values(gbs_mat A, const double *v, int mode, cudaStream_t s) {
   GBS_TRY(sell_values(A, s));
   A->values_set = true;
   A->val32_valid = false;
+  A->values_version += 1;
   return GBS_OK;
 }
 

@@ -106,7 +106,7 @@ __device__ __forceinline__ void cta_true_residual(const PcgArgs &a, const SysRan
 }
 
 // FP64 PCG: the phases A, B, C of phases.cuh in one CTA, same tests.
-__device__ void cta_pcg_fp64(const PcgArgs &a, const SysRange &g, CtaShared &sh) {
+static __device__ void cta_pcg_fp64(const PcgArgs &a, const SysRange &g, CtaShared &sh) {
   const CallArgs &C = *a.call;
   const double *b = C.b;
   double *x = C.x;
@@ -217,7 +217,7 @@ __device__ void cta_pcg_fp64(const PcgArgs &a, const SysRange &g, CtaShared &sh)
 }
 
 // FP32 inner PCG under FP64 refinement, the oracle's order of steps.
-__device__ void cta_pcg_refined(const PcgArgs &a, const SysRange &g, CtaShared &sh) {
+static __device__ void cta_pcg_refined(const PcgArgs &a, const SysRange &g, CtaShared &sh) {
   const CallArgs &C = *a.call;
   const double *b = C.b;
   double *x = C.x;

@@ -163,6 +163,15 @@ struct gbs_mat_s {
 
   // cached executable graphs [refined][per_system] of the solve loop
   cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+
+  // nonsymmetric solvers (krylov.cu): the transpose as an internal handle
+  // (its CSR and sliced copy), refreshed when the values change; the work
+  // vectors; per-system first rows and first slices (device, nsys + 1)
+  int64_t values_version = 0;       // bumped by every numeric stage
+  gbs_mat_s *At = nullptr;
+  int64_t at_version = -1;          // values_version the transpose holds
+  double *kv = nullptr;             // KRYLOV_NVEC vectors of nrows
+  int32_t *sys_row0 = nullptr, *sys_slice0 = nullptr;  // one allocation (sys_row0)
 };
 
 namespace gbs {
@@ -182,6 +191,11 @@ int symbolic(gbs_mat A, const int32_t *i, const int32_t *j, const int64_t *coo_o
              cudaStream_t s);
 int solve(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool per_system,
           cudaStream_t s);
+void free_handle(gbs_mat A);
+int solve_krylov(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool per_system,
+                 cudaStream_t s);
+CallArgs call_args(const double *b, double *x, const ksp_opts &o);
+int put_call(CallArgs *dst, const CallArgs &c, cudaStream_t s, DevCtl *ctl = nullptr);
 int read_results(gbs_mat A, ksp_result *res, int32_t count, cudaStream_t s);
 int read_phase_ns(gbs_mat A, int64_t *phase_ns, cudaStream_t s);
 int auto_lanes(int64_t nnz, int64_t nrows);

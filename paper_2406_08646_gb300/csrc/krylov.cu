@@ -1,0 +1,593 @@
+// Nonsymmetric batched Krylov solvers (Sec. 7: PETSc's batched solvers are
+// TFQMR and BiCG with diagonal preconditioning), one CTA per system.
+//
+// Both methods run FP64 and keep every iteration of a system inside one CTA of
+// one kernel launch, like the per-CTA PCG (cta.cuh): CTA barriers only, block
+// reductions in a fixed tree whose totals reach every thread, and scalar
+// recurrences that every thread evaluates identically from those totals, so
+// all control flow is uniform across the CTA without extra broadcasts.
+//
+//   BiCG (Jacobi on both sequences, rt0 = r0): per iteration the p/pt update,
+//   the products q = A p (fused with pt.q) and qt = A^T pt, and the x/r/rt
+//   update fused with ||r||^2 and (D^-1 r).rt.  A^T is a second sliced-ELL
+//   copy made from the transpose of the COO pattern by the library's own
+//   symbolic stage (deterministic, bit-exact), kept as an internal handle.
+//
+//   TFQMR (Freund 1993, right-preconditioned: B = A D^-1): per step two
+//   products with B over t = D^-1 y, each fused with the elementwise work
+//   that follows it, three reductions.  The x update of each half step is
+//   deferred into the next pass over the rows (it only needs that half
+//   step's eta and d), and applied at exit when the loop ends on a half step.
+//
+// The oracle counts, statuses and tests are followed exactly; only the
+// summation order of the dot products differs (a fixed tree here).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "cta.cuh"
+#include "device_util.cuh"
+#include "internal.cuh"
+#include "phases.cuh"
+
+namespace gbs {
+
+constexpr int KRYLOV_NVEC = 9;  // TFQMR: w, y1, y2, rt, v, B y1, B y2, d, t
+
+struct KrylovArgs {
+  int32_t ensemble;                        // 1: one CTA over the whole matrix
+  int32_t nrows, nslices;                  // whole matrix (ensemble)
+  const int32_t *order;                    // system of each CTA, largest first
+  const int32_t *sys_row0, *sys_slice0;    // nsys + 1
+  const int32_t *sptr, *srow0, *scol;      // sliced-ELL copy of A
+  const double *sval;
+  const int32_t *tptr, *tcol;              // sliced-ELL copy of A^T (same slices)
+  const double *tval;
+  int32_t stream_matrix;                   // evict-first loads of the copies
+  const double *dinv;
+  double *v[KRYLOV_NVEC];
+  SysState *st;
+  DevCtl *ctl;
+  const CallArgs *call;
+};
+
+struct KSys {
+  int s, r0, r1, s0, s1;
+};
+
+__device__ __forceinline__ KSys kry_system(const KrylovArgs &a) {
+  KSys g;
+  if (a.ensemble) {
+    g.s = 0;
+    g.r0 = 0;
+    g.r1 = a.nrows;
+    g.s0 = 0;
+    g.s1 = a.nslices;
+  } else {
+    g.s = __ldg(a.order + blockIdx.x);
+    g.r0 = __ldg(a.sys_row0 + g.s);
+    g.r1 = __ldg(a.sys_row0 + g.s + 1);
+    g.s0 = __ldg(a.sys_slice0 + g.s);
+    g.s1 = __ldg(a.sys_slice0 + g.s + 1);
+  }
+  return g;
+}
+
+// Row products of the system with one of the two sliced copies; x may have
+// been written by this CTA, so its gathers take the coherent path.
+template <class F>
+__device__ __forceinline__ void kry_rows(const KrylovArgs &a, const KSys &g, const int32_t *sptr,
+                                         const int32_t *scol, const double *sval, const double *x,
+                                         F &f) {
+  if (a.stream_matrix) sell_rows<double, true, false>(sptr, a.srow0, scol, sval, x, g.s0, g.s1, f);
+  else sell_rows<double, false, false>(sptr, a.srow0, scol, sval, x, g.s0, g.s1, f);
+}
+
+// Wall-clock limit, read by thread 0 and shared through one barrier (the flag
+// is rewritten only after the next block reduction's barriers).
+__device__ __forceinline__ bool kry_timed_out(const KrylovArgs &a, CtaShared &sh) {
+  if (threadIdx.x == 0) {
+    const int64_t lim = a.call->timeout_ns;
+    sh.flag[1] = lim > 0 && (int64_t)global_ns() - ldcg(&a.ctl->t_start) > lim;
+  }
+  __syncthreads();
+  return sh.flag[1] != 0;
+}
+
+// Closing state of the system (thread 0), then ||b - A x||^2 into S.tt.
+__device__ void kry_close(const KrylovArgs &a, const KSys &g, CtaShared &sh, int status,
+                          bool timed_out, int iterations, double bb, double rnorm0,
+                          double rnorm) {
+  SysState &S = a.st[g.s];
+  __syncthreads();  // x complete
+  if (threadIdx.x == 0) {
+    memset(&S, 0, sizeof(SysState));
+    S.bb = bb;
+    S.rnorm0 = rnorm0;
+    S.rnorm = rnorm;
+    S.iterations = iterations;
+    S.status = timed_out ? GBS_OK : status;
+    S.active = timed_out ? 1 : 0;  // reported as the control word's error
+    if (timed_out) a.ctl->err = GBS_ERR_TIMEOUT;
+  }
+  const double *b = a.call->b;
+  const double *x = a.call->x;
+  double tt[1] = {0.0};
+  auto f = [&](int r, double t) {
+    const double d = b[r] - t;
+    tt[0] = fma(d, d, tt[0]);
+  };
+  kry_rows(a, g, a.sptr, a.scol, a.sval, x, f);
+  cta_sum<double, 1>(tt, sh);
+  if (threadIdx.x == 0) S.tt = tt[0];
+}
+
+// Start-up checks shared by both methods: a missing or non-positive diagonal
+// (NOT_SPD, the Jacobi preconditioner's requirement), b not finite (NAN), or
+// b = 0 (x = 0, OK).  Returns the status, or -1 to iterate.
+__device__ __forceinline__ int kry_start_status(double missing, double bb) {
+  if (missing > 0.0) return GBS_ERR_NOT_SPD;
+  if (!isfinite(bb)) return GBS_ERR_NAN;
+  if (bb == 0.0) return GBS_OK;
+  return -1;
+}
+
+__device__ __forceinline__ void kry_zero_x(const KSys &g, double *x) {
+  for (int r = g.r0 + threadIdx.x; r < g.r1; r += blockDim.x) x[r] = 0.0;
+}
+
+// ------------------------------------------------------------------ BiCG
+__device__ void kry_bicg(const KrylovArgs &a, const KSys &g, CtaShared &sh) {
+  const CallArgs &C = *a.call;
+  const double *b = C.b;
+  double *x = C.x;
+  const double *dinv = a.dinv;
+  double *r = a.v[0], *rt = a.v[1], *p = a.v[2], *pt = a.v[3], *q = a.v[4], *qt = a.v[5];
+  // r0 = b - A x0, rt0 = r0; sums r.r, b.b, (D^-1 r).rt, missing diagonals
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  auto start = [&](int i, double ax) {
+    const double bv = b[i], rv = bv - ax, dv = dinv[i];
+    r[i] = rv;
+    rt[i] = rv;
+    v[0] = fma(rv, rv, v[0]);
+    v[1] = fma(bv, bv, v[1]);
+    v[2] = fma(dv * rv, rv, v[2]);
+    v[3] += (dv == 0.0) ? 1.0 : 0.0;
+  };
+  if (C.nonzero_guess) {
+    kry_rows(a, g, a.sptr, a.scol, a.sval, x, start);
+  } else {
+    for (int i = g.r0 + threadIdx.x; i < g.r1; i += blockDim.x) {
+      x[i] = 0.0;
+      start(i, 0.0);
+    }
+  }
+  cta_sum<double, 4>(v, sh);
+  const double bb = v[1], thr = C.rtol * sqrt(bb);
+  double rn = sqrt(v[0]), rho = v[2], rho_prev = 0.0;
+  double rnorm0 = rn;
+  int status = kry_start_status(v[3], bb), it = 0;
+  bool timed = false;
+  if (status == GBS_OK) {  // b = 0
+    kry_zero_x(g, x);
+    rn = rnorm0 = 0.0;
+  }
+  while (status < 0) {
+    if (!isfinite(rn)) {
+      status = GBS_ERR_NAN;
+      break;
+    }
+    if (rn <= thr) {
+      status = GBS_OK;
+      break;
+    }
+    if (it >= C.maxit) {
+      status = GBS_ERR_MAXIT;
+      break;
+    }
+    if (rho == 0.0) {
+      status = GBS_ERR_BREAKDOWN;
+      break;
+    }
+    if (it > 0 && kry_timed_out(a, sh)) {
+      timed = true;
+      break;
+    }
+    // p = z + beta p, pt = zt + beta pt (z = D^-1 r, zt = D^-1 rt)
+    const bool first = it == 0;
+    const double beta = first ? 0.0 : rho / rho_prev;
+    for (int i = g.r0 + threadIdx.x; i < g.r1; i += blockDim.x) {
+      const double dv = dinv[i], z = dv * r[i], zt = dv * rt[i];
+      p[i] = first ? z : fma(beta, p[i], z);
+      pt[i] = first ? zt : fma(beta, pt[i], zt);
+    }
+    __syncthreads();
+    // q = A p with pt.q, qt = A^T pt
+    double sg[1] = {0.0};
+    auto fq = [&](int i, double y) {
+      q[i] = y;
+      sg[0] = fma(pt[i], y, sg[0]);
+    };
+    kry_rows(a, g, a.sptr, a.scol, a.sval, p, fq);
+    auto fqt = [&](int i, double y) { qt[i] = y; };
+    kry_rows(a, g, a.tptr, a.tcol, a.tval, pt, fqt);
+    ++it;
+    cta_sum<double, 1>(sg, sh);
+    if (isnan(sg[0])) {
+      status = GBS_ERR_NAN;
+      break;
+    }
+    if (sg[0] == 0.0) {
+      status = GBS_ERR_BREAKDOWN;
+      break;
+    }
+    const double alpha = rho / sg[0];
+    // x += alpha p, r -= alpha q, rt -= alpha qt; ||r||^2, (D^-1 r).rt
+    double u[2] = {0.0, 0.0};
+    for (int i = g.r0 + threadIdx.x; i < g.r1; i += blockDim.x) {
+      x[i] = fma(alpha, p[i], x[i]);
+      const double rv = fma(-alpha, q[i], r[i]);
+      const double rtv = fma(-alpha, qt[i], rt[i]);
+      r[i] = rv;
+      rt[i] = rtv;
+      u[0] = fma(rv, rv, u[0]);
+      u[1] = fma(dinv[i] * rv, rtv, u[1]);
+    }
+    cta_sum<double, 2>(u, sh);
+    rn = sqrt(u[0]);
+    rho_prev = rho;
+    rho = u[1];
+  }
+  kry_close(a, g, sh, status, timed, it, bb, rnorm0, rn);
+}
+
+// ------------------------------------------------------------------ TFQMR
+__device__ void kry_tfqmr(const KrylovArgs &a, const KSys &g, CtaShared &sh) {
+  const CallArgs &C = *a.call;
+  const double *b = C.b;
+  double *x = C.x;
+  const double *dinv = a.dinv;
+  double *w = a.v[0], *y1 = a.v[1], *y2 = a.v[2], *rt = a.v[3], *vv = a.v[4], *by1 = a.v[5],
+         *by2 = a.v[6], *d = a.v[7], *t = a.v[8];
+  // r0 = b - A x0 into w, y1 and rt; d = 0; t = D^-1 y1; sums r.r, b.b,
+  // missing diagonals
+  double v[3] = {0.0, 0.0, 0.0};
+  auto start = [&](int i, double ax) {
+    const double bv = b[i], rv = bv - ax, dv = dinv[i];
+    w[i] = rv;
+    y1[i] = rv;
+    rt[i] = rv;
+    d[i] = 0.0;
+    t[i] = dv * rv;
+    v[0] = fma(rv, rv, v[0]);
+    v[1] = fma(bv, bv, v[1]);
+    v[2] += (dv == 0.0) ? 1.0 : 0.0;
+  };
+  if (C.nonzero_guess) {
+    kry_rows(a, g, a.sptr, a.scol, a.sval, x, start);
+  } else {
+    for (int i = g.r0 + threadIdx.x; i < g.r1; i += blockDim.x) {
+      x[i] = 0.0;
+      start(i, 0.0);
+    }
+  }
+  cta_sum<double, 3>(v, sh);
+  const double bb = v[1], thr = C.rtol * sqrt(bb);
+  double rnorm0 = sqrt(v[0]), rn = rnorm0;
+  int status = kry_start_status(v[2], bb), it = 0;
+  bool timed = false;
+  if (status == GBS_OK) {  // b = 0
+    kry_zero_x(g, x);
+    rn = rnorm0 = 0.0;
+  } else if (status < 0 && rnorm0 <= thr) {
+    status = GBS_OK;  // x0 already meets the test
+  }
+  double pend = 0.0;  // eta of the x update not yet applied (x += eta D^-1 d)
+  bool has_pend = false;
+  if (status < 0) {
+    // v = B y1 (= A t), rt.v
+    double sg[1] = {0.0};
+    auto f0 = [&](int i, double y) {
+      by1[i] = y;
+      vv[i] = y;
+      sg[0] = fma(rt[i], y, sg[0]);
+    };
+    kry_rows(a, g, a.sptr, a.scol, a.sval, t, f0);
+    it = 1;
+    cta_sum<double, 1>(sg, sh);
+    double sigma = sg[0], rho = v[0];  // rho = rt.r0 = ||r0||^2
+    double tau = rnorm0, theta = 0.0, eta = 0.0;
+    int m = 0;
+    for (;;) {
+      if (!isfinite(tau) || !isfinite(rho)) {
+        status = GBS_ERR_NAN;
+        break;
+      }
+      if (sigma == 0.0 || rho == 0.0) {
+        status = GBS_ERR_BREAKDOWN;
+        break;
+      }
+      const double alpha = rho / sigma;
+      ++it;  // the product B y2 of this step
+      // half step 1 with (y1, B y1); y2 = y1 - alpha v, t = D^-1 y2
+      double coef = theta * theta * eta / alpha;
+      double s1[1] = {0.0};
+      for (int i = g.r0 + threadIdx.x; i < g.r1; i += blockDim.x) {
+        const double y1i = y1[i];
+        const double y2i = y1i - alpha * vv[i];
+        y2[i] = y2i;
+        t[i] = dinv[i] * y2i;
+        const double wn = w[i] - alpha * by1[i];
+        w[i] = wn;
+        d[i] = y1i + coef * d[i];
+        s1[0] = fma(wn, wn, s1[0]);
+      }
+      cta_sum<double, 1>(s1, sh);
+      theta = sqrt(s1[0]) / tau;
+      double c = 1.0 / sqrt(1.0 + theta * theta);
+      tau = tau * theta * c;
+      eta = c * c * alpha;
+      ++m;
+      rn = tau * sqrt((double)(m + 1));
+      pend = eta;
+      has_pend = true;
+      if (!isfinite(rn)) {
+        status = GBS_ERR_NAN;
+        break;
+      }
+      if (rn <= thr) {
+        status = GBS_OK;
+        break;
+      }
+      // B y2 (= A t) fused with half step 1's x update and half step 2
+      coef = theta * theta * eta / alpha;
+      const double e1 = eta;
+      double s2[2] = {0.0, 0.0};
+      auto f1 = [&](int i, double y) {
+        by2[i] = y;
+        const double di = d[i];
+        x[i] = fma(e1, dinv[i] * di, x[i]);
+        d[i] = y2[i] + coef * di;
+        const double wn = w[i] - alpha * y;
+        w[i] = wn;
+        s2[0] = fma(wn, wn, s2[0]);
+        s2[1] = fma(rt[i], wn, s2[1]);
+      };
+      kry_rows(a, g, a.sptr, a.scol, a.sval, t, f1);
+      cta_sum<double, 2>(s2, sh);
+      theta = sqrt(s2[0]) / tau;
+      c = 1.0 / sqrt(1.0 + theta * theta);
+      tau = tau * theta * c;
+      eta = c * c * alpha;
+      ++m;
+      rn = tau * sqrt((double)(m + 1));
+      pend = eta;
+      if (!isfinite(rn)) {
+        status = GBS_ERR_NAN;
+        break;
+      }
+      if (rn <= thr) {
+        status = GBS_OK;
+        break;
+      }
+      if (it >= C.maxit) {
+        status = GBS_ERR_MAXIT;
+        break;
+      }
+      if (kry_timed_out(a, sh)) {
+        timed = true;
+        break;
+      }
+      const double beta = s2[1] / rho;
+      rho = s2[1];
+      // y1 = w + beta y2, t = D^-1 y1, half step 2's x update
+      const double e2 = eta;
+      for (int i = g.r0 + threadIdx.x; i < g.r1; i += blockDim.x) {
+        const double dv = dinv[i];
+        const double y = w[i] + beta * y2[i];
+        y1[i] = y;
+        t[i] = dv * y;
+        x[i] = fma(e2, dv * d[i], x[i]);
+      }
+      has_pend = false;
+      __syncthreads();
+      // B y1 (= A t), v = B y1 + beta (B y2 + beta v), rt.v
+      double s3[1] = {0.0};
+      auto f2 = [&](int i, double y) {
+        by1[i] = y;
+        const double vn = y + beta * (by2[i] + beta * vv[i]);
+        vv[i] = vn;
+        s3[0] = fma(rt[i], vn, s3[0]);
+      };
+      kry_rows(a, g, a.sptr, a.scol, a.sval, t, f2);
+      ++it;
+      cta_sum<double, 1>(s3, sh);
+      sigma = s3[0];
+    }
+  }
+  if (has_pend)
+    for (int i = g.r0 + threadIdx.x; i < g.r1; i += blockDim.x)
+      x[i] = fma(pend, dinv[i] * d[i], x[i]);
+  kry_close(a, g, sh, status, timed, it, bb, rnorm0, rn);
+}
+
+template <int METHOD>
+__global__ void __launch_bounds__(CTA_TPB, 1) k_cta_krylov(KrylovArgs a) {
+  __shared__ CtaShared sh;
+  const KSys g = kry_system(a);
+  if (METHOD == GBS_KSP_BICG) kry_bicg(a, g, sh);
+  else kry_tfqmr(a, g, sh);
+}
+
+// ------------------------------------------------------------------ transpose
+
+// Transposed COO indices, local to each system: nonzero p of row r (system s,
+// first row o_s) becomes (col_p - o_s, r - o_s).  Its COO index is p, so the
+// transpose's numeric stage reads A's CSR values directly.
+__global__ void k_transpose_coo(int64_t nrows, int32_t nsys, const int64_t *__restrict__ row_off,
+                                const int32_t *__restrict__ row_ptr,
+                                const int32_t *__restrict__ col, int32_t *__restrict__ ti,
+                                int32_t *__restrict__ tj) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nsys;  // row_off[lo] <= r < row_off[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (row_off[mid] <= r) lo = mid;
+      else hi = mid;
+    }
+    const int64_t o = row_off[lo];
+    for (int32_t p = row_ptr[r]; p < row_ptr[r + 1]; ++p) {
+      ti[p] = col[p] - (int32_t)o;
+      tj[p] = (int32_t)(r - o);
+    }
+  }
+}
+
+// nnz offsets of the systems: row_ptr at each system's first row.
+__global__ void k_system_nnz_off(int32_t nsys, const int64_t *__restrict__ row_off,
+                                 const int32_t *__restrict__ row_ptr, int64_t *__restrict__ out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s <= nsys) out[s] = row_ptr[row_off[s]];
+}
+
+namespace {
+struct DevBuf {  // device scratch freed on every exit path
+  void *p = nullptr;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+};
+unsigned grid_rows(int64_t n) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 1 << 16));
+}
+}  // namespace
+
+static int build_transpose(gbs_mat A, cudaStream_t s) {
+  const int32_t ns = A->nsys;
+  DevBuf off, ti, tj, cnt;
+  const size_t m = (size_t)std::max<int64_t>(A->nnz, 1);
+  GBS_TRY_CUDA(cudaMalloc(&off.p, sizeof(int64_t) * (ns + 1)));
+  GBS_TRY_CUDA(cudaMalloc(&cnt.p, sizeof(int64_t) * (ns + 1)));
+  GBS_TRY_CUDA(cudaMalloc(&ti.p, sizeof(int32_t) * m));
+  GBS_TRY_CUDA(cudaMalloc(&tj.p, sizeof(int32_t) * m));
+  GBS_TRY_CUDA(cudaMemcpyAsync(off.p, A->row_off_h.data(), sizeof(int64_t) * (ns + 1),
+                               cudaMemcpyHostToDevice, s));
+  std::vector<int64_t> coo_off(ns + 1, 0);
+  if (A->nrows > 0) {
+    k_transpose_coo<<<grid_rows(A->nrows), 256, 0, s>>>(A->nrows, ns, (const int64_t *)off.p,
+                                                        A->row_ptr, A->col, (int32_t *)ti.p,
+                                                        (int32_t *)tj.p);
+    GBS_LAUNCHED(1);
+  }
+  k_system_nnz_off<<<(ns + 256) / 256, 256, 0, s>>>(ns, (const int64_t *)off.p, A->row_ptr,
+                                                    (int64_t *)cnt.p);
+  GBS_LAUNCHED(1);
+  GBS_TRY_CUDA(cudaMemcpyAsync(coo_off.data(), cnt.p, sizeof(int64_t) * (ns + 1),
+                               cudaMemcpyDeviceToHost, s));
+  GBS_TRY_CUDA(cudaStreamSynchronize(s));
+  gbs_mat T = new (std::nothrow) gbs_mat_s();
+  if (!T) return GBS_ERR_ALLOC;
+  T->device = A->device;
+  T->nrows = A->ncols;
+  T->ncols = A->nrows;
+  T->ncoo = A->nnz;
+  T->nsys = ns;
+  T->batched = A->batched;
+  T->row_off_h = A->row_off_h;
+  int st = symbolic(T, (const int32_t *)ti.p, (const int32_t *)tj.p,
+                    A->batched ? coo_off.data() : nullptr, s);
+  if (st == GBS_OK) st = sell_build(T, s);
+  if (st == GBS_OK && (T->nnz != A->nnz || T->nslices != A->nslices)) {
+    set_error("transpose: %lld nonzeros in %lld slices, expected %lld in %lld",
+              (long long)T->nnz, (long long)T->nslices, (long long)A->nnz,
+              (long long)A->nslices);
+    st = GBS_ERR_CUDA;
+  }
+  if (st != GBS_OK) {
+    free_handle(T);
+    return st;
+  }
+  A->At = T;
+  A->at_version = -1;
+  return GBS_OK;
+}
+
+// Sliced copy of A, work vectors, per-system ranges and (BiCG) the transpose
+// with A's current values.
+static int ensure_krylov(gbs_mat A, bool transpose, cudaStream_t s) {
+  GBS_TRY(sell_build(A, s));
+  if (!A->kv)
+    GBS_TRY_CUDA(cudaMalloc(&A->kv, sizeof(double) * KRYLOV_NVEC *
+                                        (size_t)std::max<int64_t>(A->nrows, 1)));
+  if (!A->sys_row0) {
+    std::vector<int32_t> r0(A->nsys + 1), s0(A->nsys + 1);
+    for (int32_t q = 0; q <= A->nsys; ++q) {
+      r0[q] = (int32_t)A->row_off_h[q];
+      s0[q] = A->sell_slice0_h[q];
+    }
+    int32_t *d = nullptr;
+    GBS_TRY_CUDA(cudaMalloc(&d, sizeof(int32_t) * 2 * (A->nsys + 1)));
+    A->sys_row0 = d;
+    A->sys_slice0 = d + A->nsys + 1;
+    GBS_TRY_CUDA(cudaMemcpy(A->sys_row0, r0.data(), sizeof(int32_t) * (A->nsys + 1),
+                            cudaMemcpyHostToDevice));
+    GBS_TRY_CUDA(cudaMemcpy(A->sys_slice0, s0.data(), sizeof(int32_t) * (A->nsys + 1),
+                            cudaMemcpyHostToDevice));
+  }
+  if (transpose) {
+    if (!A->At) GBS_TRY(build_transpose(A, s));
+    if (A->at_version != A->values_version) {
+      GBS_TRY(launch_set_values(A->At, A->val, GBS_INSERT, s));
+      A->at_version = A->values_version;
+    }
+  }
+  return GBS_OK;
+}
+
+int solve_krylov(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool per_system,
+                 cudaStream_t s) {
+  const bool bicg = o.method == GBS_KSP_BICG;
+  GBS_TRY(ensure_solver_workspace(A, false));
+  GBS_TRY(ensure_krylov(A, bicg, s));
+  A->last_count = per_system ? A->nsys : 1;
+  A->last_ensemble = !per_system;
+  A->trips_counted = true;
+  A->last_solver = GBS_SOLVER_CTA;
+  GBS_TRY_CUDA(cudaMemsetAsync(A->ctl, 0, sizeof(DevCtl), s));
+  GBS_TRY(put_call(A->call, call_args(b, x, o), s, A->ctl));
+  KrylovArgs a;
+  memset(&a, 0, sizeof(a));
+  a.ensemble = per_system ? 0 : 1;
+  a.nrows = (int32_t)A->nrows;
+  a.nslices = (int32_t)A->nslices;
+  a.order = A->cta_order;
+  a.sys_row0 = A->sys_row0;
+  a.sys_slice0 = A->sys_slice0;
+  a.sptr = A->sell_ptr;
+  a.srow0 = A->sell_row0;
+  a.scol = A->sell_col;
+  a.sval = A->sell_val;
+  if (bicg) {
+    a.tptr = A->At->sell_ptr;
+    a.tcol = A->At->sell_col;
+    a.tval = A->At->sell_val;
+  }
+  a.stream_matrix = stream_matrix(A, bicg ? 24 : 12);
+  a.dinv = A->dinv;
+  for (int k = 0; k < KRYLOV_NVEC; ++k) a.v[k] = A->kv + (size_t)k * (size_t)A->nrows;
+  a.st = A->st;
+  a.ctl = A->ctl;
+  a.call = A->call;
+  const unsigned grid = per_system ? (unsigned)A->nsys : 1u;
+  if (bicg) k_cta_krylov<GBS_KSP_BICG><<<grid, CTA_TPB, 0, s>>>(a);
+  else k_cta_krylov<GBS_KSP_TFQMR><<<grid, CTA_TPB, 0, s>>>(a);
+  GBS_LAUNCHED(1);
+  return GBS_OK;
+}
+
+}  // namespace gbs

@@ -199,7 +199,7 @@ static int64_t max_trips_for(const ksp_opts &o) {
              : (int64_t)o.maxit + 4;
 }
 
-static CallArgs call_args(const double *b, double *x, const ksp_opts &o) {
+CallArgs call_args(const double *b, double *x, const ksp_opts &o) {
   CallArgs c;
   memset(&c, 0, sizeof(c));
   c.b = b;
@@ -215,7 +215,7 @@ static CallArgs call_args(const double *b, double *x, const ksp_opts &o) {
   return c;
 }
 
-static int put_call(CallArgs *dst, const CallArgs &c, cudaStream_t s, DevCtl *ctl = nullptr) {
+int put_call(CallArgs *dst, const CallArgs &c, cudaStream_t s, DevCtl *ctl) {
   k_put_call<<<1, 1, 0, s>>>(dst, c, ctl);
   GBS_LAUNCHED(1);
   return GBS_OK;

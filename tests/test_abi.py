@@ -54,9 +54,9 @@ def test_struct_sizes_match_header():
 #include <stddef.h>
 #include "gbs.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu\n", sizeof(ksp_opts), sizeof(ksp_result),
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(ksp_opts), sizeof(ksp_result),
          offsetof(ksp_opts, timeout_ns), offsetof(ksp_opts, host_loop),
-         offsetof(ksp_result, true_rel_residual));
+         offsetof(ksp_opts, method), offsetof(ksp_result, true_rel_residual));
   return 0;
 }
 """
@@ -69,7 +69,7 @@ int main(void) {
     got = [int(v) for v in out]
     assert got == [ctypes.sizeof(B.KspOpts), ctypes.sizeof(B.KspResult),
                    B.KspOpts.timeout_ns.offset, B.KspOpts.host_loop.offset,
-                   B.KspResult.true_rel_residual.offset]
+                   B.KspOpts.method.offset, B.KspResult.true_rel_residual.offset]
 
 
 def test_opts_defaults_and_errors_without_gpu(lib):
