@@ -31,6 +31,10 @@ prints its own JSON line; the default is the Q1 benchmark above):
       solve, plus the batched adjoint
   vec vector COO assembly of the Q1 96^3 element load vector (7.08M entries
       into 912,673 nodes): symbolic and numeric stage times, numeric GB/s
+  nonsym  batched TFQMR and BiCG (Jacobi) on 16, 64, 256 and 1024 independent
+      2D convection-diffusion systems (1k-50k rows each, Peclet 1-100): solves
+      per second of the batched solve on the per-CTA solver and on the phase
+      kernels, against the stacked ensemble solve (Sec. 7's comparison)
 
 --impl reference times the FP64 CPU oracle (the plain C implementation in
 oracle/) on a bounded sample of the same workload on the host cores.
@@ -246,6 +250,22 @@ def _base_line(args, metric_value, config, extra):
     return line
 
 
+def tfqmr_alg_bytes(n: int, nnz: int, products: int) -> float:
+    """Algorithmic bytes of the fused TFQMR loop per product with A D^-1: the
+    matrix once (12 B per nonzero) and 17.5 FP64 vectors of n (a step of two
+    products reads or writes 35: the first half step 10, the product fused
+    with the second half step 10 plus its gathered vector, the y1 / x update
+    8, the product with the v update 5 plus its gathered vector)."""
+    return products * (12.0 * nnz + 140.0 * n)
+
+
+def bicg_alg_bytes(n: int, nnz: int, iterations: int) -> float:
+    """Algorithmic bytes of the fused BiCG loop per iteration: A and A^T once
+    each (24 B per nonzero) and 23 FP64 vectors of n (directions 7, products 4
+    plus the two gathered vectors, updates 10)."""
+    return iterations * (24.0 * nnz + 184.0 * n)
+
+
 def run_suite(args):
     import numpy as np
     import torch
@@ -407,6 +427,61 @@ def run_suite(args):
              "batched_vs_sequential": rows["batched_fp64"]["s"] / rows["sequential_fp64"]["s"],
              "batched_vs_ensemble": rows["batched_fp64"]["s"] / rows["ensemble_fp64"]["s"],
              "refined_vs_fp64": rows["batched_fp32_refined"]["s"] / rows["batched_fp64"]["s"]})
+        print(json.dumps(line), flush=True)
+        return 0
+    if args.workload == "nonsym":
+        sweep = {}
+        for nsys in (16, 64, 256, 1024):
+            bt = W.convdiff_batch(nsys, seed=W.SEED_C6)
+            A = B.Mat.from_coo_batched(bt.nrows, bt.ncoo, t(bt.i), t(bt.j))
+            A.set_values(t(bt.v))
+            b = t(bt.b)
+            x = torch.empty_like(b)
+            ro = bt.row_off
+            nnz_s = None
+            entry = {"rows": int(bt.nrows.sum()), "nnz": A.nnz}
+            for mname, method in (("tfqmr", B.KSP_TFQMR), ("bicg", B.KSP_BICG)):
+                res = {}
+                for sname, solver in (("cta", B.SOLVER_CTA), ("phases", B.SOLVER_PHASES)):
+                    A.set_solver(solver)
+                    ts, (_, rs) = _ev_time(stream, lambda: A.solve_batched(
+                        b, x, rtol=1e-8, method=method), reps=1, warm=1)
+                    if nnz_s is None:
+                        rp = A.csr()[0].cpu().numpy()
+                        nnz_s = np.diff(rp[ro])
+                    its = np.array([q["iterations"] for q in rs])
+                    alg = (tfqmr_alg_bytes if method == B.KSP_TFQMR else bicg_alg_bytes)(
+                        np.diff(ro), nnz_s, its).sum()
+                    res[f"batched_{sname}"] = {
+                        "s": ts, "solves_per_s": nsys / ts,
+                        "ok": int(sum(q["status"] == B.OK for q in rs)),
+                        "iterations_max": int(its.max()), "iterations_mean": float(its.mean()),
+                        "gbs": float(alg / ts / 1e9), "frac": float(alg / ts / 1e9 / hbm)}
+                A.set_solver(B.SOLVER_AUTO)
+                _, rs = A.solve_batched(b, x, rtol=1e-8, method=method)
+                res["auto_picks"] = "cta" if rs[0]["solver"] == B.SOLVER_CTA else "phases"
+                A.set_solver(B.SOLVER_PHASES)
+                te, (_, re) = _ev_time(stream, lambda: A.solve(b, x, rtol=1e-8, method=method),
+                                       reps=1, warm=1)
+                res["ensemble"] = {"s": te, "solves_per_s": nsys / te, "status": re["status"],
+                                   "iterations": re["iterations"]}
+                best = min(res["batched_cta"]["s"], res["batched_phases"]["s"])
+                res["batched_vs_ensemble_speedup"] = te / best
+                entry[mname] = res
+            sweep[str(nsys)] = entry
+            A.close()
+        top = sweep["1024"]["tfqmr"]
+        line = _base_line(
+            args, min(top["batched_cta"]["s"], top["batched_phases"]["s"]),
+            {"workload": "convdiff_batch: 2D upwind convection-diffusion systems, rows "
+                         "uniform on [1k, 50k], Peclet log-uniform [1, 100], seed 1006; "
+                         "value = batched TFQMR on 1024 systems",
+             "batch_sizes": [16, 64, 256, 1024]},
+            {"sweep": sweep,
+             "what": "solves_per_s = systems / solve time; ensemble = the stacked system "
+                     "with one global norm on the phase kernels; gbs = algorithmic bytes "
+                     "(bench.tfqmr_alg_bytes / bicg_alg_bytes over each system's "
+                     "iterations) / time"})
         print(json.dumps(line), flush=True)
         return 0
     raise SystemExit(f"unknown workload {args.workload}")
@@ -652,7 +727,7 @@ def main():
     ap.add_argument("--impl", default="gbs", choices=["gbs", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "vec"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "vec", "nonsym"],
                     help="c2 = the benchmark (default); c3/c4/c5 = comparison runs")
     ap.add_argument("--host-loop", action="store_true",
                     help="run the solves' loop from the host (for profiler launch lists)")

@@ -52,6 +52,8 @@ struct SysState {
   double prev_rn;   // refined: previous outer residual norm
   double r0in;      // refined: inner stopping threshold (target x initial norm)
   double tt;        // ||b - A x||^2 at exit
+  double tau, theta, eta;  // TFQMR: quasi-residual recurrence (eta of the last half step)
+  double coef;             // TFQMR: theta^2 eta / alpha for the next d update
   int32_t status;
   int32_t active;   // 1 while the system still iterates
   int32_t iterations;
@@ -61,8 +63,18 @@ struct SysState {
   int32_t stall;
   int32_t first;    // refined: next p update is p = z
   int32_t zero_x;   // b == 0: x must be set to 0
+  int32_t m;        // TFQMR: half steps taken
+  int32_t pend;     // TFQMR: x += eta D^-1 d of the last half step not yet applied
   int32_t pad;
 };
+
+// Work vectors of the nonsymmetric solvers (TFQMR: w, y1, y2, rt, v, B y1,
+// B y2, d, t; BiCG uses the first six as r, rt, p, pt, q, qt).
+constexpr int KRYLOV_NVEC = 9;
+
+// Cached solve graphs of a handle, by loop kind.
+enum { GBS_GRAPH_CG = 0, GBS_GRAPH_CG32 = 1, GBS_GRAPH_BICG = 2, GBS_GRAPH_TFQMR = 3,
+       GBS_GRAPH_KINDS = 4 };
 
 // Per-solve control words (device).  Zeroed before every solve.
 struct DevCtl {
@@ -161,8 +173,9 @@ struct gbs_mat_s {
   bool trips_counted = true;         // launch counter already holds the last loop
   int32_t last_solver = 0;           // solver the last solve ran
 
-  // cached executable graphs [refined][per_system] of the solve loop
-  cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  // cached executable graphs [loop kind][per_system] of the solve loop
+  cudaGraphExec_t graph[gbs::GBS_GRAPH_KINDS][2] = {};
+  int32_t loop_body = 3;             // kernels per trip of the last phase-kernel loop
 
   // nonsymmetric solvers (krylov.cu): the transpose as an internal handle
   // (its CSR and sliced copy), refreshed when the values change; the work
@@ -170,7 +183,7 @@ struct gbs_mat_s {
   int64_t values_version = 0;       // bumped by every numeric stage
   gbs_mat_s *At = nullptr;
   int64_t at_version = -1;          // values_version the transpose holds
-  double *kv = nullptr;             // KRYLOV_NVEC vectors of nrows
+  double *kv = nullptr;             // gbs::KRYLOV_NVEC vectors of nrows
   int32_t *sys_row0 = nullptr, *sys_slice0 = nullptr;  // one allocation (sys_row0)
 };
 

@@ -19,6 +19,15 @@
 //   deferred into the next pass over the rows (it only needs that half
 //   step's eta and d), and applied at exit when the loop ends on a half step.
 //
+// The same two methods also run on the grid-wide phase kernels (the CG
+// driver's block tables, last-arriver reductions and graph WHILE loop): for
+// one large system, and for the stacked "ensemble" of Sec. 7 that a standard
+// solver would see.  BiCG: setup, WHILE { products and pt.q; updates with
+// ||r||^2 and (D^-1 r).rt; directions }, closing residual.  TFQMR: setup,
+// WHILE { B y1 with rt.v; half step 1; B y2 fused with half step 2; y1 and
+// the x update }, the x update left pending by a half step that ended the
+// solve, closing residual.
+//
 // The oracle counts, statuses and tests are followed exactly; only the
 // summation order of the dot products differs (a fixed tree here).
 #include <cuda_runtime.h>
@@ -35,8 +44,6 @@
 #include "phases.cuh"
 
 namespace gbs {
-
-constexpr int KRYLOV_NVEC = 9;  // TFQMR: w, y1, y2, rt, v, B y1, B y2, d, t
 
 struct KrylovArgs {
   int32_t ensemble;                        // 1: one CTA over the whole matrix
@@ -423,6 +430,515 @@ __global__ void __launch_bounds__(CTA_TPB, 1) k_cta_krylov(KrylovArgs a) {
   else kry_tfqmr(a, g, sh);
 }
 
+// ------------------------------------------------------------------ phases
+//
+// Grid-wide versions: every kernel walks a block table, so one system spans
+// the whole GPU; per-system scalars live in SysState and are finished by the
+// last CTA to reduce (phases.cuh).  Row products use the sliced copies (the
+// block tables carry slice offsets whatever the plan's kernel).
+
+struct NsView {
+  double alpha, beta, eta, coef;
+  int first;
+};
+__device__ __forceinline__ NsView ns_view(const PcgArgs &a, int s) {
+  const SysState *S = a.st + s;
+  return NsView{ldcg(&S->alpha), ldcg(&S->beta), ldcg(&S->eta), ldcg(&S->coef),
+                ldcg(&S->first)};
+}
+
+// Row products of block b with A^T's sliced copy.
+template <class F>
+__device__ __forceinline__ void rows_t(const PcgArgs &a, int b, const double *x, F &f) {
+  const int s0 = __ldg(a.ta.slice0 + b), s1 = __ldg(a.ta.slice0 + b + 1);
+  if (a.stream_matrix) sell_rows<double, true, true>(a.tptr, a.srow0, a.tcol, a.tval, x, s0, s1, f);
+  else sell_rows<double, false, true>(a.tptr, a.srow0, a.tcol, a.tval, x, s0, s1, f);
+}
+
+__device__ __forceinline__ void ns_activate(const PcgArgs &a, SysState &S, int status) {
+  if (status >= 0) {
+    S.status = status;
+    S.active = 0;
+  } else {
+    S.status = GBS_OK;
+    S.active = 1;
+    atomicAdd(&a.ctl->n_active, 1);
+  }
+}
+
+// BiCG's tests before an iteration: NAN, converged, limit, rho = 0.
+__device__ __forceinline__ int bicg_top(const CallArgs &C, const SysState &S) {
+  if (!isfinite(S.rnorm)) return GBS_ERR_NAN;
+  if (S.rnorm <= C.rtol * sqrt(S.bb)) return GBS_OK;
+  if (S.iterations >= C.maxit) return GBS_ERR_MAXIT;
+  if (S.rho == 0.0) return GBS_ERR_BREAKDOWN;
+  return -1;
+}
+
+// r = b - A x0, rt = r, p = pt = D^-1 r; r.r, b.b, (D^-1 r).rt, missing
+// diagonals; fin: start-up and pre-iteration tests.  Table A.
+__device__ __forceinline__ void bicg_setup(const PcgArgs &a, double *red) {
+  const CallArgs &C = *a.call;
+  const double *b = C.b;
+  double *x = C.x;
+  double *r = a.kv[0], *rt = a.kv[1], *p = a.kv[2], *pt = a.kv[3];
+  auto want = [&](int) -> int { return 1; };
+  auto row = [&](int i, double ax, double(&acc)[4]) {
+    const double bv = b[i], rv = bv - ax, dv = a.dinv[i], z = dv * rv;
+    r[i] = rv;
+    rt[i] = rv;
+    p[i] = z;
+    pt[i] = z;
+    acc[0] = fma(rv, rv, acc[0]);
+    acc[1] = fma(bv, bv, acc[1]);
+    acc[2] = fma(z, rv, acc[2]);
+    acc[3] += (dv == 0.0) ? 1.0 : 0.0;
+  };
+  auto work = [&](int, int blk, int r0, int r1, double(&acc)[4]) {
+    if (C.nonzero_guess) {
+      auto f = [&](int i, double ax) { row(i, ax, acc); };
+      row_products<double, 0>(a, blk, r0, r1, a.val, a.sval, x, f);
+    } else {
+      for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        x[i] = 0.0;
+        row(i, 0.0, acc);
+      }
+    }
+  };
+  auto fin = [&](int s, double(&tot)[4]) {
+    SysState &S = a.st[s];
+    memset(&S, 0, sizeof(SysState));
+    S.bb = tot[1];
+    S.rr = tot[0];
+    S.rho = tot[2];
+    S.rnorm0 = S.rnorm = sqrt(tot[0]);
+    int st = kry_start_status(tot[3], tot[1]);
+    if (st == GBS_OK) {
+      S.zero_x = 1;
+      S.rnorm0 = S.rnorm = 0.0;
+    } else if (st < 0) {
+      st = bicg_top(C, S);
+    }
+    ns_activate(a, S, st);
+  };
+  walk<4>(a, a.ta, 0, red, want, work, fin);
+}
+
+// q = A p with pt.q, qt = A^T pt; fin: alpha.  Table A.
+__device__ __forceinline__ void bicg_products(const PcgArgs &a, double *red) {
+  const double *p = a.kv[2], *pt = a.kv[3];
+  double *q = a.kv[4], *qt = a.kv[5];
+  auto want = [&](int s) -> int { return sys_active(a, s) ? 1 : 0; };
+  auto work = [&](int, int blk, int r0, int r1, double(&acc)[1]) {
+    double sg = acc[0];
+    auto fq = [&](int i, double y) {
+      q[i] = y;
+      sg = fma(__ldg(pt + i), y, sg);
+    };
+    row_products<double, 0>(a, blk, r0, r1, a.val, a.sval, p, fq);
+    auto fqt = [&](int i, double y) { qt[i] = y; };
+    rows_t(a, blk, pt, fqt);
+    acc[0] = sg;
+  };
+  auto fin = [&](int s, double(&tot)[1]) {
+    SysState &S = a.st[s];
+    S.iterations += 1;
+    if (isnan(tot[0])) deactivate(a, S, GBS_ERR_NAN);
+    else if (tot[0] == 0.0) deactivate(a, S, GBS_ERR_BREAKDOWN);
+    else S.alpha = S.rho / tot[0];
+  };
+  walk<1>(a, a.ta, 0, red, want, work, fin);
+}
+
+// x += alpha p, r -= alpha q, rt -= alpha qt; ||r||^2, (D^-1 r).rt; fin:
+// the tests of the next iteration, beta.  Table E.
+__device__ __forceinline__ void bicg_update(const PcgArgs &a, double *red) {
+  const CallArgs &C = *a.call;
+  double *x = C.x;
+  double *r = a.kv[0], *rt = a.kv[1];
+  const double *p = a.kv[2], *q = a.kv[4], *qt = a.kv[5];
+  NsView v{};
+  auto want = [&](int s) -> int {
+    if (!sys_active(a, s)) return 0;
+    v = ns_view(a, s);
+    return 1;
+  };
+  auto work = [&](int, int, int r0, int r1, double(&acc)[2]) {
+    const double al = v.alpha;
+    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      x[i] = fma(al, p[i], x[i]);
+      const double rv = fma(-al, q[i], r[i]);
+      const double rtv = fma(-al, qt[i], rt[i]);
+      r[i] = rv;
+      rt[i] = rtv;
+      acc[0] = fma(rv, rv, acc[0]);
+      acc[1] = fma(a.dinv[i] * rv, rtv, acc[1]);
+    }
+  };
+  auto fin = [&](int s, double(&tot)[2]) {
+    SysState &S = a.st[s];
+    const double beta = tot[1] / S.rho;
+    S.rr = tot[0];
+    S.rnorm = sqrt(tot[0]);
+    S.rho = tot[1];
+    const int st = bicg_top(C, S);
+    if (st >= 0) deactivate(a, S, st);
+    else S.beta = beta;
+  };
+  walk<2>(a, a.te, a.part_e, red, want, work, fin);
+}
+
+// p = D^-1 r + beta p, pt = D^-1 rt + beta pt.  Table E.
+__device__ __forceinline__ void bicg_direction(const PcgArgs &a, double *red) {
+  const double *r = a.kv[0], *rt = a.kv[1];
+  double *p = a.kv[2], *pt = a.kv[3];
+  NsView v{};
+  auto want = [&](int s) -> int {
+    if (!sys_active(a, s)) return 0;
+    v = ns_view(a, s);
+    return 1;
+  };
+  auto work = [&](int, int, int r0, int r1, double(&)[1]) {
+    const double be = v.beta;
+    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      const double dv = a.dinv[i];
+      p[i] = fma(be, p[i], dv * r[i]);
+      pt[i] = fma(be, pt[i], dv * rt[i]);
+    }
+  };
+  auto fin = [&](int, double(&)[1]) {};
+  walk<0>(a, a.te, a.part_e, red, want, work, fin);
+}
+
+// One TFQMR half step's scalars from ||w||^2: theta, c, tau, eta, m; returns
+// the bound tau sqrt(m + 1).
+__device__ __forceinline__ double tfq_half(SysState &S, double ww) {
+  S.theta = sqrt(ww) / S.tau;
+  const double c = 1.0 / sqrt(1.0 + S.theta * S.theta);
+  S.tau = S.tau * S.theta * c;
+  S.eta = c * c * S.alpha;
+  S.m += 1;
+  return S.tau * sqrt((double)(S.m + 1));
+}
+
+// r0 = b - A x0 into w, y1, rt; d = 0; t = D^-1 r0; r.r, b.b, missing
+// diagonals; fin: start-up tests.  Table A.
+__device__ __forceinline__ void tfq_setup(const PcgArgs &a, double *red) {
+  const CallArgs &C = *a.call;
+  const double *b = C.b;
+  double *x = C.x;
+  double *w = a.kv[0], *y1 = a.kv[1], *rt = a.kv[3], *d = a.kv[7], *t = a.kv[8];
+  auto want = [&](int) -> int { return 1; };
+  auto row = [&](int i, double ax, double(&acc)[3]) {
+    const double bv = b[i], rv = bv - ax, dv = a.dinv[i];
+    w[i] = rv;
+    y1[i] = rv;
+    rt[i] = rv;
+    d[i] = 0.0;
+    t[i] = dv * rv;
+    acc[0] = fma(rv, rv, acc[0]);
+    acc[1] = fma(bv, bv, acc[1]);
+    acc[2] += (dv == 0.0) ? 1.0 : 0.0;
+  };
+  auto work = [&](int, int blk, int r0, int r1, double(&acc)[3]) {
+    if (C.nonzero_guess) {
+      auto f = [&](int i, double ax) { row(i, ax, acc); };
+      row_products<double, 0>(a, blk, r0, r1, a.val, a.sval, x, f);
+    } else {
+      for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        x[i] = 0.0;
+        row(i, 0.0, acc);
+      }
+    }
+  };
+  auto fin = [&](int s, double(&tot)[3]) {
+    SysState &S = a.st[s];
+    memset(&S, 0, sizeof(SysState));
+    S.bb = tot[1];
+    S.rr = tot[0];
+    S.rnorm0 = S.rnorm = sqrt(tot[0]);
+    int st = kry_start_status(tot[2], tot[1]);
+    if (st == GBS_OK) {
+      S.zero_x = 1;
+      S.rnorm0 = S.rnorm = 0.0;
+    } else if (st < 0 && S.rnorm0 <= C.rtol * sqrt(S.bb)) {
+      st = GBS_OK;  // x0 already meets the test
+    }
+    S.rho = tot[0];  // rt.r0 = ||r0||^2
+    S.tau = S.rnorm0;
+    S.first = 1;
+    ns_activate(a, S, st);
+  };
+  walk<3>(a, a.ta, 0, red, want, work, fin);
+}
+
+// B y1 (= A t), v = B y1 (+ beta (B y2 + beta v) after the first step), rt.v;
+// fin: the tests at the top of a step, alpha.  Table A.
+__device__ __forceinline__ void tfq_v(const PcgArgs &a, double *red) {
+  const double *rt = a.kv[3], *by2 = a.kv[6], *t = a.kv[8];
+  double *vv = a.kv[4], *by1 = a.kv[5];
+  NsView v{};
+  auto want = [&](int s) -> int {
+    if (!sys_active(a, s)) return 0;
+    v = ns_view(a, s);
+    return 1;
+  };
+  auto work = [&](int, int blk, int r0, int r1, double(&acc)[1]) {
+    const double be = v.beta;
+    const bool first = v.first != 0;
+    double sg = acc[0];
+    auto f = [&](int i, double y) {
+      by1[i] = y;
+      const double vn = first ? y : y + be * (by2[i] + be * vv[i]);
+      vv[i] = vn;
+      sg = fma(rt[i], vn, sg);
+    };
+    row_products<double, 0>(a, blk, r0, r1, a.val, a.sval, t, f);
+    acc[0] = sg;
+  };
+  auto fin = [&](int s, double(&tot)[1]) {
+    SysState &S = a.st[s];
+    S.iterations += 1;
+    S.first = 0;
+    S.pend = 0;  // the last step's x update has been applied
+    if (!isfinite(S.tau) || !isfinite(S.rho)) deactivate(a, S, GBS_ERR_NAN);
+    else if (tot[0] == 0.0 || S.rho == 0.0) deactivate(a, S, GBS_ERR_BREAKDOWN);
+    else {
+      S.alpha = S.rho / tot[0];
+      S.coef = S.theta * S.theta * S.eta / S.alpha;
+    }
+  };
+  walk<1>(a, a.ta, 0, red, want, work, fin);
+}
+
+// Half step 1: y2 = y1 - alpha v, t = D^-1 y2, w -= alpha B y1,
+// d = y1 + coef d; ||w||^2; fin: its scalars and tests.  Table E.
+__device__ __forceinline__ void tfq_half1(const PcgArgs &a, double *red) {
+  const CallArgs &C = *a.call;
+  const double *y1 = a.kv[1], *vv = a.kv[4], *by1 = a.kv[5];
+  double *w = a.kv[0], *y2 = a.kv[2], *d = a.kv[7], *t = a.kv[8];
+  NsView v{};
+  auto want = [&](int s) -> int {
+    if (!sys_active(a, s)) return 0;
+    v = ns_view(a, s);
+    return 1;
+  };
+  auto work = [&](int, int, int r0, int r1, double(&acc)[1]) {
+    const double al = v.alpha, cf = v.coef;
+    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      const double y1i = y1[i];
+      const double y2i = y1i - al * vv[i];
+      y2[i] = y2i;
+      t[i] = a.dinv[i] * y2i;
+      const double wn = w[i] - al * by1[i];
+      w[i] = wn;
+      d[i] = y1i + cf * d[i];
+      acc[0] = fma(wn, wn, acc[0]);
+    }
+  };
+  auto fin = [&](int s, double(&tot)[1]) {
+    SysState &S = a.st[s];
+    S.iterations += 1;  // the product B y2 of this step
+    const double rn = tfq_half(S, tot[0]);
+    S.rnorm = rn;
+    S.pend = 1;
+    if (!isfinite(rn)) deactivate(a, S, GBS_ERR_NAN);
+    else if (rn <= C.rtol * sqrt(S.bb)) deactivate(a, S, GBS_OK);
+    else S.coef = S.theta * S.theta * S.eta / S.alpha;
+  };
+  walk<1>(a, a.te, a.part_e, red, want, work, fin);
+}
+
+// B y2 (= A t) fused with half step 1's x update and half step 2:
+// x += eta D^-1 d, d = y2 + coef d, w -= alpha B y2; ||w||^2, rt.w; fin:
+// its scalars, tests and beta.  Table A.
+__device__ __forceinline__ void tfq_half2(const PcgArgs &a, double *red) {
+  const CallArgs &C = *a.call;
+  double *x = C.x;
+  const double *y2 = a.kv[2], *rt = a.kv[3], *t = a.kv[8];
+  double *w = a.kv[0], *by2 = a.kv[6], *d = a.kv[7];
+  NsView v{};
+  auto want = [&](int s) -> int {
+    if (!sys_active(a, s)) return 0;
+    v = ns_view(a, s);
+    return 1;
+  };
+  auto work = [&](int, int blk, int r0, int r1, double(&acc)[2]) {
+    const double al = v.alpha, e1 = v.eta, cf = v.coef;
+    double a0 = acc[0], a1 = acc[1];
+    auto f = [&](int i, double y) {
+      by2[i] = y;
+      const double di = d[i];
+      x[i] = fma(e1, a.dinv[i] * di, x[i]);
+      d[i] = y2[i] + cf * di;
+      const double wn = w[i] - al * y;
+      w[i] = wn;
+      a0 = fma(wn, wn, a0);
+      a1 = fma(rt[i], wn, a1);
+    };
+    row_products<double, 0>(a, blk, r0, r1, a.val, a.sval, t, f);
+    acc[0] = a0;
+    acc[1] = a1;
+  };
+  auto fin = [&](int s, double(&tot)[2]) {
+    SysState &S = a.st[s];
+    const double rn = tfq_half(S, tot[0]);
+    S.rnorm = rn;
+    if (!isfinite(rn)) deactivate(a, S, GBS_ERR_NAN);
+    else if (rn <= C.rtol * sqrt(S.bb)) deactivate(a, S, GBS_OK);
+    else if (S.iterations >= C.maxit) deactivate(a, S, GBS_ERR_MAXIT);
+    else {
+      S.beta = tot[1] / S.rho;
+      S.rho = tot[1];
+    }
+  };
+  walk<2>(a, a.ta, 0, red, want, work, fin);
+}
+
+// y1 = w + beta y2, t = D^-1 y1, half step 2's x update.  Table E.
+__device__ __forceinline__ void tfq_next(const PcgArgs &a, double *red) {
+  double *x = a.call->x;
+  const double *w = a.kv[0], *y2 = a.kv[2], *d = a.kv[7];
+  double *y1 = a.kv[1], *t = a.kv[8];
+  NsView v{};
+  auto want = [&](int s) -> int {
+    if (!sys_active(a, s)) return 0;
+    v = ns_view(a, s);
+    return 1;
+  };
+  auto work = [&](int, int, int r0, int r1, double(&)[1]) {
+    const double be = v.beta, e2 = v.eta;
+    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      const double dv = a.dinv[i];
+      const double y = w[i] + be * y2[i];
+      y1[i] = y;
+      t[i] = dv * y;
+      x[i] = fma(e2, dv * d[i], x[i]);
+    }
+  };
+  auto fin = [&](int, double(&)[1]) {};
+  walk<0>(a, a.te, a.part_e, red, want, work, fin);
+}
+
+// The x update of a half step that ended its system's solve.  Table E.
+__device__ __forceinline__ void tfq_pending_x(const PcgArgs &a, double *red) {
+  double *x = a.call->x;
+  const double *d = a.kv[7];
+  double eta = 0.0;
+  auto want = [&](int s) -> int {
+    const SysState *S = a.st + s;
+    if (ldcg(&S->active) || !ldcg(&S->pend)) return 0;
+    eta = ldcg(&S->eta);
+    return 1;
+  };
+  auto work = [&](int, int, int r0, int r1, double(&)[1]) {
+    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x)
+      x[i] = fma(eta, a.dinv[i] * d[i], x[i]);
+  };
+  auto fin = [&](int, double(&)[1]) {};
+  walk<0>(a, a.te, a.part_e, red, want, work, fin);
+}
+
+#define NS_ROWS __launch_bounds__(PHASE_TPB, SELL_MIN_CTAS)
+#define NS_UPD __launch_bounds__(PHASE_TPB)
+
+__device__ __forceinline__ void ns_start_clock(const PcgArgs &a) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->t_start = (int64_t)global_ns();
+}
+
+__global__ void NS_ROWS k_bicg_setup(PcgArgs a) {
+  __shared__ double red[4 * 32];
+  ns_start_clock(a);
+  bicg_setup(a, red);
+}
+__global__ void NS_ROWS k_bicg_products(PcgArgs a) {
+  __shared__ double red[4 * 32];
+  if (!trip_live(a)) return;
+  bicg_products(a, red);
+}
+__global__ void NS_UPD k_bicg_update(PcgArgs a) {
+  __shared__ double red[4 * 32];
+  if (!trip_live(a)) return;
+  bicg_update(a, red);
+}
+__global__ void NS_UPD k_bicg_direction(PcgArgs a) {
+  __shared__ double red[4 * 32];
+  const bool live = trip_live(a);
+  loop_control(a, live);  // after the update's tests: n_active is final
+  if (!live) return;
+  bicg_direction(a, red);
+}
+__global__ void NS_ROWS k_tfq_setup(PcgArgs a) {
+  __shared__ double red[4 * 32];
+  ns_start_clock(a);
+  tfq_setup(a, red);
+}
+__global__ void NS_ROWS k_tfq_v(PcgArgs a) {
+  __shared__ double red[4 * 32];
+  if (!trip_live(a)) return;
+  tfq_v(a, red);
+}
+__global__ void NS_UPD k_tfq_half1(PcgArgs a) {
+  __shared__ double red[4 * 32];
+  if (!trip_live(a)) return;
+  tfq_half1(a, red);
+}
+__global__ void NS_ROWS k_tfq_half2(PcgArgs a) {
+  __shared__ double red[4 * 32];
+  if (!trip_live(a)) return;
+  tfq_half2(a, red);
+}
+__global__ void NS_UPD k_tfq_next(PcgArgs a) {
+  __shared__ double red[4 * 32];
+  const bool live = trip_live(a);
+  loop_control(a, live);  // after half step 2's tests: n_active is final
+  if (!live) return;
+  tfq_next(a, red);
+}
+__global__ void NS_UPD k_tfq_pending_x(PcgArgs a) {
+  __shared__ double red[4 * 32];
+  tfq_pending_x(a, red);
+}
+__global__ void NS_ROWS k_ns_final(PcgArgs a) {
+  __shared__ double red[4 * 32];
+  phase_final<0>(a, red);
+}
+
+static LoopPlan bicg_plan() {
+  LoopPlan P;
+  memset(&P, 0, sizeof(P));
+  P.setup = k_bicg_setup;
+  P.nbody = 3;
+  P.body[0] = k_bicg_products;
+  P.body[1] = k_bicg_update;
+  P.body[2] = k_bicg_direction;
+  P.body_e[1] = P.body_e[2] = true;
+  P.npost = 1;
+  P.post[0] = k_ns_final;
+  return P;
+}
+
+// Body order: the step's first product, half step 1, the product fused with
+// half step 2, then y1 (whose kernel sets the loop condition after half step
+// 2's tests).  A system retired by a later step's top tests leaves one empty
+// trip at most.
+static LoopPlan tfqmr_plan() {
+  LoopPlan P;
+  memset(&P, 0, sizeof(P));
+  P.setup = k_tfq_setup;
+  P.nbody = 4;
+  P.body[0] = k_tfq_v;
+  P.body[1] = k_tfq_half1;
+  P.body[2] = k_tfq_half2;
+  P.body[3] = k_tfq_next;
+  P.body_e[1] = P.body_e[3] = true;
+  P.npost = 2;
+  P.post[0] = k_tfq_pending_x;
+  P.post_e[0] = true;
+  P.post[1] = k_ns_final;
+  return P;
+}
+
 // ------------------------------------------------------------------ transpose
 
 // Transposed COO indices, local to each system: nonzero p of row r (system s,
@@ -557,6 +1073,20 @@ int solve_krylov(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool 
   A->last_count = per_system ? A->nsys : 1;
   A->last_ensemble = !per_system;
   A->trips_counted = true;
+  const bool on_ctas = A->solver == GBS_SOLVER_CTA ||
+                       (A->solver == GBS_SOLVER_AUTO && cta_size_rule(A, per_system));
+  if (!on_ctas) {
+    A->last_solver = GBS_SOLVER_PHASES;
+    if (A->ta.nblocks == 0) {  // empty matrix: nothing to iterate
+      GBS_TRY_CUDA(cudaMemsetAsync(A->st, 0, sizeof(SysState) * A->nsys, s));
+      GBS_TRY_CUDA(cudaMemsetAsync(A->ctl, 0, sizeof(DevCtl), s));
+      return GBS_OK;
+    }
+    PcgArgs pa = make_args(A, per_system, false);
+    pa.stream_matrix = stream_matrix(A, bicg ? 24 : 12);
+    return run_loop(A, bicg ? bicg_plan() : tfqmr_plan(),
+                    bicg ? GBS_GRAPH_BICG : GBS_GRAPH_TFQMR, pa, b, x, o, per_system, s);
+  }
   A->last_solver = GBS_SOLVER_CTA;
   GBS_TRY_CUDA(cudaMemsetAsync(A->ctl, 0, sizeof(DevCtl), s));
   GBS_TRY(put_call(A->call, call_args(b, x, o), s, A->ctl));

@@ -221,7 +221,7 @@ int put_call(CallArgs *dst, const CallArgs &c, cudaStream_t s, DevCtl *ctl) {
   return GBS_OK;
 }
 
-static PcgArgs make_args(gbs_mat A, bool per_system, bool refined) {
+PcgArgs make_args(gbs_mat A, bool per_system, bool refined) {
   PcgArgs a;
   memset(&a, 0, sizeof(a));
   a.nsys = per_system ? A->nsys : 1;
@@ -253,6 +253,13 @@ static PcgArgs make_args(gbs_mat A, bool per_system, bool refined) {
   a.st = A->st;
   a.ctl = A->ctl;
   a.call = A->call;
+  if (A->kv)
+    for (int k = 0; k < KRYLOV_NVEC; ++k) a.kv[k] = A->kv + (size_t)k * (size_t)A->nrows;
+  if (A->At) {
+    a.tptr = A->At->sell_ptr;
+    a.tcol = A->At->sell_col;
+    a.tval = A->At->sell_val;
+  }
   return a;
 }
 
@@ -268,15 +275,31 @@ static cudaKernelNodeParams kernel_node(void (*k)(PcgArgs), int grid, void **arg
   return p;
 }
 
-// The solve graph of handle A for one (refined, per_system) shape.
-static int build_graph(gbs_mat A, bool refined, bool per_system, cudaGraphExec_t *out) {
+// CG's loop: setup, WHILE { A (table A), B, C (table E) }, final (table A).
+static LoopPlan cg_plan(bool refined, int lanes) {
+  const PhaseKernels K = phase_kernels(refined, lanes);
+  LoopPlan P;
+  memset(&P, 0, sizeof(P));
+  P.setup = K.setup;
+  P.nbody = 3;
+  P.body[0] = K.spmv;
+  P.body[1] = K.update;
+  P.body[2] = K.direction;
+  P.body_e[1] = P.body_e[2] = true;
+  P.npost = 1;
+  P.post[0] = K.final_;
+  return P;
+}
+
+// The solve graph of a loop plan:
+//   memset control words -> memset counters -> setup -> WHILE { body } -> post.
+int build_loop_graph(gbs_mat A, const LoopPlan &P, PcgArgs a, cudaGraphExec_t *out) {
   *out = nullptr;
-  const PhaseKernels K = phase_kernels(refined, A->lanes);
   cudaGraph_t g = nullptr;
   GBS_TRY_CUDA(cudaGraphCreate(&g, 0));
   cudaError_t e = cudaSuccess;
   auto fail = [&](const char *what) {
-    set_error("building the PCG graph (%s): %s", what, cudaGetErrorString(e));
+    set_error("building the solve graph (%s): %s", what, cudaGetErrorString(e));
     cudaGraphDestroy(g);
     return GBS_ERR_CUDA;
   };
@@ -285,13 +308,13 @@ static int build_graph(gbs_mat A, bool refined, bool per_system, cudaGraphExec_t
   // every system the setup already retired frozen and clears the condition
   e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
   if (e != cudaSuccess) return fail("conditional handle");
-  PcgArgs a = make_args(A, per_system, refined);
   a.cond = h;
   a.stepped = 0;
   a.trip = 0;
   void *args[] = {&a};
+  auto grid = [&](bool e_table) { return e_table ? A->te.grid : A->ta.grid; };
 
-  cudaGraphNode_t n_ctl, n_cnt, n_setup, n_loop, n_final;
+  cudaGraphNode_t n_ctl, n_cnt, n_setup, n_loop;
   cudaMemsetParams ms;
   memset(&ms, 0, sizeof(ms));
   ms.dst = A->ctl;
@@ -305,7 +328,7 @@ static int build_graph(gbs_mat A, bool refined, bool per_system, cudaGraphExec_t
   ms.width = (size_t)A->nsys;
   e = cudaGraphAddMemsetNode(&n_cnt, g, &n_ctl, 1, &ms);
   if (e != cudaSuccess) return fail("memset");
-  cudaKernelNodeParams kp = kernel_node(K.setup, A->ta.grid, args);
+  cudaKernelNodeParams kp = kernel_node(P.setup, A->ta.grid, args);
   e = cudaGraphAddKernelNode(&n_setup, g, &n_cnt, 1, &kp);
   if (e != cudaSuccess) return fail("setup node");
 
@@ -316,26 +339,28 @@ static int build_graph(gbs_mat A, bool refined, bool per_system, cudaGraphExec_t
   e = cudaGraphAddNode(&n_loop, g, &n_setup, nullptr, 1, &cp);
   if (e != cudaSuccess) return fail("conditional node");
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  cudaGraphNode_t n_a, n_b, n_c;
-  kp = kernel_node(K.spmv, A->ta.grid, args);
-  e = cudaGraphAddKernelNode(&n_a, body, nullptr, 0, &kp);
-  if (e != cudaSuccess) return fail("phase A node");
-  kp = kernel_node(K.update, A->te.grid, args);
-  e = cudaGraphAddKernelNode(&n_b, body, &n_a, 1, &kp);
-  if (e != cudaSuccess) return fail("phase B node");
-  kp = kernel_node(K.direction, A->te.grid, args);
-  e = cudaGraphAddKernelNode(&n_c, body, &n_b, 1, &kp);
-  if (e != cudaSuccess) return fail("phase C node");
-
-  kp = kernel_node(K.final_, A->ta.grid, args);
-  e = cudaGraphAddKernelNode(&n_final, g, &n_loop, 1, &kp);
-  if (e != cudaSuccess) return fail("final node");
+  cudaGraphNode_t prev = nullptr;
+  for (int k = 0; k < P.nbody; ++k) {
+    cudaGraphNode_t n;
+    kp = kernel_node(P.body[k], grid(P.body_e[k]), args);
+    e = cudaGraphAddKernelNode(&n, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
+    if (e != cudaSuccess) return fail("loop body node");
+    prev = n;
+  }
+  prev = n_loop;
+  for (int k = 0; k < P.npost; ++k) {
+    cudaGraphNode_t n;
+    kp = kernel_node(P.post[k], grid(P.post_e[k]), args);
+    e = cudaGraphAddKernelNode(&n, g, &prev, 1, &kp);
+    if (e != cudaSuccess) return fail("closing node");
+    prev = n;
+  }
 
   e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) {
     *out = nullptr;
-    set_error("instantiating the PCG graph: %s", cudaGetErrorString(e));
+    set_error("instantiating the solve graph: %s", cudaGetErrorString(e));
     return GBS_ERR_CUDA;
   }
   return GBS_OK;
@@ -347,28 +372,28 @@ constexpr int STEP_CHUNK = 16;  // host-stepped loop: trips launched between sto
 // trip's kernels skip their work once the previous trip has stopped the loop
 // (DevCtl::stop), and the host reads the stop flag after every chunk.  The
 // control words must be zero and the call arguments in place; setup runs
-// first, the closing kernel last.
-static int run_stepped(const PhaseKernels &K, PcgArgs a, int grid_a, int grid_e, int64_t cap,
-                       DevCtl *ctl, cudaStream_t s) {
+// first, the closing kernels last.
+int run_loop_stepped(const LoopPlan &P, PcgArgs a, int grid_a, int grid_e, int64_t cap,
+                     DevCtl *ctl, cudaStream_t s) {
   a.stepped = 1;
   a.trip = 0;
-  K.setup<<<(unsigned)grid_a, PHASE_TPB, 0, s>>>(a);
+  auto grid = [&](bool e_table) { return (unsigned)(e_table ? grid_e : grid_a); };
+  P.setup<<<(unsigned)grid_a, PHASE_TPB, 0, s>>>(a);
   GBS_LAUNCHED(1);
   for (int64_t t = 0;;) {
     for (int k = 0; k < STEP_CHUNK; ++k, ++t) {
       a.trip = (int32_t)(t & 1);
-      K.spmv<<<(unsigned)grid_a, PHASE_TPB, 0, s>>>(a);
-      K.update<<<(unsigned)grid_e, PHASE_TPB, 0, s>>>(a);
-      K.direction<<<(unsigned)grid_e, PHASE_TPB, 0, s>>>(a);
-      GBS_LAUNCHED(3);
+      for (int q = 0; q < P.nbody; ++q)
+        P.body[q]<<<grid(P.body_e[q]), PHASE_TPB, 0, s>>>(a);
+      GBS_LAUNCHED(P.nbody);
     }
     int32_t stop = 0;  // written by the last trip launched, for the next one
     GBS_TRY_CUDA(cudaMemcpyAsync(&stop, &ctl->stop[t & 1], sizeof(stop), cudaMemcpyDeviceToHost, s));
     GBS_TRY_CUDA(cudaStreamSynchronize(s));
     if (stop || t > cap) break;
   }
-  K.final_<<<(unsigned)grid_a, PHASE_TPB, 0, s>>>(a);
-  GBS_LAUNCHED(1);
+  for (int q = 0; q < P.npost; ++q) P.post[q]<<<grid(P.post_e[q]), PHASE_TPB, 0, s>>>(a);
+  GBS_LAUNCHED(P.npost);
   return GBS_OK;
 }
 
@@ -379,13 +404,17 @@ static int run_stepped(const PhaseKernels &K, PcgArgs a, int grid_a, int grid_e,
 // and batches with enough systems to fill every SM with CTAs.
 constexpr int64_t CTA_AUTO_NNZ = 32768;
 
-static bool use_cta_solver(gbs_mat A, bool per_system) {
-  if (A->solver == GBS_SOLVER_CTA) return true;
-  if (A->solver == GBS_SOLVER_PHASES || A->lanes != GBS_SPMV_SELL) return false;
+bool cta_size_rule(gbs_mat A, bool per_system) {
   int nsm = 1;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, A->device);
   const int64_t nz = per_system ? A->max_sys_nnz : A->nnz;
   return nz <= CTA_AUTO_NNZ || (per_system && A->nsys >= 2 * nsm);
+}
+
+bool use_cta_solver(gbs_mat A, bool per_system) {
+  if (A->solver == GBS_SOLVER_CTA) return true;
+  if (A->solver == GBS_SOLVER_PHASES || A->lanes != GBS_SPMV_SELL) return false;
+  return cta_size_rule(A, per_system);
 }
 
 int solve(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool per_system,
@@ -418,18 +447,26 @@ int solve(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool per_sys
     GBS_LAUNCHED(1);
     return GBS_OK;
   }
+  return run_loop(A, cg_plan(refined, A->lanes), refined ? GBS_GRAPH_CG32 : GBS_GRAPH_CG,
+                  make_args(A, per_system, refined), b, x, o, per_system, s);
+}
+
+// Runs a loop plan on the phase kernels: host-stepped (o.host_loop) or as the
+// cached graph of its kind.
+int run_loop(gbs_mat A, const LoopPlan &P, int kind, const PcgArgs &a, const double *b,
+             double *x, const ksp_opts &o, bool per_system, cudaStream_t s) {
+  A->loop_body = P.nbody;
   if (o.host_loop) {
     GBS_TRY_CUDA(cudaMemsetAsync(A->ctl, 0, sizeof(DevCtl), s));
     GBS_TRY_CUDA(cudaMemsetAsync(A->sys_cnt, 0, sizeof(unsigned) * A->nsys, s));
     GBS_TRY(put_call(A->call, call_args(b, x, o), s));
-    return run_stepped(phase_kernels(refined, A->lanes), make_args(A, per_system, refined), A->ta.grid,
-                       A->te.grid, max_trips_for(o), A->ctl, s);
+    return run_loop_stepped(P, a, A->ta.grid, A->te.grid, max_trips_for(o), A->ctl, s);
   }
-  cudaGraphExec_t &G = A->graph[refined ? 1 : 0][per_system ? 1 : 0];
-  if (!G) GBS_TRY(build_graph(A, refined, per_system, &G));
+  cudaGraphExec_t &G = A->graph[kind][per_system ? 1 : 0];
+  if (!G) GBS_TRY(build_loop_graph(A, P, a, &G));
   GBS_TRY(put_call(A->call, call_args(b, x, o), s));
   GBS_TRY_CUDA(cudaGraphLaunch(G, s));
-  count_launches(2);  // setup + final; the loop's kernels are counted when read
+  count_launches(1 + P.npost);  // setup + closing; the loop's kernels are counted when read
   A->trips_counted = false;
   return GBS_OK;
 }
@@ -449,7 +486,7 @@ int read_results(gbs_mat A, ksp_result *res, int32_t count, cudaStream_t s) {
   GBS_TRY_CUDA(cudaMemcpyAsync(&ctl, A->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, s));
   GBS_TRY_CUDA(cudaStreamSynchronize(s));
   if (!A->trips_counted) {
-    count_launches(3 * ctl.trips);
+    count_launches(A->loop_body * ctl.trips);
     A->trips_counted = true;
   }
   int first = GBS_OK;
@@ -639,8 +676,8 @@ extern "C" int ksp_solve_cg_noalloc(int64_t n, const int32_t *row_ptr, const int
   a.st = S->st;
   a.ctl = &S->ctl;
   a.call = &S->call;
-  GBS_TRY(run_stepped(phase_kernels(false, NOALLOC_LANES), a, nba, nbe, max_trips_for(oo),
-                      &S->ctl, s));
+  GBS_TRY(run_loop_stepped(cg_plan(false, NOALLOC_LANES), a, nba, nbe, max_trips_for(oo),
+                           &S->ctl, s));
   if (!res) return GBS_OK;
 
   SysState st;

@@ -74,7 +74,31 @@ struct PcgArgs {
   cudaGraphConditionalHandle cond;  // loop condition of the graph (stepped == 0)
   int32_t stepped;                  // 1: loop trips launched by the host
   int32_t trip;                     // stepped: index of this trip
+  double *kv[KRYLOV_NVEC];          // nonsymmetric solvers' work vectors
+  const int32_t *tptr, *tcol;       // sliced-ELL copy of A^T (BiCG), A's slices
+  const double *tval;
 };
+
+// A solve loop on the phase kernels: setup, the WHILE body (run while any
+// system is active), the closing kernels.  Each kernel walks the SpMV block
+// table (A) or, where *_e is set, the update table (E).
+struct LoopPlan {
+  void (*setup)(PcgArgs);
+  int nbody, npost;
+  void (*body[4])(PcgArgs);
+  bool body_e[4];
+  void (*post[2])(PcgArgs);
+  bool post_e[2];
+};
+
+PcgArgs make_args(gbs_mat A, bool per_system, bool refined);
+int build_loop_graph(gbs_mat A, const LoopPlan &P, PcgArgs a, cudaGraphExec_t *out);
+int run_loop_stepped(const LoopPlan &P, PcgArgs a, int grid_a, int grid_e, int64_t cap,
+                     DevCtl *ctl, cudaStream_t s);
+int run_loop(gbs_mat A, const LoopPlan &P, int kind, const PcgArgs &a, const double *b,
+             double *x, const ksp_opts &o, bool per_system, cudaStream_t s);
+bool use_cta_solver(gbs_mat A, bool per_system);
+bool cta_size_rule(gbs_mat A, bool per_system);
 
 __device__ __forceinline__ int sys_of(const PcgArgs &a, const BlockTable &t, int b) {
   return a.ensemble ? 0 : __ldg(t.sys + b);

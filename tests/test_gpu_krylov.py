@@ -25,6 +25,7 @@ pytestmark = pytest.mark.gpu
 
 DEV = "cuda:0"
 METHODS = [B.KSP_BICG, B.KSP_TFQMR]
+SOLVERS = [B.SOLVER_CTA, B.SOLVER_PHASES]
 ORACLE = {B.KSP_BICG: oracle.bicg, B.KSP_TFQMR: oracle.tfqmr}
 
 
@@ -81,16 +82,18 @@ def assemble_batch(bt):
     return A, O
 
 
+@pytest.mark.parametrize("solver", SOLVERS)
 @pytest.mark.parametrize("method", METHODS)
 @pytest.mark.parametrize("m,bx,by,rtol", [(40, 30.0, -10.0, 1e-10), (23, -5.0, 60.0, 1e-8),
                                           (64, 100.0, 100.0, 1e-8)])
-def test_single_system_parity(method, m, bx, by, rtol):
+def test_single_system_parity(method, m, bx, by, rtol, solver):
     p = W.convdiff2d(m, bx, by, seed=100 + m)
     A, O = single(p)
+    A.set_solver(solver)
     x, r = A.solve(t(p.b), rtol=rtol, method=method)
     xo, ro = ORACLE[method](O, p.b, rtol=rtol)
     assert r["status"] == ro["status"] == B.OK, (r, ro)
-    assert r["solver"] == B.SOLVER_CTA
+    assert r["solver"] == solver
     assert iters_close(r["iterations"], ro["iterations"], method), (r, ro)
     tr = true_rel(O, p.b, x.cpu().numpy())
     assert resid_ok(tr, ro, rtol), (tr, ro)
@@ -99,10 +102,12 @@ def test_single_system_parity(method, m, bx, by, rtol):
     A.close()
 
 
+@pytest.mark.parametrize("solver", SOLVERS)
 @pytest.mark.parametrize("method", METHODS)
-def test_batched_parity(method):
+def test_batched_parity(method, solver):
     bt = W.convdiff_batch(24, seed=61, size_range=(50, 3000), peclet=(1.0, 200.0))
     A, O = assemble_batch(bt)
+    A.set_solver(solver)
     rtol = 1e-9
     x, rs = A.solve_batched(t(bt.b), rtol=rtol, method=method)
     xo, ros = oracle.krylov_batched(O, bt.row_off, bt.b, method, rtol=rtol)
@@ -122,8 +127,9 @@ def test_batched_parity(method):
     A.close()
 
 
+@pytest.mark.parametrize("solver", SOLVERS)
 @pytest.mark.parametrize("method", METHODS)
-def test_ragged_and_degenerate_batch(method):
+def test_ragged_and_degenerate_batch(method, solver):
     """Sizes 1, 0, 4, 36 (ragged slices), 121 and 1089 rows; the empty system and
     a zero right-hand side end at once with OK and x = 0."""
     probs = [W.convdiff2d(mm, 20.0, 5.0, seed=200 + mm) for mm in (1, 2, 6, 11, 33)]
@@ -133,6 +139,7 @@ def test_ragged_and_degenerate_batch(method):
     probs[3].b[:] = 0.0                        # the 6 x 6 system gets b = 0
     bt = batch_of(probs)
     A, O = assemble_batch(bt)
+    A.set_solver(solver)
     x, rs = A.solve_batched(t(bt.b), rtol=1e-10, method=method)
     xo, ros = oracle.krylov_batched(O, bt.row_off, bt.b, method, rtol=1e-10)
     xg = x.cpu().numpy()
@@ -165,10 +172,12 @@ def test_bicg_on_spd_matches_pcg():
     A.close()
 
 
+@pytest.mark.parametrize("solver", SOLVERS)
 @pytest.mark.parametrize("method", METHODS)
-def test_iteration_limit_counts_exactly(method):
+def test_iteration_limit_counts_exactly(method, solver):
     p = W.convdiff2d(30, 40.0, 10.0, seed=7)
     A, O = single(p)
+    A.set_solver(solver)
     for maxit in (1, 2, 5, 8):
         x, r = A.solve(t(p.b), rtol=1e-14, maxit=maxit, method=method)
         xo, ro = ORACLE[method](O, p.b, rtol=1e-14, maxit=maxit)
@@ -179,10 +188,12 @@ def test_iteration_limit_counts_exactly(method):
     A.close()
 
 
+@pytest.mark.parametrize("solver", SOLVERS)
 @pytest.mark.parametrize("method", METHODS)
-def test_nonzero_guess(method):
+def test_nonzero_guess(method, solver):
     p = W.convdiff2d(25, -15.0, 25.0, seed=3)
     A, O = single(p)
+    A.set_solver(solver)
     x0 = np.random.default_rng(1).standard_normal(p.nrows)
     xg = t(x0.copy())
     x, r = A.solve(t(p.b), x=xg, rtol=1e-10, nonzero_guess=True, method=method)
@@ -194,13 +205,15 @@ def test_nonzero_guess(method):
     A.close()
 
 
+@pytest.mark.parametrize("solver", SOLVERS)
 @pytest.mark.parametrize("method", METHODS)
-def test_new_values_refresh_the_transpose(method):
+def test_new_values_refresh_the_transpose(method, solver):
     """mat_set_values_coo after a solve: the next solve (BiCG: its A^T copy)
     sees the new values."""
     p = W.convdiff2d(20, 10.0, 0.0, seed=5)
     q = W.convdiff2d(20, -30.0, 50.0, seed=5)     # same pattern, other values
     A, O = single(p)
+    A.set_solver(solver)
     A.solve(t(p.b), rtol=1e-10, method=method)
     A.set_values(t(q.v))
     Oq = oracle.coo_symbolic(q.nrows, q.ncols, q.i, q.j)
@@ -212,22 +225,26 @@ def test_new_values_refresh_the_transpose(method):
     A.close()
 
 
+@pytest.mark.parametrize("solver", SOLVERS)
 @pytest.mark.parametrize("method", METHODS)
-def test_missing_diagonal_is_reported(method):
+def test_missing_diagonal_is_reported(method, solver):
     p = W.convdiff2d(8, 5.0, 5.0, seed=2)
     v = p.v.copy()
     v[(p.i == 3) & (p.j == 3)] = -1.0            # a negative diagonal entry
     A, O = single(W.Problem("neg", p.nrows, p.ncols, p.i, p.j, v, p.b))
+    A.set_solver(solver)
     x, r = A.solve(t(p.b), method=method)
     xo, ro = ORACLE[method](O, p.b)
     assert r["status"] == ro["status"] == B.ERR_NOT_SPD
     A.close()
 
 
+@pytest.mark.parametrize("solver", SOLVERS)
 @pytest.mark.parametrize("method", METHODS)
-def test_time_limit(method):
+def test_time_limit(method, solver):
     p = W.convdiff2d(90, 200.0, 150.0, seed=4)
     A, O = single(p)
+    A.set_solver(solver)
     x, r = A.solve(t(p.b), rtol=1e-15, maxit=100000, timeout_ns=1, method=method)
     assert r["status"] == B.ERR_TIMEOUT and r["iterations"] >= 1
     # the handle stays usable
@@ -247,4 +264,50 @@ def test_option_checks():
         A.solve(b, method=B.KSP_BICG, precision=B.FP32_REFINED)
     with pytest.raises(B.GbsError):
         A.solve(b, method=7)
+    A.close()
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_phases_host_loop_matches_graph(method):
+    """The host-stepped loop runs the same kernels: identical x and counts."""
+    p = W.convdiff2d(70, 50.0, -20.0, seed=8)
+    A, O = single(p)
+    A.set_solver(B.SOLVER_PHASES)
+    x1, r1 = A.solve(t(p.b), rtol=1e-9, method=method)
+    x2, r2 = A.solve(t(p.b), rtol=1e-9, method=method, host_loop=True)
+    assert torch.equal(x1, x2) and r1["iterations"] == r2["iterations"]
+    assert r1["status"] == B.OK
+    A.close()
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_ensemble_is_the_stacked_system(method):
+    """ksp_solve on a batched handle solves the stacked block-diagonal system
+    with one global norm and one set of scalars (the Sec. 7 ensemble): the
+    oracle's solver on the stacked CSR is its reference."""
+    bt = W.convdiff_batch(12, seed=62, size_range=(200, 2000), peclet=(1.0, 50.0))
+    A, O = assemble_batch(bt)
+    A.set_solver(B.SOLVER_PHASES)
+    x, r = A.solve(t(bt.b), rtol=1e-9, method=method)
+    xo, ro = ORACLE[method](O, bt.b, rtol=1e-9)
+    assert r["status"] == ro["status"] == B.OK
+    assert iters_close(r["iterations"], ro["iterations"], method), (r, ro)
+    assert resid_ok(true_rel(O, bt.b, x.cpu().numpy()), ro, 1e-9)
+    A.close()
+
+
+def test_launch_counts_of_the_phase_loops():
+    """Per trip: BiCG 3 kernels, TFQMR 4; plus setup, closing kernels and the
+    call-argument write (TFQMR closes with the pending x update as well)."""
+    p = W.convdiff2d(50, 20.0, 20.0, seed=9)
+    A, O = single(p)
+    A.set_solver(B.SOLVER_PHASES)
+    for method, per_trip, post in ((B.KSP_BICG, 3, 1), (B.KSP_TFQMR, 4, 2)):
+        A.solve(t(p.b), rtol=1e-9, method=method)         # builds the graph
+        n0 = B.launch_count()
+        x, r = A.solve(t(p.b), rtol=1e-9, method=method)
+        n = B.launch_count() - n0
+        trips = r["iterations"] if method == B.KSP_BICG else (r["iterations"] + 1) // 2
+        assert n >= 1 + 1 + post + per_trip * trips, (method, n, r)
+        assert n <= 1 + 1 + post + per_trip * (trips + 2), (method, n, r)
     A.close()
