@@ -431,7 +431,8 @@ def run_suite(args):
         return 0
     if args.workload == "nonsym":
         sweep = {}
-        for nsys in (16, 64, 256, 1024):
+        sizes = [int(v) for v in args.nonsym_sizes.split(",")]
+        for nsys in sizes:
             bt = W.convdiff_batch(nsys, seed=W.SEED_C6)
             A = B.Mat.from_coo_batched(bt.nrows, bt.ncoo, t(bt.i), t(bt.j))
             A.set_values(t(bt.v))
@@ -470,13 +471,13 @@ def run_suite(args):
                 entry[mname] = res
             sweep[str(nsys)] = entry
             A.close()
-        top = sweep["1024"]["tfqmr"]
+        top = sweep[str(sizes[-1])]["tfqmr"]
         line = _base_line(
             args, min(top["batched_cta"]["s"], top["batched_phases"]["s"]),
             {"workload": "convdiff_batch: 2D upwind convection-diffusion systems, rows "
                          "uniform on [1k, 50k], Peclet log-uniform [1, 100], seed 1006; "
-                         "value = batched TFQMR on 1024 systems",
-             "batch_sizes": [16, 64, 256, 1024]},
+                         f"value = batched TFQMR on {sizes[-1]} systems",
+             "batch_sizes": sizes},
             {"sweep": sweep,
              "what": "solves_per_s = systems / solve time; ensemble = the stacked system "
                      "with one global norm on the phase kernels; gbs = algorithmic bytes "
@@ -727,6 +728,8 @@ def main():
     ap.add_argument("--impl", default="gbs", choices=["gbs", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--nonsym-sizes", default="16,64,256,1024",
+                    help="batch sizes of --workload nonsym (comma-separated)")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "vec", "nonsym"],
                     help="c2 = the benchmark (default); c3/c4/c5 = comparison runs")
     ap.add_argument("--host-loop", action="store_true",

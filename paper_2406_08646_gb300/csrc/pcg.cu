@@ -404,17 +404,21 @@ int run_loop_stepped(const LoopPlan &P, PcgArgs a, int grid_a, int grid_e, int64
 // and batches with enough systems to fill every SM with CTAs.
 constexpr int64_t CTA_AUTO_NNZ = 32768;
 
-bool cta_size_rule(gbs_mat A, bool per_system) {
+bool cta_size_rule(gbs_mat A, bool per_system, int systems_per_sm) {
+  const int64_t nz = per_system ? A->max_sys_nnz : A->nnz;
+  return nz <= CTA_AUTO_NNZ || (per_system && A->nsys >= (int64_t)systems_per_sm * sm_count(A));
+}
+
+int sm_count(gbs_mat A) {
   int nsm = 1;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, A->device);
-  const int64_t nz = per_system ? A->max_sys_nnz : A->nnz;
-  return nz <= CTA_AUTO_NNZ || (per_system && A->nsys >= 2 * nsm);
+  return nsm;
 }
 
 bool use_cta_solver(gbs_mat A, bool per_system) {
   if (A->solver == GBS_SOLVER_CTA) return true;
   if (A->solver == GBS_SOLVER_PHASES || A->lanes != GBS_SPMV_SELL) return false;
-  return cta_size_rule(A, per_system);
+  return cta_size_rule(A, per_system, 2);  // two 1024-thread PCG CTAs fit an SM
 }
 
 int solve(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool per_system,

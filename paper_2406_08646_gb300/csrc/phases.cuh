@@ -98,7 +98,10 @@ int run_loop_stepped(const LoopPlan &P, PcgArgs a, int grid_a, int grid_e, int64
 int run_loop(gbs_mat A, const LoopPlan &P, int kind, const PcgArgs &a, const double *b,
              double *x, const ksp_opts &o, bool per_system, cudaStream_t s);
 bool use_cta_solver(gbs_mat A, bool per_system);
-bool cta_size_rule(gbs_mat A, bool per_system);
+// The per-CTA solver's automatic choice: the largest system solved has at
+// most CTA_AUTO_NNZ nonzeros, or a batch gives every SM systems_per_sm CTAs.
+bool cta_size_rule(gbs_mat A, bool per_system, int systems_per_sm);
+int sm_count(gbs_mat A);
 
 __device__ __forceinline__ int sys_of(const PcgArgs &a, const BlockTable &t, int b) {
   return a.ensemble ? 0 : __ldg(t.sys + b);

@@ -311,3 +311,25 @@ def test_launch_counts_of_the_phase_loops():
         assert n >= 1 + 1 + post + per_trip * trips, (method, n, r)
         assert n <= 1 + 1 + post + per_trip * (trips + 2), (method, n, r)
     A.close()
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_large_batch_two_ctas_per_sm(method):
+    """A batch of at least two systems per SM runs two 1024-thread CTAs per
+    SM (the 32-register build of the kernel): every system against the
+    oracle."""
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    bt = W.convdiff_batch(2 * nsm + 9, seed=63, size_range=(16, 600), peclet=(1.0, 80.0))
+    A, O = assemble_batch(bt)
+    x, rs = A.solve_batched(t(bt.b), rtol=1e-9, method=method)
+    xo, ros = oracle.krylov_batched(O, bt.row_off, bt.b, method, rtol=1e-9)
+    resid = bt.b - oracle.spmv(O, x.cpu().numpy())
+    ro = bt.row_off
+    for s in range(bt.nsys):
+        assert rs[s]["solver"] == B.SOLVER_CTA
+        assert rs[s]["status"] == ros[s]["status"] == B.OK, (s, rs[s], ros[s])
+        assert iters_close(rs[s]["iterations"], ros[s]["iterations"], method), (s, rs[s], ros[s])
+        sl = slice(ro[s], ro[s + 1])
+        tr = np.linalg.norm(resid[sl]) / np.linalg.norm(bt.b[sl])
+        assert resid_ok(tr, ros[s], 1e-9), (s, tr, ros[s])
+    A.close()
