@@ -30,6 +30,11 @@
  *   orc_bicg / orc_tfqmr / orc_krylov_batched -- Sec. 7's batched solvers
  *       for nonsymmetric systems (BiCG and TFQMR with the diagonal
  *       preconditioner), one system at a time.
+ *   orc_pipecg         -- a CG whose iteration needs one global reduction,
+ *       for the latency-bound (small-NNZ) regime where Sec. 6.2's
+ *       asynchronous solvers gain most: the preconditioned pipelined CG of
+ *       Ghysels and Vanroose (Parallel Computing 40, 2014), Jacobi
+ *       preconditioner.  In exact arithmetic its iterates are PCG's.
  *   orc_vec_set_values_coo -- Sec. 5's COO interface for vectors
  *       (VecSetPreallocationCOO / VecSetValuesCOO): y_r is the sum of the
  *       contributions v[k] with i[k] = r.
@@ -669,7 +674,95 @@ int orc_tfqmr(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
   return res->status = st;
 }
 
-/* Batched nonsymmetric solves: method 1 = BiCG, 2 = TFQMR, each system alone. */
+/*
+ * Pipelined PCG (Ghysels-Vanroose), M = diag(A).  Alongside x and r it keeps
+ * u = M^-1 r, w = A u, p, s = A p, q = M^-1 s, z = A q by recurrences, so
+ * that one iteration needs one reduction and one product:
+ *   r = b - A x0; u = M^-1 r; w = A u;
+ *   for i = 0, 1, ...:
+ *     gamma = r.u; delta = w.u; rr = r.r   (the one reduction)
+ *     stop if sqrt(rr) <= rtol ||b|| (iterations = i), or i >= maxit (MAXIT)
+ *     m = M^-1 w; n = A m                  (the one product)
+ *     beta = 0 and alpha = gamma / delta at i = 0, else
+ *     beta = gamma / gamma_prev, alpha = gamma / (delta - beta gamma / alpha_prev)
+ *     z = n + beta z; q = m + beta q; s = w + beta s; p = u + beta p
+ *     x += alpha p; r -= alpha s; u -= alpha q; w -= alpha z.
+ * A non-positive gamma or alpha denominator: BREAKDOWN.  rnorm reports the
+ * last recursive ||r||.  aux (7 n doubles, or NULL) receives r, u, w, p, s,
+ * q, z at exit, for checking the recurrences' invariants.
+ */
+int orc_pipecg(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
+               const double *b, double *x, double rtol, int64_t maxit, int nonzero_guess,
+               orc_result *res, double *aux) {
+  memset(res, 0, sizeof(*res));
+  double *wk = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double) * 10);
+  if (!wk) return res->status = ORC_ERR_ALLOC;
+  double *dinv = wk, *r = wk + n, *u = r + n, *w = u + n, *m = w + n, *nv = m + n,
+         *p = nv + n, *s = p + n, *q = s + n, *z = q + n;
+  double bnorm = 0.0;
+  int st = jacobi(n, rp, ci, a, dinv);
+  if (st == ORC_OK) st = start_residual(n, rp, ci, a, b, x, nonzero_guess, r, &bnorm, res);
+  if (st == ORC_OK && bnorm == 0.0) {
+    for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+    res->rnorm0 = res->rnorm = 0.0;
+  } else if (st == ORC_OK) {
+    for (int64_t i = 0; i < n; ++i) u[i] = dinv[i] * r[i];
+    orc_spmv(n, rp, ci, a, u, w);
+    for (int64_t i = 0; i < n; ++i) p[i] = s[i] = q[i] = z[i] = 0.0;
+    double gamma_prev = 0.0, alpha_prev = 0.0;
+    int64_t it = 0;
+    for (;;) {
+      const double gamma = dot(n, r, u);
+      const double delta = dot(n, w, u);
+      const double rn = sqrt(dot(n, r, r));
+      res->rnorm = rn;
+      if (!isfinite(rn) || !isfinite(gamma) || !isfinite(delta)) {
+        st = ORC_ERR_NAN;
+        break;
+      }
+      if (rn <= rtol * bnorm) break;
+      if (it >= maxit) {
+        st = ORC_ERR_MAXIT;
+        break;
+      }
+      for (int64_t i = 0; i < n; ++i) m[i] = dinv[i] * w[i];
+      orc_spmv(n, rp, ci, a, m, nv);
+      double beta = 0.0, den = delta;
+      if (it > 0) {
+        beta = gamma / gamma_prev;
+        den = delta - beta * gamma / alpha_prev;
+      }
+      if (!(gamma > 0.0) || !(den > 0.0)) {
+        st = ORC_ERR_BREAKDOWN;
+        break;
+      }
+      const double alpha = gamma / den;
+      for (int64_t i = 0; i < n; ++i) z[i] = nv[i] + beta * z[i];
+      for (int64_t i = 0; i < n; ++i) q[i] = m[i] + beta * q[i];
+      for (int64_t i = 0; i < n; ++i) s[i] = w[i] + beta * s[i];
+      for (int64_t i = 0; i < n; ++i) p[i] = u[i] + beta * p[i];
+      for (int64_t i = 0; i < n; ++i) x[i] = x[i] + alpha * p[i];
+      for (int64_t i = 0; i < n; ++i) r[i] = r[i] - alpha * s[i];
+      for (int64_t i = 0; i < n; ++i) u[i] = u[i] - alpha * q[i];
+      for (int64_t i = 0; i < n; ++i) w[i] = w[i] - alpha * z[i];
+      gamma_prev = gamma;
+      alpha_prev = alpha;
+      ++it;
+    }
+    res->iterations = (int32_t)it;
+  }
+  if (aux && n > 0) {
+    const double *src[7] = {r, u, w, p, s, q, z};
+    for (int k = 0; k < 7; ++k) memcpy(aux + (size_t)k * (size_t)n, src[k], sizeof(double) * (size_t)n);
+  }
+  if (st == ORC_OK || st == ORC_ERR_MAXIT || st == ORC_ERR_BREAKDOWN || st == ORC_ERR_NAN)
+    res->true_rel_residual = true_rel(n, rp, ci, a, b, x, bnorm, m);
+  free(wk);
+  return res->status = st;
+}
+
+/* Batched solves, each system alone: method 1 = BiCG, 2 = TFQMR, 3 =
+ * pipelined CG. */
 int orc_krylov_batched(int32_t nsys, const int64_t *row_off, const int32_t *rp,
                        const int32_t *ci, const double *a, const double *b, double *x,
                        double rtol, int64_t maxit, int method, orc_result *res) {
@@ -686,9 +779,11 @@ int orc_krylov_batched(int32_t nsys, const int64_t *row_off, const int32_t *rp,
     }
     for (int64_t i = 0; i <= n; ++i) lrp[i] = (int32_t)(rp[r0 + i] - base);
     for (int64_t p = 0; p < nz; ++p) lci[p] = (int32_t)(ci[base + p] - r0);
-    const int st = method == 1
-                       ? orc_bicg(n, lrp, lci, a + base, b + r0, x + r0, rtol, maxit, 0, &res[s])
-                       : orc_tfqmr(n, lrp, lci, a + base, b + r0, x + r0, rtol, maxit, 0, &res[s]);
+    const int st =
+        method == 1   ? orc_bicg(n, lrp, lci, a + base, b + r0, x + r0, rtol, maxit, 0, &res[s])
+        : method == 2 ? orc_tfqmr(n, lrp, lci, a + base, b + r0, x + r0, rtol, maxit, 0, &res[s])
+                      : orc_pipecg(n, lrp, lci, a + base, b + r0, x + r0, rtol, maxit, 0,
+                                   &res[s], NULL);
     if (st != ORC_OK && first == ORC_OK) first = st;
     free(lrp);
     free(lci);
