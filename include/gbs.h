@@ -71,8 +71,8 @@ enum { GBS_FP64 = 0, GBS_FP32_REFINED = 1 };
 enum { GBS_SPMV_AUTO = -1, GBS_SPMV_SELL = 0 };
 /* Solvers (mat_set_solver). */
 enum { GBS_SOLVER_AUTO = 0, GBS_SOLVER_PHASES = 1, GBS_SOLVER_CTA = 2 };
-/* Krylov methods (ksp_opts.method; Sec. 7 batched solvers). */
-enum { GBS_KSP_CG = 0, GBS_KSP_BICG = 1, GBS_KSP_TFQMR = 2 };
+/* Krylov methods (ksp_opts.method; Sec. 7 batched solvers, Sec. 6.2). */
+enum { GBS_KSP_CG = 0, GBS_KSP_BICG = 1, GBS_KSP_TFQMR = 2, GBS_KSP_PIPECG = 3 };
 
 /* Solver options (host struct).  Fill with ksp_opts_default(), then override. */
 typedef struct {
@@ -98,16 +98,17 @@ typedef struct {
                            (synchronising the stream once per chunk), so
                            profilers that cannot follow device-side graph
                            loops see every kernel */
-  int32_t method;       /* GBS_KSP_CG (default), GBS_KSP_BICG or GBS_KSP_TFQMR;
-                           only ksp_solve / ksp_solve_batched accept a method
-                           other than CG */
+  int32_t method;       /* GBS_KSP_CG (default), GBS_KSP_BICG, GBS_KSP_TFQMR
+                           or GBS_KSP_PIPECG; only ksp_solve /
+                           ksp_solve_batched accept a method other than CG */
 } ksp_opts;
 
 /* Per-solve (or per-system) result, host struct. */
 typedef struct {
   int32_t status;           /* GBS_OK or the GBS_ERR_* that ended the solve */
   int32_t iterations;       /* CG and BiCG: products q = A p (refined: total
-                               inner ones); TFQMR: products with A D^-1 */
+                               inner ones); TFQMR: products with A D^-1;
+                               pipelined CG: x updates (= CG's count) */
   int32_t outer_iterations; /* refined: refinement steps; FP64: 0 */
   int32_t solver;           /* GBS_SOLVER_PHASES or GBS_SOLVER_CTA: which ran */
   double rnorm0;            /* ||b - A x0||_2 */
@@ -217,17 +218,30 @@ int ksp_solve_cg_batched(gbs_mat A, const double *b, double *x, const ksp_opts *
  *     M = diag(A) (right preconditioning, so its bound refers to b - A x);
  *     stops when the quasi-residual bound tau sqrt(m + 1) <= rtol ||b||
  *     (m = half steps).  Two products with A per step.
+ *   GBS_KSP_PIPECG: pipelined Jacobi-PCG (Ghysels-Vanroose): PCG's iterates
+ *     in exact arithmetic, with the recurrences u = M^-1 r, w = A u, s = A p,
+ *     q = M^-1 s, z = A q carried along so that an iteration needs ONE
+ *     reduction (r.u, w.u, ||r||^2 together) and one product.  For the
+ *     latency-bound regime where Sec. 6.2's asynchronous solvers gain most:
+ *     it always runs on the phase kernels, one fused kernel per iteration
+ *     (CG takes three, with two reductions), at the price of more vector
+ *     traffic (152 n + 12 nnz bytes per iteration against CG's 112 n + 12
+ *     nnz) and the method's larger drift between the recursive and the true
+ *     residual.  Same stopping test and statuses as CG.
  *
- * BiCG and TFQMR run in FP64 on the per-CTA solver (one 1024-thread CTA per
- * system, every iteration inside one kernel launch, systems largest first),
- * whatever mat_set_solver chose for CG; o->precision must be GBS_FP64 and
- * o->host_loop is ignored.  A zero or negative diagonal entry ends the solve
+ * BiCG, TFQMR and pipelined CG run in FP64 (o->precision must be
+ * GBS_FP64).  BiCG and TFQMR run on the per-CTA solver (one 1024-thread CTA
+ * per system, every iteration inside one kernel launch, systems largest
+ * first) or on the grid-wide phase kernels in a CUDA graph, chosen as for CG
+ * by mat_set_solver (automatic: per-CTA when the largest system has at most
+ * 32768 nonzeros or a batch has at least one system per SM); o->host_loop
+ * applies to the phase kernels.  A zero or negative diagonal entry ends the solve
  * with GBS_ERR_NOT_SPD (the Jacobi preconditioner needs a positive diagonal);
  * rt.v = 0 or rho = 0 (TFQMR), rho = 0 or pt.q = 0 (BiCG) with
  * GBS_ERR_BREAKDOWN.  Arguments, results and synchronisation as in
  * ksp_solve_cg / ksp_solve_cg_batched (a handle made by mat_create_coo has
  * one system).  Workspace: 9 (TFQMR) or 6 (BiCG) FP64 vectors of
- * nrows, allocated on first use and kept with the handle.
+ * nrows (pipelined CG: 9), allocated on first use and kept with the handle.
  */
 int ksp_solve(gbs_mat A, const double *b, double *x, const ksp_opts *o, ksp_result *res,
               void *stream);

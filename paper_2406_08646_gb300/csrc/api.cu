@@ -74,12 +74,13 @@ static int fill_opts(gbs_mat A, const ksp_opts *in, ksp_opts &o, bool per_system
     set_error("ksp opts: host_loop must be 0 or 1");
     return GBS_ERR_ARG;
   }
-  if (o.method != GBS_KSP_CG && o.method != GBS_KSP_BICG && o.method != GBS_KSP_TFQMR) {
-    set_error("ksp opts: method must be GBS_KSP_CG, GBS_KSP_BICG or GBS_KSP_TFQMR");
+  if (o.method < GBS_KSP_CG || o.method > GBS_KSP_PIPECG) {
+    set_error("ksp opts: method must be GBS_KSP_CG, GBS_KSP_BICG, GBS_KSP_TFQMR or "
+              "GBS_KSP_PIPECG");
     return GBS_ERR_ARG;
   }
   if (o.method != GBS_KSP_CG && o.precision != GBS_FP64) {
-    set_error("ksp opts: BiCG and TFQMR run in FP64 only (precision GBS_FP64)");
+    set_error("ksp opts: BiCG, TFQMR and pipelined CG run in FP64 only (precision GBS_FP64)");
     return GBS_ERR_ARG;
   }
   const int64_t n = max_system_rows(A, per_system);

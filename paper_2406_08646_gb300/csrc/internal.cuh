@@ -68,13 +68,14 @@ struct SysState {
   int32_t pad;
 };
 
-// Work vectors of the nonsymmetric solvers (TFQMR: w, y1, y2, rt, v, B y1,
-// B y2, d, t; BiCG uses the first six as r, rt, p, pt, q, qt).
+// Work vectors of the solvers in krylov.cu (TFQMR: w, y1, y2, rt, v, B y1,
+// B y2, d, t; BiCG uses the first six as r, rt, p, pt, q, qt; pipelined CG
+// all nine as r, u, w, p, s, q, z and the two buffers of m).
 constexpr int KRYLOV_NVEC = 9;
 
 // Cached solve graphs of a handle, by loop kind.
 enum { GBS_GRAPH_CG = 0, GBS_GRAPH_CG32 = 1, GBS_GRAPH_BICG = 2, GBS_GRAPH_TFQMR = 3,
-       GBS_GRAPH_KINDS = 4 };
+       GBS_GRAPH_PIPECG = 4, GBS_GRAPH_KINDS = 5 };
 
 // Per-solve control words (device).  Zeroed before every solve.
 struct DevCtl {

@@ -911,7 +911,8 @@ __global__ void NS_ROWS k_ns_final(PcgArgs a) {
 static LoopPlan bicg_plan() {
   LoopPlan P;
   memset(&P, 0, sizeof(P));
-  P.setup = k_bicg_setup;
+  P.npre = 1;
+  P.pre[0] = k_bicg_setup;
   P.nbody = 3;
   P.body[0] = k_bicg_products;
   P.body[1] = k_bicg_update;
@@ -929,7 +930,8 @@ static LoopPlan bicg_plan() {
 static LoopPlan tfqmr_plan() {
   LoopPlan P;
   memset(&P, 0, sizeof(P));
-  P.setup = k_tfq_setup;
+  P.npre = 1;
+  P.pre[0] = k_tfq_setup;
   P.nbody = 4;
   P.body[0] = k_tfq_v;
   P.body[1] = k_tfq_half1;
@@ -943,6 +945,204 @@ static LoopPlan tfqmr_plan() {
   return P;
 }
 
+// ------------------------------------------------------------------ pipelined CG
+//
+// Pipelined Jacobi-PCG (one reduction per iteration; Ghysels-Vanroose, the
+// oracle's recurrences): u = M^-1 r, w = A u, p, s = A p, q = M^-1 s, z = A q
+// updated alongside x and r.  The loop body is ONE kernel on table A: the
+// product n = A m (m = M^-1 w, gathered from the buffer of this iteration's
+// parity), fused per row with all eight updates, the next m = M^-1 w (into
+// the other buffer: other CTAs still gather this iteration's m) and the
+// partial gamma = r.u, delta = w.u, ||r||^2; the last arriver's fin runs the
+// tests and computes the next alpha and beta.  CG's three kernels and two
+// reductions per iteration become one and one.
+
+// The tests at the top of an iteration and the next alpha, beta from
+// (gamma, delta, r.r); returns the status, or -1 to go on.
+__device__ __forceinline__ int pipe_top(const CallArgs &C, SysState &S, double gamma,
+                                        double delta, double rr) {
+  const double rn = sqrt(rr);
+  S.rr = rr;
+  S.rnorm = rn;
+  if (!isfinite(rn) || !isfinite(gamma) || !isfinite(delta)) return GBS_ERR_NAN;
+  if (rn <= C.rtol * sqrt(S.bb)) return GBS_OK;
+  if (S.iterations >= C.maxit) return GBS_ERR_MAXIT;
+  double beta = 0.0, den = delta;
+  if (S.iterations > 0) {
+    beta = gamma / S.rho;  // S.rho: the previous gamma
+    den = delta - beta * gamma / S.alpha;
+  }
+  if (!(gamma > 0.0) || !(den > 0.0)) return GBS_ERR_BREAKDOWN;
+  S.beta = beta;
+  S.alpha = gamma / den;
+  S.rho = gamma;
+  return -1;
+}
+
+// r = b - A x0, u = M^-1 r; r.r, b.b, missing diagonals; fin: start-up
+// tests.  Table A.
+__device__ __forceinline__ void pipe_setup(const PcgArgs &a, double *red) {
+  const CallArgs &C = *a.call;
+  const double *b = C.b;
+  double *x = C.x;
+  double *r = a.kv[0], *u = a.kv[1];
+  auto want = [&](int) -> int { return 1; };
+  auto row = [&](int i, double ax, double(&acc)[3]) {
+    const double bv = b[i], rv = bv - ax, dv = a.dinv[i];
+    r[i] = rv;
+    u[i] = dv * rv;
+    acc[0] = fma(rv, rv, acc[0]);
+    acc[1] = fma(bv, bv, acc[1]);
+    acc[2] += (dv == 0.0) ? 1.0 : 0.0;
+  };
+  auto work = [&](int, int blk, int r0, int r1, double(&acc)[3]) {
+    if (C.nonzero_guess) {
+      auto f = [&](int i, double ax) { row(i, ax, acc); };
+      row_products<double, 0>(a, blk, r0, r1, a.val, a.sval, x, f);
+    } else {
+      for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        x[i] = 0.0;
+        row(i, 0.0, acc);
+      }
+    }
+  };
+  auto fin = [&](int s, double(&tot)[3]) {
+    SysState &S = a.st[s];
+    memset(&S, 0, sizeof(SysState));
+    S.bb = tot[1];
+    S.rr = tot[0];
+    S.rnorm0 = S.rnorm = sqrt(tot[0]);
+    const int st = kry_start_status(tot[2], tot[1]);
+    if (st == GBS_OK) {
+      S.zero_x = 1;
+      S.rnorm0 = S.rnorm = 0.0;
+    }
+    ns_activate(a, S, st);
+  };
+  walk<3>(a, a.ta, 0, red, want, work, fin);
+}
+
+// w = A u with m = M^-1 w (buffer 0), gamma, delta, r.r; p = s = q = z = 0;
+// fin: the first iteration's tests, alpha.  Table A.
+__device__ __forceinline__ void pipe_start(const PcgArgs &a, double *red) {
+  const CallArgs &C = *a.call;
+  const double *r = a.kv[0], *u = a.kv[1];
+  double *w = a.kv[2], *p = a.kv[3], *sv = a.kv[4], *q = a.kv[5], *z = a.kv[6], *m = a.kv[7];
+  auto want = [&](int s) -> int { return sys_active(a, s) ? 1 : 0; };
+  auto work = [&](int, int blk, int r0, int r1, double(&acc)[3]) {
+    double a0 = acc[0], a1 = acc[1], a2 = acc[2];
+    auto f = [&](int i, double y) {
+      const double ri = r[i], ui = u[i];
+      w[i] = y;
+      m[i] = a.dinv[i] * y;
+      p[i] = 0.0;
+      sv[i] = 0.0;
+      q[i] = 0.0;
+      z[i] = 0.0;
+      a0 = fma(ri, ui, a0);
+      a1 = fma(y, ui, a1);
+      a2 = fma(ri, ri, a2);
+    };
+    row_products<double, 0>(a, blk, r0, r1, a.val, a.sval, u, f);
+    acc[0] = a0;
+    acc[1] = a1;
+    acc[2] = a2;
+  };
+  auto fin = [&](int s, double(&tot)[3]) {
+    SysState &S = a.st[s];
+    const int st = pipe_top(C, S, tot[0], tot[1], tot[2]);
+    if (st >= 0) deactivate(a, S, st);
+  };
+  walk<3>(a, a.ta, 0, red, want, work, fin);
+}
+
+// One iteration.  Table A.
+__device__ __forceinline__ void pipe_iterate(const PcgArgs &a, double *red) {
+  const CallArgs &C = *a.call;
+  double *x = C.x;
+  double *r = a.kv[0], *u = a.kv[1], *w = a.kv[2], *p = a.kv[3], *sv = a.kv[4],
+         *q = a.kv[5], *z = a.kv[6];
+  double alpha = 0.0, beta = 0.0;
+  int par = 0;
+  auto want = [&](int s) -> int {
+    if (!sys_active(a, s)) return 0;
+    const SysState *S = a.st + s;
+    alpha = ldcg(&S->alpha);
+    beta = ldcg(&S->beta);
+    par = ldcg(&S->iterations) & 1;
+    return 1;
+  };
+  auto work = [&](int, int blk, int r0, int r1, double(&acc)[3]) {
+    const double *m_in = a.kv[7 + par];
+    double *m_out = a.kv[8 - par];
+    double a0 = acc[0], a1 = acc[1], a2 = acc[2];
+    auto f = [&](int i, double nv) {
+      const double dv = a.dinv[i];
+      const double wi = w[i], ui = u[i];
+      const double zi = nv + beta * z[i];
+      const double qi = dv * wi + beta * q[i];  // m = M^-1 w at this row
+      const double si = wi + beta * sv[i];
+      const double pi = ui + beta * p[i];
+      z[i] = zi;
+      q[i] = qi;
+      sv[i] = si;
+      p[i] = pi;
+      x[i] = x[i] + alpha * pi;
+      const double rn = r[i] - alpha * si;
+      const double un = ui - alpha * qi;
+      const double wn = wi - alpha * zi;
+      r[i] = rn;
+      u[i] = un;
+      w[i] = wn;
+      m_out[i] = dv * wn;
+      a0 = fma(rn, un, a0);
+      a1 = fma(wn, un, a1);
+      a2 = fma(rn, rn, a2);
+    };
+    row_products<double, 0>(a, blk, r0, r1, a.val, a.sval, m_in, f);
+    acc[0] = a0;
+    acc[1] = a1;
+    acc[2] = a2;
+  };
+  auto fin = [&](int s, double(&tot)[3]) {
+    SysState &S = a.st[s];
+    S.iterations += 1;
+    const int st = pipe_top(C, S, tot[0], tot[1], tot[2]);
+    if (st >= 0) deactivate(a, S, st);
+  };
+  walk<3>(a, a.ta, 0, red, want, work, fin);
+}
+
+__global__ void NS_ROWS k_pipe_setup(PcgArgs a) {
+  __shared__ double red[4 * 32];
+  ns_start_clock(a);
+  pipe_setup(a, red);
+}
+__global__ void NS_ROWS k_pipe_start(PcgArgs a) {
+  __shared__ double red[4 * 32];
+  pipe_start(a, red);
+}
+__global__ void __launch_bounds__(PHASE_TPB, 2) k_pipe_iterate(PcgArgs a) {
+  __shared__ double red[4 * 32];
+  const bool live = trip_live(a);
+  loop_control(a, live);  // after the previous iteration's tests
+  if (!live) return;
+  pipe_iterate(a, red);
+}
+
+// setup, w = A u, WHILE { iterate }, final residual.
+static LoopPlan pipecg_plan() {
+  LoopPlan P;
+  memset(&P, 0, sizeof(P));
+  P.npre = 2;
+  P.pre[0] = k_pipe_setup;
+  P.pre[1] = k_pipe_start;
+  P.nbody = 1;
+  P.body[0] = k_pipe_iterate;
+  P.npost = 1;
+  P.post[0] = k_ns_final;
+  return P;
+}
 // ------------------------------------------------------------------ transpose
 
 // Transposed COO indices, local to each system: nonzero p of row r (system s,
@@ -1071,15 +1271,16 @@ static int ensure_krylov(gbs_mat A, bool transpose, cudaStream_t s) {
 
 int solve_krylov(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool per_system,
                  cudaStream_t s) {
-  const bool bicg = o.method == GBS_KSP_BICG;
+  const bool bicg = o.method == GBS_KSP_BICG, pipe = o.method == GBS_KSP_PIPECG;
   GBS_TRY(ensure_solver_workspace(A, false));
   GBS_TRY(ensure_krylov(A, bicg, s));
   A->last_count = per_system ? A->nsys : 1;
   A->last_ensemble = !per_system;
   A->trips_counted = true;
-  // automatic: one 1024-thread CTA per SM already beats the phase kernels
-  const bool on_ctas = A->solver == GBS_SOLVER_CTA ||
-                       (A->solver == GBS_SOLVER_AUTO && cta_size_rule(A, per_system, 1));
+  // automatic: one 1024-thread CTA per SM already beats the phase kernels;
+  // pipelined CG exists for the phase kernels only
+  const bool on_ctas = !pipe && (A->solver == GBS_SOLVER_CTA ||
+                                 (A->solver == GBS_SOLVER_AUTO && cta_size_rule(A, per_system, 1)));
   if (!on_ctas) {
     A->last_solver = GBS_SOLVER_PHASES;
     if (A->ta.nblocks == 0) {  // empty matrix: nothing to iterate
@@ -1089,6 +1290,7 @@ int solve_krylov(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool 
     }
     PcgArgs pa = make_args(A, per_system, false);
     pa.stream_matrix = stream_matrix(A, bicg ? 24 : 12);
+    if (pipe) return run_loop(A, pipecg_plan(), GBS_GRAPH_PIPECG, pa, b, x, o, per_system, s);
     return run_loop(A, bicg ? bicg_plan() : tfqmr_plan(),
                     bicg ? GBS_GRAPH_BICG : GBS_GRAPH_TFQMR, pa, b, x, o, per_system, s);
   }

@@ -280,7 +280,8 @@ static LoopPlan cg_plan(bool refined, int lanes) {
   const PhaseKernels K = phase_kernels(refined, lanes);
   LoopPlan P;
   memset(&P, 0, sizeof(P));
-  P.setup = K.setup;
+  P.npre = 1;
+  P.pre[0] = K.setup;
   P.nbody = 3;
   P.body[0] = K.spmv;
   P.body[1] = K.update;
@@ -314,7 +315,7 @@ int build_loop_graph(gbs_mat A, const LoopPlan &P, PcgArgs a, cudaGraphExec_t *o
   void *args[] = {&a};
   auto grid = [&](bool e_table) { return e_table ? A->te.grid : A->ta.grid; };
 
-  cudaGraphNode_t n_ctl, n_cnt, n_setup, n_loop;
+  cudaGraphNode_t n_ctl, n_cnt, n_loop;
   cudaMemsetParams ms;
   memset(&ms, 0, sizeof(ms));
   ms.dst = A->ctl;
@@ -328,18 +329,24 @@ int build_loop_graph(gbs_mat A, const LoopPlan &P, PcgArgs a, cudaGraphExec_t *o
   ms.width = (size_t)A->nsys;
   e = cudaGraphAddMemsetNode(&n_cnt, g, &n_ctl, 1, &ms);
   if (e != cudaSuccess) return fail("memset");
-  cudaKernelNodeParams kp = kernel_node(P.setup, A->ta.grid, args);
-  e = cudaGraphAddKernelNode(&n_setup, g, &n_cnt, 1, &kp);
-  if (e != cudaSuccess) return fail("setup node");
+  cudaKernelNodeParams kp;
+  cudaGraphNode_t prev = n_cnt;
+  for (int k = 0; k < P.npre; ++k) {
+    cudaGraphNode_t n;
+    kp = kernel_node(P.pre[k], grid(P.pre_e[k]), args);
+    e = cudaGraphAddKernelNode(&n, g, &prev, 1, &kp);
+    if (e != cudaSuccess) return fail("start-up node");
+    prev = n;
+  }
 
   cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};  // other members zeroed
   cp.conditional.handle = h;
   cp.conditional.type = cudaGraphCondTypeWhile;
   cp.conditional.size = 1;
-  e = cudaGraphAddNode(&n_loop, g, &n_setup, nullptr, 1, &cp);
+  e = cudaGraphAddNode(&n_loop, g, &prev, nullptr, 1, &cp);
   if (e != cudaSuccess) return fail("conditional node");
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  cudaGraphNode_t prev = nullptr;
+  prev = nullptr;
   for (int k = 0; k < P.nbody; ++k) {
     cudaGraphNode_t n;
     kp = kernel_node(P.body[k], grid(P.body_e[k]), args);
@@ -378,8 +385,8 @@ int run_loop_stepped(const LoopPlan &P, PcgArgs a, int grid_a, int grid_e, int64
   a.stepped = 1;
   a.trip = 0;
   auto grid = [&](bool e_table) { return (unsigned)(e_table ? grid_e : grid_a); };
-  P.setup<<<(unsigned)grid_a, PHASE_TPB, 0, s>>>(a);
-  GBS_LAUNCHED(1);
+  for (int q = 0; q < P.npre; ++q) P.pre[q]<<<grid(P.pre_e[q]), PHASE_TPB, 0, s>>>(a);
+  GBS_LAUNCHED(P.npre);
   for (int64_t t = 0;;) {
     for (int k = 0; k < STEP_CHUNK; ++k, ++t) {
       a.trip = (int32_t)(t & 1);
@@ -470,7 +477,7 @@ int run_loop(gbs_mat A, const LoopPlan &P, int kind, const PcgArgs &a, const dou
   if (!G) GBS_TRY(build_loop_graph(A, P, a, &G));
   GBS_TRY(put_call(A->call, call_args(b, x, o), s));
   GBS_TRY_CUDA(cudaGraphLaunch(G, s));
-  count_launches(1 + P.npost);  // setup + closing; the loop's kernels are counted when read
+  count_launches(P.npre + P.npost);  // the loop's kernels are counted when read
   A->trips_counted = false;
   return GBS_OK;
 }

@@ -79,12 +79,13 @@ struct PcgArgs {
   const double *tval;
 };
 
-// A solve loop on the phase kernels: setup, the WHILE body (run while any
-// system is active), the closing kernels.  Each kernel walks the SpMV block
-// table (A) or, where *_e is set, the update table (E).
+// A solve loop on the phase kernels: the start-up kernels, the WHILE body
+// (run while any system is active), the closing kernels.  Each kernel walks
+// the SpMV block table (A) or, where *_e is set, the update table (E).
 struct LoopPlan {
-  void (*setup)(PcgArgs);
-  int nbody, npost;
+  int npre, nbody, npost;
+  void (*pre[2])(PcgArgs);
+  bool pre_e[2];
   void (*body[4])(PcgArgs);
   bool body_e[4];
   void (*post[2])(PcgArgs);
