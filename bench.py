@@ -31,6 +31,10 @@ prints its own JSON line; the default is the Q1 benchmark above):
       solve, plus the batched adjoint
   vec vector COO assembly of the Q1 96^3 element load vector (7.08M entries
       into 912,673 nodes): symbolic and numeric stage times, numeric GB/s
+  async  time per solve against NNZ (Sec. 6.2's comparison, 2D 5-point, 3D
+      7-point and 3D 27-point problems, 5e3 to 2.7e7 nonzeros): the three-kernel
+      CG loop, the one-kernel pipelined CG, the per-CTA CG (up to 2M
+      nonzeros) and TFQMR, all device-driven
   nonsym  batched TFQMR and BiCG (Jacobi) on 16, 64, 256 and 1024 independent
       2D convection-diffusion systems (1k-50k rows each, Peclet 1-100): solves
       per second of the batched solve on the per-CTA solver and on the phase
@@ -429,6 +433,54 @@ def run_suite(args):
              "refined_vs_fp64": rows["batched_fp32_refined"]["s"] / rows["batched_fp64"]["s"]})
         print(json.dumps(line), flush=True)
         return 0
+    if args.workload == "async":
+        problems = ([("poisson2d", m, lambda m=m: W.poisson2d(m))
+                     for m in (32, 64, 128, 256, 512, 1024, 2048)]
+                    + [("poisson3d", m, lambda m=m: W.poisson3d(m, seed=W.SEED_C3))
+                       for m in (16, 32, 64, 128)]
+                    + [("q1hex", m, lambda m=m: W.q1_hex(m, seed=W.SEED_C2))
+                       for m in (8, 16, 32, 64)])
+        if args.async_problems:
+            keep = set(args.async_problems.split(","))
+            problems = [q for q in problems if f"{q[0]}_{q[1]}" in keep]
+        rows = []
+        for kind, m, make in problems:
+            p = make()
+            if kind == "poisson2d":  # its own rhs is an eigenvector: use a random one
+                p.b = np.random.default_rng(W.SEED_C7 + m).standard_normal(p.nrows)
+            A = B.Mat.from_coo(p.nrows, p.ncols, t(p.i), t(p.j))
+            A.set_values(t(p.v))
+            b = t(p.b)
+            x = torch.empty_like(b)
+            row = {"problem": f"{kind}_{m}", "n": p.nrows, "nnz": A.nnz}
+            runs = [("cg", B.KSP_CG, B.SOLVER_PHASES), ("pipecg", B.KSP_PIPECG, B.SOLVER_PHASES),
+                    ("tfqmr", B.KSP_TFQMR, B.SOLVER_PHASES)]
+            if A.nnz <= 2_000_000:
+                runs.append(("cg_cta", B.KSP_CG, B.SOLVER_CTA))
+            for name, method, solver in runs:
+                A.set_solver(solver)
+                ts, (_, r) = _ev_time(stream, lambda: A.solve(b, x, rtol=1e-8, method=method,
+                                                              host_loop=args.host_loop),
+                                      reps=max(1, min(reps, 3)), warm=1)
+                row[name] = {"s": ts, "iterations": r["iterations"], "status": r["status"],
+                             "us_per_iteration": ts * 1e6 / max(r["iterations"], 1),
+                             "true_rel_residual": r["true_rel_residual"]}
+            row["pipecg_vs_cg"] = row["cg"]["s"] / row["pipecg"]["s"]
+            rows.append(row)
+            A.close()
+        big = rows[-1]
+        line = _base_line(
+            args, big["pipecg"]["s"],
+            {"workload": "stencil sweep: poisson2d 32^2..2048^2 (random rhs, seed 1007 + m), "
+                         "poisson3d 16^3..128^3 (seed 1003), q1_hex 8^3..64^3 (seed 1002); "
+                         "value = pipelined CG on q1_hex_64",
+             "rtol": 1e-8},
+            {"sweep": rows,
+             "what": "s = CUDA-event time of one solve (inputs resident); pipecg_vs_cg = "
+                     "CG time / pipelined CG time"})
+        print(json.dumps(line), flush=True)
+        return 0
+
     if args.workload == "nonsym":
         sweep = {}
         sizes = [int(v) for v in args.nonsym_sizes.split(",")]
@@ -728,9 +780,11 @@ def main():
     ap.add_argument("--impl", default="gbs", choices=["gbs", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--async-problems", default="",
+                    help="--workload async: only these problems (e.g. poisson2d_32,q1hex_8)")
     ap.add_argument("--nonsym-sizes", default="16,64,256,1024",
                     help="batch sizes of --workload nonsym (comma-separated)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "vec", "nonsym"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "vec", "nonsym", "async"],
                     help="c2 = the benchmark (default); c3/c4/c5 = comparison runs")
     ap.add_argument("--host-loop", action="store_true",
                     help="run the solves' loop from the host (for profiler launch lists)")

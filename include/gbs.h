@@ -89,7 +89,10 @@ typedef struct {
   int64_t timeout_ns;   /* wall-clock limit of the iteration loop, checked
                            on the device once per iteration; systems still
                            iterating then end with GBS_ERR_TIMEOUT (<= 0:
-                           no limit, the default) */
+                           no limit, the default).  The per-CTA solver and
+                           the host-stepped loop stop at that iteration; the
+                           graph-driven loop finishes its body of 8 trips,
+                           so up to 7 more iterations may run */
   int32_t nonzero_guess;/* 1: x holds the initial guess; 0: start from x = 0 */
   int32_t host_loop;    /* 0 (default): one CUDA graph launch per solve, the
                            loop runs on the device.  1: no graph; the host

@@ -23,10 +23,23 @@ namespace gbs {
 constexpr int CTA_TPB = 1024;  // threads of a system's CTA
 
 struct CtaShared {
-  double red[4 * 32];
-  double sc[4];   // scalars broadcast by thread 0
-  int flag[2];    // [0]: keep iterating, [1]: spare
+  double red[2 * 4 * 32];  // two halves of block_allreduce scratch
+  int flag[2];             // [1]: the wall-clock limit was reached
 };
+
+// Block sums for the per-CTA solvers: every thread receives the totals (one
+// barrier each), so every thread runs the scalar recurrences and the tests
+// itself, identically, and control flow stays uniform without broadcasts.
+struct CtaRed {
+  CtaShared &sh;
+  int half;
+};
+
+template <typename T, int NV>
+__device__ __forceinline__ void cta_sum(T (&v)[NV], CtaRed &R) {
+  block_allreduce<T, NV>(v, reinterpret_cast<T *>(R.sh.red), R.half);
+  R.half ^= 1;
+}
 
 // Rows [r0, r1) and slices [s0, s1) of the system this CTA solves.
 struct SysRange {
@@ -60,48 +73,51 @@ __device__ __forceinline__ void cta_rows(const PcgArgs &a, const SysRange &g, co
   else sell_rows<T, false, false>(a.sptr, a.srow0, a.scol, sval, x, g.s0, g.s1, f);
 }
 
-// Block sum of NV values in a fixed tree; every thread gets the totals.
-template <typename T, int NV>
-__device__ __forceinline__ void cta_sum(T (&v)[NV], CtaShared &sh) {
-  block_reduce<T, NV>(v, reinterpret_cast<T *>(sh.red));
-  if (threadIdx.x == 0)
-#pragma unroll
-    for (int k = 0; k < NV; ++k) reinterpret_cast<T *>(sh.sc)[k] = v[k];
+// Wall-clock limit (from the solve's start, DevCtl::t_start): thread 0 reads
+// the clock, one barrier shares the answer (the flag is rewritten only after
+// later barriers).  Callers skip it when no limit is set.
+__device__ __forceinline__ bool cta_timed_out(const DevCtl *ctl, int64_t lim, CtaShared &sh) {
+  if (threadIdx.x == 0) sh.flag[1] = (int64_t)global_ns() - ldcg(&ctl->t_start) > lim;
   __syncthreads();
-#pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = reinterpret_cast<T *>(sh.sc)[k];
-  __syncthreads();
+  return sh.flag[1] != 0;
 }
 
-// Wall-clock limit (from the solve's start, DevCtl::t_start), checked by
-// thread 0 once per iteration.
-__device__ __forceinline__ bool cta_timed_out(const PcgArgs &a) {
-  const int64_t lim = a.call->timeout_ns;
-  return lim > 0 && (int64_t)global_ns() - ldcg(&a.ctl->t_start) > lim;
+// The system's closing state, written by thread 0: status (a system stopped
+// by the time limit stays active and is reported through DevCtl::err),
+// iterations, norms.
+__device__ __forceinline__ void cta_store_state(const PcgArgs &a, SysState &S, int status,
+                                                bool timed_out, int iterations, int outer,
+                                                double bb, double rnorm0, double rnorm,
+                                                bool zero_x) {
+  if (threadIdx.x != 0) return;
+  memset(&S, 0, sizeof(SysState));
+  S.bb = bb;
+  S.rnorm0 = rnorm0;
+  S.rnorm = rnorm;
+  S.iterations = iterations;
+  S.outer = outer;
+  S.zero_x = zero_x ? 1 : 0;
+  S.status = timed_out ? GBS_OK : status;
+  S.active = timed_out ? 1 : 0;
+  if (timed_out) a.ctl->err = GBS_ERR_TIMEOUT;
 }
 
-__device__ __forceinline__ void cta_finish(const PcgArgs &a, SysState &S, int status) {
-  S.status = status;
-  S.active = 0;
-}
-
-// ||b - A x||^2 into S.tt (x = 0 exactly where b = 0).
+// ||b - A x||^2 into S.tt (x set to 0 first where b = 0).
 __device__ __forceinline__ void cta_true_residual(const PcgArgs &a, const SysRange &g,
-                                                  SysState &S, CtaShared &sh) {
+                                                  SysState &S, bool zero_x, CtaRed &R) {
   const CallArgs &C = *a.call;
   const double *b = C.b;
   double *x = C.x;
-  if (ldcg(&S.zero_x)) {
+  if (zero_x)
     for (int r = g.r0 + threadIdx.x; r < g.r1; r += blockDim.x) x[r] = 0.0;
-    __syncthreads();
-  }
+  __syncthreads();  // x complete
   double tt[1] = {0.0};
   auto f = [&](int r, double t) {
     const double d = b[r] - t;
     tt[0] = fma(d, d, tt[0]);
   };
   cta_rows<double>(a, g, a.sval, x, f);
-  cta_sum<double, 1>(tt, sh);
+  cta_sum<double, 1>(tt, R);
   if (threadIdx.x == 0) S.tt = tt[0];
 }
 
@@ -111,6 +127,7 @@ static __device__ void cta_pcg_fp64(const PcgArgs &a, const SysRange &g, CtaShar
   const double *b = C.b;
   double *x = C.x;
   SysState &S = a.st[g.s];
+  CtaRed R{sh, 0};
   // setup: r = b - A x0, z = D^-1 r, p = z
   double v[4] = {0.0, 0.0, 0.0, 0.0};  // r.z, r.r, b.b, missing diagonals
   auto row = [&](int r, double t) {
@@ -130,31 +147,24 @@ static __device__ void cta_pcg_fp64(const PcgArgs &a, const SysRange &g, CtaShar
       row(r, 0.0);
     }
   }
-  cta_sum<double, 4>(v, sh);
+  cta_sum<double, 4>(v, R);
   double rho = v[0];
-  const double bb = v[2];
-  if (threadIdx.x == 0) {
-    memset(&S, 0, sizeof(SysState));
-    S.bb = bb;
-    S.rho = rho;
-    S.rr = v[1];
-    S.rnorm0 = S.rnorm = sqrt(v[1]);
-    int status = -1;
-    if (v[3] > 0.0) status = GBS_ERR_NOT_SPD;
-    else if (!isfinite(bb)) status = GBS_ERR_NAN;
-    else if (bb == 0.0) {
-      status = GBS_OK;
-      S.zero_x = 1;
-      S.rnorm0 = S.rnorm = 0.0;
-    } else if (!isfinite(v[1]) || !isfinite(rho)) status = GBS_ERR_NAN;
-    else if (sqrt(v[1]) <= C.rtol * sqrt(bb)) status = GBS_OK;
-    else if (C.maxit <= 0) status = GBS_ERR_MAXIT;
-    S.status = status >= 0 ? status : GBS_OK;
-    S.active = status >= 0 ? 0 : 1;
-    sh.flag[0] = S.active;
-  }
-  __syncthreads();
-  while (sh.flag[0]) {
+  const double bb = v[2], thr = C.rtol * sqrt(bb);
+  double rn = sqrt(v[1]), rnorm0 = rn;
+  bool zero = false;
+  int status = -1;
+  if (v[3] > 0.0) status = GBS_ERR_NOT_SPD;
+  else if (!isfinite(bb)) status = GBS_ERR_NAN;
+  else if (bb == 0.0) {
+    status = GBS_OK;
+    zero = true;
+    rn = rnorm0 = 0.0;
+  } else if (!isfinite(v[1]) || !isfinite(rho)) status = GBS_ERR_NAN;
+  else if (rn <= thr) status = GBS_OK;
+  else if (C.maxit <= 0) status = GBS_ERR_MAXIT;
+  int it = 0;
+  bool timed = false;
+  while (status < 0) {
     // A: q = A p, p.q
     double pq[1] = {0.0};
     auto fa = [&](int r, double qv) {
@@ -162,18 +172,17 @@ static __device__ void cta_pcg_fp64(const PcgArgs &a, const SysRange &g, CtaShar
       pq[0] = fma(a.p[r], qv, pq[0]);
     };
     cta_rows<double>(a, g, a.sval, a.p, fa);
-    cta_sum<double, 1>(pq, sh);
-    if (threadIdx.x == 0) {
-      S.iterations += 1;
-      if (isnan(pq[0])) cta_finish(a, S, GBS_ERR_NAN);
-      else if (!(pq[0] > 0.0)) cta_finish(a, S, GBS_ERR_BREAKDOWN);
-      else S.alpha = S.rho / pq[0];
-      sh.flag[0] = S.active;
-      sh.sc[3] = S.alpha;
+    cta_sum<double, 1>(pq, R);
+    ++it;
+    if (isnan(pq[0])) {
+      status = GBS_ERR_NAN;
+      break;
     }
-    __syncthreads();
-    if (!sh.flag[0]) break;
-    const double al = sh.sc[3];
+    if (!(pq[0] > 0.0)) {
+      status = GBS_ERR_BREAKDOWN;
+      break;
+    }
+    const double al = rho / pq[0];
     // B: x += alpha p, r -= alpha q, z = D^-1 r (over q), r.z, r.r
     double w[2] = {0.0, 0.0};
     for (int r = g.r0 + threadIdx.x; r < g.r1; r += blockDim.x) {
@@ -185,35 +194,32 @@ static __device__ void cta_pcg_fp64(const PcgArgs &a, const SysRange &g, CtaShar
       w[0] = fma(rv, z, w[0]);
       w[1] = fma(rv, rv, w[1]);
     }
-    cta_sum<double, 2>(w, sh);
-    if (threadIdx.x == 0) {
-      const double rn = sqrt(w[1]);
-      S.rr = w[1];
-      S.rnorm = rn;
-      if (!isfinite(rn) || !isfinite(w[0])) cta_finish(a, S, GBS_ERR_NAN);
-      else if (rn <= C.rtol * sqrt(S.bb)) cta_finish(a, S, GBS_OK);
-      else if (S.iterations >= C.maxit) cta_finish(a, S, GBS_ERR_MAXIT);
-      else {
-        S.beta = w[0] / S.rho;
-        S.rho = w[0];
-      }
-      int go = S.active;
-      if (go && cta_timed_out(a)) {  // the system stays active: reported as TIMEOUT
-        a.ctl->err = GBS_ERR_TIMEOUT;
-        go = 0;
-      }
-      sh.flag[0] = go;
-      sh.sc[3] = S.beta;
+    cta_sum<double, 2>(w, R);
+    rn = sqrt(w[1]);
+    if (!isfinite(rn) || !isfinite(w[0])) {
+      status = GBS_ERR_NAN;
+      break;
     }
-    __syncthreads();
-    if (!sh.flag[0]) break;
-    const double be = sh.sc[3];
-    // C: p = z + beta p
+    if (rn <= thr) {
+      status = GBS_OK;
+      break;
+    }
+    if (it >= C.maxit) {
+      status = GBS_ERR_MAXIT;
+      break;
+    }
+    if (C.timeout_ns > 0 && cta_timed_out(a.ctl, C.timeout_ns, sh)) {
+      timed = true;
+      break;
+    }
+    const double be = w[0] / rho;
+    rho = w[0];
+    // C: p = z + beta p (each thread its own rows: the rows B wrote)
     for (int r = g.r0 + threadIdx.x; r < g.r1; r += blockDim.x) a.p[r] = fma(be, a.p[r], a.q[r]);
-    __syncthreads();
+    __syncthreads();  // p complete before the next product gathers it
   }
-  __syncthreads();
-  cta_true_residual(a, g, S, sh);
+  cta_store_state(a, S, status, timed, it, 0, bb, rnorm0, rn, zero);
+  cta_true_residual(a, g, S, zero, R);
 }
 
 // FP32 inner PCG under FP64 refinement, the oracle's order of steps.
@@ -222,33 +228,28 @@ static __device__ void cta_pcg_refined(const PcgArgs &a, const SysRange &g, CtaS
   const double *b = C.b;
   double *x = C.x;
   SysState &S = a.st[g.s];
-  double v[3] = {0.0, 0.0, 0.0};  // b.b, missing diagonals, (unused)
+  CtaRed R{sh, 0};
+  double v[2] = {0.0, 0.0};  // b.b, missing diagonals
   if (!C.nonzero_guess)
     for (int r = g.r0 + threadIdx.x; r < g.r1; r += blockDim.x) x[r] = 0.0;
   for (int r = g.r0 + threadIdx.x; r < g.r1; r += blockDim.x) {
     v[0] = fma(b[r], b[r], v[0]);
     v[1] += (a.dinv[r] == 0.0) ? 1.0 : 0.0;
   }
-  cta_sum<double, 3>(v, sh);
-  const double bb = v[0];
-  if (threadIdx.x == 0) {
-    memset(&S, 0, sizeof(SysState));
-    S.bb = bb;
-    S.prev_rn = INFINITY;
-    int status = -1;
-    if (v[1] > 0.0) status = GBS_ERR_NOT_SPD;
-    else if (!isfinite(bb)) status = GBS_ERR_NAN;
-    else if (bb == 0.0) {
-      status = GBS_OK;
-      S.zero_x = 1;
-    }
-    S.status = status >= 0 ? status : GBS_OK;
-    S.active = status >= 0 ? 0 : 1;
-    sh.flag[0] = S.active;
+  cta_sum<double, 2>(v, R);  // (also orders the x writes before the first product)
+  const double bb = v[0], bnorm = sqrt(bb);
+  bool zero = false;
+  int status = -1;
+  if (v[1] > 0.0) status = GBS_ERR_NOT_SPD;
+  else if (!isfinite(bb)) status = GBS_ERR_NAN;
+  else if (bb == 0.0) {
+    status = GBS_OK;
+    zero = true;
   }
-  __syncthreads();
-  const double bnorm = sqrt(bb);
-  while (sh.flag[0]) {
+  double rnorm0 = 0.0, rn = 0.0, prev_rn = INFINITY;
+  int outer = 0, stall = 0, iters = 0;
+  bool timed = false;
+  while (status < 0) {
     // outer FP64 residual r = b - A x
     double rr[1] = {0.0};
     auto fo = [&](int r, double t) {
@@ -257,31 +258,33 @@ static __device__ void cta_pcg_refined(const PcgArgs &a, const SysRange &g, CtaS
       rr[0] = fma(rv, rv, rr[0]);
     };
     cta_rows<double>(a, g, a.sval, x, fo);
-    cta_sum<double, 1>(rr, sh);
-    const double rn = sqrt(rr[0]);
-    if (threadIdx.x == 0) {
-      if (S.outer == 0) S.rnorm0 = rn;
-      S.rnorm = rn;
-      int go = 1;
-      if (!isfinite(rn)) cta_finish(a, S, GBS_ERR_NAN);
-      else if (rn <= C.rtol * bnorm) cta_finish(a, S, GBS_OK);
-      else if (S.outer >= C.max_outer) cta_finish(a, S, GBS_ERR_MAXIT);
-      else if (S.outer > 0) {
-        S.stall = (rn > 0.5 * S.prev_rn) ? S.stall + 1 : 0;
-        if (S.stall >= 2) cta_finish(a, S, GBS_ERR_STAGNATION);
-      }
-      if (S.active && cta_timed_out(a)) {
-        a.ctl->err = GBS_ERR_TIMEOUT;
-        go = 0;
-      }
-      if (S.active && go) {
-        S.prev_rn = rn;
-        S.scale = rn;
-      }
-      sh.flag[0] = S.active && go;
+    cta_sum<double, 1>(rr, R);
+    rn = sqrt(rr[0]);
+    if (outer == 0) rnorm0 = rn;
+    if (!isfinite(rn)) {
+      status = GBS_ERR_NAN;
+      break;
     }
-    __syncthreads();
-    if (!sh.flag[0]) break;
+    if (rn <= C.rtol * bnorm) {
+      status = GBS_OK;
+      break;
+    }
+    if (outer >= C.max_outer) {
+      status = GBS_ERR_MAXIT;
+      break;
+    }
+    if (outer > 0) {
+      stall = (rn > 0.5 * prev_rn) ? stall + 1 : 0;
+      if (stall >= 2) {
+        status = GBS_ERR_STAGNATION;
+        break;
+      }
+    }
+    if (C.timeout_ns > 0 && cta_timed_out(a.ctl, C.timeout_ns, sh)) {
+      timed = true;
+      break;
+    }
+    prev_rn = rn;
     // inner FP32 PCG on RN(r / s) from d = 0
     const double s = rn;
     float w[2] = {0.0f, 0.0f};
@@ -295,7 +298,7 @@ static __device__ void cta_pcg_refined(const PcgArgs &a, const SysRange &g, CtaS
       w[0] = fmaf(rv, z, w[0]);
       w[1] = fmaf(rv, rv, w[1]);
     }
-    cta_sum<float, 2>(w, sh);
+    cta_sum<float, 2>(w, R);
     float rho = w[0], rr32 = w[1];
     const double tgt = fmax(C.inner_rtol, 0.5 * C.rtol * bnorm / s);
     const double thr = tgt * (double)sqrtf(rr32);
@@ -307,7 +310,7 @@ static __device__ void cta_pcg_refined(const PcgArgs &a, const SysRange &g, CtaS
         pq[0] = fmaf(a.p32[r], qv, pq[0]);
       };
       cta_rows<float>(a, g, a.sval32, a.p32, fa);
-      cta_sum<float, 1>(pq, sh);
+      cta_sum<float, 1>(pq, R);
       if (!(pq[0] > 0.0f)) break;
       ++it;
       const float al = rho / pq[0];
@@ -321,7 +324,7 @@ static __device__ void cta_pcg_refined(const PcgArgs &a, const SysRange &g, CtaS
         u[0] = fmaf(rv, z, u[0]);
         u[1] = fmaf(rv, rv, u[1]);
       }
-      cta_sum<float, 2>(u, sh);
+      cta_sum<float, 2>(u, R);
       const float be = u[0] / rho;
       rho = u[0];
       rr32 = u[1];
@@ -329,20 +332,18 @@ static __device__ void cta_pcg_refined(const PcgArgs &a, const SysRange &g, CtaS
         a.p32[r] = fmaf(be, a.p32[r], a.q32[r]);
       __syncthreads();
     }
-    if (threadIdx.x == 0) {
-      S.iterations += it;
-      if (it == 0) cta_finish(a, S, GBS_ERR_BREAKDOWN);
-      else S.outer += 1;
-      sh.flag[0] = S.active;
+    iters += it;
+    if (it == 0) {
+      status = GBS_ERR_BREAKDOWN;
+      break;
     }
-    __syncthreads();
-    if (!sh.flag[0]) break;
+    ++outer;
     for (int r = g.r0 + threadIdx.x; r < g.r1; r += blockDim.x)
       x[r] = fma(s, (double)a.d32[r], x[r]);
-    __syncthreads();
+    __syncthreads();  // x complete before the next outer residual gathers it
   }
-  __syncthreads();
-  cta_true_residual(a, g, S, sh);
+  cta_store_state(a, S, status, timed, iters, outer, bb, rnorm0, rn, zero);
+  cta_true_residual(a, g, S, zero, R);
 }
 
 template <bool REFINED>

@@ -94,19 +94,14 @@ __device__ __forceinline__ void kry_rows(const KrylovArgs &a, const KSys &g, con
   else sell_rows<double, false, false>(sptr, a.srow0, scol, sval, x, g.s0, g.s1, f);
 }
 
-// Wall-clock limit, read by thread 0 and shared through one barrier (the flag
-// is rewritten only after the next block reduction's barriers).
+// Wall-clock limit (cta.cuh's check; nothing to do without a limit).
 __device__ __forceinline__ bool kry_timed_out(const KrylovArgs &a, CtaShared &sh) {
-  if (threadIdx.x == 0) {
-    const int64_t lim = a.call->timeout_ns;
-    sh.flag[1] = lim > 0 && (int64_t)global_ns() - ldcg(&a.ctl->t_start) > lim;
-  }
-  __syncthreads();
-  return sh.flag[1] != 0;
+  const int64_t lim = a.call->timeout_ns;
+  return lim > 0 && cta_timed_out(a.ctl, lim, sh);
 }
 
 // Closing state of the system (thread 0), then ||b - A x||^2 into S.tt.
-__device__ void kry_close(const KrylovArgs &a, const KSys &g, CtaShared &sh, int status,
+__device__ void kry_close(const KrylovArgs &a, const KSys &g, CtaRed &R, int status,
                           bool timed_out, int iterations, double bb, double rnorm0,
                           double rnorm) {
   SysState &S = a.st[g.s];
@@ -129,7 +124,7 @@ __device__ void kry_close(const KrylovArgs &a, const KSys &g, CtaShared &sh, int
     tt[0] = fma(d, d, tt[0]);
   };
   kry_rows(a, g, a.sptr, a.scol, a.sval, x, f);
-  cta_sum<double, 1>(tt, sh);
+  cta_sum<double, 1>(tt, R);
   if (threadIdx.x == 0) S.tt = tt[0];
 }
 
@@ -150,6 +145,7 @@ __device__ __forceinline__ void kry_zero_x(const KSys &g, double *x) {
 // ------------------------------------------------------------------ BiCG
 __device__ void kry_bicg(const KrylovArgs &a, const KSys &g, CtaShared &sh) {
   const CallArgs &C = *a.call;
+  CtaRed R{sh, 0};
   const double *b = C.b;
   double *x = C.x;
   const double *dinv = a.dinv;
@@ -173,7 +169,7 @@ __device__ void kry_bicg(const KrylovArgs &a, const KSys &g, CtaShared &sh) {
       start(i, 0.0);
     }
   }
-  cta_sum<double, 4>(v, sh);
+  cta_sum<double, 4>(v, R);
   const double bb = v[1], thr = C.rtol * sqrt(bb);
   double rn = sqrt(v[0]), rho = v[2], rho_prev = 0.0;
   double rnorm0 = rn;
@@ -223,7 +219,7 @@ __device__ void kry_bicg(const KrylovArgs &a, const KSys &g, CtaShared &sh) {
     auto fqt = [&](int i, double y) { qt[i] = y; };
     kry_rows(a, g, a.tptr, a.tcol, a.tval, pt, fqt);
     ++it;
-    cta_sum<double, 1>(sg, sh);
+    cta_sum<double, 1>(sg, R);
     if (isnan(sg[0])) {
       status = GBS_ERR_NAN;
       break;
@@ -244,17 +240,18 @@ __device__ void kry_bicg(const KrylovArgs &a, const KSys &g, CtaShared &sh) {
       u[0] = fma(rv, rv, u[0]);
       u[1] = fma(dinv[i] * rv, rtv, u[1]);
     }
-    cta_sum<double, 2>(u, sh);
+    cta_sum<double, 2>(u, R);
     rn = sqrt(u[0]);
     rho_prev = rho;
     rho = u[1];
   }
-  kry_close(a, g, sh, status, timed, it, bb, rnorm0, rn);
+  kry_close(a, g, R, status, timed, it, bb, rnorm0, rn);
 }
 
 // ------------------------------------------------------------------ TFQMR
 __device__ void kry_tfqmr(const KrylovArgs &a, const KSys &g, CtaShared &sh) {
   const CallArgs &C = *a.call;
+  CtaRed R{sh, 0};
   const double *b = C.b;
   double *x = C.x;
   const double *dinv = a.dinv;
@@ -282,7 +279,7 @@ __device__ void kry_tfqmr(const KrylovArgs &a, const KSys &g, CtaShared &sh) {
       start(i, 0.0);
     }
   }
-  cta_sum<double, 3>(v, sh);
+  cta_sum<double, 3>(v, R);
   const double bb = v[1], thr = C.rtol * sqrt(bb);
   double rnorm0 = sqrt(v[0]), rn = rnorm0;
   int status = kry_start_status(v[2], bb), it = 0;
@@ -305,7 +302,7 @@ __device__ void kry_tfqmr(const KrylovArgs &a, const KSys &g, CtaShared &sh) {
     };
     kry_rows(a, g, a.sptr, a.scol, a.sval, t, f0);
     it = 1;
-    cta_sum<double, 1>(sg, sh);
+    cta_sum<double, 1>(sg, R);
     double sigma = sg[0], rho = v[0];  // rho = rt.r0 = ||r0||^2
     double tau = rnorm0, theta = 0.0, eta = 0.0;
     int m = 0;
@@ -333,7 +330,7 @@ __device__ void kry_tfqmr(const KrylovArgs &a, const KSys &g, CtaShared &sh) {
         d[i] = y1i + coef * d[i];
         s1[0] = fma(wn, wn, s1[0]);
       }
-      cta_sum<double, 1>(s1, sh);
+      cta_sum<double, 1>(s1, R);
       theta = sqrt(s1[0]) / tau;
       double c = 1.0 / sqrt(1.0 + theta * theta);
       tau = tau * theta * c;
@@ -365,7 +362,7 @@ __device__ void kry_tfqmr(const KrylovArgs &a, const KSys &g, CtaShared &sh) {
         s2[1] = fma(rt[i], wn, s2[1]);
       };
       kry_rows(a, g, a.sptr, a.scol, a.sval, t, f1);
-      cta_sum<double, 2>(s2, sh);
+      cta_sum<double, 2>(s2, R);
       theta = sqrt(s2[0]) / tau;
       c = 1.0 / sqrt(1.0 + theta * theta);
       tau = tau * theta * c;
@@ -412,14 +409,14 @@ __device__ void kry_tfqmr(const KrylovArgs &a, const KSys &g, CtaShared &sh) {
       };
       kry_rows(a, g, a.sptr, a.scol, a.sval, t, f2);
       ++it;
-      cta_sum<double, 1>(s3, sh);
+      cta_sum<double, 1>(s3, R);
       sigma = s3[0];
     }
   }
   if (has_pend)
     for (int i = g.r0 + threadIdx.x; i < g.r1; i += blockDim.x)
       x[i] = fma(pend, dinv[i] * d[i], x[i]);
-  kry_close(a, g, sh, status, timed, it, bb, rnorm0, rn);
+  kry_close(a, g, R, status, timed, it, bb, rnorm0, rn);
 }
 
 // MINB CTAs per SM: 1 keeps every value in registers (64 per thread); 2 (32

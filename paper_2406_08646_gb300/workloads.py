@@ -38,6 +38,7 @@ import numpy as np
 
 SEED_C2, SEED_C3, SEED_C4, SEED_C4_SMALL, SEED_C5 = 1002, 1003, 1004, 1014, 1005
 SEED_C6 = 1006  # nonsymmetric (convection-diffusion) batches
+SEED_C7 = 1007  # right-hand sides of the 2D stencil sweep (time per solve vs NNZ)
 
 
 @dataclass
