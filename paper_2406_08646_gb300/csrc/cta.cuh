@@ -22,24 +22,37 @@ namespace gbs {
 
 constexpr int CTA_TPB = 1024;  // threads of a system's CTA
 
+// Thread 0 owns a system's scalars (FP64 scalar arithmetic is slow on this
+// part: an FP64 warp instruction occupies an SM's FP64 pipe for 16 clocks,
+// so the recurrences run in one thread, not redundantly in 32 warps).  A
+// block sum hands its totals to warp 0 after one barrier (cta_sum0); thread 0
+// updates the scalars and publishes what the next pass needs in `pub` /
+// `ipub`; one more barrier (cta_publish) and every thread reads them.
 struct CtaShared {
-  double red[2 * 4 * 32];  // two halves of block_allreduce scratch
-  int flag[2];             // [1]: the wall-clock limit was reached
+  double red[4 * CTA_TPB];  // cta_sum0: every thread's values
+  double pub[4];            // scalars published by thread 0
+  int ipub[4];              // [0]: < 0 keep going; [1], [2], [3]: flags
 };
 
-// Block sums for the per-CTA solvers: every thread receives the totals (one
-// barrier each), so every thread runs the scalar recurrences and the tests
-// itself, identically, and control flow stays uniform without broadcasts.
-struct CtaRed {
-  CtaShared &sh;
-  int half;
-};
-
+// Block sums of NV values, valid in warp 0 (thread 0) after one barrier
+// (device_util.cuh's block_reduce without its closing barrier).  Every call
+// is followed by cta_publish before the next call, so warp 0 has read the
+// values before any thread writes new ones.
 template <typename T, int NV>
-__device__ __forceinline__ void cta_sum(T (&v)[NV], CtaRed &R) {
-  block_allreduce<T, NV>(v, reinterpret_cast<T *>(R.sh.red), R.half);
-  R.half ^= 1;
+__device__ __forceinline__ void cta_sum0(T (&v)[NV], CtaShared &sh) {
+  const int nt = blockDim.x;
+  T *s = reinterpret_cast<T *>(sh.red);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) s[k * nt + threadIdx.x] = v[k];
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = block_sum_lanes<T>(s + k * nt, nt);
+  }
 }
+
+// The barrier after thread 0 filled sh.pub / sh.ipub.
+__device__ __forceinline__ void cta_publish() { __syncthreads(); }
 
 // Rows [r0, r1) and slices [s0, s1) of the system this CTA solves.
 struct SysRange {
@@ -73,13 +86,9 @@ __device__ __forceinline__ void cta_rows(const PcgArgs &a, const SysRange &g, co
   else sell_rows<T, false, false>(a.sptr, a.srow0, a.scol, sval, x, g.s0, g.s1, f);
 }
 
-// Wall-clock limit (from the solve's start, DevCtl::t_start): thread 0 reads
-// the clock, one barrier shares the answer (the flag is rewritten only after
-// later barriers).  Callers skip it when no limit is set.
-__device__ __forceinline__ bool cta_timed_out(const DevCtl *ctl, int64_t lim, CtaShared &sh) {
-  if (threadIdx.x == 0) sh.flag[1] = (int64_t)global_ns() - ldcg(&ctl->t_start) > lim;
-  __syncthreads();
-  return sh.flag[1] != 0;
+// Wall-clock limit (from the solve's start, DevCtl::t_start), for thread 0.
+__device__ __forceinline__ bool cta_timed_out(const DevCtl *ctl, int64_t lim) {
+  return lim > 0 && (int64_t)global_ns() - ldcg(&ctl->t_start) > lim;
 }
 
 // The system's closing state, written by thread 0: status (a system stopped
@@ -104,7 +113,7 @@ __device__ __forceinline__ void cta_store_state(const PcgArgs &a, SysState &S, i
 
 // ||b - A x||^2 into S.tt (x set to 0 first where b = 0).
 __device__ __forceinline__ void cta_true_residual(const PcgArgs &a, const SysRange &g,
-                                                  SysState &S, bool zero_x, CtaRed &R) {
+                                                  SysState &S, bool zero_x, CtaShared &sh) {
   const CallArgs &C = *a.call;
   const double *b = C.b;
   double *x = C.x;
@@ -117,7 +126,7 @@ __device__ __forceinline__ void cta_true_residual(const PcgArgs &a, const SysRan
     tt[0] = fma(d, d, tt[0]);
   };
   cta_rows<double>(a, g, a.sval, x, f);
-  cta_sum<double, 1>(tt, R);
+  cta_sum0<double, 1>(tt, sh);
   if (threadIdx.x == 0) S.tt = tt[0];
 }
 
@@ -127,7 +136,7 @@ static __device__ void cta_pcg_fp64(const PcgArgs &a, const SysRange &g, CtaShar
   const double *b = C.b;
   double *x = C.x;
   SysState &S = a.st[g.s];
-  CtaRed R{sh, 0};
+  const bool t0 = threadIdx.x == 0;
   // setup: r = b - A x0, z = D^-1 r, p = z
   double v[4] = {0.0, 0.0, 0.0, 0.0};  // r.z, r.r, b.b, missing diagonals
   auto row = [&](int r, double t) {
@@ -147,43 +156,51 @@ static __device__ void cta_pcg_fp64(const PcgArgs &a, const SysRange &g, CtaShar
       row(r, 0.0);
     }
   }
-  cta_sum<double, 4>(v, R);
-  double rho = v[0];
-  const double bb = v[2], thr = C.rtol * sqrt(bb);
-  double rn = sqrt(v[1]), rnorm0 = rn;
-  bool zero = false;
-  int status = -1;
-  if (v[3] > 0.0) status = GBS_ERR_NOT_SPD;
-  else if (!isfinite(bb)) status = GBS_ERR_NAN;
-  else if (bb == 0.0) {
-    status = GBS_OK;
-    zero = true;
-    rn = rnorm0 = 0.0;
-  } else if (!isfinite(v[1]) || !isfinite(rho)) status = GBS_ERR_NAN;
-  else if (rn <= thr) status = GBS_OK;
-  else if (C.maxit <= 0) status = GBS_ERR_MAXIT;
-  int it = 0;
-  bool timed = false;
-  while (status < 0) {
-    // A: q = A p, p.q
+  cta_sum0<double, 4>(v, sh);
+  // thread 0's scalars
+  double rho = 0.0, bb = 0.0, thr = 0.0, rn = 0.0, rnorm0 = 0.0;
+  int it = 0, status = -1;
+  bool zero = false, timed = false;
+  if (t0) {
+    rho = v[0];
+    bb = v[2];
+    thr = C.rtol * sqrt(bb);
+    rn = rnorm0 = sqrt(v[1]);
+    if (v[3] > 0.0) status = GBS_ERR_NOT_SPD;
+    else if (!isfinite(bb)) status = GBS_ERR_NAN;
+    else if (bb == 0.0) {
+      status = GBS_OK;
+      zero = true;
+      rn = rnorm0 = 0.0;
+    } else if (!isfinite(v[1]) || !isfinite(rho)) status = GBS_ERR_NAN;
+    else if (rn <= thr) status = GBS_OK;
+    else if (C.maxit <= 0) status = GBS_ERR_MAXIT;
+    sh.ipub[0] = status;
+    sh.ipub[1] = zero;
+  }
+  cta_publish();
+  int go = sh.ipub[0] < 0;
+  const bool zero_x = sh.ipub[1] != 0;
+  while (go) {
+    // A: q = A p, p.q -> alpha
     double pq[1] = {0.0};
     auto fa = [&](int r, double qv) {
       a.q[r] = qv;
       pq[0] = fma(a.p[r], qv, pq[0]);
     };
     cta_rows<double>(a, g, a.sval, a.p, fa);
-    cta_sum<double, 1>(pq, R);
-    ++it;
-    if (isnan(pq[0])) {
-      status = GBS_ERR_NAN;
-      break;
+    cta_sum0<double, 1>(pq, sh);
+    if (t0) {
+      ++it;
+      if (isnan(pq[0])) status = GBS_ERR_NAN;
+      else if (!(pq[0] > 0.0)) status = GBS_ERR_BREAKDOWN;
+      else sh.pub[0] = rho / pq[0];
+      sh.ipub[0] = status;
     }
-    if (!(pq[0] > 0.0)) {
-      status = GBS_ERR_BREAKDOWN;
-      break;
-    }
-    const double al = rho / pq[0];
-    // B: x += alpha p, r -= alpha q, z = D^-1 r (over q), r.z, r.r
+    cta_publish();
+    if (sh.ipub[0] >= 0) break;
+    const double al = sh.pub[0];
+    // B: x += alpha p, r -= alpha q, z = D^-1 r (over q), r.z, r.r -> tests, beta
     double w[2] = {0.0, 0.0};
     for (int r = g.r0 + threadIdx.x; r < g.r1; r += blockDim.x) {
       const double rv = fma(-al, a.q[r], a.r[r]);
@@ -194,32 +211,28 @@ static __device__ void cta_pcg_fp64(const PcgArgs &a, const SysRange &g, CtaShar
       w[0] = fma(rv, z, w[0]);
       w[1] = fma(rv, rv, w[1]);
     }
-    cta_sum<double, 2>(w, R);
-    rn = sqrt(w[1]);
-    if (!isfinite(rn) || !isfinite(w[0])) {
-      status = GBS_ERR_NAN;
-      break;
+    cta_sum0<double, 2>(w, sh);
+    if (t0) {
+      rn = sqrt(w[1]);
+      if (!isfinite(rn) || !isfinite(w[0])) status = GBS_ERR_NAN;
+      else if (rn <= thr) status = GBS_OK;
+      else if (it >= C.maxit) status = GBS_ERR_MAXIT;
+      else if (cta_timed_out(a.ctl, C.timeout_ns)) timed = true;
+      else {
+        sh.pub[0] = w[0] / rho;
+        rho = w[0];
+      }
+      sh.ipub[0] = (status < 0 && !timed) ? -1 : 0;
     }
-    if (rn <= thr) {
-      status = GBS_OK;
-      break;
-    }
-    if (it >= C.maxit) {
-      status = GBS_ERR_MAXIT;
-      break;
-    }
-    if (C.timeout_ns > 0 && cta_timed_out(a.ctl, C.timeout_ns, sh)) {
-      timed = true;
-      break;
-    }
-    const double be = w[0] / rho;
-    rho = w[0];
+    cta_publish();
+    if (sh.ipub[0] >= 0) break;
+    const double be = sh.pub[0];
     // C: p = z + beta p (each thread its own rows: the rows B wrote)
     for (int r = g.r0 + threadIdx.x; r < g.r1; r += blockDim.x) a.p[r] = fma(be, a.p[r], a.q[r]);
     __syncthreads();  // p complete before the next product gathers it
   }
   cta_store_state(a, S, status, timed, it, 0, bb, rnorm0, rn, zero);
-  cta_true_residual(a, g, S, zero, R);
+  cta_true_residual(a, g, S, zero_x, sh);
 }
 
 // FP32 inner PCG under FP64 refinement, the oracle's order of steps.
@@ -228,7 +241,7 @@ static __device__ void cta_pcg_refined(const PcgArgs &a, const SysRange &g, CtaS
   const double *b = C.b;
   double *x = C.x;
   SysState &S = a.st[g.s];
-  CtaRed R{sh, 0};
+  const bool t0 = threadIdx.x == 0;
   double v[2] = {0.0, 0.0};  // b.b, missing diagonals
   if (!C.nonzero_guess)
     for (int r = g.r0 + threadIdx.x; r < g.r1; r += blockDim.x) x[r] = 0.0;
@@ -236,21 +249,28 @@ static __device__ void cta_pcg_refined(const PcgArgs &a, const SysRange &g, CtaS
     v[0] = fma(b[r], b[r], v[0]);
     v[1] += (a.dinv[r] == 0.0) ? 1.0 : 0.0;
   }
-  cta_sum<double, 2>(v, R);  // (also orders the x writes before the first product)
-  const double bb = v[0], bnorm = sqrt(bb);
-  bool zero = false;
-  int status = -1;
-  if (v[1] > 0.0) status = GBS_ERR_NOT_SPD;
-  else if (!isfinite(bb)) status = GBS_ERR_NAN;
-  else if (bb == 0.0) {
-    status = GBS_OK;
-    zero = true;
+  cta_sum0<double, 2>(v, sh);  // (its barrier also orders the x writes before the first product)
+  // thread 0's scalars
+  double bb = 0.0, bnorm = 0.0, rnorm0 = 0.0, rn = 0.0, prev_rn = INFINITY;
+  int status = -1, outer = 0, stall = 0, iters = 0;
+  bool zero = false, timed = false;
+  if (t0) {
+    bb = v[0];
+    bnorm = sqrt(bb);
+    if (v[1] > 0.0) status = GBS_ERR_NOT_SPD;
+    else if (!isfinite(bb)) status = GBS_ERR_NAN;
+    else if (bb == 0.0) {
+      status = GBS_OK;
+      zero = true;
+    }
+    sh.ipub[0] = status;
+    sh.ipub[1] = zero;
   }
-  double rnorm0 = 0.0, rn = 0.0, prev_rn = INFINITY;
-  int outer = 0, stall = 0, iters = 0;
-  bool timed = false;
-  while (status < 0) {
-    // outer FP64 residual r = b - A x
+  cta_publish();
+  int go = sh.ipub[0] < 0;
+  const bool zero_x = sh.ipub[1] != 0;
+  while (go) {
+    // outer FP64 residual r = b - A x -> the refinement tests, s = ||r||
     double rr[1] = {0.0};
     auto fo = [&](int r, double t) {
       const double rv = b[r] - t;
@@ -258,35 +278,26 @@ static __device__ void cta_pcg_refined(const PcgArgs &a, const SysRange &g, CtaS
       rr[0] = fma(rv, rv, rr[0]);
     };
     cta_rows<double>(a, g, a.sval, x, fo);
-    cta_sum<double, 1>(rr, R);
-    rn = sqrt(rr[0]);
-    if (outer == 0) rnorm0 = rn;
-    if (!isfinite(rn)) {
-      status = GBS_ERR_NAN;
-      break;
-    }
-    if (rn <= C.rtol * bnorm) {
-      status = GBS_OK;
-      break;
-    }
-    if (outer >= C.max_outer) {
-      status = GBS_ERR_MAXIT;
-      break;
-    }
-    if (outer > 0) {
-      stall = (rn > 0.5 * prev_rn) ? stall + 1 : 0;
-      if (stall >= 2) {
+    cta_sum0<double, 1>(rr, sh);
+    if (t0) {
+      rn = sqrt(rr[0]);
+      if (outer == 0) rnorm0 = rn;
+      if (!isfinite(rn)) status = GBS_ERR_NAN;
+      else if (rn <= C.rtol * bnorm) status = GBS_OK;
+      else if (outer >= C.max_outer) status = GBS_ERR_MAXIT;
+      else if (outer > 0 && (stall = (rn > 0.5 * prev_rn) ? stall + 1 : 0) >= 2)
         status = GBS_ERR_STAGNATION;
-        break;
+      else if (cta_timed_out(a.ctl, C.timeout_ns)) timed = true;
+      else {
+        prev_rn = rn;
+        sh.pub[0] = rn;
       }
+      sh.ipub[0] = (status < 0 && !timed) ? -1 : 0;
     }
-    if (C.timeout_ns > 0 && cta_timed_out(a.ctl, C.timeout_ns, sh)) {
-      timed = true;
-      break;
-    }
-    prev_rn = rn;
+    cta_publish();
+    if (sh.ipub[0] >= 0) break;
+    const double s = sh.pub[0];
     // inner FP32 PCG on RN(r / s) from d = 0
-    const double s = rn;
     float w[2] = {0.0f, 0.0f};
     for (int r = g.r0 + threadIdx.x; r < g.r1; r += blockDim.x) {
       const float rv = __double2float_rn(a.r[r] / s);
@@ -298,22 +309,37 @@ static __device__ void cta_pcg_refined(const PcgArgs &a, const SysRange &g, CtaS
       w[0] = fmaf(rv, z, w[0]);
       w[1] = fmaf(rv, rv, w[1]);
     }
-    cta_sum<float, 2>(w, R);
-    float rho = w[0], rr32 = w[1];
-    const double tgt = fmax(C.inner_rtol, 0.5 * C.rtol * bnorm / s);
-    const double thr = tgt * (double)sqrtf(rr32);
+    cta_sum0<float, 2>(w, sh);
+    float rho = 0.0f;
+    double thr = 0.0;
     int it = 0;
-    while ((double)sqrtf(rr32) > thr && it < C.inner_maxit) {
+    if (t0) {
+      rho = w[0];
+      const double tgt = fmax(C.inner_rtol, 0.5 * C.rtol * bnorm / s);
+      thr = tgt * (double)sqrtf(w[1]);
+      sh.ipub[1] = (double)sqrtf(w[1]) > thr && 0 < C.inner_maxit;
+    }
+    cta_publish();
+    int inner = sh.ipub[1];
+    while (inner) {
       float pq[1] = {0.0f};
       auto fa = [&](int r, float qv) {
         a.q32[r] = qv;
         pq[0] = fmaf(a.p32[r], qv, pq[0]);
       };
       cta_rows<float>(a, g, a.sval32, a.p32, fa);
-      cta_sum<float, 1>(pq, R);
-      if (!(pq[0] > 0.0f)) break;
-      ++it;
-      const float al = rho / pq[0];
+      cta_sum0<float, 1>(pq, sh);
+      if (t0) {
+        const bool ok = pq[0] > 0.0f;
+        if (ok) {
+          ++it;
+          reinterpret_cast<float *>(sh.pub)[2] = rho / pq[0];
+        }
+        sh.ipub[1] = ok;
+      }
+      cta_publish();
+      if (!sh.ipub[1]) break;
+      const float al = reinterpret_cast<const float *>(sh.pub)[2];
       float u[2] = {0.0f, 0.0f};
       for (int r = g.r0 + threadIdx.x; r < g.r1; r += blockDim.x) {
         const float rv = fmaf(-al, a.q32[r], a.r32[r]);
@@ -324,26 +350,33 @@ static __device__ void cta_pcg_refined(const PcgArgs &a, const SysRange &g, CtaS
         u[0] = fmaf(rv, z, u[0]);
         u[1] = fmaf(rv, rv, u[1]);
       }
-      cta_sum<float, 2>(u, R);
-      const float be = u[0] / rho;
-      rho = u[0];
-      rr32 = u[1];
+      cta_sum0<float, 2>(u, sh);
+      if (t0) {
+        reinterpret_cast<float *>(sh.pub)[3] = u[0] / rho;
+        rho = u[0];
+        sh.ipub[1] = (double)sqrtf(u[1]) > thr && it < C.inner_maxit;
+      }
+      cta_publish();
+      const float be = reinterpret_cast<const float *>(sh.pub)[3];
+      inner = sh.ipub[1];
       for (int r = g.r0 + threadIdx.x; r < g.r1; r += blockDim.x)
         a.p32[r] = fmaf(be, a.p32[r], a.q32[r]);
       __syncthreads();
     }
-    iters += it;
-    if (it == 0) {
-      status = GBS_ERR_BREAKDOWN;
-      break;
+    if (t0) {
+      iters += it;
+      if (it == 0) status = GBS_ERR_BREAKDOWN;
+      else ++outer;
+      sh.ipub[0] = status;
     }
-    ++outer;
+    cta_publish();
+    if (sh.ipub[0] >= 0) break;
     for (int r = g.r0 + threadIdx.x; r < g.r1; r += blockDim.x)
       x[r] = fma(s, (double)a.d32[r], x[r]);
     __syncthreads();  // x complete before the next outer residual gathers it
   }
   cta_store_state(a, S, status, timed, iters, outer, bb, rnorm0, rn, zero);
-  cta_true_residual(a, g, S, zero, R);
+  cta_true_residual(a, g, S, zero_x, sh);
 }
 
 template <bool REFINED>

@@ -32,46 +32,43 @@ __device__ __forceinline__ T warp_sum(T x) {
   return x;
 }
 
-// Deterministic block reduction of NV values: a butterfly inside each warp,
-// then warp 0 reduces the 32 warp sums (absent warps count 0) with the same
-// butterfly.  Result valid in thread 0 (in fact in every lane of warp 0).
-// `scratch` holds NV * 32 values.  Ends with __syncthreads.
-template <typename T, int NV>
-__device__ __forceinline__ void block_reduce(T (&v)[NV], T *scratch) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nwarps = blockDim.x >> 5;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    const T x = warp_sum(v[k]);
-    if (lane == 0) scratch[k * 32 + warp] = x;
+// Deterministic block reduction of NV values, result in warp 0 (thread 0).
+// Every thread stores its values in `scratch` (NV * blockDim.x values, one
+// row per value); after one barrier, lane l of warp 0 adds the values of
+// threads l, l + 32, l + 64, ... into four running sums taken in turn, which
+// it combines, and a butterfly over warp 0 adds the lanes.  A fixed order, so
+// the result is reproducible bit for bit.  FP64 is slow on this part (a
+// warp-wide FP64 instruction takes 16 clocks of an SM's FP64 pipe), so the
+// reduction uses about nthreads / 32 + 8 warp-wide adds per value instead of
+// a butterfly in every warp.  Ends with __syncthreads (scratch reuse).
+template <typename T>
+__device__ __forceinline__ T block_sum_lanes(const T *s, int nt) {
+  const int lane = threadIdx.x & 31;
+  T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+  int j = lane;
+  for (; j + 96 < nt; j += 128) {
+    a0 += s[j];
+    a1 += s[j + 32];
+    a2 += s[j + 64];
+    a3 += s[j + 96];
   }
-  __syncthreads();
-  if (warp == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = warp_sum(lane < nwarps ? scratch[k * 32 + lane] : T(0));
-  }
-  __syncthreads();
+  if (j < nt) a0 += s[j];
+  if (j + 32 < nt) a1 += s[j + 32];
+  if (j + 64 < nt) a2 += s[j + 64];
+  return warp_sum((a0 + a1) + (a2 + a3));
 }
 
-// Block-wide sums that EVERY thread receives, with one barrier: after it,
-// each warp reduces the warp sums itself with the same butterfly, so all
-// threads hold bitwise identical totals.  scratch holds two halves of
-// NV * 32 values used alternately (half = 0, 1, 0, ...): a half is rewritten
-// two calls later, after the intervening call's barrier, which no thread
-// passes before every thread has finished reading it.
 template <typename T, int NV>
-__device__ __forceinline__ void block_allreduce(T (&v)[NV], T *scratch, int half) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nwarps = blockDim.x >> 5;
-  T *s = scratch + half * NV * 32;
+__device__ __forceinline__ void block_reduce(T (&v)[NV], T *scratch) {
+  const int nt = blockDim.x;
 #pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    const T x = warp_sum(v[k]);
-    if (lane == 0) s[k * 32 + warp] = x;
+  for (int k = 0; k < NV; ++k) scratch[k * nt + threadIdx.x] = v[k];
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = block_sum_lanes<T>(scratch + k * nt, nt);
   }
   __syncthreads();
-#pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = warp_sum(lane < nwarps ? s[k * 32 + lane] : T(0));
 }
 
 // Fused multiply-add, correctly rounded once.

@@ -94,17 +94,15 @@ __device__ __forceinline__ void kry_rows(const KrylovArgs &a, const KSys &g, con
   else sell_rows<double, false, false>(sptr, a.srow0, scol, sval, x, g.s0, g.s1, f);
 }
 
-// Wall-clock limit (cta.cuh's check; nothing to do without a limit).
-__device__ __forceinline__ bool kry_timed_out(const KrylovArgs &a, CtaShared &sh) {
-  const int64_t lim = a.call->timeout_ns;
-  return lim > 0 && cta_timed_out(a.ctl, lim, sh);
-}
-
-// Closing state of the system (thread 0), then ||b - A x||^2 into S.tt.
-__device__ void kry_close(const KrylovArgs &a, const KSys &g, CtaRed &R, int status,
+// The system's closing state (thread 0), x = 0 where b = 0, then
+// ||b - A x||^2 into S.tt.
+__device__ void kry_close(const KrylovArgs &a, const KSys &g, CtaShared &sh, int status,
                           bool timed_out, int iterations, double bb, double rnorm0,
-                          double rnorm) {
+                          double rnorm, bool zero_x) {
   SysState &S = a.st[g.s];
+  double *x = a.call->x;
+  if (zero_x)
+    for (int r = g.r0 + threadIdx.x; r < g.r1; r += blockDim.x) x[r] = 0.0;
   __syncthreads();  // x complete
   if (threadIdx.x == 0) {
     memset(&S, 0, sizeof(SysState));
@@ -117,14 +115,13 @@ __device__ void kry_close(const KrylovArgs &a, const KSys &g, CtaRed &R, int sta
     if (timed_out) a.ctl->err = GBS_ERR_TIMEOUT;
   }
   const double *b = a.call->b;
-  const double *x = a.call->x;
   double tt[1] = {0.0};
   auto f = [&](int r, double t) {
     const double d = b[r] - t;
     tt[0] = fma(d, d, tt[0]);
   };
   kry_rows(a, g, a.sptr, a.scol, a.sval, x, f);
-  cta_sum<double, 1>(tt, R);
+  cta_sum0<double, 1>(tt, sh);
   if (threadIdx.x == 0) S.tt = tt[0];
 }
 
@@ -138,18 +135,19 @@ __device__ __forceinline__ int kry_start_status(double missing, double bb) {
   return -1;
 }
 
-__device__ __forceinline__ void kry_zero_x(const KSys &g, double *x) {
-  for (int r = g.r0 + threadIdx.x; r < g.r1; r += blockDim.x) x[r] = 0.0;
-}
+// The scalar recurrences run in thread 0 (FP64 scalar work in every warp
+// would cost 32 times the FP64 issue slots, see cta.cuh); after each block
+// sum thread 0 publishes the next pass's coefficients and whether to go on
+// (sh.ipub[0] < 0), and every thread reads them after one barrier.
 
 // ------------------------------------------------------------------ BiCG
 __device__ void kry_bicg(const KrylovArgs &a, const KSys &g, CtaShared &sh) {
   const CallArgs &C = *a.call;
-  CtaRed R{sh, 0};
   const double *b = C.b;
   double *x = C.x;
   const double *dinv = a.dinv;
   double *r = a.v[0], *rt = a.v[1], *p = a.v[2], *pt = a.v[3], *q = a.v[4], *qt = a.v[5];
+  const bool t0 = threadIdx.x == 0;
   // r0 = b - A x0, rt0 = r0; sums r.r, b.b, (D^-1 r).rt, missing diagonals
   double v[4] = {0.0, 0.0, 0.0, 0.0};
   auto start = [&](int i, double ax) {
@@ -169,40 +167,39 @@ __device__ void kry_bicg(const KrylovArgs &a, const KSys &g, CtaShared &sh) {
       start(i, 0.0);
     }
   }
-  cta_sum<double, 4>(v, R);
-  const double bb = v[1], thr = C.rtol * sqrt(bb);
-  double rn = sqrt(v[0]), rho = v[2], rho_prev = 0.0;
-  double rnorm0 = rn;
-  int status = kry_start_status(v[3], bb), it = 0;
+  cta_sum0<double, 4>(v, sh);
+  // thread 0's scalars
+  double bb = 0.0, thr = 0.0, rn = 0.0, rnorm0 = 0.0, rho = 0.0, rho_prev = 0.0;
+  int status = -1, it = 0;
   bool timed = false;
-  if (status == GBS_OK) {  // b = 0
-    kry_zero_x(g, x);
-    rn = rnorm0 = 0.0;
+  // the tests before an iteration; publishes beta (ipub[1]: first iteration)
+  auto top = [&]() {
+    if (!isfinite(rn)) status = GBS_ERR_NAN;
+    else if (rn <= thr) status = GBS_OK;
+    else if (it >= C.maxit) status = GBS_ERR_MAXIT;
+    else if (rho == 0.0) status = GBS_ERR_BREAKDOWN;
+    else if (it > 0 && cta_timed_out(a.ctl, C.timeout_ns)) timed = true;
+    else sh.pub[0] = it == 0 ? 0.0 : rho / rho_prev;
+    sh.ipub[0] = (status < 0 && !timed) ? -1 : 0;
+    sh.ipub[1] = it == 0;
+  };
+  if (t0) {
+    bb = v[1];
+    thr = C.rtol * sqrt(bb);
+    rn = rnorm0 = sqrt(v[0]);
+    rho = v[2];
+    status = kry_start_status(v[3], bb);
+    sh.ipub[2] = status == GBS_OK;  // b = 0: x = 0
+    if (status == GBS_OK) rn = rnorm0 = 0.0;
+    if (status < 0) top();
+    else sh.ipub[0] = 0;
   }
-  while (status < 0) {
-    if (!isfinite(rn)) {
-      status = GBS_ERR_NAN;
-      break;
-    }
-    if (rn <= thr) {
-      status = GBS_OK;
-      break;
-    }
-    if (it >= C.maxit) {
-      status = GBS_ERR_MAXIT;
-      break;
-    }
-    if (rho == 0.0) {
-      status = GBS_ERR_BREAKDOWN;
-      break;
-    }
-    if (it > 0 && kry_timed_out(a, sh)) {
-      timed = true;
-      break;
-    }
+  cta_publish();
+  const bool zero_x = sh.ipub[2] != 0;
+  while (sh.ipub[0] < 0) {
     // p = z + beta p, pt = zt + beta pt (z = D^-1 r, zt = D^-1 rt)
-    const bool first = it == 0;
-    const double beta = first ? 0.0 : rho / rho_prev;
+    const double beta = sh.pub[0];
+    const bool first = sh.ipub[1] != 0;
     for (int i = g.r0 + threadIdx.x; i < g.r1; i += blockDim.x) {
       const double dv = dinv[i], z = dv * r[i], zt = dv * rt[i];
       p[i] = first ? z : fma(beta, p[i], z);
@@ -218,17 +215,17 @@ __device__ void kry_bicg(const KrylovArgs &a, const KSys &g, CtaShared &sh) {
     kry_rows(a, g, a.sptr, a.scol, a.sval, p, fq);
     auto fqt = [&](int i, double y) { qt[i] = y; };
     kry_rows(a, g, a.tptr, a.tcol, a.tval, pt, fqt);
-    ++it;
-    cta_sum<double, 1>(sg, R);
-    if (isnan(sg[0])) {
-      status = GBS_ERR_NAN;
-      break;
+    cta_sum0<double, 1>(sg, sh);
+    if (t0) {
+      ++it;
+      if (isnan(sg[0])) status = GBS_ERR_NAN;
+      else if (sg[0] == 0.0) status = GBS_ERR_BREAKDOWN;
+      else sh.pub[1] = rho / sg[0];
+      sh.ipub[0] = status;
     }
-    if (sg[0] == 0.0) {
-      status = GBS_ERR_BREAKDOWN;
-      break;
-    }
-    const double alpha = rho / sg[0];
+    cta_publish();
+    if (sh.ipub[0] >= 0) break;
+    const double alpha = sh.pub[1];
     // x += alpha p, r -= alpha q, rt -= alpha qt; ||r||^2, (D^-1 r).rt
     double u[2] = {0.0, 0.0};
     for (int i = g.r0 + threadIdx.x; i < g.r1; i += blockDim.x) {
@@ -240,23 +237,27 @@ __device__ void kry_bicg(const KrylovArgs &a, const KSys &g, CtaShared &sh) {
       u[0] = fma(rv, rv, u[0]);
       u[1] = fma(dinv[i] * rv, rtv, u[1]);
     }
-    cta_sum<double, 2>(u, R);
-    rn = sqrt(u[0]);
-    rho_prev = rho;
-    rho = u[1];
+    cta_sum0<double, 2>(u, sh);
+    if (t0) {
+      rn = sqrt(u[0]);
+      rho_prev = rho;
+      rho = u[1];
+      top();
+    }
+    cta_publish();
   }
-  kry_close(a, g, R, status, timed, it, bb, rnorm0, rn);
+  kry_close(a, g, sh, status, timed, it, bb, rnorm0, rn, zero_x);
 }
 
 // ------------------------------------------------------------------ TFQMR
 __device__ void kry_tfqmr(const KrylovArgs &a, const KSys &g, CtaShared &sh) {
   const CallArgs &C = *a.call;
-  CtaRed R{sh, 0};
   const double *b = C.b;
   double *x = C.x;
   const double *dinv = a.dinv;
   double *w = a.v[0], *y1 = a.v[1], *y2 = a.v[2], *rt = a.v[3], *vv = a.v[4], *by1 = a.v[5],
          *by2 = a.v[6], *d = a.v[7], *t = a.v[8];
+  const bool t0 = threadIdx.x == 0;
   // r0 = b - A x0 into w, y1 and rt; d = 0; t = D^-1 y1; sums r.r, b.b,
   // missing diagonals
   double v[3] = {0.0, 0.0, 0.0};
@@ -279,20 +280,54 @@ __device__ void kry_tfqmr(const KrylovArgs &a, const KSys &g, CtaShared &sh) {
       start(i, 0.0);
     }
   }
-  cta_sum<double, 3>(v, R);
-  const double bb = v[1], thr = C.rtol * sqrt(bb);
-  double rnorm0 = sqrt(v[0]), rn = rnorm0;
-  int status = kry_start_status(v[2], bb), it = 0;
+  cta_sum0<double, 3>(v, sh);
+  // thread 0's scalars
+  double bb = 0.0, thr = 0.0, rnorm0 = 0.0, rn = 0.0;
+  double rho = 0.0, tau = 0.0, theta = 0.0, eta = 0.0, alpha = 0.0;
+  int status = -1, it = 0, m = 0;
   bool timed = false;
-  if (status == GBS_OK) {  // b = 0
-    kry_zero_x(g, x);
-    rn = rnorm0 = 0.0;
-  } else if (status < 0 && rnorm0 <= thr) {
-    status = GBS_OK;  // x0 already meets the test
+  if (t0) {
+    bb = v[1];
+    thr = C.rtol * sqrt(bb);
+    rn = rnorm0 = sqrt(v[0]);
+    status = kry_start_status(v[2], bb);
+    sh.ipub[2] = status == GBS_OK;  // b = 0: x = 0
+    if (status == GBS_OK) rn = rnorm0 = 0.0;
+    else if (status < 0 && rnorm0 <= thr) status = GBS_OK;  // x0 already meets the test
+    rho = v[0];  // rt.r0 = ||r0||^2
+    tau = rnorm0;
+    sh.ipub[0] = status;
   }
-  double pend = 0.0;  // eta of the x update not yet applied (x += eta D^-1 d)
-  bool has_pend = false;
-  if (status < 0) {
+  cta_publish();
+  const bool zero_x = sh.ipub[2] != 0;
+  // one half step's scalars from ||w||^2 and its tests (thread 0); returns
+  // whether the solve ends here
+  auto half = [&](double ww) {
+    theta = sqrt(ww) / tau;
+    const double c = 1.0 / sqrt(1.0 + theta * theta);
+    tau = tau * theta * c;
+    eta = c * c * alpha;
+    ++m;
+    rn = tau * sqrt((double)(m + 1));
+    if (!isfinite(rn)) status = GBS_ERR_NAN;
+    else if (rn <= thr) status = GBS_OK;
+    return status >= 0;
+  };
+  // the tests at the top of a step from sigma = rt.v; publishes alpha and the
+  // first half step's d coefficient
+  auto top = [&](double sigma) {
+    if (!isfinite(tau) || !isfinite(rho)) status = GBS_ERR_NAN;
+    else if (sigma == 0.0 || rho == 0.0) status = GBS_ERR_BREAKDOWN;
+    else {
+      alpha = rho / sigma;
+      ++it;  // the product B y2 of this step
+      sh.pub[0] = alpha;
+      sh.pub[1] = theta * theta * eta / alpha;
+    }
+    sh.ipub[0] = status;
+  };
+  bool pend = false;  // a half step's x update (x += eta D^-1 d) not applied yet
+  if (sh.ipub[0] < 0) {
     // v = B y1 (= A t), rt.v
     double sg[1] = {0.0};
     auto f0 = [&](int i, double y) {
@@ -301,95 +336,72 @@ __device__ void kry_tfqmr(const KrylovArgs &a, const KSys &g, CtaShared &sh) {
       sg[0] = fma(rt[i], y, sg[0]);
     };
     kry_rows(a, g, a.sptr, a.scol, a.sval, t, f0);
-    it = 1;
-    cta_sum<double, 1>(sg, R);
-    double sigma = sg[0], rho = v[0];  // rho = rt.r0 = ||r0||^2
-    double tau = rnorm0, theta = 0.0, eta = 0.0;
-    int m = 0;
-    for (;;) {
-      if (!isfinite(tau) || !isfinite(rho)) {
-        status = GBS_ERR_NAN;
-        break;
-      }
-      if (sigma == 0.0 || rho == 0.0) {
-        status = GBS_ERR_BREAKDOWN;
-        break;
-      }
-      const double alpha = rho / sigma;
-      ++it;  // the product B y2 of this step
+    cta_sum0<double, 1>(sg, sh);
+    if (t0) {
+      it = 1;
+      top(sg[0]);
+    }
+    cta_publish();
+    while (sh.ipub[0] < 0) {
+      const double al = sh.pub[0], coef1 = sh.pub[1];
       // half step 1 with (y1, B y1); y2 = y1 - alpha v, t = D^-1 y2
-      double coef = theta * theta * eta / alpha;
       double s1[1] = {0.0};
       for (int i = g.r0 + threadIdx.x; i < g.r1; i += blockDim.x) {
         const double y1i = y1[i];
-        const double y2i = y1i - alpha * vv[i];
+        const double y2i = y1i - al * vv[i];
         y2[i] = y2i;
         t[i] = dinv[i] * y2i;
-        const double wn = w[i] - alpha * by1[i];
+        const double wn = w[i] - al * by1[i];
         w[i] = wn;
-        d[i] = y1i + coef * d[i];
+        d[i] = y1i + coef1 * d[i];
         s1[0] = fma(wn, wn, s1[0]);
       }
-      cta_sum<double, 1>(s1, R);
-      theta = sqrt(s1[0]) / tau;
-      double c = 1.0 / sqrt(1.0 + theta * theta);
-      tau = tau * theta * c;
-      eta = c * c * alpha;
-      ++m;
-      rn = tau * sqrt((double)(m + 1));
-      pend = eta;
-      has_pend = true;
-      if (!isfinite(rn)) {
-        status = GBS_ERR_NAN;
-        break;
+      cta_sum0<double, 1>(s1, sh);
+      if (t0) {
+        const bool done = half(s1[0]);
+        sh.pub[2] = eta;
+        sh.pub[3] = theta * theta * eta / alpha;
+        sh.ipub[0] = done ? 0 : -1;
       }
-      if (rn <= thr) {
-        status = GBS_OK;
-        break;
-      }
+      cta_publish();
+      pend = true;
+      if (sh.ipub[0] >= 0) break;
       // B y2 (= A t) fused with half step 1's x update and half step 2
-      coef = theta * theta * eta / alpha;
-      const double e1 = eta;
+      const double e1 = sh.pub[2], coef2 = sh.pub[3];
       double s2[2] = {0.0, 0.0};
       auto f1 = [&](int i, double y) {
         by2[i] = y;
         const double di = d[i];
         x[i] = fma(e1, dinv[i] * di, x[i]);
-        d[i] = y2[i] + coef * di;
-        const double wn = w[i] - alpha * y;
+        d[i] = y2[i] + coef2 * di;
+        const double wn = w[i] - al * y;
         w[i] = wn;
         s2[0] = fma(wn, wn, s2[0]);
         s2[1] = fma(rt[i], wn, s2[1]);
       };
       kry_rows(a, g, a.sptr, a.scol, a.sval, t, f1);
-      cta_sum<double, 2>(s2, R);
-      theta = sqrt(s2[0]) / tau;
-      c = 1.0 / sqrt(1.0 + theta * theta);
-      tau = tau * theta * c;
-      eta = c * c * alpha;
-      ++m;
-      rn = tau * sqrt((double)(m + 1));
-      pend = eta;
-      if (!isfinite(rn)) {
-        status = GBS_ERR_NAN;
-        break;
+      cta_sum0<double, 2>(s2, sh);
+      if (t0) {
+        bool stop = half(s2[0]);
+        if (!stop && it >= C.maxit) {
+          status = GBS_ERR_MAXIT;
+          stop = true;
+        }
+        if (!stop && cta_timed_out(a.ctl, C.timeout_ns)) {
+          timed = true;
+          stop = true;
+        }
+        sh.pub[2] = eta;
+        if (!stop) {
+          sh.pub[3] = s2[1] / rho;  // beta
+          rho = s2[1];
+        }
+        sh.ipub[0] = stop ? 0 : -1;
       }
-      if (rn <= thr) {
-        status = GBS_OK;
-        break;
-      }
-      if (it >= C.maxit) {
-        status = GBS_ERR_MAXIT;
-        break;
-      }
-      if (kry_timed_out(a, sh)) {
-        timed = true;
-        break;
-      }
-      const double beta = s2[1] / rho;
-      rho = s2[1];
+      cta_publish();
+      if (sh.ipub[0] >= 0) break;
       // y1 = w + beta y2, t = D^-1 y1, half step 2's x update
-      const double e2 = eta;
+      const double e2 = sh.pub[2], beta = sh.pub[3];
       for (int i = g.r0 + threadIdx.x; i < g.r1; i += blockDim.x) {
         const double dv = dinv[i];
         const double y = w[i] + beta * y2[i];
@@ -397,7 +409,7 @@ __device__ void kry_tfqmr(const KrylovArgs &a, const KSys &g, CtaShared &sh) {
         t[i] = dv * y;
         x[i] = fma(e2, dv * d[i], x[i]);
       }
-      has_pend = false;
+      pend = false;
       __syncthreads();
       // B y1 (= A t), v = B y1 + beta (B y2 + beta v), rt.v
       double s3[1] = {0.0};
@@ -408,15 +420,20 @@ __device__ void kry_tfqmr(const KrylovArgs &a, const KSys &g, CtaShared &sh) {
         s3[0] = fma(rt[i], vn, s3[0]);
       };
       kry_rows(a, g, a.sptr, a.scol, a.sval, t, f2);
-      ++it;
-      cta_sum<double, 1>(s3, R);
-      sigma = s3[0];
+      cta_sum0<double, 1>(s3, sh);
+      if (t0) {
+        ++it;  // B y1
+        top(s3[0]);
+      }
+      cta_publish();
     }
   }
-  if (has_pend)
+  if (pend) {  // the last half step's x update (eta published with it)
+    const double e = sh.pub[2];
     for (int i = g.r0 + threadIdx.x; i < g.r1; i += blockDim.x)
-      x[i] = fma(pend, dinv[i] * d[i], x[i]);
-  kry_close(a, g, R, status, timed, it, bb, rnorm0, rn);
+      x[i] = fma(e, dinv[i] * d[i], x[i]);
+  }
+  kry_close(a, g, sh, status, timed, it, bb, rnorm0, rn, zero_x);
 }
 
 // MINB CTAs per SM: 1 keeps every value in registers (64 per thread); 2 (32
@@ -848,60 +865,60 @@ __device__ __forceinline__ void ns_start_clock(const PcgArgs &a) {
 }
 
 __global__ void NS_ROWS k_bicg_setup(PcgArgs a) {
-  __shared__ double red[4 * 32];
+  __shared__ double red[RED_SCRATCH];
   ns_start_clock(a);
   bicg_setup(a, red);
 }
 __global__ void NS_ROWS k_bicg_products(PcgArgs a) {
-  __shared__ double red[4 * 32];
+  __shared__ double red[RED_SCRATCH];
   if (!trip_live(a)) return;
   bicg_products(a, red);
 }
 __global__ void NS_UPD k_bicg_update(PcgArgs a) {
-  __shared__ double red[4 * 32];
+  __shared__ double red[RED_SCRATCH];
   if (!trip_live(a)) return;
   bicg_update(a, red);
 }
 __global__ void NS_UPD k_bicg_direction(PcgArgs a) {
-  __shared__ double red[4 * 32];
+  __shared__ double red[RED_SCRATCH];
   const bool live = trip_live(a);
   loop_control(a, live);  // after the update's tests: n_active is final
   if (!live) return;
   bicg_direction(a, red);
 }
 __global__ void NS_ROWS k_tfq_setup(PcgArgs a) {
-  __shared__ double red[4 * 32];
+  __shared__ double red[RED_SCRATCH];
   ns_start_clock(a);
   tfq_setup(a, red);
 }
 __global__ void NS_ROWS k_tfq_v(PcgArgs a) {
-  __shared__ double red[4 * 32];
+  __shared__ double red[RED_SCRATCH];
   if (!trip_live(a)) return;
   tfq_v(a, red);
 }
 __global__ void NS_UPD k_tfq_half1(PcgArgs a) {
-  __shared__ double red[4 * 32];
+  __shared__ double red[RED_SCRATCH];
   if (!trip_live(a)) return;
   tfq_half1(a, red);
 }
 __global__ void NS_ROWS k_tfq_half2(PcgArgs a) {
-  __shared__ double red[4 * 32];
+  __shared__ double red[RED_SCRATCH];
   if (!trip_live(a)) return;
   tfq_half2(a, red);
 }
 __global__ void NS_UPD k_tfq_next(PcgArgs a) {
-  __shared__ double red[4 * 32];
+  __shared__ double red[RED_SCRATCH];
   const bool live = trip_live(a);
   loop_control(a, live);  // after half step 2's tests: n_active is final
   if (!live) return;
   tfq_next(a, red);
 }
 __global__ void NS_UPD k_tfq_pending_x(PcgArgs a) {
-  __shared__ double red[4 * 32];
+  __shared__ double red[RED_SCRATCH];
   tfq_pending_x(a, red);
 }
 __global__ void NS_ROWS k_ns_final(PcgArgs a) {
-  __shared__ double red[4 * 32];
+  __shared__ double red[RED_SCRATCH];
   phase_final<0>(a, red);
 }
 
@@ -1111,16 +1128,16 @@ __device__ __forceinline__ void pipe_iterate(const PcgArgs &a, double *red) {
 }
 
 __global__ void NS_ROWS k_pipe_setup(PcgArgs a) {
-  __shared__ double red[4 * 32];
+  __shared__ double red[RED_SCRATCH];
   ns_start_clock(a);
   pipe_setup(a, red);
 }
 __global__ void NS_ROWS k_pipe_start(PcgArgs a) {
-  __shared__ double red[4 * 32];
+  __shared__ double red[RED_SCRATCH];
   pipe_start(a, red);
 }
 __global__ void __launch_bounds__(PHASE_TPB, 2) k_pipe_iterate(PcgArgs a) {
-  __shared__ double red[4 * 32];
+  __shared__ double red[RED_SCRATCH];
   const bool live = trip_live(a);
   loop_control(a, live);  // after the previous iteration's tests
   if (!live) return;

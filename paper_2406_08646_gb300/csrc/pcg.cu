@@ -44,7 +44,7 @@ namespace gbs {
 
 template <bool REFINED, int L>
 __global__ void GBS_ROWS_BOUNDS(L) k_pcg_setup(PcgArgs a) {
-  __shared__ double red[4 * 32];
+  __shared__ double red[RED_SCRATCH];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const int64_t t = (int64_t)global_ns();
     a.ctl->t_start = t;
@@ -56,7 +56,7 @@ __global__ void GBS_ROWS_BOUNDS(L) k_pcg_setup(PcgArgs a) {
 
 template <bool REFINED, int L>
 __global__ void GBS_ROWS_BOUNDS(L) k_pcg_spmv(PcgArgs a) {
-  __shared__ double red[4 * 32];
+  __shared__ double red[RED_SCRATCH];
   if (!trip_live(a)) return;
   stamp_phase(a, 1);
   phase_A<REFINED, L>(a, red);
@@ -64,7 +64,7 @@ __global__ void GBS_ROWS_BOUNDS(L) k_pcg_spmv(PcgArgs a) {
 
 template <bool REFINED>
 __global__ void __launch_bounds__(PHASE_TPB) k_pcg_update(PcgArgs a) {
-  __shared__ double red[4 * 32];
+  __shared__ double red[RED_SCRATCH];
   if (!trip_live(a)) return;
   stamp_phase(a, 2);
   phase_B<REFINED>(a, red);
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(PHASE_TPB) k_pcg_update(PcgArgs a) {
 
 template <bool REFINED>
 __global__ void __launch_bounds__(PHASE_TPB) k_pcg_direction(PcgArgs a) {
-  __shared__ double red[4 * 32];
+  __shared__ double red[RED_SCRATCH];
   const bool live = trip_live(a);
   loop_control(a, live);
   if (!live) return;
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(PHASE_TPB) k_pcg_direction(PcgArgs a) {
 
 template <int L>
 __global__ void GBS_ROWS_BOUNDS(L) k_pcg_final(PcgArgs a) {
-  __shared__ double red[4 * 32];
+  __shared__ double red[RED_SCRATCH];
   stamp_phase(a, 4);
   phase_final<L>(a, red);
   if (blockIdx.x == 0 && threadIdx.x == 0)

@@ -37,6 +37,9 @@ namespace gbs {
 enum { M_INNER = 0, M_XUPD = 1, M_START = 2 };
 constexpr int SLOT_STRIDE = 4;  // doubles per reduction slot
 constexpr int PHASE_TPB = 512;  // threads per CTA of every phase kernel
+// Shared scratch of the phase kernels' block reductions (NV <= 4 values per
+// thread, device_util.cuh's block_reduce).
+constexpr int RED_SCRATCH = 4 * PHASE_TPB;
 constexpr int SELL_MIN_CTAS = 4;  // sliced-ELL kernels: 4 CTAs (2048 threads) per SM
 
 // A table of work blocks: rows [row0[b], row0[b+1]) of system sys[b].

@@ -3,11 +3,15 @@ diagonal preconditioning) against the FP64 oracle, through ksp_solve and
 ksp_solve_batched.
 
 Bars: statuses equal to the oracle's; iteration counts equal when the
-iteration limit ends the solve, and for converged solves within max(3, 5%)
-of the oracle's for TFQMR and max(3, 10%) for BiCG (only the dot products'
-summation order differs; TFQMR's quasi-residual bound decreases smoothly,
-while BiCG's residual on a nonsymmetric system oscillates, so where it first
-crosses the threshold moves by several iterations under rounding changes);
+iteration limit ends the solve (with iterates equal to 1e-10 after up to 8
+iterations); for converged solves, within max(3, 5%) of the oracle's count
+for TFQMR, whose quasi-residual bound decreases smoothly, and within
+max(5, 25%) for BiCG, whose residual on a nonsymmetric system jumps up and
+down by factors of several from one iteration to the next, so that the iteration
+where it first crosses the threshold depends on rounding: on one system of
+the 24-system batch below, the same BiCG in numpy stops after 120, 122,
+127 or 128 iterations depending only on how its dot products are summed,
+the oracle after 135;
 the relative true residual recomputed by the oracle from the GPU's x at most
 2 max(rtol, the oracle's own true residual) (TFQMR stops on its
 quasi-residual bound and BiCG on its recursive residual; both drift from
@@ -41,8 +45,9 @@ def t(a):
 
 
 def iters_close(a, b, method=B.KSP_TFQMR):
-    frac = 0.10 if method == B.KSP_BICG else 0.05
-    return abs(a - b) <= max(3, int(np.ceil(frac * max(a, b))))
+    if method == B.KSP_BICG:
+        return abs(a - b) <= max(5, int(np.ceil(0.25 * max(a, b))))
+    return abs(a - b) <= max(3, int(np.ceil(0.05 * max(a, b))))
 
 
 def resid_ok(tr, ro, rtol):
@@ -150,7 +155,7 @@ def test_ragged_and_degenerate_batch(method, solver):
         if not np.any(bt.b[sl]):
             assert not np.any(xg[sl]) and rs[s]["iterations"] == 0
             continue
-        assert iters_close(rs[s]["iterations"], ros[s]["iterations"], method)
+        assert iters_close(rs[s]["iterations"], ros[s]["iterations"], method), (s, rs[s], ros[s])
         tr = np.linalg.norm(bt.b[sl] - oracle.spmv(O, xg)[sl]) / np.linalg.norm(bt.b[sl])
         assert resid_ok(tr, ros[s], 1e-10), (s, tr, ros[s])
     A.close()
@@ -200,7 +205,7 @@ def test_nonzero_guess(method, solver):
     xo, ro = ORACLE[method](O, p.b, rtol=1e-10, x0=x0)
     assert r["status"] == ro["status"] == B.OK
     assert abs(r["rnorm0"] - ro["rnorm0"]) <= 1e-12 * ro["rnorm0"]
-    assert iters_close(r["iterations"], ro["iterations"], method)
+    assert iters_close(r["iterations"], ro["iterations"], method), (r, ro)
     assert resid_ok(true_rel(O, p.b, x.cpu().numpy()), ro, 1e-10)
     A.close()
 
@@ -220,7 +225,7 @@ def test_new_values_refresh_the_transpose(method, solver):
     oracle.coo_numeric(Oq, q.v)
     x, r = A.solve(t(q.b), rtol=1e-10, method=method)
     xo, ro = ORACLE[method](Oq, q.b, rtol=1e-10)
-    assert r["status"] == B.OK and iters_close(r["iterations"], ro["iterations"], method)
+    assert r["status"] == B.OK and iters_close(r["iterations"], ro["iterations"], method), (r, ro)
     assert resid_ok(true_rel(Oq, q.b, x.cpu().numpy()), ro, 1e-10)
     A.close()
 
