@@ -577,9 +577,8 @@ __device__ __forceinline__ void bicg_update(const PcgArgs &a, double *red) {
   const double *p = a.kv[2], *q = a.kv[4], *qt = a.kv[5];
   NsView v{};
   auto want = [&](int s) -> int {
-    if (!sys_active(a, s)) return 0;
-    v = ns_view(a, s);
-    return 1;
+    v = ns_view(a, s);  // issued with the active flag: one round trip
+    return sys_active(a, s) ? 1 : 0;
   };
   auto work = [&](int, int, int r0, int r1, double(&acc)[2]) {
     const double al = v.alpha;
@@ -612,9 +611,8 @@ __device__ __forceinline__ void bicg_direction(const PcgArgs &a, double *red) {
   double *p = a.kv[2], *pt = a.kv[3];
   NsView v{};
   auto want = [&](int s) -> int {
-    if (!sys_active(a, s)) return 0;
-    v = ns_view(a, s);
-    return 1;
+    v = ns_view(a, s);  // issued with the active flag: one round trip
+    return sys_active(a, s) ? 1 : 0;
   };
   auto work = [&](int, int, int r0, int r1, double(&)[1]) {
     const double be = v.beta;
@@ -697,9 +695,8 @@ __device__ __forceinline__ void tfq_v(const PcgArgs &a, double *red) {
   double *vv = a.kv[4], *by1 = a.kv[5];
   NsView v{};
   auto want = [&](int s) -> int {
-    if (!sys_active(a, s)) return 0;
-    v = ns_view(a, s);
-    return 1;
+    v = ns_view(a, s);  // issued with the active flag: one round trip
+    return sys_active(a, s) ? 1 : 0;
   };
   auto work = [&](int, int blk, int r0, int r1, double(&acc)[1]) {
     const double be = v.beta;
@@ -737,9 +734,8 @@ __device__ __forceinline__ void tfq_half1(const PcgArgs &a, double *red) {
   double *w = a.kv[0], *y2 = a.kv[2], *d = a.kv[7], *t = a.kv[8];
   NsView v{};
   auto want = [&](int s) -> int {
-    if (!sys_active(a, s)) return 0;
-    v = ns_view(a, s);
-    return 1;
+    v = ns_view(a, s);  // issued with the active flag: one round trip
+    return sys_active(a, s) ? 1 : 0;
   };
   auto work = [&](int, int, int r0, int r1, double(&acc)[1]) {
     const double al = v.alpha, cf = v.coef;
@@ -777,9 +773,8 @@ __device__ __forceinline__ void tfq_half2(const PcgArgs &a, double *red) {
   double *w = a.kv[0], *by2 = a.kv[6], *d = a.kv[7];
   NsView v{};
   auto want = [&](int s) -> int {
-    if (!sys_active(a, s)) return 0;
-    v = ns_view(a, s);
-    return 1;
+    v = ns_view(a, s);  // issued with the active flag: one round trip
+    return sys_active(a, s) ? 1 : 0;
   };
   auto work = [&](int, int blk, int r0, int r1, double(&acc)[2]) {
     const double al = v.alpha, e1 = v.eta, cf = v.coef;
@@ -820,9 +815,8 @@ __device__ __forceinline__ void tfq_next(const PcgArgs &a, double *red) {
   double *y1 = a.kv[1], *t = a.kv[8];
   NsView v{};
   auto want = [&](int s) -> int {
-    if (!sys_active(a, s)) return 0;
-    v = ns_view(a, s);
-    return 1;
+    v = ns_view(a, s);  // issued with the active flag: one round trip
+    return sys_active(a, s) ? 1 : 0;
   };
   auto work = [&](int, int, int r0, int r1, double(&)[1]) {
     const double be = v.beta, e2 = v.eta;
@@ -1079,12 +1073,11 @@ __device__ __forceinline__ void pipe_iterate(const PcgArgs &a, double *red) {
   double alpha = 0.0, beta = 0.0;
   int par = 0;
   auto want = [&](int s) -> int {
-    if (!sys_active(a, s)) return 0;
-    const SysState *S = a.st + s;
+    const SysState *S = a.st + s;  // all loads issued together: one round trip
     alpha = ldcg(&S->alpha);
     beta = ldcg(&S->beta);
     par = ldcg(&S->iterations) & 1;
-    return 1;
+    return sys_active(a, s) ? 1 : 0;
   };
   auto work = [&](int, int blk, int r0, int r1, double(&acc)[3]) {
     const double *m_in = a.kv[7 + par];

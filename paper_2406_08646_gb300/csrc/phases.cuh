@@ -175,8 +175,12 @@ __device__ __forceinline__ void flush(const PcgArgs &a, const BlockTable &t, int
     s_last = (prev == (unsigned)(ns - 1)) ? 1 : 0;
   }
   __syncthreads();
+  // The last CTA reads the slots through L2 (ldcg): every writer fenced its
+  // slot before counting itself in, so all slots are visible once the count
+  // is complete.  No fence after fin: the state it writes is read by later
+  // kernels only (a CTA reads a system's state before its own flush, hence
+  // before that system's fin), and kernel boundaries order those accesses.
   if (s_last) {
-    __threadfence();
     if (f32) {
       float tot[NV];
 #pragma unroll
@@ -191,7 +195,6 @@ __device__ __forceinline__ void flush(const PcgArgs &a, const BlockTable &t, int
         for (int k = 0; k < NV; ++k) d[k] = (double)tot[k];
         a.sys_cnt[s] = 0u;
         fin(s, d);
-        __threadfence();
       }
     } else {
       double tot[NV];
@@ -204,7 +207,6 @@ __device__ __forceinline__ void flush(const PcgArgs &a, const BlockTable &t, int
       if (threadIdx.x == 0) {
         a.sys_cnt[s] = 0u;
         fin(s, tot);
-        __threadfence();
       }
     }
   }
@@ -579,9 +581,9 @@ __device__ __forceinline__ void phase_A(const PcgArgs &a, double *red) {
   };
   int mode = M_INNER;
   auto want = [&](int s) -> int {
+    mode = ldcg(&a.st[s].mode);  // issued with the active flag: one round trip
     if (!sys_active(a, s)) return 0;
     if (!REFINED) return 1;
-    mode = ldcg(&a.st[s].mode);
     return mode == M_INNER ? 2 : (mode == M_XUPD ? 1 : 0);
   };
   auto work = [&](int, int blk, int r0, int r1, double(&acc)[1]) {
@@ -666,8 +668,8 @@ __device__ __forceinline__ void phase_B(const PcgArgs &a, double *red) {
   };
   SysView v{};
   auto want = [&](int s) -> int {
+    v = view_sys(a, s);  // issued with the active flag: one round trip
     if (!sys_active(a, s)) return 0;
-    v = view_sys(a, s);
     if (!REFINED) return 1;
     return (v.mode == M_INNER || v.mode == M_START) ? 2 : 0;
   };
@@ -736,8 +738,8 @@ __device__ __forceinline__ void phase_C(const PcgArgs &a, double *red) {
   auto fin = [&](int, double(&)[1]) {};
   SysView v{};
   auto want = [&](int s) -> int {
+    v = view_sys(a, s);  // issued with the active flag: one round trip
     if (!sys_active(a, s)) return 0;
-    v = view_sys(a, s);
     if (!REFINED) return 1;
     return (v.mode == M_INNER || v.mode == M_XUPD) ? 1 : 0;
   };
