@@ -151,7 +151,6 @@ template <int NV, class Fin>
 __device__ __forceinline__ void flush(const PcgArgs &a, const BlockTable &t, int64_t part_off,
                                       int s, int b, double (&acc)[NV], double *red, bool f32,
                                       Fin &fin) {
-  __shared__ int s_last;
   const int G = gridDim.x;
   if (f32) {
     float v[NV];
@@ -167,50 +166,44 @@ __device__ __forceinline__ void flush(const PcgArgs &a, const BlockTable &t, int
   const int ns = min(nb, G);
   const int slot = (b - b0) % G;
   const int64_t base = part_off + sys_slot0(a, t, s);
-  if (threadIdx.x == 0) {
+  // Warp 0 alone finishes: the other warps go on to their next blocks (or
+  // exit) at once instead of waiting at a barrier for the fence and the
+  // arrival count.  The last CTA's warp 0 reads the slots through L2
+  // (ldcg): every writer fenced its slot before counting itself in, so all
+  // slots are visible once the count is complete.  No fence after fin: the
+  // state it writes is read by later kernels only (a CTA reads a system's
+  // state before its own flush, hence before that system's fin), and kernel
+  // boundaries order those accesses.
+  if ((threadIdx.x >> 5) != 0) return;
+  const int lane = threadIdx.x & 31;
+  unsigned prev = 0;
+  if (lane == 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) a.part[(base + slot) * SLOT_STRIDE + k] = acc[k];
     __threadfence();
-    const unsigned prev = atomicAdd(a.sys_cnt + s, 1u);
-    s_last = (prev == (unsigned)(ns - 1)) ? 1 : 0;
+    prev = atomicAdd(a.sys_cnt + s, 1u);
   }
-  __syncthreads();
-  // The last CTA reads the slots through L2 (ldcg): every writer fenced its
-  // slot before counting itself in, so all slots are visible once the count
-  // is complete.  No fence after fin: the state it writes is read by later
-  // kernels only (a CTA reads a system's state before its own flush, hence
-  // before that system's fin), and kernel boundaries order those accesses.
-  if (s_last) {
-    if (f32) {
-      float tot[NV];
+  if (__shfl_sync(FULL_MASK, prev, 0) != (unsigned)(ns - 1)) return;
+  double tot[NV];
+  if (f32) {
 #pragma unroll
-      for (int k = 0; k < NV; ++k) tot[k] = 0.f;
-      for (int i = threadIdx.x; i < ns; i += blockDim.x)
+    for (int k = 0; k < NV; ++k) {
+      float x = 0.f;
+      for (int i = lane; i < ns; i += 32) x += (float)ldcg(a.part + (base + i) * SLOT_STRIDE + k);
+      tot[k] = (double)warp_sum(x);
+    }
+  } else {
 #pragma unroll
-        for (int k = 0; k < NV; ++k) tot[k] += (float)ldcg(a.part + (base + i) * SLOT_STRIDE + k);
-      block_reduce<float, NV>(tot, reinterpret_cast<float *>(red));
-      if (threadIdx.x == 0) {
-        double d[NV];
-#pragma unroll
-        for (int k = 0; k < NV; ++k) d[k] = (double)tot[k];
-        a.sys_cnt[s] = 0u;
-        fin(s, d);
-      }
-    } else {
-      double tot[NV];
-#pragma unroll
-      for (int k = 0; k < NV; ++k) tot[k] = 0.0;
-      for (int i = threadIdx.x; i < ns; i += blockDim.x)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) tot[k] += ldcg(a.part + (base + i) * SLOT_STRIDE + k);
-      block_reduce<double, NV>(tot, red);
-      if (threadIdx.x == 0) {
-        a.sys_cnt[s] = 0u;
-        fin(s, tot);
-      }
+    for (int k = 0; k < NV; ++k) {
+      double x = 0.0;
+      for (int i = lane; i < ns; i += 32) x += ldcg(a.part + (base + i) * SLOT_STRIDE + k);
+      tot[k] = warp_sum(x);
     }
   }
-  __syncthreads();
+  if (lane == 0) {
+    a.sys_cnt[s] = 0u;
+    fin(s, tot);
+  }
 }
 
 // The CTA's pass over its blocks of table t (b = blockIdx.x, + G, ...).
