@@ -237,8 +237,8 @@ int ksp_solve_cg_batched(gbs_mat A, const double *b, double *x, const ksp_opts *
  * per system, every iteration inside one kernel launch, systems largest
  * first) or on the grid-wide phase kernels in a CUDA graph, chosen as for CG
  * by mat_set_solver (automatic: per-CTA when the largest system has at most
- * 32768 nonzeros or a batch has at least one system per SM); o->host_loop
- * applies to the phase kernels.  A zero or negative diagonal entry ends the solve
+ * 40000 nonzeros plus eight per row, or a batch has at least one system per
+ * SM); o->host_loop applies to the phase kernels.  A zero or negative diagonal entry ends the solve
  * with GBS_ERR_NOT_SPD (the Jacobi preconditioner needs a positive diagonal);
  * rt.v = 0 or rho = 0 (TFQMR), rho = 0 or pt.q = 0 (BiCG) with
  * GBS_ERR_BREAKDOWN.  Arguments, results and synchronisation as in
@@ -363,7 +363,9 @@ int mat_get_plan(gbs_mat A, int32_t *spmv_rows, int32_t *update_rows, int32_t *k
  *     largest first.  Needs the sliced-ELL plan kernel (GBS_ERR_ARG from the
  *     solve otherwise); ignores host_loop; ksp_get_phase_ns reports zeros;
  *   GBS_SOLVER_AUTO (default): CTA when the largest system solved has at
- *     most 32768 nonzeros, or a batched solve has at least 2 systems per SM.
+ *     most 40000 nonzeros plus eight per row (the FP64 work of one iteration
+ *     that one SM does faster than the phase kernels' fixed cost per
+ *     iteration), or a batched solve has at least 2 systems per SM.
  * ksp_result.solver tells which one ran.  No synchronisation.
  */
 int mat_set_solver(gbs_mat A, int32_t solver);

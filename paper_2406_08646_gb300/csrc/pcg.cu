@@ -415,15 +415,20 @@ int run_loop_stepped(const LoopPlan &P, PcgArgs a, int grid_a, int grid_e, int64
 }
 
 // The per-CTA solver takes systems small enough that one SM iterates them
-// faster than the phase kernels' launch and reduction latency allows (a CTA
-// has one SM's FP64 rate, 2 FMAs per clock: about 16k nonzeros per
-// iteration match the ~20 us a phase-kernel iteration costs at any size),
-// and batches with enough systems to fill every SM with CTAs.
-constexpr int64_t CTA_AUTO_NNZ = 32768;
+// faster than the phase kernels' launch and reduction latency allows, and
+// batches with enough systems to fill every SM with CTAs.  A CTA has one
+// SM's FP64 rate (2 FMAs per clock), so its iteration costs about one FP64
+// operation per nonzero plus eight per row; measured on GB300, up to about
+// 40,000 of those it beats a phase-kernel CG iteration (about 17-20 us at
+// small sizes): q1_hex 8^3 (729 rows, 15,625 nonzeros) 16 against 24 us,
+// poisson2d 64^2 (4,096 rows, 20,224 nonzeros) 22 against 17 us.
+constexpr int64_t CTA_AUTO_WORK = 40000;
 
 bool cta_size_rule(gbs_mat A, bool per_system, int systems_per_sm) {
   const int64_t nz = per_system ? A->max_sys_nnz : A->nnz;
-  return nz <= CTA_AUTO_NNZ || (per_system && A->nsys >= (int64_t)systems_per_sm * sm_count(A));
+  const int64_t rows = per_system ? A->max_sys_rows : A->nrows;
+  return nz + 8 * rows <= CTA_AUTO_WORK ||
+         (per_system && A->nsys >= (int64_t)systems_per_sm * sm_count(A));
 }
 
 int sm_count(gbs_mat A) {

@@ -103,7 +103,8 @@ int run_loop(gbs_mat A, const LoopPlan &P, int kind, const PcgArgs &a, const dou
              double *x, const ksp_opts &o, bool per_system, cudaStream_t s);
 bool use_cta_solver(gbs_mat A, bool per_system);
 // The per-CTA solver's automatic choice: the largest system solved has at
-// most CTA_AUTO_NNZ nonzeros, or a batch gives every SM systems_per_sm CTAs.
+// most CTA_AUTO_WORK nonzeros plus eight per row, or a batch gives every SM
+// systems_per_sm CTAs.
 bool cta_size_rule(gbs_mat A, bool per_system, int systems_per_sm);
 int sm_count(gbs_mat A);
 

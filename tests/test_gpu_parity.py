@@ -488,12 +488,17 @@ def test_launch_counter_and_phase_timers():
 
 
 def test_solver_auto_choice_and_determinism():
-    p = W.poisson2d(64)
+    p = W.poisson2d(32)
     A, O = assemble_both(p.nrows, p.ncols, p.i, p.j, p.v)
     x, r = A.solve(t(p.b), rtol=1e-10)
-    assert r["solver"] == B.SOLVER_CTA            # 4096 rows: the latency path
+    assert r["solver"] == B.SOLVER_CTA            # 1024 rows: the latency path
     x2, r2 = A.solve(t(p.b), rtol=1e-10)
     assert torch.equal(x, x2) and r2 == r
+    A.close()
+    p = W.poisson2d(64)                           # 4096 rows: the phase kernels
+    A, O = assemble_both(p.nrows, p.ncols, p.i, p.j, p.v)
+    x, r = A.solve(t(p.b), rtol=1e-10)
+    assert r["solver"] == B.SOLVER_PHASES
     A.close()
     p = W.q1_hex(16, seed=6)                       # 117,649 nonzeros: the phase kernels
     A, O = assemble_both(p.nrows, p.ncols, p.i, p.j, p.v)
