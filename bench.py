@@ -457,6 +457,7 @@ def run_suite(args):
                     ("tfqmr", B.KSP_TFQMR, B.SOLVER_PHASES)]
             if A.nnz <= 2_000_000:
                 runs.append(("cg_cta", B.KSP_CG, B.SOLVER_CTA))
+                runs.append(("cg_cluster", B.KSP_CG, B.SOLVER_CLUSTER))
             for name, method, solver in runs:
                 A.set_solver(solver)
                 ts, (_, r) = _ev_time(stream, lambda: A.solve(b, x, rtol=1e-8, method=method,

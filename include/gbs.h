@@ -70,7 +70,7 @@ enum { GBS_FP64 = 0, GBS_FP32_REFINED = 1 };
  * {1, 2, 4, 8, 32} selects the CSR-vector kernel with n lanes per row. */
 enum { GBS_SPMV_AUTO = -1, GBS_SPMV_SELL = 0 };
 /* Solvers (mat_set_solver). */
-enum { GBS_SOLVER_AUTO = 0, GBS_SOLVER_PHASES = 1, GBS_SOLVER_CTA = 2 };
+enum { GBS_SOLVER_AUTO = 0, GBS_SOLVER_PHASES = 1, GBS_SOLVER_CTA = 2, GBS_SOLVER_CLUSTER = 3 };
 /* Krylov methods (ksp_opts.method; Sec. 7 batched solvers, Sec. 6.2). */
 enum { GBS_KSP_CG = 0, GBS_KSP_BICG = 1, GBS_KSP_TFQMR = 2, GBS_KSP_PIPECG = 3 };
 
@@ -113,7 +113,7 @@ typedef struct {
                                inner ones); TFQMR: products with A D^-1;
                                pipelined CG: x updates (= CG's count) */
   int32_t outer_iterations; /* refined: refinement steps; FP64: 0 */
-  int32_t solver;           /* GBS_SOLVER_PHASES or GBS_SOLVER_CTA: which ran */
+  int32_t solver;           /* GBS_SOLVER_PHASES, _CTA or _CLUSTER: which ran */
   double rnorm0;            /* ||b - A x0||_2 */
   double rnorm;             /* last recursively updated residual norm
                                (refined: last FP64 outer residual norm;
@@ -362,6 +362,13 @@ int mat_get_plan(gbs_mat A, int32_t *spmv_rows, int32_t *update_rows, int32_t *k
  *     and for batches of many systems, which then run as concurrent CTAs,
  *     largest first.  Needs the sliced-ELL plan kernel (GBS_ERR_ARG from the
  *     solve otherwise); ignores host_loop; ksp_get_phase_ns reports zeros;
+ *   GBS_SOLVER_CLUSTER: FP64 CG only (other methods and the refined solve
+ *     take the phase kernels): one thread-block cluster of up to 16 CTAs per
+ *     system, its slices split over the cluster's SMs, every iteration in
+ *     one kernel, reductions through distributed shared memory and cluster
+ *     barriers -- between the per-CTA solver (one SM) and the phase kernels
+ *     (the whole GPU, a fixed cost per iteration).  Needs the sliced-ELL
+ *     plan kernel; ignores host_loop; ksp_get_phase_ns reports zeros;
  *   GBS_SOLVER_AUTO (default): CTA when the largest system solved has at
  *     most 40000 nonzeros plus eight per row (the FP64 work of one iteration
  *     that one SM does faster than the phase kernels' fixed cost per

@@ -379,8 +379,8 @@ int mat_set_plan(gbs_mat A, int32_t spmv_rows, int32_t update_rows, int32_t kern
 
 int mat_set_solver(gbs_mat A, int32_t solver) {
   GBS_TRY(check_mat(A, "mat_set_solver"));
-  if (solver != GBS_SOLVER_AUTO && solver != GBS_SOLVER_PHASES && solver != GBS_SOLVER_CTA) {
-    set_error("mat_set_solver: solver must be GBS_SOLVER_AUTO, _PHASES or _CTA");
+  if (solver < GBS_SOLVER_AUTO || solver > GBS_SOLVER_CLUSTER) {
+    set_error("mat_set_solver: solver must be GBS_SOLVER_AUTO, _PHASES, _CTA or _CLUSTER");
     return GBS_ERR_ARG;
   }
   A->solver = solver;

@@ -90,8 +90,8 @@ template <class F>
 __device__ __forceinline__ void kry_rows(const KrylovArgs &a, const KSys &g, const int32_t *sptr,
                                          const int32_t *scol, const double *sval, const double *x,
                                          F &f) {
-  if (a.stream_matrix) sell_rows<double, true, false>(sptr, a.srow0, scol, sval, x, g.s0, g.s1, f);
-  else sell_rows<double, false, false>(sptr, a.srow0, scol, sval, x, g.s0, g.s1, f);
+  if (a.stream_matrix) sell_rows<double, true, GATHER_CA>(sptr, a.srow0, scol, sval, x, g.s0, g.s1, f);
+  else sell_rows<double, false, GATHER_CA>(sptr, a.srow0, scol, sval, x, g.s0, g.s1, f);
 }
 
 // The system's closing state (thread 0), x = 0 where b = 0, then
@@ -469,8 +469,8 @@ __device__ __forceinline__ NsView ns_view(const PcgArgs &a, int s) {
 template <class F>
 __device__ __forceinline__ void rows_t(const PcgArgs &a, int b, const double *x, F &f) {
   const int s0 = __ldg(a.ta.slice0 + b), s1 = __ldg(a.ta.slice0 + b + 1);
-  if (a.stream_matrix) sell_rows<double, true, true>(a.tptr, a.srow0, a.tcol, a.tval, x, s0, s1, f);
-  else sell_rows<double, false, true>(a.tptr, a.srow0, a.tcol, a.tval, x, s0, s1, f);
+  if (a.stream_matrix) sell_rows<double, true, GATHER_NC>(a.tptr, a.srow0, a.tcol, a.tval, x, s0, s1, f);
+  else sell_rows<double, false, GATHER_NC>(a.tptr, a.srow0, a.tcol, a.tval, x, s0, s1, f);
 }
 
 __device__ __forceinline__ void ns_activate(const PcgArgs &a, SysState &S, int status) {

@@ -30,6 +30,7 @@
 
 #include "device_util.cuh"
 #include "internal.cuh"
+#include "cluster.cuh"
 #include "cta.cuh"
 #include "phases.cuh"
 
@@ -439,8 +440,62 @@ int sm_count(gbs_mat A) {
 
 bool use_cta_solver(gbs_mat A, bool per_system) {
   if (A->solver == GBS_SOLVER_CTA) return true;
-  if (A->solver == GBS_SOLVER_PHASES || A->lanes != GBS_SPMV_SELL) return false;
+  if (A->solver == GBS_SOLVER_PHASES || A->solver == GBS_SOLVER_CLUSTER ||
+      A->lanes != GBS_SPMV_SELL)
+    return false;  // (a refined solve asked for the cluster solver takes the phase kernels)
   return cta_size_rule(A, per_system, 2);  // two 1024-thread PCG CTAs fit an SM
+}
+
+// Cluster size for the cluster solver: about one SM per 40,000 FP64
+// operations of an iteration of the largest system (the per-CTA solver's
+// break-even), at least 2, at most CLUSTER_MAX, and no more than the device
+// can hold as one cluster.
+static int cluster_size(gbs_mat A, bool per_system) {
+  const int64_t nz = per_system ? A->max_sys_nnz : A->nnz;
+  const int64_t rows = per_system ? A->max_sys_rows : A->nrows;
+  int want = (int)std::min<int64_t>(CLUSTER_MAX, std::max<int64_t>(2, (nz + 8 * rows + CTA_AUTO_WORK - 1) / CTA_AUTO_WORK));
+  static bool opted_in = false;
+  if (!opted_in) {
+    cudaFuncSetAttribute(k_cluster_pcg, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    opted_in = true;
+  }
+  for (; want > 1; --want) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)want);
+    cfg.blockDim = dim3(CTA_TPB);
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = (unsigned)want;
+    at.val.clusterDim.y = 1;
+    at.val.clusterDim.z = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_cluster_pcg, &cfg) == cudaSuccess && n > 0) break;
+    cudaGetLastError();  // clear a refused size
+  }
+  return want;
+}
+
+// nclusters systems (a.order, or the whole matrix when a.ensemble), one
+// cluster each.
+static int launch_cluster(gbs_mat A, const PcgArgs &a, int32_t nclusters, cudaStream_t s) {
+  const int cs = cluster_size(A, !a.ensemble);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(nclusters * cs));
+  cfg.blockDim = dim3(CTA_TPB);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at;
+  at.id = cudaLaunchAttributeClusterDimension;
+  at.val.clusterDim.x = (unsigned)cs;
+  at.val.clusterDim.y = 1;
+  at.val.clusterDim.z = 1;
+  cfg.attrs = &at;
+  cfg.numAttrs = 1;
+  GBS_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_cluster_pcg, a));
+  GBS_LAUNCHED(1);
+  return GBS_OK;
 }
 
 int solve(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool per_system,
@@ -456,6 +511,18 @@ int solve(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool per_sys
     GBS_TRY_CUDA(cudaMemsetAsync(A->st, 0, sizeof(SysState) * A->nsys, s));
     GBS_TRY_CUDA(cudaMemsetAsync(A->ctl, 0, sizeof(DevCtl), s));
     return GBS_OK;
+  }
+  if (!refined && A->solver == GBS_SOLVER_CLUSTER) {
+    if (A->lanes != GBS_SPMV_SELL) {
+      set_error("the cluster solver needs the sliced-ELL row products (plan kernel)");
+      return GBS_ERR_ARG;
+    }
+    A->last_solver = GBS_SOLVER_CLUSTER;
+    GBS_TRY_CUDA(cudaMemsetAsync(A->ctl, 0, sizeof(DevCtl), s));
+    GBS_TRY(put_call(A->call, call_args(b, x, o), s, A->ctl));
+    PcgArgs a = make_args(A, per_system, refined);
+    a.order = per_system ? A->cta_order : nullptr;
+    return launch_cluster(A, a, per_system ? A->nsys : 1, s);
   }
   if (use_cta_solver(A, per_system)) {
     if (A->lanes != GBS_SPMV_SELL) {

@@ -345,11 +345,16 @@ struct Vals {
   T v[N];
 };
 
-// Gather of x: the read-only path when NC, else a plain (L1-cached, coherent
-// within the CTA) load.
-template <bool NC, typename T>
+// How a row product gathers x: GATHER_NC the read-only path (x is not
+// written during the kernel), GATHER_CA a plain L1-cached load (coherent for
+// values the same CTA wrote before a barrier), GATHER_CG an L2 load (values
+// other CTAs of a cluster wrote before a cluster barrier).
+enum { GATHER_CA = 0, GATHER_NC = 1, GATHER_CG = 2 };
+
+template <int GATHER, typename T>
 __device__ __forceinline__ T ld_x(const T *p) {
-  if constexpr (NC) return __ldg(p);
+  if constexpr (GATHER == GATHER_NC) return __ldg(p);
+  else if constexpr (GATHER == GATHER_CG) return __ldcg(p);
   else return __ldca(p);
 }
 
@@ -380,10 +385,11 @@ struct Pair<float> {
 // rows are loaded before its entries, so no dependent load is left for the
 // end.  f(r, sum) runs on every lane whose row exists.  STREAM: the entries
 // are loaded with the evict-first hint, so that a matrix larger than L2 does
-// not push the vectors (x and the solver's vectors) out of it.  NC: x is not
-// written during the kernel, so its gathers may take the read-only path;
-// false where the same CTA wrote x before a __syncthreads.
-template <typename T, bool STREAM, bool NC, class F>
+// not push the vectors (x and the solver's vectors) out of it.  NC: how x is
+// gathered (GATHER_NC where x is not written during the kernel, GATHER_CA
+// where the same CTA wrote it before a __syncthreads, GATHER_CG where other
+// CTAs of a cluster wrote it before a cluster barrier).
+template <typename T, bool STREAM, int NC, class F>
 __device__ __forceinline__ void sell_rows(const int32_t *__restrict__ sptr,
                                           const int32_t *__restrict__ srow0,
                                           const int32_t *__restrict__ scol,
@@ -431,8 +437,8 @@ __device__ __forceinline__ void row_products(const PcgArgs &a, int b, int r0, in
                                              F &f) {
   if constexpr (L == 0) {
     const int s0 = __ldg(a.ta.slice0 + b), s1 = __ldg(a.ta.slice0 + b + 1);
-    if (a.stream_matrix) sell_rows<T, true, true>(a.sptr, a.srow0, a.scol, sell_val, x, s0, s1, f);
-    else sell_rows<T, false, true>(a.sptr, a.srow0, a.scol, sell_val, x, s0, s1, f);
+    if (a.stream_matrix) sell_rows<T, true, GATHER_NC>(a.sptr, a.srow0, a.scol, sell_val, x, s0, s1, f);
+    else sell_rows<T, false, GATHER_NC>(a.sptr, a.srow0, a.scol, sell_val, x, s0, s1, f);
   } else
     csr_rows<T, L>(a.row_ptr, a.col, csr_val, x, r0, r1, f);
 }
