@@ -109,8 +109,9 @@ template <int GATHER, class F>
 __device__ __forceinline__ void cluster_rows(const PcgArgs &a, const ClusterPart &c,
                                              const double *x, F &f) {
   if (a.stream_matrix)
-    sell_rows<double, true, GATHER>(a.sptr, a.srow0, a.scol, a.sval, x, c.s0, c.s1, f);
-  else sell_rows<double, false, GATHER>(a.sptr, a.srow0, a.scol, a.sval, x, c.s0, c.s1, f);
+    sell_rows<double, true, GATHER>(a.sptr, a.srow0, a.scol, a.soff, a.sval, x, c.s0, c.s1,
+                                    f);
+  else sell_rows<double, false, GATHER>(a.sptr, a.srow0, a.scol, a.soff, a.sval, x, c.s0, c.s1, f);
 }
 
 // FP64 PCG of phases.cuh / cta.cuh, the system spread over a cluster.

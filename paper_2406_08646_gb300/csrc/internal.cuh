@@ -144,6 +144,8 @@ struct gbs_mat_s {
   int32_t *sell_ptr = nullptr;     // nslices + 1 entry offsets (< 2^31)
   int32_t *sell_row0 = nullptr;    // nslices + 1 first rows
   int32_t *sell_col = nullptr;     // sell_nnz, -1 = padding
+  int16_t *sell_off16 = nullptr;   // sell_nnz column offsets col - row when they all fit
+                                   // in 16 bits (padding -32768); the kernels read these then
   double *sell_val = nullptr;      // sell_nnz
   float *sell_val32 = nullptr;     // sell_nnz (refined solves)
   std::vector<int32_t> sell_slice0_h;  // nsys + 1 first slice of each system

@@ -236,7 +236,8 @@ PcgArgs make_args(gbs_mat A, bool per_system, bool refined) {
   a.val32 = A->val32;
   a.sptr = A->sell_ptr;
   a.srow0 = A->sell_row0;
-  a.scol = A->sell_col;
+  a.scol = A->sell_off16 ? nullptr : A->sell_col;
+  a.soff = A->sell_off16;
   a.sval = A->sell_val;
   a.sval32 = A->sell_val32;
   a.stream_matrix = stream_matrix(A, refined ? 8 : 12);
@@ -258,7 +259,8 @@ PcgArgs make_args(gbs_mat A, bool per_system, bool refined) {
     for (int k = 0; k < KRYLOV_NVEC; ++k) a.kv[k] = A->kv + (size_t)k * (size_t)A->nrows;
   if (A->At) {
     a.tptr = A->At->sell_ptr;
-    a.tcol = A->At->sell_col;
+    a.tcol = A->At->sell_off16 ? nullptr : A->At->sell_col;
+    a.toff = A->At->sell_off16;
     a.tval = A->At->sell_val;
   }
   return a;

@@ -61,6 +61,7 @@ struct PcgArgs {
   const float *val32;
   const int32_t *sptr;   // sliced-ELL copy (kernels with L == 0)
   const int32_t *srow0, *scol;
+  const int16_t *soff;   // 16-bit column offsets of the sliced copy (scol null then)
   const double *sval;
   const float *sval32;
   int32_t stream_matrix;  // 1: load the sliced copy evict-first (larger than L2 / 2)
@@ -79,6 +80,7 @@ struct PcgArgs {
   int32_t trip;                     // stepped: index of this trip
   double *kv[KRYLOV_NVEC];          // nonsymmetric solvers' work vectors
   const int32_t *tptr, *tcol;       // sliced-ELL copy of A^T (BiCG), A's slices
+  const int16_t *toff;              //   (its 16-bit offsets, tcol null then)
   const double *tval;
 };
 
@@ -378,25 +380,46 @@ struct Pair<float> {
 
 // Row products of the 32-row slices [s0, s1) of the sliced-ELL copy: warp w
 // takes slices s0 + w, s0 + w + nw, ...; lane i sums row i of the slice in
-// CSR order, one FMA per stored nonzero; padding (column -1) is skipped.
-// Entries k = 2m, 2m + 1 of a lane's row are adjacent (pair layout, sell.cu),
-// so one 8-byte column load and one 8- or 16-byte value load fetch two
-// entries; two pairs are in flight per step.  A slice's offsets and first
-// rows are loaded before its entries, so no dependent load is left for the
-// end.  f(r, sum) runs on every lane whose row exists.  STREAM: the entries
-// are loaded with the evict-first hint, so that a matrix larger than L2 does
-// not push the vectors (x and the solver's vectors) out of it.  NC: how x is
-// gathered (GATHER_NC where x is not written during the kernel, GATHER_CA
-// where the same CTA wrote it before a __syncthreads, GATHER_CG where other
-// CTAs of a cluster wrote it before a cluster barrier).
+// CSR order, one FMA per stored nonzero; padding is skipped.  Entries
+// k = 2m, 2m + 1 of a lane's row are adjacent (pair layout, sell.cu), so one
+// load fetches two column indices and one 8- or 16-byte load two values; two
+// pairs are in flight per step.  Column indices come as 32-bit columns
+// (scol, padding -1) or, when every column is within 2^15 - 1 of its row, as
+// 16-bit offsets col - row (soff, padding SELL_PAD16): 10 bytes per FP64
+// nonzero instead of 12.  Exactly one of scol and soff is non-null.  A
+// slice's offsets and first rows are loaded before its entries, so no
+// dependent load is left for the end.  f(r, sum) runs on every lane whose row
+// exists.  STREAM: the entries are loaded with the evict-first hint, so that
+// a matrix larger than L2 does not push the vectors (x and the solver's
+// vectors) out of it.  NC: how x is gathered (GATHER_NC where x is not
+// written during the kernel, GATHER_CA where the same CTA wrote it before a
+// __syncthreads, GATHER_CG where other CTAs of a cluster wrote it before a
+// cluster barrier).
+constexpr int16_t SELL_PAD16 = -32768;
+
+// The two column indices of a pair (entries 2m, 2m + 1 of a lane's row): from
+// the 32-bit columns, or decoded from the two 16-bit offsets; padding -1.
+template <bool STREAM>
+__device__ __forceinline__ int2 sell_pair_cols(const int2 *__restrict__ c2,
+                                               const int *__restrict__ o2, int pi, int r) {
+  if (o2) {
+    const int o = ld_entry<STREAM>(o2 + pi);
+    const int lo = (int)(int16_t)o, hi = o >> 16;
+    return make_int2(lo == SELL_PAD16 ? -1 : r + lo, hi == SELL_PAD16 ? -1 : r + hi);
+  }
+  return ld_entry<STREAM>(c2 + pi);
+}
+
 template <typename T, bool STREAM, int NC, class F>
 __device__ __forceinline__ void sell_rows(const int32_t *__restrict__ sptr,
                                           const int32_t *__restrict__ srow0,
                                           const int32_t *__restrict__ scol,
+                                          const int16_t *__restrict__ soff,
                                           const T *__restrict__ sval, const T *x,
                                           int s0, int s1, F &f) {
   typedef typename Pair<T>::type P;
   const int2 *__restrict__ c2 = reinterpret_cast<const int2 *>(scol);
+  const int *__restrict__ o2 = reinterpret_cast<const int *>(soff);  // two offsets per int
   const P *__restrict__ v2 = reinterpret_cast<const P *>(sval);
   const int lane = threadIdx.x & 31;
   for (int sl = s0 + (int)(threadIdx.x >> 5); sl < s1; sl += (int)(blockDim.x >> 5)) {
@@ -407,7 +430,8 @@ __device__ __forceinline__ void sell_rows(const int32_t *__restrict__ sptr,
     const int pend = pi + 32 * ((b1 - b0) >> 6);
     T acc = T(0);
     for (; pi + 32 < pend; pi += 64) {
-      const int2 ca = ld_entry<STREAM>(c2 + pi), cb = ld_entry<STREAM>(c2 + pi + 32);
+      const int2 ca = sell_pair_cols<STREAM>(c2, o2, pi, r);
+      const int2 cb = sell_pair_cols<STREAM>(c2, o2, pi + 32, r);
       const P va = ld_entry<STREAM>(v2 + pi), vb = ld_entry<STREAM>(v2 + pi + 32);
       if (ca.x >= 0) acc = fma_rn(va.x, ld_x<NC>(x + ca.x), acc);
       if (ca.y >= 0) acc = fma_rn(va.y, ld_x<NC>(x + ca.y), acc);
@@ -415,14 +439,20 @@ __device__ __forceinline__ void sell_rows(const int32_t *__restrict__ sptr,
       if (cb.y >= 0) acc = fma_rn(vb.y, ld_x<NC>(x + cb.y), acc);
     }
     if (pi < pend) {
-      const int2 ca = ld_entry<STREAM>(c2 + pi);
+      const int2 ca = sell_pair_cols<STREAM>(c2, o2, pi, r);
       const P va = ld_entry<STREAM>(v2 + pi);
       if (ca.x >= 0) acc = fma_rn(va.x, ld_x<NC>(x + ca.x), acc);
       if (ca.y >= 0) acc = fma_rn(va.y, ld_x<NC>(x + ca.y), acc);
     }
     if (((b1 - b0) >> 5) & 1) {  // the odd last entry, stored after the pairs
       const int q = b1 - 32 + lane;
-      const int c = ld_entry<STREAM>(scol + q);
+      int c;
+      if (soff) {
+        const int o = ld_entry<STREAM>(soff + q);
+        c = o == SELL_PAD16 ? -1 : r + o;
+      } else {
+        c = ld_entry<STREAM>(scol + q);
+      }
       if (c >= 0) acc = fma_rn(ld_entry<STREAM>(sval + q), ld_x<NC>(x + c), acc);
     }
     if (r < re) f(r, acc);
@@ -437,8 +467,8 @@ __device__ __forceinline__ void row_products(const PcgArgs &a, int b, int r0, in
                                              F &f) {
   if constexpr (L == 0) {
     const int s0 = __ldg(a.ta.slice0 + b), s1 = __ldg(a.ta.slice0 + b + 1);
-    if (a.stream_matrix) sell_rows<T, true, GATHER_NC>(a.sptr, a.srow0, a.scol, sell_val, x, s0, s1, f);
-    else sell_rows<T, false, GATHER_NC>(a.sptr, a.srow0, a.scol, sell_val, x, s0, s1, f);
+    if (a.stream_matrix) sell_rows<T, true, GATHER_NC>(a.sptr, a.srow0, a.scol, a.soff, sell_val, x, s0, s1, f);
+    else sell_rows<T, false, GATHER_NC>(a.sptr, a.srow0, a.scol, a.soff, sell_val, x, s0, s1, f);
   } else
     csr_rows<T, L>(a.row_ptr, a.col, csr_val, x, r0, r1, f);
 }

@@ -38,13 +38,15 @@ __global__ void k_slice_width(int64_t nslices, const int32_t *__restrict__ srow0
   }
 }
 
-// Columns (and, with val != nullptr, values) of the sliced copy: one warp per
-// slice, lane i on row i of the slice, padding written as (-1, 0).
+// Columns (and, with val != nullptr, values; with soff != nullptr, the 16-bit
+// offsets col - row, padding -32768) of the sliced copy: one warp per slice,
+// lane i on row i of the slice, padding written as (-1, 0).
 template <typename T>
 __global__ void k_sell_fill(int64_t nslices, const int32_t *__restrict__ sptr,
                             const int32_t *__restrict__ srow0, const int32_t *__restrict__ row_ptr,
                             const int32_t *__restrict__ col, const T *__restrict__ val,
-                            int32_t *__restrict__ scol, T *__restrict__ sval) {
+                            int32_t *__restrict__ scol, int16_t *__restrict__ soff,
+                            T *__restrict__ sval) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < nslices; s += nw) {
@@ -57,9 +59,24 @@ __global__ void k_sell_fill(int64_t nslices, const int32_t *__restrict__ sptr,
       const bool ok = k < len;
       const int64_t q = k < 2 * np ? b + 64 * (k >> 1) + 2 * lane + (k & 1) : b + 64 * np + lane;
       if (scol) scol[q] = ok ? col[rs + k] : -1;
+      if (soff) soff[q] = ok ? (int16_t)(col[rs + k] - r) : (int16_t)-32768;
       if (sval) sval[q] = ok ? val[rs + k] : T(0);
     }
   }
+}
+
+// Largest |col - row| over the matrix (the 16-bit offsets need < 2^15).
+__global__ void k_col_span(int64_t nrows, const int32_t *__restrict__ row_ptr,
+                           const int32_t *__restrict__ col, int32_t *__restrict__ span) {
+  int32_t m = 0;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows;
+       r += (int64_t)gridDim.x * blockDim.x)
+    for (int32_t p = row_ptr[r]; p < row_ptr[r + 1]; ++p) {
+      const int64_t d = (int64_t)col[p] - r, ad = d < 0 ? -d : d;
+      m = max(m, (int32_t)(ad > (1 << 30) ? (1 << 30) : ad));
+    }
+  m = (int32_t)__reduce_max_sync(0xffffffffu, (unsigned)m);
+  if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(span, m);
 }
 
 // FP32 values of the sliced copy, RN(FP64 values), padding stays 0.
@@ -71,11 +88,12 @@ __global__ void k_sell_to_fp32(int64_t n, const double *__restrict__ v, float *_
 
 void free_sell(gbs_mat A) {
   for (void *p : {(void *)A->sell_ptr, (void *)A->sell_row0, (void *)A->sell_col,
-                  (void *)A->sell_val, (void *)A->sell_val32})
+                  (void *)A->sell_off16, (void *)A->sell_val, (void *)A->sell_val32})
     if (p) cudaFree(p);
   A->sell_ptr = nullptr;
   A->sell_row0 = nullptr;
   A->sell_col = nullptr;
+  A->sell_off16 = nullptr;
   A->sell_val = nullptr;
   A->sell_val32 = nullptr;
   A->nslices = A->sell_nnz = 0;
@@ -133,10 +151,27 @@ int sell_build(gbs_mat A, cudaStream_t s) {
     const size_t m = (size_t)std::max<int64_t>(A->sell_nnz, 1);
     GBS_TRY_CUDA(cudaMalloc(&A->sell_col, sizeof(int32_t) * m));
     GBS_TRY_CUDA(cudaMalloc(&A->sell_val, sizeof(double) * m));
+    // 16-bit column offsets when every column lies within 2^15 - 1 of its row
+    int32_t span = 0;
+    if (A->nrows > 0) {
+      int32_t *d = nullptr;
+      GBS_TRY_CUDA(cudaMalloc(&d, sizeof(int32_t)));
+      cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int32_t), s);
+      if (e == cudaSuccess) {
+        k_col_span<<<grid_of(A->nrows, 256), 256, 0, s>>>(A->nrows, A->row_ptr, A->col, d);
+        count_launches(1);
+        e = cudaGetLastError();
+      }
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&span, d, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      cudaFree(d);
+      GBS_TRY_CUDA(e);
+    }
+    if (span <= 32767) GBS_TRY_CUDA(cudaMalloc(&A->sell_off16, sizeof(int16_t) * m));
     if (A->nslices > 0) {
       k_sell_fill<double><<<grid_of(A->nslices * 32, 256), 256, 0, s>>>(
           A->nslices, A->sell_ptr, A->sell_row0, A->row_ptr, A->col, (const double *)nullptr,
-          A->sell_col, (double *)nullptr);
+          A->sell_col, A->sell_off16, (double *)nullptr);
       GBS_LAUNCHED(1);
     }
     if (A->values_set) GBS_TRY(sell_values(A, s));
@@ -151,7 +186,7 @@ int sell_values(gbs_mat A, cudaStream_t s) {
   if (!A->sell_val || A->nslices == 0) return GBS_OK;
   k_sell_fill<double><<<grid_of(A->nslices * 32, 256), 256, 0, s>>>(
       A->nslices, A->sell_ptr, A->sell_row0, A->row_ptr, A->col, A->val, (int32_t *)nullptr,
-      A->sell_val);
+      (int16_t *)nullptr, A->sell_val);
   GBS_LAUNCHED(1);
   return GBS_OK;
 }
