@@ -115,6 +115,20 @@ def pcg_alg_bytes(n: int, nnz: int, iterations: int) -> float:
     return iterations * it + 40.0 * n + 12.0 * nnz + 4.0 * (n + 1) + 16.0 * n
 
 
+def fp64_pipe(nnz: int, seconds: float, clk: dict) -> dict:
+    """The SpMV's other bound: one FP64 FMA per stored nonzero against the FP64
+    pipe's peak, 2 FMAs per clock per SM (GB300's FP64 rate, 1.25 TFLOP/s
+    nominal) times the SMs and the SM clock sampled during the run."""
+    import torch
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0
+    peak = 2.0 * nsm * mhz * 1e6 / 1e9  # G FMA/s
+    got = nnz / seconds / 1e9
+    return {"achieved": got, "peak": peak, "unit": "G FMA/s", "frac": got / peak,
+            "what": "the row product's FP64 FMAs (one per nonzero) over the FP64 pipe's "
+                    "peak at the sampled SM clock"}
+
+
 def spmv_alg_bytes(n: int, nnz: int) -> float:
     """Values and column indices once (12 B per nonzero), x once and y once
     (16 B per row); the sliced layout's slice offsets replace row pointers and
@@ -707,7 +721,8 @@ def run_gpu(args, rank: int, world: int):
                          "frac": spmv_gbs / hbm, "peak_kind": f"{peak_kind} (copy, burst)",
                          "traffic": traffic, "alg_bytes": spmv_alg_bytes(n, nnz),
                          "timing": f"CUDA events around {SPMV_REPS} back-to-back launches "
-                                   "on the launching stream, median over steps"},
+                                   "on the launching stream, median over steps",
+                         "fp64": fp64_pipe(nnz, spmv_s, clk)},
             "solve_roofline": {"what": "whole FP64 solve (one graph launch): PCG floor bytes "
                                        "12 nnz + 4(n+1) + 72 n per iteration, plus setup and "
                                        "closing residual, over the solve's event time",
