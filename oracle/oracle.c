@@ -687,9 +687,16 @@ int orc_tfqmr(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
  *     beta = gamma / gamma_prev, alpha = gamma / (delta - beta gamma / alpha_prev)
  *     z = n + beta z; q = m + beta q; s = w + beta s; p = u + beta p
  *     x += alpha p; r -= alpha s; u -= alpha q; w -= alpha z.
+ * The recurrences let the recursive r drift from b - A x (more than CG's
+ * do), so a recursive residual that meets the test is confirmed with the
+ * true one, r = b - A x: if that misses the test too, the recurrences
+ * restart from x (u = M^-1 r, w = A u, p = s = q = z = 0, the next
+ * iteration with beta = 0); outer_iterations counts the restarts, and
+ * iterations (the x updates) keeps counting across them.
  * A non-positive gamma or alpha denominator: BREAKDOWN.  rnorm reports the
- * last recursive ||r||.  aux (7 n doubles, or NULL) receives r, u, w, p, s,
- * q, z at exit, for checking the recurrences' invariants.
+ * last ||r|| (at a normal exit the confirmed true residual).  aux (7 n
+ * doubles, or NULL) receives r, u, w, p, s, q, z at exit, for checking the
+ * recurrences' invariants.
  */
 int orc_pipecg(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
                const double *b, double *x, double rtol, int64_t maxit, int nonzero_guess,
@@ -710,7 +717,8 @@ int orc_pipecg(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
     orc_spmv(n, rp, ci, a, u, w);
     for (int64_t i = 0; i < n; ++i) p[i] = s[i] = q[i] = z[i] = 0.0;
     double gamma_prev = 0.0, alpha_prev = 0.0;
-    int64_t it = 0;
+    int64_t it = 0, restarts = 0;
+    int fresh = 1; /* the next iteration starts the recurrences: beta = 0 */
     for (;;) {
       const double gamma = dot(n, r, u);
       const double delta = dot(n, w, u);
@@ -720,7 +728,25 @@ int orc_pipecg(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
         st = ORC_ERR_NAN;
         break;
       }
-      if (rn <= rtol * bnorm) break;
+      if (rn <= rtol * bnorm) {
+        /* confirm with the true residual (m as scratch) */
+        orc_spmv(n, rp, ci, a, x, m);
+        for (int64_t i = 0; i < n; ++i) r[i] = b[i] - m[i];
+        const double tn = sqrt(dot(n, r, r));
+        res->rnorm = tn;
+        if (!isfinite(tn)) {
+          st = ORC_ERR_NAN;
+          break;
+        }
+        if (tn <= rtol * bnorm) break;
+        /* restart the recurrences from x */
+        ++restarts;
+        for (int64_t i = 0; i < n; ++i) u[i] = dinv[i] * r[i];
+        orc_spmv(n, rp, ci, a, u, w);
+        for (int64_t i = 0; i < n; ++i) p[i] = s[i] = q[i] = z[i] = 0.0;
+        fresh = 1;
+        continue;
+      }
       if (it >= maxit) {
         st = ORC_ERR_MAXIT;
         break;
@@ -728,7 +754,7 @@ int orc_pipecg(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
       for (int64_t i = 0; i < n; ++i) m[i] = dinv[i] * w[i];
       orc_spmv(n, rp, ci, a, m, nv);
       double beta = 0.0, den = delta;
-      if (it > 0) {
+      if (!fresh) {
         beta = gamma / gamma_prev;
         den = delta - beta * gamma / alpha_prev;
       }
@@ -747,9 +773,11 @@ int orc_pipecg(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
       for (int64_t i = 0; i < n; ++i) w[i] = w[i] - alpha * z[i];
       gamma_prev = gamma;
       alpha_prev = alpha;
+      fresh = 0;
       ++it;
     }
     res->iterations = (int32_t)it;
+    res->outer_iterations = (int32_t)restarts;
   }
   if (aux && n > 0) {
     const double *src[7] = {r, u, w, p, s, q, z};

@@ -3,7 +3,9 @@ Ghysels-Vanroose; the latency-bound regime of Sec. 6.2's asynchronous
 solvers): PCG's iterates in exact arithmetic (same counts, same solutions),
 the auxiliary recurrences' invariants (u = M^-1 r, w = A u, s = A p,
 q = M^-1 s, z = A q, r = b - A x), dense solves, finite termination with
-three eigenvectors, the error paths and the batched driver."""
+three eigenvectors, the error paths, the batched driver, and the restart
+that brings the true residual to the tolerance where the recursive one
+drifted below it."""
 import numpy as np
 import pytest
 
@@ -155,3 +157,47 @@ def test_batched_equals_one_at_a_time():
         xs, r = oracle.pipecg(As, bt.b[ro[s]:ro[s + 1]], rtol=1e-9)
         assert x[ro[s]:ro[s + 1]].tobytes() == xs.tobytes()
         assert rs[s]["iterations"] == r["iterations"] and r["status"] == oracle.OK
+
+
+def test_restart_confirms_the_true_residual():
+    """On a 512 x 512 Laplacian (kappa ~ 1e5) the recursive residual of
+    pipelined CG falls below rtol ||b|| while b - A x is still above it; the
+    confirmation catches that and restarts the recurrences from x, and the
+    solve ends with the true residual within the tolerance, after about as
+    many x updates as CG needs."""
+    m = 512
+    p = W.poisson2d(m)
+    b = np.random.default_rng(1007 + m).standard_normal(p.nrows)
+    A = assemble(p)
+    x, r = oracle.pipecg(A, b, rtol=1e-8)
+    xc, rc = oracle.pcg(A, b, rtol=1e-8)
+    assert r["status"] == oracle.OK
+    assert r["outer_iterations"] >= 1                      # at least one restart
+    assert r["true_rel_residual"] <= 1e-8 * (1 + 1e-6)
+    assert abs(r["rnorm"] / np.linalg.norm(b) - r["true_rel_residual"]) <= 1e-12
+    assert rc["iterations"] <= r["iterations"] <= 1.2 * rc["iterations"]
+
+
+def test_restart_reinitialises_the_recurrences():
+    """After a restart the invariants hold again (u = M^-1 r, w = A u, and
+    p, s, q, z consistent), checked at the end of the solve, some iterations
+    past the restart: the drift the recurrences accumulate after it is a few
+    parts in a million of these small vectors; a restart that left any of
+    them stale would be off by order one."""
+    m = 512
+    p = W.poisson2d(m)
+    b = np.random.default_rng(1007 + m).standard_normal(p.nrows)
+    A = assemble(p)
+    x0, r0 = oracle.pipecg(A, b, rtol=1e-8)
+    k = r0["iterations"]                   # an iteration limit just past the restart
+    x, r, v = oracle.pipecg(A, b, rtol=1e-8, maxit=k, want_aux=True)
+    import scipy.sparse as sp
+    S = sp.csr_matrix((A.val, A.col, A.row_ptr), shape=(A.nrows, A.nrows))
+    dinv = 1.0 / S.diagonal()
+    nr = lambda t: np.linalg.norm(t)
+    assert nr(v["r"] - (b - S @ x)) <= 1e-6 * nr(b)
+    assert r["outer_iterations"] >= 1
+    assert nr(v["u"] - dinv * v["r"]) <= 1e-4 * nr(dinv * v["r"])
+    assert nr(v["w"] - S @ v["u"]) <= 1e-4 * nr(S @ v["u"])
+    assert nr(v["s"] - S @ v["p"]) <= 1e-4 * nr(S @ v["p"])
+    assert nr(v["q"] - dinv * v["s"]) <= 1e-4 * nr(dinv * v["s"])
