@@ -968,19 +968,28 @@ static LoopPlan tfqmr_plan() {
 // partial gamma = r.u, delta = w.u, ||r||^2; the last arriver's fin runs the
 // tests and computes the next alpha and beta.  CG's three kernels and two
 // reductions per iteration become one and one.
+//
+// A recursive residual that meets the test is confirmed with the true one
+// (the oracle's reading): the same kernel, in mode PIPE_VERIFY for that
+// system, computes r = b - A x and u = M^-1 r; if ||r|| misses the test too,
+// mode PIPE_RESTART computes w = A u and the next m, zeroes p, s, q, z and
+// restarts the recurrences (beta = 0), counted in outer_iterations.
+enum { PIPE_ITER = 0, PIPE_VERIFY = 1, PIPE_RESTART = 2 };
 
 // The tests at the top of an iteration and the next alpha, beta from
-// (gamma, delta, r.r); returns the status, or -1 to go on.
+// (gamma, delta, r.r); returns the status (GBS_OK: the recursive residual
+// meets the test, to be confirmed), or -1 to go on.  S.first: the
+// recurrences (re)start here, beta = 0.
 __device__ __forceinline__ int pipe_top(const CallArgs &C, SysState &S, double gamma,
-                                        double delta, double rr) {
+                                        double delta, double rr, bool may_converge) {
   const double rn = sqrt(rr);
   S.rr = rr;
   S.rnorm = rn;
   if (!isfinite(rn) || !isfinite(gamma) || !isfinite(delta)) return GBS_ERR_NAN;
-  if (rn <= C.rtol * sqrt(S.bb)) return GBS_OK;
+  if (may_converge && rn <= C.rtol * sqrt(S.bb)) return GBS_OK;
   if (S.iterations >= C.maxit) return GBS_ERR_MAXIT;
   double beta = 0.0, den = delta;
-  if (S.iterations > 0) {
+  if (!S.first) {
     beta = gamma / S.rho;  // S.rho: the previous gamma
     den = delta - beta * gamma / S.alpha;
   }
@@ -988,7 +997,15 @@ __device__ __forceinline__ int pipe_top(const CallArgs &C, SysState &S, double g
   S.beta = beta;
   S.alpha = gamma / den;
   S.rho = gamma;
+  S.first = 0;
   return -1;
+}
+
+// After pipe_top: a recursive convergence goes to the confirmation, any
+// other status ends the system.
+__device__ __forceinline__ void pipe_after_top(const PcgArgs &a, SysState &S, int st) {
+  if (st == GBS_OK) S.mode = PIPE_VERIFY;
+  else if (st >= 0) deactivate(a, S, st);
 }
 
 // r = b - A x0, u = M^-1 r; r.r, b.b, missing diagonals; fin: start-up
@@ -1024,6 +1041,8 @@ __device__ __forceinline__ void pipe_setup(const PcgArgs &a, double *red) {
     S.bb = tot[1];
     S.rr = tot[0];
     S.rnorm0 = S.rnorm = sqrt(tot[0]);
+    S.first = 1;
+    S.mode = PIPE_ITER;
     const int st = kry_start_status(tot[2], tot[1]);
     if (st == GBS_OK) {
       S.zero_x = 1;
@@ -1062,64 +1081,107 @@ __device__ __forceinline__ void pipe_start(const PcgArgs &a, double *red) {
   };
   auto fin = [&](int s, double(&tot)[3]) {
     SysState &S = a.st[s];
-    const int st = pipe_top(C, S, tot[0], tot[1], tot[2]);
-    if (st >= 0) deactivate(a, S, st);
+    pipe_after_top(a, S, pipe_top(C, S, tot[0], tot[1], tot[2], true));
   };
   walk<3>(a, a.ta, 0, red, want, work, fin);
 }
 
-// One iteration.  Table A.
+// One trip: an iteration, or for a system in PIPE_VERIFY / PIPE_RESTART the
+// confirmation or the restart.  Table A.
 __device__ __forceinline__ void pipe_iterate(const PcgArgs &a, double *red) {
   const CallArgs &C = *a.call;
+  const double *b = C.b;
   double *x = C.x;
   double *r = a.kv[0], *u = a.kv[1], *w = a.kv[2], *p = a.kv[3], *sv = a.kv[4],
          *q = a.kv[5], *z = a.kv[6];
   double alpha = 0.0, beta = 0.0;
-  int par = 0;
+  int par = 0, mode = PIPE_ITER;
   auto want = [&](int s) -> int {
     const SysState *S = a.st + s;  // all loads issued together: one round trip
     alpha = ldcg(&S->alpha);
     beta = ldcg(&S->beta);
     par = ldcg(&S->iterations) & 1;
+    mode = ldcg(&S->mode);
     return sys_active(a, s) ? 1 : 0;
   };
   auto work = [&](int, int blk, int r0, int r1, double(&acc)[3]) {
-    const double *m_in = a.kv[7 + par];
-    double *m_out = a.kv[8 - par];
     double a0 = acc[0], a1 = acc[1], a2 = acc[2];
-    auto f = [&](int i, double nv) {
-      const double dv = a.dinv[i];
-      const double wi = w[i], ui = u[i];
-      const double zi = nv + beta * z[i];
-      const double qi = dv * wi + beta * q[i];  // m = M^-1 w at this row
-      const double si = wi + beta * sv[i];
-      const double pi = ui + beta * p[i];
-      z[i] = zi;
-      q[i] = qi;
-      sv[i] = si;
-      p[i] = pi;
-      x[i] = x[i] + alpha * pi;
-      const double rn = r[i] - alpha * si;
-      const double un = ui - alpha * qi;
-      const double wn = wi - alpha * zi;
-      r[i] = rn;
-      u[i] = un;
-      w[i] = wn;
-      m_out[i] = dv * wn;
-      a0 = fma(rn, un, a0);
-      a1 = fma(wn, un, a1);
-      a2 = fma(rn, rn, a2);
-    };
-    row_products<double, 0>(a, blk, r0, r1, a.val, a.sval, m_in, f);
+    if (mode == PIPE_ITER) {
+      const double *m_in = a.kv[7 + par];
+      double *m_out = a.kv[8 - par];
+      auto f = [&](int i, double nv) {
+        const double dv = a.dinv[i];
+        const double wi = w[i], ui = u[i];
+        const double zi = nv + beta * z[i];
+        const double qi = dv * wi + beta * q[i];  // m = M^-1 w at this row
+        const double si = wi + beta * sv[i];
+        const double pi = ui + beta * p[i];
+        z[i] = zi;
+        q[i] = qi;
+        sv[i] = si;
+        p[i] = pi;
+        x[i] = x[i] + alpha * pi;
+        const double rn = r[i] - alpha * si;
+        const double un = ui - alpha * qi;
+        const double wn = wi - alpha * zi;
+        r[i] = rn;
+        u[i] = un;
+        w[i] = wn;
+        m_out[i] = dv * wn;
+        a0 = fma(rn, un, a0);
+        a1 = fma(wn, un, a1);
+        a2 = fma(rn, rn, a2);
+      };
+      row_products<double, 0>(a, blk, r0, r1, a.val, a.sval, m_in, f);
+    } else if (mode == PIPE_VERIFY) {  // r = b - A x, u = M^-1 r, ||r||^2
+      auto f = [&](int i, double ax) {
+        const double rv = b[i] - ax;
+        r[i] = rv;
+        u[i] = a.dinv[i] * rv;
+        a0 = fma(rv, rv, a0);
+      };
+      row_products<double, 0>(a, blk, r0, r1, a.val, a.sval, x, f);
+    } else {  // PIPE_RESTART: w = A u, the next m, p = s = q = z = 0
+      double *m_next = a.kv[7 + par];
+      auto f = [&](int i, double y) {
+        const double ri = r[i], ui = u[i];
+        w[i] = y;
+        m_next[i] = a.dinv[i] * y;
+        p[i] = 0.0;
+        sv[i] = 0.0;
+        q[i] = 0.0;
+        z[i] = 0.0;
+        a0 = fma(ri, ui, a0);
+        a1 = fma(y, ui, a1);
+        a2 = fma(ri, ri, a2);
+      };
+      row_products<double, 0>(a, blk, r0, r1, a.val, a.sval, u, f);
+    }
     acc[0] = a0;
     acc[1] = a1;
     acc[2] = a2;
   };
   auto fin = [&](int s, double(&tot)[3]) {
     SysState &S = a.st[s];
-    S.iterations += 1;
-    const int st = pipe_top(C, S, tot[0], tot[1], tot[2]);
-    if (st >= 0) deactivate(a, S, st);
+    const int md = S.mode;
+    if (md == PIPE_ITER) {
+      S.iterations += 1;
+      pipe_after_top(a, S, pipe_top(C, S, tot[0], tot[1], tot[2], true));
+    } else if (md == PIPE_VERIFY) {
+      const double tn = sqrt(tot[0]);
+      S.rnorm = tn;
+      if (!isfinite(tn)) deactivate(a, S, GBS_ERR_NAN);
+      else if (tn <= C.rtol * sqrt(S.bb)) deactivate(a, S, GBS_OK);
+      else {
+        S.outer += 1;  // a restart
+        S.mode = PIPE_RESTART;
+      }
+    } else {  // the restarted recurrences' first tests (the true residual just missed)
+      S.first = 1;
+      const int st = pipe_top(C, S, tot[0], tot[1], tot[2], false);
+      if (st >= 0) deactivate(a, S, st);
+      else S.mode = PIPE_ITER;
+    }
   };
   walk<3>(a, a.ta, 0, red, want, work, fin);
 }

@@ -195,6 +195,8 @@ int ensure_solver_workspace(gbs_mat A, bool refined) {
 
 // Loop-trip cap: a safety net only (each trip advances every active system).
 static int64_t max_trips_for(const ksp_opts &o) {
+  if (o.method == GBS_KSP_PIPECG)  // an iteration, a confirmation and a restart at most
+    return 3 * (int64_t)o.maxit + 8;
   return o.precision == GBS_FP32_REFINED
              ? ((int64_t)o.max_outer + 1) * ((int64_t)o.inner_maxit + 3) + 4
              : (int64_t)o.maxit + 4;

@@ -117,3 +117,63 @@ def test_c5_batched_full_size_sampled_systems():
         assert tr <= 1.05e-8, (s, tr)
         assert abs(rs[s]["true_rel_residual"] - tr) <= 1e-3 * tr + 1e-13
     A.close()
+
+
+@pytest.mark.parametrize("method", [B.KSP_TFQMR, B.KSP_BICG])
+def test_c6_nonsymmetric_batch_full_size_sampled_systems(method):
+    """The 1024-system convection-diffusion batch as bench.py --workload nonsym
+    solves it (automatic engine: one CTA per system, two per SM): sampled
+    systems re-assembled and solved by the oracle one by one."""
+    bt = W.convdiff_batch(1024, seed=W.SEED_C6)
+    A = B.Mat.from_coo_batched(bt.nrows, bt.ncoo, t(bt.i), t(bt.j))
+    A.set_values(t(bt.v))
+    x, rs = A.solve_batched(t(bt.b), rtol=1e-8, method=method)
+    assert all(q["status"] == B.OK for q in rs)
+    assert all(q["solver"] == B.SOLVER_CTA for q in rs)
+    xg = x.cpu().numpy()
+    ro, co = bt.row_off, bt.coo_off
+    rng = np.random.default_rng(11)
+    solver = oracle.tfqmr if method == B.KSP_TFQMR else oracle.bicg
+    for s in sorted(set(rng.integers(0, bt.nsys, 6).tolist()) | {0, bt.nsys - 1}):
+        n = int(bt.nrows[s])
+        sl = slice(int(co[s]), int(co[s + 1]))
+        O = oracle.coo_symbolic(n, n, bt.i[sl], bt.j[sl])
+        oracle.coo_numeric(O, bt.v[sl])
+        a0, a1 = int(ro[s]), int(ro[s + 1])
+        bs = bt.b[a0:a1]
+        tr = np.linalg.norm(bs - oracle.spmv(O, xg[a0:a1])) / np.linalg.norm(bs)
+        xo, r = solver(O, bs, rtol=1e-8)
+        assert r["status"] == B.OK
+        assert tr <= 2 * max(1e-8, r["true_rel_residual"]), (s, tr, r)
+        assert abs(rs[s]["true_rel_residual"] - tr) <= 1e-3 * tr + 1e-15
+        slack = 0.25 if method == B.KSP_BICG else 0.05
+        assert abs(rs[s]["iterations"] - r["iterations"]) <= max(5, slack * r["iterations"]), (s, rs[s], r)
+    A.close()
+
+
+@pytest.mark.parametrize("name,make", [
+    ("poisson2d_2048", lambda: W.poisson2d(2048)),
+    ("q1hex_64", lambda: W.q1_hex(64, seed=W.SEED_C2)),
+])
+def test_async_sweep_largest_problems(name, make):
+    """The largest problems of bench.py --workload async, with its right-hand
+    sides, through the pipelined CG and the three-kernel CG: both reach the
+    tolerance in the oracle's recomputed true residual (the pipelined CG
+    after the restarts its confirmation triggers), with comparable counts."""
+    p = make()
+    if name.startswith("poisson2d"):
+        p.b = np.random.default_rng(W.SEED_C7 + 2048).standard_normal(p.nrows)
+    A = B.Mat.from_coo(p.nrows, p.ncols, t(p.i), t(p.j))
+    A.set_values(t(p.v))
+    O = oracle.coo_symbolic(p.nrows, p.ncols, p.i, p.j)
+    oracle.coo_numeric(O, p.v)
+    bn = np.linalg.norm(p.b)
+    xc, rc = A.solve(t(p.b), rtol=1e-8)
+    xp, rp = A.solve(t(p.b), rtol=1e-8, method=B.KSP_PIPECG)
+    assert rc["status"] == rp["status"] == B.OK
+    trc = np.linalg.norm(p.b - oracle.spmv(O, xc.cpu().numpy())) / bn
+    trp = np.linalg.norm(p.b - oracle.spmv(O, xp.cpu().numpy())) / bn
+    assert trc <= 1.05e-8, trc
+    assert trp <= 1.05e-8, trp     # confirmed with b - A x (restarts when it drifted)
+    assert rc["iterations"] <= rp["iterations"] <= 1.2 * rc["iterations"] + 2
+    A.close()

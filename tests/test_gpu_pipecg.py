@@ -78,8 +78,28 @@ def test_pipecg_parity(name, make, rtol):
     assert resid_ok(tr, ro, rtol), (tr, ro)
     assert abs(r["true_rel_residual"] - tr) <= 1e-3 * tr + 1e-15
     assert abs(r["rnorm0"] - ro["rnorm0"]) <= 1e-12 * ro["rnorm0"]
+    assert r["outer_iterations"] == ro["outer_iterations"]   # restarts (none here)
     xc, rc = A.solve(t(p.b), rtol=rtol)                 # the GPU's CG
     assert abs(r["iterations"] - rc["iterations"]) <= 2, (r, rc)
+    A.close()
+
+
+def test_restart_when_the_recursive_residual_drifts():
+    """512 x 512 Laplacian, random rhs: the recursive residual meets rtol
+    before b - A x does; the confirmation restarts the recurrences, as in the
+    oracle, and the solve ends with the true residual within rtol."""
+    m = 512
+    p = W.poisson2d(m)
+    p.b = np.random.default_rng(1007 + m).standard_normal(p.nrows)
+    A, O = single(p)
+    x, r = A.solve(t(p.b), rtol=1e-8, method=B.KSP_PIPECG)
+    xo, ro = oracle.pipecg(O, p.b, rtol=1e-8)
+    assert r["status"] == ro["status"] == B.OK
+    assert r["outer_iterations"] >= 1 and ro["outer_iterations"] >= 1
+    tr = true_rel(O, p.b, x.cpu().numpy())
+    assert tr <= 1.05e-8, tr
+    assert abs(r["true_rel_residual"] - tr) <= 1e-3 * tr
+    assert abs(r["iterations"] - ro["iterations"]) <= max(5, 0.03 * ro["iterations"]), (r, ro)
     A.close()
 
 
