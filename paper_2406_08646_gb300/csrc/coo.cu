@@ -247,19 +247,31 @@ __global__ void __launch_bounds__(RS_T) k_radix_hist(const uint64_t *keys, int64
 // Stable scatter of one tile.  Warp w owns the contiguous items
 // [base + w*SLOTS*32, base + (w+1)*SLOTS*32); it walks them slot by slot, lane
 // order within a slot, which is the input order, so ranks of equal digits
-// follow input order.  vals_in == null means payload = item index.
+// follow input order.  The tile is first reordered by digit in shared memory
+// (stable), then written out by consecutive threads to consecutive addresses
+// of each digit's run, so the stores coalesce instead of scattering single
+// items over 256 runs.  vals_in == null means payload = item index.
+struct RadixShared {
+  uint64_t key[RS_TILE];
+  uint32_t val[RS_TILE];
+  uint32_t whist[RS_WARPS][256];  // per-warp digit counts, then per-warp offsets in the tile
+  uint32_t toff[256];             // the tile's global offset of each digit
+  uint32_t dbase[256];            // first position of each digit in the reordered tile
+};
+
 __global__ void __launch_bounds__(RS_T) k_radix_scatter(const uint64_t *keys_in,
                                                         const uint32_t *vals_in, int64_t n,
                                                         int shift, const uint32_t *offsets,
                                                         int64_t ntiles, uint64_t *keys_out,
                                                         uint32_t *vals_out) {
-  __shared__ uint32_t whist[RS_WARPS][256];
-  __shared__ uint32_t toff[256];
+  extern __shared__ __align__(16) unsigned char smem[];
+  RadixShared &S = *reinterpret_cast<RadixShared *>(smem);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int w = 0; w < RS_WARPS; ++w) whist[w][threadIdx.x] = 0;
-  toff[threadIdx.x] = offsets[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+  for (int w = 0; w < RS_WARPS; ++w) S.whist[w][threadIdx.x] = 0;
+  S.toff[threadIdx.x] = offsets[(int64_t)threadIdx.x * ntiles + blockIdx.x];
   __syncthreads();
-  const int64_t base = (int64_t)blockIdx.x * RS_TILE + (int64_t)warp * RS_SLOTS * 32;
+  const int64_t tile0 = (int64_t)blockIdx.x * RS_TILE;
+  const int64_t base = tile0 + (int64_t)warp * RS_SLOTS * 32;
   const unsigned lt_mask = (1u << lane) - 1u;
   uint64_t key[RS_SLOTS];
   uint32_t val[RS_SLOTS], rank[RS_SLOTS];
@@ -275,32 +287,63 @@ __global__ void __launch_bounds__(RS_T) k_radix_scatter(const uint64_t *keys_in,
     const int64_t idx = base + sl * 32 + lane;
     const uint32_t d = idx < n ? (uint32_t)((key[sl] >> shift) & 255u) : 256u;
     const unsigned peers = __match_any_sync(FULL_MASK, d);
-    const uint32_t before = d < 256u ? whist[warp][d] : 0u;
+    const uint32_t before = d < 256u ? S.whist[warp][d] : 0u;
     rank[sl] = before + (uint32_t)__popc(peers & lt_mask);
     __syncwarp();
-    if (d < 256u && lane == __ffs(peers) - 1) whist[warp][d] = before + __popc(peers);
+    if (d < 256u && lane == __ffs(peers) - 1) S.whist[warp][d] = before + __popc(peers);
     __syncwarp();
   }
   __syncthreads();
-  {  // per digit: exclusive prefix over warps, plus the tile's global offset
+  {  // per digit: exclusive prefix over warps; the digit's total
     const int d = threadIdx.x;
-    uint32_t run = toff[d];
+    uint32_t run = 0;
     for (int w = 0; w < RS_WARPS; ++w) {
-      const uint32_t c = whist[w][d];
-      whist[w][d] = run;
+      const uint32_t c = S.whist[w][d];
+      S.whist[w][d] = run;
       run += c;
+    }
+    S.dbase[d] = run;
+  }
+  __syncthreads();
+  if (warp == 0) {  // exclusive scan of the 256 digit totals (8 per lane)
+    uint32_t t[8], sum = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      t[k] = S.dbase[lane * 8 + k];
+      sum += t[k];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL_MASK, incl, off);
+      if (lane >= off) incl += y;
+    }
+    uint32_t run = incl - sum;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      S.dbase[lane * 8 + k] = run;
+      run += t[k];
     }
   }
   __syncthreads();
 #pragma unroll
-  for (int sl = 0; sl < RS_SLOTS; ++sl) {
+  for (int sl = 0; sl < RS_SLOTS; ++sl) {  // reorder the tile by digit (stable)
     const int64_t idx = base + sl * 32 + lane;
     if (idx < n) {
       const uint32_t d = (uint32_t)((key[sl] >> shift) & 255u);
-      const uint32_t dst = whist[warp][d] + rank[sl];
-      keys_out[dst] = key[sl];
-      vals_out[dst] = val[sl];
+      const uint32_t lp = S.dbase[d] + S.whist[warp][d] + rank[sl];
+      S.key[lp] = key[sl];
+      S.val[lp] = val[sl];
     }
+  }
+  __syncthreads();
+  const int cnt = (int)(n - tile0 < RS_TILE ? n - tile0 : RS_TILE);
+  for (int i = threadIdx.x; i < cnt; i += RS_T) {  // runs of a digit go to consecutive addresses
+    const uint64_t k = S.key[i];
+    const uint32_t d = (uint32_t)((k >> shift) & 255u);
+    const uint32_t dst = S.toff[d] + (uint32_t)i - S.dbase[d];
+    keys_out[dst] = k;
+    vals_out[dst] = S.val[i];
   }
 }
 
@@ -442,7 +485,15 @@ int symbolic(gbs_mat A, const int32_t *i, const int32_t *j, const int64_t *coo_o
       GBS_LAUNCHED(1);
     }
 
-    // 2. stable LSD radix sort
+    // 2. stable LSD radix sort (the scatter stages a tile in ~58 KB of shared memory)
+    {
+      static bool smem_opt_in = false;
+      if (!smem_opt_in) {
+        SYM_CUDA(cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sizeof(RadixShared)));
+        smem_opt_in = true;
+      }
+    }
     const uint64_t maxkey = (uint64_t)A->nrows * (uint64_t)A->ncols;
     int bits = 0;
     while (bits < 64 && (maxkey > 1) && ((maxkey - 1) >> bits) != 0) ++bits;
@@ -464,8 +515,8 @@ int symbolic(gbs_mat A, const int32_t *i, const int32_t *j, const int64_t *coo_o
           cudaFreeAsync(ctmp, s);
           goto cleanup;
         }
-        k_radix_scatter<<<(unsigned)ntiles, RS_T, 0, s>>>(kin, vin, nkept, shift, counts,
-                                                          ntiles, kout, vout);
+        k_radix_scatter<<<(unsigned)ntiles, RS_T, sizeof(RadixShared), s>>>(
+            kin, vin, nkept, shift, counts, ntiles, kout, vout);
         GBS_LAUNCHED(1);
         std::swap(kin, kout);
         std::swap(vin, vout);
