@@ -71,6 +71,27 @@ __device__ __forceinline__ void block_reduce(T (&v)[NV], T *scratch) {
   __syncthreads();
 }
 
+// A hint to bring bytes [p, p + n) into L2: one bulk prefetch, which holds
+// no registers and has no completion to wait for, so a warp can put a whole
+// run of data in flight before its first load of it.  The bulk prefetch
+// wants a 16-byte aligned start and a length in whole 16-byte units: the
+// range is shrunk to the aligned units inside it (and to 64 KB), which
+// keeps every prefetched byte inside [p, p + n).
+__device__ __forceinline__ void prefetch_l2(const void *p, size_t n) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  const uintptr_t s = (a + 15) & ~(uintptr_t)15;
+  uintptr_t e = (a + n) & ~(uintptr_t)15;
+  if (e > s + 65536) e = s + 65536;
+  if (e > s)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(s), "r"((uint32_t)(e - s))
+                 : "memory");
+}
+
+template <typename T>
+__device__ __forceinline__ void prefetch_rows(const T *v, int r0, int r1) {
+  if (r1 > r0) prefetch_l2(v + r0, (size_t)(r1 - r0) * sizeof(T));
+}
+
 // Fused multiply-add, correctly rounded once.
 __device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }

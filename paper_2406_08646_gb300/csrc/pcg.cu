@@ -39,8 +39,9 @@ namespace gbs {
 // ------------------------------------------------------------------ kernels
 
 // Kernels with row products (setup, A, final) on the sliced-ELL layout
-// (L == 0) are held to 32 registers so that 8 CTAs fit per SM: the sliced
-// product is latency-bound and needs every warp slot to keep HBM busy.
+// (L == 0) are held to 32 registers so that four 512-thread CTAs (64 warps)
+// fit per SM: the sliced product is latency-bound and needs every warp slot
+// to keep HBM busy.
 #define GBS_ROWS_BOUNDS(L) __launch_bounds__(PHASE_TPB, (L) == 0 ? SELL_MIN_CTAS : 1)
 
 template <bool REFINED, int L>
