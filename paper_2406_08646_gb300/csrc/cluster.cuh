@@ -31,8 +31,9 @@ namespace cgrp = cooperative_groups;
 constexpr int CLUSTER_MAX = 16;  // CTAs per cluster (16 needs the non-portable opt-in)
 
 struct ClusterShared {
-  double red[4 * CTA_TPB];  // block sums: every thread's values
-  double part[2][4];        // this CTA's sums, two halves used in turn
+  double red[4 * CTA_TPB];         // block sums: every thread's values
+  double lanes[BLOCK_SUMS_EXTRA];  // block sums: lane partials
+  double part[2][4];               // this CTA's sums, two halves used in turn
   double pub[4];            // scalars published by thread 0
   int ipub[4];              // [0]: < 0 keep going; [1]: x = 0 (b = 0)
 };
@@ -45,14 +46,7 @@ struct ClusterShared {
 template <int NV>
 __device__ __forceinline__ void cluster_sum0(double (&v)[NV], ClusterShared &sh, int &half,
                                              const cgrp::cluster_group &cl) {
-  const int nt = blockDim.x;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) sh.red[k * nt + threadIdx.x] = v[k];
-  __syncthreads();
-  if ((threadIdx.x >> 5) == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = block_sum_lanes<double>(sh.red + k * nt, nt);
-  }
+  block_sums<double, NV>(v, sh.red, sh.lanes);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) sh.part[half][k] = v[k];

@@ -29,26 +29,18 @@ constexpr int CTA_TPB = 1024;  // threads of a system's CTA
 // updates the scalars and publishes what the next pass needs in `pub` /
 // `ipub`; one more barrier (cta_publish) and every thread reads them.
 struct CtaShared {
-  double red[4 * CTA_TPB];  // cta_sum0: every thread's values
-  double pub[4];            // scalars published by thread 0
-  int ipub[4];              // [0]: < 0 keep going; [1], [2], [3]: flags
+  double red[4 * CTA_TPB];            // cta_sum0: every thread's values
+  double lanes[BLOCK_SUMS_EXTRA];     // cta_sum0: lane partials
+  double pub[4];                      // scalars published by thread 0
+  int ipub[4];                        // [0]: < 0 keep going; [1], [2], [3]: flags
 };
 
-// Block sums of NV values, valid in warp 0 (thread 0) after one barrier
-// (device_util.cuh's block_reduce without its closing barrier).  Every call
-// is followed by cta_publish before the next call, so warp 0 has read the
-// values before any thread writes new ones.
+// Block sums of NV values, valid in warp 0 (thread 0): device_util.cuh's
+// block_sums, spread over the four sub-partitions' FP64 pipes.
 template <typename T, int NV>
 __device__ __forceinline__ void cta_sum0(T (&v)[NV], CtaShared &sh) {
-  const int nt = blockDim.x;
-  T *s = reinterpret_cast<T *>(sh.red);
-#pragma unroll
-  for (int k = 0; k < NV; ++k) s[k * nt + threadIdx.x] = v[k];
-  __syncthreads();
-  if ((threadIdx.x >> 5) == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = block_sum_lanes<T>(s + k * nt, nt);
-  }
+  static_assert(CTA_TPB % 128 == 0 && CTA_TPB >= 256, "block_sums needs 128 k threads");
+  block_sums<T, NV>(v, reinterpret_cast<T *>(sh.red), reinterpret_cast<T *>(sh.lanes));
 }
 
 // The barrier after thread 0 filled sh.pub / sh.ipub.

@@ -32,43 +32,88 @@ __device__ __forceinline__ T warp_sum(T x) {
   return x;
 }
 
-// Deterministic block reduction of NV values, result in warp 0 (thread 0).
-// Every thread stores its values in `scratch` (NV * blockDim.x values, one
-// row per value); after one barrier, lane l of warp 0 adds the values of
-// threads l, l + 32, l + 64, ... into four running sums taken in turn, which
-// it combines, and a butterfly over warp 0 adds the lanes.  A fixed order, so
-// the result is reproducible bit for bit.  FP64 is slow on this part (a
-// warp-wide FP64 instruction takes 16 clocks of an SM's FP64 pipe), so the
-// reduction uses about nthreads / 32 + 8 warp-wide adds per value instead of
-// a butterfly in every warp.  Ends with __syncthreads (scratch reuse).
-template <typename T>
-__device__ __forceinline__ T block_sum_lanes(const T *s, int nt) {
+// Sums over the 32 lanes of NV <= 4 values at once: at distance 16 (and 8
+// when NV > 2) each lane keeps half of the values, sends the other half to
+// its partner and adds what it receives, so later steps work on fewer values
+// per lane; a butterfly over the remaining distances completes the sums.
+// Value k ends in lane 16 k (NV = 2) or 8 k (NV > 2) and is broadcast from
+// there.  5 or 6 warp-wide adds for the NV values together, against 5 NV
+// for one butterfly per value (an FP64 warp instruction holds a
+// sub-partition's FP64 pipe for 64 clocks on this part).  A fixed order.
+template <typename T, int NV>
+__device__ __forceinline__ void warp_sums(T (&t)[NV]) {
+  static_assert(NV >= 1 && NV <= 4, "warp_sums: 1 to 4 values");
   const int lane = threadIdx.x & 31;
-  T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-  int j = lane;
-  for (; j + 96 < nt; j += 128) {
-    a0 += s[j];
-    a1 += s[j + 32];
-    a2 += s[j + 64];
-    a3 += s[j + 96];
+  if constexpr (NV == 1) {
+    t[0] = warp_sum(t[0]);
+  } else if constexpr (NV == 2) {
+    const bool hi = lane & 16;
+    T u = (hi ? t[1] : t[0]) + __shfl_xor_sync(FULL_MASK, hi ? t[0] : t[1], 16);
+#pragma unroll
+    for (int d = 8; d > 0; d >>= 1) u += __shfl_xor_sync(FULL_MASK, u, d);
+    t[0] = __shfl_sync(FULL_MASK, u, 0);
+    t[1] = __shfl_sync(FULL_MASK, u, 16);
+  } else {
+    const T t3 = NV == 4 ? t[NV - 1] : T(0);
+    const bool h16 = lane & 16, h8 = lane & 8;
+    // lanes < 16 keep values 0, 1; lanes >= 16 keep values 2, 3
+    const T a = (h16 ? t[2] : t[0]) + __shfl_xor_sync(FULL_MASK, h16 ? t[0] : t[2], 16);
+    const T b = (h16 ? t3 : t[1]) + __shfl_xor_sync(FULL_MASK, h16 ? t[1] : t3, 16);
+    // bit 3 clear keeps the first of them, set the second
+    T u = (h8 ? b : a) + __shfl_xor_sync(FULL_MASK, h8 ? a : b, 8);
+#pragma unroll
+    for (int d = 4; d > 0; d >>= 1) u += __shfl_xor_sync(FULL_MASK, u, d);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) t[k] = __shfl_sync(FULL_MASK, u, 8 * k);
   }
-  if (j < nt) a0 += s[j];
-  if (j + 32 < nt) a1 += s[j + 32];
-  if (j + 64 < nt) a2 += s[j + 64];
-  return warp_sum((a0 + a1) + (a2 + a3));
 }
 
+// Deterministic block sums of NV <= 4 values per thread, spread over the
+// SM's four sub-partitions (whose FP64 pipes work in parallel): every thread
+// stores its values (row k of s holds value k of all nt threads); after a
+// barrier, warp 4k + q -- on sub-partition q -- adds quarter q of row k,
+// two values per lane at a time, and leaves 32 lane partials in p; after a
+// second barrier warp 0 adds the four quarters' partials lane by lane and
+// warp_sums adds the lanes.  About nt / 128 + 3 + 6 / NV warp-wide adds per
+// value on the critical path, against nt / 32 + 8 for one warp doing it all.
+// Totals in warp 0.  nt = blockDim.x must be a multiple of 128 and at least
+// 256 (the kernels here run 512 or 1024 threads); s holds NV nt values, p
+// 128 NV.  s is free once the second barrier is passed; p is read by warp 0
+// only, so a later call (whose first barrier warp 0 must reach) cannot
+// overwrite it early.
 template <typename T, int NV>
-__device__ __forceinline__ void block_reduce(T (&v)[NV], T *scratch) {
-  const int nt = blockDim.x;
+__device__ __forceinline__ void block_sums(T (&v)[NV], T *s, T *p) {
+  const int nt = blockDim.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-  for (int k = 0; k < NV; ++k) scratch[k * nt + threadIdx.x] = v[k];
+  for (int k = 0; k < NV; ++k) s[k * nt + threadIdx.x] = v[k];
   __syncthreads();
-  if ((threadIdx.x >> 5) == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = block_sum_lanes<T>(scratch + k * nt, nt);
+  if (w < 4 * NV) {
+    const int len = nt >> 2;
+    const T *q = s + (w >> 2) * nt + (w & 3) * len;
+    T a0 = q[lane], a1 = q[lane + 32];
+    for (int j = lane + 64; j < len; j += 64) {
+      a0 += q[j];
+      a1 += q[j + 32];
+    }
+    p[w * 32 + lane] = a0 + a1;
   }
   __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      const T *r = p + 128 * k + lane;
+      v[k] = (r[0] + r[32]) + (r[64] + r[96]);
+    }
+    warp_sums<T, NV>(v);
+  }
+}
+
+// The phase kernels' block reduction: block_sums with s and p in one
+// scratch array of 4 nt + 512 values.
+constexpr int BLOCK_SUMS_EXTRA = 512;  // p: 128 values per reduced value, up to 4
+template <typename T, int NV>
+__device__ __forceinline__ void block_reduce(T (&v)[NV], T *scratch) {
+  block_sums<T, NV>(v, scratch, scratch + 4 * blockDim.x);
 }
 
 // A hint to bring bytes [p, p + n) into L2: one bulk prefetch, which holds

@@ -38,8 +38,9 @@ enum { M_INNER = 0, M_XUPD = 1, M_START = 2 };
 constexpr int SLOT_STRIDE = 4;  // doubles per reduction slot
 constexpr int PHASE_TPB = 512;  // threads per CTA of every phase kernel
 // Shared scratch of the phase kernels' block reductions (NV <= 4 values per
-// thread, device_util.cuh's block_reduce).
-constexpr int RED_SCRATCH = 4 * PHASE_TPB;
+// thread and the lane partials, device_util.cuh's block_reduce).
+constexpr int RED_SCRATCH = 4 * PHASE_TPB + BLOCK_SUMS_EXTRA;
+static_assert(PHASE_TPB % 128 == 0 && PHASE_TPB >= 256, "block_sums needs 128 k threads");
 constexpr int SELL_MIN_CTAS = 4;  // sliced-ELL kernels: 4 CTAs (2048 threads) per SM
 
 // A table of work blocks: rows [row0[b], row0[b+1]) of system sys[b].
@@ -136,11 +137,16 @@ __device__ __forceinline__ bool trip_live(const PcgArgs &a) {
 
 // CTA 0 books the time since the previous phase kernel started to that
 // phase and marks the start of phase k (kernels of one solve run in order).
+// The two loads go out together and the sum is a fire-and-forget atomic, so
+// the stamp costs CTA 0 one L2 round trip.
 __device__ __forceinline__ void stamp_phase(const PcgArgs &a, int k) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     DevCtl *c = a.ctl;
+    const int lp = c->last_phase;
+    const int64_t st = c->stamp;
     const int64_t t = (int64_t)global_ns();
-    c->phase_ns[c->last_phase] += t - c->stamp;
+    atomicAdd(reinterpret_cast<unsigned long long *>(c->phase_ns + lp),
+              (unsigned long long)(t - st));
     c->stamp = t;
     c->last_phase = k;
   }
@@ -187,21 +193,30 @@ __device__ __forceinline__ void flush(const PcgArgs &a, const BlockTable &t, int
     prev = atomicAdd(a.sys_cnt + s, 1u);
   }
   if (__shfl_sync(FULL_MASK, prev, 0) != (unsigned)(ns - 1)) return;
+  // lane l adds slots l, l + 32, ... (each slot's NV values are adjacent),
+  // then warp_sums adds the lanes
   double tot[NV];
   if (f32) {
+    float x[NV];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      float x = 0.f;
-      for (int i = lane; i < ns; i += 32) x += (float)ldcg(a.part + (base + i) * SLOT_STRIDE + k);
-      tot[k] = (double)warp_sum(x);
+    for (int k = 0; k < NV; ++k) x[k] = 0.f;
+    for (int i = lane; i < ns; i += 32) {
+      const double *sl = a.part + (base + i) * SLOT_STRIDE;
+#pragma unroll
+      for (int k = 0; k < NV; ++k) x[k] += (float)ldcg(sl + k);
     }
+    warp_sums<float, NV>(x);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) tot[k] = (double)x[k];
   } else {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      double x = 0.0;
-      for (int i = lane; i < ns; i += 32) x += ldcg(a.part + (base + i) * SLOT_STRIDE + k);
-      tot[k] = warp_sum(x);
+    for (int k = 0; k < NV; ++k) tot[k] = 0.0;
+    for (int i = lane; i < ns; i += 32) {
+      const double *sl = a.part + (base + i) * SLOT_STRIDE;
+#pragma unroll
+      for (int k = 0; k < NV; ++k) tot[k] += ldcg(sl + k);
     }
+    warp_sums<double, NV>(tot);
   }
   if (lane == 0) {
     a.sys_cnt[s] = 0u;
@@ -225,6 +240,7 @@ __device__ __forceinline__ void walk(const PcgArgs &a, const BlockTable &t, int6
   for (int k = 0; k < NA; ++k) acc[k] = 0.0;
   for (int b = blockIdx.x; b < t.nblocks; b += G) {
     const int s = sys_of(a, t, b);
+    const int r0 = __ldg(t.row0 + b), r1 = __ldg(t.row0 + b + 1);  // issued with want's loads
     if (s != cur_s) {
       if constexpr (NV > 0) {
         if (kind) flush<NV>(a, t, part_off, cur_s, cur_b, acc, red, kind == 2, fin);
@@ -236,7 +252,7 @@ __device__ __forceinline__ void walk(const PcgArgs &a, const BlockTable &t, int6
     }
     if (!kind) continue;
     cur_b = b;
-    work(s, b, __ldg(t.row0 + b), __ldg(t.row0 + b + 1), acc);
+    work(s, b, r0, r1, acc);
   }
   if constexpr (NV > 0) {
     if (kind) flush<NV>(a, t, part_off, cur_s, cur_b, acc, red, kind == 2, fin);
@@ -807,13 +823,13 @@ __device__ __forceinline__ void phase_C(const PcgArgs &a, double *red) {
   walk<0>(a, a.te, a.part_e, red, want, work, fin);
 }
 
-// CTA 0 of phase C: count the trip and set the loop condition.  Every phase
-// that can retire a system (setup, A, B) has completed, so n_active is final
-// for this trip.  The trip cap and the wall-clock limit end the loop with the
+// The last CTA of phase C: count the trip and set the loop condition (not
+// CTA 0, which already stamps the phase timer).  Every phase that can retire
+// a system (setup, A, B) has completed, so n_active is final for this trip.  The trip cap and the wall-clock limit end the loop with the
 // remaining systems still active (reported as GBS_ERR_MAXIT / TIMEOUT).  A
 // trip that did not run (host-stepped loop) passes the stop on.
 __device__ __forceinline__ void loop_control(const PcgArgs &a, bool live) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  if (blockIdx.x != gridDim.x - 1 || threadIdx.x != 0) return;
   const CallArgs &C = *a.call;
   DevCtl *c = a.ctl;
   int go = 0;
