@@ -52,6 +52,7 @@ struct SysState {
   double prev_rn;   // refined: previous outer residual norm
   double r0in;      // refined: inner stopping threshold (target x initial norm)
   double tt;        // ||b - A x||^2 at exit
+  double thr;       // rtol ||b_s||, the convergence threshold (set by the setup)
   double tau, theta, eta;  // TFQMR: quasi-residual recurrence (eta of the last half step)
   double coef;             // TFQMR: theta^2 eta / alpha for the next d update
   int32_t status;

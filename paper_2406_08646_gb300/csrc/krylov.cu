@@ -491,7 +491,7 @@ __device__ __forceinline__ void ns_activate(const PcgArgs &a, SysState &S, int s
 // BiCG's tests before an iteration: NAN, converged, limit, rho = 0.
 __device__ __forceinline__ int bicg_top(const CallArgs &C, const SysState &S) {
   if (!isfinite(S.rnorm)) return GBS_ERR_NAN;
-  if (S.rnorm <= C.rtol * sqrt(S.bb)) return GBS_OK;
+  if (S.rnorm <= S.thr) return GBS_OK;
   if (S.iterations >= C.maxit) return GBS_ERR_MAXIT;
   if (S.rho == 0.0) return GBS_ERR_BREAKDOWN;
   return -1;
@@ -531,6 +531,7 @@ __device__ __forceinline__ void bicg_setup(const PcgArgs &a, double *red) {
     SysState &S = a.st[s];
     memset(&S, 0, sizeof(SysState));
     S.bb = tot[1];
+    S.thr = C.rtol * sqrt(S.bb);
     S.rr = tot[0];
     S.rho = tot[2];
     S.rnorm0 = S.rnorm = sqrt(tot[0]);
@@ -675,13 +676,14 @@ __device__ __forceinline__ void tfq_setup(const PcgArgs &a, double *red) {
     SysState &S = a.st[s];
     memset(&S, 0, sizeof(SysState));
     S.bb = tot[1];
+    S.thr = C.rtol * sqrt(S.bb);
     S.rr = tot[0];
     S.rnorm0 = S.rnorm = sqrt(tot[0]);
     int st = kry_start_status(tot[2], tot[1]);
     if (st == GBS_OK) {
       S.zero_x = 1;
       S.rnorm0 = S.rnorm = 0.0;
-    } else if (st < 0 && S.rnorm0 <= C.rtol * sqrt(S.bb)) {
+    } else if (st < 0 && S.rnorm0 <= S.thr) {
       st = GBS_OK;  // x0 already meets the test
     }
     S.rho = tot[0];  // rt.r0 = ||r0||^2
@@ -761,7 +763,7 @@ __device__ __forceinline__ void tfq_half1(const PcgArgs &a, double *red) {
     S.rnorm = rn;
     S.pend = 1;
     if (!isfinite(rn)) deactivate(a, S, GBS_ERR_NAN);
-    else if (rn <= C.rtol * sqrt(S.bb)) deactivate(a, S, GBS_OK);
+    else if (rn <= S.thr) deactivate(a, S, GBS_OK);
     else S.coef = S.theta * S.theta * S.eta / S.alpha;
   };
   walk<1>(a, a.te, a.part_e, red, want, work, fin);
@@ -802,7 +804,7 @@ __device__ __forceinline__ void tfq_half2(const PcgArgs &a, double *red) {
     const double rn = tfq_half(S, tot[0]);
     S.rnorm = rn;
     if (!isfinite(rn)) deactivate(a, S, GBS_ERR_NAN);
-    else if (rn <= C.rtol * sqrt(S.bb)) deactivate(a, S, GBS_OK);
+    else if (rn <= S.thr) deactivate(a, S, GBS_OK);
     else if (S.iterations >= C.maxit) deactivate(a, S, GBS_ERR_MAXIT);
     else {
       S.beta = tot[1] / S.rho;
@@ -986,7 +988,7 @@ __device__ __forceinline__ int pipe_top(const CallArgs &C, SysState &S, double g
   S.rr = rr;
   S.rnorm = rn;
   if (!isfinite(rn) || !isfinite(gamma) || !isfinite(delta)) return GBS_ERR_NAN;
-  if (may_converge && rn <= C.rtol * sqrt(S.bb)) return GBS_OK;
+  if (may_converge && rn <= S.thr) return GBS_OK;
   if (S.iterations >= C.maxit) return GBS_ERR_MAXIT;
   double beta = 0.0, den = delta;
   if (!S.first) {
@@ -1039,6 +1041,7 @@ __device__ __forceinline__ void pipe_setup(const PcgArgs &a, double *red) {
     SysState &S = a.st[s];
     memset(&S, 0, sizeof(SysState));
     S.bb = tot[1];
+    S.thr = C.rtol * sqrt(S.bb);
     S.rr = tot[0];
     S.rnorm0 = S.rnorm = sqrt(tot[0]);
     S.first = 1;
@@ -1171,7 +1174,7 @@ __device__ __forceinline__ void pipe_iterate(const PcgArgs &a, double *red) {
       const double tn = sqrt(tot[0]);
       S.rnorm = tn;
       if (!isfinite(tn)) deactivate(a, S, GBS_ERR_NAN);
-      else if (tn <= C.rtol * sqrt(S.bb)) deactivate(a, S, GBS_OK);
+      else if (tn <= S.thr) deactivate(a, S, GBS_OK);
       else {
         S.outer += 1;  // a restart
         S.mode = PIPE_RESTART;

@@ -562,6 +562,7 @@ __device__ __forceinline__ void phase_setup(const PcgArgs &a, double *red) {
     const double rho = REFINED ? 0.0 : tot[0];
     memset(&S, 0, sizeof(SysState));
     S.bb = bb;
+    S.thr = C.rtol * sqrt(S.bb);
     S.rho = rho;
     S.rr = rr;
     S.rnorm0 = S.rnorm = sqrt(rr);
@@ -625,7 +626,7 @@ __device__ __forceinline__ void phase_A(const PcgArgs &a, double *red) {
       const double rn = sqrt(tot[0]);
       S.rnorm = rn;
       if (!isfinite(rn)) deactivate(a, S, GBS_ERR_NAN);
-      else if (rn <= C.rtol * sqrt(S.bb)) deactivate(a, S, GBS_OK);
+      else if (rn <= S.thr) deactivate(a, S, GBS_OK);
       else if (S.outer >= C.max_outer) deactivate(a, S, GBS_ERR_MAXIT);
       else {
         S.stall = (rn > 0.5 * S.prev_rn) ? S.stall + 1 : 0;
@@ -690,7 +691,7 @@ __device__ __forceinline__ void phase_B(const PcgArgs &a, double *red) {
       S.rr = rr;
       S.rnorm = rn;
       if (!isfinite(rn) || !isfinite(rho_new)) deactivate(a, S, GBS_ERR_NAN);
-      else if (rn <= C.rtol * sqrt(S.bb)) deactivate(a, S, GBS_OK);
+      else if (rn <= S.thr) deactivate(a, S, GBS_OK);
       else if (S.iterations >= C.maxit) deactivate(a, S, GBS_ERR_MAXIT);
       else {
         S.beta = rho_new / S.rho;
@@ -701,7 +702,7 @@ __device__ __forceinline__ void phase_B(const PcgArgs &a, double *red) {
       const float r0 = sqrtf(rr);
       // inner target: inner_rtol, or the smaller reduction that already
       // brings the outer residual to half of rtol ||b||
-      const double tgt = fmax(C.inner_rtol, 0.5 * C.rtol * sqrt(S.bb) / S.scale);
+      const double tgt = fmax(C.inner_rtol, 0.5 * S.thr / S.scale);
       S.rho = rho;
       S.rr = rr;
       S.r0in = tgt * (double)r0;  // the inner stopping threshold
