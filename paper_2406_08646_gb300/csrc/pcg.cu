@@ -425,9 +425,9 @@ int run_loop_stepped(const LoopPlan &P, PcgArgs a, int grid_a, int grid_e, int64
 // batches with enough systems to fill every SM with CTAs.  A CTA has one
 // SM's FP64 rate (2 FMAs per clock), so its iteration costs about one FP64
 // operation per nonzero plus eight per row; measured on GB300, up to about
-// 40,000 of those it beats a phase-kernel CG iteration (about 17-20 us at
-// small sizes): q1_hex 8^3 (729 rows, 15,625 nonzeros) 16 against 24 us,
-// poisson2d 64^2 (4,096 rows, 20,224 nonzeros) 22 against 17 us.
+// 40,000 of those it beats a phase-kernel CG iteration (about 14-16 us at
+// small sizes): q1_hex 8^3 (729 rows, 15,625 nonzeros) 13.6 against 21.9
+// us, poisson2d 64^2 (4,096 rows, 20,224 nonzeros) 18.4 against 14.0 us.
 constexpr int64_t CTA_AUTO_WORK = 40000;
 
 bool cta_size_rule(gbs_mat A, bool per_system, int systems_per_sm) {
