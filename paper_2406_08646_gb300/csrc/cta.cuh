@@ -23,11 +23,12 @@ namespace gbs {
 constexpr int CTA_TPB = 1024;  // threads of a system's CTA
 
 // Thread 0 owns a system's scalars (FP64 scalar arithmetic is slow on this
-// part: an FP64 warp instruction occupies an SM's FP64 pipe for 16 clocks,
-// so the recurrences run in one thread, not redundantly in 32 warps).  A
-// block sum hands its totals to warp 0 after one barrier (cta_sum0); thread 0
-// updates the scalars and publishes what the next pass needs in `pub` /
-// `ipub`; one more barrier (cta_publish) and every thread reads them.
+// part: an FP64 warp instruction occupies a sub-partition's FP64 pipe for 64
+// clocks, so the recurrences run in one thread, not redundantly in 32
+// warps).  A block sum hands its totals to warp 0 (cta_sum0, two barriers);
+// thread 0 updates the scalars and publishes what the next pass needs in
+// `pub` / `ipub`; one more barrier (cta_publish) and every thread reads
+// them.
 struct CtaShared {
   double red[4 * CTA_TPB];            // cta_sum0: every thread's values
   double lanes[BLOCK_SUMS_EXTRA];     // cta_sum0: lane partials
