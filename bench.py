@@ -555,6 +555,19 @@ def run_suite(args):
     raise SystemExit(f"unknown workload {args.workload}")
 
 
+def max_over_ranks(vals, device):
+    """Each value's maximum over the ranks of the default process group (a
+    replica job takes as long as its slowest rank); unchanged on one rank or
+    without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in vals]
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
 def run_gpu(args, rank: int, world: int):
     import numpy as np
     import torch
@@ -663,13 +676,12 @@ def run_gpu(args, rank: int, world: int):
     med = {k: statistics.median(r[k] for r in rows) for k in rows[0]}
     step_ms = statistics.mean(r["step"] for r in rows)
     solve_s = med["solve_fp64"] / 1e3
-    if world > 1:
-        tt = torch.tensor([solve_s, step_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        solve_s, step_ms = float(tt[0]), float(tt[1])
+    solve_s, step_ms = max_over_ranks([solve_s, step_ms], dev)
 
     # ---- end to end through the C-ABI from pinned host buffers (H2D + D2H in region)
     e2e_s = None if args.no_e2e else e2e_time(p, dev, stream, sp, L, B, o64, check)
+    if e2e_s is not None:
+        e2e_s = max_over_ranks([e2e_s], dev)[0]
 
     r64 = results[-1]["fp64"]
     it = r64["iterations"]
