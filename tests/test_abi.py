@@ -93,3 +93,74 @@ def test_product_path_has_no_cpu_fallback():
         if fn.endswith(".py"):
             src = open(os.path.join(pkg, fn)).read()
             assert "import oracle" not in src and "from oracle" not in src, fn
+
+
+P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+HANDLE_CALLS = {  # every entry point taking a matrix / vector handle: its argument types
+    "mat_set_values_coo": [P, P, I32, P],
+    "mat_mult": [P, P, P, P],
+    "ksp_solve_cg": [P, P, P, P, P, P],
+    "ksp_solve_cg_batched": [P, P, P, P, P, P],
+    "ksp_solve": [P, P, P, P, P, P],
+    "ksp_solve_batched": [P, P, P, P, P, P],
+    "ksp_adjoint": [P, P, P, P, P, P, P, P, P],
+    "ksp_adjoint_batched": [P, P, P, P, P, P, P, P, P],
+    "ksp_get_result": [P, P, I32, P],
+    "ksp_get_phase_ns": [P, P, P],
+    "mat_get_info": [P, P, P, P, P, P],
+    "mat_get_csr": [P, P, P, P, P],
+    "mat_get_coo_maps": [P, P, P, P],
+    "mat_set_plan": [P, I32, I32, I32, I32],
+    "mat_get_plan": [P, P, P, P, P, P],
+    "mat_set_solver": [P, I32],
+    "mat_autotune": [P, P],
+    "vec_set_values_coo": [P, P, I32, P, P],
+    "vec_get_info": [P, P, P, P],
+}
+
+
+def test_every_handle_entry_point_rejects_a_null_handle_without_gpu(lib):
+    """A null handle is an argument error (GBS_ERR_ARG with a message), found
+    before any device call; destroying a null handle is a no-op."""
+    from paper_2406_08646_gb300 import binding as B
+    assert set(HANDLE_CALLS) | {"mat_destroy", "vec_destroy"} == {
+        n for n in declared_functions()
+        if n.startswith(("mat_", "ksp_", "vec_")) and n not in (
+            "mat_create_coo", "mat_create_coo_batched", "vec_create_coo",
+            "ksp_opts_default", "ksp_solve_cg_noalloc")}
+    for name, types in HANDLE_CALLS.items():
+        f = getattr(lib, name)
+        f.argtypes = types
+        f.restype = ctypes.c_int
+        args = [None if t is P else 0 for t in types]
+        assert f(*args) == B.ERR_ARG, name
+        assert B.last_error(), name
+    for name in ("mat_destroy", "vec_destroy"):
+        f = getattr(lib, name)
+        f.argtypes = [P]
+        f.restype = ctypes.c_int
+        assert f(None) == B.OK, name
+
+
+def test_create_size_checks_without_gpu(lib):
+    """Sizes and counts are checked on the host before any device call."""
+    from paper_2406_08646_gb300 import binding as B
+    h = ctypes.c_void_p()
+    f = lib.mat_create_coo
+    f.argtypes = [I64, I64, I64, P, P, P, P]
+    f.restype = ctypes.c_int
+    assert f(4, -1, 0, None, None, None, ctypes.byref(h)) == B.ERR_ARG
+    assert f(4, 4, -5, None, None, None, ctypes.byref(h)) == B.ERR_ARG
+    assert f(1 << 31, 4, 0, None, None, None, ctypes.byref(h)) == B.ERR_ARG  # int32 indices
+    g = lib.mat_create_coo_batched
+    g.argtypes = [I32, P, P, P, P, P, P]
+    g.restype = ctypes.c_int
+    assert g(0, None, None, None, None, None, ctypes.byref(h)) == B.ERR_ARG
+    v = lib.vec_create_coo
+    v.argtypes = [I64, I64, P, P, P]
+    v.restype = ctypes.c_int
+    assert v(-1, 0, None, None, ctypes.byref(h)) == B.ERR_ARG
+    n = lib.ksp_solve_cg_noalloc
+    n.argtypes = [I64, P, P, P, P, P, P, P, P]
+    n.restype = ctypes.c_int
+    assert n(-1, None, None, None, None, None, None, None, None) == B.ERR_ARG
