@@ -8,8 +8,8 @@
 //
 //   memset control words -> setup -> WHILE(cond) { A -> B -> C } -> final
 //
-// The WHILE body repeats while its condition is non-zero; CTA 0 of phase C
-// sets it on the device (cudaGraphSetConditional), so the iteration count is
+// The WHILE body repeats while its condition is non-zero; the last CTA of
+// phase C sets it on the device (cudaGraphSetConditional), so the count is
 // decided where the scalars live and the host never waits inside the loop.
 // The per-call arguments (b, x, tolerances, limits) sit in a small device
 // struct written by a one-thread kernel ahead of the graph, so one
