@@ -40,10 +40,16 @@ def test_max_over_ranks_two_gloo_ranks():
         procs.append(subprocess.Popen([sys.executable, "-c", RANK_SCRIPT], env=env, cwd=ROOT,
                                       stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True))
     outs = []
-    for p in procs:
-        o, e = p.communicate(timeout=120)
-        assert p.returncode == 0, e
-        outs.append(json.loads(o.strip().splitlines()[-1]))
+    try:
+        for p in procs:
+            o, e = p.communicate(timeout=120)
+            assert p.returncode == 0, e
+            outs.append(json.loads(o.strip().splitlines()[-1]))
+    finally:
+        for p in procs:  # a rank left waiting on its peer is ended here
+            if p.poll() is None:
+                p.kill()
+                p.wait()
     for o in outs:
         assert o["world"] == 2
         assert o["out"] == [2.0, 10.0, 0.25], o
