@@ -196,9 +196,10 @@ int ksp_solve_cg(gbs_mat A, const double *b, double *x, const ksp_opts *o,
  * Batched solve of a handle made by mat_create_coo_batched: every system runs
  * its own PCG (own alpha, beta, norms, stopping test ||r_s|| <= rtol ||b_s||)
  * in the same graph launch, each kernel covering all systems; converged
- * systems are frozen and the loop ends when none is left.  b, x: double[sum nrows] in system order.  res_h: HOST array of nsys
- * results or NULL (asynchronous).  Returns the first non-OK system status when
- * res_h is given.
+ * systems are frozen and the loop ends when none is left.  b, x: double[sum
+ * nrows] in system order.  res_h: HOST array of nsys results or NULL
+ * (asynchronous).  Returns the first non-OK system status when res_h is
+ * given.
  */
 int ksp_solve_cg_batched(gbs_mat A, const double *b, double *x, const ksp_opts *o,
                          ksp_result *res_h, void *stream);

@@ -458,7 +458,8 @@ bool use_cta_solver(gbs_mat A, bool per_system) {
 static int cluster_size(gbs_mat A, bool per_system) {
   const int64_t nz = per_system ? A->max_sys_nnz : A->nnz;
   const int64_t rows = per_system ? A->max_sys_rows : A->nrows;
-  int want = (int)std::min<int64_t>(CLUSTER_MAX, std::max<int64_t>(2, (nz + 8 * rows + CTA_AUTO_WORK - 1) / CTA_AUTO_WORK));
+  const int64_t units = (nz + 8 * rows + CTA_AUTO_WORK - 1) / CTA_AUTO_WORK;
+  int want = (int)std::min<int64_t>(CLUSTER_MAX, std::max<int64_t>(2, units));
   static bool opted_in = false;
   if (!opted_in) {
     cudaFuncSetAttribute(k_cluster_pcg, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);

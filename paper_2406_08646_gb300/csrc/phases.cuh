@@ -496,8 +496,10 @@ __device__ __forceinline__ void row_products(const PcgArgs &a, int b, int r0, in
                                              F &f) {
   if constexpr (L == 0) {
     const int s0 = __ldg(a.ta.slice0 + b), s1 = __ldg(a.ta.slice0 + b + 1);
-    if (a.stream_matrix) sell_rows<T, true, GATHER_NC>(a.sptr, a.srow0, a.scol, a.soff, sell_val, x, s0, s1, f);
-    else sell_rows<T, false, GATHER_NC>(a.sptr, a.srow0, a.scol, a.soff, sell_val, x, s0, s1, f);
+    if (a.stream_matrix)
+      sell_rows<T, true, GATHER_NC>(a.sptr, a.srow0, a.scol, a.soff, sell_val, x, s0, s1, f);
+    else
+      sell_rows<T, false, GATHER_NC>(a.sptr, a.srow0, a.scol, a.soff, sell_val, x, s0, s1, f);
   } else
     csr_rows<T, L>(a.row_ptr, a.col, csr_val, x, r0, r1, f);
 }
@@ -826,9 +828,10 @@ __device__ __forceinline__ void phase_C(const PcgArgs &a, double *red) {
 
 // The last CTA of phase C: count the trip and set the loop condition (not
 // CTA 0, which already stamps the phase timer).  Every phase that can retire
-// a system (setup, A, B) has completed, so n_active is final for this trip.  The trip cap and the wall-clock limit end the loop with the
-// remaining systems still active (reported as GBS_ERR_MAXIT / TIMEOUT).  A
-// trip that did not run (host-stepped loop) passes the stop on.
+// a system (setup, A, B) has completed, so n_active is final for this trip.
+// The trip cap and the wall-clock limit end the loop with the remaining
+// systems still active (reported as GBS_ERR_MAXIT / TIMEOUT).  A trip that
+// did not run (host-stepped loop) passes the stop on.
 __device__ __forceinline__ void loop_control(const PcgArgs &a, bool live) {
   if (blockIdx.x != gridDim.x - 1 || threadIdx.x != 0) return;
   const CallArgs &C = *a.call;
