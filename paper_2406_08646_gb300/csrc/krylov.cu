@@ -735,7 +735,6 @@ __device__ __forceinline__ void tfq_v(const PcgArgs &a, double *red) {
 // Half step 1: y2 = y1 - alpha v, t = D^-1 y2, w -= alpha B y1,
 // d = y1 + coef d; ||w||^2; fin: its scalars and tests.  Table E.
 __device__ __forceinline__ void tfq_half1(const PcgArgs &a, double *red) {
-  const CallArgs &C = *a.call;
   const double *y1 = a.kv[1], *vv = a.kv[4], *by1 = a.kv[5];
   double *w = a.kv[0], *y2 = a.kv[2], *d = a.kv[7], *t = a.kv[8];
   NsView v{};

@@ -270,8 +270,7 @@ PcgArgs make_args(gbs_mat A, bool per_system, bool refined) {
 }
 
 static cudaKernelNodeParams kernel_node(void (*k)(PcgArgs), int grid, void **args) {
-  cudaKernelNodeParams p;
-  memset(&p, 0, sizeof(p));
+  cudaKernelNodeParams p = {};
   p.func = (void *)k;
   p.gridDim = dim3((unsigned)std::max(grid, 1));
   p.blockDim = dim3(PHASE_TPB);
