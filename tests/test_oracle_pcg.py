@@ -263,3 +263,32 @@ def test_batched_each_system_matches_dense():
             assert np.linalg.norm(Ds @ x[sl] - bt.b[sl]) <= 1.01e-10 * np.linalg.norm(bt.b[sl])
             xs = np.linalg.solve(Ds, bt.b[sl])
             assert np.linalg.norm(x[sl] - xs) <= np.linalg.cond(Ds) * 2e-10 * np.linalg.norm(xs)
+
+
+def test_batched_degenerate_systems_closed_forms():
+    """A batch holding a 2 x 2 SPD block, an empty system, a 1 x 1 system and a
+    system with b = 0: CG's finite termination (at most n iterations, here 2
+    and 1), x = b / a for the 1 x 1 block (Jacobi-PCG takes alpha = 1 there),
+    x = 0 with no iteration for b = 0, and nothing to do for the empty one --
+    in FP64 and in the refined form."""
+    blocks = [np.array([[4.0, 1.0], [1.0, 3.0]]), np.zeros((0, 0)), np.array([[2.5]]),
+              np.array([[2.0, -1.0, 0.0], [-1.0, 2.0, -1.0], [0.0, -1.0, 2.0]])]
+    N = sum(B_.shape[0] for B_ in blocks)
+    D = np.zeros((N, N))
+    off = [0]
+    for B_ in blocks:
+        o, n = off[-1], B_.shape[0]
+        D[o:o + n, o:o + n] = B_
+        off.append(o + n)
+    A = from_dense(D)
+    b = np.array([1.0, 2.0, 5.0, 0.0, 0.0, 0.0])
+    for prec in (0, 1):
+        x, rs = oracle.pcg_batched(A, np.array(off), b, rtol=1e-12, precision=prec)
+        assert [r["status"] for r in rs] == [oracle.OK] * 4
+        assert rs[1]["iterations"] == 0 and rs[3]["iterations"] == 0
+        assert not np.any(x[3:])                                   # b = 0: x = 0 exactly
+        xs = np.linalg.solve(blocks[0], b[:2])
+        assert np.linalg.norm(x[:2] - xs) <= 1e-12 * np.linalg.norm(xs) * 10
+        assert abs(x[2] - 5.0 / 2.5) <= 4 * np.spacing(2.0)
+        if prec == 0:
+            assert rs[0]["iterations"] == 2 and rs[2]["iterations"] == 1
