@@ -108,3 +108,37 @@ def test_error_statuses():
         x, r = solver(A, np.zeros(p.nrows))
         assert r["status"] == oracle.OK and r["iterations"] == 0 and not x.any()
         assert solver(A, p.b, rtol=1e-14, maxit=2)[1]["status"] == oracle.ERR_MAXIT
+
+
+@pytest.mark.parametrize("method", ["bicg", "tfqmr"])
+def test_batched_degenerate_systems(method):
+    """A batch holding a 2 x 2 nonsymmetric block, an empty system, a 1 x 1
+    system and a system with b = 0: the 2 x 2 and 1 x 1 solves reach the dense
+    solution within BiCG's n-step finite termination (TFQMR: two half steps
+    per BiCG step, plus its closing one), x = 0 with no iteration where b = 0,
+    and nothing to do for the empty system."""
+    blocks = [np.array([[4.0, 1.5], [-0.5, 3.0]]), np.zeros((0, 0)), np.array([[2.5]]),
+              np.array([[2.0, -1.3, 0.0], [-0.7, 2.0, -1.0], [0.0, -1.0, 2.0]])]
+    N = sum(B_.shape[0] for B_ in blocks)
+    D = np.zeros((N, N))
+    off = [0]
+    for B_ in blocks:
+        o, n = off[-1], B_.shape[0]
+        D[o:o + n, o:o + n] = B_
+        off.append(o + n)
+    i, j = np.nonzero(D)
+    A = oracle.coo_symbolic(N, N, i.astype(np.int32), j.astype(np.int32))
+    oracle.coo_numeric(A, D[i, j])
+    b = np.array([1.0, 2.0, 5.0, 0.0, 0.0, 0.0])
+    m = oracle.BICG if method == "bicg" else oracle.TFQMR
+    x, rs = oracle.krylov_batched(A, np.array(off), b, m, rtol=1e-12)
+    assert [r["status"] for r in rs] == [oracle.OK] * 4
+    assert rs[1]["iterations"] == 0 and rs[3]["iterations"] == 0
+    assert not np.any(x[3:])
+    xs = np.linalg.solve(blocks[0], b[:2])
+    assert np.linalg.norm(x[:2] - xs) <= 1e-11 * np.linalg.norm(xs)
+    assert abs(x[2] - 2.0) <= 4 * np.spacing(2.0)
+    steps = [2, 0, 1, 0]
+    for r, n in zip(rs, steps):
+        limit = n if method == "bicg" else 2 * n + (n > 0)
+        assert r["iterations"] <= limit, (method, r, n)
