@@ -201,3 +201,29 @@ def test_restart_reinitialises_the_recurrences():
     assert nr(v["w"] - S @ v["u"]) <= 1e-4 * nr(S @ v["u"])
     assert nr(v["s"] - S @ v["p"]) <= 1e-4 * nr(S @ v["p"])
     assert nr(v["q"] - dinv * v["s"]) <= 1e-4 * nr(dinv * v["s"])
+
+
+def test_batched_degenerate_systems():
+    """A batch holding a 2 x 2 SPD block, an empty system, a 1 x 1 system and a
+    system with b = 0: CG's finite termination carries over to the pipelined
+    recurrences (2 and 1 iterations), x = b / a for the 1 x 1 block, x = 0
+    with no iteration where b = 0, nothing to do for the empty system."""
+    blocks = [np.array([[4.0, 1.0], [1.0, 3.0]]), np.zeros((0, 0)), np.array([[2.5]]),
+              np.array([[2.0, -1.0, 0.0], [-1.0, 2.0, -1.0], [0.0, -1.0, 2.0]])]
+    N = sum(B_.shape[0] for B_ in blocks)
+    D = np.zeros((N, N))
+    off = [0]
+    for B_ in blocks:
+        o, n = off[-1], B_.shape[0]
+        D[o:o + n, o:o + n] = B_
+        off.append(o + n)
+    A = from_dense(D)
+    b = np.array([1.0, 2.0, 5.0, 0.0, 0.0, 0.0])
+    x, rs = oracle.krylov_batched(A, np.array(off), b, oracle.PIPECG, rtol=1e-12)
+    assert [r["status"] for r in rs] == [oracle.OK] * 4
+    assert [r["iterations"] for r in rs] == [2, 0, 1, 0]
+    assert all(r["outer_iterations"] == 0 for r in rs)          # no restart needed
+    assert not np.any(x[3:])
+    xs = np.linalg.solve(blocks[0], b[:2])
+    assert np.linalg.norm(x[:2] - xs) <= 1e-12 * np.linalg.norm(xs) * 10
+    assert abs(x[2] - 2.0) <= 4 * np.spacing(2.0)
