@@ -164,3 +164,20 @@ def test_create_size_checks_without_gpu(lib):
     n.argtypes = [I64, P, P, P, P, P, P, P, P]
     n.restype = ctypes.c_int
     assert n(-1, None, None, None, None, None, None, None, None) == B.ERR_ARG
+
+
+def test_binding_rejects_host_tensors_and_fills_options_without_gpu():
+    """The binding passes only CUDA tensors to the library (a host tensor is
+    refused before any call: there is no CPU path), and make_opts fills the
+    header's struct field by field."""
+    import torch
+    from paper_2406_08646_gb300 import binding as B
+    with pytest.raises(ValueError):
+        B._dev(torch.zeros(3, dtype=torch.float64), torch.float64, 3, "b")
+    assert B._dev(None, torch.float64) is None
+    o = B.make_opts(rtol=1e-10, maxit=77, precision=B.FP32_REFINED, inner_rtol=1e-3,
+                    max_outer=5, inner_maxit=9, timeout_ns=123, nonzero_guess=True,
+                    host_loop=True, method=B.KSP_TFQMR)
+    assert (o.rtol, o.maxit, o.precision, o.inner_rtol, o.max_outer, o.inner_maxit,
+            o.timeout_ns, o.nonzero_guess, o.host_loop, o.method) == (
+        1e-10, 77, B.FP32_REFINED, 1e-3, 5, 9, 123, 1, 1, B.KSP_TFQMR)
