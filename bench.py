@@ -115,6 +115,37 @@ def pcg_alg_bytes(n: int, nnz: int, iterations: int) -> float:
     return iterations * it + 40.0 * n + 12.0 * nnz + 4.0 * (n + 1) + 16.0 * n
 
 
+def pcg_fp64_ops(n: int, nnz: int, iterations: int) -> float:
+    """FP64 pipe instructions (FMA, multiply or add, one slot each, per lane)
+    of one FP64 PCG launch on the phase kernels: per iteration one FMA per
+    stored nonzero and one per row for q = A p and p.q, five per row in the
+    update (r, z, x, r.z, r.r) and one in the direction (p); the setup and the
+    closing residual add about nnz + 7 n.  Reductions are not counted."""
+    return iterations * (nnz + 7.0 * n) + nnz + 7.0 * n
+
+
+def fp64_peak_gops(clk: dict) -> float:
+    """The FP64 pipe's peak in G instructions (per lane) per second: 2 per
+    clock per SM at the SM clock sampled during the run."""
+    import torch
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0
+    return 2.0 * nsm * mhz * 1e6 / 1e9
+
+
+def solve_fp64_pipe(n: int, nnz: int, iterations: int, seconds: float, clk: dict):
+    """The whole FP64 solve against the FP64 pipe (its co-bound with HBM on
+    this part), or None if it cannot be computed."""
+    try:
+        peak = fp64_peak_gops(clk)
+        got = pcg_fp64_ops(n, nnz, iterations) / seconds / 1e9
+        return {"achieved": got, "peak": peak, "unit": "G FP64 op/s", "frac": got / peak,
+                "what": "FP64 instructions of the solve (bench.pcg_fp64_ops: nnz + 7 n per "
+                        "iteration) over its event time, against 2 per SM per clock"}
+    except Exception:
+        return None
+
+
 def fp64_pipe(nnz: int, seconds: float, clk: dict) -> dict:
     """The SpMV's other bound: one FP64 FMA per stored nonzero against the FP64
     pipe's peak, 2 FMAs per clock per SM (GB300's FP64 rate, 1.25 TFLOP/s
@@ -741,6 +772,7 @@ def run_gpu(args, rank: int, world: int):
                                "achieved": solve_gbs, "peak": hbm, "unit": "GB/s",
                                "frac": solve_gbs / hbm,
                                "alg_bytes": pcg_alg_bytes(n, nnz, it)},
+            "solve_fp64_pipe": solve_fp64_pipe(n, nnz, it, solve_s, clk),
             "solve_phases": phases,
             "refined_vs_fp64": med["solve_fp32_refined"] / med["solve_fp64"],
             "adjoint_vs_fp64": med["adjoint"] / med["solve_fp64"],

@@ -67,3 +67,4 @@ def test_reference_arm_runs_on_rank_zero_only():
         gpus, steps, warmup = 2, 1, 0
     # rank 1 of 2 returns at once: no oracle work, nothing printed
     assert bench.run_reference(Args(), 1, 2) == 0
+
