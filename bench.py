@@ -33,8 +33,8 @@ prints its own JSON line; the default is the Q1 benchmark above):
       into 912,673 nodes): symbolic and numeric stage times, numeric GB/s
   async  time per solve against NNZ (Sec. 6.2's comparison, 2D 5-point, 3D
       7-point and 3D 27-point problems, 5e3 to 2.7e7 nonzeros): the three-kernel
-      CG loop, the one-kernel pipelined CG, the per-CTA CG (up to 2M
-      nonzeros) and TFQMR, all device-driven
+      CG loop, the one-kernel pipelined CG, the per-CTA and cluster CG (up to
+      2M nonzeros) and TFQMR, all device-driven
   nonsym  batched TFQMR and BiCG (Jacobi) on 16, 64, 256 and 1024 independent
       2D convection-diffusion systems (1k-50k rows each, Peclet 1-100): solves
       per second of the batched solve on the per-CTA solver and on the phase
