@@ -3,7 +3,9 @@
 
 One step is one pass of the whole hot path over the Q1 hexahedral FE Poisson
 workload (96^3 elements, 912,673 rows, 56,623,104 COO entries, 24,137,569
-nonzeros), inputs resident in HBM:
+nonzeros), inputs (the element coefficients kappa and b) resident in HBM:
+  q1_hex_element_coo / q1_hex_element_values (the COO triples generated on
+  the device from kappa, the user Jacobian kernel pattern),
   mat_create_coo (symbolic COO -> CSR on the device), mat_set_values_coo
   (duplicate-summing numeric stage + Jacobi), FP64 fused PCG to rtol 1e-8,
   100 SpMVs, FP32-inner / FP64-refined PCG to rtol 1e-8, adjoint solve plus
@@ -158,6 +160,19 @@ def fp64_pipe(nnz: int, seconds: float, clk: dict) -> dict:
     return {"achieved": got, "peak": peak, "unit": "G FMA/s", "frac": got / peak,
             "what": "the row product's FP64 FMAs (one per nonzero) over the FP64 pipe's "
                     "peak at the sampled SM clock"}
+
+
+def s0_rows(med: dict, ne: int, hbm: float) -> dict:
+    """The device-side COO generation of the step against HBM: the values
+    kernel reads kappa (8 B per element) and writes 64 doubles per element;
+    the index kernel writes 64 (i, j) int32 pairs per element."""
+    E = float(ne) ** 3
+    out = {}
+    for key, alg in (("gen_values", 8.0 * E + 512.0 * E), ("gen_indices", 512.0 * E)):
+        s = med[key] / 1e3
+        out[key] = {"us": s * 1e6, "alg_bytes": alg, "gbs": alg / s / 1e9,
+                    "frac": alg / s / 1e9 / hbm}
+    return out
 
 
 def spmv_alg_bytes(n: int, nnz: int) -> float:
@@ -616,9 +631,12 @@ def run_gpu(args, rank: int, world: int):
     p = W.q1_hex(args.ne, seed=W.SEED_C2)
     rng = np.random.default_rng(77)
     xt_h = rng.standard_normal(p.nrows)
-    i_d = torch.from_numpy(p.i).to(dev)
-    j_d = torch.from_numpy(p.j).to(dev)
-    v_d = torch.from_numpy(p.v).to(dev)
+    # the step's inputs are the element coefficients and b; the COO triples
+    # are generated on the device each step (S0), then assembled
+    kappa_d = torch.from_numpy(p.extra["kappa"]).to(dev)
+    i_d = torch.empty(p.ncoo, dtype=torch.int32, device=dev)
+    j_d = torch.empty(p.ncoo, dtype=torch.int32, device=dev)
+    v_d = torch.empty(p.ncoo, dtype=torch.float64, device=dev)
     b_d = torch.from_numpy(p.b).to(dev)
     xt_d = torch.from_numpy(xt_h).to(dev)
     n, ncoo = p.nrows, p.ncoo
@@ -642,7 +660,14 @@ def run_gpu(args, rank: int, world: int):
 
     def step(record):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
+        eg = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         res = {}
+        eg[0].record(stream)
+        check(L.q1_hex_element_coo(args.ne, B._dev(i_d, torch.int32), B._dev(j_d, torch.int32),
+                                   sp))
+        eg[1].record(stream)
+        check(L.q1_hex_element_values(args.ne, B._dev(kappa_d, torch.float64),
+                                      B._dev(v_d, torch.float64), sp))
         ev[0].record(stream)
         A = B.mat_create_coo(n, n, i_d, j_d, stream)
         ev[1].record(stream)
@@ -674,11 +699,12 @@ def run_gpu(args, rank: int, world: int):
         plan = B.mat_get_plan(A)
         B.mat_destroy(A)
         stream.synchronize()
-        t = {"create": ev[0].elapsed_time(ev[1]), "set_values": ev[1].elapsed_time(ev[2]),
+        t = {"gen_indices": eg[0].elapsed_time(eg[1]), "gen_values": eg[1].elapsed_time(ev[0]),
+             "create": ev[0].elapsed_time(ev[1]), "set_values": ev[1].elapsed_time(ev[2]),
              "solve_fp64": ev[2].elapsed_time(ev[3]),
              "spmv_x100": ev[4].elapsed_time(ev[5]),
              "solve_fp32_refined": ev[5].elapsed_time(ev[6]),
-             "adjoint": ev7.elapsed_time(ev[7]), "step": ev[0].elapsed_time(ev[7])}
+             "adjoint": ev7.elapsed_time(ev[7]), "step": eg[0].elapsed_time(ev[7])}
         return t, res, nnz, plan
 
     def barrier():
@@ -710,9 +736,10 @@ def run_gpu(args, rank: int, world: int):
     solve_s, step_ms = max_over_ranks([solve_s, step_ms], dev)
 
     # ---- end to end through the C-ABI from pinned host buffers (H2D + D2H in region)
-    e2e_s = None if args.no_e2e else e2e_time(p, dev, stream, sp, L, B, o64, check)
-    if e2e_s is not None:
-        e2e_s = max_over_ranks([e2e_s], dev)[0]
+    e2e = None if args.no_e2e else e2e_time(p, dev, stream, sp, L, B, o64, check)
+    if e2e is not None:
+        e2e["kappa"]["value"], e2e["host_coo"]["value"] = max_over_ranks(
+            [e2e["kappa"]["value"], e2e["host_coo"]["value"]], dev)
 
     r64 = results[-1]["fp64"]
     it = r64["iterations"]
@@ -759,6 +786,7 @@ def run_gpu(args, rank: int, world: int):
             "status": {k: last[k]["status"] for k in ("fp64", "fp32_refined", "adjoint")},
             "spmv": {"gbs": spmv_gbs, "frac": spmv_gbs / hbm, "us": spmv_s * 1e6,
                      "alg_bytes": spmv_alg_bytes(n, nnz)},
+            "generate": s0_rows(med, args.ne, hbm),
             "roofline": {"kernel": "k_spmv_sell (MatMult, sliced-ELL FP64 row product)",
                          "bound": "hbm", "achieved": spmv_gbs, "peak": hbm, "unit": "GB/s",
                          "frac": spmv_gbs / hbm, "peak_kind": f"{peak_kind} (copy, burst)",
@@ -776,10 +804,15 @@ def run_gpu(args, rank: int, world: int):
             "solve_phases": phases,
             "refined_vs_fp64": med["solve_fp32_refined"] / med["solve_fp64"],
             "adjoint_vs_fp64": med["adjoint"] / med["solve_fp64"],
-            "e2e": None if e2e_s is None else {"value": e2e_s, "unit": "s",
-                    "h2d_bytes_per_step": int(ncoo * 16 + n * 8),
-                    "d2h_bytes_per_step": int(n * 8),
-                    "what": "pinned host COO + b -> device, assemble, FP64 solve, x -> host"},
+            "e2e": None if e2e is None else {
+                "value": e2e["kappa"]["value"], "unit": "s",
+                "h2d_bytes_per_step": e2e["kappa"]["h2d_bytes"],
+                "d2h_bytes_per_step": e2e["kappa"]["d2h_bytes"],
+                "stages_ms": e2e["kappa"]["stages_ms"],
+                "what": "pinned host kappa + b -> device, COO triples generated on the "
+                        "device, assemble, FP64 solve, x -> host",
+                "host_coo": dict(e2e["host_coo"], what="pinned host COO (i, j, v) + b -> "
+                                 "device, assemble, FP64 solve, x -> host")},
             "gpu_launches": launches,
             "clocks": clk,
             "wall_s": wall,
@@ -790,46 +823,73 @@ def run_gpu(args, rank: int, world: int):
 
 
 def e2e_time(p, dev, stream, sp, L, B, o64, check):
-    """Median over 2 timed reps (after 1 untimed) of: pinned host COO (i, j, v)
-    and b copied to the device, mat_create_coo, mat_set_values_coo, FP64
-    ksp_solve_cg, x copied back to pinned host memory -- all on one stream,
-    timed with CUDA events."""
+    """End to end through the C-ABI from pinned host memory, two ways, each the
+    median over 2 timed reps (after 1 untimed), all on one stream, CUDA events
+    between the stages:
+      kappa:    the element coefficients and b copied to the device, the COO
+                triples generated there (q1_hex_element_coo / _values), then
+                mat_create_coo, mat_set_values_coo, FP64 ksp_solve_cg, x copied
+                back to the host;
+      host_coo: the COO triples (i, j, v) and b copied to the device, then the
+                same assembly, solve and copy back.
+    Returns {name: {"value": s, "stages_ms": {...}, "h2d_bytes": B, "d2h_bytes": B}}."""
     import torch
-    n = p.nrows
-    i_h = torch.from_numpy(p.i).pin_memory()
-    j_h = torch.from_numpy(p.j).pin_memory()
-    v_h = torch.from_numpy(p.v).pin_memory()
-    b_h = torch.from_numpy(p.b).pin_memory()
+    n, ne = p.nrows, p.extra["ne"]
+    kap = p.extra["kappa"]
+    pin = lambda a: torch.from_numpy(a).pin_memory()
+    i_h, j_h, v_h, b_h, k_h = pin(p.i), pin(p.j), pin(p.v), pin(p.b), pin(kap)
     x_h = torch.empty(n, dtype=torch.float64).pin_memory()
     i2 = torch.empty(p.ncoo, dtype=torch.int32, device=dev)
     j2 = torch.empty(p.ncoo, dtype=torch.int32, device=dev)
     v2 = torch.empty(p.ncoo, dtype=torch.float64, device=dev)
     b2 = torch.empty(n, dtype=torch.float64, device=dev)
+    k2 = torch.empty(kap.shape[0], dtype=torch.float64, device=dev)
     x2 = torch.empty(n, dtype=torch.float64, device=dev)
-    out = []
-    for rep in range(3):
+    names = ("h2d", "generate", "create", "set_values", "solve", "d2h")
+
+    def run(from_kappa):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
         torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        i2.copy_(i_h, non_blocking=True)
-        j2.copy_(j_h, non_blocking=True)
-        v2.copy_(v_h, non_blocking=True)
+        ev[0].record(stream)
+        if from_kappa:
+            k2.copy_(k_h, non_blocking=True)
+        else:
+            i2.copy_(i_h, non_blocking=True)
+            j2.copy_(j_h, non_blocking=True)
+            v2.copy_(v_h, non_blocking=True)
         b2.copy_(b_h, non_blocking=True)
+        ev[1].record(stream)
+        if from_kappa:
+            check(L.q1_hex_element_coo(ne, B._dev(i2, torch.int32), B._dev(j2, torch.int32), sp))
+            check(L.q1_hex_element_values(ne, B._dev(k2, torch.float64),
+                                          B._dev(v2, torch.float64), sp))
+        ev[2].record(stream)
         A = B.mat_create_coo(n, n, i2, j2, stream)
+        ev[3].record(stream)
         check(L.mat_set_values_coo(A, B._dev(v2, torch.float64), B.INSERT, sp))
+        ev[4].record(stream)
         check(L.ksp_solve_cg(A, B._dev(b2, torch.float64), B._dev(x2, torch.float64),
                              B.ctypes.byref(o64), None, sp))
+        ev[5].record(stream)
         x_h.copy_(x2, non_blocking=True)
-        e1.record(stream)
-        e1.synchronize()
+        ev[6].record(stream)
+        ev[6].synchronize()
         r = B.ksp_get_result(A, 1, stream)[0]
         B.mat_destroy(A)
         if r["status"] != B.OK:
             raise B.GbsError(r["status"], "end-to-end solve failed")
-        if rep > 0:
-            out.append(e0.elapsed_time(e1) / 1e3)
-    return statistics.median(out)
+        st = {nm: ev[k].elapsed_time(ev[k + 1]) for k, nm in enumerate(names)}
+        return ev[0].elapsed_time(ev[6]) / 1e3, st
+
+    out = {}
+    for name, from_kappa in (("kappa", True), ("host_coo", False)):
+        reps = [run(from_kappa) for _ in range(3)][1:]
+        tot = statistics.median(t for t, _ in reps)
+        stages = {nm: statistics.median(st[nm] for _, st in reps) for nm in names}
+        h2d = (kap.nbytes if from_kappa else p.i.nbytes + p.j.nbytes + p.v.nbytes) + p.b.nbytes
+        out[name] = {"value": tot, "stages_ms": stages, "h2d_bytes": int(h2d),
+                     "d2h_bytes": int(n * 8)}
+    return out
 
 
 def main():

@@ -284,13 +284,18 @@ int ksp_adjoint_batched(gbs_mat A, const double *x, const double *dLdx, double *
  * GBS_ERR_ARG without touching the GPU.  It calls no cudaMalloc, cudaFree or
  * other allocating routine, and builds no CUDA graph: the host launches the
  * iterations in chunks of 16 and reads a 4-byte stop flag after each chunk,
- * so the call synchronises `stream` once per chunk.  Every call shares that array, which keeps the
- * last call's contents: calls that overlap on the GPU (other streams or host
- * threads) race, so the caller must serialise them.  The first call on a
- * device looks up the array's device address; make that first call before
- * any stream capture.  o: NULL (defaults) or precision GBS_FP64.  res (host):
- * non-NULL synchronises and fills it; NULL leaves the call asynchronous (its
- * result is then not retrievable).
+ * so the call synchronises `stream` once per chunk and once at the end, and
+ * always returns the solve's status (GBS_ERR_NOT_SPD for a missing or
+ * non-positive diagonal, GBS_ERR_MAXIT, ... as ksp_solve_cg).  Every call
+ * shares that array, which keeps the last call's contents: calls that overlap
+ * on the GPU (other streams or host threads) race, so the caller must
+ * serialise them.  The first call on a device looks up the array's device
+ * address and keeps it for the life of the process; make that first call
+ * before any stream capture, and do not call this entry point on a device
+ * after a cudaDeviceReset of it (the kept address is then stale).  o: NULL
+ * (defaults) or method GBS_KSP_CG with precision GBS_FP64 (GBS_ERR_ARG
+ * otherwise; host_loop is ignored, the loop is always host-stepped).  res
+ * (host): NULL or the result to fill.
  */
 int ksp_solve_cg_noalloc(int64_t n, const int32_t *row_ptr, const int32_t *col,
                          const double *val, const double *b, double *x,
@@ -401,6 +406,37 @@ int vec_create_coo(int64_t n, int64_t ncoo, const int32_t *i, void *stream, gbs_
 int vec_set_values_coo(gbs_vec V, const double *v, int mode, double *y, void *stream);
 int vec_get_info(gbs_vec V, int64_t *n, int64_t *nentries, int64_t *ncoo);
 int vec_destroy(gbs_vec V);
+
+/*
+ * Device-side COO generation for the model problems: Sec. 3's pattern of a
+ * user Jacobian kernel that fills the COO values on the device and hands
+ * them to MatSetValuesCOO, with Sec. 5's per-element offsets (64 e for a Q1
+ * hexahedron, 4 e for a graph edge).  All pointers are device pointers; the
+ * calls are asynchronous on `stream`; errors: GBS_ERR_ARG (sizes, null or
+ * misaligned pointers), GBS_ERR_CUDA.
+ *
+ * q1_hex_element_coo: the COO indices of ne^3 Q1 hexahedra of the unit cube
+ *   (ne >= 1, 64 ne^3 < 2^31): entry 64 e + 8 a + b is (g(e, a), g(e, b)),
+ *   node g = ix + (ne+1) (iy + (ne+1) iz), element e = ex + ne (ey + ne ez),
+ *   local node a = ax + 2 ay + 4 az.  i, j: int32[64 ne^3], 16-byte aligned.
+ * q1_hex_element_values: the matching values v[64 e + 8 a + b] =
+ *   (kappa[e] h) K_ref[a][b], h = 1/ne, K_ref the Q1 reference stiffness
+ *   (1/3 on the diagonal, 0 for nodes differing in one coordinate, -1/12 in
+ *   two or three), each product rounded once after kappa[e] h; Dirichlet on
+ *   the outer faces keeping every row: an off-diagonal entry touching a
+ *   boundary node is 0 and a boundary node's diagonal entry is 1/m (m = 1,
+ *   2, 4 elements at a corner, edge, face node), so its assembled diagonal
+ *   is 1.  kappa: double[ne^3] (8-byte aligned); v: double[64 ne^3]
+ *   (16-byte aligned).
+ * edge_coo_values: the values of a variable-coefficient graph Laplacian
+ *   given as 4 COO entries per edge, (a, a), (b, b), (a, b), (b, a): v[4 e ..
+ *   4 e + 3] = (+kappa[e], +kappa[e], -kappa[e], -kappa[e]).  nedges in
+ *   [0, 2^29); kappa: double[nedges]; v: double[4 nedges] (16-byte aligned).
+ *   The indices (with -1 for a Dirichlet ghost) are the caller's.
+ */
+int q1_hex_element_coo(int32_t ne, int32_t *i, int32_t *j, void *stream);
+int q1_hex_element_values(int32_t ne, const double *kappa, double *v, void *stream);
+int edge_coo_values(int64_t nedges, const double *kappa, double *v, void *stream);
 
 /* Number of kernels this library has launched in this process (a diagnostic
  * counter).  A solve graph counts its setup and closing kernels at launch and

@@ -35,7 +35,8 @@ EXPORTED = ["ksp_opts_default", "mat_create_coo", "mat_create_coo_batched",
             "mat_autotune", "mat_destroy", "gbs_launch_count", "gbs_last_error",
             "ksp_solve_cg_noalloc", "ksp_get_phase_ns", "mat_set_solver",
             "vec_create_coo", "vec_set_values_coo", "vec_get_info", "vec_destroy",
-            "ksp_solve", "ksp_solve_batched"]
+            "ksp_solve", "ksp_solve_batched", "q1_hex_element_coo", "q1_hex_element_values",
+            "edge_coo_values"]
 
 
 class KspOpts(ctypes.Structure):
@@ -105,6 +106,9 @@ def lib() -> ctypes.CDLL:
         "vec_set_values_coo": (ctypes.c_int, [P, P, ctypes.c_int, P, P]),
         "vec_get_info": (ctypes.c_int, [P, P, P, P]),
         "vec_destroy": (ctypes.c_int, [P]),
+        "q1_hex_element_coo": (ctypes.c_int, [I32, P, P, P]),
+        "q1_hex_element_values": (ctypes.c_int, [I32, P, P, P]),
+        "edge_coo_values": (ctypes.c_int, [I64, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -353,6 +357,28 @@ def vec_create_coo(n: int, i: torch.Tensor, stream=None):
 def vec_set_values_coo(V, v: torch.Tensor, y: torch.Tensor, mode: int = INSERT, stream=None):
     _check(lib().vec_set_values_coo(V, _dev(v, torch.float64, None, "v"), mode,
                                     _dev(y, torch.float64, None, "y"), _stream(stream)))
+
+
+def q1_hex_element_coo(ne: int, i: torch.Tensor, j: torch.Tensor, stream=None):
+    """COO indices of the ne^3 Q1 element blocks (int32[64 ne^3] each)."""
+    n = 64 * ne ** 3
+    _check(lib().q1_hex_element_coo(int(ne), _dev(i, torch.int32, n, "i"),
+                                    _dev(j, torch.int32, n, "j"), _stream(stream)))
+
+
+def q1_hex_element_values(ne: int, kappa: torch.Tensor, v: torch.Tensor, stream=None):
+    """COO values (kappa_e h) K_ref of the ne^3 Q1 element blocks with the
+    Dirichlet edits (float64[64 ne^3]) from kappa (float64[ne^3])."""
+    _check(lib().q1_hex_element_values(int(ne), _dev(kappa, torch.float64, ne ** 3, "kappa"),
+                                       _dev(v, torch.float64, 64 * ne ** 3, "v"),
+                                       _stream(stream)))
+
+
+def edge_coo_values(kappa: torch.Tensor, v: torch.Tensor, stream=None):
+    """COO values (+k, +k, -k, -k) of every edge (float64[4 nedges])."""
+    m = kappa.numel()
+    _check(lib().edge_coo_values(m, _dev(kappa, torch.float64, m, "kappa"),
+                                 _dev(v, torch.float64, 4 * m, "v"), _stream(stream)))
 
 
 def vec_get_info(V) -> dict:

@@ -632,7 +632,10 @@ int read_phase_ns(gbs_mat A, int64_t *phase_ns, cudaStream_t s) {
 // overlap on the GPU (other streams, other host threads) race and must be
 // serialised by the caller.  The first call on a device looks the array's
 // device address up (cudaGetSymbolAddress, with that device current); make
-// that first call before any stream capture.
+// that first call before any stream capture.  The looked-up address is kept
+// for the life of the process: after a cudaDeviceReset on that device the
+// module is loaded again and the kept address is stale, so a process that
+// resets a device must not call this entry point on it afterwards.
 
 namespace {
 
@@ -731,11 +734,20 @@ extern "C" int ksp_solve_cg_noalloc(int64_t n, const int32_t *row_ptr, const int
     set_error("ksp_solve_cg_noalloc: only GBS_FP64 is supported");
     return GBS_ERR_ARG;
   }
-  if (!(oo.rtol >= 0.0)) {
-    set_error("ksp_solve_cg_noalloc: invalid options");
+  if (oo.method != GBS_KSP_CG) {
+    set_error("ksp_solve_cg_noalloc: o->method must be GBS_KSP_CG");
+    return GBS_ERR_ARG;
+  }
+  if (!(oo.rtol >= 0.0) || !std::isfinite(oo.rtol)) {
+    set_error("ksp_solve_cg_noalloc: rtol must be finite and >= 0");
+    return GBS_ERR_ARG;
+  }
+  if (oo.host_loop != 0 && oo.host_loop != 1) {
+    set_error("ksp_solve_cg_noalloc: host_loop must be 0 or 1");
     return GBS_ERR_ARG;
   }
   if (oo.maxit < 0) oo.maxit = (int32_t)std::min<int64_t>(10 * std::max<int64_t>(n, 1), 100000);
+  if (oo.timeout_ns < 0) oo.timeout_ns = 0;
   if (n == 0) {
     if (res) memset(res, 0, sizeof(*res));
     return GBS_OK;
@@ -776,22 +788,25 @@ extern "C" int ksp_solve_cg_noalloc(int64_t n, const int32_t *row_ptr, const int
   a.call = &S->call;
   GBS_TRY(run_loop_stepped(cg_plan(false, NOALLOC_LANES), a, nba, nbe, max_trips_for(oo),
                            &S->ctl, s));
-  if (!res) return GBS_OK;
 
+  // the loop has synchronised the stream once per chunk already; one more
+  // small read gives the status, returned whether or not res is given
   SysState st;
   DevCtl ctl;
   GBS_TRY_CUDA(cudaMemcpyAsync(&st, S->st, sizeof(SysState), cudaMemcpyDeviceToHost, s));
   GBS_TRY_CUDA(cudaMemcpyAsync(&ctl, &S->ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, s));
   GBS_TRY_CUDA(cudaStreamSynchronize(s));
-  res->status = st.active ? (ctl.err ? ctl.err : GBS_ERR_MAXIT) : st.status;
-  res->iterations = st.iterations;
-  res->outer_iterations = 0;
-  res->solver = GBS_SOLVER_PHASES;
-  res->rnorm0 = st.rnorm0;
-  res->rnorm = st.rnorm;
-  const double bn = sqrt(st.bb);
-  res->true_rel_residual = bn > 0.0 ? sqrt(st.tt) / bn : sqrt(st.tt);
-  if (res->status != GBS_OK)
-    set_error("ksp_solve_cg_noalloc: solve ended with status %d", res->status);
-  return res->status;
+  const int status = st.active ? (ctl.err ? ctl.err : GBS_ERR_MAXIT) : st.status;
+  if (res) {
+    res->status = status;
+    res->iterations = st.iterations;
+    res->outer_iterations = 0;
+    res->solver = GBS_SOLVER_PHASES;
+    res->rnorm0 = st.rnorm0;
+    res->rnorm = st.rnorm;
+    const double bn = sqrt(st.bb);
+    res->true_rel_residual = bn > 0.0 ? sqrt(st.tt) / bn : sqrt(st.tt);
+  }
+  if (status != GBS_OK) set_error("ksp_solve_cg_noalloc: solve ended with status %d", status);
+  return status;
 }
