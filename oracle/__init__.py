@@ -76,6 +76,8 @@ def _load():
         lib.orc_tfqmr.argtypes = [I64, P, P, P, P, P, D, I64, ctypes.c_int, P]
         lib.orc_pipecg.restype = ctypes.c_int
         lib.orc_pipecg.argtypes = [I64, P, P, P, P, P, D, I64, ctypes.c_int, P, P]
+        lib.orc_pcg_sr.restype = ctypes.c_int
+        lib.orc_pcg_sr.argtypes = [I64, P, P, P, P, P, D, I64, ctypes.c_int, P, P]
         lib.orc_krylov_batched.restype = ctypes.c_int
         lib.orc_krylov_batched.argtypes = [I32, P, P, P, P, P, P, D, I64, ctypes.c_int, P]
         lib.orc_vec_set_values_coo.restype = I64
@@ -181,7 +183,7 @@ def coo_scatter(A: CSR, dlda) -> np.ndarray:
     return out
 
 
-BICG, TFQMR, PIPECG = 1, 2, 3
+BICG, TFQMR, PIPECG, PCG_SR = 1, 2, 3, 4
 
 
 def _nonsym(fn, A: CSR, b, rtol, maxit, x0):
@@ -225,10 +227,32 @@ def pipecg(A: CSR, b, rtol: float = 1e-8, maxit: int | None = None, x0=None,
     return x, res.as_dict(), {k: aux[i * n:(i + 1) * n].copy() for i, k in enumerate(names)}
 
 
+def pcg_sr(A: CSR, b, rtol: float = 1e-8, maxit: int | None = None, x0=None,
+           want_aux: bool = False):
+    """Jacobi-PCG in Chronopoulos and Gear's single-reduction form (one
+    reduction per iteration, taken after the product w = A u; PCG's iterates
+    in exact arithmetic).  With want_aux, also returns the final r, u, w, p,
+    s (dict)."""
+    lib = _load()
+    b = _c(b, np.float64)
+    x = np.zeros(A.nrows, np.float64) if x0 is None else _c(x0, np.float64).copy()
+    res = _Result()
+    maxit = default_maxit(A.nrows) if maxit is None else maxit
+    aux = np.zeros(5 * A.nrows, np.float64) if want_aux else None
+    lib.orc_pcg_sr(A.nrows, _p(A.row_ptr), _p(A.col), _p(A.val), _p(b), _p(x), rtol, maxit,
+                   0 if x0 is None else 1, ctypes.byref(res),
+                   _p(aux) if want_aux else None)
+    if not want_aux:
+        return x, res.as_dict()
+    n = A.nrows
+    names = ("r", "u", "w", "p", "s")
+    return x, res.as_dict(), {k: aux[i * n:(i + 1) * n].copy() for i, k in enumerate(names)}
+
+
 def krylov_batched(A: CSR, row_off, b, method: int, rtol: float = 1e-8,
                    maxit: int | None = None):
-    """Batched BiCG (method 1), TFQMR (method 2) or pipelined CG (method 3):
-    each diagonal block alone."""
+    """Batched BiCG (method 1), TFQMR (method 2), pipelined CG (method 3) or
+    single-reduction CG (method 4): each diagonal block alone."""
     lib = _load()
     row_off = _c(row_off, np.int64)
     nsys = int(row_off.shape[0] - 1)

@@ -35,6 +35,12 @@
  *       asynchronous solvers gain most: the preconditioned pipelined CG of
  *       Ghysels and Vanroose (Parallel Computing 40, 2014), Jacobi
  *       preconditioner.  In exact arithmetic its iterates are PCG's.
+ *   orc_pcg_sr         -- the same Jacobi-PCG in Chronopoulos and Gear's
+ *       single-reduction form (J. Comput. Appl. Math. 25, 1989): PCG's
+ *       iterates in exact arithmetic with the two inner products of an
+ *       iteration taken in one reduction after the product -- the form the
+ *       GPU's two-kernel CG iteration follows (Sec. 6.1's CG with the
+ *       scalars kept on the device).
  *   orc_vec_set_values_coo -- Sec. 5's COO interface for vectors
  *       (VecSetPreallocationCOO / VecSetValuesCOO): y_r is the sum of the
  *       contributions v[k] with i[k] = r.
@@ -789,8 +795,92 @@ int orc_pipecg(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
   return res->status = st;
 }
 
+/*
+ * Single-reduction Jacobi-PCG: Chronopoulos and Gear's reformulation of CG
+ * (J. Comput. Appl. Math. 25, 1989), in its preconditioned form.  The same
+ * iterates as PCG in exact arithmetic; the two inner products of an
+ * iteration are taken together, right after the product w = A u:
+ *   r = b - A x0, u = M^-1 r; then per iteration
+ *     w = A u; gamma = r.u, delta = w.u, ||r||^2 (one reduction);
+ *     stop if ||r|| <= rtol ||b||;
+ *     beta = gamma / gamma_prev (0 on the first iteration);
+ *     den = delta - beta gamma / alpha_prev (= p.Ap; delta on the first);
+ *     alpha = gamma / den;
+ *     p = u + beta p, s = w + beta s (s = A p by recurrence);
+ *     x += alpha p, r -= alpha s, u = M^-1 r.
+ * M = diag(A).  Stops when ||r||_2 <= rtol ||b||_2 (the recursively updated
+ * r, tested before each update); iterations counts the x updates (= PCG's
+ * count).  A missing or non-positive diagonal: NOT_SPD; gamma <= 0 or
+ * den <= 0: BREAKDOWN; a non-finite norm or product: NAN.  aux (5 n doubles
+ * or NULL) receives r, u, w, p, s at exit, for checking the invariants
+ * u = M^-1 r, w = A u, s = A p, r = b - A x.
+ */
+int orc_pcg_sr(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
+               const double *b, double *x, double rtol, int64_t maxit, int nonzero_guess,
+               orc_result *res, double *aux) {
+  memset(res, 0, sizeof(*res));
+  double *wk = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double) * 6);
+  if (!wk) return res->status = ORC_ERR_ALLOC;
+  double *dinv = wk, *r = wk + n, *u = r + n, *w = u + n, *p = w + n, *s = p + n;
+  double bnorm = 0.0;
+  int st = jacobi(n, rp, ci, a, dinv);
+  if (st == ORC_OK) st = start_residual(n, rp, ci, a, b, x, nonzero_guess, r, &bnorm, res);
+  for (int64_t i = 0; i < n; ++i) u[i] = w[i] = p[i] = s[i] = 0.0;
+  if (st == ORC_OK && bnorm == 0.0) {
+    for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+    res->rnorm0 = res->rnorm = 0.0;
+  } else if (st == ORC_OK) {
+    for (int64_t i = 0; i < n; ++i) u[i] = dinv[i] * r[i];
+    double gamma_prev = 0.0, alpha_prev = 0.0;
+    int64_t it = 0;
+    for (;;) {
+      orc_spmv(n, rp, ci, a, u, w);
+      const double gamma = dot(n, r, u);
+      const double delta = dot(n, w, u);
+      const double rn = sqrt(dot(n, r, r));
+      res->rnorm = rn;
+      if (!isfinite(rn) || !isfinite(gamma) || !isfinite(delta)) {
+        st = ORC_ERR_NAN;
+        break;
+      }
+      if (rn <= rtol * bnorm) break;
+      if (it >= maxit) {
+        st = ORC_ERR_MAXIT;
+        break;
+      }
+      double beta = 0.0, den = delta;
+      if (it > 0) {
+        beta = gamma / gamma_prev;
+        den = delta - beta * gamma / alpha_prev;
+      }
+      if (!(gamma > 0.0) || !(den > 0.0)) {
+        st = ORC_ERR_BREAKDOWN;
+        break;
+      }
+      const double alpha = gamma / den;
+      for (int64_t i = 0; i < n; ++i) p[i] = u[i] + beta * p[i];
+      for (int64_t i = 0; i < n; ++i) s[i] = w[i] + beta * s[i];
+      for (int64_t i = 0; i < n; ++i) x[i] = x[i] + alpha * p[i];
+      for (int64_t i = 0; i < n; ++i) r[i] = r[i] - alpha * s[i];
+      for (int64_t i = 0; i < n; ++i) u[i] = dinv[i] * r[i];
+      gamma_prev = gamma;
+      alpha_prev = alpha;
+      ++it;
+    }
+    res->iterations = (int32_t)it;
+  }
+  if (aux && n > 0) {
+    const double *src[5] = {r, u, w, p, s};
+    for (int k = 0; k < 5; ++k) memcpy(aux + (size_t)k * (size_t)n, src[k], sizeof(double) * (size_t)n);
+  }
+  if (st == ORC_OK || st == ORC_ERR_MAXIT || st == ORC_ERR_BREAKDOWN || st == ORC_ERR_NAN)
+    res->true_rel_residual = true_rel(n, rp, ci, a, b, x, bnorm, w);
+  free(wk);
+  return res->status = st;
+}
+
 /* Batched solves, each system alone: method 1 = BiCG, 2 = TFQMR, 3 =
- * pipelined CG. */
+ * pipelined CG, 4 = single-reduction CG. */
 int orc_krylov_batched(int32_t nsys, const int64_t *row_off, const int32_t *rp,
                        const int32_t *ci, const double *a, const double *b, double *x,
                        double rtol, int64_t maxit, int method, orc_result *res) {
@@ -810,7 +900,9 @@ int orc_krylov_batched(int32_t nsys, const int64_t *row_off, const int32_t *rp,
     const int st =
         method == 1   ? orc_bicg(n, lrp, lci, a + base, b + r0, x + r0, rtol, maxit, 0, &res[s])
         : method == 2 ? orc_tfqmr(n, lrp, lci, a + base, b + r0, x + r0, rtol, maxit, 0, &res[s])
-                      : orc_pipecg(n, lrp, lci, a + base, b + r0, x + r0, rtol, maxit, 0,
+        : method == 3 ? orc_pipecg(n, lrp, lci, a + base, b + r0, x + r0, rtol, maxit, 0,
+                                   &res[s], NULL)
+                      : orc_pcg_sr(n, lrp, lci, a + base, b + r0, x + r0, rtol, maxit, 0,
                                    &res[s], NULL);
     if (st != ORC_OK && first == ORC_OK) first = st;
     free(lrp);
