@@ -35,7 +35,7 @@ prints its own JSON line; the default is the Q1 benchmark above):
       into 912,673 nodes): symbolic and numeric stage times, numeric GB/s
   async  time per solve against NNZ (Sec. 6.2's comparison, 2D 5-point, 3D
       7-point and 3D 27-point problems, 5e3 to 2.7e7 nonzeros): the three-kernel
-      CG loop, the one-kernel pipelined CG, the per-CTA and cluster CG (up to
+      CG loop, the two-kernel single-reduction CG, the one-kernel pipelined CG, the per-CTA and cluster CG (up to
       2M nonzeros) and TFQMR, all device-driven
   nonsym  batched TFQMR and BiCG (Jacobi) on 16, 64, 256 and 1024 independent
       2D convection-diffusion systems (1k-50k rows each, Peclet 1-100): solves
@@ -499,7 +499,7 @@ def run_suite(args):
                     + [("poisson3d", m, lambda m=m: W.poisson3d(m, seed=W.SEED_C3))
                        for m in (16, 32, 64, 128)]
                     + [("q1hex", m, lambda m=m: W.q1_hex(m, seed=W.SEED_C2))
-                       for m in (8, 16, 32, 64)])
+                       for m in (8, 16, 32, 64, 96)])
         if args.async_problems:
             keep = set(args.async_problems.split(","))
             problems = [q for q in problems if f"{q[0]}_{q[1]}" in keep]
@@ -513,7 +513,8 @@ def run_suite(args):
             b = t(p.b)
             x = torch.empty_like(b)
             row = {"problem": f"{kind}_{m}", "n": p.nrows, "nnz": A.nnz}
-            runs = [("cg", B.KSP_CG, B.SOLVER_PHASES), ("pipecg", B.KSP_PIPECG, B.SOLVER_PHASES),
+            runs = [("cg", B.KSP_CG, B.SOLVER_PHASES), ("cgsr", B.KSP_CGSR, B.SOLVER_PHASES),
+                    ("pipecg", B.KSP_PIPECG, B.SOLVER_PHASES),
                     ("tfqmr", B.KSP_TFQMR, B.SOLVER_PHASES)]
             if A.nnz <= 2_000_000:
                 runs.append(("cg_cta", B.KSP_CG, B.SOLVER_CTA))
@@ -526,14 +527,20 @@ def run_suite(args):
                 row[name] = {"s": ts, "iterations": r["iterations"], "status": r["status"],
                              "us_per_iteration": ts * 1e6 / max(r["iterations"], 1),
                              "true_rel_residual": r["true_rel_residual"]}
+                if name in ("cg", "cgsr"):
+                    ph = A.phase_ns()
+                    row[name]["phase_us_per_iteration"] = {
+                        k: v / 1e3 / max(r["iterations"], 1) for k, v in ph.items()
+                        if k in ("spmv", "update_xr", "update_p")}
             row["pipecg_vs_cg"] = row["cg"]["s"] / row["pipecg"]["s"]
+            row["cgsr_vs_cg"] = row["cg"]["s"] / row["cgsr"]["s"]
             rows.append(row)
             A.close()
         big = rows[-1]
         line = _base_line(
             args, big["pipecg"]["s"],
             {"workload": "stencil sweep: poisson2d 32^2..2048^2 (random rhs, seed 1007 + m), "
-                         "poisson3d 16^3..128^3 (seed 1003), q1_hex 8^3..64^3 (seed 1002); "
+                         "poisson3d 16^3..128^3 (seed 1003), q1_hex 8^3..96^3 (seed 1002); "
                          "value = pipelined CG on q1_hex_64",
              "rtol": 1e-8},
             {"sweep": rows,

@@ -72,7 +72,8 @@ enum { GBS_SPMV_AUTO = -1, GBS_SPMV_SELL = 0 };
 /* Solvers (mat_set_solver). */
 enum { GBS_SOLVER_AUTO = 0, GBS_SOLVER_PHASES = 1, GBS_SOLVER_CTA = 2, GBS_SOLVER_CLUSTER = 3 };
 /* Krylov methods (ksp_opts.method; Sec. 7 batched solvers, Sec. 6.2). */
-enum { GBS_KSP_CG = 0, GBS_KSP_BICG = 1, GBS_KSP_TFQMR = 2, GBS_KSP_PIPECG = 3 };
+enum { GBS_KSP_CG = 0, GBS_KSP_BICG = 1, GBS_KSP_TFQMR = 2, GBS_KSP_PIPECG = 3,
+       GBS_KSP_CGSR = 4 };
 
 /* Solver options (host struct).  Fill with ksp_opts_default(), then override. */
 typedef struct {
@@ -101,9 +102,10 @@ typedef struct {
                            (synchronising the stream once per chunk), so
                            profilers that cannot follow device-side graph
                            loops see every kernel */
-  int32_t method;       /* GBS_KSP_CG (default), GBS_KSP_BICG, GBS_KSP_TFQMR
-                           or GBS_KSP_PIPECG; only ksp_solve /
-                           ksp_solve_batched accept a method other than CG */
+  int32_t method;       /* GBS_KSP_CG (default), GBS_KSP_CGSR, GBS_KSP_BICG,
+                           GBS_KSP_TFQMR or GBS_KSP_PIPECG; the CG entry
+                           points (ksp_solve_cg*, ksp_adjoint*) take the two
+                           CG forms, ksp_solve / ksp_solve_batched all */
 } ksp_opts;
 
 /* Per-solve (or per-system) result, host struct. */
@@ -187,7 +189,8 @@ int mat_mult(gbs_mat A, const double *x, double *y, void *stream);
  * inside FP64 iterative refinement (Sec. 2, A7).  o may be NULL (defaults).
  * res (host): if non-NULL the call synchronises and fills it, and returns its
  * status; if NULL the call is asynchronous and the result can be fetched later
- * with ksp_get_result.  o->method must be GBS_KSP_CG (else GBS_ERR_ARG).
+ * with ksp_get_result.  o->method must be GBS_KSP_CG or GBS_KSP_CGSR (the
+ * single-reduction form described at ksp_solve; else GBS_ERR_ARG).
  */
 int ksp_solve_cg(gbs_mat A, const double *b, double *x, const ksp_opts *o,
                  ksp_result *res, void *stream);
@@ -212,6 +215,16 @@ int ksp_solve_cg_batched(gbs_mat A, const double *b, double *x, const ksp_opts *
  * batched handle on its own, with its own scalars and stopping test.
  *
  *   GBS_KSP_CG: identical to ksp_solve_cg / ksp_solve_cg_batched.
+ *   GBS_KSP_CGSR: the same Jacobi-PCG in Chronopoulos and Gear's
+ *     single-reduction form (PCG's iterates in exact arithmetic): r.u, w.u
+ *     and ||r||^2 are reduced together right after the product w = A u, and
+ *     alpha, beta follow from them (alpha = r.u / (w.u - beta r.u /
+ *     alpha_prev)), so an iteration is TWO kernels -- the product fused with
+ *     the one reduction, then one element-wise update of p, s = A p, x, r and
+ *     u = M^-1 r with no reduction -- against the textbook form's three and
+ *     two.  Same stopping test, counts (x updates) and statuses as CG;
+ *     traffic 12 nnz + 128 n bytes per iteration.  Runs on the phase kernels
+ *     (any solver setting), FP64.
  *   GBS_KSP_BICG: biconjugate gradients with M = diag(A) on both sequences
  *     and shadow residual rt0 = r0; q = A p and qt = A^T pt each iteration,
  *     A^T from a transposed sliced-ELL copy built on the first BiCG solve
@@ -233,8 +246,8 @@ int ksp_solve_cg_batched(gbs_mat A, const double *b, double *x, const ksp_opts *
  *     nnz) and the method's larger drift between the recursive and the true
  *     residual.  Same stopping test and statuses as CG.
  *
- * BiCG, TFQMR and pipelined CG run in FP64 (o->precision must be
- * GBS_FP64).  BiCG and TFQMR run on the per-CTA solver (one 1024-thread CTA
+ * BiCG, TFQMR, pipelined and single-reduction CG run in FP64 (o->precision
+ * must be GBS_FP64).  BiCG and TFQMR run on the per-CTA solver (one 1024-thread CTA
  * per system, every iteration inside one kernel launch, systems largest
  * first) or on the grid-wide phase kernels in a CUDA graph, chosen as for CG
  * by mat_set_solver (automatic: per-CTA when the largest system has at most

@@ -88,7 +88,7 @@ def _load():
         lib.orc_pcg.argtypes = [I64, P, P, P, P, P, D, I64, ctypes.c_int, P]
         lib.orc_pcg_refined.restype = ctypes.c_int
         lib.orc_pcg_refined.argtypes = [I64, P, P, P, P, P, D, D, I64, I32,
-                                        ctypes.c_int, P]
+                                        ctypes.c_int, P, P]
         lib.orc_csr_is_symmetric.restype = ctypes.c_int
         lib.orc_csr_is_symmetric.argtypes = [I64, P, P, P]
         lib.orc_adjoint.restype = ctypes.c_int
@@ -302,17 +302,23 @@ def pcg(A: CSR, b, rtol: float = 1e-8, maxit: int | None = None, x0=None):
 
 
 def pcg_refined(A: CSR, b, rtol: float = 1e-8, inner_rtol: float = 1e-4,
-                inner_maxit: int | None = None, max_outer: int = 30, x0=None):
-    """FP32-inner PCG inside FP64 iterative refinement (Sec. 2, multiprecision)."""
+                inner_maxit: int | None = None, max_outer: int = 30, x0=None,
+                want_trace: bool = False):
+    """FP32-inner PCG inside FP64 iterative refinement (Sec. 2, multiprecision).
+    With want_trace, also returns each outer step's inner iteration count."""
     lib = _load()
     b = _c(b, np.float64)
     x = np.zeros(A.nrows, np.float64) if x0 is None else _c(x0, np.float64).copy()
     res = _Result()
     inner_maxit = default_maxit(A.nrows) if inner_maxit is None else inner_maxit
+    trace = np.zeros(max(max_outer, 1), np.int32)
     lib.orc_pcg_refined(A.nrows, _p(A.row_ptr), _p(A.col), _p(A.val), _p(b), _p(x),
                         rtol, inner_rtol, inner_maxit, max_outer,
-                        0 if x0 is None else 1, ctypes.byref(res))
-    return x, res.as_dict()
+                        0 if x0 is None else 1, ctypes.byref(res), _p(trace))
+    if not want_trace:
+        return x, res.as_dict()
+    r = res.as_dict()
+    return x, r, [int(v) for v in trace[:r["outer_iterations"]]]
 
 
 def is_symmetric(A: CSR) -> bool:

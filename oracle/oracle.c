@@ -359,11 +359,13 @@ int orc_pcg(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
  * x += s * d in FP64.
  * Stagnation: ||r|| fails to halve on two consecutive outer steps.
  * A32 = RN(A64) elementwise; dinv32 = RN(1/a_ii) with the reciprocal in FP64.
+ * inner_its (max_outer entries, or NULL) receives each outer step's inner
+ * iteration count.
  */
 int orc_pcg_refined(int64_t n, const int32_t *rp, const int32_t *ci,
                     const double *a, const double *b, double *x, double rtol,
                     double inner_rtol, int64_t inner_maxit, int32_t max_outer,
-                    int nonzero_guess, orc_result *res) {
+                    int nonzero_guess, orc_result *res, int32_t *inner_its) {
   memset(res, 0, sizeof(*res));
   int64_t nnz = rp[n];
   double *dinv = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double) * 2);
@@ -454,6 +456,7 @@ int orc_pcg_refined(int64_t n, const int32_t *rp, const int32_t *ci,
       break;
     }
     inner_total += it;
+    if (inner_its) inner_its[outer] = (int32_t)it;
     for (int64_t i = 0; i < n; ++i) x[i] += s * (double)d32[i];
     ++outer;
   }
@@ -985,7 +988,7 @@ int orc_pcg_batched(int32_t nsys, const int64_t *row_off, const int32_t *rp,
       st = orc_pcg(n, lrp, lci, a + base, b + r0, x + r0, rtol, maxit, 0, &res[s]);
     else
       st = orc_pcg_refined(n, lrp, lci, a + base, b + r0, x + r0, rtol, inner_rtol,
-                           inner_maxit, max_outer, 0, &res[s]);
+                           inner_maxit, max_outer, 0, &res[s], NULL);
     if (st != ORC_OK && first == ORC_OK) first = st;
     free(lrp);
     free(lci);

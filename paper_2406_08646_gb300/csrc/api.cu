@@ -74,13 +74,14 @@ static int fill_opts(gbs_mat A, const ksp_opts *in, ksp_opts &o, bool per_system
     set_error("ksp opts: host_loop must be 0 or 1");
     return GBS_ERR_ARG;
   }
-  if (o.method < GBS_KSP_CG || o.method > GBS_KSP_PIPECG) {
-    set_error("ksp opts: method must be GBS_KSP_CG, GBS_KSP_BICG, GBS_KSP_TFQMR or "
-              "GBS_KSP_PIPECG");
+  if (o.method < GBS_KSP_CG || o.method > GBS_KSP_CGSR) {
+    set_error("ksp opts: method must be GBS_KSP_CG, GBS_KSP_CGSR, GBS_KSP_BICG, "
+              "GBS_KSP_TFQMR or GBS_KSP_PIPECG");
     return GBS_ERR_ARG;
   }
   if (o.method != GBS_KSP_CG && o.precision != GBS_FP64) {
-    set_error("ksp opts: BiCG, TFQMR and pipelined CG run in FP64 only (precision GBS_FP64)");
+    set_error("ksp opts: BiCG, TFQMR, pipelined and single-reduction CG run in FP64 only "
+              "(precision GBS_FP64)");
     return GBS_ERR_ARG;
   }
   const int64_t n = max_system_rows(A, per_system);
@@ -255,8 +256,9 @@ static int solve_entry(gbs_mat A, const double *b, double *x, const ksp_opts *o,
   }
   ksp_opts oo;
   GBS_TRY(fill_opts(A, o, oo, per_system));
-  if (!any_method && oo.method != GBS_KSP_CG) {
-    set_error("%s: o->method must be GBS_KSP_CG (ksp_solve takes the others)", fn);
+  if (!any_method && oo.method != GBS_KSP_CG && oo.method != GBS_KSP_CGSR) {
+    set_error("%s: o->method must be GBS_KSP_CG or GBS_KSP_CGSR (ksp_solve takes the others)",
+              fn);
     return GBS_ERR_ARG;
   }
   GBS_TRY(use_device(A));

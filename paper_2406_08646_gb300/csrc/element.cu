@@ -21,7 +21,9 @@
 // The values are rounded in the order written above (kappa_e h first, then
 // the product with K_ref), so they are the same bits a host program gets
 // with the same two roundings.  Every kernel is a pure streaming write
-// (HBM-bound: 8 bytes per value written, 8 per element read).
+// (HBM-bound: 8 bytes per value written, 8 per element read); the FP64
+// multiplies, which on this part would otherwise bound the values kernel,
+// are formed once per element (three), not once per value (64).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,73 +35,108 @@ namespace gbs {
 
 constexpr int GEN_TPB = 256;
 
-// Thread t writes entries 2 t and 2 t + 1 of the element blocks (one 16-byte
-// store): element e = t / 32, local row a = (t / 4) % 8, columns b, b + 1
-// with b = 2 (t % 4).
+// Per-element data one warp shares: node coordinates of the element's corner
+// and its three distinct products (kappa_e h) K_ref -- FP64 is scarce on this
+// part, so each element's products are formed once, by one lane, and every
+// value of its block is a selection among them.
+struct ElemInfo {
+  double p_diag, p_edge, p_face;  // (kappa h)/3, (kappa h)(-1/12), (kappa h) 0
+  int32_t ex, ey, ez, pad;
+};
+
+// Warp w takes elements 32 w .. 32 w + 31: lane l forms element 32 w + l's
+// products (three FP64 multiplies per element in all), then the warp writes
+// the 32 blocks one after the other, lane l storing entries 2 l, 2 l + 1 of
+// the block (local row a = l / 4, columns b = 2 (l % 4), b + 1) as one
+// 16-byte store: 512 contiguous bytes per store instruction.
 __global__ void __launch_bounds__(GEN_TPB)
-    k_q1_values(int32_t ne, const double *__restrict__ kappa, double2 *__restrict__ v) {
-  const int64_t nelem = (int64_t)ne * ne * ne;
-  const int64_t npairs = nelem * 32;
-  const double h = 1.0 / (double)ne;
-  const double kd = 1.0 / 3.0, k2 = -1.0 / 12.0;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < npairs;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e = t >> 5;
-    const int a = (int)((t >> 2) & 7), b0 = (int)(t & 3) * 2;
-    const int32_t ex = (int32_t)(e % ne), ey = (int32_t)((e / ne) % ne),
-                  ez = (int32_t)(e / ((int64_t)ne * ne));
-    const double ke = __dmul_rn(__ldg(kappa + e), h);
-    double out[2];
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int b = b0 + u;
-      // boundary tests of local nodes a and b (coordinate 0 or ne on a face)
-      const int ax = ex + (a & 1), ay = ey + ((a >> 1) & 1), az = ez + (a >> 2);
-      const int bx = ex + (b & 1), by = ey + ((b >> 1) & 1), bz = ez + (b >> 2);
-      const bool fax = ax == 0 || ax == ne, fay = ay == 0 || ay == ne, faz = az == 0 || az == ne;
-      const bool fbx = bx == 0 || bx == ne, fby = by == 0 || by == ne, fbz = bz == 0 || bz == ne;
-      const bool ba = fax || fay || faz, bb = fbx || fby || fbz;
-      double val;
-      if (a == b) {
-        if (ba) {
-          const int m = (fax ? 1 : 2) * (fay ? 1 : 2) * (faz ? 1 : 2);
-          val = 1.0 / (double)m;  // 1, 1/2, 1/4 or 1/8: exact
-        } else {
-          val = __dmul_rn(ke, kd);
-        }
-      } else if (ba || bb) {
-        val = 0.0;
-      } else {  // K_ref: 0 for one differing coordinate, -1/12 for two or three
-        val = __dmul_rn(ke, __popc(a ^ b) == 1 ? 0.0 : k2);
-      }
-      out[u] = val;
+    k_q1_values(int32_t ne, double h, const double *__restrict__ kappa,
+                double2 *__restrict__ v) {
+  __shared__ ElemInfo info[GEN_TPB];
+  const int32_t nelem = ne * ne * ne;
+  const int lane = threadIdx.x & 31;
+  ElemInfo *wi = info + (threadIdx.x & ~31);
+  const int a = lane >> 2, b0 = (lane & 3) * 2;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * 32 < nelem;
+       w += nwarps) {
+    const int32_t e0 = (int32_t)(w * 32);
+    const int32_t e = e0 + lane;
+    __syncwarp();
+    if (e < nelem) {
+      const double ke = __dmul_rn(__ldg(kappa + e), h);
+      ElemInfo E;
+      E.p_diag = __dmul_rn(ke, 1.0 / 3.0);
+      E.p_edge = __dmul_rn(ke, -1.0 / 12.0);
+      E.p_face = __dmul_rn(ke, 0.0);
+      E.ex = e % ne;
+      E.ey = (e / ne) % ne;
+      E.ez = e / (ne * ne);
+      E.pad = 0;
+      wi[lane] = E;
     }
-    v[t] = make_double2(out[0], out[1]);
+    __syncwarp();
+    const int cnt = nelem - e0 < 32 ? nelem - e0 : 32;
+    for (int j = 0; j < cnt; ++j) {
+      const ElemInfo E = wi[j];
+      double out[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int b = b0 + u;
+        // boundary tests of local nodes a and b (coordinate 0 or ne)
+        const int ax = E.ex + (a & 1), ay = E.ey + ((a >> 1) & 1), az = E.ez + (a >> 2);
+        const int bx = E.ex + (b & 1), by = E.ey + ((b >> 1) & 1), bz = E.ez + (b >> 2);
+        const bool fax = ax == 0 || ax == ne, fay = ay == 0 || ay == ne, faz = az == 0 || az == ne;
+        const bool fbx = bx == 0 || bx == ne, fby = by == 0 || by == ne, fbz = bz == 0 || bz == ne;
+        const bool ba = fax || fay || faz, bb = fbx || fby || fbz;
+        double val;
+        if (a == b) {
+          // a boundary node's diagonal: 1/m with m = 1, 2 or 4 elements
+          const int nf = (int)fax + (int)fay + (int)faz;  // faces it lies on
+          val = ba ? (nf == 3 ? 1.0 : (nf == 2 ? 0.5 : 0.25)) : E.p_diag;
+        } else if (ba || bb) {
+          val = 0.0;
+        } else {  // K_ref: 0 for one differing coordinate, -1/12 for two or three
+          val = __popc(a ^ b) == 1 ? E.p_face : E.p_edge;
+        }
+        out[u] = val;
+      }
+      v[(int64_t)(e0 + j) * 32 + lane] = make_double2(out[0], out[1]);
+    }
   }
 }
 
 // Row and column indices of the element blocks: entry 64 e + 8 a + b is
-// (g(e, a), g(e, b)).  Thread t writes the 8 entries of row a of element e
-// (t = 8 e + a): two 16-byte stores of i (all g(e, a)) and two of j.
+// (g(e, a), g(e, b)).  Warp w takes elements 32 w .. 32 w + 31; lane l
+// computes element 32 w + l's first node, then the warp writes the blocks
+// one after the other, lane l storing entries 2 l, 2 l + 1 of i and of j
+// (8-byte stores, 256 contiguous bytes per instruction).
 __global__ void __launch_bounds__(GEN_TPB)
-    k_q1_indices(int32_t ne, int4 *__restrict__ i4, int4 *__restrict__ j4) {
-  const int64_t nrow = (int64_t)ne * ne * ne * 8;
+    k_q1_indices(int32_t ne, int2 *__restrict__ i2, int2 *__restrict__ j2) {
+  __shared__ int32_t g0s[GEN_TPB];
+  const int32_t nelem = ne * ne * ne;
   const int32_t nn = ne + 1;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nrow;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e = t >> 3;
-    const int a = (int)(t & 7);
-    const int32_t ex = (int32_t)(e % ne), ey = (int32_t)((e / ne) % ne),
-                  ez = (int32_t)(e / ((int64_t)ne * ne));
-    const int32_t g0 = ex + nn * (ey + nn * ez);
-    int32_t g[8];
-#pragma unroll
-    for (int b = 0; b < 8; ++b) g[b] = g0 + (b & 1) + nn * (((b >> 1) & 1) + nn * (b >> 2));
-    const int32_t ga = g0 + (a & 1) + nn * (((a >> 1) & 1) + nn * (a >> 2));
-    i4[2 * t] = make_int4(ga, ga, ga, ga);
-    i4[2 * t + 1] = make_int4(ga, ga, ga, ga);
-    j4[2 * t] = make_int4(g[0], g[1], g[2], g[3]);
-    j4[2 * t + 1] = make_int4(g[4], g[5], g[6], g[7]);
+  const int lane = threadIdx.x & 31;
+  int32_t *wg = g0s + (threadIdx.x & ~31);
+  const int a = lane >> 2, b0 = (lane & 3) * 2;
+  // offsets of local nodes a, b0, b0 + 1 from the element's first node
+  auto off = [&](int q) { return (q & 1) + nn * (((q >> 1) & 1) + nn * (q >> 2)); };
+  const int32_t oa = off(a), ob0 = off(b0), ob1 = off(b0 + 1);
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * 32 < nelem;
+       w += nwarps) {
+    const int32_t e0 = (int32_t)(w * 32);
+    const int32_t e = e0 + lane;
+    __syncwarp();
+    if (e < nelem) wg[lane] = e % ne + nn * ((e / ne) % ne + nn * (e / (ne * ne)));
+    __syncwarp();
+    const int cnt = nelem - e0 < 32 ? nelem - e0 : 32;
+    for (int j = 0; j < cnt; ++j) {
+      const int32_t g0 = wg[j];
+      const int64_t q = (int64_t)(e0 + j) * 32 + lane;
+      i2[q] = make_int2(g0 + oa, g0 + oa);
+      j2[q] = make_int2(g0 + ob0, g0 + ob1);
+    }
   }
 }
 
@@ -138,9 +175,9 @@ extern "C" int q1_hex_element_coo(int32_t ne, int32_t *i, int32_t *j, void *stre
     set_error("q1_hex_element_coo: i and j must be non-null 16-byte aligned device pointers");
     return GBS_ERR_ARG;
   }
-  const int64_t nrow = (int64_t)ne * ne * ne * 8;
-  k_q1_indices<<<gen_grid(nrow), GEN_TPB, 0, (cudaStream_t)stream>>>(
-      ne, reinterpret_cast<int4 *>(i), reinterpret_cast<int4 *>(j));
+  const int64_t warps = ((int64_t)ne * ne * ne + 31) / 32;
+  k_q1_indices<<<gen_grid(32 * warps), GEN_TPB, 0, (cudaStream_t)stream>>>(
+      ne, reinterpret_cast<int2 *>(i), reinterpret_cast<int2 *>(j));
   GBS_LAUNCHED(1);
   return GBS_OK;
 }
@@ -155,9 +192,9 @@ extern "C" int q1_hex_element_values(int32_t ne, const double *kappa, double *v,
               "non-null device pointers");
     return GBS_ERR_ARG;
   }
-  const int64_t npairs = (int64_t)ne * ne * ne * 32;
-  k_q1_values<<<gen_grid(npairs), GEN_TPB, 0, (cudaStream_t)stream>>>(
-      ne, kappa, reinterpret_cast<double2 *>(v));
+  const int64_t warps = ((int64_t)ne * ne * ne + 31) / 32;
+  k_q1_values<<<gen_grid(32 * warps), GEN_TPB, 0, (cudaStream_t)stream>>>(
+      ne, 1.0 / (double)ne, kappa, reinterpret_cast<double2 *>(v));
   GBS_LAUNCHED(1);
   return GBS_OK;
 }

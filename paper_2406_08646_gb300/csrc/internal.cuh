@@ -76,7 +76,7 @@ constexpr int KRYLOV_NVEC = 9;
 
 // Cached solve graphs of a handle, by loop kind.
 enum { GBS_GRAPH_CG = 0, GBS_GRAPH_CG32 = 1, GBS_GRAPH_BICG = 2, GBS_GRAPH_TFQMR = 3,
-       GBS_GRAPH_PIPECG = 4, GBS_GRAPH_KINDS = 5 };
+       GBS_GRAPH_PIPECG = 4, GBS_GRAPH_CGSR = 5, GBS_GRAPH_KINDS = 6 };
 
 // Per-solve control words (device).  Zeroed before every solve.
 struct DevCtl {

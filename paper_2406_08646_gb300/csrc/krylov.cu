@@ -1218,6 +1218,149 @@ static LoopPlan pipecg_plan() {
   P.post[0] = k_ns_final;
   return P;
 }
+// ------------------------------------------------------------------ single-reduction CG
+//
+// Jacobi-PCG in Chronopoulos and Gear's single-reduction form (the oracle's
+// orc_pcg_sr): PCG's iterates in exact arithmetic, with both inner products
+// of an iteration taken right after the product, so that an iteration needs
+// one reduction and TWO kernels instead of the textbook form's two and three:
+//   SpMV kernel (table A): w = A u fused with gamma = r.u, delta = w.u and
+//     ||r||^2; the last arriver's fin runs the tests and computes
+//     beta = gamma / gamma_prev and alpha = gamma / (delta - beta gamma /
+//     alpha_prev) (pipe_top, shared with the pipelined CG);
+//   update kernel (table E, no reduction): p = u + beta p, s = w + beta s,
+//     x += alpha p, r -= alpha s, u = M^-1 r; its last CTA sets the loop
+//     condition.
+// The start-up is the pipelined CG's (r = b - A x0, u = M^-1 r and the
+// start-up tests), the close its true-residual kernel.  Work vectors: r, u,
+// w, p, s = kv[0..4].  Traffic 12 nnz + 128 n bytes and nnz + 8 n FP64
+// operations per iteration.
+
+// w = A u with gamma, delta, ||r||^2; fin: tests, alpha, beta.  Table A.
+__device__ __forceinline__ void sr_spmv(const PcgArgs &a, double *red) {
+  const CallArgs &C = *a.call;
+  const double *r = a.kv[0], *u = a.kv[1];
+  double *w = a.kv[2];
+  auto want = [&](int s) -> int { return sys_active(a, s) ? 1 : 0; };
+  auto work = [&](int, int blk, int r0, int r1, double(&acc)[3]) {
+    double a0 = acc[0], a1 = acc[1], a2 = acc[2];
+    auto f = [&](int i, double y) {
+      const double ri = r[i], ui = __ldg(u + i);
+      w[i] = y;
+      a0 = fma(ri, ui, a0);
+      a1 = fma(y, ui, a1);
+      a2 = fma(ri, ri, a2);
+    };
+    row_products<double, 0>(a, blk, r0, r1, a.val, a.sval, u, f);
+    acc[0] = a0;
+    acc[1] = a1;
+    acc[2] = a2;
+  };
+  auto fin = [&](int s, double(&tot)[3]) {
+    SysState &S = a.st[s];
+    const int st = pipe_top(C, S, tot[0], tot[1], tot[2], true);
+    if (st >= 0) deactivate(a, S, st);
+    else S.iterations += 1;  // the update kernel applies this iteration
+  };
+  walk<3>(a, a.ta, 0, red, want, work, fin);
+}
+
+// p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = M^-1 r
+// (beta = 0: p = u, s = w, whatever p and s held).  Table E, no reduction.
+__device__ __forceinline__ void sr_update(const PcgArgs &a, double *red) {
+  double *x = a.call->x;
+  double *r = a.kv[0], *u = a.kv[1], *p = a.kv[3], *sv = a.kv[4];
+  const double *w = a.kv[2];
+  double alpha = 0.0, beta = 0.0;
+  auto want = [&](int s) -> int {
+    const SysState *S = a.st + s;  // issued with the active flag: one round trip
+    alpha = ldcg(&S->alpha);
+    beta = ldcg(&S->beta);
+    return sys_active(a, s) ? 1 : 0;
+  };
+  auto fin = [&](int, double(&)[1]) {};
+  auto work = [&](int, int, int r0, int r1, double(&)[1]) {
+    const double al = alpha, be = beta;
+    if (be == 0.0) {  // the first iteration
+      for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        const double ui = u[i], wi = w[i];
+        p[i] = ui;
+        sv[i] = wi;
+        x[i] = fma(al, ui, x[i]);
+        const double rn = fma(-al, wi, r[i]);
+        r[i] = rn;
+        u[i] = a.dinv[i] * rn;
+      }
+      return;
+    }
+    auto load = [&](int i) {
+      return Vals<double, 7>{{u[i], w[i], p[i], sv[i], x[i], r[i], a.dinv[i]}};
+    };
+    auto apply = [&](int i, const Vals<double, 7> &v) {
+      const double pi = fma(be, v.v[2], v.v[0]);
+      const double si = fma(be, v.v[3], v.v[1]);
+      p[i] = pi;
+      sv[i] = si;
+      x[i] = fma(al, pi, v.v[4]);
+      const double rn = fma(-al, si, v.v[5]);
+      r[i] = rn;
+      u[i] = v.v[6] * rn;
+    };
+    rows2(r0, r1, load, apply);
+  };
+  walk<0>(a, a.te, a.part_e, red, want, work, fin);
+}
+
+__global__ void NS_ROWS k_sr_spmv(PcgArgs a) {
+  __shared__ double red[RED_SCRATCH];
+  if (!trip_live(a)) return;
+  stamp_phase(a, 1);
+  sr_spmv(a, red);
+}
+__global__ void __launch_bounds__(PHASE_TPB) k_sr_update(PcgArgs a) {
+  __shared__ double red[RED_SCRATCH];
+  const bool live = trip_live(a);
+  loop_control(a, live);  // after this trip's tests (the SpMV kernel's fin)
+  if (!live) return;
+  stamp_phase(a, 2);
+  sr_update(a, red);
+}
+
+// The pipelined CG's start-up (r = b - A x0, u = M^-1 r, start-up tests) and
+// closing residual, with the phase clock of ksp_get_phase_ns started and
+// closed as for CG (setup, SpMV phase, update phase, closing residual).
+__global__ void NS_ROWS k_sr_setup(PcgArgs a) {
+  __shared__ double red[RED_SCRATCH];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int64_t t = (int64_t)global_ns();
+    a.ctl->t_start = t;
+    a.ctl->stamp = t;
+    a.ctl->last_phase = 0;
+  }
+  pipe_setup(a, red);
+}
+__global__ void NS_ROWS k_sr_final(PcgArgs a) {
+  __shared__ double red[RED_SCRATCH];
+  stamp_phase(a, 4);
+  phase_final<0>(a, red);
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->phase_ns[4] += (int64_t)global_ns() - a.ctl->stamp;
+}
+
+// setup, WHILE { SpMV + reduction, update }, final residual.
+static LoopPlan cgsr_plan() {
+  LoopPlan P;
+  memset(&P, 0, sizeof(P));
+  P.npre = 1;
+  P.pre[0] = k_sr_setup;
+  P.nbody = 2;
+  P.body[0] = k_sr_spmv;
+  P.body[1] = k_sr_update;
+  P.body_e[1] = true;
+  P.npost = 1;
+  P.post[0] = k_sr_final;
+  return P;
+}
+
 // ------------------------------------------------------------------ transpose
 
 // Transposed COO indices, local to each system: nonzero p of row r (system s,
@@ -1346,15 +1489,16 @@ static int ensure_krylov(gbs_mat A, bool transpose, cudaStream_t s) {
 
 int solve_krylov(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool per_system,
                  cudaStream_t s) {
-  const bool bicg = o.method == GBS_KSP_BICG, pipe = o.method == GBS_KSP_PIPECG;
+  const bool bicg = o.method == GBS_KSP_BICG, pipe = o.method == GBS_KSP_PIPECG,
+             sr = o.method == GBS_KSP_CGSR;
   GBS_TRY(ensure_solver_workspace(A, false));
   GBS_TRY(ensure_krylov(A, bicg, s));
   A->last_count = per_system ? A->nsys : 1;
   A->last_ensemble = !per_system;
   A->trips_counted = true;
   // automatic: one 1024-thread CTA per SM already beats the phase kernels;
-  // pipelined CG exists for the phase kernels only
-  const bool on_ctas = !pipe && (A->solver == GBS_SOLVER_CTA ||
+  // pipelined and single-reduction CG exist for the phase kernels only
+  const bool on_ctas = !pipe && !sr && (A->solver == GBS_SOLVER_CTA ||
                                  (A->solver == GBS_SOLVER_AUTO && cta_size_rule(A, per_system, 1)));
   if (!on_ctas) {
     A->last_solver = GBS_SOLVER_PHASES;
@@ -1366,6 +1510,7 @@ int solve_krylov(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool 
     PcgArgs pa = make_args(A, per_system, false);
     pa.stream_matrix = stream_matrix(A, bicg ? 24 : 12);
     if (pipe) return run_loop(A, pipecg_plan(), GBS_GRAPH_PIPECG, pa, b, x, o, per_system, s);
+    if (sr) return run_loop(A, cgsr_plan(), GBS_GRAPH_CGSR, pa, b, x, o, per_system, s);
     return run_loop(A, bicg ? bicg_plan() : tfqmr_plan(),
                     bicg ? GBS_GRAPH_BICG : GBS_GRAPH_TFQMR, pa, b, x, o, per_system, s);
   }
