@@ -55,6 +55,7 @@ struct SysState {
   double thr;       // rtol ||b_s||, the convergence threshold (set by the setup)
   double tau, theta, eta;  // TFQMR: quasi-residual recurrence (eta of the last half step)
   double coef;             // TFQMR: theta^2 eta / alpha for the next d update
+  double gam;              // single-reduction CG: r.u of the start residual
   int32_t status;
   int32_t active;   // 1 while the system still iterates
   int32_t iterations;

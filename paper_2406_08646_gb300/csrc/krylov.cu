@@ -1222,51 +1222,109 @@ static LoopPlan pipecg_plan() {
 //
 // Jacobi-PCG in Chronopoulos and Gear's single-reduction form (the oracle's
 // orc_pcg_sr): PCG's iterates in exact arithmetic, with both inner products
-// of an iteration taken right after the product, so that an iteration needs
+// of an iteration taken together after the product, so that an iteration is
 // one reduction and TWO kernels instead of the textbook form's two and three:
-//   SpMV kernel (table A): w = A u fused with gamma = r.u, delta = w.u and
-//     ||r||^2; the last arriver's fin runs the tests and computes
+//   SpMV kernel (table A): w = A u fused with the partial delta = w.u; its
+//     last arriver adds up delta and the update kernel's partials of
+//     gamma = r.u and ||r||^2 (below), runs the tests and computes
 //     beta = gamma / gamma_prev and alpha = gamma / (delta - beta gamma /
 //     alpha_prev) (pipe_top, shared with the pipelined CG);
-//   update kernel (table E, no reduction): p = u + beta p, s = w + beta s,
-//     x += alpha p, r -= alpha s, u = M^-1 r; its last CTA sets the loop
-//     condition.
-// The start-up is the pipelined CG's (r = b - A x0, u = M^-1 r and the
-// start-up tests), the close its true-residual kernel.  Work vectors: r, u,
-// w, p, s = kv[0..4].  Traffic 12 nnz + 128 n bytes and nnz + 8 n FP64
+//   update kernel (table E): p = u + beta p, s = w + beta s, x += alpha p,
+//     r -= alpha s, u = M^-1 r, fused with the partial sums of the new
+//     r.u and r.r; each CTA writes its partials to its reduction slot and
+//     goes on -- no arrival count, no last CTA waiting: the next SpMV
+//     kernel's fin sums the slots.  Its last CTA sets the loop condition.
+// So the SpMV kernel does exactly the textbook CG's product work, and the
+// update kernel has no reduction tail.  The first trip takes r.u and ||r||^2
+// of the start residual from the setup (S.gam, S.rr).  Work vectors: r, u,
+// w, p, s = kv[0..4].  Traffic 12 nnz + 120 n bytes and nnz + 8 n FP64
 // operations per iteration.
 
-// w = A u with gamma, delta, ||r||^2; fin: tests, alpha, beta.  Table A.
+// r = b - A x0, u = M^-1 r; partials r.r, b.b, missing diagonals, r.u;
+// fin: start-up tests (those of the pipelined CG), S.gam = r.u.  Table A.
+__device__ __forceinline__ void sr_setup(const PcgArgs &a, double *red) {
+  const CallArgs &C = *a.call;
+  const double *b = C.b;
+  double *x = C.x;
+  double *r = a.kv[0], *u = a.kv[1];
+  auto want = [&](int) -> int { return 1; };
+  auto row = [&](int i, double ax, double(&acc)[4]) {
+    const double bv = b[i], rv = bv - ax, dv = a.dinv[i], uv = dv * rv;
+    r[i] = rv;
+    u[i] = uv;
+    acc[0] = fma(rv, rv, acc[0]);
+    acc[1] = fma(bv, bv, acc[1]);
+    acc[2] += (dv == 0.0) ? 1.0 : 0.0;
+    acc[3] = fma(rv, uv, acc[3]);
+  };
+  auto work = [&](int, int blk, int r0, int r1, double(&acc)[4]) {
+    if (C.nonzero_guess) {
+      auto f = [&](int i, double ax) { row(i, ax, acc); };
+      row_products<double, 0>(a, blk, r0, r1, a.val, a.sval, x, f);
+    } else {
+      for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        x[i] = 0.0;
+        row(i, 0.0, acc);
+      }
+    }
+  };
+  auto fin = [&](int s, double(&tot)[4]) {
+    SysState &S = a.st[s];
+    memset(&S, 0, sizeof(SysState));
+    S.bb = tot[1];
+    S.thr = C.rtol * sqrt(S.bb);
+    S.rr = tot[0];
+    S.gam = tot[3];
+    S.rnorm0 = S.rnorm = sqrt(tot[0]);
+    S.first = 1;
+    const int st = kry_start_status(tot[2], tot[1]);
+    if (st == GBS_OK) {
+      S.zero_x = 1;
+      S.rnorm0 = S.rnorm = 0.0;
+    }
+    ns_activate(a, S, st);
+  };
+  walk<4>(a, a.ta, 0, red, want, work, fin);
+}
+
+// w = A u with delta = w.u; fin (warp 0 of the last arriver): gamma and
+// ||r||^2 from the update kernel's slots (the setup's on the first trip),
+// the tests, alpha, beta.  Table A.
 __device__ __forceinline__ void sr_spmv(const PcgArgs &a, double *red) {
   const CallArgs &C = *a.call;
-  const double *r = a.kv[0], *u = a.kv[1];
+  const double *u = a.kv[1];
   double *w = a.kv[2];
   auto want = [&](int s) -> int { return sys_active(a, s) ? 1 : 0; };
-  auto work = [&](int, int blk, int r0, int r1, double(&acc)[3]) {
-    double a0 = acc[0], a1 = acc[1], a2 = acc[2];
+  auto work = [&](int, int blk, int r0, int r1, double(&acc)[1]) {
+    double dl = acc[0];
     auto f = [&](int i, double y) {
-      const double ri = r[i], ui = __ldg(u + i);
       w[i] = y;
-      a0 = fma(ri, ui, a0);
-      a1 = fma(y, ui, a1);
-      a2 = fma(ri, ri, a2);
+      dl = fma(y, __ldg(u + i), dl);
     };
     row_products<double, 0>(a, blk, r0, r1, a.val, a.sval, u, f);
-    acc[0] = a0;
-    acc[1] = a1;
-    acc[2] = a2;
+    acc[0] = dl;
   };
-  auto fin = [&](int s, double(&tot)[3]) {
+  auto fin = [&](int s, double(&tot)[1], int lane) {
     SysState &S = a.st[s];
-    const int st = pipe_top(C, S, tot[0], tot[1], tot[2], true);
+    double gr[2];
+    if (ldcg(&S.first)) {
+      gr[0] = ldcg(&S.gam);
+      gr[1] = ldcg(&S.rr);
+    } else {
+      const int ns = min(sys_nblk(a, a.te, s), a.grid_e);
+      slot_sums<2>(a.part, a.part_e + sys_slot0(a, a.te, s), ns, gr);
+    }
+    if (lane != 0) return;
+    const int st = pipe_top(C, S, gr[0], tot[0], gr[1], true);
     if (st >= 0) deactivate(a, S, st);
     else S.iterations += 1;  // the update kernel applies this iteration
   };
-  walk<3>(a, a.ta, 0, red, want, work, fin);
+  walk<1>(a, a.ta, 0, red, want, work, fin);
 }
 
 // p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = M^-1 r
-// (beta = 0: p = u, s = w, whatever p and s held).  Table E, no reduction.
+// (beta = 0: p = u, s = w, whatever p and s held), with the partial r.u and
+// r.r of the new r, u written to the CTA's slot (no arrival).  Table E.
 __device__ __forceinline__ void sr_update(const PcgArgs &a, double *red) {
   double *x = a.call->x;
   double *r = a.kv[0], *u = a.kv[1], *p = a.kv[3], *sv = a.kv[4];
@@ -1278,9 +1336,10 @@ __device__ __forceinline__ void sr_update(const PcgArgs &a, double *red) {
     beta = ldcg(&S->beta);
     return sys_active(a, s) ? 1 : 0;
   };
-  auto fin = [&](int, double(&)[1]) {};
-  auto work = [&](int, int, int r0, int r1, double(&)[1]) {
+  auto fin = [&](int, double(&)[2]) {};
+  auto work = [&](int, int, int r0, int r1, double(&acc)[2]) {
     const double al = alpha, be = beta;
+    double g = acc[0], q = acc[1];
     if (be == 0.0) {  // the first iteration
       for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
         const double ui = u[i], wi = w[i];
@@ -1288,27 +1347,35 @@ __device__ __forceinline__ void sr_update(const PcgArgs &a, double *red) {
         sv[i] = wi;
         x[i] = fma(al, ui, x[i]);
         const double rn = fma(-al, wi, r[i]);
+        const double un = a.dinv[i] * rn;
         r[i] = rn;
-        u[i] = a.dinv[i] * rn;
+        u[i] = un;
+        g = fma(rn, un, g);
+        q = fma(rn, rn, q);
       }
-      return;
+    } else {
+      auto load = [&](int i) {
+        return Vals<double, 7>{{u[i], w[i], p[i], sv[i], x[i], r[i], a.dinv[i]}};
+      };
+      auto apply = [&](int i, const Vals<double, 7> &v) {
+        const double pi = fma(be, v.v[2], v.v[0]);
+        const double si = fma(be, v.v[3], v.v[1]);
+        p[i] = pi;
+        sv[i] = si;
+        x[i] = fma(al, pi, v.v[4]);
+        const double rn = fma(-al, si, v.v[5]);
+        const double un = v.v[6] * rn;
+        r[i] = rn;
+        u[i] = un;
+        g = fma(rn, un, g);
+        q = fma(rn, rn, q);
+      };
+      rows2(r0, r1, load, apply);
     }
-    auto load = [&](int i) {
-      return Vals<double, 7>{{u[i], w[i], p[i], sv[i], x[i], r[i], a.dinv[i]}};
-    };
-    auto apply = [&](int i, const Vals<double, 7> &v) {
-      const double pi = fma(be, v.v[2], v.v[0]);
-      const double si = fma(be, v.v[3], v.v[1]);
-      p[i] = pi;
-      sv[i] = si;
-      x[i] = fma(al, pi, v.v[4]);
-      const double rn = fma(-al, si, v.v[5]);
-      r[i] = rn;
-      u[i] = v.v[6] * rn;
-    };
-    rows2(r0, r1, load, apply);
+    acc[0] = g;
+    acc[1] = q;
   };
-  walk<0>(a, a.te, a.part_e, red, want, work, fin);
+  walk<2, false>(a, a.te, a.part_e, red, want, work, fin);
 }
 
 __global__ void NS_ROWS k_sr_spmv(PcgArgs a) {
@@ -1326,9 +1393,9 @@ __global__ void __launch_bounds__(PHASE_TPB) k_sr_update(PcgArgs a) {
   sr_update(a, red);
 }
 
-// The pipelined CG's start-up (r = b - A x0, u = M^-1 r, start-up tests) and
-// closing residual, with the phase clock of ksp_get_phase_ns started and
-// closed as for CG (setup, SpMV phase, update phase, closing residual).
+// The start-up and the closing residual, with the phase clock of
+// ksp_get_phase_ns started and closed as for CG (setup, SpMV phase, update
+// phase, closing residual).
 __global__ void NS_ROWS k_sr_setup(PcgArgs a) {
   __shared__ double red[RED_SCRATCH];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1337,7 +1404,7 @@ __global__ void NS_ROWS k_sr_setup(PcgArgs a) {
     a.ctl->stamp = t;
     a.ctl->last_phase = 0;
   }
-  pipe_setup(a, red);
+  sr_setup(a, red);
 }
 __global__ void NS_ROWS k_sr_final(PcgArgs a) {
   __shared__ double red[RED_SCRATCH];

@@ -233,6 +233,7 @@ PcgArgs make_args(gbs_mat A, bool per_system, bool refined) {
   a.ta = view(A->ta);
   a.te = view(A->te);
   a.part_e = A->ta.nslots;
+  a.grid_e = A->te.grid;
   a.row_ptr = A->row_ptr;
   a.col = A->col;
   a.val = A->val;
@@ -774,6 +775,7 @@ extern "C" int ksp_solve_cg_noalloc(int64_t n, const int32_t *row_ptr, const int
   a.ta = BlockTable{nba, S->row0_a, nullptr, nullptr, nullptr, nullptr};
   a.te = BlockTable{nbe, S->row0_e, nullptr, nullptr, nullptr, nullptr};
   a.part_e = nba;
+  a.grid_e = nbe;
   a.row_ptr = row_ptr;
   a.col = col;
   a.val = val;

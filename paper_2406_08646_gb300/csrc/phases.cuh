@@ -29,6 +29,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "device_util.cuh"
 #include "internal.cuh"
 
@@ -57,6 +59,7 @@ struct PcgArgs {
   int32_t nsys, ensemble;
   BlockTable ta, te;  // SpMV blocks, update blocks
   int64_t part_e;     // first reduction slot of table te
+  int32_t grid_e;     // CTAs of the kernels that walk table te
   const int32_t *row_ptr, *col;
   const double *val;
   const float *val32;
@@ -152,11 +155,46 @@ __device__ __forceinline__ void stamp_phase(const PcgArgs &a, int k) {
   }
 }
 
+// Sums over the warp of a system's ns reduction slots from base on (NV
+// values each, SLOT_STRIDE apart): lane l adds slots l, l + 32, l + 64, ...
+// in that order, then warp_sums adds the lanes -- a fixed order.  The lane's
+// loads for a batch of slots (8 values in registers) are all issued before
+// its first add, so the sum over a one-wave grid's slots takes a few L2
+// round trips, not one per slot a lane holds.  Every lane ends with the
+// totals.
+template <int NV>
+__device__ __forceinline__ void slot_sums(const double *part, int64_t base, int ns,
+                                          double (&tot)[NV]) {
+  constexpr int SLOT_BATCH = 8 / NV > 0 ? 8 / NV : 1;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) tot[k] = 0.0;
+  for (int i0 = 0; i0 < ns; i0 += 32 * SLOT_BATCH) {
+    double v[SLOT_BATCH][NV];
+#pragma unroll
+    for (int j = 0; j < SLOT_BATCH; ++j) {
+      const int i = i0 + lane + 32 * j;
+#pragma unroll
+      for (int k = 0; k < NV; ++k)
+        v[j][k] = i < ns ? ldcg(part + (base + i) * SLOT_STRIDE + k) : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < SLOT_BATCH; ++j)
+#pragma unroll
+      for (int k = 0; k < NV; ++k)
+        if (i0 + lane + 32 * j < ns) tot[k] += v[j][k];
+  }
+  warp_sums<double, NV>(tot);
+}
+
 // Reduce the CTA's NV partials over its run on system s (last block b of a
 // table processed by G CTAs) into the system's slot; the last arriving CTA
-// sums all slots in slot order and calls fin(s, totals) on thread 0.
-// f32: FP32 accumulation throughout.
-template <int NV, class Fin>
+// sums all slots in slot order and calls fin(s, totals) on thread 0 -- or,
+// when fin also takes a lane index, on every lane of that CTA's warp 0 (a
+// fin that needs the warp, e.g. to sum another kernel's slots).  ARRIVE =
+// false: only the slot is written (no arrival count, no fin): a later
+// kernel's fin sums those slots itself.  f32: FP32 accumulation throughout.
+template <int NV, bool ARRIVE = true, class Fin>
 __device__ __forceinline__ void flush(const PcgArgs &a, const BlockTable &t, int64_t part_off,
                                       int s, int b, double (&acc)[NV], double *red, bool f32,
                                       Fin &fin) {
@@ -185,6 +223,13 @@ __device__ __forceinline__ void flush(const PcgArgs &a, const BlockTable &t, int
   // boundaries order those accesses.
   if ((threadIdx.x >> 5) != 0) return;
   const int lane = threadIdx.x & 31;
+  if constexpr (!ARRIVE) {
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) a.part[(base + slot) * SLOT_STRIDE + k] = acc[k];
+    }
+    return;
+  }
   unsigned prev = 0;
   if (lane == 0) {
 #pragma unroll
@@ -209,18 +254,13 @@ __device__ __forceinline__ void flush(const PcgArgs &a, const BlockTable &t, int
 #pragma unroll
     for (int k = 0; k < NV; ++k) tot[k] = (double)x[k];
   } else {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) tot[k] = 0.0;
-    for (int i = lane; i < ns; i += 32) {
-      const double *sl = a.part + (base + i) * SLOT_STRIDE;
-#pragma unroll
-      for (int k = 0; k < NV; ++k) tot[k] += ldcg(sl + k);
-    }
-    warp_sums<double, NV>(tot);
+    slot_sums<NV>(a.part, base, ns, tot);
   }
-  if (lane == 0) {
-    a.sys_cnt[s] = 0u;
-    fin(s, tot);
+  if (lane == 0) a.sys_cnt[s] = 0u;
+  if constexpr (std::is_invocable_v<Fin &, int, double(&)[NV], int>) {
+    fin(s, tot, lane);
+  } else {
+    if (lane == 0) fin(s, tot);
   }
 }
 
@@ -229,7 +269,7 @@ __device__ __forceinline__ void flush(const PcgArgs &a, const BlockTable &t, int
 // unchanged until the system's fin runs); work(s, b, r0, r1, acc) processes
 // block b, rows [r0, r1).  A CTA meets each system in one run of consecutive visits, so it
 // flushes once per system it touches (NV == 0: no reduction).
-template <int NV, class Want, class Work, class Fin>
+template <int NV, bool ARRIVE = true, class Want, class Work, class Fin>
 __device__ __forceinline__ void walk(const PcgArgs &a, const BlockTable &t, int64_t part_off,
                                      double *red, Want &want, Work &work, Fin &fin) {
   constexpr int NA = NV > 0 ? NV : 1;
@@ -243,7 +283,7 @@ __device__ __forceinline__ void walk(const PcgArgs &a, const BlockTable &t, int6
     const int r0 = __ldg(t.row0 + b), r1 = __ldg(t.row0 + b + 1);  // issued with want's loads
     if (s != cur_s) {
       if constexpr (NV > 0) {
-        if (kind) flush<NV>(a, t, part_off, cur_s, cur_b, acc, red, kind == 2, fin);
+        if (kind) flush<NV, ARRIVE>(a, t, part_off, cur_s, cur_b, acc, red, kind == 2, fin);
       }
       cur_s = s;
       kind = want(s);
@@ -255,7 +295,7 @@ __device__ __forceinline__ void walk(const PcgArgs &a, const BlockTable &t, int6
     work(s, b, r0, r1, acc);
   }
   if constexpr (NV > 0) {
-    if (kind) flush<NV>(a, t, part_off, cur_s, cur_b, acc, red, kind == 2, fin);
+    if (kind) flush<NV, ARRIVE>(a, t, part_off, cur_s, cur_b, acc, red, kind == 2, fin);
   }
 }
 

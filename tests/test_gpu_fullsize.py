@@ -4,11 +4,16 @@ the graph-driven loop).
 
 C2 (Q1 96^3) and C3 (7-point 192^3): the whole CSR structure and the values
 bit-exact against the oracle's assembly, every SpMV row within
-1e-12 * sum |a||x|, and the FP64 solve's true residual recomputed by the
-oracle from the GPU's x (C2 also against the oracle's stored iteration count,
-tests/golden/q1hex96_oracle_pcg.json).  C5 (512 systems, 51.6M rows): the
-batched launch as the benchmark runs it, checked on sampled systems the oracle
-assembles and multiplies one by one."""
+1e-12 * sum |a||x|, and the FP64 solves' (textbook and single-reduction)
+true residuals recomputed by the oracle from the GPU's x, with the oracle's
+stored iteration counts (tests/golden/, written by make_golden.py from the
+oracle alone).  C4 (edge diffusion 1024^2): the forward solve and the adjoint
+against the oracle's stored counts, norms and sampled entries of lambda and
+dL/dkappa, the adjoint identities checked exactly, and a central finite
+difference of the loss along a random direction of kappa.  C5 (512 systems,
+51.6M rows): the batched FP64, FP32-refined and adjoint launches as the
+benchmark runs them, checked on sampled systems the oracle assembles,
+multiplies and solves one by one."""
 import json
 import os
 
@@ -70,10 +75,19 @@ def test_c2_full_size():
     assert r["status"] == B.OK and tr <= 1.05e-8
     assert abs(r["iterations"] - g["iterations"]) <= max(2, int(np.ceil(0.01 * g["iterations"])))
     assert abs(r["rnorm0"] - g["rnorm0"]) <= 1e-12 * g["rnorm0"]
+    gd = json.load(open(os.path.join(GOLDEN, "q1hex96_oracle_pcg.json")))
+    xs, rs = A.solve(t(p.b), rtol=1e-8, method=B.KSP_CGSR)
+    trs = np.linalg.norm(p.b - oracle.spmv(O, xs.cpu().numpy())) / np.linalg.norm(p.b)
+    gs = gd["result_sr"]
+    assert rs["status"] == B.OK and trs <= 1.05e-8, trs
+    assert abs(rs["iterations"] - gs["iterations"]) <= max(2, int(np.ceil(0.01 * gs["iterations"])))
     # the refined solve reaches the same FP64 residual
     x32, r32 = A.solve(t(p.b), rtol=1e-8, precision=B.FP32_REFINED)
     tr32 = np.linalg.norm(p.b - oracle.spmv(O, x32.cpu().numpy())) / np.linalg.norm(p.b)
     assert r32["status"] == B.OK and tr32 <= 1.05e-8
+    gr = gd["result_refined"]
+    assert abs(r32["outer_iterations"] - gr["outer_iterations"]) <= 1
+    assert abs(r32["iterations"] - gr["iterations"]) <= max(2, int(np.ceil(0.01 * gr["iterations"])))
     A.close()
 
 
@@ -83,12 +97,80 @@ def test_c3_full_size():
     A.set_values(t(p.v))
     O = check_assembly_and_spmv(p, A, 6)
     bn = np.linalg.norm(p.b)
-    for prec in (B.FP64, B.FP32_REFINED):
-        x, r = A.solve(t(p.b), rtol=1e-10, precision=prec)
+    gd = json.load(open(os.path.join(GOLDEN, "poisson3d192_oracle_pcg.json")))
+    for prec, method, key in ((B.FP64, B.KSP_CG, "result"), (B.FP32_REFINED, B.KSP_CG, None),
+                              (B.FP64, B.KSP_CGSR, "result_sr")):
+        x, r = A.solve(t(p.b), rtol=1e-10, precision=prec, method=method)
         tr = np.linalg.norm(p.b - oracle.spmv(O, x.cpu().numpy())) / bn
-        assert r["status"] == B.OK and tr <= 1.05e-10, (prec, tr)
+        assert r["status"] == B.OK and tr <= 1.05e-10, (prec, method, tr)
         # the GPU's own closing residual agrees with the oracle's recomputation
         assert abs(r["true_rel_residual"] - tr) <= 1e-3 * tr + 1e-13
+        if key:
+            g = gd[key]
+            assert abs(r["iterations"] - g["iterations"]) <= max(
+                2, int(np.ceil(0.01 * g["iterations"]))), (method, r, g)
+            assert abs(r["rnorm0"] - g["rnorm0"]) <= 1e-12 * g["rnorm0"]
+    A.close()
+
+
+def test_c4_full_size_forward_adjoint_and_gradient():
+    p = W.edge_diffusion(1024, seed=W.SEED_C4)
+    gd = json.load(open(os.path.join(GOLDEN, "edge1024_oracle.json")))
+    A = B.Mat.from_coo(p.nrows, p.ncols, t(p.i), t(p.j))
+    kappa = t(p.extra["kappa"])
+    v = torch.empty(p.ncoo, dtype=torch.float64, device=DEV)
+    B.edge_coo_values(kappa, v)                     # the device-side generator
+    A.set_values(v)
+    O = check_assembly_and_spmv(p, A, 9)
+    bn = np.linalg.norm(p.b)
+    close = lambda a, b: abs(a - b) <= max(2, int(np.ceil(0.01 * b)))
+    # forward at the benchmark's tolerance, in both CG forms
+    for method in (B.KSP_CG, B.KSP_CGSR):
+        x8, r8 = A.solve(t(p.b), rtol=1e-8, method=method)
+        tr = np.linalg.norm(p.b - oracle.spmv(O, x8.cpu().numpy())) / bn
+        g8 = gd["forward_rtol_1e-8"]
+        assert r8["status"] == B.OK and tr <= 1.05e-8, (method, tr)
+        assert close(r8["iterations"], g8["iterations"]), (method, r8, g8)
+        assert abs(r8["rnorm0"] - g8["rnorm0"]) <= 1e-12 * g8["rnorm0"]
+    # the adjoint at a tight forward solution
+    x, r = A.solve(t(p.b), rtol=1e-12)
+    assert r["status"] == B.OK
+    xh = x.cpu().numpy()
+    assert abs(np.linalg.norm(xh) - gd["x_norm"]) <= 1e-6 * gd["x_norm"]
+    xt = p.extra["x_target"]
+    g = t(xh - xt)
+    lam, _, dldv, ra = A.adjoint(x, g, dlda=False, dldv=True, rtol=1e-12)
+    assert ra[0]["status"] == B.OK
+    lh, dv = lam.cpu().numpy(), dldv.cpu().numpy()
+    gh = xh - xt
+    assert np.linalg.norm(gh - oracle.spmv(O, lh)) <= 1.05e-12 * np.linalg.norm(gh)
+    # dL/dv = -lambda_i x_j on every kept entry, 0 on ignored ones: exactly
+    keep = (p.i >= 0) & (p.j >= 0)
+    expect = np.where(keep, -(lh[np.maximum(p.i, 0)] * xh[np.maximum(p.j, 0)]), 0.0)
+    assert dv.tobytes() == expect.tobytes()
+    gk = (dv.reshape(-1, 4) * W.EDGE_SIGNS).sum(axis=1)
+    ln, kn = gd["lambda_norm"], gd["dLdkappa_norm"]
+    assert abs(np.linalg.norm(lh) - ln) <= 1e-6 * ln
+    assert abs(np.linalg.norm(gk) - kn) <= 1e-6 * kn
+    for i, val in gd["lambda_sample"].items():
+        assert abs(lh[int(i)] - val) <= 1e-6 * ln / np.sqrt(p.nrows) * 100, (i, lh[int(i)], val)
+    for e, val in gd["dLdkappa_sample"].items():
+        assert abs(gk[int(e)] - val) <= 1e-6 * kn / np.sqrt(gk.shape[0]) * 100, (e, gk[int(e)], val)
+    # central difference of L(kappa) = 0.5 ||x(kappa) - x_t||^2 along kappa * d
+    d = np.random.default_rng(12).standard_normal(gk.shape[0])
+    d /= np.linalg.norm(d)
+    kh = p.extra["kappa"]
+    eps = 1e-3
+    losses = []
+    for sgn in (1.0, -1.0):
+        B.edge_coo_values(t(kh * (1.0 + sgn * eps * d)), v)
+        A.set_values(v)
+        xe, re = A.solve(t(p.b), rtol=1e-12)
+        assert re["status"] == B.OK
+        losses.append(0.5 * float(np.sum((xe.cpu().numpy() - xt) ** 2)))
+    fd = (losses[0] - losses[1]) / (2 * eps)
+    ad = float(np.dot(gk, kh * d))
+    assert abs(fd - ad) <= 1e-4 * abs(ad) + 1e-9 * gd["loss"], (fd, ad)
     A.close()
 
 
@@ -116,6 +198,54 @@ def test_c5_batched_full_size_sampled_systems():
         tr = np.linalg.norm(bs - oracle.spmv(O, xg[a0:a1])) / np.linalg.norm(bs)
         assert tr <= 1.05e-8, (s, tr)
         assert abs(rs[s]["true_rel_residual"] - tr) <= 1e-3 * tr + 1e-13
+    A.close()
+
+
+def test_c5_batched_refined_and_adjoint_full_size_sampled_systems():
+    """The FP32-refined batched solve and the batched adjoint of the 512
+    systems as the benchmark runs them: sampled systems re-assembled by the
+    oracle, the refined solution's true residual and counts against the
+    oracle's refined solve, the adjoint's lambda solving A_s lambda = g_s, its
+    dL/dv exactly -lambda_i x_j, and lambda against the oracle's adjoint."""
+    bt = W.batch(512, seed=W.SEED_C5)
+    A = B.Mat.from_coo_batched(bt.nrows, bt.ncoo, t(bt.i), t(bt.j))
+    A.set_values(t(bt.v))
+    b = t(bt.b)
+    x32, rs32 = A.solve_batched(b, rtol=1e-8, precision=B.FP32_REFINED)
+    assert all(q["status"] == B.OK for q in rs32)
+    x, rs = A.solve_batched(b, rtol=1e-10)
+    assert all(q["status"] == B.OK for q in rs)
+    g = (x - t(bt.extra["x_target"])).contiguous()
+    lam, _, dldv, ra = A.adjoint(x, g, dlda=False, dldv=True, batched=True, rtol=1e-12)
+    assert all(q["status"] == B.OK for q in ra)
+    xg, x32g, lg, dvg, gg = (a.cpu().numpy() for a in (x, x32, lam, dldv, g))
+    ro, co = bt.row_off, bt.coo_off
+    rng = np.random.default_rng(18)
+    for s in sorted(set(rng.integers(0, bt.nsys, 6).tolist()) | {0, 1, bt.nsys - 1}):
+        n = int(bt.nrows[s])
+        sl = slice(int(co[s]), int(co[s + 1]))
+        O = oracle.coo_symbolic(n, n, bt.i[sl], bt.j[sl])
+        oracle.coo_numeric(O, bt.v[sl])
+        a0, a1 = int(ro[s]), int(ro[s + 1])
+        bs = bt.b[a0:a1]
+        # refined
+        tr = np.linalg.norm(bs - oracle.spmv(O, x32g[a0:a1])) / np.linalg.norm(bs)
+        assert tr <= 1.05e-8, (s, tr)
+        _, rr = oracle.pcg_refined(O, bs, rtol=1e-8)
+        assert rr["status"] == oracle.OK
+        assert abs(rs32[s]["outer_iterations"] - rr["outer_iterations"]) <= 1, (s, rs32[s], rr)
+        assert abs(rs32[s]["iterations"] - rr["iterations"]) <= max(
+            2, int(np.ceil(0.01 * rr["iterations"]))), (s, rs32[s], rr)
+        # adjoint
+        xs, ls, gs = xg[a0:a1], lg[a0:a1], gg[a0:a1]
+        assert np.linalg.norm(gs - oracle.spmv(O, ls)) <= 1.05e-12 * np.linalg.norm(gs), s
+        ii, jj = bt.i[sl], bt.j[sl]
+        keep = (ii >= 0) & (jj >= 0)
+        expect = np.where(keep, -(ls[np.maximum(ii, 0)] * xs[np.maximum(jj, 0)]), 0.0)
+        assert dvg[sl].tobytes() == expect.tobytes(), s
+        lo, _, dvo, ro_ = oracle.adjoint(O, xs, gs, rtol=1e-12)
+        assert ro_["status"] == oracle.OK
+        assert np.linalg.norm(ls - lo) <= 1e-6 * np.linalg.norm(lo), s
     A.close()
 
 

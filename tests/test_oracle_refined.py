@@ -6,7 +6,7 @@ An independent emulation, written here from the reading of the method rather
 than from the oracle's code, runs the same algorithm with numpy scalars and
 arrays of the stated precisions -- FP64 outer residual r = b - A x and its
 norm s, inner right-hand side RN32(r / s), FP32 Jacobi-PCG on RN32(A) with
-RN32(1 / a_ii), FP32 products and FP32 sequential sums, stop when
+RN32(1 / a_ii), FP32 products and FP32 pairwise sums, stop when
 sqrt(r_in . r_in) <= max(inner_rtol, rtol ||b|| / (2 s)) times its initial
 value (or inner_maxit, or sigma <= 0), x += s d in FP64 -- and must
 reproduce the oracle's inner iteration count for every outer step and its x
@@ -33,6 +33,16 @@ f32, f64 = np.float32, np.float64
 def seq_sum(v):
     """Left-to-right sum in v's own precision (each addition rounded)."""
     return np.add.accumulate(v)[-1] if v.shape[0] else v.dtype.type(0)
+
+
+def pair_sum(v):
+    """Pairwise sum in v's own precision: halves of more than 8 terms summed
+    recursively and added, at most 8 terms left to right."""
+    n = v.shape[0]
+    if n <= 8:
+        return seq_sum(v) if n else v.dtype.type(0)
+    h = n // 2
+    return pair_sum(v[:h]) + pair_sum(v[h:])
 
 
 def spmv_seq(A, vals, x):
@@ -86,13 +96,13 @@ def emulate(A, b, rtol, inner_rtol, inner_maxit, max_outer):
         d = np.zeros(n, f32)
         z = dinv32 * r32
         p = z.copy()
-        rho = seq_sum(r32 * z)
-        rr = seq_sum(r32 * r32)
+        rho = pair_sum(r32 * z)
+        rr = pair_sum(r32 * r32)
         thr = tgt * f64(np.sqrt(rr))
         it = 0
         while f64(np.sqrt(rr)) > thr and it < inner_maxit:
             q = spmv_seq(A, a32, p)
-            sigma = seq_sum(p * q)
+            sigma = pair_sum(p * q)
             if not sigma > 0:
                 break
             it += 1
@@ -100,8 +110,8 @@ def emulate(A, b, rtol, inner_rtol, inner_maxit, max_outer):
             d = d + alpha * p
             r32 = r32 - alpha * q
             z = dinv32 * r32
-            rho_new = seq_sum(r32 * z)
-            rr = seq_sum(r32 * r32)
+            rho_new = pair_sum(r32 * z)
+            rr = pair_sum(r32 * r32)
             beta = rho_new / rho
             p = z + beta * p
             rho = rho_new
@@ -184,8 +194,11 @@ def test_last_correction_stops_at_the_rtol_term():
 
 MUTANTS = [
     ("FP64 accumulation in the FP32 dot products",
-     "static float dot32(int64_t n, const float *x, const float *y) {\n  float s = 0.0f;",
-     "static float dot32(int64_t n, const float *x, const float *y) {\n  double s = 0.0;"),
+     "  if (n <= 8) {\n    float s = 0.0f;",
+     "  {\n    double t = 0.0;\n    for (int64_t i = 0; i < n; ++i) t += (double)x[i] * (double)y[i];\n"
+     "    return (float)t;\n  }\n  if (n <= 8) {\n    float s = 0.0f;"),
+    ("FP32 dot products summed left to right",
+     "  if (n <= 8) {\n    float s = 0.0f;", "  if (1) {\n    float s = 0.0f;"),
     ("target factor 1/2 turned to 1", "const double tgt = fmax(inner_rtol, 0.5 * rtol * bnorm / s);",
      "const double tgt = fmax(inner_rtol, 1.0 * rtol * bnorm / s);"),
     ("no rtol term in the target", "const double tgt = fmax(inner_rtol, 0.5 * rtol * bnorm / s);",
