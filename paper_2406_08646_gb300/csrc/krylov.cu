@@ -1287,14 +1287,44 @@ __device__ __forceinline__ void sr_setup(const PcgArgs &a, double *red) {
   walk<4>(a, a.ta, 0, red, want, work, fin);
 }
 
-// w = A u with delta = w.u; fin (warp 0 of the last arriver): gamma and
-// ||r||^2 from the update kernel's slots (the setup's on the first trip),
-// the tests, alpha, beta.  Table A.
+// w = A u with delta = w.u; fin (the last arriver): the tests, alpha, beta.
+// gamma and ||r||^2 are the update kernel's slot partials, summed while the
+// product runs -- by warp 1 of the CTA that holds the system's first block,
+// before that CTA's own arrival, so the sums are in S.gam / S.rr when the
+// last arriver reads them -- and on the first trip the setup's.  Table A.
+// (Not inlined, like sr_fin below: the product kernel runs at 32 registers,
+// and these rarely run paths would otherwise make the compiler spill around
+// the row loop.)
+__device__ __noinline__ void sr_presum(const PcgArgs &a, int s) {
+  SysState &S = a.st[s];
+  if (ldcg(&S.first)) return;
+  double gr[2];
+  const int ns = min(sys_nblk(a, a.te, s), a.grid_e);
+  slot_sums<2>(a.part, a.part_e + sys_slot0(a, a.te, s), ns, gr);
+  if ((threadIdx.x & 31) == 0) {
+    S.gam = gr[0];
+    S.rr = gr[1];
+    __threadfence();  // before this CTA's arrival (block_reduce barrier, fence, count)
+  }
+}
+
+__device__ __noinline__ void sr_fin(const PcgArgs &a, int s, double delta) {
+  SysState &S = a.st[s];
+  const int st = pipe_top(*a.call, S, ldcg(&S.gam), delta, ldcg(&S.rr), true);
+  if (st >= 0) deactivate(a, S, st);
+  else S.iterations += 1;  // the update kernel applies this iteration
+}
+
 __device__ __forceinline__ void sr_spmv(const PcgArgs &a, double *red) {
-  const CallArgs &C = *a.call;
   const double *u = a.kv[1];
   double *w = a.kv[2];
-  auto want = [&](int s) -> int { return sys_active(a, s) ? 1 : 0; };
+  auto want = [&](int s) -> int {
+    if (!sys_active(a, s)) return 0;
+    // warp 1 of the CTA whose first block of s is the system's first block
+    if (blockIdx.x == sys_b0(a, a.ta, s) % gridDim.x && (threadIdx.x >> 5) == 1)
+      sr_presum(a, s);
+    return 1;
+  };
   auto work = [&](int, int blk, int r0, int r1, double(&acc)[1]) {
     double dl = acc[0];
     auto f = [&](int i, double y) {
@@ -1304,21 +1334,7 @@ __device__ __forceinline__ void sr_spmv(const PcgArgs &a, double *red) {
     row_products<double, 0>(a, blk, r0, r1, a.val, a.sval, u, f);
     acc[0] = dl;
   };
-  auto fin = [&](int s, double(&tot)[1], int lane) {
-    SysState &S = a.st[s];
-    double gr[2];
-    if (ldcg(&S.first)) {
-      gr[0] = ldcg(&S.gam);
-      gr[1] = ldcg(&S.rr);
-    } else {
-      const int ns = min(sys_nblk(a, a.te, s), a.grid_e);
-      slot_sums<2>(a.part, a.part_e + sys_slot0(a, a.te, s), ns, gr);
-    }
-    if (lane != 0) return;
-    const int st = pipe_top(C, S, gr[0], tot[0], gr[1], true);
-    if (st >= 0) deactivate(a, S, st);
-    else S.iterations += 1;  // the update kernel applies this iteration
-  };
+  auto fin = [&](int s, double(&tot)[1]) { sr_fin(a, s, tot[0]); };
   walk<1>(a, a.ta, 0, red, want, work, fin);
 }
 
