@@ -611,6 +611,85 @@ __global__ void k_coo_numeric(int64_t nnz, const int32_t *__restrict__ jmap,
   }
 }
 
+// The numeric stage straight into both layouts, one warp per 32-row slice of
+// the sliced-ELL copy.  The slice's nonzeros are a contiguous CSR range; the
+// warp takes them 32 at a time (lane l: nonzero p = c0 + l): it loads their
+// segment offsets jmap[p] (coalesced), then the chunk's whole run of perm
+// entries [jmap[c0], jmap[c0 + 32]) (contiguous, coalesced) and the v values
+// they point to (all gathers in flight together) into shared memory, and
+// lane l folds its segment from there in increasing COO index with plain
+// adds -- the same sums, bit for bit, as one thread per nonzero.  The sum
+// goes to val[p] (CSR) and to the nonzero's place in the sliced copy (entry
+// k of the slice's row j: b + 64 (k / 2) + 2 j + (k % 2) for the pairs, b +
+// 64 (w / 2) + j for an odd last one), and the diagonal's reciprocal to
+// dinv (0 when the diagonal is missing or not positive).  A chunk whose
+// segments hold more than NUM_STAGE entries (many duplicates of a few
+// nonzeros) is folded lane by lane from global memory instead.
+constexpr int NUM_TPB = 256, NUM_STAGE = 256;
+
+__global__ void __launch_bounds__(NUM_TPB)
+    k_coo_numeric_sell(int64_t nslices, const int32_t *__restrict__ sptr,
+                       const int32_t *__restrict__ srow0, const int32_t *__restrict__ row_ptr,
+                       const int32_t *__restrict__ jmap, const int32_t *__restrict__ perm,
+                       const double *__restrict__ v, const int32_t *__restrict__ diag_pos,
+                       int mode, double *__restrict__ val, double *__restrict__ sval,
+                       double *__restrict__ dinv) {
+  __shared__ double stage[NUM_TPB / 32][NUM_STAGE];
+  __shared__ int32_t rps[NUM_TPB / 32][33];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  double *st = stage[wl];
+  int32_t *rp = rps[wl];
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < nslices;
+       sl += nw) {
+    const int32_t r0 = srow0[sl], nr = srow0[sl + 1] - r0;
+    const int32_t b = sptr[sl], w = (sptr[sl + 1] - b) >> 5, np = w >> 1;
+    __syncwarp();
+    rp[lane] = row_ptr[r0 + min(lane, nr)];
+    if (lane == 0) rp[32] = row_ptr[r0 + nr];
+    const int32_t dp = lane < nr ? diag_pos[r0 + lane] : -1;
+    __syncwarp();
+    const int32_t P0 = rp[0], P1 = rp[nr];
+    for (int32_t c0 = P0; c0 < P1; c0 += 32) {
+      const int32_t p = c0 + lane;
+      const bool live = p < P1;
+      const int32_t cend = min(c0 + 32, P1);
+      const int32_t t0 = live ? jmap[p] : 0, t1 = live ? jmap[p + 1] : 0;
+      const int32_t T0 = __shfl_sync(FULL_MASK, t0, 0);
+      const int32_t TE = __shfl_sync(FULL_MASK, t1, cend - c0 - 1);
+      const int32_t L = TE - T0;
+      double sum = 0.0;
+      if (L <= NUM_STAGE) {
+        for (int32_t m = lane; m < L; m += 32) st[m] = __ldg(v + __ldg(perm + T0 + m));
+        __syncwarp();
+        if (live) {
+          sum = st[t0 - T0];
+          for (int32_t t = t0 + 1; t < t1; ++t) sum = __dadd_rn(sum, st[t - T0]);
+        }
+        __syncwarp();
+      } else if (live) {
+        sum = __ldg(v + __ldg(perm + t0));
+        for (int32_t t = t0 + 1; t < t1; ++t) sum = __dadd_rn(sum, __ldg(v + __ldg(perm + t)));
+      }
+      int lo = 0, hi = nr;  // the row of p: the last j with rp[j] <= p
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (rp[mid] <= p) lo = mid;
+        else hi = mid;
+      }
+      const int32_t dlo = __shfl_sync(FULL_MASK, dp, lo);  // that row's diagonal position
+      if (live) {
+        if (mode == GBS_ADD) sum = __dadd_rn(val[p], sum);
+        val[p] = sum;
+        const int32_t k = p - rp[lo];
+        sval[k < 2 * np ? b + 64 * (k >> 1) + 2 * lo + (k & 1) : b + 64 * np + lo] = sum;
+        if (p == dlo) dinv[r0 + lo] = (sum > 0.0) ? 1.0 / sum : 0.0;
+      }
+    }
+    if (lane < nr && dp < 0) dinv[r0 + lane] = 0.0;  // no diagonal entry
+  }
+}
+
 // Jacobi: dinv_r = 1 / a_rr; a missing or non-positive diagonal stores 0,
 // which the solves report as GBS_ERR_NOT_SPD for the system holding that row.
 __global__ void k_jacobi(int64_t nrows, const int32_t *__restrict__ diag_pos,
@@ -624,6 +703,16 @@ __global__ void k_jacobi(int64_t nrows, const int32_t *__restrict__ diag_pos,
 }
 
 int launch_set_values(gbs_mat A, const double *v, int mode, cudaStream_t s) {
+  if (A->sell_val && A->nslices > 0) {  // both layouts and D^-1 in one pass
+    k_coo_numeric_sell<<<grid_for(A->nslices * 32, NUM_TPB), NUM_TPB, 0, s>>>(
+        A->nslices, A->sell_ptr, A->sell_row0, A->row_ptr, A->jmap, A->perm, v, A->diag_pos,
+        mode, A->val, A->sell_val, A->dinv);
+    GBS_LAUNCHED(1);
+    A->values_set = true;
+    A->val32_valid = false;
+    A->values_version += 1;
+    return GBS_OK;
+  }
   if (A->nnz > 0) {
     k_coo_numeric<<<grid_for(A->nnz, 256), 256, 0, s>>>(A->nnz, A->jmap, A->perm, v, mode,
                                                         A->val);

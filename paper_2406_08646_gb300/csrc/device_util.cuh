@@ -109,11 +109,11 @@ __device__ __forceinline__ void block_sums(T (&v)[NV], T *s, T *p) {
 }
 
 // The phase kernels' block reduction: block_sums with s and p in one
-// scratch array of 4 nt + 512 values.
+// scratch array of NV (nt + 128) values (s first, then p).
 constexpr int BLOCK_SUMS_EXTRA = 512;  // p: 128 values per reduced value, up to 4
 template <typename T, int NV>
 __device__ __forceinline__ void block_reduce(T (&v)[NV], T *scratch) {
-  block_sums<T, NV>(v, scratch, scratch + 4 * blockDim.x);
+  block_sums<T, NV>(v, scratch, scratch + NV * blockDim.x);
 }
 
 // A hint to bring bytes [p, p + n) into L2: one bulk prefetch, which holds

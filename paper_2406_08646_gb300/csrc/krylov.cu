@@ -1395,7 +1395,7 @@ __device__ __forceinline__ void sr_update(const PcgArgs &a, double *red) {
 }
 
 __global__ void NS_ROWS k_sr_spmv(PcgArgs a) {
-  __shared__ double red[RED_SCRATCH];
+  __shared__ double red[RED_SCRATCH1];
   if (!trip_live(a)) return;
   stamp_phase(a, 1);
   sr_spmv(a, red);

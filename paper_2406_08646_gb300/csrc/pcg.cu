@@ -58,7 +58,7 @@ __global__ void GBS_ROWS_BOUNDS(L) k_pcg_setup(PcgArgs a) {
 
 template <bool REFINED, int L>
 __global__ void GBS_ROWS_BOUNDS(L) k_pcg_spmv(PcgArgs a) {
-  __shared__ double red[RED_SCRATCH];
+  __shared__ double red[RED_SCRATCH1];
   if (!trip_live(a)) return;
   stamp_phase(a, 1);
   phase_A<REFINED, L>(a, red);

@@ -40,8 +40,10 @@ enum { M_INNER = 0, M_XUPD = 1, M_START = 2 };
 constexpr int SLOT_STRIDE = 4;  // doubles per reduction slot
 constexpr int PHASE_TPB = 512;  // threads per CTA of every phase kernel
 // Shared scratch of the phase kernels' block reductions (NV <= 4 values per
-// thread and the lane partials, device_util.cuh's block_reduce).
+// thread and the lane partials, device_util.cuh's block_reduce); kernels
+// whose reductions carry one value need only RED_SCRATCH1.
 constexpr int RED_SCRATCH = 4 * PHASE_TPB + BLOCK_SUMS_EXTRA;
+constexpr int RED_SCRATCH1 = PHASE_TPB + BLOCK_SUMS_EXTRA / 4;
 static_assert(PHASE_TPB % 128 == 0 && PHASE_TPB >= 256, "block_sums needs 128 k threads");
 constexpr int SELL_MIN_CTAS = 4;  // sliced-ELL kernels: 4 CTAs (2048 threads) per SM
 
@@ -529,6 +531,7 @@ __device__ __forceinline__ void sell_rows(const int32_t *__restrict__ sptr,
 }
 
 // The row products of block b (rows [r0, r1) of table ta) with the plan's
+// kernel: L == 0 sliced ELL, else CSR-vector with L lanes per row.// The row products of block b (rows [r0, r1) of table ta) with the plan's
 // kernel: L == 0 sliced ELL, else CSR-vector with L lanes per row.
 template <typename T, int L, class F>
 __device__ __forceinline__ void row_products(const PcgArgs &a, int b, int r0, int r1,
