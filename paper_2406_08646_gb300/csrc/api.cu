@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "internal.cuh"
@@ -25,6 +26,52 @@ void set_error(const char *fmt, ...) {
 
 void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+// The library's memory pool of the current device, created on first use.
+static constexpr int kMaxPoolDevices = 256;
+static cudaMemPool_t g_pools[kMaxPoolDevices] = {};
+static std::mutex g_pool_mu;
+
+static int device_pool(cudaMemPool_t *out) {
+  int dev = 0;
+  GBS_TRY_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxPoolDevices) {
+    set_error("device ordinal %d out of range", dev);
+    return GBS_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    GBS_TRY_CUDA(cudaMemPoolCreate(&pool, &props));
+    uint64_t keep = POOL_KEEP_BYTES;
+    GBS_TRY_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    g_pools[dev] = pool;
+  }
+  *out = g_pools[dev];
+  return GBS_OK;
+}
+
+int dev_alloc_bytes(void **p, size_t bytes, cudaStream_t s) {
+  *p = nullptr;
+  cudaMemPool_t pool = nullptr;
+  GBS_TRY(device_pool(&pool));
+  const cudaError_t e = cudaMallocFromPoolAsync(p, bytes > 0 ? bytes : 16, pool, s);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    set_error("device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? GBS_ERR_ALLOC : GBS_ERR_CUDA;
+  }
+  return GBS_OK;
+}
+
+void dev_free(void *p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
 static constexpr int64_t kMaxIndex = 2147483647LL;
 
 void free_handle(gbs_mat A) {
@@ -32,14 +79,14 @@ void free_handle(gbs_mat A) {
   int cur = 0;
   cudaGetDevice(&cur);
   cudaSetDevice(A->device);
+  cudaDeviceSynchronize();  // the buffers may be in use on any stream
   drop_graphs(A);
   free_handle(A->At);
   void *dev[] = {A->row_ptr, A->col, A->val, A->val32, A->perm, A->jmap, A->diag_pos,
                  A->dinv, A->dinv32, A->r, A->p, A->q, A->r32, A->p32, A->q32, A->d32,
                  A->part, A->sys_cnt, A->st, A->ctl, A->call, A->cta_order,
                  A->kv, A->sys_row0};  // sys_slice0 lies inside sys_row0's block
-  for (void *p : dev)
-    if (p) cudaFree(p);
+  for (void *p : dev) dev_free(p, nullptr);
   free_table(A->ta);
   free_table(A->te);
   free_sell(A);
@@ -50,7 +97,9 @@ void free_handle(gbs_mat A) {
 
 // Default plan: everything automatic -- the row-product kernel chosen from
 // the matrix, one wave of CTAs per phase kernel, about one block per CTA.
-static int default_plan(gbs_mat A) { return build_plan(A, 0, 0, GBS_SPMV_AUTO, 0); }
+static int default_plan(gbs_mat A, cudaStream_t s) {
+  return build_plan(A, 0, 0, GBS_SPMV_AUTO, 0, s);
+}
 
 static int64_t max_system_rows(gbs_mat A, bool per_system) {
   if (!per_system) return A->nrows;
@@ -110,7 +159,11 @@ static int use_device(gbs_mat A) {
 static int create_common(gbs_mat *out, gbs_mat A, const int32_t *i, const int32_t *j,
                          const int64_t *coo_off_h, cudaStream_t s) {
   int st = symbolic(A, i, j, coo_off_h, s);
-  if (st == GBS_OK) st = default_plan(A);
+  if (st == GBS_OK) st = default_plan(A, s);
+  if (st == GBS_OK && cudaStreamSynchronize(s) != cudaSuccess) {
+    set_error("mat_create_coo: synchronising the stream failed");
+    st = GBS_ERR_CUDA;
+  }
   if (st != GBS_OK) {
     free_handle(A);
     return st;
@@ -376,7 +429,9 @@ int mat_set_plan(gbs_mat A, int32_t spmv_rows, int32_t update_rows, int32_t kern
   GBS_TRY(check_mat(A, "mat_set_plan"));
   GBS_TRY(use_device(A));
   GBS_TRY_CUDA(cudaDeviceSynchronize());  // the old tables may be in use
-  return build_plan(A, spmv_rows, update_rows, kernel, ctas_per_sm);
+  GBS_TRY(build_plan(A, spmv_rows, update_rows, kernel, ctas_per_sm, nullptr));
+  GBS_TRY_CUDA(cudaDeviceSynchronize());
+  return GBS_OK;
 }
 
 int mat_set_solver(gbs_mat A, int32_t solver) {
@@ -418,11 +473,11 @@ int mat_autotune(gbs_mat A, void *stream) {
                           {512, 1024, sk, 0}, {0, 0, sk, 4},     {256, 2048, sk, 0},
                           {0, 0, sk, 2},      {1024, 4096, sk, 0}};
   double *b = nullptr, *x = nullptr;
-  GBS_TRY_CUDA(cudaMalloc(&b, sizeof(double) * A->nrows));
-  GBS_TRY_CUDA(cudaMalloc(&x, sizeof(double) * A->nrows));
+  GBS_TRY(dev_alloc(&b, A->nrows, s));
+  GBS_TRY(dev_alloc(&x, A->nrows, s));
   // b = A * 1 (any nonzero right-hand side will do)
   std::vector<double> ones(A->nrows, 1.0);
-  cudaMemcpy(x, ones.data(), sizeof(double) * A->nrows, cudaMemcpyHostToDevice);
+  cudaMemcpyAsync(x, ones.data(), sizeof(double) * A->nrows, cudaMemcpyHostToDevice, s);
   ksp_opts o;
   ksp_opts_default(&o);
   o.rtol = 0.0;
@@ -437,7 +492,7 @@ int mat_autotune(gbs_mat A, void *stream) {
   float best = 1e30f;
   int st = GBS_OK;
   for (const auto &c : cands) {
-    if (build_plan(A, c[0], c[1], c[2], c[3]) != GBS_OK) continue;
+    if (build_plan(A, c[0], c[1], c[2], c[3], s) != GBS_OK) continue;
     if (launch_spmv(A, x, b, s) != GBS_OK) continue;
     if (solve(A, b, x, o, false, s) != GBS_OK) continue;  // warm-up (and graph build)
     cudaEventRecord(e0, s);
@@ -457,13 +512,15 @@ int mat_autotune(gbs_mat A, void *stream) {
   A->trips_counted = true;  // the timed solves' results are never read
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  cudaFree(b);
-  cudaFree(x);
+  dev_free(b, s);
+  dev_free(x, s);
   if (st != GBS_OK) {
     set_error("mat_autotune: a timed run failed");
     return st;
   }
-  return build_plan(A, best_plan[0], best_plan[1], best_plan[2], best_plan[3]);
+  GBS_TRY(build_plan(A, best_plan[0], best_plan[1], best_plan[2], best_plan[3], s));
+  GBS_TRY_CUDA(cudaStreamSynchronize(s));
+  return GBS_OK;
 }
 
 int mat_destroy(gbs_mat A) {
@@ -497,7 +554,7 @@ int vec_create_coo(int64_t n, int64_t ncoo, const int32_t *i, void *stream, gbs_
   int32_t *zeros = nullptr;
   int st = GBS_OK;
   if (ncoo > 0) {
-    if (cudaMalloc(&zeros, sizeof(int32_t) * ncoo) != cudaSuccess ||
+    if (dev_alloc(&zeros, ncoo, s) != GBS_OK ||
         cudaMemsetAsync(zeros, 0, sizeof(int32_t) * ncoo, s) != cudaSuccess) {
       set_error("vec_create_coo: allocating the column indices failed");
       st = GBS_ERR_ALLOC;
@@ -518,7 +575,7 @@ int vec_create_coo(int64_t n, int64_t ncoo, const int32_t *i, void *stream, gbs_
       else free_handle(A);
     }
   }
-  if (zeros) cudaFree(zeros);
+  dev_free(zeros, s);
   if (st != GBS_OK) {
     delete V;
     return st;

@@ -367,15 +367,23 @@ __global__ void k_seg_write(const uint64_t *keys, int64_t n, const uint32_t *fla
   }
 }
 
+// Columns, diagonal positions and the largest |col - row| (capped at 2^30,
+// into *span): the sliced copy stores 16-bit column offsets when it is
+// below 2^15.
 __global__ void k_csr_cols(const uint64_t *ukey, int64_t nnz, int64_t ncols, int32_t *col,
-                           int32_t *diag_pos) {
+                           int32_t *diag_pos, int32_t *span) {
+  int32_t m = 0;
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < nnz;
        s += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t k = ukey[s];
     const int64_t r = (int64_t)(k / (uint64_t)ncols), c = (int64_t)(k % (uint64_t)ncols);
     col[s] = (int32_t)c;
     if (r == c) diag_pos[r] = (int32_t)s;
+    const int64_t d = c - r, ad = d < 0 ? -d : d;
+    m = max(m, (int32_t)(ad > (1 << 30) ? (1 << 30) : ad));
   }
+  m = (int32_t)__reduce_max_sync(FULL_MASK, (unsigned)m);
+  if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(span, m);
 }
 
 // row_ptr[r] = first unique key >= r * ncols, for r in [0, nrows].
@@ -424,7 +432,7 @@ int symbolic(gbs_mat A, const int32_t *i, const int32_t *j, const int64_t *coo_o
   // host mirrors read back after each synchronisation
   struct Ctl {
     uint32_t nkept, nnz;
-    int32_t err, maxrow;
+    int32_t err, maxrow, span, pad;
   } hc{};
   Ctl *dctl = nullptr;
 
@@ -444,10 +452,10 @@ int symbolic(gbs_mat A, const int32_t *i, const int32_t *j, const int64_t *coo_o
   } while (0)
 
   {
-    SYM_CUDA(cudaMallocAsync(&dctl, sizeof(Ctl), s));
+    SYM_TRY(dev_alloc(&dctl, 1, s));
     SYM_CUDA(cudaMemsetAsync(dctl, 0, sizeof(Ctl), s));
     if (coo_off_h) {
-      SYM_CUDA(cudaMallocAsync(&d_off, sizeof(int64_t) * 2 * (A->nsys + 1), s));
+      SYM_TRY(dev_alloc(&d_off, 2 * (A->nsys + 1), s));
       SYM_CUDA(cudaMemcpyAsync(d_off, coo_off_h, sizeof(int64_t) * (A->nsys + 1),
                                cudaMemcpyHostToDevice, s));
       SYM_CUDA(cudaMemcpyAsync(d_off + A->nsys + 1, A->row_off_h.data(),
@@ -456,9 +464,9 @@ int symbolic(gbs_mat A, const int32_t *i, const int32_t *j, const int64_t *coo_o
       ka.row_off = d_off + A->nsys + 1;
     }
     const int64_t nflag = std::max<int64_t>(ncoo, 1);
-    SYM_CUDA(cudaMallocAsync(&flags, sizeof(uint32_t) * nflag, s));
-    SYM_CUDA(cudaMallocAsync(&dsc, sizeof(uint32_t) * nflag, s));
-    SYM_CUDA(cudaMallocAsync(&scan_tmp, sizeof(uint32_t) * scan_tmp_words(nflag), s));
+    SYM_TRY(dev_alloc(&flags, nflag, s));
+    SYM_TRY(dev_alloc(&dsc, nflag, s));
+    SYM_TRY(dev_alloc(&scan_tmp, scan_tmp_words(nflag), s));
 
     // 1. keep flags, positions, nkept
     if (ncoo > 0) {
@@ -476,10 +484,10 @@ int symbolic(gbs_mat A, const int32_t *i, const int32_t *j, const int64_t *coo_o
     const int64_t nkept = hc.nkept;
     A->nkept = nkept;
     const int64_t nk = std::max<int64_t>(nkept, 1);
-    SYM_CUDA(cudaMallocAsync(&kA, sizeof(uint64_t) * nk, s));
-    SYM_CUDA(cudaMallocAsync(&kB, sizeof(uint64_t) * nk, s));
-    SYM_CUDA(cudaMallocAsync(&vA, sizeof(uint32_t) * nk, s));
-    SYM_CUDA(cudaMalloc(&vB, sizeof(uint32_t) * nk));  // may become perm
+    SYM_TRY(dev_alloc(&kA, nk, s));
+    SYM_TRY(dev_alloc(&kB, nk, s));
+    SYM_TRY(dev_alloc(&vA, nk, s));
+    SYM_TRY(dev_alloc(&vB, nk, s));  // becomes perm
     if (ncoo > 0) {
       k_compact<<<grid_for(ncoo, 256), 256, 0, s>>>(ka, dsc, kA, vA);
       GBS_LAUNCHED(1);
@@ -501,9 +509,9 @@ int symbolic(gbs_mat A, const int32_t *i, const int32_t *j, const int64_t *coo_o
     const int64_t ntiles = (nkept + RS_TILE - 1) / RS_TILE;
     if (ntiles > 0 && passes > 0) {
       const int64_t ncount = 256 * ntiles;
-      SYM_CUDA(cudaMallocAsync(&counts, sizeof(uint32_t) * ncount, s));
+      SYM_TRY(dev_alloc(&counts, ncount, s));
       uint32_t *ctmp = nullptr;
-      SYM_CUDA(cudaMallocAsync(&ctmp, sizeof(uint32_t) * scan_tmp_words(ncount), s));
+      SYM_TRY(dev_alloc(&ctmp, scan_tmp_words(ncount), s));
       uint64_t *kin = kA, *kout = kB;
       uint32_t *vin = vA, *vout = vB;
       for (int pass = 0; pass < passes; ++pass) {
@@ -512,7 +520,7 @@ int symbolic(gbs_mat A, const int32_t *i, const int32_t *j, const int64_t *coo_o
         GBS_LAUNCHED(1);
         status = exclusive_scan(counts, counts, ncount, ctmp, nullptr, s);
         if (status != GBS_OK) {
-          cudaFreeAsync(ctmp, s);
+          dev_free(ctmp, s);
           goto cleanup;
         }
         k_radix_scatter<<<(unsigned)ntiles, RS_T, sizeof(RadixShared), s>>>(
@@ -521,11 +529,11 @@ int symbolic(gbs_mat A, const int32_t *i, const int32_t *j, const int64_t *coo_o
         std::swap(kin, kout);
         std::swap(vin, vout);
       }
-      cudaFreeAsync(ctmp, s);
+      dev_free(ctmp, s);
       // sorted data is in kin / vin; make kA / vB hold it
       if (kin != kA) std::swap(kA, kB);
       if (vin != vB) {
-        // vin == vA: copy into vB (the cudaMalloc'd buffer that becomes perm)
+        // vin == vA: copy into vB (the buffer that becomes perm)
         SYM_CUDA(cudaMemcpyAsync(vB, vA, sizeof(uint32_t) * nkept, cudaMemcpyDeviceToDevice, s));
       }
     } else if (nkept > 0) {
@@ -543,16 +551,16 @@ int symbolic(gbs_mat A, const int32_t *i, const int32_t *j, const int64_t *coo_o
     const int64_t nnz = hc.nnz;
     A->nnz = nnz;
     const int64_t nz1 = std::max<int64_t>(nnz, 1);
-    SYM_CUDA(cudaMalloc(&A->jmap, sizeof(int32_t) * (nnz + 1)));
-    SYM_CUDA(cudaMalloc(&A->col, sizeof(int32_t) * nz1));
-    SYM_CUDA(cudaMalloc(&A->val, sizeof(double) * nz1));
-    SYM_CUDA(cudaMalloc(&A->row_ptr, sizeof(int32_t) * (A->nrows + 1)));
-    SYM_CUDA(cudaMalloc(&A->diag_pos, sizeof(int32_t) * std::max<int64_t>(A->nrows, 1)));
-    SYM_CUDA(cudaMalloc(&A->dinv, sizeof(double) * std::max<int64_t>(A->nrows, 1)));
+    SYM_TRY(dev_alloc(&A->jmap, nnz + 1, s));
+    SYM_TRY(dev_alloc(&A->col, nz1, s));
+    SYM_TRY(dev_alloc(&A->val, nz1, s));
+    SYM_TRY(dev_alloc(&A->row_ptr, A->nrows + 1, s));
+    SYM_TRY(dev_alloc(&A->diag_pos, std::max<int64_t>(A->nrows, 1), s));
+    SYM_TRY(dev_alloc(&A->dinv, std::max<int64_t>(A->nrows, 1), s));
     SYM_CUDA(cudaMemsetAsync(A->val, 0, sizeof(double) * nz1, s));
     SYM_CUDA(cudaMemsetAsync(A->diag_pos, 0xff, sizeof(int32_t) * std::max<int64_t>(A->nrows, 1), s));
     SYM_CUDA(cudaMemsetAsync(A->dinv, 0, sizeof(double) * std::max<int64_t>(A->nrows, 1), s));
-    SYM_CUDA(cudaMallocAsync(&ukey, sizeof(uint64_t) * nz1, s));
+    SYM_TRY(dev_alloc(&ukey, nz1, s));
     A->perm = (int32_t *)vB;
     vB = nullptr;
     {
@@ -564,7 +572,8 @@ int symbolic(gbs_mat A, const int32_t *i, const int32_t *j, const int64_t *coo_o
       GBS_LAUNCHED(1);
     }
     if (nnz > 0) {
-      k_csr_cols<<<grid_for(nnz, 256), 256, 0, s>>>(ukey, nnz, A->ncols, A->col, A->diag_pos);
+      k_csr_cols<<<grid_for(nnz, 256), 256, 0, s>>>(ukey, nnz, A->ncols, A->col, A->diag_pos,
+                                                    &dctl->span);
       GBS_LAUNCHED(1);
     }
     k_row_ptr<<<grid_for(A->nrows + 1, 256), 256, 0, s>>>(ukey, nnz, A->ncols, A->nrows,
@@ -574,20 +583,13 @@ int symbolic(gbs_mat A, const int32_t *i, const int32_t *j, const int64_t *coo_o
     SYM_CUDA(cudaMemcpyAsync(&hc, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     SYM_CUDA(cudaStreamSynchronize(s));
     A->max_row_nnz = hc.maxrow;
+    A->col_span = hc.span;
   }
 
 cleanup:
-  if (dctl) cudaFreeAsync(dctl, s);
-  if (d_off) cudaFreeAsync(d_off, s);
-  if (flags) cudaFreeAsync(flags, s);
-  if (dsc) cudaFreeAsync(dsc, s);
-  if (scan_tmp) cudaFreeAsync(scan_tmp, s);
-  if (kA) cudaFreeAsync(kA, s);
-  if (kB) cudaFreeAsync(kB, s);
-  if (vA) cudaFreeAsync(vA, s);
-  if (counts) cudaFreeAsync(counts, s);
-  if (ukey) cudaFreeAsync(ukey, s);
-  if (vB) cudaFree(vB);
+  for (void *p : {(void *)dctl, (void *)d_off, (void *)flags, (void *)dsc, (void *)scan_tmp,
+                  (void *)kA, (void *)kB, (void *)vA, (void *)counts, (void *)ukey, (void *)vB})
+    dev_free(p, s);
   cudaStreamSynchronize(s);
   return status;
 #undef SYM_CUDA
@@ -598,95 +600,48 @@ cleanup:
 
 // One thread per nonzero: a_p = v[perm[jmap[p]]] + v[perm[jmap[p]+1]] + ...
 // in increasing COO index order (Sec. 5: each thread accumulates into a single
-// nonzero, no atomics).
+// nonzero, no atomics).  A thread takes two nonzeros per pass and loads each
+// segment's COO indices NUM_BATCH at a time before their values, so its two
+// chains of dependent loads (segment offsets -> COO indices -> values) are in
+// flight together rather than one term after the other.
+constexpr int NUM_BATCH = 4;
+
 __global__ void k_coo_numeric(int64_t nnz, const int32_t *__restrict__ jmap,
                               const int32_t *__restrict__ perm, const double *__restrict__ v,
                               int mode, double *__restrict__ val) {
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t t0 = __ldg(jmap + p), t1 = __ldg(jmap + p + 1);
-    double sum = __ldg(v + __ldg(perm + t0));
-    for (int32_t t = t0 + 1; t < t1; ++t) sum = __dadd_rn(sum, __ldg(v + __ldg(perm + t)));
-    val[p] = (mode == GBS_ADD) ? __dadd_rn(val[p], sum) : sum;
-  }
-}
-
-// The numeric stage straight into both layouts, one warp per 32-row slice of
-// the sliced-ELL copy.  The slice's nonzeros are a contiguous CSR range; the
-// warp takes them 32 at a time (lane l: nonzero p = c0 + l): it loads their
-// segment offsets jmap[p] (coalesced), then the chunk's whole run of perm
-// entries [jmap[c0], jmap[c0 + 32]) (contiguous, coalesced) and the v values
-// they point to (all gathers in flight together) into shared memory, and
-// lane l folds its segment from there in increasing COO index with plain
-// adds -- the same sums, bit for bit, as one thread per nonzero.  The sum
-// goes to val[p] (CSR) and to the nonzero's place in the sliced copy (entry
-// k of the slice's row j: b + 64 (k / 2) + 2 j + (k % 2) for the pairs, b +
-// 64 (w / 2) + j for an odd last one), and the diagonal's reciprocal to
-// dinv (0 when the diagonal is missing or not positive).  A chunk whose
-// segments hold more than NUM_STAGE entries (many duplicates of a few
-// nonzeros) is folded lane by lane from global memory instead.
-constexpr int NUM_TPB = 256, NUM_STAGE = 256;
-
-__global__ void __launch_bounds__(NUM_TPB)
-    k_coo_numeric_sell(int64_t nslices, const int32_t *__restrict__ sptr,
-                       const int32_t *__restrict__ srow0, const int32_t *__restrict__ row_ptr,
-                       const int32_t *__restrict__ jmap, const int32_t *__restrict__ perm,
-                       const double *__restrict__ v, const int32_t *__restrict__ diag_pos,
-                       int mode, double *__restrict__ val, double *__restrict__ sval,
-                       double *__restrict__ dinv) {
-  __shared__ double stage[NUM_TPB / 32][NUM_STAGE];
-  __shared__ int32_t rps[NUM_TPB / 32][33];
-  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-  double *st = stage[wl];
-  int32_t *rp = rps[wl];
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < nslices;
-       sl += nw) {
-    const int32_t r0 = srow0[sl], nr = srow0[sl + 1] - r0;
-    const int32_t b = sptr[sl], w = (sptr[sl + 1] - b) >> 5, np = w >> 1;
-    __syncwarp();
-    rp[lane] = row_ptr[r0 + min(lane, nr)];
-    if (lane == 0) rp[32] = row_ptr[r0 + nr];
-    const int32_t dp = lane < nr ? diag_pos[r0 + lane] : -1;
-    __syncwarp();
-    const int32_t P0 = rp[0], P1 = rp[nr];
-    for (int32_t c0 = P0; c0 < P1; c0 += 32) {
-      const int32_t p = c0 + lane;
-      const bool live = p < P1;
-      const int32_t cend = min(c0 + 32, P1);
-      const int32_t t0 = live ? jmap[p] : 0, t1 = live ? jmap[p + 1] : 0;
-      const int32_t T0 = __shfl_sync(FULL_MASK, t0, 0);
-      const int32_t TE = __shfl_sync(FULL_MASK, t1, cend - c0 - 1);
-      const int32_t L = TE - T0;
-      double sum = 0.0;
-      if (L <= NUM_STAGE) {
-        for (int32_t m = lane; m < L; m += 32) st[m] = __ldg(v + __ldg(perm + T0 + m));
-        __syncwarp();
-        if (live) {
-          sum = st[t0 - T0];
-          for (int32_t t = t0 + 1; t < t1; ++t) sum = __dadd_rn(sum, st[t - T0]);
-        }
-        __syncwarp();
-      } else if (live) {
-        sum = __ldg(v + __ldg(perm + t0));
-        for (int32_t t = t0 + 1; t < t1; ++t) sum = __dadd_rn(sum, __ldg(v + __ldg(perm + t)));
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += 2 * stride) {
+    const int64_t p2 = p + stride;
+    const bool two = p2 < nnz;
+    int32_t ta = __ldg(jmap + p);
+    const int32_t ea = __ldg(jmap + p + 1);
+    int32_t tb = two ? __ldg(jmap + p2) : 0;
+    const int32_t eb = two ? __ldg(jmap + p2 + 1) : 0;
+    const int32_t fa = ta, fb = tb;
+    double sa = 0.0, sb = 0.0;
+    while (ta < ea || tb < eb) {
+      int32_t ka[NUM_BATCH], kb[NUM_BATCH];
+      double xa[NUM_BATCH], xb[NUM_BATCH];
+#pragma unroll
+      for (int u = 0; u < NUM_BATCH; ++u) {
+        ka[u] = ta + u < ea ? __ldg(perm + ta + u) : 0;
+        kb[u] = tb + u < eb ? __ldg(perm + tb + u) : 0;
       }
-      int lo = 0, hi = nr;  // the row of p: the last j with rp[j] <= p
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (rp[mid] <= p) lo = mid;
-        else hi = mid;
+#pragma unroll
+      for (int u = 0; u < NUM_BATCH; ++u) {
+        xa[u] = ta + u < ea ? __ldg(v + ka[u]) : 0.0;
+        xb[u] = tb + u < eb ? __ldg(v + kb[u]) : 0.0;
       }
-      const int32_t dlo = __shfl_sync(FULL_MASK, dp, lo);  // that row's diagonal position
-      if (live) {
-        if (mode == GBS_ADD) sum = __dadd_rn(val[p], sum);
-        val[p] = sum;
-        const int32_t k = p - rp[lo];
-        sval[k < 2 * np ? b + 64 * (k >> 1) + 2 * lo + (k & 1) : b + 64 * np + lo] = sum;
-        if (p == dlo) dinv[r0 + lo] = (sum > 0.0) ? 1.0 / sum : 0.0;
+#pragma unroll
+      for (int u = 0; u < NUM_BATCH; ++u) {  // in increasing COO index: plain adds
+        if (ta + u < ea) sa = (ta + u == fa) ? xa[u] : __dadd_rn(sa, xa[u]);
+        if (tb + u < eb) sb = (tb + u == fb) ? xb[u] : __dadd_rn(sb, xb[u]);
       }
+      ta += NUM_BATCH;
+      tb += NUM_BATCH;
     }
-    if (lane < nr && dp < 0) dinv[r0 + lane] = 0.0;  // no diagonal entry
+    val[p] = (mode == GBS_ADD) ? __dadd_rn(val[p], sa) : sa;
+    if (two) val[p2] = (mode == GBS_ADD) ? __dadd_rn(val[p2], sb) : sb;
   }
 }
 
@@ -703,18 +658,8 @@ __global__ void k_jacobi(int64_t nrows, const int32_t *__restrict__ diag_pos,
 }
 
 int launch_set_values(gbs_mat A, const double *v, int mode, cudaStream_t s) {
-  if (A->sell_val && A->nslices > 0) {  // both layouts and D^-1 in one pass
-    k_coo_numeric_sell<<<grid_for(A->nslices * 32, NUM_TPB), NUM_TPB, 0, s>>>(
-        A->nslices, A->sell_ptr, A->sell_row0, A->row_ptr, A->jmap, A->perm, v, A->diag_pos,
-        mode, A->val, A->sell_val, A->dinv);
-    GBS_LAUNCHED(1);
-    A->values_set = true;
-    A->val32_valid = false;
-    A->values_version += 1;
-    return GBS_OK;
-  }
   if (A->nnz > 0) {
-    k_coo_numeric<<<grid_for(A->nnz, 256), 256, 0, s>>>(A->nnz, A->jmap, A->perm, v, mode,
+    k_coo_numeric<<<grid_for((A->nnz + 1) / 2, 256), 256, 0, s>>>(A->nnz, A->jmap, A->perm, v, mode,
                                                         A->val);
     GBS_LAUNCHED(1);
   }
@@ -742,8 +687,8 @@ __global__ void k_to_fp32(int64_t nnz, const double *__restrict__ val, float *__
 
 int launch_to_fp32(gbs_mat A, cudaStream_t s) {
   if (!A->val32) {
-    GBS_TRY_CUDA(cudaMalloc(&A->val32, sizeof(float) * std::max<int64_t>(A->nnz, 1)));
-    GBS_TRY_CUDA(cudaMalloc(&A->dinv32, sizeof(float) * std::max<int64_t>(A->nrows, 1)));
+    GBS_TRY(dev_alloc(&A->val32, std::max<int64_t>(A->nnz, 1), s));
+    GBS_TRY(dev_alloc(&A->dinv32, std::max<int64_t>(A->nrows, 1), s));
   }
   k_to_fp32<<<grid_for(std::max(A->nnz, A->nrows), 256), 256, 0, s>>>(
       A->nnz, A->val, A->val32, A->nrows, A->dinv, A->dinv32);
@@ -770,7 +715,7 @@ __global__ void k_vec_scatter(int64_t n, const int32_t *__restrict__ row_ptr,
 // numeric kernel, INSERT into val), then the scatter into y.
 int launch_vec_set_values(gbs_mat A, const double *v, int mode, double *y, cudaStream_t s) {
   if (A->nnz > 0) {
-    k_coo_numeric<<<grid_for(A->nnz, 256), 256, 0, s>>>(A->nnz, A->jmap, A->perm, v, GBS_INSERT,
+    k_coo_numeric<<<grid_for((A->nnz + 1) / 2, 256), 256, 0, s>>>(A->nnz, A->jmap, A->perm, v, GBS_INSERT,
                                                         A->val);
     GBS_LAUNCHED(1);
   }

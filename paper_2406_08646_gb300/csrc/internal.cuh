@@ -15,6 +15,24 @@ namespace gbs {
 void set_error(const char *fmt, ...);
 void count_launches(int64_t n);
 
+// ---------------------------------------------------------------- device memory
+// Every device buffer of the library (except the allocation-free solve's
+// static array) comes from one stream-ordered memory pool per device that
+// keeps up to POOL_KEEP_BYTES of freed memory for reuse, so that creating
+// and destroying handles of the same sizes does not map and unmap device
+// pages each time.  dev_alloc orders the allocation on stream s (GBS_ERR_ALLOC
+// on failure, *p = nullptr); dev_free returns the block on stream s (nullptr:
+// the legacy default stream).  A buffer used on other streams than s must be
+// ordered after s's allocation (the calls that allocate handle buffers
+// synchronise s before returning).
+constexpr uint64_t POOL_KEEP_BYTES = 32ull << 30;
+int dev_alloc_bytes(void **p, size_t bytes, cudaStream_t s);
+void dev_free(void *p, cudaStream_t s);
+template <typename T>
+int dev_alloc(T **p, size_t n, cudaStream_t s) {
+  return dev_alloc_bytes(reinterpret_cast<void **>(p), n * sizeof(T), s);
+}
+
 #define GBS_TRY_CUDA(call)                                                       \
   do {                                                                           \
     cudaError_t e_ = (call);                                                     \
@@ -124,6 +142,7 @@ struct gbs_mat_s {
   int64_t nrows = 0, ncols = 0, ncoo = 0, nkept = 0, nnz = 0;
   int32_t nsys = 1;
   int32_t max_row_nnz = 0;
+  int32_t col_span = 0;         // largest |col - row| of the pattern (capped at 2^30)
   bool batched = false;
   bool values_set = false;
   bool val32_valid = false;
@@ -194,9 +213,9 @@ struct gbs_mat_s {
 
 namespace gbs {
 
-int ensure_solver_workspace(gbs_mat A, bool refined);
+int ensure_solver_workspace(gbs_mat A, bool refined, cudaStream_t s);
 int build_plan(gbs_mat A, int32_t spmv_rows, int32_t update_rows, int32_t lanes,
-               int32_t ctas_per_sm);
+               int32_t ctas_per_sm, cudaStream_t s);
 void free_table(TableDev &t);
 void drop_graphs(gbs_mat A);
 int launch_spmv(gbs_mat A, const double *x, double *y, cudaStream_t s);
@@ -220,7 +239,7 @@ int auto_lanes(int64_t nnz, int64_t nrows);
 int phase_occupancy(int lanes, int *rows, int *upd);
 int32_t stream_matrix(gbs_mat A, int bytes_per_entry);
 void free_sell(gbs_mat A);
-int sell_shape(gbs_mat A);
+int sell_shape(gbs_mat A, cudaStream_t s);
 int sell_build(gbs_mat A, cudaStream_t s);
 int sell_values(gbs_mat A, cudaStream_t s);
 int sell_values32(gbs_mat A, cudaStream_t s);

@@ -1477,11 +1477,10 @@ __global__ void k_system_nnz_off(int32_t nsys, const int64_t *__restrict__ row_o
 }
 
 namespace {
-struct DevBuf {  // device scratch freed on every exit path
+struct DevBuf {  // device scratch returned to the pool on every exit path
   void *p = nullptr;
-  ~DevBuf() {
-    if (p) cudaFree(p);
-  }
+  cudaStream_t s = nullptr;
+  ~DevBuf() { dev_free(p, s); }
 };
 unsigned grid_rows(int64_t n) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 1 << 16));
@@ -1491,11 +1490,12 @@ unsigned grid_rows(int64_t n) {
 static int build_transpose(gbs_mat A, cudaStream_t s) {
   const int32_t ns = A->nsys;
   DevBuf off, ti, tj, cnt;
+  off.s = ti.s = tj.s = cnt.s = s;
   const size_t m = (size_t)std::max<int64_t>(A->nnz, 1);
-  GBS_TRY_CUDA(cudaMalloc(&off.p, sizeof(int64_t) * (ns + 1)));
-  GBS_TRY_CUDA(cudaMalloc(&cnt.p, sizeof(int64_t) * (ns + 1)));
-  GBS_TRY_CUDA(cudaMalloc(&ti.p, sizeof(int32_t) * m));
-  GBS_TRY_CUDA(cudaMalloc(&tj.p, sizeof(int32_t) * m));
+  GBS_TRY(dev_alloc_bytes(&off.p, sizeof(int64_t) * (ns + 1), s));
+  GBS_TRY(dev_alloc_bytes(&cnt.p, sizeof(int64_t) * (ns + 1), s));
+  GBS_TRY(dev_alloc_bytes(&ti.p, sizeof(int32_t) * m, s));
+  GBS_TRY(dev_alloc_bytes(&tj.p, sizeof(int32_t) * m, s));
   GBS_TRY_CUDA(cudaMemcpyAsync(off.p, A->row_off_h.data(), sizeof(int64_t) * (ns + 1),
                                cudaMemcpyHostToDevice, s));
   std::vector<int64_t> coo_off(ns + 1, 0);
@@ -1523,6 +1523,7 @@ static int build_transpose(gbs_mat A, cudaStream_t s) {
   int st = symbolic(T, (const int32_t *)ti.p, (const int32_t *)tj.p,
                     A->batched ? coo_off.data() : nullptr, s);
   if (st == GBS_OK) st = sell_build(T, s);
+  if (st == GBS_OK && cudaStreamSynchronize(s) != cudaSuccess) st = GBS_ERR_CUDA;
   if (st == GBS_OK && (T->nnz != A->nnz || T->nslices != A->nslices)) {
     set_error("transpose: %lld nonzeros in %lld slices, expected %lld in %lld",
               (long long)T->nnz, (long long)T->nslices, (long long)A->nnz,
@@ -1542,9 +1543,11 @@ static int build_transpose(gbs_mat A, cudaStream_t s) {
 // with A's current values.
 static int ensure_krylov(gbs_mat A, bool transpose, cudaStream_t s) {
   GBS_TRY(sell_build(A, s));
-  if (!A->kv)
-    GBS_TRY_CUDA(cudaMalloc(&A->kv, sizeof(double) * KRYLOV_NVEC *
-                                        (size_t)std::max<int64_t>(A->nrows, 1)));
+  bool grew = false;
+  if (!A->kv) {
+    GBS_TRY(dev_alloc(&A->kv, KRYLOV_NVEC * (size_t)std::max<int64_t>(A->nrows, 1), s));
+    grew = true;
+  }
   if (!A->sys_row0) {
     std::vector<int32_t> r0(A->nsys + 1), s0(A->nsys + 1);
     for (int32_t q = 0; q <= A->nsys; ++q) {
@@ -1552,14 +1555,16 @@ static int ensure_krylov(gbs_mat A, bool transpose, cudaStream_t s) {
       s0[q] = A->sell_slice0_h[q];
     }
     int32_t *d = nullptr;
-    GBS_TRY_CUDA(cudaMalloc(&d, sizeof(int32_t) * 2 * (A->nsys + 1)));
+    GBS_TRY(dev_alloc(&d, 2 * ((size_t)A->nsys + 1), s));
     A->sys_row0 = d;
     A->sys_slice0 = d + A->nsys + 1;
-    GBS_TRY_CUDA(cudaMemcpy(A->sys_row0, r0.data(), sizeof(int32_t) * (A->nsys + 1),
-                            cudaMemcpyHostToDevice));
-    GBS_TRY_CUDA(cudaMemcpy(A->sys_slice0, s0.data(), sizeof(int32_t) * (A->nsys + 1),
-                            cudaMemcpyHostToDevice));
+    GBS_TRY_CUDA(cudaMemcpyAsync(A->sys_row0, r0.data(), sizeof(int32_t) * (A->nsys + 1),
+                                 cudaMemcpyHostToDevice, s));
+    GBS_TRY_CUDA(cudaMemcpyAsync(A->sys_slice0, s0.data(), sizeof(int32_t) * (A->nsys + 1),
+                                 cudaMemcpyHostToDevice, s));
+    grew = true;
   }
+  if (grew) GBS_TRY_CUDA(cudaStreamSynchronize(s));
   if (transpose) {
     if (!A->At) GBS_TRY(build_transpose(A, s));
     if (A->at_version != A->values_version) {
@@ -1574,7 +1579,7 @@ int solve_krylov(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool 
                  cudaStream_t s) {
   const bool bicg = o.method == GBS_KSP_BICG, pipe = o.method == GBS_KSP_PIPECG,
              sr = o.method == GBS_KSP_CGSR;
-  GBS_TRY(ensure_solver_workspace(A, false));
+  GBS_TRY(ensure_solver_workspace(A, false, s));
   GBS_TRY(ensure_krylov(A, bicg, s));
   A->last_count = per_system ? A->nsys : 1;
   A->last_ensemble = !per_system;

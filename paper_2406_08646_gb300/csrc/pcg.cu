@@ -161,36 +161,49 @@ void drop_graphs(gbs_mat A) {
       }
 }
 
-int ensure_solver_workspace(gbs_mat A, bool refined) {
+// The solver's buffers, allocated on the first solve that needs them (on
+// stream s; the stream is synchronised after an allocation, so the buffers
+// are ready for any stream).
+int ensure_solver_workspace(gbs_mat A, bool refined, cudaStream_t s) {
   const size_t n = (size_t)std::max<int64_t>(A->nrows, 1);
+  bool grew = false;
   if (!A->r) {
-    GBS_TRY_CUDA(cudaMalloc(&A->r, sizeof(double) * n));
-    GBS_TRY_CUDA(cudaMalloc(&A->p, sizeof(double) * n));
-    GBS_TRY_CUDA(cudaMalloc(&A->q, sizeof(double) * n));
-    GBS_TRY_CUDA(cudaMalloc(&A->sys_cnt, sizeof(unsigned) * A->nsys));
-    GBS_TRY_CUDA(cudaMalloc(&A->st, sizeof(SysState) * A->nsys));
-    GBS_TRY_CUDA(cudaMalloc(&A->ctl, sizeof(DevCtl)));
-    GBS_TRY_CUDA(cudaMalloc(&A->call, sizeof(CallArgs)));
+    GBS_TRY(dev_alloc(&A->r, n, s));
+    GBS_TRY(dev_alloc(&A->p, n, s));
+    GBS_TRY(dev_alloc(&A->q, n, s));
+    GBS_TRY(dev_alloc(&A->sys_cnt, A->nsys, s));
+    GBS_TRY(dev_alloc(&A->st, A->nsys, s));
+    GBS_TRY(dev_alloc(&A->ctl, 1, s));
+    GBS_TRY(dev_alloc(&A->call, 1, s));
     GBS_TRY_CUDA(cudaMallocHost(&A->st_host, sizeof(SysState) * A->nsys));
-    GBS_TRY_CUDA(cudaMemset(A->sys_cnt, 0, sizeof(unsigned) * A->nsys));
-    GBS_TRY_CUDA(cudaMemset(A->ctl, 0, sizeof(DevCtl)));
+    GBS_TRY_CUDA(cudaMemsetAsync(A->sys_cnt, 0, sizeof(unsigned) * A->nsys, s));
+    GBS_TRY_CUDA(cudaMemsetAsync(A->ctl, 0, sizeof(DevCtl), s));
+    grew = true;
   }
   if (refined && !A->r32) {
-    GBS_TRY_CUDA(cudaMalloc(&A->r32, sizeof(float) * n));
-    GBS_TRY_CUDA(cudaMalloc(&A->p32, sizeof(float) * n));
-    GBS_TRY_CUDA(cudaMalloc(&A->q32, sizeof(float) * n));
-    GBS_TRY_CUDA(cudaMalloc(&A->d32, sizeof(float) * n));
+    GBS_TRY(dev_alloc(&A->r32, n, s));
+    GBS_TRY(dev_alloc(&A->p32, n, s));
+    GBS_TRY(dev_alloc(&A->q32, n, s));
+    GBS_TRY(dev_alloc(&A->d32, n, s));
     drop_graphs(A);  // a cached refined graph would hold null FP32 pointers
+    grew = true;
   }
-  const int64_t need = A->ta.nslots + A->te.nslots + 1;
+  // reduction slots: table A's, table E's, and a third region the size of
+  // table E's for partial sums of E's slots
+  const int64_t need = A->ta.nslots + 2 * A->te.nslots + 1;
   if (A->part_cap < need) {
-    if (A->part) cudaFree(A->part);
+    if (A->part) {
+      GBS_TRY_CUDA(cudaStreamSynchronize(s));
+      dev_free(A->part, s);
+    }
     A->part = nullptr;
     A->part_cap = 0;
-    GBS_TRY_CUDA(cudaMalloc(&A->part, sizeof(double) * SLOT_STRIDE * need));
+    GBS_TRY(dev_alloc(&A->part, SLOT_STRIDE * (size_t)need, s));
     A->part_cap = need;
     drop_graphs(A);  // cached graphs hold the old pointer
+    grew = true;
   }
+  if (grew) GBS_TRY_CUDA(cudaStreamSynchronize(s));
   return GBS_OK;
 }
 
@@ -507,7 +520,7 @@ static int launch_cluster(gbs_mat A, const PcgArgs &a, int32_t nclusters, cudaSt
 int solve(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool per_system,
           cudaStream_t s) {
   const bool refined = o.precision == GBS_FP32_REFINED;
-  GBS_TRY(ensure_solver_workspace(A, refined));
+  GBS_TRY(ensure_solver_workspace(A, refined, s));
   if (refined && !A->val32_valid) GBS_TRY(launch_to_fp32(A, s));
   A->last_count = per_system ? A->nsys : 1;
   A->last_ensemble = !per_system;

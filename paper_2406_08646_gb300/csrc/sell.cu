@@ -65,20 +65,6 @@ __global__ void k_sell_fill(int64_t nslices, const int32_t *__restrict__ sptr,
   }
 }
 
-// Largest |col - row| over the matrix (the 16-bit offsets need < 2^15).
-__global__ void k_col_span(int64_t nrows, const int32_t *__restrict__ row_ptr,
-                           const int32_t *__restrict__ col, int32_t *__restrict__ span) {
-  int32_t m = 0;
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows;
-       r += (int64_t)gridDim.x * blockDim.x)
-    for (int32_t p = row_ptr[r]; p < row_ptr[r + 1]; ++p) {
-      const int64_t d = (int64_t)col[p] - r, ad = d < 0 ? -d : d;
-      m = max(m, (int32_t)(ad > (1 << 30) ? (1 << 30) : ad));
-    }
-  m = (int32_t)__reduce_max_sync(0xffffffffu, (unsigned)m);
-  if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(span, m);
-}
-
 // FP32 values of the sliced copy, RN(FP64 values), padding stays 0.
 __global__ void k_sell_to_fp32(int64_t n, const double *__restrict__ v, float *__restrict__ v32) {
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
@@ -89,7 +75,7 @@ __global__ void k_sell_to_fp32(int64_t n, const double *__restrict__ v, float *_
 void free_sell(gbs_mat A) {
   for (void *p : {(void *)A->sell_ptr, (void *)A->sell_row0, (void *)A->sell_col,
                   (void *)A->sell_off16, (void *)A->sell_val, (void *)A->sell_val32})
-    if (p) cudaFree(p);
+    dev_free(p, nullptr);
   A->sell_ptr = nullptr;
   A->sell_row0 = nullptr;
   A->sell_col = nullptr;
@@ -100,8 +86,9 @@ void free_sell(gbs_mat A) {
 }
 
 // Slice table and padded size (no entries yet); when the padded size reaches
-// 2^31 only the size is recorded.  Idempotent.
-int sell_shape(gbs_mat A) {
+// 2^31 only the size is recorded.  Idempotent.  Synchronises s once (the
+// slice widths decide the sizes).
+int sell_shape(gbs_mat A, cudaStream_t st) {
   if (A->sell_row0) return GBS_OK;
   std::vector<int32_t> srow0;
   for (int32_t q = 0; q < A->nsys; ++q)
@@ -109,16 +96,18 @@ int sell_shape(gbs_mat A) {
   const int64_t ns = (int64_t)srow0.size();
   srow0.push_back((int32_t)A->nrows);
   std::vector<int32_t> w(std::max<int64_t>(ns, 1), 0);
-  GBS_TRY_CUDA(cudaMalloc(&A->sell_row0, sizeof(int32_t) * (ns + 1)));
-  GBS_TRY_CUDA(cudaMemcpy(A->sell_row0, srow0.data(), sizeof(int32_t) * (ns + 1),
-                          cudaMemcpyHostToDevice));
+  GBS_TRY(dev_alloc(&A->sell_row0, ns + 1, st));
+  GBS_TRY_CUDA(cudaMemcpyAsync(A->sell_row0, srow0.data(), sizeof(int32_t) * (ns + 1),
+                               cudaMemcpyHostToDevice, st));
   if (ns > 0) {
     int32_t *dw = nullptr;
-    GBS_TRY_CUDA(cudaMalloc(&dw, sizeof(int32_t) * ns));
-    k_slice_width<<<grid_of(ns, 256), 256>>>(ns, A->sell_row0, A->row_ptr, dw);
+    GBS_TRY(dev_alloc(&dw, ns, st));
+    k_slice_width<<<grid_of(ns, 256), 256, 0, st>>>(ns, A->sell_row0, A->row_ptr, dw);
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpy(w.data(), dw, sizeof(int32_t) * ns, cudaMemcpyDeviceToHost);
-    cudaFree(dw);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(w.data(), dw, sizeof(int32_t) * ns, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dev_free(dw, st);
     count_launches(1);
     GBS_TRY_CUDA(e);
   }
@@ -129,9 +118,9 @@ int sell_shape(gbs_mat A) {
   if (total > 2147483647LL) return GBS_OK;  // too large for 32-bit offsets: no copy
   std::vector<int32_t> sptr(ns + 1, 0);
   for (int64_t s = 0; s < ns; ++s) sptr[s + 1] = sptr[s] + 32 * w[s];
-  GBS_TRY_CUDA(cudaMalloc(&A->sell_ptr, sizeof(int32_t) * (ns + 1)));
-  GBS_TRY_CUDA(cudaMemcpy(A->sell_ptr, sptr.data(), sizeof(int32_t) * (ns + 1),
-                          cudaMemcpyHostToDevice));
+  GBS_TRY(dev_alloc(&A->sell_ptr, ns + 1, st));
+  GBS_TRY_CUDA(cudaMemcpyAsync(A->sell_ptr, sptr.data(), sizeof(int32_t) * (ns + 1),
+                               cudaMemcpyHostToDevice, st));
   A->sell_slice0_h.assign(A->nsys + 1, 0);
   for (int32_t q = 0; q < A->nsys; ++q)
     A->sell_slice0_h[q + 1] =
@@ -139,35 +128,22 @@ int sell_shape(gbs_mat A) {
   return GBS_OK;
 }
 
-// Columns and (if the values are set) FP64 values of the sliced copy.
+// Columns and (if the values are set) FP64 values of the sliced copy.  The
+// columns are stored as 16-bit offsets col - row when every column lies within
+// 2^15 - 1 of its row (the symbolic stage measured the span), else as 32-bit
+// columns.
 int sell_build(gbs_mat A, cudaStream_t s) {
-  GBS_TRY(sell_shape(A));
+  GBS_TRY(sell_shape(A, s));
   if (!A->sell_ptr) {
     set_error("the sliced-ELL copy would hold %lld entries (limit 2^31 - 1)",
               (long long)A->sell_nnz);
     return GBS_ERR_ARG;
   }
-  if (!A->sell_col) {
+  if (!A->sell_val) {
     const size_t m = (size_t)std::max<int64_t>(A->sell_nnz, 1);
-    GBS_TRY_CUDA(cudaMalloc(&A->sell_col, sizeof(int32_t) * m));
-    GBS_TRY_CUDA(cudaMalloc(&A->sell_val, sizeof(double) * m));
-    // 16-bit column offsets when every column lies within 2^15 - 1 of its row
-    int32_t span = 0;
-    if (A->nrows > 0) {
-      int32_t *d = nullptr;
-      GBS_TRY_CUDA(cudaMalloc(&d, sizeof(int32_t)));
-      cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int32_t), s);
-      if (e == cudaSuccess) {
-        k_col_span<<<grid_of(A->nrows, 256), 256, 0, s>>>(A->nrows, A->row_ptr, A->col, d);
-        count_launches(1);
-        e = cudaGetLastError();
-      }
-      if (e == cudaSuccess) e = cudaMemcpyAsync(&span, d, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-      cudaFree(d);
-      GBS_TRY_CUDA(e);
-    }
-    if (span <= 32767) GBS_TRY_CUDA(cudaMalloc(&A->sell_off16, sizeof(int16_t) * m));
+    GBS_TRY(dev_alloc(&A->sell_val, m, s));
+    if (A->col_span <= 32767) GBS_TRY(dev_alloc(&A->sell_off16, m, s));
+    else GBS_TRY(dev_alloc(&A->sell_col, m, s));
     if (A->nslices > 0) {
       k_sell_fill<double><<<grid_of(A->nslices * 32, 256), 256, 0, s>>>(
           A->nslices, A->sell_ptr, A->sell_row0, A->row_ptr, A->col, (const double *)nullptr,
@@ -193,8 +169,7 @@ int sell_values(gbs_mat A, cudaStream_t s) {
 
 int sell_values32(gbs_mat A, cudaStream_t s) {
   if (!A->sell_val) return GBS_OK;
-  if (!A->sell_val32)
-    GBS_TRY_CUDA(cudaMalloc(&A->sell_val32, sizeof(float) * std::max<int64_t>(A->sell_nnz, 1)));
+  if (!A->sell_val32) GBS_TRY(dev_alloc(&A->sell_val32, std::max<int64_t>(A->sell_nnz, 1), s));
   if (A->sell_nnz > 0) {
     k_sell_to_fp32<<<grid_of(A->sell_nnz, 256), 256, 0, s>>>(A->sell_nnz, A->sell_val,
                                                              A->sell_val32);

@@ -90,8 +90,7 @@ int auto_lanes(int64_t nnz, int64_t nrows) {
 }
 
 void free_table(TableDev &t) {
-  for (int32_t *p : {t.row0, t.sys, t.sys_blk0, t.sys_slot0, t.slice0})
-    if (p) cudaFree(p);
+  dev_free(t.row0, nullptr);  // one buffer holds all five arrays (build_table)
   t.row0 = t.sys = t.sys_blk0 = t.sys_slot0 = t.slice0 = nullptr;
   t.nblocks = 0;
   t.grid = 0;
@@ -104,7 +103,7 @@ void free_table(TableDev &t) {
 // is a whole number of the 32-row slices of the sliced-ELL layout (slice0).
 // The kernels walking the table run min(blocks, cap_per_sm x SMs) CTAs;
 // system s owns min(blocks_s, grid) reduction slots.
-static int build_table(gbs_mat A, int32_t R, int32_t cap_per_sm, TableDev &t) {
+static int build_table(gbs_mat A, int32_t R, int32_t cap_per_sm, TableDev &t, cudaStream_t st) {
   std::vector<int32_t> row0, sys, sb0(A->nsys + 1, 0), sl0;
   int32_t slices = 0;
   for (int32_t q = 0; q < A->nsys; ++q) {
@@ -128,19 +127,23 @@ static int build_table(gbs_mat A, int32_t R, int32_t cap_per_sm, TableDev &t) {
   for (int32_t q = 0; q < A->nsys; ++q)
     so[q + 1] = so[q] + (int32_t)std::min<int64_t>(sb0[q + 1] - sb0[q], grid);
   free_table(t);
-  GBS_TRY_CUDA(cudaMalloc(&t.row0, sizeof(int32_t) * (nb + 1)));
-  GBS_TRY_CUDA(cudaMalloc(&t.sys, sizeof(int32_t) * std::max(nb, 1)));
-  GBS_TRY_CUDA(cudaMalloc(&t.sys_blk0, sizeof(int32_t) * (A->nsys + 1)));
-  GBS_TRY_CUDA(cudaMalloc(&t.sys_slot0, sizeof(int32_t) * (A->nsys + 1)));
-  GBS_TRY_CUDA(cudaMalloc(&t.slice0, sizeof(int32_t) * (nb + 1)));
-  GBS_TRY_CUDA(cudaMemcpy(t.row0, row0.data(), sizeof(int32_t) * (nb + 1), cudaMemcpyHostToDevice));
-  GBS_TRY_CUDA(cudaMemcpy(t.slice0, sl0.data(), sizeof(int32_t) * (nb + 1), cudaMemcpyHostToDevice));
-  if (nb > 0)
-    GBS_TRY_CUDA(cudaMemcpy(t.sys, sys.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice));
-  GBS_TRY_CUDA(cudaMemcpy(t.sys_blk0, sb0.data(), sizeof(int32_t) * (A->nsys + 1),
-                          cudaMemcpyHostToDevice));
-  GBS_TRY_CUDA(cudaMemcpy(t.sys_slot0, so.data(), sizeof(int32_t) * (A->nsys + 1),
-                          cudaMemcpyHostToDevice));
+  // one buffer: row0 (nb + 1), slice0 (nb + 1), sys (nb), sys_blk0, sys_slot0 (nsys + 1 each)
+  const size_t tot = 3 * (size_t)nb + 2 + 2 * ((size_t)A->nsys + 1);
+  std::vector<int32_t> h;
+  h.reserve(tot);
+  h.insert(h.end(), row0.begin(), row0.end());
+  h.insert(h.end(), sl0.begin(), sl0.end());
+  h.insert(h.end(), sys.begin(), sys.end());
+  h.insert(h.end(), sb0.begin(), sb0.end());
+  h.insert(h.end(), so.begin(), so.end());
+  int32_t *d = nullptr;
+  GBS_TRY(dev_alloc(&d, tot, st));
+  GBS_TRY_CUDA(cudaMemcpyAsync(d, h.data(), sizeof(int32_t) * tot, cudaMemcpyHostToDevice, st));
+  t.row0 = d;
+  t.slice0 = d + nb + 1;
+  t.sys = d + 2 * (size_t)nb + 2;
+  t.sys_blk0 = t.sys + nb;
+  t.sys_slot0 = t.sys_blk0 + A->nsys + 1;
   t.sys_blk0_h = sb0;
   t.nblocks = nb;
   t.grid = (int32_t)grid;
@@ -158,18 +161,26 @@ __global__ void k_system_nnz(int32_t nsys, const int32_t *__restrict__ row_ptr,
 
 // Systems in decreasing row count (ties by index): the per-CTA solver hands
 // them to CTAs in this order, so the longest solves start first.  Also the
-// largest system's rows and nonzeros (the solver choice uses them).
-static int build_cta_order(gbs_mat A) {
+// largest system's rows and nonzeros (the solver choice uses them; a batch's
+// per-system counts are read back, which synchronises st).
+static int build_cta_order(gbs_mat A, cudaStream_t st) {
   std::vector<int32_t> ord(A->nsys), noff(A->nsys + 1, 0);
-  int32_t *d = nullptr;
-  GBS_TRY_CUDA(cudaMalloc(&d, sizeof(int32_t) * (A->nsys + 1)));
-  k_system_nnz<<<(A->nsys + 256) / 256, 256>>>(A->nsys, A->row_ptr, A->ta.row0, A->ta.sys_blk0, d);
-  cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess)
-    e = cudaMemcpy(noff.data(), d, sizeof(int32_t) * (A->nsys + 1), cudaMemcpyDeviceToHost);
-  cudaFree(d);
-  count_launches(1);
-  GBS_TRY_CUDA(e);
+  if (A->nsys == 1) {
+    noff[1] = (int32_t)A->nnz;
+  } else {
+    int32_t *d = nullptr;
+    GBS_TRY(dev_alloc(&d, A->nsys + 1, st));
+    k_system_nnz<<<(A->nsys + 256) / 256, 256, 0, st>>>(A->nsys, A->row_ptr, A->ta.row0,
+                                                        A->ta.sys_blk0, d);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(noff.data(), d, sizeof(int32_t) * (A->nsys + 1), cudaMemcpyDeviceToHost,
+                          st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dev_free(d, st);
+    count_launches(1);
+    GBS_TRY_CUDA(e);
+  }
   A->max_sys_rows = A->max_sys_nnz = 0;
   for (int32_t q = 0; q < A->nsys; ++q) {
     ord[q] = q;
@@ -179,9 +190,10 @@ static int build_cta_order(gbs_mat A) {
   std::stable_sort(ord.begin(), ord.end(), [&](int32_t u, int32_t v) {
     return A->row_off_h[u + 1] - A->row_off_h[u] > A->row_off_h[v + 1] - A->row_off_h[v];
   });
-  if (!A->cta_order) GBS_TRY_CUDA(cudaMalloc(&A->cta_order, sizeof(int32_t) * A->nsys));
-  GBS_TRY_CUDA(cudaMemcpy(A->cta_order, ord.data(), sizeof(int32_t) * A->nsys,
-                          cudaMemcpyHostToDevice));
+  if (!A->cta_order) GBS_TRY(dev_alloc(&A->cta_order, A->nsys, st));
+  GBS_TRY_CUDA(cudaMemcpyAsync(A->cta_order, ord.data(), sizeof(int32_t) * A->nsys,
+                               cudaMemcpyHostToDevice, st));
+  GBS_TRY_CUDA(cudaStreamSynchronize(st));  // ord is a local vector
   return GBS_OK;
 }
 
@@ -189,8 +201,9 @@ static int build_cta_order(gbs_mat A) {
 // multiples of 32), the row-product kernel (GBS_SPMV_AUTO, GBS_SPMV_SELL or
 // CSR-vector lanes per row) and a cap of CTAs per SM on the grids (0: as many
 // as fit on an SM at once, so each phase kernel runs in one wave).  Cached graphs are dropped: they bake in the tables and grids.
-// Synchronises the device when it builds the sliced copy.
-int build_plan(gbs_mat A, int32_t Ra, int32_t Re, int32_t kernel, int32_t ctas_per_sm) {
+// Work is ordered on stream st; the host copies of the tables are synchronous.
+int build_plan(gbs_mat A, int32_t Ra, int32_t Re, int32_t kernel, int32_t ctas_per_sm,
+               cudaStream_t st) {
   const bool bad_ra = Ra != 0 && (Ra < 32 || Ra > 65536 || (Ra % 32) != 0);
   const bool bad_re = Re != 0 && (Re < 32 || Re > 65536 || (Re % 32) != 0);
   if (bad_ra || bad_re ||
@@ -206,15 +219,12 @@ int build_plan(gbs_mat A, int32_t Ra, int32_t Re, int32_t kernel, int32_t ctas_p
   }
   drop_graphs(A);
   if (kernel == GBS_SPMV_AUTO) {
-    GBS_TRY(sell_shape(A));
+    GBS_TRY(sell_shape(A, st));
     kernel = (A->sell_ptr && (double)A->sell_nnz <= 1.2 * (double)A->nnz)
                  ? GBS_SPMV_SELL
                  : auto_lanes(A->nnz, A->nrows);
   }
-  if (kernel == GBS_SPMV_SELL) {
-    GBS_TRY(sell_build(A, nullptr));
-    GBS_TRY_CUDA(cudaDeviceSynchronize());
-  }
+  if (kernel == GBS_SPMV_SELL) GBS_TRY(sell_build(A, st));
   // grids: one wave of the phase kernels unless capped explicitly; automatic
   // block sizes give about one block per CTA of that wave (at least one row
   // per thread, so every warp of a CTA has rows)
@@ -229,9 +239,9 @@ int build_plan(gbs_mat A, int32_t Ra, int32_t Re, int32_t kernel, int32_t ctas_p
   };
   if (Ra == 0) Ra = auto_rows(cap_a);
   if (Re == 0) Re = auto_rows(cap_e);
-  GBS_TRY(build_table(A, Ra, cap_a, A->ta));
-  GBS_TRY(build_table(A, Re, cap_e, A->te));
-  GBS_TRY(build_cta_order(A));
+  GBS_TRY(build_table(A, Ra, cap_a, A->ta, st));
+  GBS_TRY(build_table(A, Re, cap_e, A->te, st));
+  GBS_TRY(build_cta_order(A, st));
   A->Ra = Ra;
   A->Re = Re;
   A->lanes = kernel;
