@@ -358,6 +358,14 @@ int build_loop_graph(gbs_mat A, const LoopPlan &P, PcgArgs a, cudaGraphExec_t *o
   ms.width = (size_t)A->nsys;
   e = cudaGraphAddMemsetNode(&n_cnt, g, &n_ctl, 1, &ms);
   if (e != cudaSuccess) return fail("memset");
+  // every system's state starts cleared (a system without rows is never
+  // visited by a kernel and reports OK with no iterations)
+  cudaGraphNode_t n_st;
+  ms.dst = A->st;
+  ms.width = sizeof(SysState) * (size_t)A->nsys / 4;
+  e = cudaGraphAddMemsetNode(&n_st, g, &n_cnt, 1, &ms);
+  if (e != cudaSuccess) return fail("memset");
+  n_cnt = n_st;
   cudaKernelNodeParams kp;
   cudaGraphNode_t prev = n_cnt;
   for (int k = 0; k < P.npre; ++k) {
@@ -571,6 +579,7 @@ int run_loop(gbs_mat A, const LoopPlan &P, int kind, const PcgArgs &a, const dou
   if (o.host_loop) {
     GBS_TRY_CUDA(cudaMemsetAsync(A->ctl, 0, sizeof(DevCtl), s));
     GBS_TRY_CUDA(cudaMemsetAsync(A->sys_cnt, 0, sizeof(unsigned) * A->nsys, s));
+    GBS_TRY_CUDA(cudaMemsetAsync(A->st, 0, sizeof(SysState) * A->nsys, s));
     GBS_TRY(put_call(A->call, call_args(b, x, o), s));
     return run_loop_stepped(P, a, A->ta.grid, A->te.grid, max_trips_for(o), A->ctl, s);
   }
