@@ -418,24 +418,7 @@ static unsigned grid_for(int64_t n, int tpb) {
   return (unsigned)g;
 }
 
-// Symbolic stage.  coo_off_h (host, nsys+1) is non-null for batched handles;
-// A->row_off_h, nrows, ncols, ncoo, nsys are set by the caller.
-int symbolic(gbs_mat A, const int32_t *i, const int32_t *j, const int64_t *coo_off_h,
-             cudaStream_t s) {
-  const int64_t ncoo = A->ncoo;
-  KeepArgs ka{i, j, ncoo, A->nrows, A->ncols, nullptr, nullptr, A->nsys};
-  int64_t *d_off = nullptr;
-  uint32_t *flags = nullptr, *scan_tmp = nullptr, *dsc = nullptr;
-  uint64_t *kA = nullptr, *kB = nullptr, *ukey = nullptr;
-  uint32_t *vA = nullptr, *vB = nullptr, *counts = nullptr;
-  int status = GBS_OK;
-  // host mirrors read back after each synchronisation
-  struct Ctl {
-    uint32_t nkept, nnz;
-    int32_t err, maxrow, span, pad;
-  } hc{};
-  Ctl *dctl = nullptr;
-
+// Error exits of the symbolic stages: set status and jump to cleanup.
 #define SYM_CUDA(call)                                                            \
   do {                                                                            \
     cudaError_t e_ = (call);                                                      \
@@ -450,6 +433,370 @@ int symbolic(gbs_mat A, const int32_t *i, const int32_t *j, const int64_t *coo_o
     status = (call);                                                              \
     if (status != GBS_OK) goto cleanup;                                           \
   } while (0)
+
+// ------------------------------------------------------------------ row-bucketed symbolic stage
+//
+// The symbolic stage for patterns whose rows hold at most ROW_SORT_CTA COO
+// entries (finite-element, stencil and graph matrices): no global sort.
+//   1. per-row counts of the kept entries (warp-aggregated atomics: one
+//      atomic per distinct row in a warp);
+//   2. their exclusive scan -> each row's range of the kept entries;
+//   3. every kept entry placed in its row's range as the 64-bit key
+//      (j << 32) | k (the order inside a row depends on atomic timing);
+//   4. each row sorted by that key (a warp's register bitonic sort up to
+//      ROW_SORT_WARP entries, a CTA's shared-memory one up to ROW_SORT_CTA):
+//      the keys are distinct, so the result is the same on every run, and it
+//      is the order of the radix path -- rows ascending, columns ascending,
+//      equal (i, j) by increasing COO index; the low halves are perm, and
+//      each row's distinct columns are counted;
+//   5. the scan of those counts is row_ptr (and nnz), and one pass writes
+//      col, jmap and the diagonal positions.
+// Traffic: about 56 bytes per kept entry, against about 140 for the 5-pass
+// radix sort of 40-bit keys.  A longer row sends the pattern to the radix
+// path.
+constexpr int ROW_SORT_WARP = 64, ROW_SORT_CTA = 4096, ROW_SORT_TPB = 512;
+
+// The lanes in `active` that share `key` add their count to cnt[key] with one
+// atomic; returns the old value, and in rank each lane's position among them.
+__device__ __forceinline__ uint32_t warp_agg_add(uint32_t *cnt, uint32_t key, unsigned active,
+                                                 uint32_t &rank) {
+  const int lane = threadIdx.x & 31;
+  const unsigned peers = __match_any_sync(active, key);
+  const int leader = __ffs(peers) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(cnt + key, (uint32_t)__popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  rank = (uint32_t)__popc(peers & ((1u << lane) - 1u));
+  return base;
+}
+
+// mode 0: count the kept entries per row (and flag out-of-range indices);
+// mode 1: place each at rstart[row] + its slot as (j << 32) | k.
+template <int MODE>
+__global__ void k_row_bucket(KeepArgs a, uint32_t *cnt, const uint32_t *__restrict__ rstart,
+                             uint64_t *keys, int32_t *err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < a.ncoo;
+       base += nw * 32) {
+    const int64_t k = base + lane;
+    int64_t gi = 0, gj = 0;
+    bool bad = false;
+    const bool keep = k < a.ncoo && keep_entry(a, k, gi, gj, bad);
+    if (MODE == 0 && bad) atomicExch(err, GBS_ERR_INDEX);
+    const unsigned active = __ballot_sync(FULL_MASK, keep);
+    if (keep) {
+      uint32_t rank;
+      const uint32_t b = warp_agg_add(cnt, (uint32_t)gi, active, rank);
+      if (MODE == 1)
+        keys[rstart[gi] + b + rank] = ((uint64_t)(uint32_t)gj << 32) | (uint32_t)k;
+    }
+  }
+}
+
+// Ascending bitonic sort of 64 keys held two per lane (element 2 lane + h).
+__device__ __forceinline__ void warp_sort64(uint64_t &a0, uint64_t &a1) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 2; k <= 64; k <<= 1) {
+    const bool asc = ((2 * lane) & k) == 0;
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j == 1) {
+        const uint64_t lo = a0 < a1 ? a0 : a1, hi = a0 < a1 ? a1 : a0;
+        a0 = asc ? lo : hi;
+        a1 = asc ? hi : lo;
+      } else {
+        const int lj = j >> 1;
+        const uint64_t b0 = __shfl_xor_sync(FULL_MASK, a0, lj);
+        const uint64_t b1 = __shfl_xor_sync(FULL_MASK, a1, lj);
+        const bool keep_min = ((lane & lj) == 0) == asc;
+        a0 = keep_min ? (a0 < b0 ? a0 : b0) : (a0 < b0 ? b0 : a0);
+        a1 = keep_min ? (a1 < b1 ? a1 : b1) : (a1 < b1 ? b1 : a1);
+      }
+    }
+  }
+}
+
+// Rows of at most ROW_SORT_WARP entries, one warp each: sort, write back the
+// keys and perm (their low halves), count the distinct columns into ucnt.
+// Longer rows go to long_rows (count in *nlong) for k_row_sort_cta.
+__global__ void k_row_sort_warp(int64_t nrows, const uint32_t *__restrict__ rstart,
+                                uint64_t *__restrict__ keys, int32_t *__restrict__ perm,
+                                uint32_t *__restrict__ ucnt, int32_t *__restrict__ long_rows,
+                                uint32_t *nlong) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrows; r += nw) {
+    const uint32_t s0 = rstart[r];
+    const int len = (int)(rstart[r + 1] - s0);
+    if (len > ROW_SORT_WARP) {
+      if (lane == 0) long_rows[atomicAdd(nlong, 1u)] = (int32_t)r;
+      continue;
+    }
+    const int q0 = 2 * lane, q1 = 2 * lane + 1;
+    uint64_t a0 = q0 < len ? keys[s0 + q0] : ~0ull, a1 = q1 < len ? keys[s0 + q1] : ~0ull;
+    warp_sort64(a0, a1);
+    const uint32_t j0 = (uint32_t)(a0 >> 32), j1 = (uint32_t)(a1 >> 32);
+    const uint32_t jprev = __shfl_up_sync(FULL_MASK, j1, 1);
+    const bool h0 = q0 < len && (lane == 0 || j0 != jprev), h1 = q1 < len && j1 != j0;
+    if (q0 < len) {
+      keys[s0 + q0] = a0;
+      perm[s0 + q0] = (int32_t)(uint32_t)a0;
+    }
+    if (q1 < len) {
+      keys[s0 + q1] = a1;
+      perm[s0 + q1] = (int32_t)(uint32_t)a1;
+    }
+    const int u = __popc(__ballot_sync(FULL_MASK, h0)) + __popc(__ballot_sync(FULL_MASK, h1));
+    if (lane == 0) ucnt[r] = (uint32_t)u;
+  }
+}
+
+// The long rows (ROW_SORT_WARP < len <= ROW_SORT_CTA), one CTA each: a
+// bitonic sort in shared memory, then as k_row_sort_warp.
+__global__ void __launch_bounds__(ROW_SORT_TPB)
+    k_row_sort_cta(const uint32_t *__restrict__ rstart, uint64_t *__restrict__ keys,
+                   int32_t *__restrict__ perm, uint32_t *__restrict__ ucnt,
+                   const int32_t *__restrict__ long_rows, const uint32_t *nlong) {
+  __shared__ uint64_t sk[ROW_SORT_CTA];
+  __shared__ int cnt_w[ROW_SORT_TPB / 32];
+  const uint32_t nl = *nlong;
+  for (uint32_t li = blockIdx.x; li < nl; li += gridDim.x) {
+    const int32_t r = long_rows[li];
+    const uint32_t s0 = rstart[r];
+    const int len = (int)(rstart[r + 1] - s0);
+    int m = 1;
+    while (m < len) m <<= 1;
+    for (int q = threadIdx.x; q < m; q += blockDim.x) sk[q] = q < len ? keys[s0 + q] : ~0ull;
+    __syncthreads();
+    for (int k = 2; k <= m; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int q = threadIdx.x; q < m; q += blockDim.x) {
+          const int pq = q ^ j;
+          if (pq > q) {
+            const uint64_t x = sk[q], y = sk[pq];
+            const bool asc = (q & k) == 0;
+            if ((x > y) == asc) {
+              sk[q] = y;
+              sk[pq] = x;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    int u = 0;
+    for (int q = threadIdx.x; q < len; q += blockDim.x) {
+      const uint64_t x = sk[q];
+      keys[s0 + q] = x;
+      perm[s0 + q] = (int32_t)(uint32_t)x;
+      u += (q == 0 || (x >> 32) != (sk[q - 1] >> 32)) ? 1 : 0;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) u += __shfl_xor_sync(FULL_MASK, u, off);
+    if ((threadIdx.x & 31) == 0) cnt_w[threadIdx.x >> 5] = u;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int t = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += cnt_w[w];
+      ucnt[r] = (uint32_t)t;
+    }
+    __syncthreads();
+  }
+}
+
+// col, jmap and diag_pos from the sorted rows, one warp per row; the
+// largest |col - row| into *span.
+__global__ void k_row_emit(int64_t nrows, const uint32_t *__restrict__ rstart,
+                           const uint64_t *__restrict__ keys, const int32_t *__restrict__ row_ptr,
+                           int32_t *__restrict__ jmap, int32_t *__restrict__ col,
+                           int32_t *__restrict__ diag_pos, int32_t *span) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int32_t m = 0;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrows; r += nw) {
+    const uint32_t s0 = rstart[r];
+    const int len = (int)(rstart[r + 1] - s0);
+    int run = row_ptr[r];
+    uint32_t prev = 0;  // the column of the chunk's previous entry (lane 31 of the last chunk)
+    for (int c = 0; c < len; c += 32) {
+      const int q = c + lane;
+      const bool valid = q < len;
+      const uint32_t jq = valid ? (uint32_t)(keys[s0 + q] >> 32) : 0u;
+      const uint32_t jl = __shfl_up_sync(FULL_MASK, jq, 1);
+      const uint32_t before = lane == 0 ? prev : jl;
+      const bool head = valid && (q == 0 || jq != before);
+      const unsigned hb = __ballot_sync(FULL_MASK, head);
+      if (head) {
+        const int u = run + __popc(hb & ((1u << lane) - 1u));
+        jmap[u] = (int32_t)(s0 + q);
+        col[u] = (int32_t)jq;
+        if ((int64_t)jq == r) diag_pos[r] = u;
+        const int64_t d = (int64_t)jq - r, ad = d < 0 ? -d : d;
+        m = max(m, (int32_t)(ad > (1 << 30) ? (1 << 30) : ad));
+      }
+      run += __popc(hb);
+      prev = __shfl_sync(FULL_MASK, jq, 31);
+    }
+  }
+  m = (int32_t)__reduce_max_sync(FULL_MASK, (unsigned)m);
+  if (lane == 0 && m > 0) atomicMax(span, m);
+}
+
+// Symbolic stage.  coo_off_h (host, nsys+1) is non-null for batched handles;
+// A->row_off_h, nrows, ncols, ncoo, nsys are set by the caller.  The
+// row-bucketed path runs unless a row holds more than ROW_SORT_CTA entries.
+static int symbolic_radix(gbs_mat A, const int32_t *i, const int32_t *j,
+                          const int64_t *coo_off_h, cudaStream_t s);
+static int symbolic_rows(gbs_mat A, const int32_t *i, const int32_t *j,
+                         const int64_t *coo_off_h, cudaStream_t s, bool *done);
+
+int symbolic(gbs_mat A, const int32_t *i, const int32_t *j, const int64_t *coo_off_h,
+             cudaStream_t s) {
+  bool done = false;
+  const int st = symbolic_rows(A, i, j, coo_off_h, s, &done);
+  if (st != GBS_OK || done) return st;
+  return symbolic_radix(A, i, j, coo_off_h, s);
+}
+
+static int symbolic_rows(gbs_mat A, const int32_t *i, const int32_t *j,
+                         const int64_t *coo_off_h, cudaStream_t s, bool *done) {
+  *done = false;
+  const int64_t ncoo = A->ncoo, n = A->nrows;
+  KeepArgs ka{i, j, ncoo, A->nrows, A->ncols, nullptr, nullptr, A->nsys};
+  int64_t *d_off = nullptr;
+  uint32_t *cnt = nullptr, *rstart = nullptr, *scan_tmp = nullptr, *ucnt = nullptr;
+  uint64_t *keys = nullptr;
+  int32_t *perm = nullptr, *long_rows = nullptr;
+  int status = GBS_OK;
+  struct Ctl {
+    uint32_t nkept, nnz;
+    int32_t err, maxcnt, maxrow, span;
+    uint32_t nlong, pad;
+  } hc{};
+  Ctl *dctl = nullptr;
+  const int64_t n1 = std::max<int64_t>(n, 1);
+  const int64_t nwarp_rows = std::max<int64_t>(n, 1) * 32;
+
+  {
+    SYM_TRY(dev_alloc(&dctl, 1, s));
+    SYM_CUDA(cudaMemsetAsync(dctl, 0, sizeof(Ctl), s));
+    if (coo_off_h) {
+      SYM_TRY(dev_alloc(&d_off, 2 * (A->nsys + 1), s));
+      SYM_CUDA(cudaMemcpyAsync(d_off, coo_off_h, sizeof(int64_t) * (A->nsys + 1),
+                               cudaMemcpyHostToDevice, s));
+      SYM_CUDA(cudaMemcpyAsync(d_off + A->nsys + 1, A->row_off_h.data(),
+                               sizeof(int64_t) * (A->nsys + 1), cudaMemcpyHostToDevice, s));
+      ka.coo_off = d_off;
+      ka.row_off = d_off + A->nsys + 1;
+    }
+    // 1-2. counts per row, their scan (total: nkept), the largest count
+    SYM_TRY(dev_alloc(&cnt, n1 + 1, s));
+    SYM_TRY(dev_alloc(&rstart, n1 + 1, s));
+    SYM_TRY(dev_alloc(&scan_tmp, scan_tmp_words(n1 + 1), s));
+    SYM_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (n1 + 1), s));
+    if (ncoo > 0) {
+      k_row_bucket<0><<<grid_for(ncoo, 256), 256, 0, s>>>(ka, cnt, nullptr, nullptr, &dctl->err);
+      GBS_LAUNCHED(1);
+    }
+    SYM_TRY(exclusive_scan(cnt, rstart, n + 1, scan_tmp, &dctl->nkept, s));
+    if (n > 0) {
+      k_max_row<<<grid_for(n, 256), 256, 0, s>>>(reinterpret_cast<const int32_t *>(rstart), n,
+                                                 &dctl->maxcnt);
+      GBS_LAUNCHED(1);
+    }
+    SYM_CUDA(cudaMemcpyAsync(&hc, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    SYM_CUDA(cudaStreamSynchronize(s));
+    if (hc.err != 0) {
+      set_error("mat_create_coo: a kept COO index is out of range");
+      status = GBS_ERR_INDEX;
+      goto cleanup;
+    }
+    if (hc.maxcnt > ROW_SORT_CTA) goto cleanup;  // the radix path takes it
+    const int64_t nkept = hc.nkept;
+    const int64_t nk = std::max<int64_t>(nkept, 1);
+    // 3. placement
+    SYM_TRY(dev_alloc(&keys, nk, s));
+    SYM_TRY(dev_alloc(&perm, nk, s));
+    SYM_TRY(dev_alloc(&ucnt, n1 + 1, s));
+    SYM_TRY(dev_alloc(&long_rows, n1, s));
+    SYM_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (n1 + 1), s));
+    SYM_CUDA(cudaMemsetAsync(ucnt, 0, sizeof(uint32_t) * (n1 + 1), s));
+    if (ncoo > 0) {
+      k_row_bucket<1><<<grid_for(ncoo, 256), 256, 0, s>>>(ka, cnt, rstart, keys, nullptr);
+      GBS_LAUNCHED(1);
+    }
+    // 4. per-row sorts, distinct columns
+    if (n > 0) {
+      k_row_sort_warp<<<grid_for(nwarp_rows, 256), 256, 0, s>>>(n, rstart, keys, perm, ucnt,
+                                                                 long_rows, &dctl->nlong);
+      k_row_sort_cta<<<1024, ROW_SORT_TPB, 0, s>>>(rstart, keys, perm, ucnt, long_rows,
+                                                   &dctl->nlong);
+      GBS_LAUNCHED(2);
+    }
+    // 5. row_ptr, nnz; then col, jmap, diagonal positions
+    SYM_TRY(dev_alloc(&A->row_ptr, n + 1, s));
+    SYM_TRY(exclusive_scan(ucnt, reinterpret_cast<uint32_t *>(A->row_ptr), n + 1, scan_tmp,
+                           &dctl->nnz, s));
+    SYM_CUDA(cudaMemcpyAsync(&hc, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    SYM_CUDA(cudaStreamSynchronize(s));
+    const int64_t nnz = hc.nnz;
+    A->nkept = nkept;
+    A->nnz = nnz;
+    const int64_t nz1 = std::max<int64_t>(nnz, 1);
+    SYM_TRY(dev_alloc(&A->jmap, nnz + 1, s));
+    SYM_TRY(dev_alloc(&A->col, nz1, s));
+    SYM_TRY(dev_alloc(&A->val, nz1, s));
+    SYM_TRY(dev_alloc(&A->diag_pos, n1, s));
+    SYM_TRY(dev_alloc(&A->dinv, n1, s));
+    SYM_CUDA(cudaMemsetAsync(A->val, 0, sizeof(double) * nz1, s));
+    SYM_CUDA(cudaMemsetAsync(A->diag_pos, 0xff, sizeof(int32_t) * n1, s));
+    SYM_CUDA(cudaMemsetAsync(A->dinv, 0, sizeof(double) * n1, s));
+    {
+      const int32_t nk32 = (int32_t)nkept;
+      SYM_CUDA(cudaMemcpyAsync(A->jmap + nnz, &nk32, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    }
+    if (n > 0) {
+      k_row_emit<<<grid_for(nwarp_rows, 256), 256, 0, s>>>(n, rstart, keys, A->row_ptr, A->jmap,
+                                                            A->col, A->diag_pos, &dctl->span);
+      k_max_row<<<grid_for(n, 256), 256, 0, s>>>(A->row_ptr, n, &dctl->maxrow);
+      GBS_LAUNCHED(2);
+    }
+    SYM_CUDA(cudaMemcpyAsync(&hc, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    SYM_CUDA(cudaStreamSynchronize(s));
+    A->max_row_nnz = hc.maxrow;
+    A->col_span = hc.span;
+    A->perm = perm;
+    perm = nullptr;
+    *done = true;
+  }
+
+cleanup:
+  for (void *p : {(void *)dctl, (void *)d_off, (void *)cnt, (void *)rstart, (void *)scan_tmp,
+                  (void *)ucnt, (void *)keys, (void *)perm, (void *)long_rows})
+    dev_free(p, s);
+  cudaStreamSynchronize(s);
+  return status;
+}
+
+// The radix path: keep flags and compaction, a stable LSD radix sort of the
+// 64-bit keys i * ncols + j, segment heads.
+static int symbolic_radix(gbs_mat A, const int32_t *i, const int32_t *j,
+                          const int64_t *coo_off_h, cudaStream_t s) {
+  const int64_t ncoo = A->ncoo;
+  KeepArgs ka{i, j, ncoo, A->nrows, A->ncols, nullptr, nullptr, A->nsys};
+  int64_t *d_off = nullptr;
+  uint32_t *flags = nullptr, *scan_tmp = nullptr, *dsc = nullptr;
+  uint64_t *kA = nullptr, *kB = nullptr, *ukey = nullptr;
+  uint32_t *vA = nullptr, *vB = nullptr, *counts = nullptr;
+  int status = GBS_OK;
+  // host mirrors read back after each synchronisation
+  struct Ctl {
+    uint32_t nkept, nnz;
+    int32_t err, maxrow, span, pad;
+  } hc{};
+  Ctl *dctl = nullptr;
+
 
   {
     SYM_TRY(dev_alloc(&dctl, 1, s));
@@ -592,8 +939,6 @@ cleanup:
     dev_free(p, s);
   cudaStreamSynchronize(s);
   return status;
-#undef SYM_CUDA
-#undef SYM_TRY
 }
 
 // ------------------------------------------------------------------ numeric
