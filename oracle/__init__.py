@@ -24,7 +24,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_LIB_OMP_PATH = os.path.join(_HERE, "liboracle_omp.so")
 _lib = None
+_lib_omp = None
 
 OK, ERR_ARG, ERR_INDEX, ERR_ALLOC = 0, 1, 2, 3
 ERR_NOT_SPD, ERR_BREAKDOWN, ERR_NAN, ERR_MAXIT, ERR_STAGNATION = 5, 6, 7, 8, 9
@@ -32,19 +34,27 @@ INSERT, ADD = 0, 1
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so next to it (gcc, FP64, no FMA)."""
+    """Compile oracle.c into liboracle.so next to it (gcc, FP64, no FMA), and
+    the same source with OpenMP into liboracle_omp.so (the all-cores
+    baseline; same results: see ORC_PAR in oracle.c)."""
     lock_path = _LIB_PATH + ".lock"
     with open(lock_path, "w") as lk:
         fcntl.flock(lk, fcntl.LOCK_EX)
-        stale = (not os.path.exists(_LIB_PATH)
-                 or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
-        if force or stale:
-            tmp = _LIB_PATH + f".tmp{os.getpid()}"
-            subprocess.check_call([
-                "gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11",
-                "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"])
-            os.replace(tmp, _LIB_PATH)
+        for path, extra in ((_LIB_PATH, []), (_LIB_OMP_PATH, ["-fopenmp"])):
+            stale = (not os.path.exists(path)
+                     or os.path.getmtime(path) < os.path.getmtime(_SRC))
+            if force or stale:
+                tmp = path + f".tmp{os.getpid()}"
+                subprocess.check_call([
+                    "gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11",
+                    *extra, "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"])
+                os.replace(tmp, path)
     return _LIB_PATH
+
+
+def threads() -> int:
+    """Host cores this process may run on (the all-cores build uses them all)."""
+    return len(os.sched_getaffinity(0))
 
 
 class _Result(ctypes.Structure):
@@ -57,11 +67,22 @@ class _Result(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
 
 
-def _load():
-    global _lib
+def _load(omp: bool = False):
+    """The one-thread oracle, or with omp the all-cores build of the same source."""
+    global _lib, _lib_omp
+    if omp:
+        if _lib_omp is None:
+            build()
+            _lib_omp = _signatures(ctypes.CDLL(_LIB_OMP_PATH))
+        return _lib_omp
     if _lib is None:
         build()
-        lib = ctypes.CDLL(_LIB_PATH)
+        _lib = _signatures(ctypes.CDLL(_LIB_PATH))
+    return _lib
+
+
+def _signatures(lib):
+    if True:
         P = ctypes.c_void_p
         I64, I32, D = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
         lib.orc_coo_symbolic.restype = I64
@@ -96,8 +117,7 @@ def _load():
         lib.orc_pcg_batched.restype = ctypes.c_int
         lib.orc_pcg_batched.argtypes = [I32, P, P, P, P, P, P, D, I64,
                                         ctypes.c_int, D, I64, I32, P]
-        _lib = lib
-    return _lib
+    return lib
 
 
 def _p(a: np.ndarray):
@@ -160,9 +180,10 @@ def coo_symbolic(nrows: int, ncols: int, i, j) -> CSR:
                jmap[:nnz + 1].copy(), ncoo)
 
 
-def coo_numeric(A: CSR, v, mode: int = INSERT) -> np.ndarray:
-    """Sec. 5 MatSetValuesCOO: in-order duplicate sum; INSERT replaces, ADD adds."""
-    lib = _load()
+def coo_numeric(A: CSR, v, mode: int = INSERT, omp: bool = False) -> np.ndarray:
+    """Sec. 5 MatSetValuesCOO: in-order duplicate sum; INSERT replaces, ADD adds.
+    omp: the all-cores build (same results)."""
+    lib = _load(omp)
     v = _c(v, np.float64)
     assert v.shape[0] == A.ncoo
     if A.val is None or mode == INSERT:
@@ -280,18 +301,21 @@ def vec_set_values_coo(n: int, i, v, mode: int = INSERT, y=None) -> np.ndarray:
     return y
 
 
-def spmv(A: CSR, x) -> np.ndarray:
-    """MatMult (Sec. 6.1): y_i = sum_p a_p x_{col p}, CSR order, FP64."""
-    lib = _load()
+def spmv(A: CSR, x, omp: bool = False) -> np.ndarray:
+    """MatMult (Sec. 6.1): y_i = sum_p a_p x_{col p}, CSR order, FP64.
+    omp: the all-cores build (same results)."""
+    lib = _load(omp)
     x = _c(x, np.float64)
     y = np.zeros(A.nrows, np.float64)
     lib.orc_spmv(A.nrows, _p(A.row_ptr), _p(A.col), _p(A.val), _p(x), _p(y))
     return y
 
 
-def pcg(A: CSR, b, rtol: float = 1e-8, maxit: int | None = None, x0=None):
-    """Jacobi-PCG (Sec. 6.1 CG, Sec. 7 diagonal preconditioning). Returns (x, result)."""
-    lib = _load()
+def pcg(A: CSR, b, rtol: float = 1e-8, maxit: int | None = None, x0=None,
+        omp: bool = False):
+    """Jacobi-PCG (Sec. 6.1 CG, Sec. 7 diagonal preconditioning). Returns (x, result).
+    omp: the all-cores build (same results)."""
+    lib = _load(omp)
     b = _c(b, np.float64)
     x = np.zeros(A.nrows, np.float64) if x0 is None else _c(x0, np.float64).copy()
     res = _Result()

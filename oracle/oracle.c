@@ -54,6 +54,17 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Built twice: as it stands (one thread), and with -fopenmp for the timed
+ * all-cores baseline, where ORC_PAR splits the row loops of the SpMV, the
+ * numeric COO stage and the FP64 PCG's element-wise updates across threads.
+ * Every split loop writes each element from one iteration alone, and the
+ * inner products stay sequential, so both builds give the same bits. */
+#ifdef _OPENMP
+#define ORC_PAR _Pragma("omp parallel for schedule(static)")
+#else
+#define ORC_PAR
+#endif
+
 /* status codes (numerically the same values the public C-ABI documents) */
 enum {
   ORC_OK = 0,
@@ -152,6 +163,7 @@ int64_t orc_coo_symbolic(int64_t nrows, int64_t ncols, int64_t ncoo,
  */
 void orc_coo_numeric(int64_t nnz, const int32_t *jmap, const int32_t *perm,
                      const double *v, int mode, double *val) {
+  ORC_PAR
   for (int64_t p = 0; p < nnz; ++p) {
     double s = v[perm[jmap[p]]];
     for (int64_t t = (int64_t)jmap[p] + 1; t < jmap[p + 1]; ++t) s = s + v[perm[t]];
@@ -211,6 +223,7 @@ int64_t orc_vec_set_values_coo(int64_t n, int64_t ncoo, const int32_t *ci, const
 
 void orc_spmv(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
               const double *x, double *y) {
+  ORC_PAR
   for (int64_t i = 0; i < n; ++i) {
     double s = 0.0;
     for (int64_t p = rp[i]; p < rp[i + 1]; ++p) s += a[p] * x[ci[p]];
@@ -310,8 +323,11 @@ int orc_pcg(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
     return res->status = ORC_OK;
   }
   orc_spmv(n, rp, ci, a, x, r);
+  ORC_PAR
   for (int64_t i = 0; i < n; ++i) r[i] = b[i] - r[i];
+  ORC_PAR
   for (int64_t i = 0; i < n; ++i) z[i] = dinv[i] * r[i];
+  ORC_PAR
   for (int64_t i = 0; i < n; ++i) p[i] = z[i];
   double rho = dot(n, r, z);
   double rr = dot(n, r, r);
@@ -342,12 +358,16 @@ int orc_pcg(int64_t n, const int32_t *rp, const int32_t *ci, const double *a,
       break;
     }
     double alpha = rho / sigma;
+    ORC_PAR
     for (int64_t i = 0; i < n; ++i) x[i] += alpha * p[i];
+    ORC_PAR
     for (int64_t i = 0; i < n; ++i) r[i] -= alpha * q[i];
+    ORC_PAR
     for (int64_t i = 0; i < n; ++i) z[i] = dinv[i] * r[i];
     double rho_new = dot(n, r, z);
     rr = dot(n, r, r);
     double beta = rho_new / rho;
+    ORC_PAR
     for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
     rho = rho_new;
   }

@@ -292,3 +292,20 @@ def test_batched_degenerate_systems_closed_forms():
         assert abs(x[2] - 5.0 / 2.5) <= 4 * np.spacing(2.0)
         if prec == 0:
             assert rs[0]["iterations"] == 2 and rs[2]["iterations"] == 1
+
+
+def test_all_cores_build_gives_the_same_bits():
+    """The OpenMP build of the oracle (the all-cores CPU baseline) splits only
+    loops whose iterations write separate elements and keeps the inner
+    products sequential: assembly, SpMV and the PCG solve are bit-identical
+    to the one-thread build."""
+    p = W.q1_hex(10, seed=4)
+    A = oracle.coo_symbolic(p.nrows, p.ncols, p.i, p.j)
+    v1 = oracle.coo_numeric(A, p.v).copy()
+    v2 = oracle.coo_numeric(A, p.v, omp=True).copy()
+    assert v1.tobytes() == v2.tobytes()
+    y1, y2 = oracle.spmv(A, p.b), oracle.spmv(A, p.b, omp=True)
+    assert y1.tobytes() == y2.tobytes()
+    x1, r1 = oracle.pcg(A, p.b, rtol=1e-10)
+    x2, r2 = oracle.pcg(A, p.b, rtol=1e-10, omp=True)
+    assert x1.tobytes() == x2.tobytes() and r1 == r2
