@@ -71,6 +71,8 @@ enum { GBS_FP64 = 0, GBS_FP32_REFINED = 1 };
 enum { GBS_SPMV_AUTO = -1, GBS_SPMV_SELL = 0 };
 /* Solvers (mat_set_solver). */
 enum { GBS_SOLVER_AUTO = 0, GBS_SOLVER_PHASES = 1, GBS_SOLVER_CTA = 2, GBS_SOLVER_CLUSTER = 3 };
+/* Forms of CG on the phase kernels (mat_set_cg_form, chosen by the autotuner). */
+enum { GBS_CG_TEXTBOOK = 0, GBS_CG_SINGLE_REDUCTION = 1 };
 /* Krylov methods (ksp_opts.method; Sec. 7 batched solvers, Sec. 6.2). */
 enum { GBS_KSP_CG = 0, GBS_KSP_BICG = 1, GBS_KSP_TFQMR = 2, GBS_KSP_PIPECG = 3,
        GBS_KSP_CGSR = 4 };
@@ -361,8 +363,7 @@ int mat_get_coo_maps(gbs_mat A, const int32_t **perm, const int32_t **jmap,
  * kernel then runs in one wave and keeps one reduction slot per CTA).  mat_set_plan
  * synchronises the device (the old tables may be in use) and drops the
  * cached solve graphs.  mat_create_coo picks (0, 0, GBS_SPMV_AUTO, 0);
- * mat_autotune times candidates (a fixed 30-iteration FP64 solve each, CUDA
- * events on `stream`) and keeps the fastest (it synchronises).  mat_get_plan
+ * mat_autotune (below) picks among candidates by timing them.  mat_get_plan
  * returns the kernel in use (never AUTO) and the grid of the SpMV-phase
  * kernels.  Host outputs may be NULL.
  */
@@ -395,7 +396,43 @@ int mat_get_plan(gbs_mat A, int32_t *spmv_rows, int32_t *update_rows, int32_t *k
  * ksp_result.solver tells which one ran.  No synchronisation.
  */
 int mat_set_solver(gbs_mat A, int32_t solver);
+
+/*
+ * The form of FP64 CG (ksp_solve_cg*, ksp_adjoint*, method GBS_KSP_CG) on the
+ * phase kernels: GBS_CG_TEXTBOOK (default; three kernels and two reductions
+ * per iteration) or GBS_CG_SINGLE_REDUCTION (the GBS_KSP_CGSR loop: two
+ * kernels and one reduction, the same iterates in exact arithmetic; needs the
+ * sliced-ELL plan kernel, else the textbook form runs).  The per-CTA and
+ * cluster engines and the refined solve always use the textbook form.  No
+ * synchronisation.  mat_get_tuning returns the solver setting
+ * (mat_set_solver) and the CG form (host outputs, may be NULL).
+ */
+int mat_set_cg_form(gbs_mat A, int32_t form);
+int mat_get_tuning(gbs_mat A, int32_t *solver, int32_t *cg_form);
+
+/*
+ * Autotuner of the FP64 CG solve ("rows-per-warp and block shapes picked by a
+ * project-written autotuner"): candidates are launch plans (as mat_set_plan:
+ * block rows, row-product kernel, CTAs per SM), then, for the fastest plan,
+ * the single-reduction CG form and (sliced ELL; batches, or systems within
+ * 16 times the per-CTA size rule) the per-CTA engine.  Each candidate runs a
+ * fixed 30-iteration FP64 CG (rtol 0, every candidate the same work; a
+ * batched handle solves its systems each on its own) once untimed and three
+ * times under CUDA events on `stream`; the fastest becomes the handle's plan,
+ * solver (mat_set_solver) and CG form (mat_set_cg_form).  Synchronises.
+ *
+ * mat_autotune_file: the same, persisted.  path names a text file (created if
+ * missing) of one line per tuned key: "<key> | Ra Re kernel ctas_per_sm
+ * solver cg_form | <time>".  The key holds the handle's sizes, a hash of its
+ * systems' sizes and of 257 sampled entries each of row_ptr and col, the
+ * device name and SM count, and "fp64".  A matching line is applied without
+ * timing (*from_cache = 1); otherwise the handle is tuned and the line
+ * appended (*from_cache = 0).  The file is held under an exclusive lock
+ * (flock) meanwhile.  from_cache (host) may be NULL.  GBS_ERR_ARG if the
+ * file cannot be opened.
+ */
 int mat_autotune(gbs_mat A, void *stream);
+int mat_autotune_file(gbs_mat A, const char *path, int32_t *from_cache, void *stream);
 
 /* Releases every device buffer the handle owns.  Synchronises the device
  * buffers' last stream first.  NULL is accepted. */

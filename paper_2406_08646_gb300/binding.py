@@ -27,6 +27,7 @@ FP64, FP32_REFINED = 0, 1
 SPMV_AUTO, SPMV_SELL = -1, 0  # plan kernels; 1, 2, 4, 8, 32 = CSR-vector lanes per row
 SOLVER_AUTO, SOLVER_PHASES, SOLVER_CTA, SOLVER_CLUSTER = 0, 1, 2, 3
 KSP_CG, KSP_BICG, KSP_TFQMR, KSP_PIPECG, KSP_CGSR = 0, 1, 2, 3, 4
+CG_TEXTBOOK, CG_SINGLE_REDUCTION = 0, 1
 
 EXPORTED = ["ksp_opts_default", "mat_create_coo", "mat_create_coo_batched",
             "mat_set_values_coo", "mat_mult", "ksp_solve_cg", "ksp_solve_cg_batched",
@@ -36,7 +37,7 @@ EXPORTED = ["ksp_opts_default", "mat_create_coo", "mat_create_coo_batched",
             "ksp_solve_cg_noalloc", "ksp_get_phase_ns", "mat_set_solver",
             "vec_create_coo", "vec_set_values_coo", "vec_get_info", "vec_destroy",
             "ksp_solve", "ksp_solve_batched", "q1_hex_element_coo", "q1_hex_element_values",
-            "edge_coo_values"]
+            "edge_coo_values", "mat_autotune_file", "mat_set_cg_form", "mat_get_tuning"]
 
 
 class KspOpts(ctypes.Structure):
@@ -109,6 +110,9 @@ def lib() -> ctypes.CDLL:
         "q1_hex_element_coo": (ctypes.c_int, [I32, P, P, P]),
         "q1_hex_element_values": (ctypes.c_int, [I32, P, P, P]),
         "edge_coo_values": (ctypes.c_int, [I64, P, P, P]),
+        "mat_autotune_file": (ctypes.c_int, [P, ctypes.c_char_p, P, P]),
+        "mat_set_cg_form": (ctypes.c_int, [P, I32]),
+        "mat_get_tuning": (ctypes.c_int, [P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -338,6 +342,24 @@ def mat_set_solver(A, solver: int):
     _check(lib().mat_set_solver(A, solver))
 
 
+def mat_autotune_file(A, path: str, stream=None) -> bool:
+    """Tune A, or apply the tuning stored for its key in the file at path;
+    returns True when it came from the file."""
+    hit = ctypes.c_int32(0)
+    _check(lib().mat_autotune_file(A, os.fsencode(path), ctypes.byref(hit), _stream(stream)))
+    return bool(hit.value)
+
+
+def mat_set_cg_form(A, form: int):
+    _check(lib().mat_set_cg_form(A, int(form)))
+
+
+def mat_get_tuning(A) -> dict:
+    sv, cf = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(lib().mat_get_tuning(A, ctypes.byref(sv), ctypes.byref(cf)))
+    return {"solver": sv.value, "cg_form": cf.value}
+
+
 def mat_autotune(A, stream=None):
     _check(lib().mat_autotune(A, _stream(stream)))
 
@@ -490,8 +512,19 @@ class Mat:
     def phase_ns(self) -> dict:
         return ksp_get_phase_ns(self.h)
 
-    def autotune(self, stream=None):
-        mat_autotune(self.h, stream)
+    def autotune(self, path=None, stream=None):
+        """Tune the solve (persisted in the file at path when given; returns
+        whether the tuning came from that file)."""
+        if path is None:
+            mat_autotune(self.h, stream)
+            return False
+        return mat_autotune_file(self.h, path, stream)
+
+    def set_cg_form(self, form: int):
+        mat_set_cg_form(self.h, form)
+
+    def tuning(self) -> dict:
+        return mat_get_tuning(self.h)
 
     def close(self):
         if self.h:

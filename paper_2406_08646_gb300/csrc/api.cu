@@ -3,12 +3,18 @@
 // kernels in coo.cu, spmv.cu and pcg.cu.
 #include <cuda_runtime.h>
 
+#include <fcntl.h>
+#include <sys/file.h>
+#include <unistd.h>
+
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <string>
 
 #include "internal.cuh"
 
@@ -455,21 +461,53 @@ int mat_get_plan(gbs_mat A, int32_t *spmv_rows, int32_t *update_rows, int32_t *k
   return GBS_OK;
 }
 
-// Times a fixed 30-iteration FP64 PCG run (rtol 0, so every candidate does
-// the same work) for each candidate plan and keeps the fastest.
-int mat_autotune(gbs_mat A, void *stream) {
-  GBS_TRY(check_mat(A, "mat_autotune"));
-  if (!A->values_set) {
-    set_error("mat_autotune: mat_set_values_coo has not been called");
-    return GBS_ERR_ARG;
+// ------------------------------------------------------------------ autotuner
+//
+// A candidate is a launch plan (SpMV rows, update rows, row-product kernel,
+// CTAs per SM), a solver engine and a CG form.  Each is timed on a fixed
+// 30-iteration FP64 CG run (rtol 0, so every candidate does the same work;
+// batched handles solve their systems each on their own): one untimed run
+// (it builds the graph), then three timed back to back with CUDA events.
+// First the plans with the textbook form on the phase kernels; then, with
+// the best plan, the single-reduction form and (sliced ELL) the per-CTA
+// engine -- not for one system whose iteration is far beyond one SM's share.
+
+namespace {
+struct Tuning {
+  int32_t Ra, Re, kernel, cpsm, solver, cg_form;
+};
+
+// Makes t the handle's plan (rebuilt only when it differs from the current
+// one), solver and CG form.
+int apply_tuning(gbs_mat A, const Tuning &t, cudaStream_t s) {
+  if (!(t.Ra == A->Ra && t.Re == A->Re && t.kernel == A->lanes && t.cpsm == A->ctas_per_sm))
+    GBS_TRY(build_plan(A, t.Ra, t.Re, t.kernel, t.cpsm, s));
+  A->solver = t.solver;
+  A->cg_form = t.cg_form;
+  return GBS_OK;
+}
+
+// The resolved plan of the handle with its solver and form.
+Tuning current_tuning(gbs_mat A) {
+  return Tuning{A->Ra, A->Re, A->lanes, A->ctas_per_sm, A->solver, A->cg_form};
+}
+
+// 257 evenly spaced entries each of row_ptr and col (the cache key's sample).
+__global__ void k_key_sample(const int32_t *row_ptr, const int32_t *col, int64_t n, int64_t nnz,
+                             int32_t *out) {
+  const int q = threadIdx.x;
+  if (q < 257) {
+    out[q] = row_ptr[n * q / 256];
+    out[257 + q] = nnz > 0 ? col[(nnz - 1) * q / 256] : 0;
   }
-  if (A->nrows != A->ncols || A->nrows == 0) return GBS_OK;
-  GBS_TRY(use_device(A));
-  cudaStream_t s = (cudaStream_t)stream;
+}
+}  // namespace
+
+static int autotune(gbs_mat A, cudaStream_t s, Tuning *out, float *out_ms) {
+  const bool per_system = A->nsys > 1;
   const int la = auto_lanes(A->nnz, A->nrows);
   const int sk = A->lanes;  // the kernel the current plan chose
-  // (SpMV rows, update rows, row-product kernel, CTAs per SM cap)
-  const int cands[][4] = {{0, 0, sk, 0},     {0, 0, la, 0},     {256, 512, sk, 0},
+  const int plans[][4] = {{0, 0, sk, 0},     {0, 0, la, 0},     {256, 512, sk, 0},
                           {512, 1024, sk, 0}, {0, 0, sk, 4},     {256, 2048, sk, 0},
                           {0, 0, sk, 2},      {1024, 4096, sk, 0}};
   double *b = nullptr, *x = nullptr;
@@ -482,31 +520,46 @@ int mat_autotune(gbs_mat A, void *stream) {
   ksp_opts_default(&o);
   o.rtol = 0.0;
   o.maxit = 30;
-  o.inner_maxit = 30;
-  o.inner_rtol = 1e-4;
-  o.max_outer = 30;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  int best_plan[4] = {A->Ra, A->Re, A->lanes, A->ctas_per_sm};
-  float best = 1e30f;
+  Tuning best{A->Ra, A->Re, A->lanes, A->ctas_per_sm, GBS_SOLVER_PHASES, GBS_CG_TEXTBOOK};
+  float best_ms = 1e30f;
   int st = GBS_OK;
-  for (const auto &c : cands) {
-    if (build_plan(A, c[0], c[1], c[2], c[3], s) != GBS_OK) continue;
-    if (launch_spmv(A, x, b, s) != GBS_OK) continue;
-    if (solve(A, b, x, o, false, s) != GBS_OK) continue;  // warm-up (and graph build)
+  auto timed = [&](const Tuning &t) -> bool {
+    if (apply_tuning(A, t, s) != GBS_OK) return false;
+    if (launch_spmv(A, x, b, s) != GBS_OK) return false;
+    if (solve(A, b, x, o, per_system, s) != GBS_OK) return false;  // warm-up (and graph build)
     cudaEventRecord(e0, s);
-    for (int rep = 0; rep < 3; ++rep) solve(A, b, x, o, false, s);
+    for (int rep = 0; rep < 3; ++rep) solve(A, b, x, o, per_system, s);
     cudaEventRecord(e1, s);
     if (cudaEventSynchronize(e1) != cudaSuccess) {
       st = GBS_ERR_CUDA;
-      break;
+      return false;
     }
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best) {
-      best = ms;
-      for (int k = 0; k < 4; ++k) best_plan[k] = c[k];
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = t;
+    }
+    return true;
+  };
+  for (const auto &c : plans) {
+    timed(Tuning{c[0], c[1], c[2], c[3], GBS_SOLVER_PHASES, GBS_CG_TEXTBOOK});
+    if (st != GBS_OK) break;
+  }
+  if (st == GBS_OK && best.kernel == GBS_SPMV_SELL) {
+    const Tuning base = best;
+    Tuning t = base;
+    t.cg_form = GBS_CG_SINGLE_REDUCTION;
+    timed(t);
+    const int64_t nz = per_system ? A->max_sys_nnz : A->nnz;
+    const int64_t rows = per_system ? A->max_sys_rows : A->nrows;
+    if (st == GBS_OK && (per_system || nz + 8 * rows <= 16 * CTA_AUTO_WORK)) {
+      t = base;
+      t.solver = GBS_SOLVER_CTA;
+      timed(t);
     }
   }
   A->trips_counted = true;  // the timed solves' results are never read
@@ -518,8 +571,142 @@ int mat_autotune(gbs_mat A, void *stream) {
     set_error("mat_autotune: a timed run failed");
     return st;
   }
-  GBS_TRY(build_plan(A, best_plan[0], best_plan[1], best_plan[2], best_plan[3], s));
+  GBS_TRY(apply_tuning(A, best, s));
   GBS_TRY_CUDA(cudaStreamSynchronize(s));
+  if (out) *out = current_tuning(A);  // with the plan's automatic sizes resolved
+  if (out_ms) *out_ms = best_ms / 3.0f;
+  return GBS_OK;
+}
+
+static int autotune_entry(gbs_mat A, const char *fn) {
+  GBS_TRY(check_mat(A, fn));
+  if (!A->values_set) {
+    set_error("%s: mat_set_values_coo has not been called", fn);
+    return GBS_ERR_ARG;
+  }
+  return GBS_OK;
+}
+
+int mat_autotune(gbs_mat A, void *stream) {
+  GBS_TRY(autotune_entry(A, "mat_autotune"));
+  if (A->nrows != A->ncols || A->nrows == 0) return GBS_OK;
+  GBS_TRY(use_device(A));
+  return autotune(A, (cudaStream_t)stream, nullptr, nullptr);
+}
+
+// The cache key of a handle: its sizes, a hash (FNV-1a) of its systems' row
+// counts and of 257 evenly spaced entries of row_ptr and of col, and the
+// device (name, SM count); the tuning is for FP64 CG.
+static int tuning_key(gbs_mat A, cudaStream_t s, std::string *key) {
+  const int K = 257;
+  std::vector<int32_t> sample(2 * K);
+  int32_t *d = nullptr;
+  GBS_TRY(dev_alloc(&d, 2 * K, s));
+  k_key_sample<<<1, 288, 0, s>>>(A->row_ptr, A->col, A->nrows, A->nnz, d);
+  count_launches(1);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(sample.data(), d, sizeof(int32_t) * 2 * K, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  dev_free(d, s);
+  GBS_TRY_CUDA(e);
+  const int32_t *rp = sample.data(), *cl = sample.data() + K;
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](const void *p, size_t n) {
+    const unsigned char *c = static_cast<const unsigned char *>(p);
+    for (size_t k = 0; k < n; ++k) {
+      h ^= c[k];
+      h *= 1099511628211ull;
+    }
+  };
+  mix(A->row_off_h.data(), sizeof(int64_t) * A->row_off_h.size());
+  mix(rp, sizeof(int32_t) * K);
+  mix(cl, sizeof(int32_t) * K);
+  cudaDeviceProp prop;
+  GBS_TRY_CUDA(cudaGetDeviceProperties(&prop, A->device));
+  char buf[512];
+  std::string name(prop.name);
+  for (char &c : name)
+    if (c == ' ' || c == '|') c = '_';
+  snprintf(buf, sizeof(buf), "fp64 n=%lld nnz=%lld nsys=%d sig=%016llx dev=%s sm=%d",
+           (long long)A->nrows, (long long)A->nnz, A->nsys, (unsigned long long)h, name.c_str(),
+           prop.multiProcessorCount);
+  *key = buf;
+  return GBS_OK;
+}
+
+int mat_autotune_file(gbs_mat A, const char *path, int32_t *from_cache, void *stream) {
+  GBS_TRY(autotune_entry(A, "mat_autotune_file"));
+  if (!path) {
+    set_error("mat_autotune_file: null path");
+    return GBS_ERR_ARG;
+  }
+  if (from_cache) *from_cache = 0;
+  if (A->nrows != A->ncols || A->nrows == 0) return GBS_OK;
+  GBS_TRY(use_device(A));
+  cudaStream_t s = (cudaStream_t)stream;
+  std::string key;
+  GBS_TRY(tuning_key(A, s, &key));
+  // one exclusive lock on the file for the lookup and, on a miss, the
+  // tuning and the appended line, so concurrent processes tune a key once
+  const int fd = open(path, O_RDWR | O_CREAT, 0644);
+  if (fd < 0) {
+    set_error("mat_autotune_file: cannot open %s", path);
+    return GBS_ERR_ARG;
+  }
+  flock(fd, LOCK_EX);
+  FILE *f = fdopen(fd, "r+");
+  int st = GBS_OK;
+  bool hit = false;
+  if (!f) {
+    set_error("mat_autotune_file: cannot read %s", path);
+    st = GBS_ERR_ARG;
+  } else {
+    char line[1024];
+    Tuning t{};
+    while (fgets(line, sizeof(line), f)) {
+      const char *bar = strchr(line, '|');
+      if (!bar || (size_t)(bar - line) != key.size() + 1 || strncmp(line, key.c_str(), key.size()))
+        continue;
+      if (sscanf(bar + 1, " %d %d %d %d %d %d", &t.Ra, &t.Re, &t.kernel, &t.cpsm, &t.solver,
+                 &t.cg_form) == 6)
+        hit = true;  // the last matching line wins
+    }
+    if (hit) {
+      st = apply_tuning(A, t, s);
+      if (st == GBS_OK && cudaStreamSynchronize(s) != cudaSuccess) st = GBS_ERR_CUDA;
+      if (st == GBS_OK && from_cache) *from_cache = 1;
+    } else {
+      float ms = 0;
+      st = autotune(A, s, &t, &ms);
+      if (st == GBS_OK) {
+        fseek(f, 0, SEEK_END);
+        fprintf(f, "%s | %d %d %d %d %d %d | %.4f ms per 30 iterations\n", key.c_str(), t.Ra, t.Re,
+                t.kernel, t.cpsm, t.solver, t.cg_form, ms);
+        fflush(f);
+      }
+    }
+  }
+  flock(fd, LOCK_UN);
+  if (f) fclose(f);
+  else close(fd);
+  return st;
+}
+
+int mat_set_cg_form(gbs_mat A, int32_t form) {
+  GBS_TRY(check_mat(A, "mat_set_cg_form"));
+  if (form != GBS_CG_TEXTBOOK && form != GBS_CG_SINGLE_REDUCTION) {
+    set_error("mat_set_cg_form: form must be GBS_CG_TEXTBOOK or GBS_CG_SINGLE_REDUCTION");
+    return GBS_ERR_ARG;
+  }
+  A->cg_form = form;
+  return GBS_OK;
+}
+
+int mat_get_tuning(gbs_mat A, int32_t *solver, int32_t *cg_form) {
+  GBS_TRY(check_mat(A, "mat_get_tuning"));
+  if (solver) *solver = A->solver;
+  if (cg_form) *cg_form = A->cg_form;
   return GBS_OK;
 }
 

@@ -26,6 +26,10 @@ void count_launches(int64_t n);
 // ordered after s's allocation (the calls that allocate handle buffers
 // synchronise s before returning).
 constexpr uint64_t POOL_KEEP_BYTES = 32ull << 30;
+
+// The per-CTA solver's automatic size rule: systems of at most this many
+// FP64 operations per iteration (nonzeros plus eight per row; pcg.cu).
+constexpr int64_t CTA_AUTO_WORK = 40000;
 int dev_alloc_bytes(void **p, size_t bytes, cudaStream_t s);
 void dev_free(void *p, cudaStream_t s);
 template <typename T>
@@ -179,6 +183,7 @@ struct gbs_mat_s {
   int32_t lanes = 0;
   int32_t ctas_per_sm = 0;      // grid cap per SM, 0 = as many as fit (one wave)
   int32_t solver = 0;           // GBS_SOLVER_AUTO / PHASES / CTA
+  int32_t cg_form = 0;          // GBS_CG_TEXTBOOK / GBS_CG_SINGLE_REDUCTION (phase kernels)
   int32_t *cta_order = nullptr; // nsys: systems by decreasing rows (per-CTA solver)
   int64_t max_sys_rows = 0, max_sys_nnz = 0;
 

@@ -449,8 +449,6 @@ int run_loop_stepped(const LoopPlan &P, PcgArgs a, int grid_a, int grid_e, int64
 // 40,000 of those it beats a phase-kernel CG iteration (about 14-16 us at
 // small sizes): q1_hex 8^3 (729 rows, 15,625 nonzeros) 13.6 against 21.9
 // us, poisson2d 64^2 (4,096 rows, 20,224 nonzeros) 18.4 against 14.0 us.
-constexpr int64_t CTA_AUTO_WORK = 40000;
-
 bool cta_size_rule(gbs_mat A, bool per_system, int systems_per_sm) {
   const int64_t nz = per_system ? A->max_sys_nnz : A->nnz;
   const int64_t rows = per_system ? A->max_sys_rows : A->nrows;
@@ -528,6 +526,15 @@ static int launch_cluster(gbs_mat A, const PcgArgs &a, int32_t nclusters, cudaSt
 int solve(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool per_system,
           cudaStream_t s) {
   const bool refined = o.precision == GBS_FP32_REFINED;
+  // the handle's CG form: FP64 CG on the phase kernels may run as the
+  // single-reduction loop (same iterates in exact arithmetic, two kernels per
+  // iteration instead of three)
+  if (!refined && A->cg_form == GBS_CG_SINGLE_REDUCTION && A->lanes == GBS_SPMV_SELL &&
+      A->solver != GBS_SOLVER_CLUSTER && !use_cta_solver(A, per_system)) {
+    ksp_opts sr = o;
+    sr.method = GBS_KSP_CGSR;
+    return solve_krylov(A, b, x, sr, per_system, s);
+  }
   GBS_TRY(ensure_solver_workspace(A, refined, s));
   if (refined && !A->val32_valid) GBS_TRY(launch_to_fp32(A, s));
   A->last_count = per_system ? A->nsys : 1;

@@ -114,6 +114,9 @@ HANDLE_CALLS = {  # every entry point taking a matrix / vector handle: its argum
     "mat_get_plan": [P, P, P, P, P, P],
     "mat_set_solver": [P, I32],
     "mat_autotune": [P, P],
+    "mat_autotune_file": [P, P, P, P],
+    "mat_set_cg_form": [P, I32],
+    "mat_get_tuning": [P, P, P],
     "vec_set_values_coo": [P, P, I32, P, P],
     "vec_get_info": [P, P, P, P],
 }
@@ -181,3 +184,21 @@ def test_binding_rejects_host_tensors_and_fills_options_without_gpu():
     assert (o.rtol, o.maxit, o.precision, o.inner_rtol, o.max_outer, o.inner_maxit,
             o.timeout_ns, o.nonzero_guess, o.host_loop, o.method) == (
         1e-10, 77, B.FP32_REFINED, 1e-3, 5, 9, 123, 1, 1, B.KSP_TFQMR)
+
+
+def test_generation_entry_points_check_arguments_without_gpu(lib):
+    """The device-side COO generators refuse bad sizes and null pointers on
+    the host, before any device call."""
+    from paper_2406_08646_gb300 import binding as B
+    lib.q1_hex_element_coo.argtypes = [I32, P, P, P]
+    lib.q1_hex_element_values.argtypes = [I32, P, P, P]
+    lib.edge_coo_values.argtypes = [I64, P, P, P]
+    for f in (lib.q1_hex_element_coo, lib.q1_hex_element_values, lib.edge_coo_values):
+        f.restype = ctypes.c_int
+    assert lib.q1_hex_element_coo(0, None, None, None) == B.ERR_ARG
+    assert lib.q1_hex_element_coo(400, None, None, None) == B.ERR_ARG
+    assert lib.q1_hex_element_coo(4, None, None, None) == B.ERR_ARG
+    assert lib.q1_hex_element_values(4, None, None, None) == B.ERR_ARG
+    assert lib.edge_coo_values(-1, None, None, None) == B.ERR_ARG
+    assert lib.edge_coo_values(1 << 29, None, None, None) == B.ERR_ARG
+    assert lib.edge_coo_values(0, None, None, None) == B.OK
