@@ -72,7 +72,7 @@ enum { GBS_SPMV_AUTO = -1, GBS_SPMV_SELL = 0 };
 /* Solvers (mat_set_solver). */
 enum { GBS_SOLVER_AUTO = 0, GBS_SOLVER_PHASES = 1, GBS_SOLVER_CTA = 2, GBS_SOLVER_CLUSTER = 3 };
 /* Forms of CG on the phase kernels (mat_set_cg_form, chosen by the autotuner). */
-enum { GBS_CG_TEXTBOOK = 0, GBS_CG_SINGLE_REDUCTION = 1 };
+enum { GBS_CG_TEXTBOOK = 0, GBS_CG_SINGLE_REDUCTION = 1, GBS_CG_SINGLE_KERNEL = 2 };
 /* Krylov methods (ksp_opts.method; Sec. 7 batched solvers, Sec. 6.2). */
 enum { GBS_KSP_CG = 0, GBS_KSP_BICG = 1, GBS_KSP_TFQMR = 2, GBS_KSP_PIPECG = 3,
        GBS_KSP_CGSR = 4 };
@@ -400,12 +400,21 @@ int mat_set_solver(gbs_mat A, int32_t solver);
 /*
  * The form of FP64 CG (ksp_solve_cg*, ksp_adjoint*, method GBS_KSP_CG) on the
  * phase kernels: GBS_CG_TEXTBOOK (default; three kernels and two reductions
- * per iteration) or GBS_CG_SINGLE_REDUCTION (the GBS_KSP_CGSR loop: two
- * kernels and one reduction, the same iterates in exact arithmetic; needs the
- * sliced-ELL plan kernel, else the textbook form runs).  The per-CTA and
- * cluster engines and the refined solve always use the textbook form.  No
- * synchronisation.  mat_get_tuning returns the solver setting
- * (mat_set_solver) and the CG form (host outputs, may be NULL).
+ * per iteration), GBS_CG_SINGLE_REDUCTION (the GBS_KSP_CGSR loop: two
+ * kernels and one reduction, the same iterates in exact arithmetic) or
+ * GBS_CG_SINGLE_KERNEL (the same loop as ONE kernel per iteration: each CTA
+ * updates its rows, waits -- spinning on flags in device memory, bounded by
+ * about a second, after which the solve ends with GBS_ERR_TIMEOUT -- until
+ * the CTAs holding the rows its row products read have updated theirs, then
+ * runs its row products; the grid is launched cooperatively, so all its
+ * CTAs are resident together).  The single-reduction forms need the
+ * sliced-ELL plan kernel (else the textbook form runs); the single-kernel
+ * form also needs an ensemble solve (ksp_solve_cg, one system or a batch
+ * solved as one), else the two-kernel form runs.  GBS_KSP_CGSR follows the
+ * handle's form too: the single-kernel form where it applies, else two
+ * kernels.  The per-CTA and cluster engines and the refined solve always use
+ * the textbook form.  No synchronisation.  mat_get_tuning returns the solver
+ * setting (mat_set_solver) and the CG form (host outputs, may be NULL).
  */
 int mat_set_cg_form(gbs_mat A, int32_t form);
 int mat_get_tuning(gbs_mat A, int32_t *solver, int32_t *cg_form);
@@ -414,7 +423,8 @@ int mat_get_tuning(gbs_mat A, int32_t *solver, int32_t *cg_form);
  * Autotuner of the FP64 CG solve ("rows-per-warp and block shapes picked by a
  * project-written autotuner"): candidates are launch plans (as mat_set_plan:
  * block rows, row-product kernel, CTAs per SM), then, for the fastest plan,
- * the single-reduction CG form and (sliced ELL; batches, or systems within
+ * the single-reduction CG forms (two kernels; one kernel, for a handle of
+ * one system) and (sliced ELL; batches, or systems within
  * 16 times the per-CTA size rule) the per-CTA engine.  Each candidate runs a
  * fixed 30-iteration FP64 CG (rtol 0, every candidate the same work; a
  * batched handle solves its systems each on its own) once untimed and three

@@ -27,7 +27,7 @@ FP64, FP32_REFINED = 0, 1
 SPMV_AUTO, SPMV_SELL = -1, 0  # plan kernels; 1, 2, 4, 8, 32 = CSR-vector lanes per row
 SOLVER_AUTO, SOLVER_PHASES, SOLVER_CTA, SOLVER_CLUSTER = 0, 1, 2, 3
 KSP_CG, KSP_BICG, KSP_TFQMR, KSP_PIPECG, KSP_CGSR = 0, 1, 2, 3, 4
-CG_TEXTBOOK, CG_SINGLE_REDUCTION = 0, 1
+CG_TEXTBOOK, CG_SINGLE_REDUCTION, CG_SINGLE_KERNEL = 0, 1, 2
 
 EXPORTED = ["ksp_opts_default", "mat_create_coo", "mat_create_coo_batched",
             "mat_set_values_coo", "mat_mult", "ksp_solve_cg", "ksp_solve_cg_batched",

@@ -91,7 +91,7 @@ void free_handle(gbs_mat A) {
   void *dev[] = {A->row_ptr, A->col, A->val, A->val32, A->perm, A->jmap, A->diag_pos,
                  A->dinv, A->dinv32, A->r, A->p, A->q, A->r32, A->p32, A->q32, A->d32,
                  A->part, A->sys_cnt, A->st, A->ctl, A->call, A->cta_order,
-                 A->kv, A->sys_row0};  // sys_slice0 lies inside sys_row0's block
+                 A->kv, A->sys_row0, A->halo_flags};  // sys_slice0 lies inside sys_row0's
   for (void *p : dev) dev_free(p, nullptr);
   free_table(A->ta);
   free_table(A->te);
@@ -554,6 +554,10 @@ static int autotune(gbs_mat A, cudaStream_t s, Tuning *out, float *out_ms) {
     Tuning t = base;
     t.cg_form = GBS_CG_SINGLE_REDUCTION;
     timed(t);
+    if (st == GBS_OK && !per_system) {  // the one-kernel form (where it fits, else two)
+      t.cg_form = GBS_CG_SINGLE_KERNEL;
+      timed(t);
+    }
     const int64_t nz = per_system ? A->max_sys_nnz : A->nnz;
     const int64_t rows = per_system ? A->max_sys_rows : A->nrows;
     if (st == GBS_OK && (per_system || nz + 8 * rows <= 16 * CTA_AUTO_WORK)) {
@@ -695,8 +699,9 @@ int mat_autotune_file(gbs_mat A, const char *path, int32_t *from_cache, void *st
 
 int mat_set_cg_form(gbs_mat A, int32_t form) {
   GBS_TRY(check_mat(A, "mat_set_cg_form"));
-  if (form != GBS_CG_TEXTBOOK && form != GBS_CG_SINGLE_REDUCTION) {
-    set_error("mat_set_cg_form: form must be GBS_CG_TEXTBOOK or GBS_CG_SINGLE_REDUCTION");
+  if (form != GBS_CG_TEXTBOOK && form != GBS_CG_SINGLE_REDUCTION && form != GBS_CG_SINGLE_KERNEL) {
+    set_error("mat_set_cg_form: form must be GBS_CG_TEXTBOOK, GBS_CG_SINGLE_REDUCTION or "
+              "GBS_CG_SINGLE_KERNEL");
     return GBS_ERR_ARG;
   }
   A->cg_form = form;

@@ -78,6 +78,7 @@ struct SysState {
   double tau, theta, eta;  // TFQMR: quasi-residual recurrence (eta of the last half step)
   double coef;             // TFQMR: theta^2 eta / alpha for the next d update
   double gam;              // single-reduction CG: r.u of the start residual
+  double thr2lo, thr2hi;   // bounds of thr^2 (set_thr): ||r|| <= thr decided from ||r||^2
   int32_t status;
   int32_t active;   // 1 while the system still iterates
   int32_t iterations;
@@ -89,7 +90,7 @@ struct SysState {
   int32_t zero_x;   // b == 0: x must be set to 0
   int32_t m;        // TFQMR: half steps taken
   int32_t pend;     // TFQMR: x += eta D^-1 d of the last half step not yet applied
-  int32_t pad;
+  int32_t rn_stale; // rnorm not yet taken from rr (the closing kernel takes it)
 };
 
 // Work vectors of the solvers in krylov.cu (TFQMR: w, y1, y2, rt, v, B y1,
@@ -99,7 +100,7 @@ constexpr int KRYLOV_NVEC = 9;
 
 // Cached solve graphs of a handle, by loop kind.
 enum { GBS_GRAPH_CG = 0, GBS_GRAPH_CG32 = 1, GBS_GRAPH_BICG = 2, GBS_GRAPH_TFQMR = 3,
-       GBS_GRAPH_PIPECG = 4, GBS_GRAPH_CGSR = 5, GBS_GRAPH_KINDS = 6 };
+       GBS_GRAPH_PIPECG = 4, GBS_GRAPH_CGSR = 5, GBS_GRAPH_CGSR1 = 6, GBS_GRAPH_KINDS = 7 };
 
 // Per-solve control words (device).  Zeroed before every solve.
 struct DevCtl {
@@ -183,7 +184,11 @@ struct gbs_mat_s {
   int32_t lanes = 0;
   int32_t ctas_per_sm = 0;      // grid cap per SM, 0 = as many as fit (one wave)
   int32_t solver = 0;           // GBS_SOLVER_AUTO / PHASES / CTA
-  int32_t cg_form = 0;          // GBS_CG_TEXTBOOK / GBS_CG_SINGLE_REDUCTION (phase kernels)
+  int32_t cg_form = 0;          // GBS_CG_TEXTBOOK / _SINGLE_REDUCTION / _SINGLE_KERNEL
+  // one-kernel single-reduction CG: table A's CTA c waits, before its row
+  // products, for CTAs c - halo_lo .. c - halo_lo + halo_n - 1 (mod grid) to
+  // have updated their rows of u (set by build_plan from col_span)
+  int32_t halo_lo = 0, halo_n = 0;
   int32_t *cta_order = nullptr; // nsys: systems by decreasing rows (per-CTA solver)
   int64_t max_sys_rows = 0, max_sys_nnz = 0;
 
@@ -193,6 +198,8 @@ struct gbs_mat_s {
   double *part = nullptr;       // reduction slots (table A region, then table E)
   int64_t part_cap = 0;
   unsigned *sys_cnt = nullptr;  // nsys arrival counters
+  int32_t *halo_flags = nullptr;  // table A grid: last iteration each CTA published
+  int32_t halo_cap = 0;
   gbs::SysState *st = nullptr;  // nsys
   gbs::DevCtl *ctl = nullptr;
   gbs::CallArgs *call = nullptr;

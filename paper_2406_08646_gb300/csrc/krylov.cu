@@ -464,8 +464,8 @@ struct NsView {
 };
 __device__ __forceinline__ NsView ns_view(const PcgArgs &a, int s) {
   const SysState *S = a.st + s;
-  return NsView{ldcg(&S->alpha), ldcg(&S->beta), ldcg(&S->eta), ldcg(&S->coef),
-                ldcg(&S->first)};
+  return NsView{ld_state(&S->alpha), ld_state(&S->beta), ld_state(&S->eta),
+                ld_state(&S->coef), ld_state(&S->first)};
 }
 
 // Row products of block b with A^T's sliced copy.
@@ -531,7 +531,7 @@ __device__ __forceinline__ void bicg_setup(const PcgArgs &a, double *red) {
     SysState &S = a.st[s];
     memset(&S, 0, sizeof(SysState));
     S.bb = tot[1];
-    S.thr = C.rtol * sqrt(S.bb);
+    set_thr(S, C.rtol * sqrt(S.bb));
     S.rr = tot[0];
     S.rho = tot[2];
     S.rnorm0 = S.rnorm = sqrt(tot[0]);
@@ -676,7 +676,7 @@ __device__ __forceinline__ void tfq_setup(const PcgArgs &a, double *red) {
     SysState &S = a.st[s];
     memset(&S, 0, sizeof(SysState));
     S.bb = tot[1];
-    S.thr = C.rtol * sqrt(S.bb);
+    set_thr(S, C.rtol * sqrt(S.bb));
     S.rr = tot[0];
     S.rnorm0 = S.rnorm = sqrt(tot[0]);
     int st = kry_start_status(tot[2], tot[1]);
@@ -844,8 +844,8 @@ __device__ __forceinline__ void tfq_pending_x(const PcgArgs &a, double *red) {
   double eta = 0.0;
   auto want = [&](int s) -> int {
     const SysState *S = a.st + s;
-    if (ldcg(&S->active) || !ldcg(&S->pend)) return 0;
-    eta = ldcg(&S->eta);
+    if (ld_state(&S->active) || !ld_state(&S->pend)) return 0;
+    eta = ld_state(&S->eta);
     return 1;
   };
   auto work = [&](int, int, int r0, int r1, double(&)[1]) {
@@ -1002,6 +1002,49 @@ __device__ __forceinline__ int pipe_top(const CallArgs &C, SysState &S, double g
   return -1;
 }
 
+// The single-reduction CG's step at the top of an iteration, run by all
+// lanes of one warp: pipe_top's tests and recurrences, with the tests on
+// the integer pipe (finite64, positive64, meets_thr), the square root of
+// ||r||^2 taken only when the system stops (rn_stale otherwise: the closing
+// kernel takes it), and beta = gamma / rho and gamma / alpha_prev divided in
+// one instruction sequence on two lanes -- the last CTA's scalar step waits
+// on each FP64 instruction.  den = delta - beta (gamma / alpha_prev) is the
+// oracle's delta - (beta gamma) / alpha_prev with the product and quotient
+// taken in the other order (equal in exact arithmetic).  Lane 0 writes the
+// state; the status is the same on every lane.
+__device__ __forceinline__ int sr_top(const CallArgs &C, SysState &S, double gamma, double delta,
+                                      double rr, int lane) {
+  int st = -1;
+  if (!finite64(rr) || !finite64(gamma) || !finite64(delta)) st = GBS_ERR_NAN;
+  else if (meets_thr(rr, S)) st = GBS_OK;
+  else if (S.iterations >= C.maxit) st = GBS_ERR_MAXIT;
+  double beta = 0.0, den = delta;
+  if (st < 0 && !S.first) {
+    const double d = gamma / (lane == 1 ? S.alpha : S.rho);  // lane 0: beta, lane 1: gamma / alpha
+    beta = __shfl_sync(FULL_MASK, d, 0);
+    den = delta - beta * __shfl_sync(FULL_MASK, d, 1);
+  }
+  if (st < 0 && (!positive64(gamma) || !positive64(den))) st = GBS_ERR_BREAKDOWN;
+  if (st >= 0) {
+    if (lane == 0) {
+      S.rr = rr;
+      S.rnorm = sqrt(rr);
+      S.rn_stale = 0;
+    }
+    return st;
+  }
+  const double alpha = gamma / den;
+  if (lane == 0) {
+    S.rr = rr;
+    S.rn_stale = 1;
+    S.beta = beta;
+    S.alpha = alpha;
+    S.rho = gamma;
+    S.first = 0;
+  }
+  return -1;
+}
+
 // After pipe_top: a recursive convergence goes to the confirmation, any
 // other status ends the system.
 __device__ __forceinline__ void pipe_after_top(const PcgArgs &a, SysState &S, int st) {
@@ -1040,7 +1083,7 @@ __device__ __forceinline__ void pipe_setup(const PcgArgs &a, double *red) {
     SysState &S = a.st[s];
     memset(&S, 0, sizeof(SysState));
     S.bb = tot[1];
-    S.thr = C.rtol * sqrt(S.bb);
+    set_thr(S, C.rtol * sqrt(S.bb));
     S.rr = tot[0];
     S.rnorm0 = S.rnorm = sqrt(tot[0]);
     S.first = 1;
@@ -1100,10 +1143,10 @@ __device__ __forceinline__ void pipe_iterate(const PcgArgs &a, double *red) {
   int par = 0, mode = PIPE_ITER;
   auto want = [&](int s) -> int {
     const SysState *S = a.st + s;  // all loads issued together: one round trip
-    alpha = ldcg(&S->alpha);
-    beta = ldcg(&S->beta);
-    par = ldcg(&S->iterations) & 1;
-    mode = ldcg(&S->mode);
+    alpha = ld_state(&S->alpha);
+    beta = ld_state(&S->beta);
+    par = ld_state(&S->iterations) & 1;
+    mode = ld_state(&S->mode);
     return sys_active(a, s) ? 1 : 0;
   };
   auto work = [&](int, int blk, int r0, int r1, double(&acc)[3]) {
@@ -1272,7 +1315,7 @@ __device__ __forceinline__ void sr_setup(const PcgArgs &a, double *red) {
     SysState &S = a.st[s];
     memset(&S, 0, sizeof(SysState));
     S.bb = tot[1];
-    S.thr = C.rtol * sqrt(S.bb);
+    set_thr(S, C.rtol * sqrt(S.bb));
     S.rr = tot[0];
     S.gam = tot[3];
     S.rnorm0 = S.rnorm = sqrt(tot[0]);
@@ -1288,10 +1331,12 @@ __device__ __forceinline__ void sr_setup(const PcgArgs &a, double *red) {
 }
 
 // w = A u with delta = w.u; fin (the last arriver): the tests, alpha, beta.
-// gamma and ||r||^2 are the update kernel's slot partials, summed while the
-// product runs -- by warp 1 of the CTA that holds the system's first block,
-// before that CTA's own arrival, so the sums are in S.gam / S.rr when the
-// last arriver reads them -- and on the first trip the setup's.  Table A.
+// gamma and ||r||^2 are the update kernel's slot partials (on the first trip
+// the setup's).  Ensemble solves sum them in the product kernel's wide
+// finish, with its own slots; per-system solves, whose finish is warp 0's,
+// sum them while the product runs -- by warp 1 of the CTA that holds the
+// system's first block, before that CTA's own arrival, so the sums are in
+// S.gam / S.rr when the last arriver reads them.  Table A.
 // (Not inlined, like sr_fin below: the product kernel runs at 32 registers,
 // and these rarely run paths would otherwise make the compiler spill around
 // the row loop.)
@@ -1308,21 +1353,35 @@ __device__ __noinline__ void sr_presum(const PcgArgs &a, int s) {
   }
 }
 
-__device__ __noinline__ void sr_fin(const PcgArgs &a, int s, double delta) {
+__device__ __noinline__ void sr_fin(const PcgArgs &a, int s, double delta, double gam,
+                                    double rr, int lane) {
   SysState &S = a.st[s];
-  const int st = pipe_top(*a.call, S, ldcg(&S.gam), delta, ldcg(&S.rr), true);
-  if (st >= 0) deactivate(a, S, st);
-  else S.iterations += 1;  // the update kernel applies this iteration
+  // on the first trip, and for per-system solves, r.u and ||r||^2 are in the
+  // state (the setup's, or sr_presum's sums); ensemble solves get the update
+  // kernel's sums from the wide finish
+  if (!a.ensemble || S.first) {
+    gam = ldcg(&S.gam);
+    rr = ldcg(&S.rr);
+  }
+  const int st = sr_top(*a.call, S, gam, delta, rr, lane);
+  if (lane == 0) {
+    if (st >= 0) deactivate(a, S, st);
+    else S.iterations += 1;  // the update kernel applies this iteration
+  }
 }
 
+template <bool ENS>
 __device__ __forceinline__ void sr_spmv(const PcgArgs &a, double *red) {
   const double *u = a.kv[1];
   double *w = a.kv[2];
   auto want = [&](int s) -> int {
     if (!sys_active(a, s)) return 0;
-    // warp 1 of the CTA whose first block of s is the system's first block
-    if (blockIdx.x == sys_b0(a, a.ta, s) % gridDim.x && (threadIdx.x >> 5) == 1)
-      sr_presum(a, s);
+    // per-system solves: warp 1 of the CTA whose first block of s is the
+    // system's first block (ensemble solves sum them in the wide finish)
+    if constexpr (!ENS) {
+      if (blockIdx.x == sys_b0(a, a.ta, s) % gridDim.x && (threadIdx.x >> 5) == 1)
+        sr_presum(a, s);
+    }
     return 1;
   };
   auto work = [&](int, int blk, int r0, int r1, double(&acc)[1]) {
@@ -1334,8 +1393,8 @@ __device__ __forceinline__ void sr_spmv(const PcgArgs &a, double *red) {
     row_products<double, 0>(a, blk, r0, r1, a.val, a.sval, u, f);
     acc[0] = dl;
   };
-  auto fin = [&](int s, double(&tot)[1]) { sr_fin(a, s, tot[0]); };
-  walk<1>(a, a.ta, 0, red, want, work, fin);
+  auto fin = [&](int s, double(&tot)[3], int lane) { sr_fin(a, s, tot[0], tot[1], tot[2], lane); };
+  walk<1, true, 2>(a, a.ta, 0, red, want, work, fin);
 }
 
 // p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = M^-1 r
@@ -1348,8 +1407,8 @@ __device__ __forceinline__ void sr_update(const PcgArgs &a, double *red) {
   double alpha = 0.0, beta = 0.0;
   auto want = [&](int s) -> int {
     const SysState *S = a.st + s;  // issued with the active flag: one round trip
-    alpha = ldcg(&S->alpha);
-    beta = ldcg(&S->beta);
+    alpha = ld_state(&S->alpha);
+    beta = ld_state(&S->beta);
     return sys_active(a, s) ? 1 : 0;
   };
   auto fin = [&](int, double(&)[2]) {};
@@ -1394,11 +1453,13 @@ __device__ __forceinline__ void sr_update(const PcgArgs &a, double *red) {
   walk<2, false>(a, a.te, a.part_e, red, want, work, fin);
 }
 
+// ENS: an ensemble solve (a.ensemble; no per-system pre-sums in the kernel)
+template <bool ENS>
 __global__ void NS_ROWS k_sr_spmv(PcgArgs a) {
   __shared__ double red[RED_SCRATCH1];
   if (!trip_live(a)) return;
   stamp_phase(a, 1);
-  sr_spmv(a, red);
+  sr_spmv<ENS>(a, red);
 }
 __global__ void __launch_bounds__(PHASE_TPB) k_sr_update(PcgArgs a) {
   __shared__ double red[RED_SCRATCH];
@@ -1430,18 +1491,203 @@ __global__ void NS_ROWS k_sr_final(PcgArgs a) {
 }
 
 // setup, WHILE { SpMV + reduction, update }, final residual.
-static LoopPlan cgsr_plan() {
+static LoopPlan cgsr_plan(bool ensemble) {
   LoopPlan P;
   memset(&P, 0, sizeof(P));
   P.npre = 1;
   P.pre[0] = k_sr_setup;
   P.nbody = 2;
-  P.body[0] = k_sr_spmv;
+  P.body[0] = ensemble ? k_sr_spmv<true> : k_sr_spmv<false>;
   P.body[1] = k_sr_update;
   P.body_e[1] = true;
   P.npost = 1;
   P.post[0] = k_sr_final;
   return P;
+}
+
+// ------------------------------------------------------------------ single-kernel form
+//
+// The single-reduction loop as ONE kernel per iteration (ensemble solves on
+// the sliced copy).  Between an iteration's vector update and its product
+// w = A u no global synchronisation is needed: the product of a row reads u
+// at the row's columns only, all within col_span rows of it.  So CTA c of
+// table A (blocks c, c + G, ...):
+//   1. updates its rows: p = u + beta p, s = w + beta s, x += alpha p,
+//      r -= alpha s, u = M^-1 r, with the partial r.u and r.r;
+//   2. publishes the iteration number in its flag (a barrier, a fence, a
+//      release store);
+//   3. waits until CTAs c - halo_lo .. c - halo_lo + halo_n - 1 (mod G) --
+//      those holding every row within col_span of its rows, a window
+//      build_plan derives from the block table -- have published it;
+//   4. runs its row products w = A u with the partial w.u;
+//   5. reduces the three partials; the last arriver runs the tests and the
+//      next alpha and beta (pipe_top, as the two-kernel form's product
+//      kernel does).
+// The kernel boundary orders step 4 of one iteration before step 1 of the
+// next (which overwrites u), so the flags are the only waits.  All CTAs of
+// the grid are resident at once (cooperative launch: the grid is at most the
+// kernel's occupancy times the SMs) and every CTA reaches step 2 without
+// waiting on another, so every wait ends; each is still bounded (HALO_WAIT_NS
+// of polling), after which the CTA records GBS_ERR_TIMEOUT in the control
+// words and goes on, and the fin ends the solve with that status.
+// Coherence: step 1 reads u through L2 (no L1 copy of an old value is made);
+// the gathers of step 4 may use L1: a block's rows start at a multiple of 32,
+// so each 128-byte line of u lies in one CTA's rows, and every line a CTA of
+// this SM brings into L1 after its wait belongs to a CTA that has finished
+// its update (L1 keeps nothing across launches).
+// Same iterates as the two-kernel form; r.u and r.r are summed over table
+// A's blocks instead of table E's, so they may differ from it in the last
+// bits.  Per iteration: one launch, one reduction, the two-kernel form's
+// FP64 work, and the vectors of the update read while the product's matrix
+// stream has not yet passed over them.
+constexpr uint64_t HALO_WAIT_NS = 1000000000ull;  // 1 s
+constexpr uint32_t HALO_MAX_POLLS = 1u << 22;     // and a poll count, whatever the clock
+
+// Step 3, by warp 0: lane l polls the flags of window entries l, l + 32, ...
+// With one block per CTA the window does not wrap around the grid (CTA c's
+// block is block c), with more it does (CTA c also holds c + G, ...).
+__device__ __forceinline__ void halo_wait(const PcgArgs &a, int32_t epoch) {
+  const int G = (int)gridDim.x;
+  const bool wrap = a.ta.nblocks > G;
+  const uint64_t t0 = global_ns();
+  bool late = false;
+  for (int j = (int)(threadIdx.x & 31); j < a.halo_n; j += 32) {
+    int c = (int)blockIdx.x - a.halo_lo + j;  // halo_lo < G and j < G
+    if (!wrap && (c < 0 || c >= G)) continue;
+    c = c < 0 ? c + G : (c >= G ? c - G : c);
+    const int32_t *f = a.halo_flags + c;
+    for (uint32_t polls = 0; !late && ld_acquire(f) < epoch;)
+      if (++polls >= HALO_MAX_POLLS || global_ns() - t0 > HALO_WAIT_NS) late = true;
+  }
+  if (late) atomicCAS(&a.ctl->err, 0, GBS_ERR_TIMEOUT);
+  __threadfence();
+  __syncwarp();
+}
+
+__global__ void NS_ROWS k_sr_fused(PcgArgs a) {
+  // per-warp partials: r.u and r.r of the update, w.u of the products (the
+  // sums need little shared memory, which leaves L1 its room for u)
+  __shared__ double wred[3][PHASE_TPB / 32];
+  const bool live = trip_live(a);
+  loop_control(a, live);  // after the previous iteration's tests (its fin)
+  if (!live) return;
+  stamp_phase(a, 2);
+  SysState *S = a.st;  // ensemble: one system
+  const int act = ld_state(&S->active);  // issued together: one round trip
+  const double al = ld_state(&S->alpha), be = ld_state(&S->beta);
+  const int32_t epoch = ld_state(&S->iterations);
+  if (!act) return;
+  const int G = (int)gridDim.x, nb = a.ta.nblocks;
+  double *x = a.call->x;
+  double *r = a.kv[0], *u = a.kv[1], *w = a.kv[2], *p = a.kv[3], *sv = a.kv[4];
+  double acc[2] = {0.0, 0.0};  // r.u, r.r
+  // 1. the update of the CTA's rows
+  for (int b = blockIdx.x; b < nb; b += G) {
+    const int r0 = __ldg(a.ta.row0 + b), r1 = __ldg(a.ta.row0 + b + 1);
+    for (int i = r0 + (int)threadIdx.x; i < r1; i += (int)blockDim.x) {
+      const double ui = __ldcg(u + i), wi = w[i], pv = p[i], sw = sv[i], xi = x[i], ri = r[i];
+      const double di = a.dinv[i];
+      const double pi = be == 0.0 ? ui : fma(be, pv, ui);  // beta = 0: p = u, s = w
+      const double si = be == 0.0 ? wi : fma(be, sw, wi);
+      p[i] = pi;
+      sv[i] = si;
+      x[i] = fma(al, pi, xi);
+      const double rn = fma(-al, si, ri);
+      const double un = di * rn;
+      r[i] = rn;
+      u[i] = un;
+      acc[0] = fma(rn, un, acc[0]);
+      acc[1] = fma(rn, rn, acc[1]);
+    }
+  }
+  // the update's partials wait in shared memory, one pair per warp, while the
+  // row products run
+  warp_sums<double, 2>(acc);
+  const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
+  if (lane == 0) {
+    wred[0][warp] = acc[0];
+    wred[1][warp] = acc[1];
+  }
+  // 2. publish, 3. wait for the window
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    st_release(a.halo_flags + blockIdx.x, epoch);
+  }
+  if (threadIdx.x < 32) halo_wait(a, epoch);
+  __syncthreads();
+  stamp_phase(a, 1);
+  // 4. the row products and w.u
+  int last = blockIdx.x;
+  double acc2 = 0.0;
+  for (int b = blockIdx.x; b < nb; b += G) {
+    const int s0 = __ldg(a.ta.slice0 + b), s1 = __ldg(a.ta.slice0 + b + 1);
+    double dl = acc2;
+    auto f = [&](int i, double y) {
+      w[i] = y;
+      dl = fma(y, __ldca(u + i), dl);
+    };
+    if (a.stream_matrix)
+      sell_rows<double, true, GATHER_CA>(a.sptr, a.srow0, a.scol, a.soff, a.sval, u, s0, s1, f);
+    else
+      sell_rows<double, false, GATHER_CA>(a.sptr, a.srow0, a.scol, a.soff, a.sval, u, s0, s1, f);
+    acc2 = dl;
+    last = b;
+  }
+  // 5. one reduction; the last arriver runs the tests and the next scalars
+  auto fin = [&](int s, double(&tot)[3], int lane) {
+    SysState &T = a.st[s];
+    int st = sr_top(*a.call, T, tot[0], tot[2], tot[1], lane);
+    const int err = ldcg(&a.ctl->err);  // a bounded wait that ran out
+    if (lane != 0) return;
+    if (err) {
+      st = err;
+      T.rnorm = sqrt(T.rr);
+      T.rn_stale = 0;
+    }
+    if (st >= 0) deactivate(a, T, st);
+    else T.iterations += 1;
+  };
+  acc2 = warp_sum(acc2);
+  if (lane == 0) wred[2][warp] = acc2;
+  __syncthreads();
+  if (warp != 0) return;
+  double tot[3];
+  const bool have = lane < (int)(blockDim.x >> 5);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) tot[k] = have ? wred[k][lane] : 0.0;
+  warp_sums<double, 3>(tot);
+  flush<3, true, true>(a, a.ta, 0, 0, last, tot, nullptr, false, fin);
+}
+
+// setup, first product (alpha for the first update), WHILE { one kernel },
+// final residual.
+static LoopPlan cgsr_fused_plan() {
+  LoopPlan P;
+  memset(&P, 0, sizeof(P));
+  P.npre = 2;
+  P.pre[0] = k_sr_setup;
+  P.pre[1] = k_sr_spmv<true>;
+  P.nbody = 1;
+  P.body[0] = k_sr_fused;
+  P.body_coop = true;
+  P.npost = 1;
+  P.post[0] = k_sr_final;
+  return P;
+}
+
+// The single-kernel form applies: an ensemble solve on the sliced copy whose
+// table A grid fits on the device at once.
+static bool fused_fits(gbs_mat A, bool per_system) {
+  if (per_system || A->lanes != GBS_SPMV_SELL || A->halo_n <= 0) return false;
+  int occ = 0, nsm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_sr_fused, PHASE_TPB, 0) !=
+          cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, A->device) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return A->ta.grid <= occ * nsm;
 }
 
 // ------------------------------------------------------------------ transpose
@@ -1598,7 +1844,9 @@ int solve_krylov(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool 
     PcgArgs pa = make_args(A, per_system, false);
     pa.stream_matrix = stream_matrix(A, bicg ? 24 : 12);
     if (pipe) return run_loop(A, pipecg_plan(), GBS_GRAPH_PIPECG, pa, b, x, o, per_system, s);
-    if (sr) return run_loop(A, cgsr_plan(), GBS_GRAPH_CGSR, pa, b, x, o, per_system, s);
+    if (sr && A->cg_form == GBS_CG_SINGLE_KERNEL && fused_fits(A, per_system))
+      return run_loop(A, cgsr_fused_plan(), GBS_GRAPH_CGSR1, pa, b, x, o, per_system, s);
+    if (sr) return run_loop(A, cgsr_plan(!per_system), GBS_GRAPH_CGSR, pa, b, x, o, per_system, s);
     return run_loop(A, bicg ? bicg_plan() : tfqmr_plan(),
                     bicg ? GBS_GRAPH_BICG : GBS_GRAPH_TFQMR, pa, b, x, o, per_system, s);
   }

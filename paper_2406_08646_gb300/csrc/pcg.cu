@@ -203,6 +203,19 @@ int ensure_solver_workspace(gbs_mat A, bool refined, cudaStream_t s) {
     drop_graphs(A);  // cached graphs hold the old pointer
     grew = true;
   }
+  // the one-kernel CG's flags, one per CTA of table A
+  if (A->halo_cap < A->ta.grid) {
+    if (A->halo_flags) {
+      GBS_TRY_CUDA(cudaStreamSynchronize(s));
+      dev_free(A->halo_flags, s);
+    }
+    A->halo_flags = nullptr;
+    A->halo_cap = 0;
+    GBS_TRY(dev_alloc(&A->halo_flags, (size_t)A->ta.grid, s));
+    A->halo_cap = A->ta.grid;
+    drop_graphs(A);
+    grew = true;
+  }
   if (grew) GBS_TRY_CUDA(cudaStreamSynchronize(s));
   return GBS_OK;
 }
@@ -272,6 +285,9 @@ PcgArgs make_args(gbs_mat A, bool per_system, bool refined) {
   a.st = A->st;
   a.ctl = A->ctl;
   a.call = A->call;
+  a.halo_flags = A->halo_flags;
+  a.halo_lo = A->halo_lo;
+  a.halo_n = A->halo_n;
   if (A->kv)
     for (int k = 0; k < KRYLOV_NVEC; ++k) a.kv[k] = A->kv + (size_t)k * (size_t)A->nrows;
   if (A->At) {
@@ -366,6 +382,14 @@ int build_loop_graph(gbs_mat A, const LoopPlan &P, PcgArgs a, cudaGraphExec_t *o
   e = cudaGraphAddMemsetNode(&n_st, g, &n_cnt, 1, &ms);
   if (e != cudaSuccess) return fail("memset");
   n_cnt = n_st;
+  if (P.body_coop) {  // the one-kernel CG's flags start below every iteration number
+    cudaGraphNode_t n_fl;
+    ms.dst = A->halo_flags;
+    ms.width = (size_t)A->ta.grid;
+    e = cudaGraphAddMemsetNode(&n_fl, g, &n_cnt, 1, &ms);
+    if (e != cudaSuccess) return fail("memset");
+    n_cnt = n_fl;
+  }
   cudaKernelNodeParams kp;
   cudaGraphNode_t prev = n_cnt;
   for (int k = 0; k < P.npre; ++k) {
@@ -389,6 +413,13 @@ int build_loop_graph(gbs_mat A, const LoopPlan &P, PcgArgs a, cudaGraphExec_t *o
     kp = kernel_node(P.body[k % P.nbody], grid(P.body_e[k % P.nbody]), args);
     e = cudaGraphAddKernelNode(&n, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
     if (e != cudaSuccess) return fail("loop body node");
+    if (P.body_coop) {
+      cudaLaunchAttributeValue v;
+      memset(&v, 0, sizeof(v));
+      v.cooperative = 1;
+      e = cudaGraphKernelNodeSetAttribute(n, cudaLaunchAttributeCooperative, &v);
+      if (e != cudaSuccess) return fail("cooperative loop body node");
+    }
     prev = n;
   }
   prev = n_loop;
@@ -427,8 +458,22 @@ int run_loop_stepped(const LoopPlan &P, PcgArgs a, int grid_a, int grid_e, int64
   for (int64_t t = 0;;) {
     for (int k = 0; k < STEP_CHUNK; ++k, ++t) {
       a.trip = (int32_t)(t & 1);
-      for (int q = 0; q < P.nbody; ++q)
-        P.body[q]<<<grid(P.body_e[q]), PHASE_TPB, 0, s>>>(a);
+      for (int q = 0; q < P.nbody; ++q) {
+        if (P.body_coop) {
+          cudaLaunchConfig_t cfg = {};
+          cfg.gridDim = dim3(grid(P.body_e[q]));
+          cfg.blockDim = dim3(PHASE_TPB);
+          cfg.stream = s;
+          cudaLaunchAttribute at;
+          at.id = cudaLaunchAttributeCooperative;
+          at.val.cooperative = 1;
+          cfg.attrs = &at;
+          cfg.numAttrs = 1;
+          GBS_TRY_CUDA(cudaLaunchKernelEx(&cfg, P.body[q], a));
+        } else {
+          P.body[q]<<<grid(P.body_e[q]), PHASE_TPB, 0, s>>>(a);
+        }
+      }
       GBS_LAUNCHED(P.nbody);
     }
     int32_t stop = 0;  // written by the last trip launched, for the next one
@@ -528,8 +573,8 @@ int solve(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool per_sys
   const bool refined = o.precision == GBS_FP32_REFINED;
   // the handle's CG form: FP64 CG on the phase kernels may run as the
   // single-reduction loop (same iterates in exact arithmetic, two kernels per
-  // iteration instead of three)
-  if (!refined && A->cg_form == GBS_CG_SINGLE_REDUCTION && A->lanes == GBS_SPMV_SELL &&
+  // iteration instead of three, or one)
+  if (!refined && A->cg_form != GBS_CG_TEXTBOOK && A->lanes == GBS_SPMV_SELL &&
       A->solver != GBS_SOLVER_CLUSTER && !use_cta_solver(A, per_system)) {
     ksp_opts sr = o;
     sr.method = GBS_KSP_CGSR;
@@ -587,6 +632,8 @@ int run_loop(gbs_mat A, const LoopPlan &P, int kind, const PcgArgs &a, const dou
     GBS_TRY_CUDA(cudaMemsetAsync(A->ctl, 0, sizeof(DevCtl), s));
     GBS_TRY_CUDA(cudaMemsetAsync(A->sys_cnt, 0, sizeof(unsigned) * A->nsys, s));
     GBS_TRY_CUDA(cudaMemsetAsync(A->st, 0, sizeof(SysState) * A->nsys, s));
+    if (P.body_coop)
+      GBS_TRY_CUDA(cudaMemsetAsync(A->halo_flags, 0, sizeof(int32_t) * A->ta.grid, s));
     GBS_TRY(put_call(A->call, call_args(b, x, o), s));
     return run_loop_stepped(P, a, A->ta.grid, A->te.grid, max_trips_for(o), A->ctl, s);
   }

@@ -88,6 +88,8 @@ struct PcgArgs {
   const int32_t *tptr, *tcol;       // sliced-ELL copy of A^T (BiCG), A's slices
   const int16_t *toff;              //   (its 16-bit offsets, tcol null then)
   const double *tval;
+  int32_t *halo_flags;              // one-kernel CG: iteration each CTA published
+  int32_t halo_lo, halo_n;          //   and the window of CTAs it waits for
 };
 
 // A solve loop on the phase kernels: the start-up kernels, the WHILE body
@@ -101,6 +103,7 @@ struct LoopPlan {
   bool body_e[4];
   void (*post[2])(PcgArgs);
   bool post_e[2];
+  bool body_coop;  // the body's kernels wait on one another's CTAs: cooperative launch
 };
 
 PcgArgs make_args(gbs_mat A, bool per_system, bool refined);
@@ -196,12 +199,86 @@ __device__ __forceinline__ void slot_sums(const double *part, int64_t base, int 
 // fin that needs the warp, e.g. to sum another kernel's slots).  ARRIVE =
 // false: only the slot is written (no arrival count, no fin): a later
 // kernel's fin sums those slots itself.  f32: FP32 accumulation throughout.
-template <int NV, bool ARRIVE = true, class Fin>
+// REDUCED: acc already holds the CTA's totals in warp 0 (no block sums).
+//
+// Ensemble solves (FP64, !REDUCED) finish wide: thread 0 counts the CTA in,
+// every thread learns at a barrier whether it was the last, and the last
+// CTA's first four warps sum the slots (wide_sums: one L2 round trip and
+// the adds spread over the four FP64 pipes, where warp 0 alone waits on
+// several round trips and adds on one pipe).  NE > 0 (wide
+// finish only): the last CTA also sums NE values of each of the system's
+// slots in table E's region -- partials another kernel wrote without
+// arrival -- and fin gets NV + NE totals (the NE are zero on the warp-0
+// finish of per-system solves).
+
+// The last CTA's sums, by its first four warps (one per sub-partition, whose
+// FP64 pipes work in parallel -- the FP64 adds, not the loads, are what
+// these sums wait on): thread i loads slots i, i + 128, ... of the NV-value
+// region, a batch of up to 8 / NV slots in flight before the first add,
+// adds them in slot order, then does the same over the NE-value region;
+// warp_sums adds each warp's lanes, and warp 0 adds the four warps' sums
+// with one lane per value.  A fixed order; one L2 round trip a region for up
+// to 1024 / N slots.  Totals on every lane of warp 0.  (Measured on the Q1
+// 96^3 CG against warp 0 alone, as in per-system solves: 73.6 against 75.4
+// us per iteration; issuing both regions' loads before any add, with twelve
+// values a thread in flight, gave 75.5.)
+constexpr int WIDE_WARPS = 4;
+template <int N>
+__device__ __forceinline__ void wide_region(const double *part, int64_t base, int ns, int off,
+                                            double *v) {
+  constexpr int NT = 32 * WIDE_WARPS;
+  constexpr int WIDE_BATCH = N == 1 ? 8 : (N == 2 ? 4 : 2);
+  for (int i0 = (int)threadIdx.x; i0 < ns; i0 += NT * WIDE_BATCH) {
+    double u[WIDE_BATCH][N];
+#pragma unroll
+    for (int j = 0; j < WIDE_BATCH; ++j)
+#pragma unroll
+      for (int k = 0; k < N; ++k)
+        u[j][k] = i0 + j * NT < ns ? ldcg(part + (base + i0 + j * NT) * SLOT_STRIDE + k) : 0.0;
+#pragma unroll
+    for (int j = 0; j < WIDE_BATCH; ++j)
+      if (i0 + j * NT < ns) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) v[off + k] += u[j][k];
+      }
+  }
+}
+
+template <int NV, int NE>
+__device__ __noinline__ void wide_sums(const double *part, int64_t base, int ns,
+                                       int64_t ebase, int ens, double (&tot)[NV + NE]) {
+  constexpr int NT = NV + NE;
+  static_assert(NT >= 1 && NT <= 4, "wide_sums: 1 to 4 values");
+  __shared__ double ws[WIDE_WARPS][NT];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (w < WIDE_WARPS) {
+    double v[NT];
+#pragma unroll
+    for (int k = 0; k < NT; ++k) v[k] = 0.0;
+    wide_region<NV>(part, base, ns, 0, v);
+    if constexpr (NE > 0) wide_region<NE>(part, ebase, ens, NV, v);
+    warp_sums<double, NT>(v);
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < NT; ++k) ws[w][k] = v[k];
+    }
+  }
+  __syncthreads();
+  if (w == 0) {
+    const int k = lane < NT ? lane : 0;
+    const double t = (ws[0][k] + ws[1][k]) + (ws[2][k] + ws[3][k]);
+#pragma unroll
+    for (int q = 0; q < NT; ++q) tot[q] = __shfl_sync(FULL_MASK, t, q);
+  }
+}
+
+template <int NV, bool ARRIVE = true, bool REDUCED = false, int NE = 0, class Fin>
 __device__ __forceinline__ void flush(const PcgArgs &a, const BlockTable &t, int64_t part_off,
                                       int s, int b, double (&acc)[NV], double *red, bool f32,
                                       Fin &fin) {
   const int G = gridDim.x;
-  if (f32) {
+  if constexpr (REDUCED) {
+  } else if (f32) {
     float v[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) v[k] = (float)acc[k];
@@ -215,6 +292,32 @@ __device__ __forceinline__ void flush(const PcgArgs &a, const BlockTable &t, int
   const int ns = min(nb, G);
   const int slot = (b - b0) % G;
   const int64_t base = part_off + sys_slot0(a, t, s);
+  constexpr int NT = NV + NE;
+  if constexpr (ARRIVE && !REDUCED) {
+    if (a.ensemble && !f32) {  // uniform over the CTA
+      __shared__ int last;
+      if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) a.part[(base + slot) * SLOT_STRIDE + k] = acc[k];
+        __threadfence();
+        last = atomicAdd(a.sys_cnt + s, 1u) == (unsigned)(ns - 1);
+      }
+      __syncthreads();
+      if (!last) return;
+      double tot[NT];
+      wide_sums<NV, NE>(a.part, base, ns, a.part_e + sys_slot0(a, a.te, s),
+                        min(sys_nblk(a, a.te, s), a.grid_e), tot);
+      if ((threadIdx.x >> 5) != 0) return;
+      const int lane = threadIdx.x & 31;
+      if (lane == 0) a.sys_cnt[s] = 0u;
+      if constexpr (std::is_invocable_v<Fin &, int, double(&)[NT], int>) {
+        fin(s, tot, lane);
+      } else {
+        if (lane == 0) fin(s, tot);
+      }
+      return;
+    }
+  }
   // Warp 0 alone finishes: the other warps go on to their next blocks (or
   // exit) at once instead of waiting at a barrier for the fence and the
   // arrival count.  The last CTA's warp 0 reads the slots through L2
@@ -242,7 +345,10 @@ __device__ __forceinline__ void flush(const PcgArgs &a, const BlockTable &t, int
   if (__shfl_sync(FULL_MASK, prev, 0) != (unsigned)(ns - 1)) return;
   // lane l adds slots l, l + 32, ... (each slot's NV values are adjacent),
   // then warp_sums adds the lanes
-  double tot[NV];
+  double tot[NT];
+#pragma unroll
+  for (int k = NV; k < NT; ++k) tot[k] = 0.0;
+  double (&tv)[NV] = *reinterpret_cast<double(*)[NV]>(tot);
   if (f32) {
     float x[NV];
 #pragma unroll
@@ -256,10 +362,10 @@ __device__ __forceinline__ void flush(const PcgArgs &a, const BlockTable &t, int
 #pragma unroll
     for (int k = 0; k < NV; ++k) tot[k] = (double)x[k];
   } else {
-    slot_sums<NV>(a.part, base, ns, tot);
+    slot_sums<NV>(a.part, base, ns, tv);
   }
   if (lane == 0) a.sys_cnt[s] = 0u;
-  if constexpr (std::is_invocable_v<Fin &, int, double(&)[NV], int>) {
+  if constexpr (std::is_invocable_v<Fin &, int, double(&)[NT], int>) {
     fin(s, tot, lane);
   } else {
     if (lane == 0) fin(s, tot);
@@ -271,7 +377,7 @@ __device__ __forceinline__ void flush(const PcgArgs &a, const BlockTable &t, int
 // unchanged until the system's fin runs); work(s, b, r0, r1, acc) processes
 // block b, rows [r0, r1).  A CTA meets each system in one run of consecutive visits, so it
 // flushes once per system it touches (NV == 0: no reduction).
-template <int NV, bool ARRIVE = true, class Want, class Work, class Fin>
+template <int NV, bool ARRIVE = true, int NE = 0, class Want, class Work, class Fin>
 __device__ __forceinline__ void walk(const PcgArgs &a, const BlockTable &t, int64_t part_off,
                                      double *red, Want &want, Work &work, Fin &fin) {
   constexpr int NA = NV > 0 ? NV : 1;
@@ -285,7 +391,7 @@ __device__ __forceinline__ void walk(const PcgArgs &a, const BlockTable &t, int6
     const int r0 = __ldg(t.row0 + b), r1 = __ldg(t.row0 + b + 1);  // issued with want's loads
     if (s != cur_s) {
       if constexpr (NV > 0) {
-        if (kind) flush<NV, ARRIVE>(a, t, part_off, cur_s, cur_b, acc, red, kind == 2, fin);
+        if (kind) flush<NV, ARRIVE, false, NE>(a, t, part_off, cur_s, cur_b, acc, red, kind == 2, fin);
       }
       cur_s = s;
       kind = want(s);
@@ -297,7 +403,7 @@ __device__ __forceinline__ void walk(const PcgArgs &a, const BlockTable &t, int6
     work(s, b, r0, r1, acc);
   }
   if constexpr (NV > 0) {
-    if (kind) flush<NV, ARRIVE>(a, t, part_off, cur_s, cur_b, acc, red, kind == 2, fin);
+    if (kind) flush<NV, ARRIVE, false, NE>(a, t, part_off, cur_s, cur_b, acc, red, kind == 2, fin);
   }
 }
 
@@ -547,6 +653,43 @@ __device__ __forceinline__ void row_products(const PcgArgs &a, int b, int r0, in
     csr_rows<T, L>(a.row_ptr, a.col, csr_val, x, r0, r1, f);
 }
 
+// The convergence threshold thr = rtol ||b_s|| and two bounds of thr^2
+// (FP64 roundings included: thr2lo <= thr^2 (1 - 2^-51) and thr2hi >=
+// thr^2 (1 + 2^-49) in real arithmetic), so that ||r|| <= thr, i.e.
+// RN(sqrt(rr)) <= thr, is decided from rr alone except within about 2^-49
+// of thr^2: rr <= thr2lo gives sqrt(rr) <= thr exactly, hence its rounding
+// too (thr is a double), and rr > thr2hi gives sqrt(rr) > thr (1 + 2^-51),
+// which rounds above thr (half an ulp of thr is at most thr 2^-53).  Where
+// thr^2 leaves the normal range the square root decides.
+__device__ __forceinline__ void set_thr(SysState &S, double thr) {
+  S.thr = thr;
+  S.thr2lo = thr * thr * (1.0 - 0x1p-50);
+  S.thr2hi = thr * thr * (1.0 + 0x1p-48);
+}
+// ||r|| <= thr from rr = ||r||^2 >= 0 (the comparisons on the bits, valid
+// for non-negative doubles; NaN compares above every bound and fails).
+__device__ __forceinline__ bool meets_thr(double rr, const SysState &S) {
+  const long long b = __double_as_longlong(rr);
+  const long long lo = __double_as_longlong(S.thr2lo), hi = __double_as_longlong(S.thr2hi);
+  constexpr long long NORMAL_MIN = 0x0010000000000000LL;  // bits of 2^-1022
+  if (b <= lo && lo >= NORMAL_MIN) return true;
+  if (b > hi && hi >= NORMAL_MIN) return false;
+  return sqrt(rr) <= S.thr;
+}
+
+// A system's state as a kernel reads it on meeting the system (want): it was
+// written by earlier kernels only -- a fin writes it after every CTA of its
+// launch that touches the system has read it -- and L1 holds nothing across
+// launches, so the warps of a CTA may read it through L1: about one L2
+// request per CTA instead of one per warp.  (With L2 loads the whole grid's
+// warps queued on the same few lines at one L2 slice: measured on GB300, a
+// 607-CTA launch's CTAs began their work over 8 us instead of 2.6 us, and
+// CG on the Q1 96^3 system took 77.3 instead of 75.3 us per iteration.)
+template <typename T>
+__device__ __forceinline__ T ld_state(const T *p) {
+  return __ldca(p);
+}
+
 // Per-system scalars a phase needs, read once per system run.
 struct SysView {
   double alpha, beta, scale;
@@ -554,11 +697,11 @@ struct SysView {
 };
 __device__ __forceinline__ SysView view_sys(const PcgArgs &a, int s) {
   const SysState *S = a.st + s;
-  return SysView{ldcg(&S->alpha), ldcg(&S->beta), ldcg(&S->scale),
-                 ldcg(&S->mode),  ldcg(&S->first), ldcg(&S->zero_x)};
+  return SysView{ld_state(&S->alpha), ld_state(&S->beta), ld_state(&S->scale),
+                 ld_state(&S->mode),  ld_state(&S->first), ld_state(&S->zero_x)};
 }
 __device__ __forceinline__ bool sys_active(const PcgArgs &a, int s) {
-  return ldcg(&a.st[s].active) != 0;
+  return ld_state(&a.st[s].active) != 0;
 }
 
 // ------------------------------------------------------------------ setup
@@ -607,7 +750,7 @@ __device__ __forceinline__ void phase_setup(const PcgArgs &a, double *red) {
     const double rho = REFINED ? 0.0 : tot[0];
     memset(&S, 0, sizeof(SysState));
     S.bb = bb;
-    S.thr = C.rtol * sqrt(S.bb);
+    set_thr(S, C.rtol * sqrt(S.bb));
     S.rho = rho;
     S.rr = rr;
     S.rnorm0 = S.rnorm = sqrt(rr);
@@ -647,11 +790,11 @@ __device__ __forceinline__ void phase_A(const PcgArgs &a, double *red) {
   const CallArgs &C = *a.call;
   auto fin = [&](int s, double(&tot)[1]) {
     SysState &S = a.st[s];
-    if (!REFINED) {
+    if (!REFINED) {  // (tests on the bits: see finite64)
       const double sigma = tot[0];
       S.iterations += 1;
-      if (isnan(sigma)) deactivate(a, S, GBS_ERR_NAN);
-      else if (!(sigma > 0.0)) deactivate(a, S, GBS_ERR_BREAKDOWN);
+      if (nan64(sigma)) deactivate(a, S, GBS_ERR_NAN);
+      else if (!positive64(sigma)) deactivate(a, S, GBS_ERR_BREAKDOWN);
       else S.alpha = S.rho / sigma;
     } else if (S.mode == M_INNER) {
       const float sigma = (float)tot[0];
@@ -686,7 +829,7 @@ __device__ __forceinline__ void phase_A(const PcgArgs &a, double *red) {
   };
   int mode = M_INNER;
   auto want = [&](int s) -> int {
-    mode = ldcg(&a.st[s].mode);  // issued with the active flag: one round trip
+    mode = ld_state(&a.st[s].mode);  // issued with the active flag: one round trip
     if (!sys_active(a, s)) return 0;
     if (!REFINED) return 1;
     return mode == M_INNER ? 2 : (mode == M_XUPD ? 1 : 0);
@@ -731,14 +874,20 @@ __device__ __forceinline__ void phase_B(const PcgArgs &a, double *red) {
   auto fin = [&](int s, double(&tot)[2]) {
     SysState &S = a.st[s];
     if (!REFINED) {
+      // tests on the bits, ||r|| <= thr from ||r||^2, and the square root
+      // only when the system stops (the closing kernel takes it otherwise)
       const double rho_new = tot[0], rr = tot[1];
-      const double rn = sqrt(rr);
       S.rr = rr;
-      S.rnorm = rn;
-      if (!isfinite(rn) || !isfinite(rho_new)) deactivate(a, S, GBS_ERR_NAN);
-      else if (rn <= S.thr) deactivate(a, S, GBS_OK);
-      else if (S.iterations >= C.maxit) deactivate(a, S, GBS_ERR_MAXIT);
-      else {
+      int st = -1;
+      if (!finite64(rr) || !finite64(rho_new)) st = GBS_ERR_NAN;
+      else if (meets_thr(rr, S)) st = GBS_OK;
+      else if (S.iterations >= C.maxit) st = GBS_ERR_MAXIT;
+      if (st >= 0) {
+        S.rnorm = sqrt(rr);
+        S.rn_stale = 0;
+        deactivate(a, S, st);
+      } else {
+        S.rn_stale = 1;
         S.beta = rho_new / S.rho;
         S.rho = rho_new;
       }
@@ -902,7 +1051,7 @@ __device__ __forceinline__ void phase_final(const PcgArgs &a, double *red) {
   double *x = C.x;
   int zero = 0;
   auto want = [&](int s) -> int {
-    zero = ldcg(&a.st[s].zero_x);
+    zero = ld_state(&a.st[s].zero_x);
     return 1;
   };
   auto work = [&](int, int blk, int r0, int r1, double(&acc)[1]) {
@@ -918,7 +1067,14 @@ __device__ __forceinline__ void phase_final(const PcgArgs &a, double *red) {
     row_products<double, L>(a, blk, r0, r1, a.val, a.sval, x, f);
     acc[0] = tt;
   };
-  auto fin = [&](int s, double(&tot)[1]) { a.st[s].tt = tot[0]; };
+  auto fin = [&](int s, double(&tot)[1]) {
+    SysState &S = a.st[s];
+    S.tt = tot[0];
+    if (S.rn_stale) {  // a loop stopped with the system running (trip cap, time limit)
+      S.rnorm = sqrt(S.rr);
+      S.rn_stale = 0;
+    }
+  };
   walk<1>(a, a.ta, 0, red, want, work, fin);
 }
 

@@ -151,6 +151,42 @@ static int build_table(gbs_mat A, int32_t R, int32_t cap_per_sm, TableDev &t, cu
   return GBS_OK;
 }
 
+// The one-kernel CG's wait window over table A (blocks of R rows per
+// system, grid G, CTA c taking blocks c, c + G, ...): block b's row products
+// read rows within col_span of its own, i.e. blocks b - lo_b .. b + hi_b;
+// with lo and hi the largest lo_b and hi_b, CTA c's blocks need only CTAs
+// c - lo .. c + hi (mod G).  halo_lo = lo, halo_n = lo + hi + 1, or the
+// whole grid (halo_lo = 0, halo_n = G) when that window would wrap onto
+// itself.
+static void halo_window(gbs_mat A, int32_t R, const TableDev &t) {
+  std::vector<int64_t> row0;
+  for (int32_t q = 0; q < A->nsys; ++q)
+    for (int64_t r = A->row_off_h[q]; r < A->row_off_h[q + 1]; r += R) row0.push_back(r);
+  const int64_t nb = (int64_t)row0.size();
+  row0.push_back(A->nrows);
+  const int64_t span = A->col_span;
+  auto blk = [&](int64_t r) {  // the block holding row r, 0 <= r < nrows
+    return (int64_t)(std::upper_bound(row0.begin(), row0.end() - 1, r) - row0.begin()) - 1;
+  };
+  int64_t lo = 0, hi = 0;
+  for (int64_t b = 0; b < nb; ++b) {
+    const int64_t a = std::max<int64_t>(0, row0[b] - span);
+    const int64_t e = std::min<int64_t>(A->nrows - 1, row0[b + 1] - 1 + span);
+    lo = std::max(lo, b - blk(a));
+    hi = std::max(hi, blk(e) - b);
+  }
+  const int64_t G = std::max<int32_t>(t.grid, 1);
+  if (nb == 0) {
+    A->halo_lo = A->halo_n = 0;
+  } else if (lo + hi + 1 >= G) {
+    A->halo_lo = 0;
+    A->halo_n = (int32_t)G;
+  } else {
+    A->halo_lo = (int32_t)lo;
+    A->halo_n = (int32_t)(lo + hi + 1);
+  }
+}
+
 // nnz_off[q] = row_ptr[first row of system q] (q = 0 .. nsys).
 __global__ void k_system_nnz(int32_t nsys, const int32_t *__restrict__ row_ptr,
                              const int32_t *__restrict__ row0,
@@ -240,6 +276,7 @@ int build_plan(gbs_mat A, int32_t Ra, int32_t Re, int32_t kernel, int32_t ctas_p
   if (Ra == 0) Ra = auto_rows(cap_a);
   if (Re == 0) Re = auto_rows(cap_e);
   GBS_TRY(build_table(A, Ra, cap_a, A->ta, st));
+  halo_window(A, Ra, A->ta);
   GBS_TRY(build_table(A, Re, cap_e, A->te, st));
   GBS_TRY(build_cta_order(A, st));
   A->Ra = Ra;

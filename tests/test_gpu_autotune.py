@@ -54,7 +54,7 @@ def test_tuning_file_roundtrip_single_system():
         assert A.autotune(path) is False                 # tuned, line appended
         plan1, tun1 = A.plan(), A.tuning()
         assert tun1["solver"] in (B.SOLVER_PHASES, B.SOLVER_CTA)
-        assert tun1["cg_form"] in (B.CG_TEXTBOOK, B.CG_SINGLE_REDUCTION)
+        assert tun1["cg_form"] in (B.CG_TEXTBOOK, B.CG_SINGLE_REDUCTION, B.CG_SINGLE_KERNEL)
         check_parity(A, O, p.b, 1e-9)
         A.close()
         lines = open(path).read().splitlines()
