@@ -945,26 +945,75 @@ cleanup:
 
 // One thread per nonzero: a_p = v[perm[jmap[p]]] + v[perm[jmap[p]+1]] + ...
 // in increasing COO index order (Sec. 5: each thread accumulates into a single
-// nonzero, no atomics).  A thread takes two nonzeros per pass and loads each
-// segment's COO indices NUM_BATCH at a time before their values, so its two
-// chains of dependent loads (segment offsets -> COO indices -> values) are in
-// flight together rather than one term after the other.
+// nonzero, no atomics).  A segment's sum is a chain of dependent FP64 adds,
+// and a warp issues each add step for all its lanes: with consecutive
+// nonzeros on consecutive lanes every warp runs as many steps as its longest
+// segment (on the Q1 matrix segments hold 1, 2, 4 or 8 terms and nearly every
+// warp an 8), and FP64 instructions, scarce on this part, bound the kernel.
+// So a CTA takes a tile of NUM_TILE consecutive nonzeros, orders them by
+// segment length in shared memory (a counting sort over a few length
+// classes), and its warps sum them in that order -- lanes of a warp then
+// hold segments of about one length and issue only the adds those need --
+// into a shared buffer that the CTA writes back in nonzero order (coalesced).
+// Each thread takes two nonzeros and loads each segment's COO indices
+// NUM_BATCH at a time before their values, so its two chains of dependent
+// loads (COO indices -> values) are in flight together.  The lane a nonzero
+// lands on depends on shared-memory atomics; its sum does not.
 constexpr int NUM_BATCH = 4;
+constexpr int NUM_TPB = 256, NUM_TILE = 2 * NUM_TPB, NUM_CLASSES = 5;
 
-__global__ void k_coo_numeric(int64_t nnz, const int32_t *__restrict__ jmap,
-                              const int32_t *__restrict__ perm, const double *__restrict__ v,
-                              int mode, double *__restrict__ val) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += 2 * stride) {
-    const int64_t p2 = p + stride;
-    const bool two = p2 < nnz;
-    int32_t ta = __ldg(jmap + p);
-    const int32_t ea = __ldg(jmap + p + 1);
-    int32_t tb = two ? __ldg(jmap + p2) : 0;
-    const int32_t eb = two ? __ldg(jmap + p2 + 1) : 0;
-    const int32_t fa = ta, fb = tb;
+__device__ __forceinline__ int length_class(int32_t len) {
+  return len <= 1 ? 0 : (len == 2 ? 1 : (len <= 4 ? 2 : (len <= 8 ? 3 : 4)));
+}
+
+__global__ void __launch_bounds__(NUM_TPB)
+    k_coo_numeric(int64_t nnz, const int32_t *__restrict__ jmap,
+                  const int32_t *__restrict__ perm, const double *__restrict__ v, int mode,
+                  double *__restrict__ val) {
+  __shared__ int32_t s_j0[NUM_TILE], s_j1[NUM_TILE];
+  __shared__ int16_t s_order[NUM_TILE];
+  __shared__ double s_sum[NUM_TILE];
+  __shared__ int32_t s_cnt[NUM_CLASSES], s_base[NUM_CLASSES];
+  const int tid = (int)threadIdx.x;
+  for (int64_t t0 = (int64_t)blockIdx.x * NUM_TILE; t0 < nnz;
+       t0 += (int64_t)gridDim.x * NUM_TILE) {
+    const int nt = nnz - t0 < NUM_TILE ? (int)(nnz - t0) : NUM_TILE;
+    if (tid < NUM_CLASSES) s_cnt[tid] = 0;
+    __syncthreads();
+    // 1. segment bounds and length classes; ranks within a class
+    int cls[2], rank[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = tid + h * NUM_TPB;
+      cls[h] = -1;
+      if (i < nt) {
+        const int32_t j0 = __ldg(jmap + t0 + i), j1 = __ldg(jmap + t0 + i + 1);
+        s_j0[i] = j0;
+        s_j1[i] = j1;
+        cls[h] = length_class(j1 - j0);
+        rank[h] = atomicAdd(&s_cnt[cls[h]], 1);
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int b = 0;
+      for (int c = 0; c < NUM_CLASSES; ++c) {
+        s_base[c] = b;
+        b += s_cnt[c];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      if (cls[h] >= 0) s_order[s_base[cls[h]] + rank[h]] = (int16_t)(tid + h * NUM_TPB);
+    __syncthreads();
+    // 2. the sums, in class order: positions tid and tid + NUM_TPB
+    const bool has_a = tid < nt, has_b = tid + NUM_TPB < nt;
+    const int ia = has_a ? s_order[tid] : 0, ib = has_b ? s_order[tid + NUM_TPB] : 0;
+    int32_t ta = has_a ? s_j0[ia] : 0, tb = has_b ? s_j0[ib] : 0;
+    const int32_t ea = has_a ? s_j1[ia] : 0, eb = has_b ? s_j1[ib] : 0;
     double sa = 0.0, sb = 0.0;
-    while (ta < ea || tb < eb) {
+    for (bool first = true; ta < ea || tb < eb; first = false) {
       int32_t ka[NUM_BATCH], kb[NUM_BATCH];
       double xa[NUM_BATCH], xb[NUM_BATCH];
 #pragma unroll
@@ -977,16 +1026,31 @@ __global__ void k_coo_numeric(int64_t nnz, const int32_t *__restrict__ jmap,
         xa[u] = ta + u < ea ? __ldg(v + ka[u]) : 0.0;
         xb[u] = tb + u < eb ? __ldg(v + kb[u]) : 0.0;
       }
+      if (first) {  // a segment's first term starts its sum
+        sa = xa[0];
+        sb = xb[0];
+      }
 #pragma unroll
       for (int u = 0; u < NUM_BATCH; ++u) {  // in increasing COO index: plain adds
-        if (ta + u < ea) sa = (ta + u == fa) ? xa[u] : __dadd_rn(sa, xa[u]);
-        if (tb + u < eb) sb = (tb + u == fb) ? xb[u] : __dadd_rn(sb, xb[u]);
+        if ((!first || u > 0) && ta + u < ea) sa = __dadd_rn(sa, xa[u]);
+        if ((!first || u > 0) && tb + u < eb) sb = __dadd_rn(sb, xb[u]);
       }
       ta += NUM_BATCH;
       tb += NUM_BATCH;
     }
-    val[p] = (mode == GBS_ADD) ? __dadd_rn(val[p], sa) : sa;
-    if (two) val[p2] = (mode == GBS_ADD) ? __dadd_rn(val[p2], sb) : sb;
+    if (has_a) s_sum[ia] = sa;
+    if (has_b) s_sum[ib] = sb;
+    __syncthreads();
+    // 3. back in nonzero order
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = tid + h * NUM_TPB;
+      if (i < nt) {
+        const double x = s_sum[i];
+        val[t0 + i] = (mode == GBS_ADD) ? __dadd_rn(val[t0 + i], x) : x;
+      }
+    }
+    __syncthreads();  // the shared arrays are reused by the next tile
   }
 }
 
@@ -1004,8 +1068,8 @@ __global__ void k_jacobi(int64_t nrows, const int32_t *__restrict__ diag_pos,
 
 int launch_set_values(gbs_mat A, const double *v, int mode, cudaStream_t s) {
   if (A->nnz > 0) {
-    k_coo_numeric<<<grid_for((A->nnz + 1) / 2, 256), 256, 0, s>>>(A->nnz, A->jmap, A->perm, v, mode,
-                                                        A->val);
+    k_coo_numeric<<<grid_for((A->nnz + NUM_TILE - 1) / NUM_TILE, 1), NUM_TPB, 0, s>>>(
+        A->nnz, A->jmap, A->perm, v, mode, A->val);
     GBS_LAUNCHED(1);
   }
   if (A->nrows > 0) {
@@ -1060,8 +1124,8 @@ __global__ void k_vec_scatter(int64_t n, const int32_t *__restrict__ row_ptr,
 // numeric kernel, INSERT into val), then the scatter into y.
 int launch_vec_set_values(gbs_mat A, const double *v, int mode, double *y, cudaStream_t s) {
   if (A->nnz > 0) {
-    k_coo_numeric<<<grid_for((A->nnz + 1) / 2, 256), 256, 0, s>>>(A->nnz, A->jmap, A->perm, v, GBS_INSERT,
-                                                        A->val);
+    k_coo_numeric<<<grid_for((A->nnz + NUM_TILE - 1) / NUM_TILE, 1), NUM_TPB, 0, s>>>(
+        A->nnz, A->jmap, A->perm, v, GBS_INSERT, A->val);
     GBS_LAUNCHED(1);
   }
   if (A->nrows > 0) {
