@@ -35,8 +35,9 @@ prints its own JSON line; the default is the Q1 benchmark above):
       into 912,673 nodes): symbolic and numeric stage times, numeric GB/s
   async  time per solve against NNZ (Sec. 6.2's comparison, 2D 5-point, 3D
       7-point and 3D 27-point problems, 5e3 to 2.7e7 nonzeros): the three-kernel
-      CG loop, the two-kernel single-reduction CG, the one-kernel pipelined CG, the per-CTA and cluster CG (up to
-      2M nonzeros) and TFQMR, all device-driven
+      CG loop, the two-kernel and one-kernel single-reduction CG, the one-kernel
+      pipelined CG, the per-CTA CG (up to 2M nonzeros) and TFQMR, all
+      device-driven
   nonsym  batched TFQMR and BiCG (Jacobi) on 16, 64, 256 and 1024 independent
       2D convection-diffusion systems (1k-50k rows each, Peclet 1-100): solves
       per second of the batched solve on the per-CTA solver and on the phase
@@ -454,6 +455,26 @@ def run_suite(args):
         b = t(bt.b)
         x = torch.empty_like(b)
         rows = {}
+        # the batched FP64 solve on each engine: per-CTA, phase kernels, and
+        # the size split with the k largest systems on the phase kernels
+        order = np.sort(bt.nrows)[::-1]
+        engines = {}
+        for name, solver, k in (("cta", B.SOLVER_CTA, 0), ("phases", B.SOLVER_PHASES, 0),
+                                ("split_8", B.SOLVER_SPLIT, 8), ("split_32", B.SOLVER_SPLIT, 32),
+                                ("split_128", B.SOLVER_SPLIT, 128),
+                                ("split_256", B.SOLVER_SPLIT, 256)):
+            A.set_solver(solver, split_rows=int(order[k - 1]) if k else None)
+            te_, (_, rs_) = _ev_time(stream, lambda: A.solve_batched(b, x, rtol=1e-8), reps=reps)
+            engines[name] = {"s": te_, "ok": sum(q["status"] == B.OK for q in rs_),
+                             "iterations_max": max(q["iterations"] for q in rs_)}
+        # the autotuner's choice (30-iteration candidate runs), then the rows below
+        import tempfile
+        tune_path = os.path.join(tempfile.mkdtemp(prefix="gbs_bench_c5_"), "tuning.txt")
+        A.autotune(tune_path)
+        tuned = A.tuning()
+        rows["engines"] = engines
+        rows["autotuned"] = {"solver": tuned["solver"], "split_rows": tuned["split_rows"],
+                             "plan": A.plan()}
         for prec, name in ((B.FP64, "batched_fp64"), (B.FP32_REFINED, "batched_fp32_refined")):
             ts, (_, rs) = _ev_time(stream, lambda: A.solve_batched(b, x, rtol=1e-8,
                                                                    precision=prec), reps=reps)
@@ -464,6 +485,29 @@ def run_suite(args):
         te, (_, re) = _ev_time(stream, lambda: A.solve(b, x, rtol=1e-8), reps=reps)
         rows["ensemble_fp64"] = {"s": te, "iterations": re["iterations"], "status": re["status"],
                                  "what": "the stacked block-diagonal system, one global norm"}
+        # roofline of the batched FP64 solve: per system its iterations times
+        # the PCG floor bytes and FP64 operations, summed, over the solve time
+        _, rs64 = A.solve_batched(b, x, rtol=1e-8)
+        rp = A.csr()[0].cpu().numpy().astype(np.int64)
+        ro_ = bt.row_off
+        alg = ops = 0.0
+        for q in range(bt.nsys):
+            n_q = int(ro_[q + 1] - ro_[q])
+            nz_q = int(rp[ro_[q + 1]] - rp[ro_[q]])
+            alg += pcg_alg_bytes(n_q, nz_q, rs64[q]["iterations"])
+            ops += pcg_fp64_ops(n_q, nz_q, rs64[q]["iterations"])
+        hbm_, _ = peaks()
+        t64 = rows["batched_fp64"]["s"]
+        clk_ = {"sm_mhz": None}
+        rows["roofline"] = {"bound": "hbm", "achieved": alg / t64 / 1e9, "peak": hbm_,
+                            "unit": "GB/s", "frac": alg / t64 / 1e9 / hbm_, "alg_bytes": alg,
+                            "fp64": {"achieved": ops / t64 / 1e9, "peak": fp64_peak_gops(clk_),
+                                     "unit": "G FP64 op/s",
+                                     "frac": ops / t64 / 1e9 / fp64_peak_gops(clk_)},
+                            "what": "sum over systems of iterations x (12 nnz + 4 (n + 1) + 72 n) "
+                                    "plus setup and closing residual (bench.pcg_alg_bytes), and "
+                                    "of the FP64 operations (bench.pcg_fp64_ops), over the "
+                                    "autotuned batched FP64 solve's time"}
         xb, _ = A.solve_batched(b, rtol=1e-8)
         g = (xb - t(bt.extra["x_target"])).contiguous()
         tadj, (_, _, _, ra) = _ev_time(
@@ -524,14 +568,16 @@ def run_suite(args):
             b = t(p.b)
             x = torch.empty_like(b)
             row = {"problem": f"{kind}_{m}", "n": p.nrows, "nnz": A.nnz}
-            runs = [("cg", B.KSP_CG, B.SOLVER_PHASES), ("cgsr", B.KSP_CGSR, B.SOLVER_PHASES),
-                    ("pipecg", B.KSP_PIPECG, B.SOLVER_PHASES),
-                    ("tfqmr", B.KSP_TFQMR, B.SOLVER_PHASES)]
+            TB, SR2, SR1 = B.CG_TEXTBOOK, B.CG_SINGLE_REDUCTION, B.CG_SINGLE_KERNEL
+            runs = [("cg", B.KSP_CG, B.SOLVER_PHASES, TB), ("cgsr", B.KSP_CGSR, B.SOLVER_PHASES, SR2),
+                    ("cgsr1", B.KSP_CGSR, B.SOLVER_PHASES, SR1),
+                    ("pipecg", B.KSP_PIPECG, B.SOLVER_PHASES, TB),
+                    ("tfqmr", B.KSP_TFQMR, B.SOLVER_PHASES, TB)]
             if A.nnz <= 2_000_000:
-                runs.append(("cg_cta", B.KSP_CG, B.SOLVER_CTA))
-                runs.append(("cg_cluster", B.KSP_CG, B.SOLVER_CLUSTER))
-            for name, method, solver in runs:
+                runs.append(("cg_cta", B.KSP_CG, B.SOLVER_CTA, TB))
+            for name, method, solver, form in runs:
                 A.set_solver(solver)
+                A.set_cg_form(form)
                 ts, (_, r) = _ev_time(stream, lambda: A.solve(b, x, rtol=1e-8, method=method,
                                                               host_loop=args.host_loop),
                                       reps=max(1, min(reps, 3)), warm=1)
@@ -545,6 +591,7 @@ def run_suite(args):
                         if k in ("spmv", "update_xr", "update_p")}
             row["pipecg_vs_cg"] = row["cg"]["s"] / row["pipecg"]["s"]
             row["cgsr_vs_cg"] = row["cg"]["s"] / row["cgsr"]["s"]
+            row["cgsr1_vs_cg"] = row["cg"]["s"] / row["cgsr1"]["s"]
             rows.append(row)
             A.close()
         big = rows[-1]

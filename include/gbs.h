@@ -70,7 +70,7 @@ enum { GBS_FP64 = 0, GBS_FP32_REFINED = 1 };
  * {1, 2, 4, 8, 32} selects the CSR-vector kernel with n lanes per row. */
 enum { GBS_SPMV_AUTO = -1, GBS_SPMV_SELL = 0 };
 /* Solvers (mat_set_solver). */
-enum { GBS_SOLVER_AUTO = 0, GBS_SOLVER_PHASES = 1, GBS_SOLVER_CTA = 2, GBS_SOLVER_CLUSTER = 3 };
+enum { GBS_SOLVER_AUTO = 0, GBS_SOLVER_PHASES = 1, GBS_SOLVER_CTA = 2, GBS_SOLVER_SPLIT = 3 };
 /* Forms of CG on the phase kernels (mat_set_cg_form, chosen by the autotuner). */
 enum { GBS_CG_TEXTBOOK = 0, GBS_CG_SINGLE_REDUCTION = 1, GBS_CG_SINGLE_KERNEL = 2 };
 /* Krylov methods (ksp_opts.method; Sec. 7 batched solvers, Sec. 6.2). */
@@ -382,13 +382,13 @@ int mat_get_plan(gbs_mat A, int32_t *spmv_rows, int32_t *update_rows, int32_t *k
  *     and for batches of many systems, which then run as concurrent CTAs,
  *     largest first.  Needs the sliced-ELL plan kernel (GBS_ERR_ARG from the
  *     solve otherwise); ignores host_loop; ksp_get_phase_ns reports zeros;
- *   GBS_SOLVER_CLUSTER: FP64 CG only (other methods and the refined solve
- *     take the phase kernels): one thread-block cluster of up to 16 CTAs per
- *     system, its slices split over the cluster's SMs, every iteration in
- *     one kernel, reductions through distributed shared memory and cluster
- *     barriers -- between the per-CTA solver (one SM) and the phase kernels
- *     (the whole GPU, a fixed cost per iteration).  Needs the sliced-ELL
- *     plan kernel; ignores host_loop; ksp_get_phase_ns reports zeros;
+ *   GBS_SOLVER_SPLIT: CG (FP64 or refined) of a batched solve
+ *     (ksp_solve_cg_batched, ksp_adjoint_batched) by size: the systems with
+ *     at least mat_set_split_rows' row count run on the phase kernels (the
+ *     whole GPU per iteration, one graph launch for all of them), then the
+ *     others on the per-CTA solver, so that no large system ends the batch
+ *     alone on one SM.  Needs the sliced-ELL plan kernel; a solve that is not
+ *     batched, or another method, takes GBS_SOLVER_AUTO's choice;
  *   GBS_SOLVER_AUTO (default): CTA when the largest system solved has at
  *     most 40000 nonzeros plus eight per row (the FP64 work of one iteration
  *     that one SM does faster than the phase kernels' fixed cost per
@@ -396,6 +396,10 @@ int mat_get_plan(gbs_mat A, int32_t *spmv_rows, int32_t *update_rows, int32_t *k
  * ksp_result.solver tells which one ran.  No synchronisation.
  */
 int mat_set_solver(gbs_mat A, int32_t solver);
+/* The row count from which a system of a batched solve runs on the phase
+ * kernels under GBS_SOLVER_SPLIT (>= 1; the autotuner sets it).  Cached
+ * graphs are dropped.  No synchronisation. */
+int mat_set_split_rows(gbs_mat A, int64_t min_rows);
 
 /*
  * The form of FP64 CG (ksp_solve_cg*, ksp_adjoint*, method GBS_KSP_CG) on the
@@ -414,10 +418,11 @@ int mat_set_solver(gbs_mat A, int32_t solver);
  * handle's form too: the single-kernel form where it applies, else two
  * kernels.  The per-CTA and cluster engines and the refined solve always use
  * the textbook form.  No synchronisation.  mat_get_tuning returns the solver
- * setting (mat_set_solver) and the CG form (host outputs, may be NULL).
+ * setting (mat_set_solver), the CG form and the split row count
+ * (mat_set_split_rows) (host outputs, each may be NULL).
  */
 int mat_set_cg_form(gbs_mat A, int32_t form);
-int mat_get_tuning(gbs_mat A, int32_t *solver, int32_t *cg_form);
+int mat_get_tuning(gbs_mat A, int32_t *solver, int32_t *cg_form, int64_t *split_rows);
 
 /*
  * Autotuner of the FP64 CG solve ("rows-per-warp and block shapes picked by a
@@ -425,15 +430,20 @@ int mat_get_tuning(gbs_mat A, int32_t *solver, int32_t *cg_form);
  * block rows, row-product kernel, CTAs per SM), then, for the fastest plan,
  * the single-reduction CG forms (two kernels; one kernel, for a handle of
  * one system) and (sliced ELL; batches, or systems within
- * 16 times the per-CTA size rule) the per-CTA engine.  Each candidate runs a
- * fixed 30-iteration FP64 CG (rtol 0, every candidate the same work; a
- * batched handle solves its systems each on its own) once untimed and three
- * times under CUDA events on `stream`; the fastest becomes the handle's plan,
- * solver (mat_set_solver) and CG form (mat_set_cg_form).  Synchronises.
+ * 16 times the per-CTA size rule) the per-CTA engine, and for batches the
+ * size split (GBS_SOLVER_SPLIT) at the row counts of the 1st, 4th, 16th
+ * and 64th largest systems.  Each candidate runs a fixed 30-iteration FP64
+ * CG (rtol 0, every candidate the same work; a batched handle solves its
+ * systems each on its own) once untimed and three times under CUDA events
+ * on `stream`; the fastest becomes the handle's plan, solver
+ * (mat_set_solver), CG form (mat_set_cg_form) and split row count
+ * (mat_set_split_rows); on a batched handle the engine chosen for its
+ * batched solves leaves its ensemble solves (ksp_solve on the stacked
+ * system) to GBS_SOLVER_AUTO's choice.  Synchronises.
  *
  * mat_autotune_file: the same, persisted.  path names a text file (created if
  * missing) of one line per tuned key: "<key> | Ra Re kernel ctas_per_sm
- * solver cg_form | <time>".  The key holds the handle's sizes, a hash of its
+ * solver cg_form split_rows | <time>".  The key holds the handle's sizes, a hash of its
  * systems' sizes and of 257 sampled entries each of row_ptr and col, the
  * device name and SM count, and "fp64".  A matching line is applied without
  * timing (*from_cache = 1); otherwise the handle is tuned and the line

@@ -25,7 +25,7 @@ ERR_STAGNATION, ERR_TIMEOUT, ERR_LAUNCH = 9, 10, 11
 INSERT, ADD = 0, 1
 FP64, FP32_REFINED = 0, 1
 SPMV_AUTO, SPMV_SELL = -1, 0  # plan kernels; 1, 2, 4, 8, 32 = CSR-vector lanes per row
-SOLVER_AUTO, SOLVER_PHASES, SOLVER_CTA, SOLVER_CLUSTER = 0, 1, 2, 3
+SOLVER_AUTO, SOLVER_PHASES, SOLVER_CTA, SOLVER_SPLIT = 0, 1, 2, 3
 KSP_CG, KSP_BICG, KSP_TFQMR, KSP_PIPECG, KSP_CGSR = 0, 1, 2, 3, 4
 CG_TEXTBOOK, CG_SINGLE_REDUCTION, CG_SINGLE_KERNEL = 0, 1, 2
 
@@ -37,7 +37,8 @@ EXPORTED = ["ksp_opts_default", "mat_create_coo", "mat_create_coo_batched",
             "ksp_solve_cg_noalloc", "ksp_get_phase_ns", "mat_set_solver",
             "vec_create_coo", "vec_set_values_coo", "vec_get_info", "vec_destroy",
             "ksp_solve", "ksp_solve_batched", "q1_hex_element_coo", "q1_hex_element_values",
-            "edge_coo_values", "mat_autotune_file", "mat_set_cg_form", "mat_get_tuning"]
+            "edge_coo_values", "mat_autotune_file", "mat_set_cg_form", "mat_get_tuning",
+            "mat_set_split_rows"]
 
 
 class KspOpts(ctypes.Structure):
@@ -112,7 +113,8 @@ def lib() -> ctypes.CDLL:
         "edge_coo_values": (ctypes.c_int, [I64, P, P, P]),
         "mat_autotune_file": (ctypes.c_int, [P, ctypes.c_char_p, P, P]),
         "mat_set_cg_form": (ctypes.c_int, [P, I32]),
-        "mat_get_tuning": (ctypes.c_int, [P, P, P]),
+        "mat_get_tuning": (ctypes.c_int, [P, P, P, P]),
+        "mat_set_split_rows": (ctypes.c_int, [P, I64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -355,9 +357,13 @@ def mat_set_cg_form(A, form: int):
 
 
 def mat_get_tuning(A) -> dict:
-    sv, cf = ctypes.c_int32(0), ctypes.c_int32(0)
-    _check(lib().mat_get_tuning(A, ctypes.byref(sv), ctypes.byref(cf)))
-    return {"solver": sv.value, "cg_form": cf.value}
+    sv, cf, sr = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int64(0)
+    _check(lib().mat_get_tuning(A, ctypes.byref(sv), ctypes.byref(cf), ctypes.byref(sr)))
+    return {"solver": sv.value, "cg_form": cf.value, "split_rows": sr.value}
+
+
+def mat_set_split_rows(A, min_rows: int):
+    _check(lib().mat_set_split_rows(A, int(min_rows)))
 
 
 def mat_autotune(A, stream=None):
@@ -506,7 +512,11 @@ class Mat:
     def plan(self) -> dict:
         return mat_get_plan(self.h)
 
-    def set_solver(self, solver: int):
+    def set_solver(self, solver: int, split_rows=None):
+        """The engine (SOLVER_*); with SOLVER_SPLIT, split_rows is the row
+        count from which a batch's systems run on the phase kernels."""
+        if split_rows is not None:
+            mat_set_split_rows(self.h, split_rows)
         mat_set_solver(self.h, solver)
 
     def phase_ns(self) -> dict:

@@ -7,14 +7,17 @@
 #include <sys/file.h>
 #include <unistd.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -94,6 +97,8 @@ void free_handle(gbs_mat A) {
                  A->kv, A->sys_row0, A->halo_flags};  // sys_slice0 lies inside sys_row0's
   for (void *p : dev) dev_free(p, nullptr);
   free_table(A->ta);
+  free_table(A->sa);
+  free_table(A->se);
   free_table(A->te);
   free_sell(A);
   if (A->st_host) cudaFreeHost(A->st_host);
@@ -442,11 +447,24 @@ int mat_set_plan(gbs_mat A, int32_t spmv_rows, int32_t update_rows, int32_t kern
 
 int mat_set_solver(gbs_mat A, int32_t solver) {
   GBS_TRY(check_mat(A, "mat_set_solver"));
-  if (solver < GBS_SOLVER_AUTO || solver > GBS_SOLVER_CLUSTER) {
-    set_error("mat_set_solver: solver must be GBS_SOLVER_AUTO, _PHASES, _CTA or _CLUSTER");
+  if (solver < GBS_SOLVER_AUTO || solver > GBS_SOLVER_SPLIT) {
+    set_error("mat_set_solver: solver must be GBS_SOLVER_AUTO, _PHASES, _CTA or _SPLIT");
     return GBS_ERR_ARG;
   }
+  if (solver != A->solver) drop_graphs(A);  // a split loop's graph skips the small systems
   A->solver = solver;
+  A->solver_batched_only = false;
+  return GBS_OK;
+}
+
+int mat_set_split_rows(gbs_mat A, int64_t min_rows) {
+  GBS_TRY(check_mat(A, "mat_set_split_rows"));
+  if (min_rows < 1) {
+    set_error("mat_set_split_rows: min_rows = %lld must be at least 1", (long long)min_rows);
+    return GBS_ERR_ARG;
+  }
+  if (min_rows != A->split_rows) drop_graphs(A);
+  A->split_rows = min_rows;
   return GBS_OK;
 }
 
@@ -475,6 +493,7 @@ int mat_get_plan(gbs_mat A, int32_t *spmv_rows, int32_t *update_rows, int32_t *k
 namespace {
 struct Tuning {
   int32_t Ra, Re, kernel, cpsm, solver, cg_form;
+  int64_t split_rows;
 };
 
 // Makes t the handle's plan (rebuilt only when it differs from the current
@@ -482,14 +501,17 @@ struct Tuning {
 int apply_tuning(gbs_mat A, const Tuning &t, cudaStream_t s) {
   if (!(t.Ra == A->Ra && t.Re == A->Re && t.kernel == A->lanes && t.cpsm == A->ctas_per_sm))
     GBS_TRY(build_plan(A, t.Ra, t.Re, t.kernel, t.cpsm, s));
+  if (t.solver != A->solver || t.split_rows != A->split_rows) drop_graphs(A);
   A->solver = t.solver;
+  A->solver_batched_only = A->nsys > 1;  // tuned on the batched solve
   A->cg_form = t.cg_form;
+  A->split_rows = t.split_rows;
   return GBS_OK;
 }
 
 // The resolved plan of the handle with its solver and form.
 Tuning current_tuning(gbs_mat A) {
-  return Tuning{A->Ra, A->Re, A->lanes, A->ctas_per_sm, A->solver, A->cg_form};
+  return Tuning{A->Ra, A->Re, A->lanes, A->ctas_per_sm, A->solver, A->cg_form, A->split_rows};
 }
 
 // 257 evenly spaced entries each of row_ptr and col (the cache key's sample).
@@ -523,7 +545,8 @@ static int autotune(gbs_mat A, cudaStream_t s, Tuning *out, float *out_ms) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  Tuning best{A->Ra, A->Re, A->lanes, A->ctas_per_sm, GBS_SOLVER_PHASES, GBS_CG_TEXTBOOK};
+  Tuning best{A->Ra, A->Re, A->lanes, A->ctas_per_sm, GBS_SOLVER_PHASES, GBS_CG_TEXTBOOK,
+              A->split_rows};
   float best_ms = 1e30f;
   int st = GBS_OK;
   auto timed = [&](const Tuning &t) -> bool {
@@ -546,7 +569,7 @@ static int autotune(gbs_mat A, cudaStream_t s, Tuning *out, float *out_ms) {
     return true;
   };
   for (const auto &c : plans) {
-    timed(Tuning{c[0], c[1], c[2], c[3], GBS_SOLVER_PHASES, GBS_CG_TEXTBOOK});
+    timed(Tuning{c[0], c[1], c[2], c[3], GBS_SOLVER_PHASES, GBS_CG_TEXTBOOK, A->split_rows});
     if (st != GBS_OK) break;
   }
   if (st == GBS_OK && best.kernel == GBS_SPMV_SELL) {
@@ -564,6 +587,20 @@ static int autotune(gbs_mat A, cudaStream_t s, Tuning *out, float *out_ms) {
       t = base;
       t.solver = GBS_SOLVER_CTA;
       timed(t);
+    }
+    // batches: the largest 1, 4, 16, 64 systems on the phase kernels, the
+    // rest on the per-CTA solver
+    if (per_system) {
+      std::vector<int64_t> r(A->nsys);
+      for (int32_t q = 0; q < A->nsys; ++q) r[q] = A->row_off_h[q + 1] - A->row_off_h[q];
+      std::sort(r.begin(), r.end(), std::greater<int64_t>());
+      for (int kth : {1, 4, 16, 64}) {
+        if (st != GBS_OK || kth >= A->nsys) break;
+        t = base;
+        t.solver = GBS_SOLVER_SPLIT;
+        t.split_rows = std::max<int64_t>(1, r[kth - 1]);
+        timed(t);
+      }
     }
   }
   A->trips_counted = true;  // the timed solves' results are never read
@@ -672,9 +709,13 @@ int mat_autotune_file(gbs_mat A, const char *path, int32_t *from_cache, void *st
       const char *bar = strchr(line, '|');
       if (!bar || (size_t)(bar - line) != key.size() + 1 || strncmp(line, key.c_str(), key.size()))
         continue;
-      if (sscanf(bar + 1, " %d %d %d %d %d %d", &t.Ra, &t.Re, &t.kernel, &t.cpsm, &t.solver,
-                 &t.cg_form) == 6)
-        hit = true;  // the last matching line wins
+      long long sr = 1;
+      const int nf = sscanf(bar + 1, " %d %d %d %d %d %d %lld", &t.Ra, &t.Re, &t.kernel, &t.cpsm,
+                            &t.solver, &t.cg_form, &sr);
+      if (nf >= 6) {  // the last matching line wins
+        t.split_rows = nf == 7 && sr >= 1 ? (int64_t)sr : 1;
+        hit = true;
+      }
     }
     if (hit) {
       st = apply_tuning(A, t, s);
@@ -685,8 +726,8 @@ int mat_autotune_file(gbs_mat A, const char *path, int32_t *from_cache, void *st
       st = autotune(A, s, &t, &ms);
       if (st == GBS_OK) {
         fseek(f, 0, SEEK_END);
-        fprintf(f, "%s | %d %d %d %d %d %d | %.4f ms per 30 iterations\n", key.c_str(), t.Ra, t.Re,
-                t.kernel, t.cpsm, t.solver, t.cg_form, ms);
+        fprintf(f, "%s | %d %d %d %d %d %d %lld | %.4f ms per 30 iterations\n", key.c_str(), t.Ra,
+                t.Re, t.kernel, t.cpsm, t.solver, t.cg_form, (long long)t.split_rows, ms);
         fflush(f);
       }
     }
@@ -708,10 +749,11 @@ int mat_set_cg_form(gbs_mat A, int32_t form) {
   return GBS_OK;
 }
 
-int mat_get_tuning(gbs_mat A, int32_t *solver, int32_t *cg_form) {
+int mat_get_tuning(gbs_mat A, int32_t *solver, int32_t *cg_form, int64_t *split_rows) {
   GBS_TRY(check_mat(A, "mat_get_tuning"));
   if (solver) *solver = A->solver;
   if (cg_form) *cg_form = A->cg_form;
+  if (split_rows) *split_rows = A->split_rows;
   return GBS_OK;
 }
 

@@ -134,6 +134,7 @@ struct TableDev {
   int32_t *sys_blk0 = nullptr;   // nsys + 1
   int32_t *sys_slot0 = nullptr;  // nsys + 1 (for the table's grid)
   int32_t *slice0 = nullptr;     // nblocks + 1: first 32-row slice of each block
+  int32_t *row1 = nullptr, *slice1 = nullptr;  // block ends (tables with gaps only)
   std::vector<int32_t> sys_blk0_h;
   int32_t grid = 0;              // CTAs of the kernels that walk this table
   int64_t nslots = 0;            // reduction slots: sum over systems of min(blocks, grid)
@@ -183,7 +184,12 @@ struct gbs_mat_s {
   int32_t Ra = 256, Re = 512;   // rows per SpMV block / per update block
   int32_t lanes = 0;
   int32_t ctas_per_sm = 0;      // grid cap per SM, 0 = as many as fit (one wave)
-  int32_t solver = 0;           // GBS_SOLVER_AUTO / PHASES / CTA
+  int32_t solver = 0;           // GBS_SOLVER_AUTO / PHASES / CTA / SPLIT
+  int64_t split_rows = 1;       // GBS_SOLVER_SPLIT: systems of at least this many rows on
+                                // the phase kernels, the rest on the per-CTA solver
+  bool solver_batched_only = false;  // the autotuner chose `solver` for batched solves
+  gbs::TableDev sa, se;         // the size split's block tables (its large systems only)
+  int64_t split_built = 0;      // split_rows the tables were built for (0: none)
   int32_t cg_form = 0;          // GBS_CG_TEXTBOOK / _SINGLE_REDUCTION / _SINGLE_KERNEL
   // one-kernel single-reduction CG: table A's CTA c waits, before its row
   // products, for CTAs c - halo_lo .. c - halo_lo + halo_n - 1 (mod grid) to
@@ -226,8 +232,15 @@ struct gbs_mat_s {
 namespace gbs {
 
 int ensure_solver_workspace(gbs_mat A, bool refined, cudaStream_t s);
+// The solver setting that applies to a solve: the handle's, except that a
+// choice the autotuner made for a batched handle's batched solves leaves its
+// ensemble solves (the stacked system) to the automatic choice.
+inline int32_t solver_for(gbs_mat A, bool per_system) {
+  return (A->solver_batched_only && !per_system) ? GBS_SOLVER_AUTO : A->solver;
+}
 int build_plan(gbs_mat A, int32_t spmv_rows, int32_t update_rows, int32_t lanes,
                int32_t ctas_per_sm, cudaStream_t s);
+int build_split_tables(gbs_mat A, cudaStream_t s);
 void free_table(TableDev &t);
 void drop_graphs(gbs_mat A);
 int launch_spmv(gbs_mat A, const double *x, double *y, cudaStream_t s);

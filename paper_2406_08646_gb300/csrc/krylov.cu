@@ -471,7 +471,7 @@ __device__ __forceinline__ NsView ns_view(const PcgArgs &a, int s) {
 // Row products of block b with A^T's sliced copy.
 template <class F>
 __device__ __forceinline__ void rows_t(const PcgArgs &a, int b, const double *x, F &f) {
-  const int s0 = __ldg(a.ta.slice0 + b), s1 = __ldg(a.ta.slice0 + b + 1);
+  const int s0 = __ldg(a.ta.slice0 + b), s1 = blk_slice_end(a.ta, b);
   if (a.stream_matrix)
     sell_rows<double, true, GATHER_NC>(a.tptr, a.srow0, a.tcol, a.toff, a.tval, x, s0, s1, f);
   else sell_rows<double, false, GATHER_NC>(a.tptr, a.srow0, a.tcol, a.toff, a.tval, x, s0, s1, f);
@@ -1583,7 +1583,7 @@ __global__ void NS_ROWS k_sr_fused(PcgArgs a) {
   double acc[2] = {0.0, 0.0};  // r.u, r.r
   // 1. the update of the CTA's rows
   for (int b = blockIdx.x; b < nb; b += G) {
-    const int r0 = __ldg(a.ta.row0 + b), r1 = __ldg(a.ta.row0 + b + 1);
+    const int r0 = __ldg(a.ta.row0 + b), r1 = blk_row_end(a.ta, b);
     for (int i = r0 + (int)threadIdx.x; i < r1; i += (int)blockDim.x) {
       const double ui = __ldcg(u + i), wi = w[i], pv = p[i], sw = sv[i], xi = x[i], ri = r[i];
       const double di = a.dinv[i];
@@ -1621,7 +1621,7 @@ __global__ void NS_ROWS k_sr_fused(PcgArgs a) {
   int last = blockIdx.x;
   double acc2 = 0.0;
   for (int b = blockIdx.x; b < nb; b += G) {
-    const int s0 = __ldg(a.ta.slice0 + b), s1 = __ldg(a.ta.slice0 + b + 1);
+    const int s0 = __ldg(a.ta.slice0 + b), s1 = blk_slice_end(a.ta, b);
     double dl = acc2;
     auto f = [&](int i, double y) {
       w[i] = y;
@@ -1832,8 +1832,10 @@ int solve_krylov(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool 
   A->trips_counted = true;
   // automatic: one 1024-thread CTA per SM already beats the phase kernels;
   // pipelined and single-reduction CG exist for the phase kernels only
-  const bool on_ctas = !pipe && !sr && (A->solver == GBS_SOLVER_CTA ||
-                                 (A->solver == GBS_SOLVER_AUTO && cta_size_rule(A, per_system, 1)));
+  const int32_t sv = solver_for(A, per_system);
+  const bool on_ctas = !pipe && !sr && (sv == GBS_SOLVER_CTA ||
+                                        ((sv == GBS_SOLVER_AUTO || sv == GBS_SOLVER_SPLIT) &&
+                                         cta_size_rule(A, per_system, 1)));
   if (!on_ctas) {
     A->last_solver = GBS_SOLVER_PHASES;
     if (A->ta.nblocks == 0) {  // empty matrix: nothing to iterate

@@ -30,7 +30,6 @@
 
 #include "device_util.cuh"
 #include "internal.cuh"
-#include "cluster.cuh"
 #include "cta.cuh"
 #include "phases.cuh"
 
@@ -149,7 +148,7 @@ int phase_occupancy(int lanes, int *rows, int *upd) {
 }
 
 static BlockTable view(const TableDev &t) {
-  return BlockTable{t.nblocks, t.row0, t.sys, t.sys_blk0, t.sys_slot0, t.slice0};
+  return BlockTable{t.nblocks, t.row0, t.sys, t.sys_blk0, t.sys_slot0, t.slice0, t.row1, t.slice1};
 }
 
 void drop_graphs(gbs_mat A) {
@@ -190,7 +189,7 @@ int ensure_solver_workspace(gbs_mat A, bool refined, cudaStream_t s) {
   }
   // reduction slots: table A's, table E's, and a third region the size of
   // table E's for partial sums of E's slots
-  const int64_t need = A->ta.nslots + 2 * A->te.nslots + 1;
+  const int64_t need = std::max(A->ta.nslots + 2 * A->te.nslots, A->sa.nslots + 2 * A->se.nslots) + 1;
   if (A->part_cap < need) {
     if (A->part) {
       GBS_TRY_CUDA(cudaStreamSynchronize(s));
@@ -259,6 +258,7 @@ PcgArgs make_args(gbs_mat A, bool per_system, bool refined) {
   a.ta = view(A->ta);
   a.te = view(A->te);
   a.part_e = A->ta.nslots;
+  a.grid_a = A->ta.grid;
   a.grid_e = A->te.grid;
   a.row_ptr = A->row_ptr;
   a.col = A->col;
@@ -358,7 +358,7 @@ int build_loop_graph(gbs_mat A, const LoopPlan &P, PcgArgs a, cudaGraphExec_t *o
   a.stepped = 0;
   a.trip = 0;
   void *args[] = {&a};
-  auto grid = [&](bool e_table) { return e_table ? A->te.grid : A->ta.grid; };
+  auto grid = [&](bool e_table) { return e_table ? a.grid_e : a.grid_a; };
 
   cudaGraphNode_t n_ctl, n_cnt, n_loop;
   cudaMemsetParams ms;
@@ -508,64 +508,11 @@ int sm_count(gbs_mat A) {
 }
 
 bool use_cta_solver(gbs_mat A, bool per_system) {
-  if (A->solver == GBS_SOLVER_CTA) return true;
-  if (A->solver == GBS_SOLVER_PHASES || A->solver == GBS_SOLVER_CLUSTER ||
-      A->lanes != GBS_SPMV_SELL)
-    return false;  // (a refined solve asked for the cluster solver takes the phase kernels)
+  const int32_t sv = solver_for(A, per_system);
+  if (sv == GBS_SOLVER_CTA) return true;
+  if (sv == GBS_SOLVER_PHASES || A->lanes != GBS_SPMV_SELL) return false;
+  if (sv == GBS_SOLVER_SPLIT && per_system) return false;  // solve() splits the batch
   return cta_size_rule(A, per_system, 2);  // two 1024-thread PCG CTAs fit an SM
-}
-
-// Cluster size for the cluster solver: about one SM per 40,000 FP64
-// operations of an iteration of the largest system (the per-CTA solver's
-// break-even), at least 2, at most CLUSTER_MAX, and no more than the device
-// can hold as one cluster.
-static int cluster_size(gbs_mat A, bool per_system) {
-  const int64_t nz = per_system ? A->max_sys_nnz : A->nnz;
-  const int64_t rows = per_system ? A->max_sys_rows : A->nrows;
-  const int64_t units = (nz + 8 * rows + CTA_AUTO_WORK - 1) / CTA_AUTO_WORK;
-  int want = (int)std::min<int64_t>(CLUSTER_MAX, std::max<int64_t>(2, units));
-  static bool opted_in = false;
-  if (!opted_in) {
-    cudaFuncSetAttribute(k_cluster_pcg, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    opted_in = true;
-  }
-  for (; want > 1; --want) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)want);
-    cfg.blockDim = dim3(CTA_TPB);
-    cudaLaunchAttribute at;
-    at.id = cudaLaunchAttributeClusterDimension;
-    at.val.clusterDim.x = (unsigned)want;
-    at.val.clusterDim.y = 1;
-    at.val.clusterDim.z = 1;
-    cfg.attrs = &at;
-    cfg.numAttrs = 1;
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k_cluster_pcg, &cfg) == cudaSuccess && n > 0) break;
-    cudaGetLastError();  // clear a refused size
-  }
-  return want;
-}
-
-// nclusters systems (a.order, or the whole matrix when a.ensemble), one
-// cluster each.
-static int launch_cluster(gbs_mat A, const PcgArgs &a, int32_t nclusters, cudaStream_t s) {
-  const int cs = cluster_size(A, !a.ensemble);
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(nclusters * cs));
-  cfg.blockDim = dim3(CTA_TPB);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = s;
-  cudaLaunchAttribute at;
-  at.id = cudaLaunchAttributeClusterDimension;
-  at.val.clusterDim.x = (unsigned)cs;
-  at.val.clusterDim.y = 1;
-  at.val.clusterDim.z = 1;
-  cfg.attrs = &at;
-  cfg.numAttrs = 1;
-  GBS_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_cluster_pcg, a));
-  GBS_LAUNCHED(1);
-  return GBS_OK;
 }
 
 int solve(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool per_system,
@@ -574,8 +521,10 @@ int solve(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool per_sys
   // the handle's CG form: FP64 CG on the phase kernels may run as the
   // single-reduction loop (same iterates in exact arithmetic, two kernels per
   // iteration instead of three, or one)
-  if (!refined && A->cg_form != GBS_CG_TEXTBOOK && A->lanes == GBS_SPMV_SELL &&
-      A->solver != GBS_SOLVER_CLUSTER && !use_cta_solver(A, per_system)) {
+  const bool split =
+      per_system && solver_for(A, per_system) == GBS_SOLVER_SPLIT && A->lanes == GBS_SPMV_SELL;
+  if (!refined && A->cg_form != GBS_CG_TEXTBOOK && A->lanes == GBS_SPMV_SELL && !split &&
+      !use_cta_solver(A, per_system)) {
     ksp_opts sr = o;
     sr.method = GBS_KSP_CGSR;
     return solve_krylov(A, b, x, sr, per_system, s);
@@ -590,18 +539,6 @@ int solve(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool per_sys
     GBS_TRY_CUDA(cudaMemsetAsync(A->st, 0, sizeof(SysState) * A->nsys, s));
     GBS_TRY_CUDA(cudaMemsetAsync(A->ctl, 0, sizeof(DevCtl), s));
     return GBS_OK;
-  }
-  if (!refined && A->solver == GBS_SOLVER_CLUSTER) {
-    if (A->lanes != GBS_SPMV_SELL) {
-      set_error("the cluster solver needs the sliced-ELL row products (plan kernel)");
-      return GBS_ERR_ARG;
-    }
-    A->last_solver = GBS_SOLVER_CLUSTER;
-    GBS_TRY_CUDA(cudaMemsetAsync(A->ctl, 0, sizeof(DevCtl), s));
-    GBS_TRY(put_call(A->call, call_args(b, x, o), s, A->ctl));
-    PcgArgs a = make_args(A, per_system, refined);
-    a.order = per_system ? A->cta_order : nullptr;
-    return launch_cluster(A, a, per_system ? A->nsys : 1, s);
   }
   if (use_cta_solver(A, per_system)) {
     if (A->lanes != GBS_SPMV_SELL) {
@@ -619,8 +556,50 @@ int solve(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool per_sys
     GBS_LAUNCHED(1);
     return GBS_OK;
   }
+  if (split) {
+    // the systems of at least split_rows rows on the phase kernels (the
+    // others are skipped by every phase: walk), then the rest -- a suffix of
+    // cta_order, which lists the systems by decreasing rows -- on the
+    // per-CTA solver, after the loop (whose graph clears every system's state
+    // first) on the same stream
+    const int32_t nbig = split_count(A);
+    A->last_solver = GBS_SOLVER_SPLIT;
+    if (nbig > 0) {
+      GBS_TRY(build_split_tables(A, s));
+      GBS_TRY(ensure_solver_workspace(A, refined, s));  // the split tables' slots
+      PcgArgs a = make_args(A, per_system, refined);
+      a.ta = view(A->sa);
+      a.te = view(A->se);
+      a.part_e = A->sa.nslots;
+      a.grid_a = A->sa.grid;
+      a.grid_e = A->se.grid;
+      GBS_TRY(run_loop(A, cg_plan(refined, A->lanes), refined ? GBS_GRAPH_CG32 : GBS_GRAPH_CG,
+                       a, b, x, o, per_system, s));
+    } else {
+      GBS_TRY_CUDA(cudaMemsetAsync(A->st, 0, sizeof(SysState) * A->nsys, s));
+      GBS_TRY_CUDA(cudaMemsetAsync(A->ctl, 0, sizeof(DevCtl), s));
+      GBS_TRY(put_call(A->call, call_args(b, x, o), s, A->ctl));
+    }
+    if (nbig < A->nsys) {
+      PcgArgs a = make_args(A, per_system, refined);
+      a.order = A->cta_order + nbig;
+      const unsigned grid = (unsigned)(A->nsys - nbig);
+      if (refined) k_cta_pcg<true><<<grid, CTA_TPB, 0, s>>>(a);
+      else k_cta_pcg<false><<<grid, CTA_TPB, 0, s>>>(a);
+      GBS_LAUNCHED(1);
+    }
+    return GBS_OK;
+  }
   return run_loop(A, cg_plan(refined, A->lanes), refined ? GBS_GRAPH_CG32 : GBS_GRAPH_CG,
                   make_args(A, per_system, refined), b, x, o, per_system, s);
+}
+
+// Systems with at least split_rows rows (a prefix of cta_order).
+int32_t split_count(gbs_mat A) {
+  int32_t k = 0;
+  for (int32_t q = 0; q < A->nsys; ++q)
+    if (A->row_off_h[q + 1] - A->row_off_h[q] >= A->split_rows) ++k;
+  return k;
 }
 
 // Runs a loop plan on the phase kernels: host-stepped (o.host_loop) or as the
@@ -635,7 +614,7 @@ int run_loop(gbs_mat A, const LoopPlan &P, int kind, const PcgArgs &a, const dou
     if (P.body_coop)
       GBS_TRY_CUDA(cudaMemsetAsync(A->halo_flags, 0, sizeof(int32_t) * A->ta.grid, s));
     GBS_TRY(put_call(A->call, call_args(b, x, o), s));
-    return run_loop_stepped(P, a, A->ta.grid, A->te.grid, max_trips_for(o), A->ctl, s);
+    return run_loop_stepped(P, a, a.grid_a, a.grid_e, max_trips_for(o), A->ctl, s);
   }
   cudaGraphExec_t &G = A->graph[kind][per_system ? 1 : 0];
   if (!G) GBS_TRY(build_loop_graph(A, P, a, &G));
@@ -673,6 +652,9 @@ int read_results(gbs_mat A, ksp_result *res, int32_t count, cudaStream_t s) {
     R.iterations = S.iterations;
     R.outer_iterations = S.outer;
     R.solver = A->last_solver;
+    if (R.solver == GBS_SOLVER_SPLIT)  // the engine this system ran on
+      R.solver = A->row_off_h[q + 1] - A->row_off_h[q] >= A->split_rows ? GBS_SOLVER_PHASES
+                                                                         : GBS_SOLVER_CTA;
     R.rnorm0 = S.rnorm0;
     R.rnorm = S.rnorm;
     const double bn = sqrt(S.bb);
@@ -848,9 +830,10 @@ extern "C" int ksp_solve_cg_noalloc(int64_t n, const int32_t *row_ptr, const int
   memset(&a, 0, sizeof(a));
   a.nsys = 1;
   a.ensemble = 1;
-  a.ta = BlockTable{nba, S->row0_a, nullptr, nullptr, nullptr, nullptr};
-  a.te = BlockTable{nbe, S->row0_e, nullptr, nullptr, nullptr, nullptr};
+  a.ta = BlockTable{nba, S->row0_a, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  a.te = BlockTable{nbe, S->row0_e, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   a.part_e = nba;
+  a.grid_a = nba;
   a.grid_e = nbe;
   a.row_ptr = row_ptr;
   a.col = col;

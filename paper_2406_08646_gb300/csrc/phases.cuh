@@ -55,7 +55,17 @@ struct BlockTable {
   const int32_t *sys_blk0;   // nsys + 1
   const int32_t *sys_slot0;  // nsys + 1: reduction slot offsets for this table's grid
   const int32_t *slice0;     // nblocks + 1: first 32-row slice of each block
+  // block ends, where blocks do not tile the rows (the size split's tables,
+  // which skip the small systems); null: block b ends where b + 1 starts
+  const int32_t *row1, *slice1;
 };
+
+__device__ __forceinline__ int blk_row_end(const BlockTable &t, int b) {
+  return __ldg((t.row1 ? t.row1 : t.row0 + 1) + b);
+}
+__device__ __forceinline__ int blk_slice_end(const BlockTable &t, int b) {
+  return __ldg((t.slice1 ? t.slice1 : t.slice0 + 1) + b);
+}
 
 struct PcgArgs {
   int32_t nsys, ensemble;
@@ -90,6 +100,7 @@ struct PcgArgs {
   const double *tval;
   int32_t *halo_flags;              // one-kernel CG: iteration each CTA published
   int32_t halo_lo, halo_n;          //   and the window of CTAs it waits for
+  int32_t grid_a;                   // CTAs of the kernels that walk table ta
 };
 
 // A solve loop on the phase kernels: the start-up kernels, the WHILE body
@@ -113,6 +124,7 @@ int run_loop_stepped(const LoopPlan &P, PcgArgs a, int grid_a, int grid_e, int64
 int run_loop(gbs_mat A, const LoopPlan &P, int kind, const PcgArgs &a, const double *b,
              double *x, const ksp_opts &o, bool per_system, cudaStream_t s);
 bool use_cta_solver(gbs_mat A, bool per_system);
+int32_t split_count(gbs_mat A);
 // The per-CTA solver's automatic choice: the largest system solved has at
 // most CTA_AUTO_WORK nonzeros plus eight per row, or a batch gives every SM
 // systems_per_sm CTAs.
@@ -388,7 +400,7 @@ __device__ __forceinline__ void walk(const PcgArgs &a, const BlockTable &t, int6
   for (int k = 0; k < NA; ++k) acc[k] = 0.0;
   for (int b = blockIdx.x; b < t.nblocks; b += G) {
     const int s = sys_of(a, t, b);
-    const int r0 = __ldg(t.row0 + b), r1 = __ldg(t.row0 + b + 1);  // issued with want's loads
+    const int r0 = __ldg(t.row0 + b), r1 = blk_row_end(t, b);  // issued with want's loads
     if (s != cur_s) {
       if constexpr (NV > 0) {
         if (kind) flush<NV, ARRIVE, false, NE>(a, t, part_off, cur_s, cur_b, acc, red, kind == 2, fin);
@@ -644,7 +656,7 @@ __device__ __forceinline__ void row_products(const PcgArgs &a, int b, int r0, in
                                              const T *csr_val, const T *sell_val, const T *x,
                                              F &f) {
   if constexpr (L == 0) {
-    const int s0 = __ldg(a.ta.slice0 + b), s1 = __ldg(a.ta.slice0 + b + 1);
+    const int s0 = __ldg(a.ta.slice0 + b), s1 = blk_slice_end(a.ta, b);
     if (a.stream_matrix)
       sell_rows<T, true, GATHER_NC>(a.sptr, a.srow0, a.scol, a.soff, sell_val, x, s0, s1, f);
     else

@@ -91,7 +91,7 @@ int auto_lanes(int64_t nnz, int64_t nrows) {
 
 void free_table(TableDev &t) {
   dev_free(t.row0, nullptr);  // one buffer holds all five arrays (build_table)
-  t.row0 = t.sys = t.sys_blk0 = t.sys_slot0 = t.slice0 = nullptr;
+  t.row0 = t.sys = t.sys_blk0 = t.sys_slot0 = t.slice0 = t.row1 = t.slice1 = nullptr;
   t.nblocks = 0;
   t.grid = 0;
   t.nslots = 0;
@@ -103,15 +103,21 @@ void free_table(TableDev &t) {
 // is a whole number of the 32-row slices of the sliced-ELL layout (slice0).
 // The kernels walking the table run min(blocks, cap_per_sm x SMs) CTAs;
 // system s owns min(blocks_s, grid) reduction slots.
-static int build_table(gbs_mat A, int32_t R, int32_t cap_per_sm, TableDev &t, cudaStream_t st) {
-  std::vector<int32_t> row0, sys, sb0(A->nsys + 1, 0), sl0;
+// min_rows > 0: only the systems of at least min_rows rows get blocks (the
+// size split's table; the others have none and are never visited).
+static int build_table(gbs_mat A, int32_t R, int32_t cap_per_sm, TableDev &t, cudaStream_t st,
+                       int64_t min_rows = 0) {
+  std::vector<int32_t> row0, sys, sb0(A->nsys + 1, 0), sl0, row1, sl1;
   int32_t slices = 0;
   for (int32_t q = 0; q < A->nsys; ++q) {
     const int64_t a = A->row_off_h[q], e = A->row_off_h[q + 1];
-    for (int64_t r = a; r < e; r += R) {
+    for (int64_t r = a; r < e && e - a >= min_rows; r += R) {
+      const int64_t re = std::min<int64_t>(r + R, e);
       row0.push_back((int32_t)r);
       sys.push_back(q);
       sl0.push_back(slices + (int32_t)((r - a) / 32));
+      row1.push_back((int32_t)re);
+      sl1.push_back(slices + (int32_t)((re - a + 31) / 32));
     }
     slices += (int32_t)((e - a + 31) / 32);
     sb0[q + 1] = (int32_t)row0.size();
@@ -127,8 +133,10 @@ static int build_table(gbs_mat A, int32_t R, int32_t cap_per_sm, TableDev &t, cu
   for (int32_t q = 0; q < A->nsys; ++q)
     so[q + 1] = so[q] + (int32_t)std::min<int64_t>(sb0[q + 1] - sb0[q], grid);
   free_table(t);
-  // one buffer: row0 (nb + 1), slice0 (nb + 1), sys (nb), sys_blk0, sys_slot0 (nsys + 1 each)
-  const size_t tot = 3 * (size_t)nb + 2 + 2 * ((size_t)A->nsys + 1);
+  // one buffer: row0 (nb + 1), slice0 (nb + 1), sys (nb), sys_blk0, sys_slot0 (nsys + 1
+  // each), and with gaps (min_rows > 0) row1, slice1 (nb each)
+  const bool ends = min_rows > 0;
+  const size_t tot = 3 * (size_t)nb + 2 + 2 * ((size_t)A->nsys + 1) + (ends ? 2 * (size_t)nb : 0);
   std::vector<int32_t> h;
   h.reserve(tot);
   h.insert(h.end(), row0.begin(), row0.end());
@@ -136,6 +144,10 @@ static int build_table(gbs_mat A, int32_t R, int32_t cap_per_sm, TableDev &t, cu
   h.insert(h.end(), sys.begin(), sys.end());
   h.insert(h.end(), sb0.begin(), sb0.end());
   h.insert(h.end(), so.begin(), so.end());
+  if (ends) {
+    h.insert(h.end(), row1.begin(), row1.end());
+    h.insert(h.end(), sl1.begin(), sl1.end());
+  }
   int32_t *d = nullptr;
   GBS_TRY(dev_alloc(&d, tot, st));
   GBS_TRY_CUDA(cudaMemcpyAsync(d, h.data(), sizeof(int32_t) * tot, cudaMemcpyHostToDevice, st));
@@ -144,6 +156,8 @@ static int build_table(gbs_mat A, int32_t R, int32_t cap_per_sm, TableDev &t, cu
   t.sys = d + 2 * (size_t)nb + 2;
   t.sys_blk0 = t.sys + nb;
   t.sys_slot0 = t.sys_blk0 + A->nsys + 1;
+  t.row1 = ends ? t.sys_slot0 + A->nsys + 1 : nullptr;
+  t.slice1 = ends ? t.row1 + nb : nullptr;
   t.sys_blk0_h = sb0;
   t.nblocks = nb;
   t.grid = (int32_t)grid;
@@ -185,6 +199,32 @@ static void halo_window(gbs_mat A, int32_t R, const TableDev &t) {
     A->halo_lo = (int32_t)lo;
     A->halo_n = (int32_t)(lo + hi + 1);
   }
+}
+
+// The size split's tables: the systems of at least split_rows rows, cut into
+// blocks sized for them alone (about one block per CTA of a one-wave grid, as
+// the plan's automatic sizes are for the whole batch), at the plan's
+// occupancy.  Rebuilt when the split or the plan changes.
+int build_split_tables(gbs_mat A, cudaStream_t st) {
+  if (A->split_built == A->split_rows && A->sa.row0) return GBS_OK;
+  int occ_rows = 1, occ_upd = 1, nsm = 1;
+  GBS_TRY(phase_occupancy(A->lanes, &occ_rows, &occ_upd));
+  GBS_TRY_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, A->device));
+  const int cap_a = A->ctas_per_sm ? A->ctas_per_sm : occ_rows;
+  const int cap_e = A->ctas_per_sm ? A->ctas_per_sm : occ_upd;
+  int64_t rows = 0;
+  for (int32_t q = 0; q < A->nsys; ++q) {
+    const int64_t n = A->row_off_h[q + 1] - A->row_off_h[q];
+    if (n >= A->split_rows) rows += n;
+  }
+  auto auto_rows = [&](int cap) {
+    const int64_t per = (rows + (int64_t)cap * nsm - 1) / ((int64_t)cap * nsm);
+    return (int32_t)std::min<int64_t>(65536, std::max<int64_t>(PHASE_TPB, (per + 31) / 32 * 32));
+  };
+  GBS_TRY(build_table(A, auto_rows(cap_a), cap_a, A->sa, st, A->split_rows));
+  GBS_TRY(build_table(A, auto_rows(cap_e), cap_e, A->se, st, A->split_rows));
+  A->split_built = A->split_rows;
+  return GBS_OK;
 }
 
 // nnz_off[q] = row_ptr[first row of system q] (q = 0 .. nsys).
@@ -254,6 +294,9 @@ int build_plan(gbs_mat A, int32_t Ra, int32_t Re, int32_t kernel, int32_t ctas_p
     return GBS_ERR_ARG;
   }
   drop_graphs(A);
+  free_table(A->sa);  // the size split's tables follow the plan
+  free_table(A->se);
+  A->split_built = 0;
   if (kernel == GBS_SPMV_AUTO) {
     GBS_TRY(sell_shape(A, st));
     kernel = (A->sell_ptr && (double)A->sell_nnz <= 1.2 * (double)A->nnz)

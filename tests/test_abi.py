@@ -116,7 +116,8 @@ HANDLE_CALLS = {  # every entry point taking a matrix / vector handle: its argum
     "mat_autotune": [P, P],
     "mat_autotune_file": [P, P, P, P],
     "mat_set_cg_form": [P, I32],
-    "mat_get_tuning": [P, P, P],
+    "mat_get_tuning": [P, P, P, P],
+    "mat_set_split_rows": [P, I64],
     "vec_set_values_coo": [P, P, I32, P, P],
     "vec_get_info": [P, P, P, P],
 }
