@@ -344,18 +344,20 @@ int mat_get_coo_maps(gbs_mat A, const int32_t **perm, const int32_t **jmap,
 
 /*
  * Launch plan used by mat_mult and the solves.  Every phase kernel runs
- * 256-thread CTAs; a CTA walks blocks c, c + grid, ... of its phase's block
+ * 512-thread CTAs; a CTA walks blocks c, c + grid, ... of its phase's block
  * table.  spmv_rows: rows per block of the SpMV phases (a multiple of 32 in
  * [32, 65536], or 0: about one block per CTA, at least 256); update_rows:
  * rows per block of the vector-update phases (same).  kernel: the row
  * products --
  *   GBS_SPMV_SELL: a sliced-ELL copy of the matrix (32-row slices stored
  *     column-major, padding skipped), one lane per row, built on first use
- *     (about (4 + 8) bytes per padded entry more device memory, plus 4 bytes
- *     more once a refined solve needs FP32 values);
+ *     (at most (4 + 8) bytes per padded entry more device memory, plus 4
+ *     bytes more once a refined solve needs FP32 values; column patterns,
+ *     mat_set_slice_patterns, replace the column indices);
  *   1, 2, 4, 8 or 32: the CSR arrays read by that many lanes per row;
- *   GBS_SPMV_AUTO: sliced ELL when padding adds at most 20% to the entries,
- *     else CSR-vector with lanes from the mean row length.
+ *   GBS_SPMV_AUTO: sliced ELL when padding to the slices' longest rows adds
+ *     at most 20% to the entries, else CSR-vector with lanes from the mean
+ *     row length.
  * Every kernel sums each row in CSR order with one FMA per nonzero except
  * CSR-vector with more than one lane, which splits the row over the lanes
  * and adds the lane sums in a fixed tree.  ctas_per_sm: cap on the grids in
@@ -369,6 +371,24 @@ int mat_get_coo_maps(gbs_mat A, const int32_t **perm, const int32_t **jmap,
  */
 int mat_set_plan(gbs_mat A, int32_t spmv_rows, int32_t update_rows, int32_t kernel,
                  int32_t ctas_per_sm);
+
+/*
+ * Column patterns of the sliced-ELL copy (on = 1, the default, or 0).  With
+ * patterns on, a 32-row slice whose rows draw their offsets col - row from a
+ * common set of at most 32 (at most a quarter more than its longest row)
+ * stores that set once, ascending, and one 32-bit mask per row instead of a
+ * column index per entry; its width becomes the set's size and entries a
+ * row lacks hold 0 and are skipped by the mask.  The row products sum the
+ * same terms in the same (CSR) order either way, so every result is
+ * bit-identical with patterns on or off; only the bytes read change (8 per
+ * FP64 entry plus 4 per row, against 10 or 12 per entry).  A copy that
+ * exists (and the transpose's, for BiCG) is rebuilt at once; cached graphs
+ * are dropped.  Synchronises the device.  mat_get_slices returns the copy's
+ * slices, how many of them have a pattern and its padded entries (host
+ * outputs, each may be NULL; zeros while no copy is built).
+ */
+int mat_set_slice_patterns(gbs_mat A, int32_t on);
+int mat_get_slices(gbs_mat A, int64_t *nslices, int64_t *pattern_slices, int64_t *entries);
 int mat_get_plan(gbs_mat A, int32_t *spmv_rows, int32_t *update_rows, int32_t *kernel,
                  int32_t *ctas_per_sm, int32_t *spmv_grid);
 
@@ -416,8 +436,8 @@ int mat_set_split_rows(gbs_mat A, int64_t min_rows);
  * form also needs an ensemble solve (ksp_solve_cg, one system or a batch
  * solved as one), else the two-kernel form runs.  GBS_KSP_CGSR follows the
  * handle's form too: the single-kernel form where it applies, else two
- * kernels.  The per-CTA and cluster engines and the refined solve always use
- * the textbook form.  No synchronisation.  mat_get_tuning returns the solver
+ * kernels.  The per-CTA solver and the refined solve always use the
+ * textbook form.  No synchronisation.  mat_get_tuning returns the solver
  * setting (mat_set_solver), the CG form and the split row count
  * (mat_set_split_rows) (host outputs, each may be NULL).
  */
@@ -427,23 +447,27 @@ int mat_get_tuning(gbs_mat A, int32_t *solver, int32_t *cg_form, int64_t *split_
 /*
  * Autotuner of the FP64 CG solve ("rows-per-warp and block shapes picked by a
  * project-written autotuner"): candidates are launch plans (as mat_set_plan:
- * block rows, row-product kernel, CTAs per SM), then, for the fastest plan,
- * the single-reduction CG forms (two kernels; one kernel, for a handle of
- * one system) and (sliced ELL; batches, or systems within
- * 16 times the per-CTA size rule) the per-CTA engine, and for batches the
- * size split (GBS_SOLVER_SPLIT) at the row counts of the 1st, 4th, 16th
- * and 64th largest systems.  Each candidate runs a fixed 30-iteration FP64
+ * block rows, row-product kernel, CTAs per SM) -- for a handle of one system
+ * each with the textbook and the two-kernel single-reduction CG form and
+ * with the column patterns of the sliced copy (mat_set_slice_patterns) on
+ * and off, unless the copy takes none -- then, for the fastest of them, the
+ * one-kernel form (one system) or the single-reduction form (batches), the
+ * per-CTA engine (sliced ELL; batches, or systems within 16 times the
+ * per-CTA size rule), and for batches the size split (GBS_SOLVER_SPLIT) at
+ * the row counts of the 1st, 4th, 16th and 64th largest systems and last the
+ * other pattern setting.  Each candidate runs a fixed 30-iteration FP64
  * CG (rtol 0, every candidate the same work; a batched handle solves its
  * systems each on its own) once untimed and three times under CUDA events
  * on `stream`; the fastest becomes the handle's plan, solver
- * (mat_set_solver), CG form (mat_set_cg_form) and split row count
- * (mat_set_split_rows); on a batched handle the engine chosen for its
+ * (mat_set_solver), CG form (mat_set_cg_form), split row count
+ * (mat_set_split_rows) and pattern setting; on a batched handle the engine chosen for its
  * batched solves leaves its ensemble solves (ksp_solve on the stacked
  * system) to GBS_SOLVER_AUTO's choice.  Synchronises.
  *
  * mat_autotune_file: the same, persisted.  path names a text file (created if
  * missing) of one line per tuned key: "<key> | Ra Re kernel ctas_per_sm
- * solver cg_form split_rows | <time>".  The key holds the handle's sizes, a hash of its
+ * solver cg_form split_rows patterns | <time>" (lines without the last one
+ * or two fields leave those settings as they are).  The key holds the handle's sizes, a hash of its
  * systems' sizes and of 257 sampled entries each of row_ptr and col, the
  * device name and SM count, and "fp64".  A matching line is applied without
  * timing (*from_cache = 1); otherwise the handle is tuned and the line

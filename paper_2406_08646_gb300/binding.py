@@ -38,7 +38,7 @@ EXPORTED = ["ksp_opts_default", "mat_create_coo", "mat_create_coo_batched",
             "vec_create_coo", "vec_set_values_coo", "vec_get_info", "vec_destroy",
             "ksp_solve", "ksp_solve_batched", "q1_hex_element_coo", "q1_hex_element_values",
             "edge_coo_values", "mat_autotune_file", "mat_set_cg_form", "mat_get_tuning",
-            "mat_set_split_rows"]
+            "mat_set_split_rows", "mat_set_slice_patterns", "mat_get_slices"]
 
 
 class KspOpts(ctypes.Structure):
@@ -115,6 +115,8 @@ def lib() -> ctypes.CDLL:
         "mat_set_cg_form": (ctypes.c_int, [P, I32]),
         "mat_get_tuning": (ctypes.c_int, [P, P, P, P]),
         "mat_set_split_rows": (ctypes.c_int, [P, I64]),
+        "mat_set_slice_patterns": (ctypes.c_int, [P, I32]),
+        "mat_get_slices": (ctypes.c_int, [P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -366,6 +368,16 @@ def mat_set_split_rows(A, min_rows: int):
     _check(lib().mat_set_split_rows(A, int(min_rows)))
 
 
+def mat_set_slice_patterns(A, on: bool):
+    _check(lib().mat_set_slice_patterns(A, 1 if on else 0))
+
+
+def mat_get_slices(A) -> dict:
+    v = [ctypes.c_int64(0) for _ in range(3)]
+    _check(lib().mat_get_slices(A, *[ctypes.byref(t) for t in v]))
+    return dict(zip(["nslices", "pattern_slices", "entries"], [t.value for t in v]))
+
+
 def mat_autotune(A, stream=None):
     _check(lib().mat_autotune(A, _stream(stream)))
 
@@ -511,6 +523,14 @@ class Mat:
 
     def plan(self) -> dict:
         return mat_get_plan(self.h)
+
+    def set_slice_patterns(self, on: bool):
+        """Column patterns of the sliced copy on (default) or off; results
+        are bit-identical either way."""
+        mat_set_slice_patterns(self.h, on)
+
+    def slices(self) -> dict:
+        return mat_get_slices(self.h)
 
     def set_solver(self, solver: int, split_rows=None):
         """The engine (SOLVER_*); with SOLVER_SPLIT, split_rows is the row

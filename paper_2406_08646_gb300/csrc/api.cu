@@ -445,6 +445,28 @@ int mat_set_plan(gbs_mat A, int32_t spmv_rows, int32_t update_rows, int32_t kern
   return GBS_OK;
 }
 
+int mat_set_slice_patterns(gbs_mat A, int32_t on) {
+  GBS_TRY(check_mat(A, "mat_set_slice_patterns"));
+  if (on != 0 && on != 1) {
+    set_error("mat_set_slice_patterns: on = %d must be 0 or 1", on);
+    return GBS_ERR_ARG;
+  }
+  GBS_TRY(use_device(A));
+  GBS_TRY_CUDA(cudaDeviceSynchronize());  // the old copy may be in use
+  GBS_TRY(set_slice_patterns(A, on != 0, nullptr));
+  GBS_TRY_CUDA(cudaDeviceSynchronize());
+  return GBS_OK;
+}
+
+int mat_get_slices(gbs_mat A, int64_t *nslices, int64_t *pattern_slices, int64_t *entries) {
+  GBS_TRY(check_mat(A, "mat_get_slices"));
+  const bool built = A->sell_val != nullptr;
+  if (nslices) *nslices = built ? A->nslices : 0;
+  if (pattern_slices) *pattern_slices = built ? A->sell_npat : 0;
+  if (entries) *entries = built ? A->sell_nnz : 0;
+  return GBS_OK;
+}
+
 int mat_set_solver(gbs_mat A, int32_t solver) {
   GBS_TRY(check_mat(A, "mat_set_solver"));
   if (solver < GBS_SOLVER_AUTO || solver > GBS_SOLVER_SPLIT) {
@@ -482,23 +504,28 @@ int mat_get_plan(gbs_mat A, int32_t *spmv_rows, int32_t *update_rows, int32_t *k
 // ------------------------------------------------------------------ autotuner
 //
 // A candidate is a launch plan (SpMV rows, update rows, row-product kernel,
-// CTAs per SM), a solver engine and a CG form.  Each is timed on a fixed
-// 30-iteration FP64 CG run (rtol 0, so every candidate does the same work;
-// batched handles solve their systems each on their own): one untimed run
-// (it builds the graph), then three timed back to back with CUDA events.
-// First the plans with the textbook form on the phase kernels; then, with
-// the best plan, the single-reduction form and (sliced ELL) the per-CTA
-// engine -- not for one system whose iteration is far beyond one SM's share.
+// CTAs per SM), a solver engine, a CG form and the column pattern setting.
+// Each is timed on a fixed 30-iteration FP64 CG run (rtol 0, so every
+// candidate does the same work; batched handles solve their systems each on
+// their own): one untimed run (it builds the graph), then three timed back
+// to back with CUDA events.  First the plans on the phase kernels (a single
+// system's with the textbook and the single-reduction form and with the
+// column patterns on and off; a batch's with the textbook form); then, with
+// the best of them, the other CG forms and (sliced ELL) the per-CTA engine
+// -- not for one system whose iteration is far beyond one SM's share -- and
+// for a batch the size split and last the other pattern setting.
 
 namespace {
 struct Tuning {
   int32_t Ra, Re, kernel, cpsm, solver, cg_form;
   int64_t split_rows;
+  int32_t patterns;  // column patterns of the sliced copy (1 / 0; -1: as they are)
 };
 
 // Makes t the handle's plan (rebuilt only when it differs from the current
-// one), solver and CG form.
+// one), solver, CG form and column patterns.
 int apply_tuning(gbs_mat A, const Tuning &t, cudaStream_t s) {
+  if (t.patterns >= 0) GBS_TRY(set_slice_patterns(A, t.patterns != 0, s));
   if (!(t.Ra == A->Ra && t.Re == A->Re && t.kernel == A->lanes && t.cpsm == A->ctas_per_sm))
     GBS_TRY(build_plan(A, t.Ra, t.Re, t.kernel, t.cpsm, s));
   if (t.solver != A->solver || t.split_rows != A->split_rows) drop_graphs(A);
@@ -511,7 +538,8 @@ int apply_tuning(gbs_mat A, const Tuning &t, cudaStream_t s) {
 
 // The resolved plan of the handle with its solver and form.
 Tuning current_tuning(gbs_mat A) {
-  return Tuning{A->Ra, A->Re, A->lanes, A->ctas_per_sm, A->solver, A->cg_form, A->split_rows};
+  return Tuning{A->Ra,     A->Re,         A->lanes,      A->ctas_per_sm,
+                A->solver, A->cg_form,    A->split_rows, A->sell_patterns ? 1 : 0};
 }
 
 // 257 evenly spaced entries each of row_ptr and col (the cache key's sample).
@@ -529,9 +557,10 @@ static int autotune(gbs_mat A, cudaStream_t s, Tuning *out, float *out_ms) {
   const bool per_system = A->nsys > 1;
   const int la = auto_lanes(A->nnz, A->nrows);
   const int sk = A->lanes;  // the kernel the current plan chose
-  const int plans[][4] = {{0, 0, sk, 0},     {0, 0, la, 0},     {256, 512, sk, 0},
-                          {512, 1024, sk, 0}, {0, 0, sk, 4},     {256, 2048, sk, 0},
-                          {0, 0, sk, 2},      {1024, 4096, sk, 0}};
+  const int plans[][4] = {{0, 0, sk, 0},      {0, 0, la, 0},       {256, 512, sk, 0},
+                          {512, 1024, sk, 0},  {0, 0, sk, 4},       {256, 2048, sk, 0},
+                          {0, 0, sk, 2},       {0, 0, sk, 3},       {1024, 4096, sk, 0},
+                          {2048, 4096, sk, 0}};
   double *b = nullptr, *x = nullptr;
   GBS_TRY(dev_alloc(&b, A->nrows, s));
   GBS_TRY(dev_alloc(&x, A->nrows, s));
@@ -545,8 +574,9 @@ static int autotune(gbs_mat A, cudaStream_t s, Tuning *out, float *out_ms) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
+  const int32_t pat = A->sell_patterns ? 1 : 0;
   Tuning best{A->Ra, A->Re, A->lanes, A->ctas_per_sm, GBS_SOLVER_PHASES, GBS_CG_TEXTBOOK,
-              A->split_rows};
+              A->split_rows, pat};
   float best_ms = 1e30f;
   int st = GBS_OK;
   auto timed = [&](const Tuning &t) -> bool {
@@ -568,19 +598,38 @@ static int autotune(gbs_mat A, cudaStream_t s, Tuning *out, float *out_ms) {
     }
     return true;
   };
-  for (const auto &c : plans) {
-    timed(Tuning{c[0], c[1], c[2], c[3], GBS_SOLVER_PHASES, GBS_CG_TEXTBOOK, A->split_rows});
-    if (st != GBS_OK) break;
+  // the plans on the phase kernels; a single system's with the textbook and
+  // (sliced ELL) the single-reduction form, each with the column patterns as
+  // they are and switched (unless the copy takes none): the best plan
+  // depends on both
+  const int npass = per_system || sk != GBS_SPMV_SELL ? 1 : 2;
+  for (int pass = 0; pass < npass && st == GBS_OK; ++pass) {
+    const int32_t pp = pass == 0 ? pat : 1 - pat;
+    if (pass == 1) {
+      if (set_slice_patterns(A, pp != 0, s) != GBS_OK) break;
+      if (pp == 1 && A->sell_npat == 0) break;  // patterns do not fit this matrix
+    }
+    for (const auto &c : plans) {
+      if (pass == 1 && c[2] != GBS_SPMV_SELL) continue;  // patterns concern the sliced copy
+      for (int32_t form : {GBS_CG_TEXTBOOK, GBS_CG_SINGLE_REDUCTION}) {
+        if (form != GBS_CG_TEXTBOOK && (per_system || c[2] != GBS_SPMV_SELL)) continue;
+        timed(Tuning{c[0], c[1], c[2], c[3], GBS_SOLVER_PHASES, form, A->split_rows, pp});
+        if (st != GBS_OK) break;
+      }
+      if (st != GBS_OK) break;
+    }
   }
   if (st == GBS_OK && best.kernel == GBS_SPMV_SELL) {
     const Tuning base = best;
     Tuning t = base;
-    t.cg_form = GBS_CG_SINGLE_REDUCTION;
-    timed(t);
-    if (st == GBS_OK && !per_system) {  // the one-kernel form (where it fits, else two)
+    if (per_system) {
+      t.cg_form = GBS_CG_SINGLE_REDUCTION;
+      timed(t);
+    } else {  // the one-kernel form (where it fits, else two)
       t.cg_form = GBS_CG_SINGLE_KERNEL;
       timed(t);
     }
+    t = base;
     const int64_t nz = per_system ? A->max_sys_nnz : A->nnz;
     const int64_t rows = per_system ? A->max_sys_rows : A->nrows;
     if (st == GBS_OK && (per_system || nz + 8 * rows <= 16 * CTA_AUTO_WORK)) {
@@ -602,6 +651,14 @@ static int autotune(gbs_mat A, cudaStream_t s, Tuning *out, float *out_ms) {
         timed(t);
       }
     }
+  }
+  // batches: the best candidate with the column patterns switched, unless
+  // the copy takes none either way
+  if (st == GBS_OK && per_system && best.kernel == GBS_SPMV_SELL &&
+      apply_tuning(A, best, s) == GBS_OK && (best.patterns == 0 || A->sell_npat > 0)) {
+    Tuning t = best;
+    t.patterns = best.patterns ? 0 : 1;
+    timed(t);
   }
   A->trips_counted = true;  // the timed solves' results are never read
   cudaEventDestroy(e0);
@@ -710,10 +767,12 @@ int mat_autotune_file(gbs_mat A, const char *path, int32_t *from_cache, void *st
       if (!bar || (size_t)(bar - line) != key.size() + 1 || strncmp(line, key.c_str(), key.size()))
         continue;
       long long sr = 1;
-      const int nf = sscanf(bar + 1, " %d %d %d %d %d %d %lld", &t.Ra, &t.Re, &t.kernel, &t.cpsm,
-                            &t.solver, &t.cg_form, &sr);
+      int pt = -1;
+      const int nf = sscanf(bar + 1, " %d %d %d %d %d %d %lld %d", &t.Ra, &t.Re, &t.kernel,
+                            &t.cpsm, &t.solver, &t.cg_form, &sr, &pt);
       if (nf >= 6) {  // the last matching line wins
-        t.split_rows = nf == 7 && sr >= 1 ? (int64_t)sr : 1;
+        t.split_rows = nf >= 7 && sr >= 1 ? (int64_t)sr : 1;
+        t.patterns = nf == 8 && (pt == 0 || pt == 1) ? pt : -1;
         hit = true;
       }
     }
@@ -726,8 +785,9 @@ int mat_autotune_file(gbs_mat A, const char *path, int32_t *from_cache, void *st
       st = autotune(A, s, &t, &ms);
       if (st == GBS_OK) {
         fseek(f, 0, SEEK_END);
-        fprintf(f, "%s | %d %d %d %d %d %d %lld | %.4f ms per 30 iterations\n", key.c_str(), t.Ra,
-                t.Re, t.kernel, t.cpsm, t.solver, t.cg_form, (long long)t.split_rows, ms);
+        fprintf(f, "%s | %d %d %d %d %d %d %lld %d | %.4f ms per 30 iterations\n", key.c_str(),
+                t.Ra, t.Re, t.kernel, t.cpsm, t.solver, t.cg_form, (long long)t.split_rows,
+                t.patterns, ms);
         fflush(f);
       }
     }

@@ -76,9 +76,9 @@ template <typename T, class F>
 __device__ __forceinline__ void cta_rows(const PcgArgs &a, const SysRange &g, const T *sval,
                                          const T *x, F &f) {
   if (a.stream_matrix)
-    sell_rows<T, true, GATHER_CA>(a.sptr, a.srow0, a.scol, a.soff, sval, x, g.s0, g.s1, f);
+    sell_rows<T, true, GATHER_CA>(a.sv, sval, x, g.s0, g.s1, f);
   else
-    sell_rows<T, false, GATHER_CA>(a.sptr, a.srow0, a.scol, a.soff, sval, x, g.s0, g.s1, f);
+    sell_rows<T, false, GATHER_CA>(a.sv, sval, x, g.s0, g.s1, f);
 }
 
 // Wall-clock limit (from the solve's start, DevCtl::t_start), for thread 0.

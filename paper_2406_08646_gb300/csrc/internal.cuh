@@ -140,6 +140,21 @@ struct TableDev {
   int64_t nslots = 0;            // reduction slots: sum over systems of min(blocks, grid)
 };
 
+// The sliced-ELL copy as the row products read it (sell.cu, sell_rows).
+// With column patterns (pat set) every slice takes its columns from its
+// pattern: pool[pat[s] + k] is the pattern's k-th offset col - row
+// (ascending) and bit k of mask[32 s + i] says whether row i of the slice
+// holds it.  Without, the columns come from col (32-bit columns) or off
+// (16-bit offsets), exactly one of which is set.
+struct SellView {
+  const int32_t *ptr, *row0;  // nslices + 1 entry offsets and first rows
+  const int32_t *col;
+  const int16_t *off;
+  const int32_t *pat;
+  const int32_t *pool;
+  const uint32_t *mask;
+};
+
 }  // namespace gbs
 
 // ---------------------------------------------------------------- the handle
@@ -175,6 +190,13 @@ struct gbs_mat_s {
                                    // in 16 bits (padding -32768); the kernels read these then
   double *sell_val = nullptr;      // sell_nnz
   float *sell_val32 = nullptr;     // sell_nnz (refined solves)
+  int32_t *sell_pat = nullptr;     // nslices: first offset of each slice's pattern in sell_pool
+  int32_t *sell_pool = nullptr;    // the patterns' offsets col - row
+  uint32_t *sell_mask = nullptr;   // 32 nslices: pattern entries each row holds
+  int64_t sell_npat = 0;           // slices with a pattern (0 or nslices)
+  int64_t sell_nnz_rows = 0;       // 32 x the slices' longest rows (the size without
+                                   // patterns: the automatic plan's padding rule)
+  bool sell_patterns = true;       // build column patterns when they fit
   std::vector<int32_t> sell_slice0_h;  // nsys + 1 first slice of each system
 
   // launch plan: two block tables (SpMV phases, vector-update phases), the
@@ -268,5 +290,7 @@ int sell_shape(gbs_mat A, cudaStream_t s);
 int sell_build(gbs_mat A, cudaStream_t s);
 int sell_values(gbs_mat A, cudaStream_t s);
 int sell_values32(gbs_mat A, cudaStream_t s);
+SellView sell_view(gbs_mat A);
+int set_slice_patterns(gbs_mat A, bool on, cudaStream_t s);
 
 }  // namespace gbs

@@ -50,11 +50,9 @@ struct KrylovArgs {
   int32_t nrows, nslices;                  // whole matrix (ensemble)
   const int32_t *order;                    // system of each CTA, largest first
   const int32_t *sys_row0, *sys_slice0;    // nsys + 1
-  const int32_t *sptr, *srow0, *scol;      // sliced-ELL copy of A
-  const int16_t *soff;                     //   (16-bit column offsets, scol null then)
+  SellView sv;                             // sliced-ELL copy of A
   const double *sval;
-  const int32_t *tptr, *tcol;              // sliced-ELL copy of A^T (same slices)
-  const int16_t *toff;
+  SellView tv;                             // sliced-ELL copy of A^T (same slices)
   const double *tval;
   int32_t stream_matrix;                   // evict-first loads of the copies
   const double *dinv;
@@ -89,12 +87,10 @@ __device__ __forceinline__ KSys kry_system(const KrylovArgs &a) {
 // Row products of the system with one of the two sliced copies; x may have
 // been written by this CTA, so its gathers take the coherent path.
 template <class F>
-__device__ __forceinline__ void kry_rows(const KrylovArgs &a, const KSys &g, const int32_t *sptr,
-                                         const int32_t *scol, const int16_t *soff,
+__device__ __forceinline__ void kry_rows(const KrylovArgs &a, const KSys &g, const SellView &S,
                                          const double *sval, const double *x, F &f) {
-  if (a.stream_matrix)
-    sell_rows<double, true, GATHER_CA>(sptr, a.srow0, scol, soff, sval, x, g.s0, g.s1, f);
-  else sell_rows<double, false, GATHER_CA>(sptr, a.srow0, scol, soff, sval, x, g.s0, g.s1, f);
+  if (a.stream_matrix) sell_rows<double, true, GATHER_CA>(S, sval, x, g.s0, g.s1, f);
+  else sell_rows<double, false, GATHER_CA>(S, sval, x, g.s0, g.s1, f);
 }
 
 // The system's closing state (thread 0), x = 0 where b = 0, then
@@ -123,7 +119,7 @@ __device__ void kry_close(const KrylovArgs &a, const KSys &g, CtaShared &sh, int
     const double d = b[r] - t;
     tt[0] = fma(d, d, tt[0]);
   };
-  kry_rows(a, g, a.sptr, a.scol, a.soff, a.sval, x, f);
+  kry_rows(a, g, a.sv, a.sval, x, f);
   cta_sum0<double, 1>(tt, sh);
   if (threadIdx.x == 0) S.tt = tt[0];
 }
@@ -163,7 +159,7 @@ __device__ void kry_bicg(const KrylovArgs &a, const KSys &g, CtaShared &sh) {
     v[3] += (dv == 0.0) ? 1.0 : 0.0;
   };
   if (C.nonzero_guess) {
-    kry_rows(a, g, a.sptr, a.scol, a.soff, a.sval, x, start);
+    kry_rows(a, g, a.sv, a.sval, x, start);
   } else {
     for (int i = g.r0 + threadIdx.x; i < g.r1; i += blockDim.x) {
       x[i] = 0.0;
@@ -215,9 +211,9 @@ __device__ void kry_bicg(const KrylovArgs &a, const KSys &g, CtaShared &sh) {
       q[i] = y;
       sg[0] = fma(pt[i], y, sg[0]);
     };
-    kry_rows(a, g, a.sptr, a.scol, a.soff, a.sval, p, fq);
+    kry_rows(a, g, a.sv, a.sval, p, fq);
     auto fqt = [&](int i, double y) { qt[i] = y; };
-    kry_rows(a, g, a.tptr, a.tcol, a.toff, a.tval, pt, fqt);
+    kry_rows(a, g, a.tv, a.tval, pt, fqt);
     cta_sum0<double, 1>(sg, sh);
     if (t0) {
       ++it;
@@ -276,7 +272,7 @@ __device__ void kry_tfqmr(const KrylovArgs &a, const KSys &g, CtaShared &sh) {
     v[2] += (dv == 0.0) ? 1.0 : 0.0;
   };
   if (C.nonzero_guess) {
-    kry_rows(a, g, a.sptr, a.scol, a.soff, a.sval, x, start);
+    kry_rows(a, g, a.sv, a.sval, x, start);
   } else {
     for (int i = g.r0 + threadIdx.x; i < g.r1; i += blockDim.x) {
       x[i] = 0.0;
@@ -338,7 +334,7 @@ __device__ void kry_tfqmr(const KrylovArgs &a, const KSys &g, CtaShared &sh) {
       vv[i] = y;
       sg[0] = fma(rt[i], y, sg[0]);
     };
-    kry_rows(a, g, a.sptr, a.scol, a.soff, a.sval, t, f0);
+    kry_rows(a, g, a.sv, a.sval, t, f0);
     cta_sum0<double, 1>(sg, sh);
     if (t0) {
       it = 1;
@@ -382,7 +378,7 @@ __device__ void kry_tfqmr(const KrylovArgs &a, const KSys &g, CtaShared &sh) {
         s2[0] = fma(wn, wn, s2[0]);
         s2[1] = fma(rt[i], wn, s2[1]);
       };
-      kry_rows(a, g, a.sptr, a.scol, a.soff, a.sval, t, f1);
+      kry_rows(a, g, a.sv, a.sval, t, f1);
       cta_sum0<double, 2>(s2, sh);
       if (t0) {
         bool stop = half(s2[0]);
@@ -422,7 +418,7 @@ __device__ void kry_tfqmr(const KrylovArgs &a, const KSys &g, CtaShared &sh) {
         vv[i] = vn;
         s3[0] = fma(rt[i], vn, s3[0]);
       };
-      kry_rows(a, g, a.sptr, a.scol, a.soff, a.sval, t, f2);
+      kry_rows(a, g, a.sv, a.sval, t, f2);
       cta_sum0<double, 1>(s3, sh);
       if (t0) {
         ++it;  // B y1
@@ -473,8 +469,8 @@ template <class F>
 __device__ __forceinline__ void rows_t(const PcgArgs &a, int b, const double *x, F &f) {
   const int s0 = __ldg(a.ta.slice0 + b), s1 = blk_slice_end(a.ta, b);
   if (a.stream_matrix)
-    sell_rows<double, true, GATHER_NC>(a.tptr, a.srow0, a.tcol, a.toff, a.tval, x, s0, s1, f);
-  else sell_rows<double, false, GATHER_NC>(a.tptr, a.srow0, a.tcol, a.toff, a.tval, x, s0, s1, f);
+    sell_rows<double, true, GATHER_NC>(a.tv, a.tval, x, s0, s1, f);
+  else sell_rows<double, false, GATHER_NC>(a.tv, a.tval, x, s0, s1, f);
 }
 
 __device__ __forceinline__ void ns_activate(const PcgArgs &a, SysState &S, int status) {
@@ -1628,9 +1624,9 @@ __global__ void NS_ROWS k_sr_fused(PcgArgs a) {
       dl = fma(y, __ldca(u + i), dl);
     };
     if (a.stream_matrix)
-      sell_rows<double, true, GATHER_CA>(a.sptr, a.srow0, a.scol, a.soff, a.sval, u, s0, s1, f);
+      sell_rows<double, true, GATHER_CA>(a.sv, a.sval, u, s0, s1, f);
     else
-      sell_rows<double, false, GATHER_CA>(a.sptr, a.srow0, a.scol, a.soff, a.sval, u, s0, s1, f);
+      sell_rows<double, false, GATHER_CA>(a.sv, a.sval, u, s0, s1, f);
     acc2 = dl;
     last = b;
   }
@@ -1863,15 +1859,10 @@ int solve_krylov(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool 
   a.order = A->cta_order;
   a.sys_row0 = A->sys_row0;
   a.sys_slice0 = A->sys_slice0;
-  a.sptr = A->sell_ptr;
-  a.srow0 = A->sell_row0;
-  a.scol = A->sell_off16 ? nullptr : A->sell_col;
-  a.soff = A->sell_off16;
+  a.sv = sell_view(A);
   a.sval = A->sell_val;
   if (bicg) {
-    a.tptr = A->At->sell_ptr;
-    a.tcol = A->At->sell_off16 ? nullptr : A->At->sell_col;
-    a.toff = A->At->sell_off16;
+    a.tv = sell_view(A->At);
     a.tval = A->At->sell_val;
   }
   a.stream_matrix = stream_matrix(A, bicg ? 24 : 12);

@@ -264,10 +264,7 @@ PcgArgs make_args(gbs_mat A, bool per_system, bool refined) {
   a.col = A->col;
   a.val = A->val;
   a.val32 = A->val32;
-  a.sptr = A->sell_ptr;
-  a.srow0 = A->sell_row0;
-  a.scol = A->sell_off16 ? nullptr : A->sell_col;
-  a.soff = A->sell_off16;
+  a.sv = sell_view(A);
   a.sval = A->sell_val;
   a.sval32 = A->sell_val32;
   a.stream_matrix = stream_matrix(A, refined ? 8 : 12);
@@ -291,9 +288,7 @@ PcgArgs make_args(gbs_mat A, bool per_system, bool refined) {
   if (A->kv)
     for (int k = 0; k < KRYLOV_NVEC; ++k) a.kv[k] = A->kv + (size_t)k * (size_t)A->nrows;
   if (A->At) {
-    a.tptr = A->At->sell_ptr;
-    a.tcol = A->At->sell_off16 ? nullptr : A->At->sell_col;
-    a.toff = A->At->sell_off16;
+    a.tv = sell_view(A->At);
     a.tval = A->At->sell_val;
   }
   return a;

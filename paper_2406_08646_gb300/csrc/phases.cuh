@@ -75,9 +75,7 @@ struct PcgArgs {
   const int32_t *row_ptr, *col;
   const double *val;
   const float *val32;
-  const int32_t *sptr;   // sliced-ELL copy (kernels with L == 0)
-  const int32_t *srow0, *scol;
-  const int16_t *soff;   // 16-bit column offsets of the sliced copy (scol null then)
+  SellView sv;           // sliced-ELL copy (kernels with L == 0)
   const double *sval;
   const float *sval32;
   int32_t stream_matrix;  // 1: load the sliced copy evict-first (larger than L2 / 2)
@@ -95,8 +93,7 @@ struct PcgArgs {
   int32_t stepped;                  // 1: loop trips launched by the host
   int32_t trip;                     // stepped: index of this trip
   double *kv[KRYLOV_NVEC];          // nonsymmetric solvers' work vectors
-  const int32_t *tptr, *tcol;       // sliced-ELL copy of A^T (BiCG), A's slices
-  const int16_t *toff;              //   (its 16-bit offsets, tcol null then)
+  SellView tv;                      // sliced-ELL copy of A^T (BiCG), A's slices
   const double *tval;
   int32_t *halo_flags;              // one-kernel CG: iteration each CTA published
   int32_t halo_lo, halo_n;          //   and the window of CTAs it waits for
@@ -525,14 +522,13 @@ struct Vals {
 
 // How a row product gathers x: GATHER_NC the read-only path (x is not
 // written during the kernel), GATHER_CA a plain L1-cached load (coherent for
-// values the same CTA wrote before a barrier), GATHER_CG an L2 load (values
-// other CTAs of a cluster wrote before a cluster barrier).
-enum { GATHER_CA = 0, GATHER_NC = 1, GATHER_CG = 2 };
+// values the same CTA wrote before a barrier, and for values other CTAs
+// published with a release that this thread's acquire load observed).
+enum { GATHER_CA = 0, GATHER_NC = 1 };
 
 template <int GATHER, typename T>
 __device__ __forceinline__ T ld_x(const T *p) {
   if constexpr (GATHER == GATHER_NC) return __ldg(p);
-  else if constexpr (GATHER == GATHER_CG) return __ldcg(p);
   else return __ldca(p);
 }
 
@@ -559,11 +555,14 @@ struct Pair<float> {
 // CSR order, one FMA per stored nonzero; padding is skipped.  Entries
 // k = 2m, 2m + 1 of a lane's row are adjacent (pair layout, sell.cu), so one
 // load fetches two column indices and one 8- or 16-byte load two values; two
-// pairs are in flight per step.  Column indices come as 32-bit columns
-// (scol, padding -1) or, when every column is within 2^15 - 1 of its row, as
-// 16-bit offsets col - row (soff, padding SELL_PAD16): 10 bytes per FP64
-// nonzero instead of 12.  Exactly one of scol and soff is non-null.  A
-// slice's offsets and first rows are loaded before its entries, so no
+// pairs are in flight per step.  With column patterns (S.pat set) no column
+// index is read: lane i's k-th column is r + pool[pat[sl] + k], the offsets
+// loaded two at a time by one broadcast load, and bit k of its mask says
+// whether row i holds it (8 bytes per FP64 entry plus 4 per row).  Without,
+// column indices come as 32-bit columns (S.col, padding -1) or, when every
+// column is within 2^15 - 1 of its row, as 16-bit offsets col - row (S.off,
+// padding SELL_PAD16): 10 bytes per FP64 nonzero instead of 12.  A slice's
+// bounds, first row and pattern are loaded before its entries, so no
 // dependent load is left for the end.  f(r, sum) runs on every lane whose row
 // exists.  STREAM: the entries are loaded with the evict-first hint, so that
 // a matrix larger than L2 does not push the vectors (x and the solver's
@@ -575,8 +574,7 @@ struct Pair<float> {
 // 96^3 matrix: 42.4 -> 38.3 us per FP32 inner SpMV phase; the same prefetch
 // slows the FP64 row product (53.8 -> 62.6 us; offsets alone 55.9 us).
 // NC: how x is gathered (GATHER_NC where x is not written during the kernel,
-// GATHER_CA where the same CTA wrote it before a __syncthreads, GATHER_CG
-// where other CTAs of a cluster wrote it before a cluster barrier).
+// GATHER_CA where it was written during the kernel: ld_x).
 constexpr int16_t SELL_PAD16 = -32768;
 
 // The two column indices of a pair (entries 2m, 2m + 1 of a lane's row): from
@@ -592,26 +590,68 @@ __device__ __forceinline__ int2 sell_pair_cols(const int2 *__restrict__ c2,
   return ld_entry<STREAM>(c2 + pi);
 }
 
+// Slices with column patterns (S.pat set: every slice has one).
 template <typename T, bool STREAM, int NC, class F>
-__device__ __forceinline__ void sell_rows(const int32_t *__restrict__ sptr,
-                                          const int32_t *__restrict__ srow0,
-                                          const int32_t *__restrict__ scol,
-                                          const int16_t *__restrict__ soff,
-                                          const T *__restrict__ sval, const T *x,
-                                          int s0, int s1, F &f) {
+__device__ __forceinline__ void sell_rows_pat(const SellView &S, const T *__restrict__ sval,
+                                              const T *x, int s0, int s1, F &f) {
   typedef typename Pair<T>::type P;
-  const int2 *__restrict__ c2 = reinterpret_cast<const int2 *>(scol);
-  const int *__restrict__ o2 = reinterpret_cast<const int *>(soff);  // two offsets per int
   const P *__restrict__ v2 = reinterpret_cast<const P *>(sval);
   const int lane = threadIdx.x & 31;
   for (int sl = s0 + (int)(threadIdx.x >> 5); sl < s1; sl += (int)(blockDim.x >> 5)) {
-    const int b0 = __ldg(sptr + sl), b1 = __ldg(sptr + sl + 1);
-    const int r = __ldg(srow0 + sl) + lane, re = __ldg(srow0 + sl + 1);
+    const int b0 = __ldg(S.ptr + sl), b1 = __ldg(S.ptr + sl + 1);
+    const int r = __ldg(S.row0 + sl) + lane, re = __ldg(S.row0 + sl + 1);
+    const int2 *__restrict__ pat2 = reinterpret_cast<const int2 *>(S.pool + __ldg(S.pat + sl));
+    uint32_t mk = __ldg(S.mask + 32 * (int64_t)sl + lane);
+    if constexpr (STREAM && sizeof(T) == 4) {  // the slice's whole run in flight at once
+      if (lane == 0) prefetch_rows(sval, b0, b1);
+    }
+    int pi = (b0 >> 1) + lane;
+    const int pend = pi + 32 * ((b1 - b0) >> 6);
+    T acc = T(0);
+    for (; pi + 32 < pend; pi += 64, pat2 += 2, mk >>= 4) {
+      const int2 oa = __ldg(pat2), ob = __ldg(pat2 + 1);
+      const P va = ld_entry<STREAM>(v2 + pi), vb = ld_entry<STREAM>(v2 + pi + 32);
+      if (mk & 1u) acc = fma_rn(va.x, ld_x<NC>(x + r + oa.x), acc);
+      if (mk & 2u) acc = fma_rn(va.y, ld_x<NC>(x + r + oa.y), acc);
+      if (mk & 4u) acc = fma_rn(vb.x, ld_x<NC>(x + r + ob.x), acc);
+      if (mk & 8u) acc = fma_rn(vb.y, ld_x<NC>(x + r + ob.y), acc);
+    }
+    if (pi < pend) {
+      const int2 oa = __ldg(pat2);
+      const P va = ld_entry<STREAM>(v2 + pi);
+      if (mk & 1u) acc = fma_rn(va.x, ld_x<NC>(x + r + oa.x), acc);
+      if (mk & 2u) acc = fma_rn(va.y, ld_x<NC>(x + r + oa.y), acc);
+      mk >>= 2;
+      ++pat2;
+    }
+    if ((((b1 - b0) >> 5) & 1) && (mk & 1u)) {  // the odd last entry
+      const int o = __ldg(reinterpret_cast<const int *>(pat2));
+      acc = fma_rn(ld_entry<STREAM>(sval + (b1 - 32 + lane)), ld_x<NC>(x + r + o), acc);
+    }
+    if (r < re) f(r, acc);
+  }
+}
+
+template <typename T, bool STREAM, int NC, class F>
+__device__ __forceinline__ void sell_rows(const SellView &S, const T *__restrict__ sval,
+                                          const T *x, int s0, int s1, F &f) {
+  if (S.pat) {
+    sell_rows_pat<T, STREAM, NC>(S, sval, x, s0, s1, f);
+    return;
+  }
+  typedef typename Pair<T>::type P;
+  const int2 *__restrict__ c2 = reinterpret_cast<const int2 *>(S.col);
+  const int *__restrict__ o2 = reinterpret_cast<const int *>(S.off);  // two offsets per int
+  const P *__restrict__ v2 = reinterpret_cast<const P *>(sval);
+  const int lane = threadIdx.x & 31;
+  for (int sl = s0 + (int)(threadIdx.x >> 5); sl < s1; sl += (int)(blockDim.x >> 5)) {
+    const int b0 = __ldg(S.ptr + sl), b1 = __ldg(S.ptr + sl + 1);
+    const int r = __ldg(S.row0 + sl) + lane, re = __ldg(S.row0 + sl + 1);
     if constexpr (STREAM && sizeof(T) == 4) {  // the slice's whole run in flight at once
       if (lane == 0) prefetch_rows(sval, b0, b1);
       else if (lane == 1) {
-        if (soff) prefetch_rows(soff, b0, b1);
-        else prefetch_rows(scol, b0, b1);
+        if (S.off) prefetch_rows(S.off, b0, b1);
+        else prefetch_rows(S.col, b0, b1);
       }
     }
     // pair index of this lane's first pair, and one past its last full pair
@@ -636,11 +676,11 @@ __device__ __forceinline__ void sell_rows(const int32_t *__restrict__ sptr,
     if (((b1 - b0) >> 5) & 1) {  // the odd last entry, stored after the pairs
       const int q = b1 - 32 + lane;
       int c;
-      if (soff) {
-        const int o = ld_entry<STREAM>(soff + q);
+      if (S.off) {
+        const int o = ld_entry<STREAM>(S.off + q);
         c = o == SELL_PAD16 ? -1 : r + o;
       } else {
-        c = ld_entry<STREAM>(scol + q);
+        c = ld_entry<STREAM>(S.col + q);
       }
       if (c >= 0) acc = fma_rn(ld_entry<STREAM>(sval + q), ld_x<NC>(x + c), acc);
     }
@@ -658,9 +698,9 @@ __device__ __forceinline__ void row_products(const PcgArgs &a, int b, int r0, in
   if constexpr (L == 0) {
     const int s0 = __ldg(a.ta.slice0 + b), s1 = blk_slice_end(a.ta, b);
     if (a.stream_matrix)
-      sell_rows<T, true, GATHER_NC>(a.sptr, a.srow0, a.scol, a.soff, sell_val, x, s0, s1, f);
+      sell_rows<T, true, GATHER_NC>(a.sv, sell_val, x, s0, s1, f);
     else
-      sell_rows<T, false, GATHER_NC>(a.sptr, a.srow0, a.scol, a.soff, sell_val, x, s0, s1, f);
+      sell_rows<T, false, GATHER_NC>(a.sv, sell_val, x, s0, s1, f);
   } else
     csr_rows<T, L>(a.row_ptr, a.col, csr_val, x, r0, r1, f);
 }

@@ -30,17 +30,16 @@ __global__ void __launch_bounds__(PHASE_TPB) k_spmv(const int32_t *__restrict__ 
 
 // y = A x with the sliced-ELL row product (sell_rows), 8 slices per CTA pass.
 __global__ void __launch_bounds__(PHASE_TPB, SELL_MIN_CTAS)
-    k_spmv_sell(const int32_t *__restrict__ sptr, const int32_t *__restrict__ srow0,
-                const int32_t *__restrict__ scol, const int16_t *__restrict__ soff,
-                const double *__restrict__ sval, const double *__restrict__ x,
-                double *__restrict__ y, int32_t nslices, int32_t stream_matrix) {
+    k_spmv_sell(const SellView S, const double *__restrict__ sval,
+                const double *__restrict__ x, double *__restrict__ y, int32_t nslices,
+                int32_t stream_matrix) {
   auto f = [&](int r, double s) { y[r] = s; };
   const int per = PHASE_TPB / 32;
   for (int64_t s0 = (int64_t)blockIdx.x * per; s0 < nslices; s0 += (int64_t)gridDim.x * per) {
     const int s1 = (int)(s0 + per < nslices ? s0 + per : nslices);
     if (stream_matrix)
-      sell_rows<double, true, GATHER_NC>(sptr, srow0, scol, soff, sval, x, (int)s0, s1, f);
-    else sell_rows<double, false, GATHER_NC>(sptr, srow0, scol, soff, sval, x, (int)s0, s1, f);
+      sell_rows<double, true, GATHER_NC>(S, sval, x, (int)s0, s1, f);
+    else sell_rows<double, false, GATHER_NC>(S, sval, x, (int)s0, s1, f);
   }
 }
 
@@ -50,9 +49,8 @@ int launch_spmv(gbs_mat A, const double *x, double *y, cudaStream_t s) {
   if (A->lanes == GBS_SPMV_SELL) {
     const int64_t ns = A->nslices, per = PHASE_TPB / 32;
     const unsigned grid = (unsigned)std::min<int64_t>((ns + per - 1) / per, 1 << 20);
-    k_spmv_sell<<<grid, PHASE_TPB, 0, s>>>(
-        A->sell_ptr, A->sell_row0, A->sell_off16 ? nullptr : A->sell_col, A->sell_off16,
-        A->sell_val, x, y, (int32_t)ns, stream_matrix(A, A->sell_off16 ? 10 : 12));
+    k_spmv_sell<<<grid, PHASE_TPB, 0, s>>>(sell_view(A), A->sell_val, x, y, (int32_t)ns,
+                                           stream_matrix(A, 12));
     GBS_LAUNCHED(1);
     return GBS_OK;
   }
@@ -299,7 +297,7 @@ int build_plan(gbs_mat A, int32_t Ra, int32_t Re, int32_t kernel, int32_t ctas_p
   A->split_built = 0;
   if (kernel == GBS_SPMV_AUTO) {
     GBS_TRY(sell_shape(A, st));
-    kernel = (A->sell_ptr && (double)A->sell_nnz <= 1.2 * (double)A->nnz)
+    kernel = (A->sell_ptr && (double)A->sell_nnz_rows <= 1.2 * (double)A->nnz)
                  ? GBS_SPMV_SELL
                  : auto_lanes(A->nnz, A->nrows);
   }

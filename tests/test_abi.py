@@ -118,6 +118,8 @@ HANDLE_CALLS = {  # every entry point taking a matrix / vector handle: its argum
     "mat_set_cg_form": [P, I32],
     "mat_get_tuning": [P, P, P, P],
     "mat_set_split_rows": [P, I64],
+    "mat_set_slice_patterns": [P, I32],
+    "mat_get_slices": [P, P, P, P],
     "vec_set_values_coo": [P, P, I32, P, P],
     "vec_get_info": [P, P, P, P],
 }

@@ -52,7 +52,8 @@ def test_tuning_file_roundtrip_single_system():
         A = B.Mat.from_coo(p.nrows, p.ncols, t(p.i), t(p.j))
         A.set_values(t(p.v))
         assert A.autotune(path) is False                 # tuned, line appended
-        plan1, tun1 = A.plan(), A.tuning()
+        plan1, tun1, sl1 = A.plan(), A.tuning(), A.slices()
+        assert len(open(path).read().split("|")[1].split()) == 8
         assert tun1["solver"] in (B.SOLVER_PHASES, B.SOLVER_CTA)
         assert tun1["cg_form"] in (B.CG_TEXTBOOK, B.CG_SINGLE_REDUCTION, B.CG_SINGLE_KERNEL)
         check_parity(A, O, p.b, 1e-9)
@@ -64,6 +65,7 @@ def test_tuning_file_roundtrip_single_system():
         A2.set_values(t(p.v))
         assert A2.autotune(path) is True
         assert A2.plan() == plan1 and A2.tuning() == tun1
+        assert A2.slices() == sl1                         # the pattern setting too
         check_parity(A2, O, p.b, 1e-9)
         A2.close()
         assert len(open(path).read().splitlines()) == 1
