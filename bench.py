@@ -109,6 +109,16 @@ def stored_traffic(name: str):
         return None
 
 
+PATTERNS = "tuned"  # --patterns
+
+
+def force_patterns(h):
+    """Applies --patterns on / off after the autotuner (which otherwise picks)."""
+    if PATTERNS != "tuned":
+        from paper_2406_08646_gb300 import binding
+        binding.mat_set_slice_patterns(h, PATTERNS == "on")
+
+
 def pcg_alg_bytes(n: int, nnz: int, iterations: int) -> float:
     """Algorithmic bytes of one FP64 PCG launch: per iteration the floor
     12 nnz + 4 (n+1) + 72 n (A once; x, r, p read and written; D^-1 read; q
@@ -369,6 +379,7 @@ def run_suite(args):
         spmv_s = sp / 20
         import tempfile
         A.autotune(os.path.join(tempfile.mkdtemp(prefix="gbs_bench_c3_"), "tuning.txt"))
+        force_patterns(A.h)
         rows = {}
         for rtol in (1e-10, 1e-8):
             for prec, name in ((B.FP64, "fp64"), (B.FP32_REFINED, "fp32_refined")):
@@ -386,7 +397,7 @@ def run_suite(args):
         line = _base_line(
             args, rows["fp64@1e-10"]["s"],
             {"workload": "poisson3d_192: 7-point Laplacian 192^3, random-normal rhs, seed 1003",
-             "nrows": n, "nnz": nnz, "plan": A.plan()},
+             "nrows": n, "nnz": nnz, "plan": dict(A.plan(), patterns=A.slices()["pattern_slices"] > 0)},
             {"solves": rows,
              "refined_vs_fp64": {k: rows[f"fp32_refined@{k}"]["s"] / rows[f"fp64@{k}"]["s"]
                                  for k in ("1e-10", "1e-08")},
@@ -479,10 +490,11 @@ def run_suite(args):
         import tempfile
         tune_path = os.path.join(tempfile.mkdtemp(prefix="gbs_bench_c5_"), "tuning.txt")
         A.autotune(tune_path)
+        force_patterns(A.h)
         tuned = A.tuning()
         rows["engines"] = engines
         rows["autotuned"] = {"solver": tuned["solver"], "split_rows": tuned["split_rows"],
-                             "plan": A.plan()}
+                             "plan": A.plan(), "patterns": A.slices()["pattern_slices"] > 0}
         for prec, name in ((B.FP64, "batched_fp64"), (B.FP32_REFINED, "batched_fp32_refined")):
             ts, (_, rs) = _ev_time(stream, lambda: A.solve_batched(b, x, rtol=1e-8,
                                                                    precision=prec), reps=reps)
@@ -729,7 +741,8 @@ def run_gpu(args, rank: int, world: int):
     # the autotuner's file for this run: the first warm-up step tunes the
     # matrix, later steps (new handles of the same matrix) reload its choice
     import tempfile
-    tune_path = os.path.join(tempfile.mkdtemp(prefix="gbs_bench_"), "tuning.txt")
+    tune_path = args.tune_file or os.path.join(tempfile.mkdtemp(prefix="gbs_bench_"),
+                                               "tuning.txt")
     tune_hits = []
 
     def check(st):
@@ -753,6 +766,7 @@ def run_gpu(args, rank: int, world: int):
         et = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         et[0].record(stream)
         tune_hits.append(B.mat_autotune_file(A, tune_path, stream))
+        force_patterns(A)
         et[1].record(stream)
         ev[2].record(stream)
         check(L.ksp_solve_cg(A, B._dev(b_d, torch.float64), B._dev(x64, torch.float64),
@@ -778,7 +792,8 @@ def run_gpu(args, rank: int, world: int):
         ev[7].record(stream)
         res["adjoint"] = B.ksp_get_result(A, 1, stream)[0]
         nnz = B.mat_get_info(A)["nnz"]
-        plan = dict(B.mat_get_plan(A), **B.mat_get_tuning(A))
+        plan = dict(B.mat_get_plan(A), **B.mat_get_tuning(A),
+                    patterns=B.mat_get_slices(A)["pattern_slices"] > 0)
         B.mat_destroy(A)
         stream.synchronize()
         t = {"gen_indices": eg[0].elapsed_time(eg[1]), "gen_values": eg[1].elapsed_time(ev[0]),
@@ -865,9 +880,11 @@ def run_gpu(args, rank: int, world: int):
                        "l2": "no flush: every input is larger than L2 (CSR 290 MB, COO 906 MB)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "plan": plan, "loop": "host-stepped" if hl else "graph",
-                       "tuning": "mat_autotune_file: tuned in the first warm-up step, "
-                                 f"reloaded from its file in the timed steps "
-                                 f"({sum(tune_hits[-args.steps:])}/{args.steps} hits)"},
+                       "tuning": (f"mat_autotune_file: {sum(tune_hits)} of "
+                                  f"{len(tune_hits)} steps reloaded the tuning from its file "
+                                  f"({sum(tune_hits[-args.steps:])}/{args.steps} timed steps)"
+                                  + ("" if args.tune_file else
+                                     "; the first warm-up step tuned the matrix"))},
             "rows_ms": med,
             "iterations": {k: last[k]["iterations"] for k in ("fp64", "fp32_refined", "adjoint")},
             "outer_iterations_fp32_refined": last["fp32_refined"]["outer_iterations"],
@@ -961,6 +978,7 @@ def e2e_time(p, dev, stream, sp, L, B, o64, check, tune_path):
         ev[3].record(stream)
         check(L.mat_set_values_coo(A, B._dev(v2, torch.float64), B.INSERT, sp))
         B.mat_autotune_file(A, tune_path, stream)
+        force_patterns(A)
         ev[4].record(stream)
         check(L.ksp_solve_cg(A, B._dev(b2, torch.float64), B._dev(x2, torch.float64),
                              B.ctypes.byref(o64), None, sp))
@@ -1002,10 +1020,19 @@ def main():
                     help="c2 = the benchmark (default); c3/c4/c5 = comparison runs")
     ap.add_argument("--host-loop", action="store_true",
                     help="run the solves' loop from the host (for profiler launch lists)")
+    ap.add_argument("--tune-file", default="",
+                    help="the autotuner's file for the Q1 workload (default: a new one, so "
+                         "the first warm-up step tunes; an existing file skips the tuning, "
+                         "e.g. for launch lists)")
+    ap.add_argument("--patterns", default="tuned", choices=["tuned", "on", "off"],
+                    help="column patterns of the sliced copy: the autotuner's choice "
+                         "(default), or forced on / off after it (for profiling captures)")
     ap.add_argument("--ne", type=int, default=96,
                     help="elements per side of the Q1 workload (96 = the benchmark; "
                          "smaller only for profiling captures)")
     args = ap.parse_args()
+    global PATTERNS
+    PATTERNS = args.patterns
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
