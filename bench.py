@@ -478,10 +478,16 @@ def run_suite(args):
         # the size split with the k largest systems on the phase kernels
         order = np.sort(bt.nrows)[::-1]
         engines = {}
-        for name, solver, k in (("cta", B.SOLVER_CTA, 0), ("phases", B.SOLVER_PHASES, 0),
-                                ("split_8", B.SOLVER_SPLIT, 8), ("split_32", B.SOLVER_SPLIT, 32),
-                                ("split_128", B.SOLVER_SPLIT, 128),
-                                ("split_256", B.SOLVER_SPLIT, 256)):
+        # (plans: automatic blocks, or 4096-row SpMV / 8192-row update blocks;
+        # the per-CTA solver at one CTA per SM, or two under a cap of two)
+        for name, solver, k, plan in (
+                ("cta", B.SOLVER_CTA, 0, (0, 0, 0)), ("cta_2_per_sm", B.SOLVER_CTA, 0, (0, 0, 2)),
+                ("phases", B.SOLVER_PHASES, 0, (0, 0, 0)),
+                ("phases_4096", B.SOLVER_PHASES, 0, (4096, 8192, 0)),
+                ("split_8", B.SOLVER_SPLIT, 8, (4096, 8192, 0)),
+                ("split_32", B.SOLVER_SPLIT, 32, (4096, 8192, 0)),
+                ("split_128", B.SOLVER_SPLIT, 128, (4096, 8192, 0))):
+            A.set_plan(plan[0], plan[1], B.SPMV_SELL, plan[2])
             A.set_solver(solver, split_rows=int(order[k - 1]) if k else None)
             te_, (_, rs_) = _ev_time(stream, lambda: A.solve_batched(b, x, rtol=1e-8), reps=reps)
             engines[name] = {"s": te_, "ok": sum(q["status"] == B.OK for q in rs_),

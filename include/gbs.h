@@ -362,7 +362,9 @@ int mat_get_coo_maps(gbs_mat A, const int32_t **perm, const int32_t **jmap,
  * CSR-vector with more than one lane, which splits the row over the lanes
  * and adds the lane sums in a fixed tree.  ctas_per_sm: cap on the grids in
  * CTAs per SM (1..64), or 0 for as many as fit on an SM at once (each phase
- * kernel then runs in one wave and keeps one reduction slot per CTA).  mat_set_plan
+ * kernel then runs in one wave and keeps one reduction slot per CTA); the
+ * per-CTA CG solver (mat_set_solver) runs one CTA per SM, or two under a cap
+ * of two or more when a batch has more systems than SMs.  mat_set_plan
  * synchronises the device (the old tables may be in use) and drops the
  * cached solve graphs.  mat_create_coo picks (0, 0, GBS_SPMV_AUTO, 0);
  * mat_autotune (below) picks among candidates by timing them.  mat_get_plan
@@ -400,7 +402,8 @@ int mat_get_plan(gbs_mat A, int32_t *spmv_rows, int32_t *update_rows, int32_t *k
  *   GBS_SOLVER_CTA: one 1024-thread CTA per system runs every iteration in
  *     one kernel with CTA barriers only -- the latency path for small systems,
  *     and for batches of many systems, which then run as concurrent CTAs,
- *     largest first.  Needs the sliced-ELL plan kernel (GBS_ERR_ARG from the
+ *     largest first (CG: a grid of one CTA per SM -- two under a plan
+ *     cap of two or more -- each taking the next system when it is done).  Needs the sliced-ELL plan kernel (GBS_ERR_ARG from the
  *     solve otherwise); ignores host_loop; ksp_get_phase_ns reports zeros;
  *   GBS_SOLVER_SPLIT: CG (FP64 or refined) of a batched solve
  *     (ksp_solve_cg_batched, ksp_adjoint_batched) by size: the systems with
@@ -458,9 +461,12 @@ int mat_get_tuning(gbs_mat A, int32_t *solver, int32_t *cg_form, int64_t *split_
  * other pattern setting.  Each candidate runs a fixed 30-iteration FP64
  * CG (rtol 0, every candidate the same work; a batched handle solves its
  * systems each on its own) once untimed and three times under CUDA events
- * on `stream`; the fastest becomes the handle's plan, solver
- * (mat_set_solver), CG form (mat_set_cg_form), split row count
- * (mat_set_split_rows) and pattern setting; on a batched handle the engine chosen for its
+ * on `stream`; the three fastest then each solve A x = A 1 to rtol 1e-8
+ * once (timed), which catches what 30 iterations miss (a batch's systems
+ * converging at different iterations), and the fastest of those becomes the
+ * handle's plan, solver (mat_set_solver), CG form (mat_set_cg_form), split
+ * row count (mat_set_split_rows) and pattern setting; on a batched handle
+ * the engine chosen for its
  * batched solves leaves its ensemble solves (ksp_solve on the stacked
  * system) to GBS_SOLVER_AUTO's choice.  Synchronises.
  *

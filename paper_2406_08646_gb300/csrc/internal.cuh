@@ -111,7 +111,7 @@ struct DevCtl {
   int64_t t_start;         // globaltimer at the start of the solve
   int64_t stamp;           // globaltimer when the last phase kernel started
   int32_t last_phase;      // index of that phase, -1 before the first
-  int32_t pad;
+  int32_t queue;           // per-CTA solver: systems taken beyond the grid's first ones
   int64_t phase_ns[5];     // setup, A, B, C, final: start-to-next-start time
 };
 

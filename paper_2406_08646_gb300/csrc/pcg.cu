@@ -496,6 +496,24 @@ bool cta_size_rule(gbs_mat A, bool per_system, int systems_per_sm) {
          (per_system && A->nsys >= (int64_t)systems_per_sm * sm_count(A));
 }
 
+// The per-CTA PCG solver for a.cta_n systems: one CTA per SM (each system
+// then has an SM and 64 registers a thread to itself while it runs), or two
+// (32 registers) when the plan caps the grids at two or more CTAs per SM and
+// there are more systems than SMs; at most cta_n CTAs, which take the systems
+// beyond the grid from a queue (k_cta_pcg).
+static void launch_cta_pcg(gbs_mat A, const PcgArgs &a, bool refined, cudaStream_t s) {
+  const int64_t per = A->ctas_per_sm >= 2 && a.cta_n > sm_count(A) ? 2 : 1;
+  const unsigned grid =
+      (unsigned)std::max<int64_t>(1, std::min<int64_t>(a.cta_n, per * sm_count(A)));
+  if (per == 1) {
+    if (refined) k_cta_pcg<true, 1><<<grid, CTA_TPB, 0, s>>>(a);
+    else k_cta_pcg<false, 1><<<grid, CTA_TPB, 0, s>>>(a);
+  } else {
+    if (refined) k_cta_pcg<true, 2><<<grid, CTA_TPB, 0, s>>>(a);
+    else k_cta_pcg<false, 2><<<grid, CTA_TPB, 0, s>>>(a);
+  }
+}
+
 int sm_count(gbs_mat A) {
   int nsm = 1;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, A->device);
@@ -545,9 +563,8 @@ int solve(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool per_sys
     GBS_TRY(put_call(A->call, call_args(b, x, o), s, A->ctl));
     PcgArgs a = make_args(A, per_system, refined);
     a.order = per_system ? A->cta_order : nullptr;
-    const unsigned grid = per_system ? (unsigned)A->nsys : 1u;
-    if (refined) k_cta_pcg<true><<<grid, CTA_TPB, 0, s>>>(a);
-    else k_cta_pcg<false><<<grid, CTA_TPB, 0, s>>>(a);
+    a.cta_n = per_system ? A->nsys : 1;
+    launch_cta_pcg(A, a, refined, s);
     GBS_LAUNCHED(1);
     return GBS_OK;
   }
@@ -578,9 +595,9 @@ int solve(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool per_sys
     if (nbig < A->nsys) {
       PcgArgs a = make_args(A, per_system, refined);
       a.order = A->cta_order + nbig;
-      const unsigned grid = (unsigned)(A->nsys - nbig);
-      if (refined) k_cta_pcg<true><<<grid, CTA_TPB, 0, s>>>(a);
-      else k_cta_pcg<false><<<grid, CTA_TPB, 0, s>>>(a);
+      a.cta_n = A->nsys - nbig;
+      GBS_TRY_CUDA(cudaMemsetAsync(&A->ctl->queue, 0, sizeof(int32_t), s));
+      launch_cta_pcg(A, a, refined, s);
       GBS_LAUNCHED(1);
     }
     return GBS_OK;

@@ -88,7 +88,9 @@ struct PcgArgs {
   SysState *st;
   DevCtl *ctl;
   const CallArgs *call;
-  const int32_t *order;             // per-CTA solver: system of each CTA (largest first)
+  const int32_t *order;             // per-CTA solver: its systems, largest first
+  int32_t cta_n;                    //   how many (CTA k solves order[k], then takes the
+                                    //   next one from DevCtl::queue)
   cudaGraphConditionalHandle cond;  // loop condition of the graph (stepped == 0)
   int32_t stepped;                  // 1: loop trips launched by the host
   int32_t trip;                     // stepped: index of this trip
