@@ -40,11 +40,14 @@ namespace gbs {
 // Kernels with row products (setup, A, final) on the sliced-ELL layout
 // (L == 0) are held to 32 registers so that four 512-thread CTAs (64 warps)
 // fit per SM: the sliced product is latency-bound and needs every warp slot
-// to keep HBM busy.
-#define GBS_ROWS_BOUNDS(L) __launch_bounds__(PHASE_TPB, (L) == 0 ? SELL_MIN_CTAS : 1)
+// to keep HBM busy.  MB = 2: the same kernels for plans that cap the grids at
+// one or two CTAs per SM anyway, with 64 registers a thread (no spills; C2
+// FP64 product phase at two CTAs per SM 62.9 -> 51.9 us per iteration with
+// column patterns).
+#define GBS_ROWS_BOUNDS(L, MB) __launch_bounds__(PHASE_TPB, (L) == 0 ? (MB) : 1)
 
-template <bool REFINED, int L>
-__global__ void GBS_ROWS_BOUNDS(L) k_pcg_setup(PcgArgs a) {
+template <bool REFINED, int L, int MB = SELL_MIN_CTAS>
+__global__ void GBS_ROWS_BOUNDS(L, MB) k_pcg_setup(PcgArgs a) {
   __shared__ double red[RED_SCRATCH];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const int64_t t = (int64_t)global_ns();
@@ -55,8 +58,8 @@ __global__ void GBS_ROWS_BOUNDS(L) k_pcg_setup(PcgArgs a) {
   phase_setup<REFINED, L>(a, red);
 }
 
-template <bool REFINED, int L>
-__global__ void GBS_ROWS_BOUNDS(L) k_pcg_spmv(PcgArgs a) {
+template <bool REFINED, int L, int MB = SELL_MIN_CTAS>
+__global__ void GBS_ROWS_BOUNDS(L, MB) k_pcg_spmv(PcgArgs a) {
   __shared__ double red[RED_SCRATCH1];
   if (!trip_live(a)) return;
   stamp_phase(a, 1);
@@ -81,8 +84,8 @@ __global__ void __launch_bounds__(PHASE_TPB) k_pcg_direction(PcgArgs a) {
   phase_C<REFINED>(a, red);
 }
 
-template <int L>
-__global__ void GBS_ROWS_BOUNDS(L) k_pcg_final(PcgArgs a) {
+template <int L, int MB = SELL_MIN_CTAS>
+__global__ void GBS_ROWS_BOUNDS(L, MB) k_pcg_final(PcgArgs a) {
   __shared__ double red[RED_SCRATCH];
   stamp_phase(a, 4);
   phase_final<L>(a, red);
@@ -105,13 +108,17 @@ struct PhaseKernels {
   void (*final_)(PcgArgs);
 };
 
-template <bool R, int L>
+template <bool R, int L, int MB = SELL_MIN_CTAS>
 static PhaseKernels kernels_for() {
-  return PhaseKernels{k_pcg_setup<R, L>, k_pcg_spmv<R, L>, k_pcg_update<R>, k_pcg_direction<R>,
-                      k_pcg_final<L>};
+  return PhaseKernels{k_pcg_setup<R, L, MB>, k_pcg_spmv<R, L, MB>, k_pcg_update<R>,
+                      k_pcg_direction<R>, k_pcg_final<L, MB>};
 }
 
-static PhaseKernels phase_kernels(bool refined, int lanes) {
+// wide: the plan caps the grids at one or two CTAs per SM (wide_rows), so the
+// sliced-ELL row kernels compiled for two CTAs per SM run.
+static PhaseKernels phase_kernels(bool refined, int lanes, bool wide = false) {
+  if (lanes == GBS_SPMV_SELL && wide)
+    return refined ? kernels_for<true, 0, 2>() : kernels_for<false, 0, 2>();
   switch (lanes) {
     case 1: return refined ? kernels_for<true, 1>() : kernels_for<false, 1>();
     case 2: return refined ? kernels_for<true, 2>() : kernels_for<false, 2>();
@@ -306,8 +313,8 @@ static cudaKernelNodeParams kernel_node(void (*k)(PcgArgs), int grid, void **arg
 }
 
 // CG's loop: setup, WHILE { A (table A), B, C (table E) }, final (table A).
-static LoopPlan cg_plan(bool refined, int lanes) {
-  const PhaseKernels K = phase_kernels(refined, lanes);
+static LoopPlan cg_plan(bool refined, int lanes, bool wide = false) {
+  const PhaseKernels K = phase_kernels(refined, lanes, wide);
   LoopPlan P;
   memset(&P, 0, sizeof(P));
   P.npre = 1;
@@ -585,7 +592,7 @@ int solve(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool per_sys
       a.part_e = A->sa.nslots;
       a.grid_a = A->sa.grid;
       a.grid_e = A->se.grid;
-      GBS_TRY(run_loop(A, cg_plan(refined, A->lanes), refined ? GBS_GRAPH_CG32 : GBS_GRAPH_CG,
+      GBS_TRY(run_loop(A, cg_plan(refined, A->lanes, wide_rows(A)), refined ? GBS_GRAPH_CG32 : GBS_GRAPH_CG,
                        a, b, x, o, per_system, s));
     } else {
       GBS_TRY_CUDA(cudaMemsetAsync(A->st, 0, sizeof(SysState) * A->nsys, s));
@@ -602,7 +609,7 @@ int solve(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool per_sys
     }
     return GBS_OK;
   }
-  return run_loop(A, cg_plan(refined, A->lanes), refined ? GBS_GRAPH_CG32 : GBS_GRAPH_CG,
+  return run_loop(A, cg_plan(refined, A->lanes, wide_rows(A)), refined ? GBS_GRAPH_CG32 : GBS_GRAPH_CG,
                   make_args(A, per_system, refined), b, x, o, per_system, s);
 }
 

@@ -129,6 +129,9 @@ int32_t split_count(gbs_mat A);
 // systems_per_sm CTAs.
 bool cta_size_rule(gbs_mat A, bool per_system, int systems_per_sm);
 int sm_count(gbs_mat A);
+// The plan caps the phase kernels' grids at one or two CTAs per SM: its
+// sliced-ELL row kernels run in their 64-register build.
+inline bool wide_rows(gbs_mat A) { return A->ctas_per_sm == 1 || A->ctas_per_sm == 2; }
 
 __device__ __forceinline__ int sys_of(const PcgArgs &a, const BlockTable &t, int b) {
   return a.ensemble ? 0 : __ldg(t.sys + b);
