@@ -562,7 +562,8 @@ static int autotune(gbs_mat A, cudaStream_t s, Tuning *out, float *out_ms) {
   const int plans[][4] = {{0, 0, sk, 0},      {0, 0, la, 0},       {256, 512, sk, 0},
                           {512, 1024, sk, 0},  {0, 0, sk, 4},       {256, 2048, sk, 0},
                           {0, 0, sk, 2},       {0, 0, sk, 3},       {1024, 4096, sk, 0},
-                          {2048, 4096, sk, 0}, {4096, 8192, sk, 0}};
+                          {2048, 4096, sk, 0}, {4096, 8192, sk, 0}, {2048, 4096, sk, 2},
+                          {4096, 8192, sk, 2}};
   double *b = nullptr, *x = nullptr;
   GBS_TRY(dev_alloc(&b, A->nrows, s));
   GBS_TRY(dev_alloc(&x, A->nrows, s));
