@@ -1765,6 +1765,7 @@ static int build_transpose(gbs_mat A, cudaStream_t s) {
   T->nsys = ns;
   T->batched = A->batched;
   T->row_off_h = A->row_off_h;
+  T->sell_patterns = A->sell_patterns;
   int st = symbolic(T, (const int32_t *)ti.p, (const int32_t *)tj.p,
                     A->batched ? coo_off.data() : nullptr, s);
   if (st == GBS_OK) st = sell_build(T, s);

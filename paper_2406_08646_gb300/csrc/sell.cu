@@ -311,7 +311,10 @@ SellView sell_view(gbs_mat A) {
 // Rebuilds a sliced copy that exists (and its transpose's) with or without
 // column patterns; the cached graphs hold the old arrays and are dropped.
 int set_slice_patterns(gbs_mat A, bool on, cudaStream_t s) {
-  if (A->At) GBS_TRY(set_slice_patterns(A->At, on, s));
+  if (A->At && A->At->sell_patterns != on) {
+    GBS_TRY(set_slice_patterns(A->At, on, s));
+    drop_graphs(A);  // A's BiCG graphs hold the transpose's arrays
+  }
   if (A->sell_patterns == on) return GBS_OK;
   A->sell_patterns = on;
   if (!A->sell_row0) return GBS_OK;
