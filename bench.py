@@ -421,6 +421,10 @@ def run_suite(args):
         A.set_values(t(p.v))
         b, xt = t(p.b), t(p.extra["x_target"])
         x = torch.empty_like(b)
+        untuned_s, _ = _ev_time(stream, lambda: A.solve(b, x, rtol=1e-8), reps=reps)
+        import tempfile
+        A.autotune(os.path.join(tempfile.mkdtemp(prefix="gbs_bench_c4_"), "tuning.txt"))
+        force_patterns(A.h)
         tf, (_, rf) = _ev_time(stream, lambda: A.solve(b, x, rtol=1e-8), reps=reps)
         g = (x - xt).contiguous()
         ta, (lam, _, dldv, ra) = _ev_time(
@@ -431,9 +435,11 @@ def run_suite(args):
             args, tf,
             {"workload": "edge_diffusion_1024: 2D 5-point variable-coefficient diffusion, "
                          "kappa log-uniform [0.1, 10], seed 1004",
-             "nrows": p.nrows, "nnz": A.nnz, "ncoo": p.ncoo, "plan": A.plan()},
+             "nrows": p.nrows, "nnz": A.nnz, "ncoo": p.ncoo,
+             "plan": dict(A.plan(), patterns=A.slices()["pattern_slices"] > 0)},
             {"forward": {"s": tf, "iterations": rf["iterations"], "status": rf["status"],
-                         "true_rel_residual": rf["true_rel_residual"]},
+                         "true_rel_residual": rf["true_rel_residual"],
+                         "untuned_s": untuned_s, "tuning": A.tuning()},
              "adjoint": {"s": ta, "iterations": ra[0]["iterations"], "status": ra[0]["status"],
                          "true_rel_residual": ra[0]["true_rel_residual"],
                          "what": "A^T lambda = x - x_target solve plus the dL/dv scatter"},
