@@ -538,6 +538,9 @@ bool use_cta_solver(gbs_mat A, bool per_system) {
 int solve(gbs_mat A, const double *b, double *x, const ksp_opts &o, bool per_system,
           cudaStream_t s) {
   const bool refined = o.precision == GBS_FP32_REFINED;
+  // the sliced copy (a no-op once built; rebuilt here if switching its
+  // column patterns could not rebuild it)
+  if (A->lanes == GBS_SPMV_SELL) GBS_TRY(sell_build(A, s));
   // the handle's CG form: FP64 CG on the phase kernels may run as the
   // single-reduction loop (same iterates in exact arithmetic, two kernels per
   // iteration instead of three, or one)

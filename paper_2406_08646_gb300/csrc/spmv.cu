@@ -47,6 +47,7 @@ int launch_spmv(gbs_mat A, const double *x, double *y, cudaStream_t s) {
   if (A->nrows == 0) return GBS_OK;
   const int32_t n = (int32_t)A->nrows;
   if (A->lanes == GBS_SPMV_SELL) {
+    GBS_TRY(sell_build(A, s));  // a no-op once built
     const int64_t ns = A->nslices, per = PHASE_TPB / 32;
     const unsigned grid = (unsigned)std::min<int64_t>((ns + per - 1) / per, 1 << 20);
     k_spmv_sell<<<grid, PHASE_TPB, 0, s>>>(sell_view(A), A->sell_val, x, y, (int32_t)ns,
