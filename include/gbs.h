@@ -462,7 +462,7 @@ int mat_get_tuning(gbs_mat A, int32_t *solver, int32_t *cg_form, int64_t *split_
  * CG (rtol 0, every candidate the same work; a batched handle solves its
  * systems each on its own) once untimed and three times under CUDA events
  * on `stream`; the three fastest then each solve A x = A 1 to rtol 1e-8
- * once (timed), which catches what 30 iterations miss (a batch's systems
+ * once (timed; at most 4096 iterations), which catches what 30 iterations miss (a batch's systems
  * converging at different iterations), and the fastest of those becomes the
  * handle's plan, solver (mat_set_solver), CG form (mat_set_cg_form), split
  * row count (mat_set_split_rows) and pattern setting; on a batched handle

@@ -681,6 +681,7 @@ static int autotune(gbs_mat A, cudaStream_t s, Tuning *out, float *out_ms) {
     ksp_opts want, full;
     ksp_opts_default(&want);  // rtol 1e-8, the default iteration limit
     if (fill_opts(A, &want, full, per_system) != GBS_OK) full = o;
+    full.maxit = std::min(full.maxit, 4096);  // bounds the tuning time of hard systems
     float best_full = 1e30f;
     for (size_t k = 0; k < tried.size() && k < 3 && st == GBS_OK; ++k) {
       const Tuning &t = tried[k].second;
